@@ -1,0 +1,283 @@
+"""Seeded synthetic (read, candidate window) workloads.
+
+This module only makes inputs -- it holds none of the alignment arithmetic --
+and is the one piece both the oracle and the CUDA path consume.  The C
+generator (``synth.c``) is compiled with gcc on first use.
+
+Workload recipes (the paper's datasets -- dwgsim-simulated 100/250 nt reads at
+0.1% / 1% error with 30% indels, mapped against a genome -- are not available,
+so these stand in for the candidate windows its Stage E receives):
+
+``parity``      1,000 pairs; reads 100 bp; windows 150 bp holding the read
+                mutated (2% substitutions, 0.5% indels of length 1-3) at a
+                uniform offset in random flanks.
+``throughput``  1,000,000 pairs; reads 100 bp; windows 200 bp; same mutation
+                model; 20% of windows are random decoys.
+``uneven``      2,000,000 pairs; read length from {75:.20, 100:.30, 150:.25,
+                250:.15, 400:.07, 800:.03}; window = flank U(20,100) + mutated
+                read + flank U(20,100); divergence U(0.5%, 5%), 80% of events
+                substitutions and 20% indels; 10% of reads spliced: the window
+                holds the two halves of the mutated read around a random intron
+                of U{50..2000} bp that starts with GT and ends with AG.
+``filter``      500,000 reads of 150 bp, each with U{1..64} candidate windows
+                of 250 bp: one true window at U(1%, 3%) divergence, the other
+                candidates split 50/50 between paralog-like decoys (the read
+                mutated at U(5%, 20%)) and random windows.
+``fullmix``     reads as ``uneven`` with 15% spliced and U{1..32} candidates:
+                one true at U(1%, 5%), decoys paralog U(5%, 20%) or random.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "synth.c")
+_LIB_PATH = os.path.join(_HERE, "libsynth.so")
+
+KIND_TRUE, KIND_PARALOG, KIND_RANDOM = 0, 1, 2
+
+
+class SynthSpec(ctypes.Structure):
+    _fields_ = [
+        ("seed", ctypes.c_uint64),
+        ("n_reads", ctypes.c_int64),
+        ("n_len", ctypes.c_int32),
+        ("len_val", ctypes.c_int32 * 8),
+        ("len_w", ctypes.c_double * 8),
+        ("cand_min", ctypes.c_int32),
+        ("cand_max", ctypes.c_int32),
+        ("win_len", ctypes.c_int32),
+        ("flank_min", ctypes.c_int32),
+        ("flank_max", ctypes.c_int32),
+        ("div_lo", ctypes.c_double),
+        ("div_hi", ctypes.c_double),
+        ("indel_share", ctypes.c_double),
+        ("decoy_random", ctypes.c_double),
+        ("paralog_share", ctypes.c_double),
+        ("par_lo", ctypes.c_double),
+        ("par_hi", ctypes.c_double),
+        ("splice_frac", ctypes.c_double),
+        ("intron_min", ctypes.c_int32),
+        ("intron_max", ctypes.c_int32),
+    ]
+
+
+def _spec(seed, n_reads, lengths, cand=(1, 1), win_len=0, flanks=(20, 100), div=(0.025, 0.025),
+          indel_share=0.2, decoy_random=0.0, paralog_share=0.5, par=(0.05, 0.20), splice=0.0,
+          intron=(50, 2000)) -> SynthSpec:
+    s = SynthSpec()
+    s.seed = seed
+    s.n_reads = n_reads
+    s.n_len = len(lengths)
+    for k, (v, w) in enumerate(lengths):
+        s.len_val[k] = v
+        s.len_w[k] = w
+    s.cand_min, s.cand_max = cand
+    s.win_len = win_len
+    s.flank_min, s.flank_max = flanks
+    s.div_lo, s.div_hi = div
+    s.indel_share = indel_share
+    s.decoy_random = decoy_random
+    s.paralog_share = paralog_share
+    s.par_lo, s.par_hi = par
+    s.splice_frac = splice
+    s.intron_min, s.intron_max = intron
+    return s
+
+
+UNEVEN_LENGTHS = ((75, .20), (100, .30), (150, .25), (250, .15), (400, .07), (800, .03))
+
+
+def spec_for(name: str, seed: int = 0, n_reads: int | None = None) -> SynthSpec:
+    """The generator parameters of a named workload (n_reads overrides the size)."""
+    if name == "parity":
+        return _spec(seed, n_reads or 1000, ((100, 1.0),), win_len=150, div=(0.025, 0.025))
+    if name == "throughput":
+        return _spec(seed, n_reads or 1_000_000, ((100, 1.0),), win_len=200, div=(0.025, 0.025),
+                     decoy_random=0.2)
+    if name == "uneven":
+        return _spec(seed, n_reads or 2_000_000, UNEVEN_LENGTHS, flanks=(20, 100), div=(0.005, 0.05),
+                     splice=0.10, intron=(50, 2000))
+    if name == "filter":
+        return _spec(seed, n_reads or 500_000, ((150, 1.0),), cand=(1, 64), win_len=250, div=(0.01, 0.03),
+                     paralog_share=0.5, par=(0.05, 0.20))
+    if name == "fullmix":
+        return _spec(seed, n_reads or 10_000_000, UNEVEN_LENGTHS, cand=(1, 32), flanks=(20, 100),
+                     div=(0.01, 0.05), paralog_share=0.5, par=(0.05, 0.20), splice=0.15, intron=(50, 2000))
+    raise KeyError(name)
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lpthread"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        p, i64 = ctypes.c_void_p, ctypes.c_int64
+        lib.synth_headers.argtypes = [ctypes.POINTER(SynthSpec), p, p, ctypes.c_int]
+        lib.synth_window_lengths.argtypes = [ctypes.POINTER(SynthSpec), p, p, ctypes.c_int]
+        lib.synth_fill.argtypes = [ctypes.POINTER(SynthSpec), p, p, p, p, p, p, p, ctypes.c_int]
+        lib.synth_pack.argtypes = [p, i64, p]
+        lib.synth_pack.restype = None
+        lib.synth_unpack.argtypes = [p, i64, p]
+        lib.synth_unpack.restype = None
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def packed_nbytes(n_bases: int) -> int:
+    """Bytes of a 2-bit packed buffer of n_bases, rounded up to 16 bytes so
+    that aligned 16-byte loads of the last bases stay inside the buffer."""
+    return ((int(n_bases) + 3) // 4 + 15) // 16 * 16
+
+
+def pack(codes: np.ndarray) -> np.ndarray:
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    out = np.zeros(packed_nbytes(len(codes)), dtype=np.uint8)
+    _load().synth_pack(_ptr(codes), len(codes), _ptr(out))
+    return out
+
+
+def unpack(packed: np.ndarray, n_bases: int) -> np.ndarray:
+    packed = np.ascontiguousarray(packed, dtype=np.uint8)
+    out = np.zeros(n_bases, dtype=np.uint8)
+    _load().synth_unpack(_ptr(packed), int(n_bases), _ptr(out))
+    return out
+
+
+@dataclass
+class Workload:
+    """Reads and candidate windows in CSR form (offsets in bases).
+
+    Pair p aligns read ``pair_read[p]`` against window p.  Read r owns the
+    candidate pairs ``cand_offsets[r] .. cand_offsets[r+1]``."""
+    name: str
+    reads: np.ndarray            # uint8 codes, all reads back to back
+    read_offsets: np.ndarray     # int64, n_reads + 1
+    windows: np.ndarray          # uint8 codes, all windows back to back
+    window_offsets: np.ndarray   # int64, n_pairs + 1
+    pair_read: np.ndarray        # int64, n_pairs
+    cand_offsets: np.ndarray     # int64, n_reads + 1
+    kinds: np.ndarray            # uint8, n_pairs: 0 true, 1 paralog, 2 random
+    true_cand: np.ndarray        # int32, n_reads: index of the true candidate
+    _packed: dict = field(default_factory=dict, repr=False)
+
+    @property
+    def n_reads(self) -> int:
+        return len(self.read_offsets) - 1
+
+    @property
+    def n_pairs(self) -> int:
+        return len(self.window_offsets) - 1
+
+    @property
+    def read_lengths(self) -> np.ndarray:
+        return np.diff(self.read_offsets)
+
+    @property
+    def window_lengths(self) -> np.ndarray:
+        return np.diff(self.window_offsets)
+
+    @property
+    def pair_read_lengths(self) -> np.ndarray:
+        return self.read_lengths[self.pair_read]
+
+    def cells(self) -> int:
+        """Sum of m * n over pairs: the DP cells one full pass updates."""
+        return int(np.sum(self.pair_read_lengths.astype(np.int64) * self.window_lengths))
+
+    def packed_reads(self) -> np.ndarray:
+        if "reads" not in self._packed:
+            self._packed["reads"] = pack(self.reads)
+        return self._packed["reads"]
+
+    def packed_windows(self) -> np.ndarray:
+        if "windows" not in self._packed:
+            self._packed["windows"] = pack(self.windows)
+        return self._packed["windows"]
+
+    def pair_slice(self, pairs: np.ndarray) -> "Workload":
+        """A workload holding only the given pairs (one read copy per pair)."""
+        pairs = np.asarray(pairs, dtype=np.int64)
+        rl = self.pair_read_lengths[pairs]
+        wl = self.window_lengths[pairs]
+        roff = np.zeros(len(pairs) + 1, np.int64)
+        np.cumsum(rl, out=roff[1:])
+        woff = np.zeros(len(pairs) + 1, np.int64)
+        np.cumsum(wl, out=woff[1:])
+        reads = np.concatenate([self.reads[self.read_offsets[r]:self.read_offsets[r + 1]]
+                                for r in self.pair_read[pairs]]) if len(pairs) else np.zeros(0, np.uint8)
+        wins = np.concatenate([self.windows[self.window_offsets[p]:self.window_offsets[p + 1]]
+                               for p in pairs]) if len(pairs) else np.zeros(0, np.uint8)
+        return Workload(self.name + "[slice]", reads, roff, wins, woff, np.arange(len(pairs), dtype=np.int64),
+                        np.arange(len(pairs) + 1, dtype=np.int64), self.kinds[pairs].copy(),
+                        np.zeros(len(pairs), np.int32))
+
+
+def generate(name: str, seed: int = 0, n_reads: int | None = None, threads: int | None = None) -> Workload:
+    """Generate a named workload deterministically (independent of threads)."""
+    lib = _load()
+    spec = spec_for(name, seed, n_reads)
+    nt = threads or min(os.cpu_count() or 1, 32)
+    nr = int(spec.n_reads)
+    read_len = np.zeros(nr, np.int32)
+    n_cand = np.zeros(nr, np.int32)
+    rc = lib.synth_headers(ctypes.byref(spec), _ptr(read_len), _ptr(n_cand), nt)
+    if rc:
+        raise RuntimeError(f"synth_headers failed: {rc}")
+    cand_off = np.zeros(nr + 1, np.int64)
+    np.cumsum(n_cand, out=cand_off[1:])
+    n_pairs = int(cand_off[-1])
+    win_len = np.zeros(n_pairs, np.int32)
+    rc = lib.synth_window_lengths(ctypes.byref(spec), _ptr(cand_off), _ptr(win_len), nt)
+    if rc:
+        raise RuntimeError(f"synth_window_lengths failed: {rc}")
+    read_off = np.zeros(nr + 1, np.int64)
+    np.cumsum(read_len, out=read_off[1:])
+    win_off = np.zeros(n_pairs + 1, np.int64)
+    np.cumsum(win_len, out=win_off[1:])
+    reads = np.zeros(int(read_off[-1]), np.uint8)
+    wins = np.zeros(int(win_off[-1]), np.uint8)
+    kinds = np.zeros(n_pairs, np.uint8)
+    true_cand = np.zeros(nr, np.int32)
+    rc = lib.synth_fill(ctypes.byref(spec), _ptr(cand_off), _ptr(read_off), _ptr(win_off),
+                        _ptr(reads), _ptr(wins), _ptr(kinds), _ptr(true_cand), nt)
+    if rc:
+        raise RuntimeError(f"synth_fill failed: {rc}")
+    pair_read = np.repeat(np.arange(nr, dtype=np.int64), n_cand)
+    return Workload(name, reads, read_off, wins, win_off, pair_read, cand_off, kinds, true_cand)
+
+
+def random_pairs(n_pairs: int, m_range, n_range, seed: int = 0, alphabet: int = 4) -> Workload:
+    """Independent uniform pairs with lengths drawn from the given inclusive
+    ranges (edge-case and tie-heavy test inputs; alphabet < 4 forces ties)."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    ml = rng.integers(m_range[0], m_range[1] + 1, n_pairs)
+    nl = rng.integers(n_range[0], n_range[1] + 1, n_pairs)
+    roff = np.zeros(n_pairs + 1, np.int64)
+    np.cumsum(ml, out=roff[1:])
+    woff = np.zeros(n_pairs + 1, np.int64)
+    np.cumsum(nl, out=woff[1:])
+    reads = rng.integers(0, alphabet, int(roff[-1])).astype(np.uint8)
+    wins = rng.integers(0, alphabet, int(woff[-1])).astype(np.uint8)
+    return Workload("random", reads, roff, wins, woff, np.arange(n_pairs, dtype=np.int64),
+                    np.arange(n_pairs + 1, dtype=np.int64), np.full(n_pairs, KIND_RANDOM, np.uint8),
+                    np.zeros(n_pairs, np.int32))
