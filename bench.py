@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Benchmark of the batched Smith-Waterman hot path (one JSON line).
+
+A step aligns one whole batch -- classification, score pass and traceback to
+CIGAR -- through the C ABI with the inputs already resident in device memory.
+Default workload: 1,000,000 (read, window) pairs, reads 100 bp, windows 200 bp,
+2% substitutions + 0.5% indels, 20% random decoy windows (2.0e10 DP cells).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank aligns its own batch of the same size
+(weak scaling, no collective on the data path); the reported value is the
+cells of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SW GCUPS & reads/s, plain vs learned-filtered at ≥99.5% best-hit recall"
+SCORING = (5, -4, -10, -1)
+WORKLOADS = {
+    "throughput": "plain SW, 1M pairs: reads 100 bp, windows 200 bp (2% subst, 0.5% indels 1-3 bp), "
+                  "20% random decoys; score + end + CIGAR",
+    "uneven": "batched uneven SW, 2M pairs: reads 75-800 bp, windows read + 2 x U(20,100) flanks, "
+              "U(0.5%,5%) divergence, 10% spliced with 50-2000 bp introns; score + end + CIGAR",
+}
+# Algorithmic integer work of one DP cell (int32 form): E add-max, F add-max,
+# diagonal + substitution, H three-way max with 0, H + gap-open, substitution
+# select, running max -> 7 operations; one 16x2 instruction covers two cells.
+OPS_PER_CELL = 7.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="throughput")
+    ap.add_argument("--no-cigar", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+
+
+def _cpu_baseline(wl, budget_s: float) -> dict:
+    """The oracle, as it stands, on the host cores over a bounded sample."""
+    import numpy as np
+
+    import oracle
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(12345)
+    probe = np.sort(rng.choice(wl.n_pairs, min(wl.n_pairs, 4 * cores), replace=False))
+    sub = wl.pair_slice(probe)
+    t = time.perf_counter()
+    oracle.align_batch(sub.reads, sub.read_offsets, sub.windows, sub.window_offsets,
+                       scoring=oracle.Scoring(*SCORING), threads=cores)
+    rate = sub.cells() / max(time.perf_counter() - t, 1e-6)
+    n = int(min(wl.n_pairs, max(4 * cores, budget_s * rate / max(wl.cells() / wl.n_pairs, 1.0))))
+    pairs = np.sort(rng.choice(wl.n_pairs, n, replace=False))
+    sub = wl.pair_slice(pairs)
+    t = time.perf_counter()
+    oracle.align_batch(sub.reads, sub.read_offsets, sub.windows, sub.window_offsets,
+                       scoring=oracle.Scoring(*SCORING), threads=cores)
+    dt = time.perf_counter() - t
+    return {"value": sub.cells() / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{n} of {wl.n_pairs} pairs drawn uniformly (seed 12345), score + end + CIGAR, "
+                      f"{sub.cells():.3e} cells in {dt:.1f} s",
+            "reads_per_s": n / dt}
+
+
+def _traffic_record(kernel_file: str):
+    """DRAM bytes per launch of the score kernel from the committed ncu
+    summary, if it was captured from the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    src = open(kernel_file, "rb").read()
+    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return rec
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import synth
+    wl = synth.generate(args.workload, seed=0)
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(777)
+    # size each step so the whole run stays within a few minutes
+    per_step_s = max(2.0, 120.0 / max(args.steps + args.warmup, 1))
+    probe = wl.pair_slice(np.sort(rng.choice(wl.n_pairs, 4 * cores, replace=False)))
+    t = time.perf_counter()
+    oracle.align_batch(probe.reads, probe.read_offsets, probe.windows, probe.window_offsets,
+                       scoring=oracle.Scoring(*SCORING), threads=cores)
+    rate = probe.cells() / max(time.perf_counter() - t, 1e-6)
+    n = int(min(wl.n_pairs, max(4 * cores, per_step_s * rate / (wl.cells() / wl.n_pairs))))
+    times, cells = [], 0
+    for s in range(args.warmup + args.steps):
+        sub = wl.pair_slice(np.sort(rng.choice(wl.n_pairs, n, replace=False)))
+        t = time.perf_counter()
+        oracle.align_batch(sub.reads, sub.read_offsets, sub.windows, sub.window_offsets,
+                           scoring=oracle.Scoring(*SCORING), threads=cores)
+        dt = time.perf_counter() - t
+        if s >= args.warmup:
+            times.append(dt)
+            cells += sub.cells()
+    total = sum(times)
+    value = cells / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "sample_pairs_per_step": n},
+            "reads_per_s": n * args.steps / total,
+            "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} pairs per step drawn uniformly from the {wl.n_pairs}-pair batch"},
+            "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import numpy as np
+    import torch
+
+    import synth
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    import paper_1304_0681_gb300 as sw
+    from paper_1304_0681_gb300 import DeviceBatch, align
+
+    want_cigar = not args.no_cigar
+    wl = synth.generate(args.workload, seed=rank)
+    batch = DeviceBatch.from_packed(wl.packed_reads(), wl.read_offsets, wl.packed_windows(), wl.window_offsets,
+                                    cigar=want_cigar)
+    cells, n_reads = wl.cells(), wl.n_reads
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # integer roofline: measured 16x2 DPX add-max throughput
+    dpx_ops = sw.sw_alu_probe(1, 20000)
+    peak_gcups = dpx_ops * 2.0 / OPS_PER_CELL / 1e9
+
+    for _ in range(args.warmup):
+        align(batch, SCORING, cigar=want_cigar)
+    torch.cuda.synchronize()
+
+    sw.sw_phase_timing(True)
+    clocks = Clocks(local)
+    launches0 = sw.sw_launch_count()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms, phases = [], []
+    for _ in range(args.steps):
+        flush.zero_()  # write > L2 so every step starts cold
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        align(batch, SCORING, cigar=want_cigar, sync=False)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        phases.append(sw.sw_phase_times())
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = sw.sw_launch_count() - launches0 - 0
+    sw.sw_sync_status()
+    sw.sw_phase_timing(False)
+    total_ms = sum(step_ms)
+    if pg:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * cells * args.steps / (total_ms * 1e-3) / 1e9
+    reads_per_s = ws * n_reads * args.steps / (total_ms * 1e-3)
+
+    score_ms = statistics.mean(p[1] for p in phases)
+    tb_ms = statistics.mean(p[2] for p in phases)
+    cls_ms = statistics.mean(p[0] for p in phases)
+    achieved = cells / (score_ms * 1e-3) / 1e9
+    traffic = _traffic_record(os.path.join(ROOT, "paper_1304_0681_gb300", "csrc", "sw_score.cu"))
+
+    # end to end through the host entry point: pinned inputs in, results out
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h_reads, h_wins = pin(wl.packed_reads()), pin(wl.packed_windows())
+        h_roff, h_woff = pin(wl.read_offsets), pin(wl.window_offsets)
+        n = wl.n_pairs
+        h_score = torch.zeros(n, dtype=torch.int32).pin_memory()
+        h_end = torch.zeros(2 * n, dtype=torch.int32).pin_memory()
+        cig = None
+        h2d = sum(t.numel() * t.element_size() for t in (h_reads, h_wins, h_roff, h_woff))
+        d2h = (h_score.numel() + h_end.numel()) * 4
+        if want_cigar:
+            cap = 2 * wl.pair_read_lengths + 3
+            coff = np.zeros(n + 1, np.int64)
+            np.cumsum(cap, out=coff[1:])
+            h_coff = pin(coff)
+            h_ops = torch.zeros(int(coff[-1]), dtype=torch.int32).pin_memory()
+            h_nops = torch.zeros(n, dtype=torch.int32).pin_memory()
+            cig = (h_ops, h_coff, h_nops)
+            h2d += h_coff.numel() * 8
+            d2h += (h_ops.numel() + h_nops.numel()) * 4
+        sw.sw_batch_align_host(h_reads, h_roff, h_wins, h_woff, n, SCORING, h_score, h_end, cig)
+        e_times = []
+        for _ in range(max(3, min(args.steps, 5))):
+            t0 = time.perf_counter()
+            sw.sw_batch_align_host(h_reads, h_roff, h_wins, h_woff, n, SCORING, h_score, h_end, cig)
+            e_times.append(time.perf_counter() - t0)
+        e2e_s = sum(e_times) / len(e_times)
+        if pg:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": ws * cells / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "reads_per_s": ws * n_reads / e2e_s}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "i16x2+i32", "data": "synthetic",
+                "config": {"workload": WORKLOADS[args.workload], "pairs_per_gpu": wl.n_pairs,
+                           "cells_per_gpu": cells, "cigar": want_cigar, "scoring": list(SCORING),
+                           "l2": "256 MB buffer written between timed steps (inputs 75 MB < L2)"},
+                "reads_per_s": reads_per_s,
+                "phase_ms": {"classify": cls_ms, "score": score_ms, "traceback": tb_ms},
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gcups, "unit": "GCUPS",
+                             "frac": achieved / peak_gcups,
+                             "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                             "kernel": "k_score (score + end-cell pass)",
+                             "peak_basis": f"measured 16x2 DPX add-max rate {dpx_ops / 1e12:.2f} Tops/s "
+                                           f"x 2 cells / {OPS_PER_CELL:g} ops per cell"},
+                "clocks": clk, "gpu_launches": int(launches), "e2e": e2e}
+        if rank == 0 and not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * swgb.h -- C ABI of the GB300 batched Smith-Waterman library (libswgb.so).
+ *
+ * The library computes Stage E, task iii of "Concurrent and Accurate RNA
+ * Sequencing on Multicore Platforms" (Martinez et al., 2013): every read is
+ * aligned with the Smith-Waterman algorithm onto each of its extended / joined
+ * candidate alignment locations (CALs, "windows" below), returning the
+ * alignment, its score and its position (Section 2, Stage E).  The paper does
+ * not print the recurrence; the library implements the affine-gap (Gotoh)
+ * local alignment
+ *
+ *   E(i,j) = max(H(i,j-1) + o, E(i,j-1) + e)
+ *   F(i,j) = max(H(i-1,j) + o, F(i-1,j) + e)
+ *   H(i,j) = max(0, H(i-1,j-1) + s(r_i, w_j), E(i,j), F(i,j))
+ *
+ * (a gap of length k scores o + (k-1) e), with these tie-breaks:
+ *   end cell   among cells with H == score, the smallest window index j,
+ *              then the smallest read index i (0-based); score 0 -> (-1,-1);
+ *   traceback  from the end cell: stop at H == 0; prefer the diagonal (M),
+ *              then a deletion (D, gap in the read), then an insertion (I,
+ *              gap in the window); inside a gap, open where E == H + o.
+ *
+ * Conventions shared by every entry point
+ *  - Sequences are 2-bit packed, A=0 C=1 G=2 T=3, four bases per byte, base q
+ *    of a buffer in byte q/4 at bits 2*(q%4).  Sequence k of a set occupies
+ *    bases [offsets[k], offsets[k+1]) -- sequences are packed back to back
+ *    with no alignment padding.  A packed buffer must start on a 16-byte
+ *    boundary and hold sw_packed_bytes(total bases) bytes (whole 16-byte
+ *    blocks), which the library may read in full.
+ *  - Offsets are int64 counts of bases, non-decreasing, offsets[0] >= 0.
+ *  - Every pointer named "device" is device memory of the current CUDA device,
+ *    owned by the caller; the library keeps no reference after the call's
+ *    work completes.  The library owns only its cached scratch memory.
+ *  - Calls are stream-ordered on `stream` (NULL = legacy default stream).
+ *  - Return value: SW_OK or a negative SW_ERR_* code; no exception crosses the
+ *    ABI.  Problems in device-resident inputs (offsets out of order, lengths
+ *    out of range) are detected on the device; the call then returns
+ *    SW_ERR_DEVICE_INPUT and leaves the outputs unspecified.
+ */
+#ifndef SWGB_H
+#define SWGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *sw_stream_t; /* same handle as cudaStream_t */
+
+#define SW_OK 0
+#define SW_ERR_INVALID_ARG (-1)   /* NULL pointer, negative count, bad scoring */
+#define SW_ERR_CAPACITY (-2)      /* a CIGAR did not fit its CSR slot */
+#define SW_ERR_CUDA (-3)          /* a CUDA runtime call failed */
+#define SW_ERR_DEVICE_TIMEOUT (-4)/* a device-side wait hit its iteration limit */
+#define SW_ERR_UNSUPPORTED (-5)   /* a size beyond the documented limits */
+#define SW_ERR_DEVICE_INPUT (-6)  /* device-resident input failed validation */
+#define SW_ERR_INTERNAL (-7)      /* an internal consistency check failed */
+#define SW_ERR_NO_DEVICE (-8)     /* no usable sm_103 device */
+
+#define SW_MAX_READ_LEN 8192      /* bases; longer reads -> SW_ERR_DEVICE_INPUT */
+#define SW_MAX_WINDOW_LEN 1048575 /* bases */
+
+/* Scoring.  Requirements: 1 <= match <= 127, -127 <= mismatch <= 0,
+ * gap_open <= gap_extend <= 0, gap_open < 0, and match - gap_open <= 127
+ * (so every match / mismatch score minus gap_open fits a signed byte).  A gap of length k scores
+ * gap_open + (k-1) * gap_extend (pass o + e as gap_open for the o + k e
+ * convention). */
+typedef struct {
+    int32_t match;
+    int32_t mismatch;
+    int32_t gap_open;
+    int32_t gap_extend;
+} sw_scoring_t;
+
+/* CIGAR output in CSR form, all device memory owned by the caller.
+ * ops[offsets[p] .. offsets[p+1]) receives pair p's runs, BAM-encoded as
+ * (length << 4) | op with M=0, I=1, D=2, S=4 (leading and trailing soft clips
+ * included, M covering matches and mismatches); n_ops[p] receives the number
+ * of runs (0 when the score is 0).  A slot of sw_cigar_capacity(m) runs
+ * always suffices for a read of length m; a smaller slot that overflows makes
+ * the call return SW_ERR_CAPACITY with n_ops[p] = -1. */
+typedef struct {
+    uint32_t *ops;
+    const int64_t *offsets; /* n_pairs + 1 */
+    int32_t *n_ops;         /* n_pairs */
+} sw_cigar_t;
+
+/* Upper bound on the CIGAR runs of a read of length m: 2 m + 3 (at most m
+ * M/I runs, a D run between or around each, two soft clips). */
+int64_t sw_cigar_capacity(int64_t read_len);
+
+/* Bytes of a packed buffer holding n_bases: ceil(n_bases / 4) rounded up to
+ * a multiple of 16. */
+int64_t sw_packed_bytes(int64_t n_bases);
+
+/*
+ * sw_batch_align -- align pair p = (read p, window p) for p < n_pairs
+ * (Stage E, task iii: the read is mapped onto an extended CAL with SW).
+ *
+ *  reads, read_offsets        device; packed reads, n_pairs + 1 offsets
+ *  windows, window_offsets    device; packed windows, n_pairs + 1 offsets
+ *  n_pairs                    >= 0 (0 is a no-op)
+ *  scoring                    host pointer, see sw_scoring_t
+ *  out_score                  device int32[n_pairs]: the SW score (>= 0)
+ *  out_end                    device int32[2 * n_pairs]: (i_end, j_end) of
+ *                             pair p at [2p], [2p+1]; (-1, -1) when score 0
+ *  out_cigar                  host pointer to a struct of device pointers,
+ *                             or NULL for score and end only
+ *  stream                     CUDA stream
+ *
+ * Read length must be 1..SW_MAX_READ_LEN, window length 0..SW_MAX_WINDOW_LEN
+ * (an empty window gives score 0).  The call enqueues a classification
+ * kernel, waits for it on `stream` (it reads back a few hundred bytes of
+ * per-class counts to size the launches), then enqueues the alignment
+ * kernels and returns without waiting for them (sw_sync_status waits and
+ * reports errors the alignment kernels found).  Not capturable in a CUDA
+ * graph because of the mid-call wait.
+ */
+int sw_batch_align(const uint8_t *reads, const int64_t *read_offsets,
+                   const uint8_t *windows, const int64_t *window_offsets,
+                   int64_t n_pairs, const sw_scoring_t *scoring,
+                   int32_t *out_score, int32_t *out_end, sw_cigar_t *out_cigar,
+                   sw_stream_t stream);
+
+/*
+ * sw_batch_align_indexed -- as sw_batch_align, but pair p aligns read
+ * pair_read[p] (device int64[n_pairs], each in [0, n_reads)) against window p,
+ * so the candidate windows of one read share a single copy of it (Stage E
+ * maps each read onto all of its extended CALs).  read_offsets has
+ * n_reads + 1 entries.
+ */
+int sw_batch_align_indexed(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads,
+                           const uint8_t *windows, const int64_t *window_offsets,
+                           const int64_t *pair_read, int64_t n_pairs,
+                           const sw_scoring_t *scoring,
+                           int32_t *out_score, int32_t *out_end, sw_cigar_t *out_cigar,
+                           sw_stream_t stream);
+
+/*
+ * sw_batch_align_host -- the same alignment from HOST buffers: copies the
+ * inputs to the device (library-owned staging buffers), aligns, copies
+ * score, end and CIGAR back to the host buffers and waits for `stream`.
+ * Pointers are host memory (pinned memory makes the copies asynchronous);
+ * out_cigar's members are host pointers too.  Returns after the results are
+ * in host memory.
+ */
+int sw_batch_align_host(const uint8_t *reads, const int64_t *read_offsets,
+                        const uint8_t *windows, const int64_t *window_offsets,
+                        int64_t n_pairs, const sw_scoring_t *scoring,
+                        int32_t *out_score, int32_t *out_end, sw_cigar_t *out_cigar,
+                        sw_stream_t stream);
+
+/*
+ * Wait for `stream` and report problems the alignment kernels of the last
+ * call on this device detected on the device (SW_ERR_CAPACITY when a CIGAR
+ * slot overflowed, SW_ERR_INTERNAL when a consistency check failed).
+ * sw_batch_align returns once its kernels are enqueued, so a caller that
+ * wants those errors calls this after it.
+ */
+int sw_sync_status(sw_stream_t stream);
+
+/* Text of an SW_* code (static storage). */
+const char *sw_strerror(int code);
+
+/* Number of kernel launches the library issued since load (all entry points;
+ * counts launches, not completions). */
+int64_t sw_launch_count(void);
+
+/*
+ * Tuning.  The plan for reads of a length class is the number of lanes T
+ * that share one pair (or one pair of pairs in the 16-bit path) and the
+ * rows R each lane holds in registers.  sw_set_plan overrides the built-in
+ * choice for length classes whose longest read is <= max_read_len (0 clears
+ * all overrides); r_rows must be one of the compiled row counts (sw_plan_rows
+ * lists them), and lanes * r_rows must cover the reads unless lanes == 32
+ * (longer reads are then processed in chunks of 32 * r_rows rows).
+ */
+int sw_set_plan(int32_t max_read_len, int32_t lanes, int32_t r_rows);
+int sw_plan_rows(int32_t *rows, int32_t cap);
+
+/*
+ * Phase timing (measurement support).  With timing enabled, each call records
+ * CUDA events on its stream around its three phases; sw_phase_times waits for
+ * the last call and writes the milliseconds of (0) classification including
+ * the host read-back, (1) the score kernels, (2) the traceback kernels.
+ * Returns SW_ERR_INVALID_ARG if the last call was not timed.
+ */
+int sw_phase_timing(int32_t enable);
+int sw_phase_times(float *ms3);
+
+/*
+ * ALU throughput probe (measurement support, not part of the method): runs
+ * `iters` iterations of 8 independent chains of one instruction kind on every
+ * SM and writes the achieved instructions per second (warp-lane operations,
+ * i.e. 32 per warp instruction).  kind: 0 = 32-bit add-max (DPX), 1 = 16x2
+ * add-max (DPX), 2 = 16x2 three-way max (DPX), 3 = 32-bit integer add,
+ * 4 = byte permute, 5 = 32-bit multiply-add, 6 = a mix of kinds 1 and 5.
+ * Allocates and frees a small device buffer.
+ */
+int sw_alu_probe(int32_t kind, int64_t iters, double *ops_per_s, sw_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWGB_H */

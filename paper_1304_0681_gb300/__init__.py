@@ -1,0 +1,17 @@
+"""GB300 batched Smith-Waterman (Stage E, task iii of HPG-aligner).
+
+The compute path is the CUDA library ``libswgb.so`` (C ABI in
+``include/swgb.h``); ``_swgb`` binds it with ctypes and ``device`` moves
+workloads into device memory in the layout the ABI wants.  Nothing here
+computes an alignment on the CPU.
+"""
+from . import _swgb
+from ._swgb import (SwError, sw_alu_probe, sw_batch_align, sw_batch_align_host, sw_batch_align_indexed,
+                    sw_cigar_capacity, sw_launch_count, sw_packed_bytes, sw_phase_times, sw_phase_timing,
+                    sw_plan_rows, sw_set_plan, sw_strerror, sw_sync_status)
+from .device import DeviceBatch, align
+
+__all__ = ["SwError", "sw_alu_probe", "sw_batch_align", "sw_batch_align_host", "sw_batch_align_indexed",
+           "sw_cigar_capacity", "sw_launch_count", "sw_packed_bytes", "sw_phase_times", "sw_phase_timing",
+           "sw_plan_rows", "sw_set_plan", "sw_strerror",
+           "sw_sync_status", "DeviceBatch", "align", "_swgb"]

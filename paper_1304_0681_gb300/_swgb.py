@@ -1,0 +1,178 @@
+"""ctypes binding of libswgb.so (the C ABI in include/swgb.h).
+
+Argument marshalling only: every function forwards torch tensors' device
+pointers and the current stream to the entry point of the same name.  There
+is no fallback -- if the CUDA library is missing or fails to load, importing
+this module raises."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libswgb.so")
+
+SW_OK = 0
+ERRORS = {
+    -1: "SW_ERR_INVALID_ARG", -2: "SW_ERR_CAPACITY", -3: "SW_ERR_CUDA", -4: "SW_ERR_DEVICE_TIMEOUT",
+    -5: "SW_ERR_UNSUPPORTED", -6: "SW_ERR_DEVICE_INPUT", -7: "SW_ERR_INTERNAL", -8: "SW_ERR_NO_DEVICE",
+}
+
+#: every symbol include/swgb.h declares
+EXPORTS = ("sw_cigar_capacity", "sw_packed_bytes", "sw_batch_align", "sw_batch_align_indexed",
+           "sw_batch_align_host", "sw_sync_status", "sw_strerror", "sw_launch_count", "sw_set_plan",
+           "sw_plan_rows", "sw_alu_probe", "sw_phase_timing", "sw_phase_times")
+
+
+class SwError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({code})")
+        self.code = code
+
+
+class Scoring(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32),
+                ("gap_open", ctypes.c_int32), ("gap_extend", ctypes.c_int32)]
+
+
+class Cigar(ctypes.Structure):
+    _fields_ = [("ops", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("n_ops", ctypes.c_void_p)]
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library {path} is not built; run __graft_entry__.build() "
+                          "or python -m paper_1304_0681_gb300.build")
+    lib = ctypes.CDLL(path)
+    p, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.sw_cigar_capacity.argtypes = [i64]
+    lib.sw_cigar_capacity.restype = i64
+    lib.sw_packed_bytes.argtypes = [i64]
+    lib.sw_packed_bytes.restype = i64
+    lib.sw_batch_align.argtypes = [p, p, p, p, i64, ctypes.POINTER(Scoring), p, p, ctypes.POINTER(Cigar), p]
+    lib.sw_batch_align.restype = ctypes.c_int
+    lib.sw_batch_align_indexed.argtypes = [p, p, i64, p, p, p, i64, ctypes.POINTER(Scoring), p, p,
+                                           ctypes.POINTER(Cigar), p]
+    lib.sw_batch_align_indexed.restype = ctypes.c_int
+    lib.sw_batch_align_host.argtypes = [p, p, p, p, i64, ctypes.POINTER(Scoring), p, p, ctypes.POINTER(Cigar), p]
+    lib.sw_batch_align_host.restype = ctypes.c_int
+    lib.sw_sync_status.argtypes = [p]
+    lib.sw_sync_status.restype = ctypes.c_int
+    lib.sw_strerror.argtypes = [ctypes.c_int]
+    lib.sw_strerror.restype = ctypes.c_char_p
+    lib.sw_launch_count.argtypes = []
+    lib.sw_launch_count.restype = i64
+    lib.sw_set_plan.argtypes = [i32, i32, i32]
+    lib.sw_set_plan.restype = ctypes.c_int
+    lib.sw_plan_rows.argtypes = [p, i32]
+    lib.sw_plan_rows.restype = ctypes.c_int
+    lib.sw_phase_timing.argtypes = [i32]
+    lib.sw_phase_timing.restype = ctypes.c_int
+    lib.sw_phase_times.argtypes = [p]
+    lib.sw_phase_times.restype = ctypes.c_int
+    lib.sw_alu_probe.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_double), p]
+    lib.sw_alu_probe.restype = ctypes.c_int
+    return lib
+
+
+_lib = load()
+
+
+def _check(rc: int, what: str):
+    if rc != SW_OK:
+        raise SwError(rc, what)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _scoring(sc) -> Scoring:
+    return Scoring(*(int(x) for x in sc))
+
+
+def sw_cigar_capacity(read_len: int) -> int:
+    return int(_lib.sw_cigar_capacity(int(read_len)))
+
+
+def sw_packed_bytes(n_bases: int) -> int:
+    return int(_lib.sw_packed_bytes(int(n_bases)))
+
+
+def sw_batch_align(reads, read_offsets, windows, window_offsets, n_pairs: int, scoring, out_score, out_end,
+                   cigar=None, stream=None) -> None:
+    """cigar: None or (ops uint32/int32, offsets int64, n_ops int32) device tensors."""
+    cg = Cigar(*(t.data_ptr() for t in cigar)) if cigar is not None else None
+    sc = _scoring(scoring)
+    _check(_lib.sw_batch_align(_ptr(reads), _ptr(read_offsets), _ptr(windows), _ptr(window_offsets), int(n_pairs),
+                               ctypes.byref(sc), _ptr(out_score), _ptr(out_end),
+                               ctypes.byref(cg) if cg is not None else None, _stream(stream)),
+           "sw_batch_align")
+
+
+def sw_batch_align_indexed(reads, read_offsets, n_reads: int, windows, window_offsets, pair_read, n_pairs: int,
+                           scoring, out_score, out_end, cigar=None, stream=None) -> None:
+    cg = Cigar(*(t.data_ptr() for t in cigar)) if cigar is not None else None
+    sc = _scoring(scoring)
+    _check(_lib.sw_batch_align_indexed(_ptr(reads), _ptr(read_offsets), int(n_reads), _ptr(windows),
+                                       _ptr(window_offsets), _ptr(pair_read), int(n_pairs), ctypes.byref(sc),
+                                       _ptr(out_score), _ptr(out_end), ctypes.byref(cg) if cg is not None else None,
+                                       _stream(stream)), "sw_batch_align_indexed")
+
+
+def sw_batch_align_host(reads, read_offsets, windows, window_offsets, n_pairs: int, scoring, out_score, out_end,
+                        cigar=None, stream=None) -> None:
+    """Host (CPU, ideally pinned) tensors in and out."""
+    cg = Cigar(*(t.data_ptr() for t in cigar)) if cigar is not None else None
+    sc = _scoring(scoring)
+    _check(_lib.sw_batch_align_host(_ptr(reads), _ptr(read_offsets), _ptr(windows), _ptr(window_offsets),
+                                    int(n_pairs), ctypes.byref(sc), _ptr(out_score), _ptr(out_end),
+                                    ctypes.byref(cg) if cg is not None else None, _stream(stream)),
+           "sw_batch_align_host")
+
+
+def sw_sync_status(stream=None) -> None:
+    _check(_lib.sw_sync_status(_stream(stream)), "sw_sync_status")
+
+
+def sw_strerror(code: int) -> str:
+    return _lib.sw_strerror(int(code)).decode()
+
+
+def sw_launch_count() -> int:
+    return int(_lib.sw_launch_count())
+
+
+def sw_set_plan(max_read_len: int, lanes: int, rows: int) -> None:
+    _check(_lib.sw_set_plan(int(max_read_len), int(lanes), int(rows)), "sw_set_plan")
+
+
+def sw_plan_rows() -> list:
+    n = _lib.sw_plan_rows(None, 0)
+    buf = (ctypes.c_int32 * n)()
+    _lib.sw_plan_rows(ctypes.cast(buf, ctypes.c_void_p), n)
+    return list(buf)
+
+
+def sw_alu_probe(kind: int, iters: int, stream=None) -> float:
+    out = ctypes.c_double(0.0)
+    _check(_lib.sw_alu_probe(int(kind), int(iters), ctypes.byref(out), _stream(stream)), "sw_alu_probe")
+    return out.value
+
+
+def sw_phase_timing(enable: bool) -> None:
+    _check(_lib.sw_phase_timing(1 if enable else 0), "sw_phase_timing")
+
+
+def sw_phase_times() -> tuple:
+    """(classify_ms, score_ms, traceback_ms) of the last timed call."""
+    buf = (ctypes.c_float * 3)()
+    _check(_lib.sw_phase_times(ctypes.cast(buf, ctypes.c_void_p)), "sw_phase_times")
+    return tuple(buf)

@@ -1,0 +1,110 @@
+// sw_classify.cu -- validation and length-class ordering of a batch of pairs.
+//
+// Every pair gets a sort key (arithmetic mode, read-length class, window
+// length bucket in descending order).  A counting sort over the keys then
+// lays the pairs out class by class, longest windows first, so that each
+// class can run under its own lane plan and lanes that share a warp see
+// windows of similar length.
+#include "sw_device.cuh"
+#include "swgb_internal.h"
+
+namespace swgb {
+
+__global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring sc,
+                           int32_t *__restrict__ keys, int32_t *__restrict__ hist, ClassInfo *__restrict__ info,
+                           int32_t *__restrict__ out_score, int32_t *__restrict__ out_end,
+                           int32_t *__restrict__ cig_n)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_pairs;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t rd = ps.pair_read ? ps.pair_read[p] : p;
+        bool bad = rd < 0 || rd >= n_reads;
+        int64_t m = 0, n = 0;
+        if (!bad) {
+            const int64_t r0 = ps.read_off[rd], r1 = ps.read_off[rd + 1];
+            const int64_t w0 = ps.win_off[p], w1 = ps.win_off[p + 1];
+            m = r1 - r0;
+            n = w1 - w0;
+            bad = r0 < 0 || w0 < 0 || m < 1 || m > SW_MAX_READ_LEN || n < 0 || n > SW_MAX_WINDOW_LEN;
+        }
+        int32_t key = -1;
+        if (bad) {
+            atomicOr(&info->status, ST_BAD_INPUT);
+        } else if (n == 0) {
+            // an empty window aligns nothing: score 0, no end cell, no CIGAR
+            out_score[p] = 0;
+            out_end[2 * p] = -1;
+            out_end[2 * p + 1] = -1;
+            if (cig_n) cig_n[p] = 0;
+        } else {
+            const int64_t hmax = (int64_t)sc.ma * (m < n ? m : n);
+            int mode = MODE_I32;
+            if (hmax <= 1022) mode = MODE_I16;
+            else if (hmax <= 32000) mode = MODE_I16W;
+            const int cls = mode * N_MCLASS + mclass_of((int32_t)m);
+            int nb = (int)((n - 1) >> 5);
+            nb = nb > N_NBUCKET - 1 ? N_NBUCKET - 1 : nb;
+            key = cls * N_NBUCKET + (N_NBUCKET - 1 - nb);
+            atomicAdd(&hist[key], 1);
+            atomicAdd(&info->count[cls], 1);
+            atomicMax(&info->max_n[cls], (int32_t)n);
+            atomicMax(&info->max_m[cls], (int32_t)m);
+        }
+        keys[p] = key;
+    }
+}
+
+// Exclusive scan of the key histogram (one block).
+__global__ void k_scan(const int32_t *__restrict__ hist, int32_t *__restrict__ start, int32_t *__restrict__ cursor,
+                       int n)
+{
+    __shared__ int32_t part[1024];
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int per = (n + nt - 1) / nt;
+    const int b = t * per, e = min(n, b + per);
+    int32_t s = 0;
+    for (int i = b; i < e; ++i) s += hist[i];
+    part[t] = s;
+    __syncthreads();
+    for (int d = 1; d < nt; d <<= 1) {
+        int32_t v = t >= d ? part[t - d] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int32_t run = part[t] - s;
+    for (int i = b; i < e; ++i) {
+        start[i] = run;
+        cursor[i] = run;
+        run += hist[i];
+    }
+}
+
+__global__ void k_scatter(const int32_t *__restrict__ keys, int64_t n_pairs, int32_t *__restrict__ cursor,
+                          int32_t *__restrict__ order)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_pairs;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = keys[p];
+        if (k >= 0) order[atomicAdd(&cursor[k], 1)] = (int32_t)p;
+    }
+}
+
+int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring sc,
+                    int32_t *keys, int32_t *hist, int32_t *bucket_start, int32_t *cursor,
+                    ClassInfo *info, int32_t *order, int32_t *out_score, int32_t *out_end,
+                    int32_t *cig_n, cudaStream_t st)
+{
+    const int threads = 256;
+    int64_t blocks = (n_pairs + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_classify<<<(unsigned)blocks, threads, 0, st>>>(ps, n_reads, n_pairs, sc, keys, hist, info, out_score,
+                                                     out_end, cig_n);
+    k_scan<<<1, 1024, 0, st>>>(hist, bucket_start, cursor, N_CLASS * N_NBUCKET);
+    k_scatter<<<(unsigned)blocks, threads, 0, st>>>(keys, n_pairs, cursor, order);
+    count_launch(3);
+    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
+}  // namespace swgb

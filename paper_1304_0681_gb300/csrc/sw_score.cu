@@ -1,0 +1,392 @@
+// sw_score.cu -- the Smith-Waterman score pass (score and end cell).
+//
+// Stage E, task iii of the paper aligns every read onto each of its extended
+// CALs with Smith-Waterman.  This kernel computes, for each (read, window)
+// pair, the best local-alignment score of the affine-gap recurrence
+//
+//   E(i,j) = max(H(i,j-1) + o, E(i,j-1) + e)
+//   F(i,j) = max(H(i-1,j) + o, F(i-1,j) + e)
+//   H(i,j) = max(0, H(i-1,j-1) + s(r_i, w_j), E(i,j), F(i,j))
+//
+// and the cell where it is first reached (smallest window index j, then
+// smallest read index i).
+//
+// Work layout.  A group of T consecutive lanes of a warp owns one pair (int32
+// mode) or two pairs (int16 modes: pair A in the low and pair B in the high
+// half of every register, so each DPX instruction updates two cells).  Lane
+// k of a group holds read rows k*R .. k*R+R-1 of the current row chunk in
+// registers and sweeps the window columns; lane k works on column t-k at step
+// t, receiving the row above its block from lane k-1 with one shuffle per
+// value (a wavefront along the anti-diagonal).  Reads longer than T*R are
+// processed in chunks of T*R rows; the last lane of a chunk stores its bottom
+// row (H+o, F per column) to global scratch for the first lane of the next
+// chunk.  A warp takes floor(32/T) groups' worth of pairs at a time from a
+// length-sorted list with one atomic, and loops until the list is empty.
+//
+// Arithmetic.  Each lane keeps per row E(i,j) and H(i,j)+o.  E and F are
+// floored at 0: max(E, 0) obeys the same recurrence (because e <= 0) and
+// never changes H, which is floored at 0 anyway.  The substitution score
+// comes from one byte permute: per column a 4-byte table of s(x, w_j) - o for
+// the four read bases x, per row a selector that picks the row's read base
+// (and sign-replicates, which yields 0 or -1 -- i.e. an effective score of o
+// or o-1, below zero -- for rows past the read end).  Window columns past a
+// pair's end use an all-zero table, which likewise scores o.  Padded cells can
+// therefore only hold values strictly below some real cell's value (o < 0), so
+// they never become or tie the best cell and need no masking.
+//
+// (__vibmax_s16x2 is not used for the running best: the header's inline asm
+// writes the max before re-reading its first operand without an early-clobber
+// constraint, so with `x = __vibmax_s16x2(x, ...)` the compiler may alias the
+// two and the predicates then compare the max with itself.)
+//
+// Best cell.  Every cell's H is turned into a key H*32 + (31-r) (r = row in
+// the lane's block, so equal H prefers the smaller row); a three-way-max tree
+// gives the column's best key, and the lane's running best is replaced only
+// when the column's H is strictly larger (so the smallest column wins).  The
+// 16-bit keys need H <= 1022; pairs with larger possible scores use 32-bit
+// keys built from each half (MODE_I16W) or the int32 mode.
+#include "sw_device.cuh"
+#include "swgb_internal.h"
+
+namespace swgb {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+struct PairRef {
+    int64_t rs, ws;  // first base of read / window
+    int32_t m, n;    // lengths (m == 0: no pair)
+};
+
+__device__ __forceinline__ PairRef load_pair(const ScoreLaunch &L, int64_t item, bool on)
+{
+    PairRef pr{0, 0, 0, 0};
+    if (on && item < L.n_items) {
+        const int64_t p = L.order[item];
+        const int64_t rd = L.ps.pair_read ? L.ps.pair_read[p] : p;
+        pr.rs = L.ps.read_off[rd];
+        pr.m = (int32_t)(L.ps.read_off[rd + 1] - pr.rs);
+        pr.ws = L.ps.win_off[p];
+        pr.n = (int32_t)(L.ps.win_off[p + 1] - pr.ws);
+    }
+    return pr;
+}
+
+// Read base codes of rows i0 .. i0+R-1 (4 bits each, 8 per word); rows past
+// the read end get code 4 ("no base").
+template <int R>
+__device__ __forceinline__ void load_rows(const uint32_t *__restrict__ reads, const PairRef &p, int i0,
+                                          uint32_t (&codes)[(R + 7) / 8])
+{
+#pragma unroll
+    for (int q = 0; q < (R + 7) / 8; ++q) codes[q] = 0x44444444u;
+#pragma unroll
+    for (int q16 = 0; q16 < (R + 15) / 16; ++q16) {
+        const int row = i0 + 16 * q16;
+        const int cnt = min(16, p.m - row);
+        if (cnt > 0) {
+            uint32_t w = load_bases(reads, p.rs + row, cnt);
+#pragma unroll
+            for (int b = 0; b < 16; ++b) {
+                const int r = 16 * q16 + b;
+                if (r < R && b < cnt) {
+                    uint32_t &c = codes[r / 8];
+                    const int sh = 4 * (r % 8);
+                    c = (c & ~(0xFu << sh)) | (((w >> (2 * b)) & 3u) << sh);
+                }
+            }
+        }
+    }
+}
+
+template <int MODE>
+struct Arith;
+
+template <>
+struct Arith<MODE_I32> {
+    typedef int32_t V;
+    static __device__ __forceinline__ V addmax(V a, V b, V c) { return __viaddmax_s32(a, b, c); }
+    static __device__ __forceinline__ V addmax_relu(V a, V b, V c) { return __viaddmax_s32_relu(a, b, c); }
+    static __device__ __forceinline__ V max_relu(V a, V b) { return __vimax_s32_relu(a, b); }
+    static __device__ __forceinline__ V add(V a, V b) { return a + b; }
+    static __device__ __forceinline__ V splat(int32_t x) { return x; }
+};
+
+template <>
+struct Arith<MODE_I16> {
+    typedef uint32_t V;
+    static __device__ __forceinline__ V addmax(V a, V b, V c) { return __viaddmax_s16x2(a, b, c); }
+    static __device__ __forceinline__ V addmax_relu(V a, V b, V c) { return __viaddmax_s16x2_relu(a, b, c); }
+    static __device__ __forceinline__ V max_relu(V a, V b) { return __vimax_s16x2_relu(a, b); }
+    // per-half add of a constant (no carry between halves): max(a + b, -32768)
+    static __device__ __forceinline__ V add(V a, V b) { return __viaddmax_s16x2(a, b, 0x80008000u); }
+    static __device__ __forceinline__ V splat(int32_t x) { return ((uint32_t)(uint16_t)(int16_t)x) * 0x10001u; }
+};
+template <>
+struct Arith<MODE_I16W> : Arith<MODE_I16> {};
+
+// Column table: byte x = s(x, w) - o for read base x, or all zero when the
+// column is padding.
+__device__ __forceinline__ uint32_t col_table(uint32_t w, bool valid, uint32_t mis4, uint32_t ma4)
+{
+    const uint32_t t = prmt(mis4, ma4, 0x3210u + (4u << (w * 4u)));
+    return valid ? t : 0u;
+}
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
+{
+    typedef Arith<MODE> A;
+    typedef typename A::V V;
+    constexpr bool PAIR2 = MODE != MODE_I32;
+    constexpr int NW = (R + 7) / 8;
+
+    const int lane = threadIdx.x & 31;
+    const int T = L.lanes;
+    const int G = 32 / T;
+    const int g = lane / T;
+    const int k = lane - g * T;
+    const bool on = g < G;
+    const int per_warp = G * (PAIR2 ? 2 : 1);
+    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+
+    const int32_t go = L.sc.go, ge = L.sc.ge;
+    const V GO = A::splat(go), GE = A::splat(ge);
+    const uint32_t mis4 = ((uint32_t)(uint8_t)(int8_t)(L.sc.mi - go)) * 0x01010101u;
+    const uint32_t ma4 = ((uint32_t)(uint8_t)(int8_t)(L.sc.ma - go)) * 0x01010101u;
+
+    uint8_t *bnd = L.boundary ? L.boundary + (warp_global * G + g) * L.boundary_group_bytes : nullptr;
+    const int64_t bnd_half = L.boundary_group_bytes / 2;  // bytes per buffer of the double buffer
+
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(L.work_counter, per_warp);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= L.n_items) break;
+
+        const int64_t item = base + (int64_t)g * (PAIR2 ? 2 : 1);
+        const PairRef pa = load_pair(L, item, on);
+        const PairRef pb = PAIR2 ? load_pair(L, item + 1, on) : PairRef{0, 0, 0, 0};
+        const int32_t mg = max(pa.m, pb.m), ng = max(pa.n, pb.n);
+        const int32_t mw = __reduce_max_sync(FULL, (unsigned)mg);
+        const int32_t nw = __reduce_max_sync(FULL, (unsigned)ng);
+        const int rows_per_chunk = T * R;
+        const int chunks = (mw + rows_per_chunk - 1) / rows_per_chunk;
+        const int steps = nw + T - 1;
+
+        uint64_t bestA = 0, bestB = 0;
+
+        for (int c = 0; c < chunks; ++c) {
+            const int i0 = c * rows_per_chunk + k * R;
+            // per-row selectors
+            uint32_t sel[R];
+            {
+                uint32_t ca[NW], cb[NW];
+                load_rows<R>(L.ps.reads, pa, i0, ca);
+                if (PAIR2) load_rows<R>(L.ps.reads, pb, i0, cb);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t xa = (ca[r / 8] >> (4 * (r % 8))) & 0xFu;
+                    if (!PAIR2) {
+                        sel[r] = xa < 4u ? xa * 0x1111u + 0x8880u : 0x8888u;
+                    } else {
+                        const uint32_t xb = (cb[r / 8] >> (4 * (r % 8))) & 0xFu;
+                        const uint32_t sa = xa < 4u ? xa * 0x11u + 0x80u : 0x88u;
+                        const uint32_t sb = xb < 4u ? xb * 0x11u + 0xC4u : 0xCCu;
+                        sel[r] = sa | (sb << 8);
+                    }
+                }
+            }
+            V e[R], ho[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                e[r] = 0;
+                ho[r] = GO;
+            }
+            V diag_in = GO;           // H(i0-1, j-1) + o
+            V out_ho = GO, out_f = 0;  // bottom row handed to the next lane
+            // running best of this chunk
+            uint32_t bk0 = PAIR2 && MODE == MODE_I16 ? 0x001F001Fu : 0u, bk1 = 0u;
+            uint32_t rowA = 0, rowB = 0;
+            int32_t jA = 0, jB = 0;
+            // window stream
+            uint32_t wwA = 0, wwB = 0;
+            const bool load_bnd = c > 0;
+            const bool store_bnd = c + 1 < chunks;
+            const V *bin = load_bnd ? (const V *)(bnd + (c & 1) * bnd_half) : nullptr;
+            V *bout = store_bnd ? (V *)(bnd + ((c + 1) & 1) * bnd_half) : nullptr;
+
+            for (int t = 0; t < steps; ++t) {
+                const int j = t - k;
+                V up_ho = __shfl_up_sync(FULL, out_ho, 1);
+                V up_f = __shfl_up_sync(FULL, out_f, 1);
+                if (k == 0) {
+                    if (load_bnd && j < ng) {
+                        up_ho = bin[2 * j];
+                        up_f = bin[2 * j + 1];
+                    } else {
+                        up_ho = GO;
+                        up_f = 0;
+                    }
+                }
+                // window bases of this column
+                uint32_t twA = 0, twB = 0;
+                if (j >= 0) {
+                    if ((j & 15) == 0) {
+                        wwA = j < pa.n ? load_bases(L.ps.wins, pa.ws + j, min(16, pa.n - j)) : 0u;
+                        if (PAIR2) wwB = j < pb.n ? load_bases(L.ps.wins, pb.ws + j, min(16, pb.n - j)) : 0u;
+                    }
+                    twA = col_table(wwA & 3u, j < pa.n, mis4, ma4);
+                    wwA >>= 2;
+                    if (PAIR2) {
+                        twB = col_table(wwB & 3u, j < pb.n, mis4, ma4);
+                        wwB >>= 2;
+                    }
+                }
+                V hd = diag_in, hu = up_ho, f = up_f;
+                uint32_t ck0 = 0, ck1 = 0;  // column keys
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const V s = (V)prmt(twA, twB, sel[r]);
+                    e[r] = A::addmax_relu(e[r], GE, ho[r]);
+                    f = A::addmax_relu(f, GE, hu);
+                    const V h = A::addmax(hd, s, A::max_relu(e[r], f));
+                    hd = ho[r];
+                    ho[r] = A::add(h, GO);
+                    hu = ho[r];
+                    if (MODE == MODE_I32) {
+                        const uint32_t key = (uint32_t)h * 32u + (uint32_t)(31 - r);
+                        ck0 = r == 0 ? key : max(ck0, key);
+                    } else if (MODE == MODE_I16) {
+                        const uint32_t key = (uint32_t)h * 32u + (uint32_t)(31 - r) * 0x10001u;
+                        ck0 = r == 0 ? key : __vimax3_s16x2(ck0, key, key);
+                    } else {
+                        const uint32_t ka = (uint32_t)h * 65536u + (uint32_t)(31 - r);
+                        const uint32_t kb = ((uint32_t)h & 0xFFFF0000u) | (uint32_t)(31 - r);
+                        ck0 = r == 0 ? ka : max(ck0, ka);
+                        ck1 = r == 0 ? kb : max(ck1, kb);
+                    }
+                }
+                diag_in = up_ho;
+                out_ho = ho[R - 1];
+                out_f = f;
+                if (store_bnd && k == T - 1 && j >= 0 && j < ng) {
+                    bout[2 * j] = out_ho;
+                    bout[2 * j + 1] = out_f;
+                }
+                // strict improvement of H keeps the first (smallest) column
+                if (MODE == MODE_I32) {
+                    if (ck0 > (bk0 | 31u)) {
+                        bk0 = ck0;
+                        jA = j;
+                    }
+                } else if (MODE == MODE_I16) {
+                    // per-half max of H*32+31; a half that rose is a strict
+                    // improvement of H (keys are >= 0, so the relu max is exact)
+                    const uint32_t nb = __vimax_s16x2_relu(bk0, ck0 | 0x001F001Fu);
+                    const uint32_t up = nb ^ bk0;
+                    bk0 = nb;
+                    if (up & 0xFFFFu) { rowA = ck0; jA = j; }
+                    if (up > 0xFFFFu) { rowB = ck0; jB = j; }
+                } else {
+                    if (ck0 > (bk0 | 0xFFFFu)) { bk0 = ck0; jA = j; }
+                    if (ck1 > (bk1 | 0xFFFFu)) { bk1 = ck1; jB = j; }
+                }
+            }
+            // fold the chunk's best into the 64-bit per-lane best
+            const int rbase = c * rows_per_chunk + k * R;
+            if (MODE == MODE_I32) {
+                const uint32_t h = bk0 >> 5;
+                if (h) bestA = max(bestA, cell_key(h, jA, rbase + 31 - (int)(bk0 & 31u)));
+            } else if (MODE == MODE_I16) {
+                const uint32_t ha = (bk0 & 0xFFFFu) >> 5, hb = (bk0 >> 16) >> 5;
+                if (ha) bestA = max(bestA, cell_key(ha, jA, rbase + 31 - (int)(rowA & 31u)));
+                if (hb) bestB = max(bestB, cell_key(hb, jB, rbase + 31 - (int)((rowB >> 16) & 31u)));
+            } else {
+                const uint32_t ha = bk0 >> 16, hb = bk1 >> 16;
+                if (ha) bestA = max(bestA, cell_key(ha, jA, rbase + 31 - (int)(bk0 & 0xFFFFu)));
+                if (hb) bestB = max(bestB, cell_key(hb, jB, rbase + 31 - (int)(bk1 & 0xFFFFu)));
+            }
+            __syncwarp();
+        }
+        // group reduction: lane k = 0 ends with the group's best
+        for (int d = 1; d < T; d <<= 1) {
+            const int src = (k + d < T) ? lane + d : lane;
+            bestA = max(bestA, __shfl_sync(FULL, bestA, src));
+            if (PAIR2) bestB = max(bestB, __shfl_sync(FULL, bestB, src));
+        }
+        if (on && k == 0) {
+#pragma unroll
+            for (int h2 = 0; h2 < (PAIR2 ? 2 : 1); ++h2) {
+                const int64_t it = item + h2;
+                if (it < L.n_items) {
+                    const uint64_t b = h2 ? bestB : bestA;
+                    const int32_t p = L.order[it];
+                    const uint32_t sc = key_h(b);
+                    L.out_score[p] = (int32_t)sc;
+                    L.out_end[2 * p] = sc ? key_i(b) : -1;
+                    L.out_end[2 * p + 1] = sc ? key_j(b) : -1;
+                }
+            }
+        }
+    }
+}
+
+const int kScoreRows[N_SCORE_ROWS] = {8, 16, 20, 25, 32};
+
+template <int R>
+static int launch_r(int mode, const ScoreLaunch &L, int blocks, int threads, cudaStream_t st)
+{
+    switch (mode) {
+    case MODE_I32: k_score<R, MODE_I32><<<blocks, threads, 0, st>>>(L); break;
+    case MODE_I16: k_score<R, MODE_I16><<<blocks, threads, 0, st>>>(L); break;
+    case MODE_I16W: k_score<R, MODE_I16W><<<blocks, threads, 0, st>>>(L); break;
+    default: return SW_ERR_INTERNAL;
+    }
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
+int launch_score(int rows, int mode, const ScoreLaunch &L, int blocks, int threads, cudaStream_t st)
+{
+    switch (rows) {
+    case 8: return launch_r<8>(mode, L, blocks, threads, st);
+    case 16: return launch_r<16>(mode, L, blocks, threads, st);
+    case 20: return launch_r<20>(mode, L, blocks, threads, st);
+    case 25: return launch_r<25>(mode, L, blocks, threads, st);
+    case 32: return launch_r<32>(mode, L, blocks, threads, st);
+    default: return SW_ERR_INVALID_ARG;
+    }
+}
+
+template <int R>
+static const void *kernel_ptr(int mode)
+{
+    switch (mode) {
+    case MODE_I32: return (const void *)k_score<R, MODE_I32>;
+    case MODE_I16: return (const void *)k_score<R, MODE_I16>;
+    case MODE_I16W: return (const void *)k_score<R, MODE_I16W>;
+    default: return nullptr;
+    }
+}
+
+int score_kernel_regs(int rows, int mode, int *regs, int *max_blocks_per_sm, int threads)
+{
+    const void *fn = nullptr;
+    switch (rows) {
+    case 8: fn = kernel_ptr<8>(mode); break;
+    case 16: fn = kernel_ptr<16>(mode); break;
+    case 20: fn = kernel_ptr<20>(mode); break;
+    case 25: fn = kernel_ptr<25>(mode); break;
+    case 32: fn = kernel_ptr<32>(mode); break;
+    default: return SW_ERR_INVALID_ARG;
+    }
+    if (!fn) return SW_ERR_INVALID_ARG;
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) return SW_ERR_CUDA;
+    *regs = a.numRegs;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, fn, threads, 0) != cudaSuccess)
+        return SW_ERR_CUDA;
+    return SW_OK;
+}
+
+}  // namespace swgb

@@ -1,0 +1,516 @@
+// swgb_api.cu -- host side of the C ABI declared in include/swgb.h.
+//
+// One call = classify (validate, sort pairs by length class) -> read back the
+// per-class counts -> per class: score pass, then (when a CIGAR is wanted)
+// traceback pass.  Scratch memory is owned by the library, cached per device
+// and grown on demand; calls on one device are serialised through an event so
+// that two calls never share scratch concurrently.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "sw_device.cuh"
+#include "swgb_internal.h"
+
+namespace swgb {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int n) { g_launches += n; }
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kMaxDevices = 64;
+
+struct Buffer {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct PlanOverride {
+    int32_t max_read_len, lanes, rows;
+};
+
+struct DeviceState {
+    bool ready = false;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    Buffer fixed, dyn;
+    Buffer stage;            // sw_batch_align_host device staging
+    ClassInfo *info_host = nullptr;  // pinned
+    cudaEvent_t last_done = nullptr;
+    bool last_recorded = false;
+    int32_t *last_status = nullptr;  // device status word of the last call
+    bool timing = false;             // record phase events (sw_phase_times)
+    bool timed_cells_valid = false;
+    cudaEvent_t phase[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::mutex mu;
+};
+
+DeviceState g_dev[kMaxDevices];
+std::mutex g_plan_mu;
+std::vector<PlanOverride> g_plans;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int ensure(Buffer &b, size_t bytes)
+{
+    if (b.bytes >= bytes) return SW_OK;
+    // pending work may still use the old buffer
+    if (cudaDeviceSynchronize() != cudaSuccess) return SW_ERR_CUDA;
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    const size_t want = align_up(bytes + bytes / 4, 1 << 20);
+    if (cudaMalloc(&b.ptr, want) != cudaSuccess) {
+        cudaGetLastError();
+        return SW_ERR_CUDA;
+    }
+    b.bytes = want;
+    return SW_OK;
+}
+
+int device_state(DeviceState **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SW_ERR_NO_DEVICE;
+    DeviceState &s = g_dev[dev];
+    if (!s.ready) {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return SW_ERR_NO_DEVICE;
+        s.sm_count = prop.multiProcessorCount;
+        s.cc_major = prop.major;
+        s.cc_minor = prop.minor;
+        if (cudaMallocHost(&s.info_host, sizeof(ClassInfo)) != cudaSuccess) return SW_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&s.last_done, cudaEventDisableTiming) != cudaSuccess) return SW_ERR_CUDA;
+        for (cudaEvent_t &e : s.phase)
+            if (cudaEventCreate(&e) != cudaSuccess) return SW_ERR_CUDA;
+        s.ready = true;
+    }
+    *out = &s;
+    return SW_OK;
+}
+
+bool scoring_ok(const sw_scoring_t *s)
+{
+    return s && s->match >= 1 && s->match <= 127 && s->mismatch >= -127 && s->mismatch <= 0 &&
+           s->gap_open <= s->gap_extend && s->gap_extend <= 0 && s->gap_open < 0 &&
+           s->match - s->gap_open <= 127;
+}
+
+int status_to_code(int32_t st)
+{
+    if (st & ST_BAD_INPUT) return SW_ERR_DEVICE_INPUT;
+    if (st & ST_UNSUPPORTED) return SW_ERR_UNSUPPORTED;
+    if (st & ST_CAPACITY) return SW_ERR_CAPACITY;
+    if (st & ST_TIMEOUT) return SW_ERR_DEVICE_TIMEOUT;
+    if (st & ST_INTERNAL) return SW_ERR_INTERNAL;
+    return SW_OK;
+}
+
+struct Plan {
+    int lanes, rows;
+};
+
+// Lanes per group and rows per lane for reads up to m_max in a mode.
+Plan choose_plan(int mode, int32_t m_max)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        for (const PlanOverride &o : g_plans)
+            if (m_max <= o.max_read_len) return Plan{o.lanes, o.rows};
+    }
+    (void)mode;
+    // estimated issue cost per pair-column: padded rows x ~7.5 ops + ~25 ops
+    // per lane-step, scaled by the fraction of lanes a warp leaves idle
+    double best = 1e300;
+    Plan bp{32, 32};
+    for (int ri = 0; ri < N_SCORE_ROWS; ++ri) {
+        const int R = kScoreRows[ri];
+        for (int T = 1; T <= 32; ++T) {
+            const int chunks = (m_max + T * R - 1) / (T * R);
+            if (chunks > 1 && T < 32) continue;
+            const int G = 32 / T;
+            const double lane_util = (double)(G * T) / 32.0;
+            const double cost = chunks * (double)T * (R * 7.5 + 25.0) / lane_util;
+            if (cost < best - 1e-9) {
+                best = cost;
+                bp = Plan{T, R};
+            }
+        }
+    }
+    return bp;
+}
+
+int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scoring_t *scoring,
+              int32_t *out_score, int32_t *out_end, const sw_cigar_t *cig, cudaStream_t st)
+{
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    if (ds->last_recorded && cudaStreamWaitEvent(st, ds->last_done, 0) != cudaSuccess) return SW_ERR_CUDA;
+
+    const Scoring sc{scoring->match, scoring->mismatch, scoring->gap_open, scoring->gap_extend};
+    const size_t nh = (size_t)N_CLASS * N_NBUCKET;
+    size_t off = 0;
+    const size_t o_keys = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
+    const size_t o_order = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
+    const size_t o_hist = off; off = align_up(off + sizeof(int32_t) * nh, 256);
+    const size_t o_bstart = off; off = align_up(off + sizeof(int32_t) * nh, 256);
+    const size_t o_cursor = off; off = align_up(off + sizeof(int32_t) * nh, 256);
+    const size_t o_info = off; off = align_up(off + sizeof(ClassInfo), 256);
+    const size_t o_counters = off; off = align_up(off + sizeof(int32_t) * 2 * N_CLASS, 256);
+    if ((rc = ensure(ds->fixed, off))) return rc;
+    uint8_t *fx = (uint8_t *)ds->fixed.ptr;
+    int32_t *keys = (int32_t *)(fx + o_keys), *order = (int32_t *)(fx + o_order);
+    int32_t *hist = (int32_t *)(fx + o_hist), *bstart = (int32_t *)(fx + o_bstart);
+    int32_t *cursor = (int32_t *)(fx + o_cursor), *counters = (int32_t *)(fx + o_counters);
+    ClassInfo *info = (ClassInfo *)(fx + o_info);
+    ds->last_status = &info->status;
+
+    ds->timed_cells_valid = false;
+    if (ds->timing && cudaEventRecord(ds->phase[0], st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cudaMemsetAsync(hist, 0, sizeof(int32_t) * nh, st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cudaMemsetAsync(info, 0, sizeof(ClassInfo), st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cudaMemsetAsync(counters, 0, sizeof(int32_t) * 2 * N_CLASS, st) != cudaSuccess) return SW_ERR_CUDA;
+    if ((rc = launch_classify(ps, n_reads, n_pairs, sc, keys, hist, bstart, cursor, info, order, out_score,
+                              out_end, cig ? cig->n_ops : nullptr, st)))
+        return rc;
+    if (cudaMemcpyAsync(ds->info_host, info, sizeof(ClassInfo), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SW_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
+    const ClassInfo ci = *ds->info_host;
+    if (ci.status) return status_to_code(ci.status);
+
+    // class ranges in the sorted order, plans and scratch needs
+    struct ClassRun {
+        int cls, mode;
+        int64_t start, count;
+        int32_t max_m, max_n;
+        Plan plan;
+        int tb_lanes;
+        int score_blocks, tb_blocks;
+        size_t bnd_bytes_group, slab_words_group, tb_bnd_ints_group;
+    };
+    std::vector<ClassRun> runs;
+    int64_t pos = 0;
+    size_t need_dyn = 0;
+    for (int cls = 0; cls < N_CLASS; ++cls) {
+        const int32_t cnt = ci.count[cls];
+        if (!cnt) continue;
+        ClassRun r{};
+        r.cls = cls;
+        r.mode = cls / N_MCLASS;
+        r.start = pos;
+        r.count = cnt;
+        r.max_m = ci.max_m[cls];
+        r.max_n = ci.max_n[cls];
+        pos += cnt;
+        r.plan = choose_plan(r.mode, r.max_m);
+        int regs = 0, bps = 0;
+        if ((rc = score_kernel_regs(r.plan.rows, r.mode, &regs, &bps, kThreads))) return rc;
+        if (bps < 1) return SW_ERR_INTERNAL;
+        const int G = 32 / r.plan.lanes;
+        const int per_warp = G * (r.mode == MODE_I32 ? 1 : 2);
+        const int64_t warps_needed = (cnt + per_warp - 1) / per_warp;
+        const int64_t wpb = kThreads / 32;
+        int64_t blocks = std::min<int64_t>((warps_needed + wpb - 1) / wpb, (int64_t)bps * ds->sm_count);
+        r.score_blocks = (int)std::max<int64_t>(blocks, 1);
+        const int chunks = (r.max_m + r.plan.lanes * r.plan.rows - 1) / (r.plan.lanes * r.plan.rows);
+        r.bnd_bytes_group = chunks > 1 ? (size_t)2 * r.max_n * 2 * sizeof(uint32_t) : 0;
+        size_t need = r.bnd_bytes_group * (size_t)r.score_blocks * wpb * G;
+        if (cig) {
+            r.tb_lanes = std::min(32, (r.max_m + TB_ROWS - 1) / TB_ROWS);
+            const int Gt = 32 / r.tb_lanes;
+            const int tb_chunks = (r.max_m + r.tb_lanes * TB_ROWS - 1) / (r.tb_lanes * TB_ROWS);
+            r.slab_words_group = (size_t)tb_chunks * r.tb_lanes * r.max_n;
+            r.tb_bnd_ints_group = tb_chunks > 1 ? (size_t)2 * 2 * r.max_n : 0;
+            int tbps = 0;
+            if ((rc = traceback_kernel_occupancy(&tbps, kThreads))) return rc;
+            const int64_t tw_needed = (cnt + Gt - 1) / Gt;
+            int64_t tblocks = std::min<int64_t>((tw_needed + wpb - 1) / wpb, (int64_t)std::max(tbps, 1) * ds->sm_count);
+            // keep the slabs of one launch within a memory budget
+            const size_t per_block = (size_t)wpb * Gt * (r.slab_words_group * 4 + r.tb_bnd_ints_group * 4);
+            const size_t budget = (size_t)4 << 30;
+            tblocks = std::max<int64_t>(1, std::min<int64_t>(tblocks, (int64_t)(budget / std::max<size_t>(per_block, 1))));
+            r.tb_blocks = (int)tblocks;
+            need = std::max(need, per_block * (size_t)tblocks);
+        }
+        need_dyn = std::max(need_dyn, need);
+        runs.push_back(r);
+    }
+    if ((rc = ensure(ds->dyn, std::max<size_t>(need_dyn, 256)))) return rc;
+
+    if (ds->timing && cudaEventRecord(ds->phase[1], st) != cudaSuccess) return SW_ERR_CUDA;
+    for (const ClassRun &r : runs) {
+        ScoreLaunch L{};
+        L.ps = ps;
+        L.sc = sc;
+        L.order = order + r.start;
+        L.n_items = r.count;
+        L.lanes = r.plan.lanes;
+        L.out_score = out_score;
+        L.out_end = out_end;
+        L.boundary = r.bnd_bytes_group ? (uint8_t *)ds->dyn.ptr : nullptr;
+        L.boundary_group_bytes = (int64_t)r.bnd_bytes_group;
+        L.work_counter = counters + r.cls;
+        L.status = &info->status;
+        if ((rc = launch_score(r.plan.rows, r.mode, L, r.score_blocks, kThreads, st))) return rc;
+    }
+    if (ds->timing && cudaEventRecord(ds->phase[2], st) != cudaSuccess) return SW_ERR_CUDA;
+    for (const ClassRun &r : runs) {
+        if (!cig) break;
+        TracebackLaunch B{};
+        B.ps = ps;
+        B.sc = sc;
+        B.order = order + r.start;
+        B.n_items = r.count;
+        B.lanes = r.tb_lanes;
+        B.score = out_score;
+        B.end = out_end;
+        B.cig_ops = cig->ops;
+        B.cig_off = cig->offsets;
+        B.cig_n = cig->n_ops;
+        const int Gt = 32 / r.tb_lanes;
+        const size_t slab_total = (size_t)r.tb_blocks * (kThreads / 32) * Gt * r.slab_words_group;
+        B.slab = (uint32_t *)ds->dyn.ptr;
+        B.slab_group_words = (int64_t)r.slab_words_group;
+        B.boundary = r.tb_bnd_ints_group ? (int32_t *)ds->dyn.ptr + slab_total : nullptr;
+        B.boundary_group_ints = (int64_t)r.tb_bnd_ints_group;
+        B.work_counter = counters + N_CLASS + r.cls;
+        B.status = &info->status;
+        if ((rc = launch_traceback(B, r.tb_blocks, kThreads, st))) return rc;
+    }
+    if (ds->timing && cudaEventRecord(ds->phase[3], st) != cudaSuccess) return SW_ERR_CUDA;
+    ds->timed_cells_valid = ds->timing;
+    if (cudaEventRecord(ds->last_done, st) != cudaSuccess) return SW_ERR_CUDA;
+    ds->last_recorded = true;
+    return SW_OK;
+}
+
+int read_status(DeviceState *ds, cudaStream_t st)
+{
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    if (!ds->last_status) return SW_OK;
+    int32_t v = 0;
+    if (cudaMemcpy(&v, ds->last_status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return SW_ERR_CUDA;
+    return status_to_code(v);
+}
+
+int check_common(const void *reads, const int64_t *roff, const void *wins, const int64_t *woff, int64_t n_pairs,
+                 const sw_scoring_t *scoring, const int32_t *out_score, const int32_t *out_end,
+                 const sw_cigar_t *cig)
+{
+    if (n_pairs < 0 || !scoring_ok(scoring)) return SW_ERR_INVALID_ARG;
+    if (n_pairs == 0) return SW_OK;
+    if (!reads || !roff || !wins || !woff || !out_score || !out_end) return SW_ERR_INVALID_ARG;
+    if (((uintptr_t)reads & 15u) || ((uintptr_t)wins & 15u)) return SW_ERR_INVALID_ARG;
+    if (cig && (!cig->ops || !cig->offsets || !cig->n_ops)) return SW_ERR_INVALID_ARG;
+    if (n_pairs > (int64_t)INT32_MAX - 64) return SW_ERR_UNSUPPORTED;
+    return SW_OK;
+}
+
+}  // namespace
+}  // namespace swgb
+
+using namespace swgb;
+
+extern "C" {
+
+int64_t sw_cigar_capacity(int64_t read_len) { return read_len < 0 ? 0 : 2 * read_len + 3; }
+
+int64_t sw_packed_bytes(int64_t n_bases)
+{
+    if (n_bases < 0) return 0;
+    return ((n_bases + 3) / 4 + 15) / 16 * 16;
+}
+
+int sw_batch_align(const uint8_t *reads, const int64_t *read_offsets, const uint8_t *windows,
+                   const int64_t *window_offsets, int64_t n_pairs, const sw_scoring_t *scoring, int32_t *out_score,
+                   int32_t *out_end, sw_cigar_t *out_cigar, sw_stream_t stream)
+{
+    int rc = check_common(reads, read_offsets, windows, window_offsets, n_pairs, scoring, out_score, out_end,
+                          out_cigar);
+    if (rc || n_pairs == 0) return rc;
+    PairSet ps{(const uint32_t *)reads, read_offsets, nullptr, (const uint32_t *)windows, window_offsets};
+    return run_batch(ps, n_pairs, n_pairs, scoring, out_score, out_end, out_cigar, (cudaStream_t)stream);
+}
+
+int sw_batch_align_indexed(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads,
+                           const uint8_t *windows, const int64_t *window_offsets, const int64_t *pair_read,
+                           int64_t n_pairs, const sw_scoring_t *scoring, int32_t *out_score, int32_t *out_end,
+                           sw_cigar_t *out_cigar, sw_stream_t stream)
+{
+    int rc = check_common(reads, read_offsets, windows, window_offsets, n_pairs, scoring, out_score, out_end,
+                          out_cigar);
+    if (rc || n_pairs == 0) return rc;
+    if (!pair_read || n_reads < 1) return SW_ERR_INVALID_ARG;
+    PairSet ps{(const uint32_t *)reads, read_offsets, pair_read, (const uint32_t *)windows, window_offsets};
+    return run_batch(ps, n_reads, n_pairs, scoring, out_score, out_end, out_cigar, (cudaStream_t)stream);
+}
+
+int sw_batch_align_host(const uint8_t *reads, const int64_t *read_offsets, const uint8_t *windows,
+                        const int64_t *window_offsets, int64_t n_pairs, const sw_scoring_t *scoring,
+                        int32_t *out_score, int32_t *out_end, sw_cigar_t *out_cigar, sw_stream_t stream)
+{
+    int rc = check_common(reads, read_offsets, windows, window_offsets, n_pairs, scoring, out_score, out_end,
+                          out_cigar);
+    if (rc || n_pairs == 0) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    DeviceState *ds = nullptr;
+    if ((rc = device_state(&ds))) return rc;
+    const int64_t rb = sw_packed_bytes(read_offsets[n_pairs]);
+    const int64_t wb = sw_packed_bytes(window_offsets[n_pairs]);
+    const int64_t n_cig = out_cigar ? out_cigar->offsets[n_pairs] : 0;
+    size_t off = 0;
+    const size_t o_r = off; off = align_up(off + rb, 256);
+    const size_t o_w = off; off = align_up(off + wb, 256);
+    const size_t o_ro = off; off = align_up(off + 8 * (n_pairs + 1), 256);
+    const size_t o_wo = off; off = align_up(off + 8 * (n_pairs + 1), 256);
+    const size_t o_s = off; off = align_up(off + 4 * n_pairs, 256);
+    const size_t o_e = off; off = align_up(off + 8 * n_pairs, 256);
+    const size_t o_co = off; off = align_up(off + (out_cigar ? 8 * (n_pairs + 1) : 0), 256);
+    const size_t o_cn = off; off = align_up(off + (out_cigar ? 4 * n_pairs : 0), 256);
+    const size_t o_ops = off; off = align_up(off + 4 * n_cig, 256);
+    {
+        std::lock_guard<std::mutex> lk(ds->mu);
+        if ((rc = ensure(ds->stage, off))) return rc;
+    }
+    uint8_t *b = (uint8_t *)ds->stage.ptr;
+    auto h2d = [&](size_t o, const void *src, size_t n) {
+        return n == 0 || cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    };
+    auto d2h = [&](void *dst, size_t o, size_t n) {
+        return n == 0 || cudaMemcpyAsync(dst, b + o, n, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    };
+    if (!h2d(o_r, reads, rb) || !h2d(o_w, windows, wb) || !h2d(o_ro, read_offsets, 8 * (n_pairs + 1)) ||
+        !h2d(o_wo, window_offsets, 8 * (n_pairs + 1)))
+        return SW_ERR_CUDA;
+    sw_cigar_t dc{};
+    if (out_cigar) {
+        if (!h2d(o_co, out_cigar->offsets, 8 * (n_pairs + 1))) return SW_ERR_CUDA;
+        dc.ops = (uint32_t *)(b + o_ops);
+        dc.offsets = (const int64_t *)(b + o_co);
+        dc.n_ops = (int32_t *)(b + o_cn);
+    }
+    PairSet ps{(const uint32_t *)(b + o_r), (const int64_t *)(b + o_ro), nullptr, (const uint32_t *)(b + o_w),
+               (const int64_t *)(b + o_wo)};
+    rc = run_batch(ps, n_pairs, n_pairs, scoring, (int32_t *)(b + o_s), (int32_t *)(b + o_e),
+                   out_cigar ? &dc : nullptr, st);
+    if (rc) return rc;
+    if (!d2h(out_score, o_s, 4 * n_pairs) || !d2h(out_end, o_e, 8 * n_pairs)) return SW_ERR_CUDA;
+    if (out_cigar && (!d2h(out_cigar->n_ops, o_cn, 4 * n_pairs) || !d2h(out_cigar->ops, o_ops, 4 * n_cig)))
+        return SW_ERR_CUDA;
+    return read_status(ds, st);
+}
+
+int sw_sync_status(sw_stream_t stream)
+{
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    return read_status(ds, (cudaStream_t)stream);
+}
+
+const char *sw_strerror(int code)
+{
+    switch (code) {
+    case SW_OK: return "ok";
+    case SW_ERR_INVALID_ARG: return "invalid argument";
+    case SW_ERR_CAPACITY: return "CIGAR slot too small";
+    case SW_ERR_CUDA: return "CUDA runtime error";
+    case SW_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case SW_ERR_UNSUPPORTED: return "size beyond supported limits";
+    case SW_ERR_DEVICE_INPUT: return "device-resident input failed validation";
+    case SW_ERR_INTERNAL: return "internal consistency check failed";
+    case SW_ERR_NO_DEVICE: return "no usable CUDA device";
+    default: return "unknown error";
+    }
+}
+
+int64_t sw_launch_count(void) { return g_launches.load(); }
+
+int sw_set_plan(int32_t max_read_len, int32_t lanes, int32_t r_rows)
+{
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    if (max_read_len <= 0) {
+        g_plans.clear();
+        return SW_OK;
+    }
+    if (lanes < 1 || lanes > 32) return SW_ERR_INVALID_ARG;
+    bool ok = false;
+    for (int i = 0; i < N_SCORE_ROWS; ++i) ok |= kScoreRows[i] == r_rows;
+    if (!ok) return SW_ERR_INVALID_ARG;
+    if ((max_read_len + lanes * r_rows - 1) / (lanes * r_rows) > 1 && lanes != 32) return SW_ERR_INVALID_ARG;
+    g_plans.push_back(PlanOverride{max_read_len, lanes, r_rows});
+    std::sort(g_plans.begin(), g_plans.end(),
+              [](const PlanOverride &a, const PlanOverride &b) { return a.max_read_len < b.max_read_len; });
+    return SW_OK;
+}
+
+int sw_plan_rows(int32_t *rows, int32_t cap)
+{
+    if (!rows) return N_SCORE_ROWS;
+    for (int i = 0; i < N_SCORE_ROWS && i < cap; ++i) rows[i] = kScoreRows[i];
+    return N_SCORE_ROWS;
+}
+
+int sw_phase_timing(int32_t enable)
+{
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    ds->timing = enable != 0;
+    return SW_OK;
+}
+
+int sw_phase_times(float *ms3)
+{
+    if (!ms3) return SW_ERR_INVALID_ARG;
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    if (!ds->timed_cells_valid) return SW_ERR_INVALID_ARG;
+    if (cudaEventSynchronize(ds->phase[3]) != cudaSuccess) return SW_ERR_CUDA;
+    for (int i = 0; i < 3; ++i)
+        if (cudaEventElapsedTime(&ms3[i], ds->phase[i], ds->phase[i + 1]) != cudaSuccess) return SW_ERR_CUDA;
+    return SW_OK;
+}
+
+int sw_alu_probe(int32_t kind, int64_t iters, double *ops_per_s, sw_stream_t stream)
+{
+    if (!ops_per_s || iters < 1 || kind < 0 || kind > 6) return SW_ERR_INVALID_ARG;
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int threads = 256, blocks = ds->sm_count * 8;
+    uint32_t *out = nullptr;
+    if (cudaMalloc(&out, sizeof(uint32_t) * threads * blocks) != cudaSuccess) return SW_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    rc = launch_alu_probe(kind, iters / 8 + 1, blocks, threads, out, st);  // warm-up
+    cudaEventRecord(e0, st);
+    if (!rc) rc = launch_alu_probe(kind, iters, blocks, threads, out, st);
+    cudaEventRecord(e1, st);
+    float ms = 0.f;
+    if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = SW_ERR_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (rc) return rc;
+    *ops_per_s = (double)blocks * threads * 8.0 * (double)iters / (ms * 1e-3);
+    return SW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// swgb_internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/swgb.h"
+
+namespace swgb {
+
+// Inputs of one batch as the kernels see them (all device pointers).
+struct PairSet {
+    const uint32_t *reads;      // packed reads (words)
+    const int64_t *read_off;    // n_reads + 1
+    const int64_t *pair_read;   // n_pairs, or nullptr: pair p uses read p
+    const uint32_t *wins;       // packed windows (words)
+    const int64_t *win_off;     // n_pairs + 1
+};
+
+struct Scoring {
+    int32_t ma, mi, go, ge;
+};
+
+// Arithmetic of the score pass.
+enum ScoreMode : int32_t {
+    MODE_I32 = 0,   // one pair per lane group, int32 cells
+    MODE_I16 = 1,   // two pairs per lane group in int16 halves, 16-bit keys
+    MODE_I16W = 2,  // two pairs per lane group in int16 halves, 32-bit keys
+    N_MODES = 3,
+};
+
+// Read-length classes: 16-base steps up to 1024, then 128-base steps.
+constexpr int N_MCLASS = 64 + 56;
+constexpr int N_NBUCKET = 256;       // window length / 32, clamped
+constexpr int N_CLASS = N_MODES * N_MCLASS;
+
+__host__ __device__ inline int mclass_of(int32_t m)
+{
+    return m <= 1024 ? (m + 15) / 16 - 1 : 64 + (m - 1024 + 127) / 128 - 1;
+}
+__host__ __device__ inline int32_t mclass_max(int c)
+{
+    return c < 64 ? 16 * (c + 1) : 1024 + 128 * (c - 64 + 1);
+}
+
+// Per-class facts the classify pass reads back to the host.
+struct ClassInfo {
+    int32_t count[N_CLASS];
+    int32_t max_n[N_CLASS];
+    int32_t max_m[N_CLASS];
+    int32_t status;
+    int32_t pad[3];
+};
+
+struct ScoreLaunch {
+    PairSet ps;
+    Scoring sc;
+    const int32_t *order;    // pair indices of this launch
+    int64_t n_items;
+    int32_t lanes;           // T: lanes per group
+    int32_t *out_score;
+    int32_t *out_end;
+    uint8_t *boundary;       // per-group chunk boundaries, or nullptr
+    int64_t boundary_group_bytes;
+    int32_t *work_counter;
+    int32_t *status;
+};
+
+struct TracebackLaunch {
+    PairSet ps;
+    Scoring sc;
+    const int32_t *order;
+    int64_t n_items;
+    int32_t lanes;
+    const int32_t *score;
+    const int32_t *end;
+    uint32_t *cig_ops;
+    const int64_t *cig_off;
+    int32_t *cig_n;
+    uint32_t *slab;          // per-group traceback bit slabs
+    int64_t slab_group_words;
+    int32_t *boundary;       // per-group chunk boundaries (2 x int32 per column, double-buffered)
+    int64_t boundary_group_ints;
+    int32_t *work_counter;
+    int32_t *status;
+};
+
+// Row counts compiled for the score kernels.
+constexpr int N_SCORE_ROWS = 5;
+extern const int kScoreRows[N_SCORE_ROWS];
+constexpr int TB_ROWS = 8;
+
+int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring sc,
+                    int32_t *keys, int32_t *hist, int32_t *bucket_start, int32_t *cursor,
+                    ClassInfo *info, int32_t *order, int32_t *out_score, int32_t *out_end,
+                    int32_t *cig_n, cudaStream_t st);
+int launch_score(int rows, int mode, const ScoreLaunch &L, int blocks, int threads, cudaStream_t st);
+int score_kernel_regs(int rows, int mode, int *regs, int *max_blocks_per_sm, int threads);
+int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStream_t st);
+int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads);
+int launch_alu_probe(int kind, int64_t iters, int blocks, int threads, uint32_t *out, cudaStream_t st);
+
+void count_launch(int n = 1);
+
+}  // namespace swgb

@@ -1,0 +1,43 @@
+"""The C-ABI library builds, loads and exports every symbol include/swgb.h
+declares (no compute calls: runs without a GPU)."""
+import os
+import re
+import subprocess
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "swgb.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sw_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_declared_symbols():
+    import __graft_entry__
+    lib = __graft_entry__._cuda_build_module().build()
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (sw_\w+)", out))
+    declared = _declared()
+    assert declared, "no declarations found"
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+
+
+def test_binding_covers_declarations_and_loads():
+    from paper_1304_0681_gb300 import _swgb
+    assert sorted(_swgb.EXPORTS) == _declared()
+    assert _swgb.sw_cigar_capacity(100) == 203
+    assert _swgb.sw_packed_bytes(0) == 0
+    assert _swgb.sw_packed_bytes(1) == 16
+    assert _swgb.sw_packed_bytes(64) == 16
+    assert _swgb.sw_packed_bytes(65) == 32
+    assert _swgb.sw_strerror(-2) == "CIGAR slot too small"
+    assert _swgb.sw_plan_rows() == [8, 16, 20, 25, 32]
+
+
+def test_packing_agrees_with_generator():
+    import synth
+    from paper_1304_0681_gb300 import _swgb
+    for n in (0, 1, 63, 64, 65, 1000, 4097):
+        assert synth.packed_nbytes(n) == _swgb.sw_packed_bytes(n)

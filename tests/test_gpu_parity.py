@@ -1,0 +1,197 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle, bit-exact
+(scores, end cells and CIGARs are integers, so the tolerance is zero)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import assert_parity, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+DEFAULT = (5, -4, -10, -1)
+# match*min(m,n) decides the arithmetic: <= 1022 -> 16-bit lanes with 16-bit
+# keys, <= 32000 -> 16-bit lanes with 32-bit keys, else int32 lanes
+WIDE16 = (50, -30, -60, -5)
+INT32 = (120, -60, -7, -3)
+
+
+@pytest.fixture(autouse=True)
+def _reset_plans():
+    import paper_1304_0681_gb300 as sw
+    sw.sw_set_plan(0, 1, 8)
+    yield
+    sw.sw_set_plan(0, 1, 8)
+
+
+def test_parity_workload_full():
+    wl = synth.generate("parity")
+    got = run_gpu(wl, DEFAULT)
+    assert_parity(wl, got, DEFAULT)
+
+
+@pytest.mark.parametrize("scoring", [WIDE16, (2, -3, -5, -2), (1, -1, -2, -1)])
+def test_parity_workload_other_scorings(scoring):
+    wl = synth.generate("parity", seed=1, n_reads=400)
+    got = run_gpu(wl, scoring)
+    assert_parity(wl, got, scoring)
+
+
+def test_int32_path_long_reads():
+    wl = synth.random_pairs(60, (280, 320), (380, 420), seed=3)
+    # plant true matches so the scores are large
+    for p in range(0, 60, 2):
+        r0, r1 = wl.read_offsets[p], wl.read_offsets[p + 1]
+        w0 = wl.window_offsets[p]
+        wl.windows[w0 + 40:w0 + 40 + (r1 - r0)] = wl.reads[r0:r1]
+    got = run_gpu(wl, INT32)
+    assert_parity(wl, got, INT32)
+    assert got["score"].max() > 32000
+
+
+@pytest.mark.parametrize("alphabet", [2, 4])
+def test_random_lengths_and_ties(alphabet):
+    wl = synth.random_pairs(1500, (1, 200), (0, 260), seed=10 + alphabet, alphabet=alphabet)
+    for sc in (DEFAULT, (1, -1, -2, -1), (3, 0, -3, -3)):
+        got = run_gpu(wl, sc)
+        assert_parity(wl, got, sc)
+
+
+def test_edge_cases():
+    seqs = [("A", ""), ("A", "A"), ("A", "C"), ("ACGT", "A"), ("A", "ACGT"), ("ACGTACGT", "ACGTTACGT"),
+            ("AAAA", "CCCC"), ("ACAGT", "ACCGT")]
+    rng = np.random.default_rng(0)
+    enc = {c: i for i, c in enumerate("ACGT")}
+    reads = [np.array([enc[c] for c in r], np.uint8) for r, _ in seqs]
+    wins = [np.array([enc[c] for c in w], np.uint8) for _, w in seqs]
+    # lengths around the 16-base word and the lane-block edges
+    for m in (15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257):
+        reads.append(rng.integers(0, 4, m).astype(np.uint8))
+        w = rng.integers(0, 4, m + 40).astype(np.uint8)
+        w[20:20 + m] = reads[-1]
+        wins.append(w)
+    wl = _workload(reads, wins)
+    for sc in (DEFAULT, (5, -30, -3, -1)):
+        got = run_gpu(wl, sc)
+        assert_parity(wl, got, sc)
+    assert got["score"][0] == 0 and got["i_end"][0] == -1 and got["n_ops"][0] == 0
+
+
+def _workload(reads, wins):
+    roff = np.zeros(len(reads) + 1, np.int64)
+    np.cumsum([len(r) for r in reads], out=roff[1:])
+    woff = np.zeros(len(wins) + 1, np.int64)
+    np.cumsum([len(w) for w in wins], out=woff[1:])
+    n = len(reads)
+    return synth.Workload("edge", np.concatenate(reads), roff,
+                          np.concatenate(wins) if sum(len(w) for w in wins) else np.zeros(0, np.uint8), woff,
+                          np.arange(n, dtype=np.int64), np.arange(n + 1, dtype=np.int64),
+                          np.zeros(n, np.uint8), np.zeros(n, np.int32))
+
+
+@pytest.mark.parametrize("lanes,rows", [(1, 8), (3, 16), (4, 25), (5, 20), (7, 16), (13, 8), (32, 8), (32, 32)])
+def test_lane_plans(lanes, rows):
+    """Every (lanes, rows) plan gives the same answer, including plans that
+    split a read into several row chunks (lanes * rows < read length)."""
+    import paper_1304_0681_gb300 as sw
+    if lanes * rows < 100 and lanes != 32:
+        pytest.skip("plan must cover the read unless it uses 32 lanes")
+    wl = synth.generate("parity", seed=5, n_reads=300)
+    sw.sw_set_plan(100, lanes, rows)
+    got = run_gpu(wl, DEFAULT)
+    assert_parity(wl, got, DEFAULT)
+
+
+def test_multichunk_long_reads():
+    """Reads longer than 32 lanes x rows go through several row chunks with
+    the boundary row in scratch memory."""
+    import paper_1304_0681_gb300 as sw
+    wl = synth.random_pairs(24, (600, 1300), (700, 1500), seed=21)
+    for p in range(0, 24, 3):
+        r0, r1 = wl.read_offsets[p], wl.read_offsets[p + 1]
+        w0, w1 = wl.window_offsets[p], wl.window_offsets[p + 1]
+        L = min(r1 - r0, w1 - w0 - 10)
+        wl.windows[w0 + 5:w0 + 5 + L] = wl.reads[r0:r0 + L]
+    sw.sw_set_plan(100000, 32, 8)
+    for sc in (DEFAULT, (1, -1, -2, -1)):
+        got = run_gpu(wl, sc)
+        assert_parity(wl, got, sc)
+
+
+def test_uneven_sample():
+    wl = synth.generate("uneven", seed=2, n_reads=3000)
+    got = run_gpu(wl, DEFAULT)
+    rng = np.random.default_rng(1)
+    assert_parity(wl, got, DEFAULT, pairs=np.sort(rng.choice(wl.n_pairs, 600, replace=False)))
+
+
+def test_indexed_candidates():
+    wl = synth.generate("filter", seed=3, n_reads=200)
+    got = run_gpu(wl, DEFAULT, indexed=True)
+    rng = np.random.default_rng(2)
+    assert_parity(wl, got, DEFAULT, pairs=np.sort(rng.choice(wl.n_pairs, 800, replace=False)))
+
+
+def test_host_entry_point():
+    import torch
+    import paper_1304_0681_gb300 as sw
+    wl = synth.generate("parity", seed=7, n_reads=300)
+    n = wl.n_pairs
+    cap = 2 * wl.pair_read_lengths + 3
+    coff = np.zeros(n + 1, np.int64)
+    np.cumsum(cap, out=coff[1:])
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    score = torch.zeros(n, dtype=torch.int32).pin_memory()
+    end = torch.zeros(2 * n, dtype=torch.int32).pin_memory()
+    ops = torch.zeros(int(coff[-1]), dtype=torch.int32).pin_memory()
+    nops = torch.zeros(n, dtype=torch.int32).pin_memory()
+    sw.sw_batch_align_host(t(wl.packed_reads()), t(wl.read_offsets), t(wl.packed_windows()), t(wl.window_offsets),
+                           n, DEFAULT, score, end, (ops, t(coff), nops))
+    e = end.numpy().reshape(-1, 2)
+    got = {"score": score.numpy().astype(np.int64), "i_end": e[:, 0].astype(np.int64),
+           "j_end": e[:, 1].astype(np.int64), "ops": ops.numpy().view(np.uint32), "cigar_offsets": coff,
+           "n_ops": nops.numpy().astype(np.int64)}
+    assert_parity(wl, got, DEFAULT)
+
+
+def test_errors_are_reported():
+    import torch
+    import paper_1304_0681_gb300 as sw
+    from paper_1304_0681_gb300 import DeviceBatch, align
+    wl = synth.generate("parity", seed=8, n_reads=50)
+    b = DeviceBatch.from_packed(wl.packed_reads(), wl.read_offsets, wl.packed_windows(), wl.window_offsets)
+    with pytest.raises(sw.SwError) as ei:
+        align(b, (5, 4, -10, -1))          # positive mismatch
+    assert ei.value.code == -1
+    with pytest.raises(sw.SwError) as ei:
+        align(b, (5, -4, -1, -10))         # open cheaper than extend
+    assert ei.value.code == -1
+    # read offsets out of order -> detected on the device
+    bad = wl.read_offsets.copy()
+    bad[10], bad[11] = bad[11], bad[10]
+    b2 = DeviceBatch.from_packed(wl.packed_reads(), bad, wl.packed_windows(), wl.window_offsets)
+    with pytest.raises(sw.SwError) as ei:
+        align(b2, DEFAULT)
+    assert ei.value.code == -6
+    # CIGAR slots of one run overflow
+    b3 = DeviceBatch.from_packed(wl.packed_reads(), wl.read_offsets, wl.packed_windows(), wl.window_offsets)
+    b3.cigar_offsets = torch.arange(wl.n_pairs + 1, dtype=torch.int64, device="cuda")
+    with pytest.raises(sw.SwError) as ei:
+        align(b3, DEFAULT)
+    assert ei.value.code == -2
+    # the library still works afterwards
+    got = run_gpu(wl, DEFAULT)
+    assert_parity(wl, got, DEFAULT)
+
+
+def test_throughput_full_size_sampled():
+    """The bench workload at full size (1M pairs), in the bench's launch
+    configuration, checked on a sample of pairs."""
+    wl = synth.generate("throughput")
+    got = run_gpu(wl, DEFAULT)
+    rng = np.random.default_rng(3)
+    pairs = np.sort(rng.choice(wl.n_pairs, 3000, replace=False))
+    assert_parity(wl, got, DEFAULT, pairs=pairs)
+    # every decoy-free pair aligns most of the read
+    true = wl.kinds == synth.KIND_TRUE
+    assert np.median(got["score"][true]) > 400
