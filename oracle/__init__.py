@@ -65,6 +65,10 @@ def load_library(path: str):
     lib.sw_oracle_deletion_bound.restype = i64
     lib.sw_oracle_batch.argtypes = [p, p, p, p, p, i64, i64, i64, i64, i64, p, p, p, p, p, p, ctypes.c_int]
     lib.sw_oracle_batch.restype = ctypes.c_int
+    lib.sw_oracle_insertion_bound.argtypes = [i64, i64, i64, i64, i64]
+    lib.sw_oracle_insertion_bound.restype = i64
+    lib.sw_oracle_band_traceback.argtypes = [p, i64, p, i64, i64, i64, i64, i64, i64, i64, i64, p, i64, p]
+    lib.sw_oracle_band_traceback.restype = ctypes.c_int
     lib.sw_brute_tables.argtypes = [p, i64, p, i64, i64, i64, i64, i64, p, p, p]
     lib.sw_brute_tables.restype = ctypes.c_int
     return lib
@@ -153,6 +157,26 @@ def rect_traceback(r, w, score: int, i_end: int, j_end: int, scoring: Scoring = 
     if rc != 0:
         raise RuntimeError(f"sw_oracle_rect_traceback failed: {rc}")
     return ops[: int(nops[0])].copy(), int(jlo[0])
+
+
+def insertion_bound(i_end: int, score: int, scoring: Scoring = DEFAULT_SCORING) -> int:
+    return int(_load().sw_oracle_insertion_bound(i_end, score, scoring.match, scoring.gap_open,
+                                                 scoring.gap_extend))
+
+
+def band_traceback(r, w, score: int, i_end: int, j_end: int, scoring: Scoring = DEFAULT_SCORING, lib=None):
+    """CIGAR recomputed over the diagonal band that holds every optimal
+    alignment ending at the end cell."""
+    lib = _load(lib)
+    r, w = _codes(r), _codes(w)
+    cap = cigar_capacity(len(r))
+    ops = np.zeros(cap, dtype=np.uint32)
+    nops = np.zeros(1, dtype=np.int64)
+    rc = lib.sw_oracle_band_traceback(_ptr(r), len(r), _ptr(w), len(w), *map(int, scoring),
+                                      score, i_end, j_end, _ptr(ops), cap, _ptr(nops))
+    if rc != 0:
+        raise RuntimeError(f"sw_oracle_band_traceback failed: {rc}")
+    return ops[: int(nops[0])].copy()
 
 
 def align_batch(reads, read_offsets, windows, window_offsets, pair_read=None,

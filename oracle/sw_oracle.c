@@ -251,6 +251,68 @@ int sw_oracle_rect_traceback(const uint8_t *r, int64_t m, const uint8_t *w, int6
     return rc;
 }
 
+/*
+ * Upper bound on the number of insertions (read bases aligned to gaps) in any
+ * alignment with the given score that ends at read row i_end: I inserted
+ * bases leave at most i_end+1-I aligned ones, and with o <= e <= 0 one run of
+ * I costs at least o + (I-1) e, so
+ * score <= match (i_end+1-I) + o + (I-1) e, i.e.
+ * I <= (match (i_end+1) + o - e - score) / (match - e).
+ */
+int64_t sw_oracle_insertion_bound(int64_t i_end, int64_t score, int64_t ma, int64_t go, int64_t ge)
+{
+    const int64_t num = ma * (i_end + 1) + go - ge - score;
+    return num < 0 ? 0 : num / (ma - ge);
+}
+
+/*
+ * Band traceback: like the rectangle traceback, but cells whose diagonal
+ * d = j - i lies outside [j_end - i_end - D, j_end - i_end + I] are treated
+ * as unreachable (H = 0, E = F = -inf).  Walking back from the end cell, every
+ * deletion lowers d by one and every insertion raises it by one, so every
+ * optimal alignment ending there stays inside the band.  Returns as
+ * sw_oracle_rect_traceback.
+ */
+int sw_oracle_band_traceback(const uint8_t *r, int64_t m, const uint8_t *w, int64_t n,
+                             int64_t ma, int64_t mi, int64_t go, int64_t ge,
+                             int64_t score, int64_t i_end, int64_t j_end,
+                             uint32_t *cigar, int64_t cap, int64_t *n_ops)
+{
+    *n_ops = 0;
+    if (score <= 0) return 0;
+    (void)n;
+    const int64_t dmax = sw_oracle_deletion_bound(i_end, score, ma, go, ge);
+    const int64_t imax = sw_oracle_insertion_bound(i_end, score, ma, go, ge);
+    const int64_t dend = j_end - i_end;
+    const int64_t dlo = dmax < 0 ? -(i_end + 1) - 1 : dend - dmax;
+    const int64_t dhi = dend + imax;
+    const int64_t rm = i_end + 1, rn = j_end + 1;
+    const int64_t ld = rn + 1, cells = (rm + 1) * ld;
+    int64_t *H = (int64_t *)malloc((size_t)cells * sizeof(int64_t));
+    int64_t *E = (int64_t *)malloc((size_t)cells * sizeof(int64_t));
+    int64_t *F = (int64_t *)malloc((size_t)cells * sizeof(int64_t));
+    if (!H || !E || !F) { free(H); free(E); free(F); return -3; }
+    for (int64_t k = 0; k < cells; ++k) { H[k] = 0; E[k] = ORC_NEG_INF; F[k] = ORC_NEG_INF; }
+    for (int64_t i = 1; i <= rm; ++i) {
+        for (int64_t j = 1; j <= rn; ++j) {
+            const int64_t d = (j - 1) - (i - 1);
+            if (d < dlo || d > dhi) continue;      /* outside the band */
+            const int64_t s = (r[i - 1] == w[j - 1]) ? ma : mi;
+            const int64_t e = max2(H[i * ld + j - 1] + go, E[i * ld + j - 1] + ge);
+            const int64_t f = max2(H[(i - 1) * ld + j] + go, F[(i - 1) * ld + j] + ge);
+            int64_t h = max2(max2(H[(i - 1) * ld + j - 1] + s, e), max2(f, 0));
+            E[i * ld + j] = e;
+            F[i * ld + j] = f;
+            H[i * ld + j] = h;
+        }
+    }
+    int rc;
+    if (H[rm * ld + rn] != score) rc = -2;
+    else rc = gotoh_traceback(r, m, w, rn, ma, mi, go, ge, H, E, F, rm, rn, i_end, cigar, cap, n_ops);
+    free(H); free(E); free(F);
+    return rc;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Batch driver: pairs split across pthreads (used for the CPU baseline).    */
 

@@ -107,4 +107,17 @@ int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring
     return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
 }
 
+int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, int32_t *hist, int32_t *bucket_start,
+                        int32_t *cursor, int32_t *order, cudaStream_t st)
+{
+    const int threads = 256;
+    int64_t blocks = (n_pairs + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_scan<<<1, 1024, 0, st>>>(hist, bucket_start, cursor, N_CLASS * N_NBUCKET);
+    k_scatter<<<(unsigned)blocks, threads, 0, st>>>(keys, n_pairs, cursor, order);
+    count_launch(2);
+    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
 }  // namespace swgb

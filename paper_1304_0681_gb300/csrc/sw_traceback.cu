@@ -3,25 +3,36 @@
 // The paper's Stage E, task iii returns the alignment itself, not only its
 // score; downstream, long runs of deletions in it mark splice junctions.
 // The score pass keeps no traceback.  This pass recomputes the DP exactly
-// (int32, unfloored E and F) over a rectangle that provably holds every
-// optimal alignment ending at the end cell (i_end, j_end):
+// (int32, unfloored E and F) over a region that provably holds every optimal
+// alignment ending at the end cell (i_end, j_end), and walks back through it.
 //
-//   rows 0 .. i_end,  window columns j_lo .. j_end,  j_lo = j_end - i_end - D
+// The region.  Any alignment with this score that ends on read row i_end
+// holds at most i_end+1 aligned read bases, each worth at most `match`, and
+// with o <= e <= 0 one gap run is the cheapest way to spend gap bases, so
+//   deletions  D <= (match (i_end+1) + o - score) / (-e) + 1
+//   insertions I <= (match (i_end+1) + o - e - score) / (match - e).
+// Walking back from the end cell, a deletion lowers the diagonal d = j - i by
+// one and an insertion raises it by one, so every optimal path stays in the
+// band  j_end - i_end - D <= j - i <= j_end - i_end + I,  rows 0..i_end.
+// Cells outside the band are treated as unreachable (H = 0, E = F = -inf);
+// that can only lower recomputed values, and cells on optimal paths keep
+// theirs, so every comparison of the walk comes out as in the full matrix.
 //
-// where D bounds the deletions of any alignment with this score ending on
-// read row i_end: with o <= e <= 0 it holds at most i_end+1 aligned read
-// bases worth at most `match` each, and D deleted window bases cost at least
-// o + (D-1) e, so D <= (match*(i_end+1) + o - score)/(-e) + 1.  Cells outside
-// the rectangle can only lower the recomputed values, and every cell on an
-// optimal path keeps its value, so every comparison made by the walk comes
-// out as in the full matrix and the CIGAR is the full-matrix one.
-//
-// Each cell stores 4 bits: bits 0-1 the source of H (0: H == 0, 1: diagonal,
+// Layout.  A group of T lanes owns one pair; lane k holds 8 rows of a chunk of
+// 8T rows and sweeps the chunk's band window of columns with a one-step
+// wavefront (shuffles pass the bottom row down); the chunk's last lane hands
+// its bottom row to the next chunk through a double-buffered scratch row.
+// Each cell stores 4 bits -- bits 0-1 the source of H (0: H == 0, 1: diagonal,
 // 2: E, 3: F, in that order of preference), bit 2 "E opens here"
-// (E == H(i,j-1) + o), bit 3 "F opens here".  Lane k of a T-lane group holds
-// 8 rows, so one 32-bit word per lane and column holds its cells.  The words
-// go to a per-group slab in global memory; then the group's first lane walks
-// back from the end cell, emitting runs in reverse, and reverses them.
+// (E == H(i,j-1) + o), bit 3 "F opens here" -- one 32-bit word per lane and
+// column, in a per-group slab.  The group's first lane then walks back from
+// the end cell, writes the runs reversed into the pair's CSR slot and
+// reverses them in place.
+//
+// Scheduling.  k_tb_keys gives every pair a cost key (rows x window), a
+// counting sort orders each length class by cost so a warp's groups sweep
+// similar windows, and pairs whose slab exceeds the per-group slab of the
+// main launch form a separate launch with larger slabs.
 #include "sw_device.cuh"
 #include "swgb_internal.h"
 
@@ -32,41 +43,48 @@ constexpr int32_t TB_NEG = -(1 << 28);
 
 struct TbPair {
     int64_t rs, ws;
-    int32_t m, n, score, ie, je, jlo, W, rows;
+    int32_t m, n, score, ie, je;
+    int32_t jlo, W, rows;   // rectangle: window columns jlo .. jlo+W-1, rows 0..rows-1
+    int32_t a, b;           // band in rectangle columns: row i spans [i + a, i + b]
     int32_t p;
 };
 
-__device__ __forceinline__ TbPair tb_pair(const TracebackLaunch &L, int64_t item, bool on)
+__device__ __forceinline__ TbPair tb_pair(const TbParams &P, int32_t p, int32_t *status)
 {
-    TbPair q{0, 0, 0, 0, 0, -1, -1, 0, 0, 0, -1};
-    if (!on || item >= L.n_items) return q;
-    const int32_t p = L.order[item];
-    const int64_t rd = L.ps.pair_read ? L.ps.pair_read[p] : p;
+    TbPair q{};
     q.p = p;
-    q.rs = L.ps.read_off[rd];
-    q.m = (int32_t)(L.ps.read_off[rd + 1] - q.rs);
-    q.ws = L.ps.win_off[p];
-    q.n = (int32_t)(L.ps.win_off[p + 1] - q.ws);
-    q.score = L.score[p];
+    q.ie = -1;
+    q.je = -1;
+    if (p < 0) return q;
+    const int64_t rd = P.ps.pair_read ? P.ps.pair_read[p] : p;
+    q.rs = P.ps.read_off[rd];
+    q.m = (int32_t)(P.ps.read_off[rd + 1] - q.rs);
+    q.ws = P.ps.win_off[p];
+    q.n = (int32_t)(P.ps.win_off[p + 1] - q.ws);
+    q.score = P.score[p];
     if (q.score <= 0) return q;
-    q.ie = L.end[2 * p];
-    q.je = L.end[2 * p + 1];
-    if (q.ie < 0 || q.ie >= q.m || q.je < 0 || q.je >= q.n || q.score > L.sc.ma * min(q.m, q.n)) {
+    q.ie = P.end[2 * p];
+    q.je = P.end[2 * p + 1];
+    if (q.ie < 0 || q.ie >= q.m || q.je < 0 || q.je >= q.n || q.score > P.sc.ma * min(q.m, q.n)) {
         // an end cell outside the pair: never walk it
-        atomicOr(L.status, ST_INTERNAL);
+        if (status) atomicOr(status, ST_INTERNAL);
         q.score = 0;
         return q;
     }
-    int32_t jlo = 0;
-    if (L.sc.ge < 0) {
-        const int32_t num = L.sc.ma * (q.ie + 1) + L.sc.go - q.score;
-        const int32_t dmax = num < 0 ? 0 : num / (-L.sc.ge) + 1;
-        jlo = q.je - q.ie - dmax;
-        if (jlo < 0) jlo = 0;
+    const int32_t ma = P.sc.ma, go = P.sc.go, ge = P.sc.ge;
+    const int32_t dend = q.je - q.ie;
+    int32_t dlo = -q.ie - 1;  // no lower limit when gaps are free
+    if (ge < 0) {
+        const int32_t num = ma * (q.ie + 1) + go - q.score;
+        dlo = dend - (num < 0 ? 0 : num / (-ge) + 1);
     }
-    q.jlo = jlo;
-    q.W = q.je - jlo + 1;
+    const int32_t inum = ma * (q.ie + 1) + go - ge - q.score;
+    const int32_t dhi = dend + (inum < 0 ? 0 : inum / (ma - ge));
+    q.jlo = max(0, dlo);
+    q.W = q.je - q.jlo + 1;
     q.rows = q.ie + 1;
+    q.a = dlo - q.jlo;
+    q.b = dhi - q.jlo;
     return q;
 }
 
@@ -81,7 +99,10 @@ struct RevCigar {
     __device__ void push(uint32_t o, int32_t l)
     {
         if (l <= 0) return;
-        if (len > 0 && o == op) { len += l; return; }
+        if (len > 0 && o == op) {
+            len += l;
+            return;
+        }
         flush();
         op = o;
         len = l;
@@ -97,19 +118,68 @@ struct RevCigar {
     }
 };
 
+// Band window of chunk c (rows c*rc .. c*rc+rc-1) in rectangle columns.
+__device__ __forceinline__ void chunk_window(const TbPair &q, int c, int rc, int &lo, int &hi)
+{
+    lo = max(0, c * rc + q.a);
+    hi = min(q.W - 1, c * rc + rc - 1 + q.b);
+}
+
+// Slab words a pair needs with T lanes: sum over chunks of window x T.
+__device__ __forceinline__ int64_t slab_need(const TbPair &q, int T)
+{
+    if (q.score <= 0) return 0;
+    const int rc = T * TB_ROWS;
+    const int chunks = (q.rows + rc - 1) / rc;
+    const int wcap = min(q.W, rc - 1 + (q.b - q.a) + 1);
+    return (int64_t)chunks * wcap * T;
+}
+
+// Cost key per pair: class-major, most expensive first within a class.
+__global__ void k_tb_keys(TbParams P, const int32_t *__restrict__ order, int64_t n_items,
+                          const int32_t *__restrict__ score_keys, int32_t *__restrict__ tb_keys,
+                          int32_t *__restrict__ hist, TbClassInfo *__restrict__ info)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_items;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = order[q];
+        const int cls = score_keys[p] / N_NBUCKET;
+        const int T = P.lanes;
+        const TbPair t = tb_pair(P, p, nullptr);
+        const int64_t need = slab_need(t, T);
+        // big slabs first, then by falling cost (~9% buckets of rows x window)
+        int32_t key;
+        if (need > P.small_slab_words) {
+            key = cls * N_NBUCKET;
+        } else {
+            const float cost = t.score > 0 ? (float)t.rows * (float)min(t.W, 8 * T + (t.b - t.a)) : 1.f;
+            const int cb = min(254, max(0, (int)(8.f * __log2f(cost))));
+            key = cls * N_NBUCKET + 1 + (254 - cb);
+        }
+        tb_keys[p] = key;
+        atomicAdd(&hist[key], 1);
+        if (need > 0) {
+            atomicMax(&info->max_need[cls], (int32_t)(need < (int64_t)INT32_MAX ? need : (int64_t)INT32_MAX));
+            if (need > P.small_slab_words) atomicAdd(&info->n_big[cls], 1);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
 {
+    const TbParams &P = L.P;
     const int lane = threadIdx.x & 31;
     const int T = L.lanes;
     const int G = 32 / T;
     const int g = lane / T;
     const int k = lane - g * T;
     const bool on = g < G;
+    const int rc = T * TB_ROWS;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint32_t *slab = on ? L.slab + (warp_global * G + g) * L.slab_group_words : nullptr;
-    int32_t *bnd = (on && L.boundary) ? L.boundary + (warp_global * G + g) * L.boundary_group_ints : nullptr;
+    int32_t *bnd = on ? L.boundary + (warp_global * G + g) * L.boundary_group_ints : nullptr;
     const int64_t bnd_half = L.boundary_group_ints / 2;
-    const int32_t ma = L.sc.ma, mi = L.sc.mi, go = L.sc.go, ge = L.sc.ge;
+    const int32_t ma = P.sc.ma, mi = P.sc.mi, go = P.sc.go, ge = P.sc.ge;
 
     for (;;) {
         int base = 0;
@@ -117,20 +187,31 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
         base = __shfl_sync(FULLMASK, base, 0);
         if (base >= L.n_items) break;
         const int64_t item = base + g;
-        const TbPair q = tb_pair(L, item, on);
-        const int32_t rows_w = __reduce_max_sync(FULLMASK, (unsigned)q.rows);
-        const int32_t W_w = __reduce_max_sync(FULLMASK, (unsigned)q.W);
-        const int rpc = T * TB_ROWS;
-        const int chunks = (rows_w + rpc - 1) / rpc;
-        const int steps = W_w + T - 1;
+        const int32_t p = (on && item < L.n_items) ? L.order[item] : -1;
+        TbPair q = tb_pair(P, p, L.status);
+        if (q.score > 0 && slab_need(q, T) > L.slab_group_words) {
+            // the launch was sized from the class maximum; never overrun a slab
+            atomicOr(L.status, ST_INTERNAL);
+            q.score = 0;
+            q.rows = 0;
+        }
+        const int32_t rows_w = __reduce_max_sync(FULLMASK, (unsigned)(q.score > 0 ? q.rows : 0));
+        const int chunks = (rows_w + rc - 1) / rc;
+        const int wcap = q.score > 0 ? min(q.W, rc - 1 + (q.b - q.a) + 1) : 0;
+        int64_t slab_off = 0;  // words before chunk c in this group's slab
 
+        int prev_lo = 0, prev_hi = -1;
         for (int c = 0; c < chunks; ++c) {
-            const int i0 = c * rpc + k * TB_ROWS;
+            int lo = 0, hi = -1;
+            if (q.score > 0 && c * rc < q.rows) chunk_window(q, c, rc, lo, hi);
+            const int width = hi - lo + 1;
+            const int steps = __reduce_max_sync(FULLMASK, (unsigned)max(width, 0)) + T - 1;
+            const int i0 = c * rc + k * TB_ROWS;
             uint32_t codes = 0x44444444u;  // 4 bits per row, 4 = no base
             {
                 const int cnt = min(TB_ROWS, q.rows - i0);
-                if (cnt > 0) {
-                    const uint32_t w = load_bases(L.ps.reads, q.rs + i0, cnt);
+                if (q.score > 0 && cnt > 0) {
+                    const uint32_t w = load_bases(P.ps.reads, q.rs + i0, cnt);
 #pragma unroll
                     for (int r = 0; r < TB_ROWS; ++r)
                         if (r < cnt) codes = (codes & ~(0xFu << (4 * r))) | (((w >> (2 * r)) & 3u) << (4 * r));
@@ -142,27 +223,32 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
                 E[r] = TB_NEG;
                 Hp[r] = 0;
             }
-            int32_t diag_in = 0, out_h = 0, out_f = TB_NEG;
+            const int32_t *bin = (bnd && c > 0) ? bnd + (c & 1) * bnd_half : nullptr;
+            int32_t *bout = (bnd && c + 1 < chunks) ? bnd + ((c + 1) & 1) * bnd_half : nullptr;
+            // diagonal into the chunk's first column: the previous chunk's
+            // bottom row one column to the left, if it computed it
+            int32_t diag_in = 0;
+            if (k == 0 && bin && lo - 1 >= prev_lo && lo - 1 <= prev_hi) diag_in = bin[2 * (lo - 1)];
+            int32_t out_h = 0, out_f = TB_NEG;
             uint32_t ww = 0;
-            const bool load_bnd = c > 0, store_bnd = c + 1 < chunks;
-            const int32_t *bin = load_bnd && bnd ? bnd + (c & 1) * bnd_half : nullptr;
-            int32_t *bout = store_bnd && bnd ? bnd + ((c + 1) & 1) * bnd_half : nullptr;
 
             for (int t = 0; t < steps; ++t) {
-                const int j = t - k;
+                const int jl = t - k;       // column within the window
+                const int jj = lo + jl;     // rectangle column
                 int32_t up_h = __shfl_up_sync(FULLMASK, out_h, 1);
                 int32_t up_f = __shfl_up_sync(FULLMASK, out_f, 1);
                 if (k == 0) {
-                    if (bin && j < q.W) {
-                        up_h = bin[2 * j];
-                        up_f = bin[2 * j + 1];
+                    if (bin && jj >= prev_lo && jj <= prev_hi) {
+                        up_h = bin[2 * jj];
+                        up_f = bin[2 * jj + 1];
                     } else {
                         up_h = 0;
                         up_f = TB_NEG;
                     }
                 }
-                if (j >= 0 && j < q.W) {
-                    if ((j & 15) == 0) ww = load_bases(L.ps.wins, q.ws + q.jlo + j, min(16, q.W - j));
+                if (jl >= 0 && jl < width) {
+                    if (jl == 0 || (((q.jlo + jj) & 15) == 0))
+                        ww = load_bases(P.ps.wins, q.ws + q.jlo + jj, min(16 - ((q.jlo + jj) & 15), hi - jj + 1));
                     const uint32_t w = ww & 3u;
                     ww >>= 2;
                     int32_t d0 = diag_in, hu = up_h, f = up_f;
@@ -182,72 +268,112 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
                         Hp[r] = h;
                         E[r] = e;
                         hu = h;
-                        if (i0 + r == q.ie && j == q.W - 1 && h != q.score) atomicOr(L.status, ST_INTERNAL);
                     }
-                    slab[((int64_t)c * q.W + j) * T + k] = word;
+                    slab[slab_off + (int64_t)jl * T + k] = word;
                     out_h = hu;
                     out_f = f;
                     if (bout && k == T - 1) {
-                        bout[2 * j] = out_h;
-                        bout[2 * j + 1] = out_f;
+                        bout[2 * jj] = out_h;
+                        bout[2 * jj + 1] = out_f;
                     }
                 }
                 diag_in = up_h;
             }
+            slab_off += (int64_t)max(width, 0) * T;
+            prev_lo = lo;
+            prev_hi = hi;
             __syncwarp();
         }
 
         // walk back from the end cell (the group's first lane)
-        if (on && k == 0 && q.p >= 0) {
-            const int64_t off = L.cig_off[q.p];
-            const int64_t cap = L.cig_off[q.p + 1] - off;
+        if (on && k == 0 && p >= 0) {
+            const int64_t off = P.cig_off[p];
+            const int64_t cap = P.cig_off[p + 1] - off;
             if (q.score <= 0) {
-                L.cig_n[q.p] = 0;
+                P.cig_n[p] = 0;
             } else {
-                RevCigar rc{L.cig_ops + off, cap, 0, 0u, 0, false};
-                rc.push(4u, q.m - 1 - q.ie);  // trailing soft clip
+                RevCigar rcg{P.cig_ops + off, cap, 0, 0u, 0, false};
+                rcg.push(4u, q.m - 1 - q.ie);  // trailing soft clip
                 int32_t i = q.ie, jj = q.W - 1;
                 int state = 0;
                 const int64_t limit = (int64_t)q.rows + q.W + 4;
-                int64_t it = 0;
-                for (; it < limit; ++it) {
-                    if (i < 0 || jj < 0) break;
-                    const int cc = i / rpc, kk = (i % rpc) / TB_ROWS, nib = i % TB_ROWS;
-                    const uint32_t code = (slab[((int64_t)cc * q.W + jj) * T + kk] >> (4 * nib)) & 0xFu;
+                // words of chunk cc start after the windows of chunks 0..cc-1
+                int cc = i / rc, clo, chi;
+                int64_t cbase = 0;
+                for (int c2 = 0; c2 < cc; ++c2) {
+                    int l2, h2;
+                    chunk_window(q, c2, rc, l2, h2);
+                    cbase += (int64_t)max(h2 - l2 + 1, 0) * T;
+                }
+                chunk_window(q, cc, rc, clo, chi);
+                bool ok = false;
+                for (int64_t it = 0; it < limit; ++it) {
+                    if (i < 0 || jj < 0) {
+                        ok = state == 0;
+                        break;
+                    }
+                    while (i < cc * rc) {  // moved up into the previous chunk
+                        --cc;
+                        chunk_window(q, cc, rc, clo, chi);
+                        cbase -= (int64_t)max(chi - clo + 1, 0) * T;
+                    }
+                    if (jj < clo || jj > chi) break;  // left the band: inconsistent
+                    const int kk = (i - cc * rc) / TB_ROWS, nib = i % TB_ROWS;
+                    const uint32_t code = (slab[cbase + (int64_t)(jj - clo) * T + kk] >> (4 * nib)) & 0xFu;
                     if (state == 0) {
                         const uint32_t src = code & 3u;
-                        if (src == 0u) break;
-                        if (src == 1u) { rc.push(0u, 1); --i; --jj; }
-                        else state = src == 2u ? 1 : 2;
+                        if (src == 0u) {
+                            ok = true;
+                            break;
+                        }
+                        if (src == 1u) {
+                            rcg.push(0u, 1);
+                            --i;
+                            --jj;
+                        } else {
+                            state = src == 2u ? 1 : 2;
+                        }
                     } else if (state == 1) {
-                        rc.push(2u, 1);
+                        rcg.push(2u, 1);
                         if (code & 4u) state = 0;
                         --jj;
                     } else {
-                        rc.push(1u, 1);
+                        rcg.push(1u, 1);
                         if (code & 8u) state = 0;
                         --i;
                     }
                 }
-                if (it >= limit || state != 0) atomicOr(L.status, ST_INTERNAL);
-                rc.push(4u, i + 1);  // leading soft clip
-                rc.flush();
-                if (rc.overflow) {
-                    L.cig_n[q.p] = -1;
+                if (!ok) atomicOr(L.status, ST_INTERNAL);
+                rcg.push(4u, i + 1);  // leading soft clip
+                rcg.flush();
+                if (rcg.overflow) {
+                    P.cig_n[p] = -1;
                     atomicOr(L.status, ST_CAPACITY);
                 } else {
-                    uint32_t *o = L.cig_ops + off;
-                    for (int32_t a = 0, b = rc.n - 1; a < b; ++a, --b) {
-                        const uint32_t tmp = o[a];
-                        o[a] = o[b];
-                        o[b] = tmp;
+                    uint32_t *o = P.cig_ops + off;
+                    for (int32_t a2 = 0, b2 = rcg.n - 1; a2 < b2; ++a2, --b2) {
+                        const uint32_t tmp = o[a2];
+                        o[a2] = o[b2];
+                        o[b2] = tmp;
                     }
-                    L.cig_n[q.p] = rc.n;
+                    P.cig_n[p] = rcg.n;
                 }
             }
         }
         __syncwarp();
     }
+}
+
+int launch_tb_keys(const TbParams &P, const int32_t *order, int64_t n_items, const int32_t *score_keys,
+                   int32_t *tb_keys, int32_t *hist, TbClassInfo *info, cudaStream_t st)
+{
+    const int threads = 256;
+    int64_t blocks = (n_items + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_tb_keys<<<(unsigned)blocks, threads, 0, st>>>(P, order, n_items, score_keys, tb_keys, hist, info);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
 }
 
 int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStream_t st)

@@ -24,6 +24,9 @@ void count_launch(int n) { g_launches += n; }
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kTbLanes = 1;            // lanes per pair in the traceback
+constexpr int kSmallSlabWords = 4096;  // per-pair slab of the main traceback launch
+constexpr size_t kSlabBudget = (size_t)4 << 30;
 constexpr int kMaxDevices = 64;
 
 struct Buffer {
@@ -42,6 +45,7 @@ struct DeviceState {
     Buffer fixed, dyn;
     Buffer stage;            // sw_batch_align_host device staging
     ClassInfo *info_host = nullptr;  // pinned
+    TbClassInfo *tbinfo_host = nullptr;  // pinned
     cudaEvent_t last_done = nullptr;
     bool last_recorded = false;
     int32_t *last_status = nullptr;  // device status word of the last call
@@ -86,6 +90,7 @@ int device_state(DeviceState **out)
         s.cc_major = prop.major;
         s.cc_minor = prop.minor;
         if (cudaMallocHost(&s.info_host, sizeof(ClassInfo)) != cudaSuccess) return SW_ERR_CUDA;
+        if (cudaMallocHost(&s.tbinfo_host, sizeof(TbClassInfo)) != cudaSuccess) return SW_ERR_CUDA;
         if (cudaEventCreateWithFlags(&s.last_done, cudaEventDisableTiming) != cudaSuccess) return SW_ERR_CUDA;
         for (cudaEvent_t &e : s.phase)
             if (cudaEventCreate(&e) != cudaSuccess) return SW_ERR_CUDA;
@@ -164,20 +169,25 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
     const size_t o_bstart = off; off = align_up(off + sizeof(int32_t) * nh, 256);
     const size_t o_cursor = off; off = align_up(off + sizeof(int32_t) * nh, 256);
     const size_t o_info = off; off = align_up(off + sizeof(ClassInfo), 256);
-    const size_t o_counters = off; off = align_up(off + sizeof(int32_t) * 2 * N_CLASS, 256);
+    const size_t o_counters = off; off = align_up(off + sizeof(int32_t) * 4 * N_CLASS, 256);
+    const size_t o_tbkeys = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
+    const size_t o_tborder = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
+    const size_t o_tbinfo = off; off = align_up(off + sizeof(TbClassInfo), 256);
     if ((rc = ensure(ds->fixed, off))) return rc;
     uint8_t *fx = (uint8_t *)ds->fixed.ptr;
     int32_t *keys = (int32_t *)(fx + o_keys), *order = (int32_t *)(fx + o_order);
     int32_t *hist = (int32_t *)(fx + o_hist), *bstart = (int32_t *)(fx + o_bstart);
     int32_t *cursor = (int32_t *)(fx + o_cursor), *counters = (int32_t *)(fx + o_counters);
     ClassInfo *info = (ClassInfo *)(fx + o_info);
+    int32_t *tb_keys = (int32_t *)(fx + o_tbkeys), *tb_order = (int32_t *)(fx + o_tborder);
+    TbClassInfo *tbinfo = (TbClassInfo *)(fx + o_tbinfo);
     ds->last_status = &info->status;
 
     ds->timed_cells_valid = false;
     if (ds->timing && cudaEventRecord(ds->phase[0], st) != cudaSuccess) return SW_ERR_CUDA;
     if (cudaMemsetAsync(hist, 0, sizeof(int32_t) * nh, st) != cudaSuccess) return SW_ERR_CUDA;
     if (cudaMemsetAsync(info, 0, sizeof(ClassInfo), st) != cudaSuccess) return SW_ERR_CUDA;
-    if (cudaMemsetAsync(counters, 0, sizeof(int32_t) * 2 * N_CLASS, st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cudaMemsetAsync(counters, 0, sizeof(int32_t) * 4 * N_CLASS, st) != cudaSuccess) return SW_ERR_CUDA;
     if ((rc = launch_classify(ps, n_reads, n_pairs, sc, keys, hist, bstart, cursor, info, order, out_score,
                               out_end, cig ? cig->n_ops : nullptr, st)))
         return rc;
@@ -193,9 +203,8 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         int64_t start, count;
         int32_t max_m, max_n;
         Plan plan;
-        int tb_lanes;
-        int score_blocks, tb_blocks;
-        size_t bnd_bytes_group, slab_words_group, tb_bnd_ints_group;
+        int score_blocks;
+        size_t bnd_bytes_group;
     };
     std::vector<ClassRun> runs;
     int64_t pos = 0;
@@ -224,23 +233,6 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         const int chunks = (r.max_m + r.plan.lanes * r.plan.rows - 1) / (r.plan.lanes * r.plan.rows);
         r.bnd_bytes_group = chunks > 1 ? (size_t)2 * r.max_n * 2 * sizeof(uint32_t) : 0;
         size_t need = r.bnd_bytes_group * (size_t)r.score_blocks * wpb * G;
-        if (cig) {
-            r.tb_lanes = std::min(32, (r.max_m + TB_ROWS - 1) / TB_ROWS);
-            const int Gt = 32 / r.tb_lanes;
-            const int tb_chunks = (r.max_m + r.tb_lanes * TB_ROWS - 1) / (r.tb_lanes * TB_ROWS);
-            r.slab_words_group = (size_t)tb_chunks * r.tb_lanes * r.max_n;
-            r.tb_bnd_ints_group = tb_chunks > 1 ? (size_t)2 * 2 * r.max_n : 0;
-            int tbps = 0;
-            if ((rc = traceback_kernel_occupancy(&tbps, kThreads))) return rc;
-            const int64_t tw_needed = (cnt + Gt - 1) / Gt;
-            int64_t tblocks = std::min<int64_t>((tw_needed + wpb - 1) / wpb, (int64_t)std::max(tbps, 1) * ds->sm_count);
-            // keep the slabs of one launch within a memory budget
-            const size_t per_block = (size_t)wpb * Gt * (r.slab_words_group * 4 + r.tb_bnd_ints_group * 4);
-            const size_t budget = (size_t)4 << 30;
-            tblocks = std::max<int64_t>(1, std::min<int64_t>(tblocks, (int64_t)(budget / std::max<size_t>(per_block, 1))));
-            r.tb_blocks = (int)tblocks;
-            need = std::max(need, per_block * (size_t)tblocks);
-        }
         need_dyn = std::max(need_dyn, need);
         runs.push_back(r);
     }
@@ -263,28 +255,73 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         if ((rc = launch_score(r.plan.rows, r.mode, L, r.score_blocks, kThreads, st))) return rc;
     }
     if (ds->timing && cudaEventRecord(ds->phase[2], st) != cudaSuccess) return SW_ERR_CUDA;
-    for (const ClassRun &r : runs) {
-        if (!cig) break;
-        TracebackLaunch B{};
-        B.ps = ps;
-        B.sc = sc;
-        B.order = order + r.start;
-        B.n_items = r.count;
-        B.lanes = r.tb_lanes;
-        B.score = out_score;
-        B.end = out_end;
-        B.cig_ops = cig->ops;
-        B.cig_off = cig->offsets;
-        B.cig_n = cig->n_ops;
-        const int Gt = 32 / r.tb_lanes;
-        const size_t slab_total = (size_t)r.tb_blocks * (kThreads / 32) * Gt * r.slab_words_group;
-        B.slab = (uint32_t *)ds->dyn.ptr;
-        B.slab_group_words = (int64_t)r.slab_words_group;
-        B.boundary = r.tb_bnd_ints_group ? (int32_t *)ds->dyn.ptr + slab_total : nullptr;
-        B.boundary_group_ints = (int64_t)r.tb_bnd_ints_group;
-        B.work_counter = counters + N_CLASS + r.cls;
-        B.status = &info->status;
-        if ((rc = launch_traceback(B, r.tb_blocks, kThreads, st))) return rc;
+    if (cig) {
+        // order each class by traceback cost, then size the slabs from the
+        // per-class maxima (a second, small read-back)
+        const int64_t n_items = pos;
+        TbParams P{ps, sc, out_score, out_end, cig->ops, cig->offsets, cig->n_ops, kTbLanes, kSmallSlabWords};
+        if (cudaMemsetAsync(hist, 0, sizeof(int32_t) * nh, st) != cudaSuccess) return SW_ERR_CUDA;
+        if (cudaMemsetAsync(tbinfo, 0, sizeof(TbClassInfo), st) != cudaSuccess) return SW_ERR_CUDA;
+        if (cudaMemsetAsync(tb_keys, 0xFF, sizeof(int32_t) * n_pairs, st) != cudaSuccess) return SW_ERR_CUDA;
+        if ((rc = launch_tb_keys(P, order, n_items, keys, tb_keys, hist, tbinfo, st))) return rc;
+        if ((rc = launch_scan_scatter(tb_keys, n_pairs, hist, bstart, cursor, tb_order, st))) return rc;
+        if (cudaMemcpyAsync(ds->tbinfo_host, tbinfo, sizeof(TbClassInfo), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess)
+            return SW_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
+        const TbClassInfo ti = *ds->tbinfo_host;
+        int tbps = 0;
+        if ((rc = traceback_kernel_occupancy(&tbps, kThreads))) return rc;
+        const int G = 32 / kTbLanes;
+        const int64_t wpb = kThreads / 32;
+        struct TbRun {
+            int64_t start, count;
+            int64_t slab_words, bnd_ints;
+            int blocks;
+            int cls, part;
+        };
+        std::vector<TbRun> tbr;
+        size_t need = 0;
+        for (const ClassRun &r : runs) {
+            const int64_t big = ti.n_big[r.cls];
+            const int64_t max_need = std::max<int64_t>(ti.max_need[r.cls], 1);
+            const int64_t parts[2][2] = {{r.start, big}, {r.start + big, r.count - big}};
+            for (int part = 0; part < 2; ++part) {
+                const int64_t cnt = parts[part][1];
+                if (cnt <= 0) continue;
+                TbRun t{};
+                t.start = parts[part][0];
+                t.count = cnt;
+                t.slab_words = part == 0 ? max_need : std::min<int64_t>(max_need, kSmallSlabWords);
+                const int chunks = (r.max_m + kTbLanes * TB_ROWS - 1) / (kTbLanes * TB_ROWS);
+                t.bnd_ints = chunks > 1 ? (int64_t)2 * 2 * r.max_n : 0;
+                const size_t per_block = (size_t)wpb * G * (t.slab_words + t.bnd_ints) * 4;
+                int64_t blocks = std::min<int64_t>(((cnt + G - 1) / G + wpb - 1) / wpb,
+                                                   (int64_t)std::max(tbps, 1) * ds->sm_count);
+                blocks = std::min<int64_t>(blocks, (int64_t)(kSlabBudget / std::max<size_t>(per_block, 1)));
+                t.blocks = (int)std::max<int64_t>(blocks, 1);
+                t.cls = r.cls;
+                t.part = part;
+                need = std::max(need, per_block * (size_t)t.blocks);
+                tbr.push_back(t);
+            }
+        }
+        if ((rc = ensure(ds->dyn, std::max<size_t>(need, 256)))) return rc;
+        for (const TbRun &t : tbr) {
+            TracebackLaunch B{};
+            B.P = P;
+            B.order = tb_order + t.start;
+            B.n_items = t.count;
+            B.lanes = kTbLanes;
+            B.slab = (uint32_t *)ds->dyn.ptr;
+            B.slab_group_words = t.slab_words;
+            const size_t slab_total = (size_t)t.blocks * wpb * G * t.slab_words;
+            B.boundary = (int32_t *)ds->dyn.ptr + slab_total;
+            B.boundary_group_ints = t.bnd_ints;
+            B.work_counter = counters + 2 * N_CLASS + 2 * t.cls + t.part;
+            B.status = &info->status;
+            if ((rc = launch_traceback(B, t.blocks, kThreads, st))) return rc;
+        }
     }
     if (ds->timing && cudaEventRecord(ds->phase[3], st) != cudaSuccess) return SW_ERR_CUDA;
     ds->timed_cells_valid = ds->timing;

@@ -65,17 +65,30 @@ struct ScoreLaunch {
     int32_t *status;
 };
 
-struct TracebackLaunch {
+// What every traceback kernel needs about the batch.
+struct TbParams {
     PairSet ps;
     Scoring sc;
-    const int32_t *order;
-    int64_t n_items;
-    int32_t lanes;
     const int32_t *score;
     const int32_t *end;
     uint32_t *cig_ops;
     const int64_t *cig_off;
     int32_t *cig_n;
+    int32_t lanes;            // T lanes per pair
+    int32_t small_slab_words; // per-group slab of the main launch
+};
+
+// Per-class facts of the traceback sort, read back to size the slabs.
+struct TbClassInfo {
+    int32_t max_need[N_CLASS];  // largest slab (words) a pair of the class needs
+    int32_t n_big[N_CLASS];     // pairs needing more than small_slab_words
+};
+
+struct TracebackLaunch {
+    TbParams P;
+    const int32_t *order;
+    int64_t n_items;
+    int32_t lanes;
     uint32_t *slab;          // per-group traceback bit slabs
     int64_t slab_group_words;
     int32_t *boundary;       // per-group chunk boundaries (2 x int32 per column, double-buffered)
@@ -95,6 +108,10 @@ int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring
                     int32_t *cig_n, cudaStream_t st);
 int launch_score(int rows, int mode, const ScoreLaunch &L, int blocks, int threads, cudaStream_t st);
 int score_kernel_regs(int rows, int mode, int *regs, int *max_blocks_per_sm, int threads);
+int launch_tb_keys(const TbParams &P, const int32_t *order, int64_t n_items, const int32_t *score_keys,
+                   int32_t *tb_keys, int32_t *hist, TbClassInfo *info, cudaStream_t st);
+int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, int32_t *hist, int32_t *bucket_start,
+                        int32_t *cursor, int32_t *order, cudaStream_t st);
 int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStream_t st);
 int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads);
 int launch_alu_probe(int kind, int64_t iters, int blocks, int threads, uint32_t *out, cudaStream_t st);

@@ -198,6 +198,27 @@ def test_rectangle_traceback_equals_full():
             np.testing.assert_array_equal(ops, ops2)
 
 
+def test_band_traceback_equals_full():
+    """Rectangle and band are exactness arguments of the CUDA traceback; the
+    oracle checks both against its full matrix on tie-heavy inputs."""
+    wl = synth.generate("parity", seed=14, n_reads=150)
+    rnd = synth.random_pairs(400, (1, 60), (1, 90), seed=16, alphabet=2)
+    spl = synth.generate("uneven", seed=3, n_reads=60)
+    for wk in (wl, rnd, spl):
+        for p in range(wk.n_pairs):
+            sc = SCORINGS[p % len(SCORINGS)]
+            r = wk.reads[wk.read_offsets[wk.pair_read[p]]:wk.read_offsets[wk.pair_read[p] + 1]]
+            w = wk.windows[wk.window_offsets[p]:wk.window_offsets[p + 1]]
+            s, ie, je, ops = oracle.align(r, w, sc)
+            np.testing.assert_array_equal(ops, oracle.band_traceback(r, w, s, ie, je, sc))
+
+
+def test_insertion_bound():
+    # 490 with one inserted read base in 101: (5*101 - 10 + 1 - 490) / 6 = 1
+    assert oracle.insertion_bound(100, 490) == 1
+    assert oracle.insertion_bound(99, 500) == 0
+
+
 def test_deletion_bound_is_tight_enough():
     # a 1-bp window insertion in an otherwise perfect 100-bp alignment: score
     # 490, so at most (5*100 - 10 - 490) / 1 + 1 = 1 deletion
