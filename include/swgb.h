@@ -160,6 +160,37 @@ int sw_batch_align_host(const uint8_t *reads, const int64_t *read_offsets,
  */
 int sw_sync_status(sw_stream_t stream);
 
+/*
+ * sw_batch_align_noalloc -- score and end cell of pair p = (read p, window p),
+ * like sw_batch_align with out_cigar == NULL, without the library allocating
+ * any memory.  The paper has no counterpart; this is for callers that cannot
+ * let a library call cudaMalloc or cudaFree: applications that give all
+ * device memory to their own pool allocator, or latency-sensitive services
+ * that cannot afford the device synchronisation those calls imply.
+ *
+ * Its scratch (work counter, status word, pair order) is one fixed array of
+ * 4 * (64 + SW_NOALLOC_MAX_PAIRS) bytes in the library's static device
+ * memory, which every GPU that loads the library holds until the process
+ * exits.  Limits: n_pairs <= SW_NOALLOC_MAX_PAIRS (else SW_ERR_UNSUPPORTED,
+ * checked before any GPU work) and reads of at most SW_NOALLOC_MAX_READ_LEN
+ * bases (else SW_ERR_UNSUPPORTED, detected on the device).  Arguments,
+ * layouts, scoring requirements and outputs are those of sw_batch_align.
+ *
+ * The first call on a device looks up the array's device address, so make it
+ * before any other work that must not be interrupted by that set-up.  Every
+ * call on a device uses the same array (it keeps the previous call's
+ * contents; the call clears what must start at zero), so calls whose GPU
+ * work overlaps -- on different streams or from different threads -- race;
+ * serialise them.  Like sw_batch_align, the call waits on `stream` for a
+ * validation step, then enqueues the score kernel and returns.
+ */
+#define SW_NOALLOC_MAX_PAIRS 262144
+#define SW_NOALLOC_MAX_READ_LEN 1024
+int sw_batch_align_noalloc(const uint8_t *reads, const int64_t *read_offsets,
+                           const uint8_t *windows, const int64_t *window_offsets,
+                           int64_t n_pairs, const sw_scoring_t *scoring,
+                           int32_t *out_score, int32_t *out_end, sw_stream_t stream);
+
 /* Text of an SW_* code (static storage). */
 const char *sw_strerror(int code);
 

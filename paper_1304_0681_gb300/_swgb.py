@@ -23,7 +23,7 @@ ERRORS = {
 #: every symbol include/swgb.h declares
 EXPORTS = ("sw_cigar_capacity", "sw_packed_bytes", "sw_batch_align", "sw_batch_align_indexed",
            "sw_batch_align_host", "sw_sync_status", "sw_strerror", "sw_launch_count", "sw_set_plan",
-           "sw_plan_rows", "sw_alu_probe", "sw_phase_timing", "sw_phase_times")
+           "sw_plan_rows", "sw_alu_probe", "sw_phase_timing", "sw_phase_times", "sw_batch_align_noalloc")
 
 
 class SwError(RuntimeError):
@@ -58,6 +58,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_batch_align_indexed.restype = ctypes.c_int
     lib.sw_batch_align_host.argtypes = [p, p, p, p, i64, ctypes.POINTER(Scoring), p, p, ctypes.POINTER(Cigar), p]
     lib.sw_batch_align_host.restype = ctypes.c_int
+    lib.sw_batch_align_noalloc.argtypes = [p, p, p, p, i64, ctypes.POINTER(Scoring), p, p, p]
+    lib.sw_batch_align_noalloc.restype = ctypes.c_int
     lib.sw_sync_status.argtypes = [p]
     lib.sw_sync_status.restype = ctypes.c_int
     lib.sw_strerror.argtypes = [ctypes.c_int]
@@ -136,6 +138,16 @@ def sw_batch_align_host(reads, read_offsets, windows, window_offsets, n_pairs: i
                                     int(n_pairs), ctypes.byref(sc), _ptr(out_score), _ptr(out_end),
                                     ctypes.byref(cg) if cg is not None else None, _stream(stream)),
            "sw_batch_align_host")
+
+
+def sw_batch_align_noalloc(reads, read_offsets, windows, window_offsets, n_pairs: int, scoring, out_score, out_end,
+                           stream=None) -> None:
+    """Score and end cell with the library's fixed static scratch (no
+    allocation); see include/swgb.h for the limits."""
+    sc = _scoring(scoring)
+    _check(_lib.sw_batch_align_noalloc(_ptr(reads), _ptr(read_offsets), _ptr(windows), _ptr(window_offsets),
+                                       int(n_pairs), ctypes.byref(sc), _ptr(out_score), _ptr(out_end),
+                                       _stream(stream)), "sw_batch_align_noalloc")
 
 
 def sw_sync_status(stream=None) -> None:
