@@ -105,6 +105,8 @@ def test_clean_copy_passes(tmp_path):
 def test_mutant_is_caught(tmp_path, name):
     before, after = MUTANTS[name]
     text = open(ORACLE_SRC).read()
-    assert text.count(before) == 1, f"mutation anchor for {name!r} not found exactly once"
+    # the recurrence is written out in more than one oracle function: plant
+    # the mistake wherever the anchor text occurs
+    assert text.count(before) >= 1, f"mutation anchor for {name!r} not found"
     lib = _build_variant(tmp_path, "mut", text.replace(before, after))
     assert run_pins(lib), f"planted mistake {name!r} passed every pin"
