@@ -106,7 +106,7 @@ struct Arith<MODE_I32> {
     typedef int32_t V;
     static __device__ __forceinline__ V addmax(V a, V b, V c) { return __viaddmax_s32(a, b, c); }
     static __device__ __forceinline__ V addmax_relu(V a, V b, V c) { return __viaddmax_s32_relu(a, b, c); }
-    static __device__ __forceinline__ V max_relu(V a, V b) { return __vimax_s32_relu(a, b); }
+    static __device__ __forceinline__ V max3(V a, V b, V c) { return __vimax3_s32(a, b, c); }
     static __device__ __forceinline__ V add(V a, V b) { return a + b; }
     static __device__ __forceinline__ V splat(int32_t x) { return x; }
 };
@@ -116,29 +116,42 @@ struct Arith<MODE_I16> {
     typedef uint32_t V;
     static __device__ __forceinline__ V addmax(V a, V b, V c) { return __viaddmax_s16x2(a, b, c); }
     static __device__ __forceinline__ V addmax_relu(V a, V b, V c) { return __viaddmax_s16x2_relu(a, b, c); }
-    static __device__ __forceinline__ V max_relu(V a, V b) { return __vimax_s16x2_relu(a, b); }
-    // per-half add of a constant (no carry between halves): max(a + b, -32768)
+    static __device__ __forceinline__ V max3(V a, V b, V c) { return __vimax3_s16x2(a, b, c); }
+    // per-half add (no carry between halves): max(a + b, -32768)
     static __device__ __forceinline__ V add(V a, V b) { return __viaddmax_s16x2(a, b, 0x80008000u); }
     static __device__ __forceinline__ V splat(int32_t x) { return ((uint32_t)(uint16_t)(int16_t)x) * 0x10001u; }
 };
 template <>
 struct Arith<MODE_I16W> : Arith<MODE_I16> {};
 
-// Column table: byte x = s(x, w) - o for read base x, or all zero when the
-// column is padding.
-__device__ __forceinline__ uint32_t col_table(uint32_t w, bool valid, uint32_t mis4, uint32_t ma4)
+// a * one + c on the FMA pipe; `one` is a kernel argument equal to 1, so the
+// multiply-add cannot be folded into an ALU add.  With both halves of a and c
+// non-negative and their sums below 32768 it is an exact per-half add.
+__device__ __forceinline__ uint32_t mad_add(uint32_t a, uint32_t one, uint32_t c)
 {
-    const uint32_t t = prmt(mis4, ma4, 0x3210u + (4u << (w * 4u)));
-    return valid ? t : 0u;
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(one), "r"(c));
+    return d;
 }
 
-template <int R, int MODE>
+template <int R, int MODE, bool FMA_ADD>
 __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
 {
     typedef Arith<MODE> A;
     typedef typename A::V V;
     constexpr bool PAIR2 = MODE != MODE_I32;
     constexpr int NW = (R + 7) / 8;
+
+    // column tables: s_tab[w] byte x = s(x, w) - o; s_tab[4] = 0 (padding)
+    __shared__ uint32_t s_tab[8];
+    const int32_t go = L.sc.go, ge = L.sc.ge;
+    {
+        const uint32_t mis4 = ((uint32_t)(uint8_t)(int8_t)(L.sc.mi - go)) * 0x01010101u;
+        const uint32_t ma4 = ((uint32_t)(uint8_t)(int8_t)(L.sc.ma - go)) * 0x01010101u;
+        if (threadIdx.x < 8)
+            s_tab[threadIdx.x] = threadIdx.x < 4 ? prmt(mis4, ma4, 0x3210u + (4u << (4u * threadIdx.x))) : 0u;
+        __syncthreads();
+    }
 
     const int lane = threadIdx.x & 31;
     const int T = L.lanes;
@@ -148,13 +161,10 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
     const bool on = g < G;
     const int per_warp = G * (PAIR2 ? 2 : 1);
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-
-    const int32_t go = L.sc.go, ge = L.sc.ge;
+    const uint32_t one = (uint32_t)L.one;
     const V GO = A::splat(go), GE = A::splat(ge);
-    const uint32_t mis4 = ((uint32_t)(uint8_t)(int8_t)(L.sc.mi - go)) * 0x01010101u;
-    const uint32_t ma4 = ((uint32_t)(uint8_t)(int8_t)(L.sc.ma - go)) * 0x01010101u;
 
-    uint8_t *bnd = L.boundary ? L.boundary + (warp_global * G + g) * L.boundary_group_bytes : nullptr;
+    uint8_t *bnd = (on && L.boundary) ? L.boundary + (warp_global * G + g) * L.boundary_group_bytes : nullptr;
     const int64_t bnd_half = L.boundary_group_bytes / 2;  // bytes per buffer of the double buffer
 
     for (;;) {
@@ -169,6 +179,10 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
         const int32_t mg = max(pa.m, pb.m), ng = max(pa.n, pb.n);
         const int32_t mw = __reduce_max_sync(FULL, (unsigned)mg);
         const int32_t nw = __reduce_max_sync(FULL, (unsigned)ng);
+        // columns every real pair of the warp has (empty slots never feed a
+        // real pair, so they do not limit the fast path)
+        const int32_t na = pa.m ? pa.n : INT32_MAX, nbb = pb.m ? pb.n : INT32_MAX;
+        const int32_t nmin_w = (int32_t)__reduce_min_sync(FULL, (unsigned)min(na, nbb));
         const int rows_per_chunk = T * R;
         const int chunks = (mw + rows_per_chunk - 1) / rows_per_chunk;
         const int steps = nw + T - 1;
@@ -196,81 +210,103 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
                     }
                 }
             }
-            V e[R], ho[R];
+            // per row: E - o and H of the previous column (E floored at o,
+            // which never changes H)
+            V e[R], h[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 e[r] = 0;
-                ho[r] = GO;
+                h[r] = 0;
             }
-            V diag_in = GO;           // H(i0-1, j-1) + o
-            V out_ho = GO, out_f = 0;  // bottom row handed to the next lane
+            V diag_in = 0;             // H(i0-1, j-1)
+            V out_h = 0, out_f = 0;    // bottom row (H, F - o) handed to the next lane
             // running best of this chunk
             uint32_t bk0 = PAIR2 && MODE == MODE_I16 ? 0x001F001Fu : 0u, bk1 = 0u;
             uint32_t rowA = 0, rowB = 0;
             int32_t jA = 0, jB = 0;
-            // window stream
+            // window stream: 2-bit codes of the next columns (up to 16)
             uint32_t wwA = 0, wwB = 0;
             const bool load_bnd = c > 0;
             const bool store_bnd = c + 1 < chunks;
-            const V *bin = load_bnd ? (const V *)(bnd + (c & 1) * bnd_half) : nullptr;
-            V *bout = store_bnd ? (V *)(bnd + ((c + 1) & 1) * bnd_half) : nullptr;
+            const V *bin = load_bnd && bnd ? (const V *)(bnd + (c & 1) * bnd_half) : nullptr;
+            V *bout = store_bnd && bnd ? (V *)(bnd + ((c + 1) & 1) * bnd_half) : nullptr;
 
             for (int t = 0; t < steps; ++t) {
                 const int j = t - k;
-                V up_ho = __shfl_up_sync(FULL, out_ho, 1);
+                V up_h = __shfl_up_sync(FULL, out_h, 1);
                 V up_f = __shfl_up_sync(FULL, out_f, 1);
                 if (k == 0) {
-                    if (load_bnd && j < ng) {
-                        up_ho = bin[2 * j];
+                    if (bin && j < ng) {
+                        up_h = bin[2 * j];
                         up_f = bin[2 * j + 1];
                     } else {
-                        up_ho = GO;
+                        up_h = 0;
                         up_f = 0;
                     }
                 }
-                // window bases of this column
+                // column tables
                 uint32_t twA = 0, twB = 0;
                 if (j >= 0) {
                     if ((j & 15) == 0) {
                         wwA = j < pa.n ? load_bases(L.ps.wins, pa.ws + j, min(16, pa.n - j)) : 0u;
                         if (PAIR2) wwB = j < pb.n ? load_bases(L.ps.wins, pb.ws + j, min(16, pb.n - j)) : 0u;
                     }
-                    twA = col_table(wwA & 3u, j < pa.n, mis4, ma4);
-                    wwA >>= 2;
-                    if (PAIR2) {
-                        twB = col_table(wwB & 3u, j < pb.n, mis4, ma4);
-                        wwB >>= 2;
+                    if (t < nmin_w) {  // every real pair of the warp has column j
+                        twA = s_tab[wwA & 3u];
+                        if (PAIR2) twB = s_tab[wwB & 3u];
+                    } else {
+                        twA = s_tab[j < pa.n ? wwA & 3u : 4u];
+                        if (PAIR2) twB = s_tab[j < pb.n ? wwB & 3u : 4u];
                     }
+                    wwA >>= 2;
+                    if (PAIR2) wwB >>= 2;
                 }
-                V hd = diag_in, hu = up_ho, f = up_f;
-                uint32_t ck0 = 0, ck1 = 0;  // column keys
+                V hd = diag_in, hu = up_h, f = up_f;
+                uint32_t ck0 = 0, ck1 = 0, pk0 = 0, pk1 = 0;  // column keys, pending key
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const V s = (V)prmt(twA, twB, sel[r]);
-                    e[r] = A::addmax_relu(e[r], GE, ho[r]);
-                    f = A::addmax_relu(f, GE, hu);
-                    const V h = A::addmax(hd, s, A::max_relu(e[r], f));
-                    hd = ho[r];
-                    ho[r] = A::add(h, GO);
-                    hu = ho[r];
+                    e[r] = A::addmax(e[r], GE, h[r]);
+                    f = A::addmax(f, GE, hu);
+                    const V d = FMA_ADD ? (V)mad_add((uint32_t)hd, one, (uint32_t)s) : A::add(hd, s);
+                    const V hn = A::addmax_relu(A::max3(d, e[r], f), GO, 0);
+                    hd = h[r];
+                    h[r] = hn;
+                    hu = hn;
+                    uint32_t k0, k1 = 0;
                     if (MODE == MODE_I32) {
-                        const uint32_t key = (uint32_t)h * 32u + (uint32_t)(31 - r);
-                        ck0 = r == 0 ? key : max(ck0, key);
+                        k0 = mad_add((uint32_t)hn, 32u, (uint32_t)(31 - r));
                     } else if (MODE == MODE_I16) {
-                        const uint32_t key = (uint32_t)h * 32u + (uint32_t)(31 - r) * 0x10001u;
-                        ck0 = r == 0 ? key : __vimax3_s16x2(ck0, key, key);
+                        k0 = mad_add((uint32_t)hn, 32u, (uint32_t)(31 - r) * 0x10001u);
                     } else {
-                        const uint32_t ka = (uint32_t)h * 65536u + (uint32_t)(31 - r);
-                        const uint32_t kb = ((uint32_t)h & 0xFFFF0000u) | (uint32_t)(31 - r);
-                        ck0 = r == 0 ? ka : max(ck0, ka);
-                        ck1 = r == 0 ? kb : max(ck1, kb);
+                        k0 = mad_add((uint32_t)hn, 65536u, (uint32_t)(31 - r));
+                        k1 = ((uint32_t)hn & 0xFFFF0000u) | (uint32_t)(31 - r);
+                    }
+                    // three-way max over pairs of rows
+                    if (r % 2 == 0) {
+                        pk0 = k0;
+                        pk1 = k1;
+                    } else if (MODE == MODE_I16) {
+                        ck0 = r == 1 ? __vimax_s16x2_relu(pk0, k0) : __vimax3_s16x2(ck0, pk0, k0);
+                    } else {
+                        ck0 = r == 1 ? max(pk0, k0) : (uint32_t)__vimax3_s32((int)ck0, (int)pk0, (int)k0);
+                        if (MODE == MODE_I16W)
+                            ck1 = r == 1 ? max(pk1, k1) : (uint32_t)__vimax3_s32((int)ck1, (int)pk1, (int)k1);
                     }
                 }
-                diag_in = up_ho;
-                out_ho = ho[R - 1];
+                if (R % 2 == 1) {
+                    if (MODE == MODE_I16) {
+                        ck0 = R == 1 ? pk0 : __vimax_s16x2_relu(ck0, pk0);
+                    } else {
+                        ck0 = R == 1 ? pk0 : max(ck0, pk0);
+                        if (MODE == MODE_I16W) ck1 = R == 1 ? pk1 : max(ck1, pk1);
+                    }
+                }
+                diag_in = up_h;
+                out_h = h[R - 1];
                 out_f = f;
-                if (store_bnd && k == T - 1 && j >= 0 && j < ng) {
-                    bout[2 * j] = out_ho;
+                if (bout && k == T - 1 && j >= 0 && j < ng) {
+                    bout[2 * j] = out_h;
                     bout[2 * j + 1] = out_f;
                 }
                 // strict improvement of H keeps the first (smallest) column
@@ -295,8 +331,8 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
             // fold the chunk's best into the 64-bit per-lane best
             const int rbase = c * rows_per_chunk + k * R;
             if (MODE == MODE_I32) {
-                const uint32_t h = bk0 >> 5;
-                if (h) bestA = max(bestA, cell_key(h, jA, rbase + 31 - (int)(bk0 & 31u)));
+                const uint32_t hb = bk0 >> 5;
+                if (hb) bestA = max(bestA, cell_key(hb, jA, rbase + 31 - (int)(bk0 & 31u)));
             } else if (MODE == MODE_I16) {
                 const uint32_t ha = (bk0 & 0xFFFFu) >> 5, hb = (bk0 >> 16) >> 5;
                 if (ha) bestA = max(bestA, cell_key(ha, jA, rbase + 31 - (int)(rowA & 31u)));
@@ -334,26 +370,31 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
 const int kScoreRows[N_SCORE_ROWS] = {8, 16, 20, 25, 32};
 
 template <int R>
-static int launch_r(int mode, const ScoreLaunch &L, int blocks, int threads, cudaStream_t st)
+static int launch_r(int mode, bool fma, const ScoreLaunch &L, int blocks, int threads, cudaStream_t st)
 {
-    switch (mode) {
-    case MODE_I32: k_score<R, MODE_I32><<<blocks, threads, 0, st>>>(L); break;
-    case MODE_I16: k_score<R, MODE_I16><<<blocks, threads, 0, st>>>(L); break;
-    case MODE_I16W: k_score<R, MODE_I16W><<<blocks, threads, 0, st>>>(L); break;
-    default: return SW_ERR_INTERNAL;
-    }
+    if (mode == MODE_I32) k_score<R, MODE_I32, true><<<blocks, threads, 0, st>>>(L);
+    else if (mode == MODE_I16 && fma) k_score<R, MODE_I16, true><<<blocks, threads, 0, st>>>(L);
+    else if (mode == MODE_I16) k_score<R, MODE_I16, false><<<blocks, threads, 0, st>>>(L);
+    else if (mode == MODE_I16W && fma) k_score<R, MODE_I16W, true><<<blocks, threads, 0, st>>>(L);
+    else if (mode == MODE_I16W) k_score<R, MODE_I16W, false><<<blocks, threads, 0, st>>>(L);
+    else return SW_ERR_INTERNAL;
     count_launch();
     return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
 }
 
+// The FMA-pipe diagonal add needs every substitution score minus gap_open
+// to be >= 0 in the 16-bit modes (no borrow between halves).
+static bool fma_add_ok(const ScoreLaunch &L) { return L.sc.mi - L.sc.go >= 0; }
+
 int launch_score(int rows, int mode, const ScoreLaunch &L, int blocks, int threads, cudaStream_t st)
 {
+    const bool fma = fma_add_ok(L);
     switch (rows) {
-    case 8: return launch_r<8>(mode, L, blocks, threads, st);
-    case 16: return launch_r<16>(mode, L, blocks, threads, st);
-    case 20: return launch_r<20>(mode, L, blocks, threads, st);
-    case 25: return launch_r<25>(mode, L, blocks, threads, st);
-    case 32: return launch_r<32>(mode, L, blocks, threads, st);
+    case 8: return launch_r<8>(mode, fma, L, blocks, threads, st);
+    case 16: return launch_r<16>(mode, fma, L, blocks, threads, st);
+    case 20: return launch_r<20>(mode, fma, L, blocks, threads, st);
+    case 25: return launch_r<25>(mode, fma, L, blocks, threads, st);
+    case 32: return launch_r<32>(mode, fma, L, blocks, threads, st);
     default: return SW_ERR_INVALID_ARG;
     }
 }
@@ -362,9 +403,9 @@ template <int R>
 static const void *kernel_ptr(int mode)
 {
     switch (mode) {
-    case MODE_I32: return (const void *)k_score<R, MODE_I32>;
-    case MODE_I16: return (const void *)k_score<R, MODE_I16>;
-    case MODE_I16W: return (const void *)k_score<R, MODE_I16W>;
+    case MODE_I32: return (const void *)k_score<R, MODE_I32, true>;
+    case MODE_I16: return (const void *)k_score<R, MODE_I16, false>;
+    case MODE_I16W: return (const void *)k_score<R, MODE_I16W, false>;
     default: return nullptr;
     }
 }
