@@ -1,0 +1,107 @@
+"""Pins of the learned-filter reference (oracle/filter_oracle.py)."""
+import numpy as np
+
+from oracle import filter_oracle as fo
+from sw_checks import encode
+
+
+def test_feature_closed_forms():
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        m = int(rng.integers(4, 200))
+        r = rng.integers(0, 4, m).astype(np.uint8)
+        # identical strings: every 4-mer shared, features sum to 1
+        assert abs(fo.features(r, r).sum() - 1.0) < 1e-12
+        # window holding the read twice: still capped by the read's counts
+        assert abs(fo.features(r, np.concatenate([r, r])).sum() - 1.0) < 1e-12
+        # disjoint alphabets share nothing
+        a = rng.integers(0, 2, m).astype(np.uint8)
+        b = (rng.integers(0, 2, m + 5) + 2).astype(np.uint8)
+        assert fo.features(a, b).sum() == 0.0
+    # homopolymers: A^m against A^n -> only prefix AAA, min(m-3, n-3)/(m-3)
+    f = fo.features(np.zeros(10, np.uint8), np.zeros(7, np.uint8))
+    assert f[0] == 4 / 7 and f[1:].sum() == 0
+    # reads shorter than one 4-mer have no features
+    assert fo.features(np.zeros(3, np.uint8), np.zeros(50, np.uint8)).sum() == 0
+
+
+def test_feature_fold_by_prefix():
+    # ACGT and ACGA share prefix ACG (k = 0*16 + 1*4 + 2 = 6)
+    r = encode("ACGT")
+    w = encode("ACGTACGA")
+    f = fo.features(r, w)
+    assert f[6] == 1.0 and f.sum() == 1.0
+    # a window containing only ACGA shares nothing with a read ACGT
+    assert fo.features(encode("ACGT"), encode("ACGA")).sum() == 0.0
+
+
+def test_kmer_counts_against_string_windows():
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        s = rng.integers(0, 4, int(rng.integers(0, 40))).astype(np.uint8)
+        text = "".join("ACGT"[x] for x in s)
+        c = fo.kmer_counts(s)
+        for q in range(256):
+            kmer = "".join("ACGT"[(q >> sh) & 3] for sh in (6, 4, 2, 0))
+            assert c[q] == sum(text[i:i + 4] == kmer for i in range(max(len(text) - 3, 0)))
+
+
+def test_gradient_matches_finite_differences():
+    rng = np.random.default_rng(2)
+    P = fo.Params.init(3)
+    X = rng.uniform(0, 0.3, (16, fo.N_FEAT))
+    t = rng.uniform(0, 1, 16)
+    g = fo.backward(P, X, t)
+    theta = P.flat()
+    assert len(theta) == fo.N_PARAMS == 33153
+    idx = rng.choice(len(theta), 300, replace=False)
+    h = 1e-6
+    for i in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        num = (fo.loss(fo.Params.from_flat(tp), X, t) - fo.loss(fo.Params.from_flat(tm), X, t)) / (2 * h)
+        assert abs(num - g[i]) <= 1e-6 * max(1.0, abs(num)), (i, num, g[i])
+
+
+def test_forward_closed_forms():
+    z = fo.Params(np.zeros((64, 256)), np.zeros(256), np.zeros((256, 64)), np.zeros(64), np.zeros(64), 0.25)
+    X = np.random.default_rng(4).uniform(0, 1, (5, 64))
+    np.testing.assert_array_equal(fo.forward(z, X)[0], np.full(5, 0.25))
+    # a path that copies feature 7 through both ReLUs
+    W1 = np.zeros((64, 256)); W1[7, 3] = 1.0
+    W2 = np.zeros((256, 64)); W2[3, 5] = 2.0
+    w3 = np.zeros(64); w3[5] = 0.5
+    P = fo.Params(W1, np.zeros(256), W2, np.zeros(64), w3, 0.0)
+    np.testing.assert_allclose(fo.forward(P, X)[0], X[:, 7])
+    # negative pre-activations are cut by the ReLU
+    P.b1[3] = -10.0
+    np.testing.assert_array_equal(fo.forward(P, X)[0], np.zeros(5))
+
+
+def test_adam_first_step_is_lr_times_sign():
+    g = np.array([0.5, -2.0, 1e-3])
+    th, m, v = fo.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, 0.01)
+    np.testing.assert_allclose(th, -0.01 * np.sign(g), rtol=1e-4)
+
+
+def test_bf16_round():
+    v = np.array([1.0, 1.0 + 2 ** -9, 1.0 + 3 * 2 ** -9, -2.5, 3.140625, 1e-40])
+    r = fo.bf16_round(v)
+    assert r[0] == 1.0
+    assert r[1] == 1.0                   # halfway, ties to even
+    assert r[2] == 1.0 + 2 ** -7         # halfway, ties to even (up)
+    assert r[3] == -2.5 and r[4] == 3.140625
+
+
+def test_select_candidates():
+    pred = np.array([0.9, 0.1, 0.5, 0.2, 0.2, 0.8, 0.79, 0.1])
+    off = np.array([0, 4, 8])
+    sel = fo.select_candidates(pred, off, k=1, tau=0.05)
+    # read 0: best 0.9, next 0.5 -> margin 0.4 -> only candidate 0
+    # read 1: best 0.8, next 0.79 -> margin 0.01 < tau -> all four
+    np.testing.assert_array_equal(sel, [True, False, False, False, True, True, True, True])
+    sel = fo.select_candidates(pred, off, k=2, tau=0.0)
+    np.testing.assert_array_equal(sel, [True, False, True, False, False, True, True, False])
+    best = fo.best_per_read(np.array([5, 9, 1, 2, 7, 3, 8, 0]), off, sel)
+    np.testing.assert_array_equal(best, [5, 8])
