@@ -53,6 +53,8 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-filter", action="store_true", help="skip the learned-filter comparison")
+    ap.add_argument("--filter-reads", type=int, default=500_000)
     return ap.parse_args()
 
 
@@ -146,6 +148,95 @@ def _traffic_record(kernel_file: str):
     if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
         return None
     return rec
+
+
+def _filter_section(args, rank, steps: int) -> dict:
+    """Plain vs learned-filtered best-hit search on the candidate workload:
+    500k reads of 150 bp, U{1..64} candidate windows of 250 bp (one true at
+    1-3% divergence, paralog decoys at 5-20% or random).  The network is
+    trained on SW scores of ~5M pairs from another seed, and (k, tau) are
+    picked on a held-out seed for >= 99.6% best-hit recall; neither is timed.
+    A step is one whole search over the batch (score and end, no CIGAR)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1304_0681_gb300 import DeviceBatch
+    from paper_1304_0681_gb300 import filter as flt
+
+    def load(name, seed, n_reads):
+        wl = synth.generate(name, seed=seed, n_reads=n_reads)
+        b = DeviceBatch.from_packed(wl.packed_reads(), wl.read_offsets, wl.packed_windows(), wl.window_offsets,
+                                    pair_read=wl.pair_read, cigar=False)
+        return wl, b, torch.from_numpy(wl.cand_offsets).cuda()
+
+    # training set: SW scores from the method itself are the targets
+    t0 = time.perf_counter()
+    wl_tr, b_tr, co_tr = load("filter", 1000 + rank, 150_000)
+    flt.exhaustive_best(b_tr, co_tr, SCORING)
+    feats_tr = flt.features(b_tr, co_tr)
+    tgt = flt.targets(b_tr.score, torch.from_numpy(wl_tr.pair_read_lengths).cuda(), SCORING[0])
+    model = flt.FilterModel(seed=1)
+    losses = model.train(feats_tr, tgt, epochs=4, batch=8192, lr=2e-3)
+    n_train = wl_tr.n_pairs
+    del b_tr, feats_tr, tgt
+    # calibration on a held-out seed
+    wl_cal, b_cal, co_cal = load("filter", 2000 + rank, 40_000)
+    flt.exhaustive_best(b_cal, co_cal, SCORING)
+    pred_cal = model.forward(flt.features(b_cal, co_cal)).cpu().numpy()
+    cal = flt.calibrate(pred_cal, b_cal.score.cpu().numpy().astype(np.int64), wl_cal.cand_offsets, 0.996)
+    k, tau = (cal[0], cal[1]) if cal else (8, 1.0)  # no setting reached the recall: align every candidate
+    del b_cal
+    setup_s = time.perf_counter() - t0
+
+    wl, b, co = load("filter", rank, args.filter_reads)
+    cells = wl.cells()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return out, sum(ms) / len(ms)
+
+    (best_plain, _), ms_plain = timed(lambda: flt.exhaustive_best(b, co, SCORING))
+    best_plain = best_plain.cpu().numpy()
+    res, ms_filt = timed(lambda: flt.filtered_best(b, co, model, k, tau, SCORING))
+    best_filt = res.best_score.cpu().numpy()
+    aligned = int(res.mask.sum().item())
+    sel_cells = int(np.sum((wl.pair_read_lengths.astype(np.int64) * wl.window_lengths)[res.mask.cpu().numpy() > 0]))
+    # phase split of one filtered step (features + network, then the rest)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    feats = flt.features(b, co)
+    pred = model.forward(feats)
+    e1.record(stream)
+    flt.filtered_best(b, co, model, k, tau, SCORING, feats=feats)
+    e2.record(stream)
+    e2.synchronize()
+    recall = float(np.mean(best_filt == best_plain))
+    return {"workload": "learned filter: 500k reads 150 bp, U{1..64} candidates of 250 bp, 16.25M pairs; "
+                        "best hit per read, score + end",
+            "reads": wl.n_reads, "pairs": wl.n_pairs, "cells_exhaustive": cells,
+            "plain": {"ms_per_step": ms_plain, "reads_per_s": wl.n_reads / (ms_plain * 1e-3),
+                      "gcups": cells / (ms_plain * 1e-3) / 1e9},
+            "filtered": {"ms_per_step": ms_filt, "reads_per_s": wl.n_reads / (ms_filt * 1e-3),
+                         "aligned_pairs": aligned, "aligned_cells": sel_cells,
+                         "features_and_mlp_ms": e0.elapsed_time(e1), "select_align_best_ms": e1.elapsed_time(e2),
+                         "gcups_aligned": sel_cells / (ms_filt * 1e-3) / 1e9},
+            "speedup_reads_per_s": ms_plain / ms_filt, "best_hit_recall": recall, "k": k, "tau": tau,
+            "calibration_recall": cal[3] if cal else None,
+            "training": {"pairs": n_train, "epochs": 4, "loss_per_epoch": losses, "setup_s": setup_s},
+            "steps": steps}
 
 
 def run_reference(args, ws, rank):
@@ -299,6 +390,10 @@ def main():
         e2e = {"value": ws * cells / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "reads_per_s": ws * n_reads / e2e_s}
 
+    filt = None
+    if not args.no_filter:
+        filt = _filter_section(args, rank, steps=max(2, min(args.steps, 5)))
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -314,7 +409,7 @@ def main():
                              "kernel": "k_score (score + end-cell pass)",
                              "peak_basis": f"measured 16x2 DPX add-max rate {dpx_ops / 1e12:.2f} Tops/s "
                                            f"x 2 cells / {OPS_PER_CELL:g} ops per cell"},
-                "clocks": clk, "gpu_launches": int(launches), "e2e": e2e}
+                "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "learned_filter": filt}
         if rank == 0 and not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
         print(json.dumps(line), flush=True)

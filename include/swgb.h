@@ -152,6 +152,84 @@ int sw_batch_align_host(const uint8_t *reads, const int64_t *read_offsets,
                         sw_stream_t stream);
 
 /*
+ * sw_batch_align_masked -- as sw_batch_align_indexed, but only pairs with
+ * pair_mask[p] != 0 (device uint8[n_pairs]) are aligned; the others get
+ * score -1, end (-1, -1) and 0 CIGAR runs.  This is how the candidates a
+ * filter selected are aligned without copying their windows.
+ */
+int sw_batch_align_masked(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads,
+                          const uint8_t *windows, const int64_t *window_offsets,
+                          const int64_t *pair_read, const uint8_t *pair_mask, int64_t n_pairs,
+                          const sw_scoring_t *scoring,
+                          int32_t *out_score, int32_t *out_end, sw_cigar_t *out_cigar,
+                          sw_stream_t stream);
+
+/*
+ * Learned candidate filter (an addition to the paper's method: the paper
+ * aligns every extended CAL; the filter ranks a read's candidates so that only
+ * the top ones are aligned, with exhaustive alignment as the fallback for
+ * reads whose ranking is not clear-cut.  It never changes a reported score).
+ *
+ * Candidates are grouped by read: cand_offsets (device int64[n_reads + 1])
+ * gives read r the pairs cand_offsets[r] .. cand_offsets[r+1]-1, and pair p
+ * is window p of window_offsets (device int64[n_pairs + 1]).
+ *
+ * sw_filter_features: per pair 64 bf16 features (device uint16[n_pairs * 64],
+ * row-major): the 4-mers q = 64 b0 + 16 b1 + 4 b2 + b3 of read and window
+ * are counted, and f[k] = sum over b of min(c_read(4k+b), c_window(4k+b)) /
+ * (m - 3) for k = 0..63 (0 when the read is shorter than 4).
+ */
+int sw_filter_features(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads,
+                       const uint8_t *windows, const int64_t *window_offsets,
+                       const int64_t *cand_offsets, uint16_t *out_features, sw_stream_t stream);
+
+/*
+ * The network: y = w3 . relu(W2^T relu(W1^T f + b1) + b2) + b3, W1 64x256,
+ * W2 256x64, w3 64 (33,153 parameters).  A model is one caller-owned device
+ * buffer of sw_mlp_bytes() bytes, fp32, laid out as
+ *   [0, 33153)         parameters: W1 row-major [64][256], b1[256],
+ *                      W2 row-major [256][64], b2[64], w3[64], b3
+ *   [33153, 66306)     Adam first moments
+ *   [66306, 99459)     Adam second moments
+ *   [99459, 132612)    gradient of the last sw_mlp_grad call
+ *   [132612]           unused
+ *   [132616, 140808)   bf16 W1 transposed [256][64] (serving copy)
+ *   [140808, 149000)   bf16 W2 transposed [64][256] (serving copy)
+ * sw_mlp_refresh rebuilds the bf16 copies after the caller writes parameters.
+ */
+int64_t sw_mlp_bytes(void);
+int sw_mlp_init(float *model, uint64_t seed, sw_stream_t stream);
+int sw_mlp_refresh(float *model, sw_stream_t stream);
+
+/* Predictions for n feature rows on the tensor cores (bf16 inputs and
+ * weights, fp32 accumulation): out device float[n]. */
+int sw_mlp_forward(const float *model, const uint16_t *features, int64_t n, float *out, sw_stream_t stream);
+
+/* Gradient of mean((y - target)^2) over n samples (fp32 forward and
+ * backward), written to the model's gradient region.  Sample s uses feature
+ * row idx[s] and target[idx[s]] (idx device int32[n], or NULL for s). */
+int sw_mlp_grad(float *model, const uint16_t *features, const float *target, const int32_t *idx, int64_t n,
+                sw_stream_t stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) from the stored gradient;
+ * step counts from 1.  Also refreshes the bf16 copies. */
+int sw_mlp_adam(float *model, float lr, int32_t step, sw_stream_t stream);
+
+/* Per read: mark its k best-predicted candidates (ties: lower candidate
+ * index first) in pair_mask (device uint8[n_pairs]), or all of them when
+ * the k-th and (k+1)-th predictions differ by less than tau, or when the read
+ * has at most k candidates.  1 <= k <= SW_FILTER_MAX_K. */
+#define SW_FILTER_MAX_K 16
+int sw_filter_select(const float *pred, const int64_t *cand_offsets, int64_t n_reads, int32_t k, float tau,
+                     uint8_t *pair_mask, sw_stream_t stream);
+
+/* Per read: the largest score over its candidates with pair_mask[p] != 0
+ * (pair_mask may be NULL: all), and that candidate's index within the read
+ * (first on ties); -1 and -1 when none. */
+int sw_best_per_read(const int32_t *score, const int64_t *cand_offsets, int64_t n_reads,
+                     const uint8_t *pair_mask, int32_t *best_score, int32_t *best_cand, sw_stream_t stream);
+
+/*
  * Wait for `stream` and report problems the alignment kernels of the last
  * call on this device detected on the device (SW_ERR_CAPACITY when a CIGAR
  * slot overflowed, SW_ERR_INTERNAL when a consistency check failed).

@@ -149,7 +149,9 @@ def select_candidates(pred, cand_offsets, k: int, tau: float):
             sel[a:b] = True
             continue
         order = np.lexsort((np.arange(c), -pred[a:b]))
-        if pred[a + order[k - 1]] - pred[a + order[k]] < tau:
+        # the margin decision is taken in fp32, the precision of the kernel
+        gap = np.float32(pred[a + order[k - 1]]) - np.float32(pred[a + order[k]])
+        if gap < np.float32(tau):
             sel[a:b] = True
         else:
             sel[a + order[:k]] = True

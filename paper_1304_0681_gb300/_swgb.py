@@ -23,7 +23,9 @@ ERRORS = {
 #: every symbol include/swgb.h declares
 EXPORTS = ("sw_cigar_capacity", "sw_packed_bytes", "sw_batch_align", "sw_batch_align_indexed",
            "sw_batch_align_host", "sw_sync_status", "sw_strerror", "sw_launch_count", "sw_set_plan",
-           "sw_plan_rows", "sw_alu_probe", "sw_phase_timing", "sw_phase_times", "sw_batch_align_noalloc")
+           "sw_plan_rows", "sw_alu_probe", "sw_phase_timing", "sw_phase_times", "sw_batch_align_noalloc",
+           "sw_batch_align_masked", "sw_filter_features", "sw_mlp_bytes", "sw_mlp_init", "sw_mlp_refresh",
+           "sw_mlp_forward", "sw_mlp_grad", "sw_mlp_adam", "sw_filter_select", "sw_best_per_read")
 
 
 class SwError(RuntimeError):
@@ -60,6 +62,27 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_batch_align_host.restype = ctypes.c_int
     lib.sw_batch_align_noalloc.argtypes = [p, p, p, p, i64, ctypes.POINTER(Scoring), p, p, p]
     lib.sw_batch_align_noalloc.restype = ctypes.c_int
+    lib.sw_batch_align_masked.argtypes = [p, p, i64, p, p, p, p, i64, ctypes.POINTER(Scoring), p, p,
+                                          ctypes.POINTER(Cigar), p]
+    lib.sw_batch_align_masked.restype = ctypes.c_int
+    lib.sw_filter_features.argtypes = [p, p, i64, p, p, p, p, p]
+    lib.sw_filter_features.restype = ctypes.c_int
+    lib.sw_mlp_bytes.argtypes = []
+    lib.sw_mlp_bytes.restype = i64
+    lib.sw_mlp_init.argtypes = [p, ctypes.c_uint64, p]
+    lib.sw_mlp_init.restype = ctypes.c_int
+    lib.sw_mlp_refresh.argtypes = [p, p]
+    lib.sw_mlp_refresh.restype = ctypes.c_int
+    lib.sw_mlp_forward.argtypes = [p, p, i64, p, p]
+    lib.sw_mlp_forward.restype = ctypes.c_int
+    lib.sw_mlp_grad.argtypes = [p, p, p, p, i64, p]
+    lib.sw_mlp_grad.restype = ctypes.c_int
+    lib.sw_mlp_adam.argtypes = [p, ctypes.c_float, i32, p]
+    lib.sw_mlp_adam.restype = ctypes.c_int
+    lib.sw_filter_select.argtypes = [p, p, i64, i32, ctypes.c_float, p, p]
+    lib.sw_filter_select.restype = ctypes.c_int
+    lib.sw_best_per_read.argtypes = [p, p, i64, p, p, p, p]
+    lib.sw_best_per_read.restype = ctypes.c_int
     lib.sw_sync_status.argtypes = [p]
     lib.sw_sync_status.restype = ctypes.c_int
     lib.sw_strerror.argtypes = [ctypes.c_int]
@@ -188,3 +211,56 @@ def sw_phase_times() -> tuple:
     buf = (ctypes.c_float * 3)()
     _check(_lib.sw_phase_times(ctypes.cast(buf, ctypes.c_void_p)), "sw_phase_times")
     return tuple(buf)
+
+
+def sw_batch_align_masked(reads, read_offsets, n_reads: int, windows, window_offsets, pair_read, pair_mask,
+                          n_pairs: int, scoring, out_score, out_end, cigar=None, stream=None) -> None:
+    cg = Cigar(*(t.data_ptr() for t in cigar)) if cigar is not None else None
+    sc = _scoring(scoring)
+    _check(_lib.sw_batch_align_masked(_ptr(reads), _ptr(read_offsets), int(n_reads), _ptr(windows),
+                                      _ptr(window_offsets), _ptr(pair_read), _ptr(pair_mask), int(n_pairs),
+                                      ctypes.byref(sc), _ptr(out_score), _ptr(out_end),
+                                      ctypes.byref(cg) if cg is not None else None, _stream(stream)),
+           "sw_batch_align_masked")
+
+
+def sw_filter_features(reads, read_offsets, n_reads: int, windows, window_offsets, cand_offsets, out_features,
+                       stream=None) -> None:
+    _check(_lib.sw_filter_features(_ptr(reads), _ptr(read_offsets), int(n_reads), _ptr(windows),
+                                   _ptr(window_offsets), _ptr(cand_offsets), _ptr(out_features), _stream(stream)),
+           "sw_filter_features")
+
+
+def sw_mlp_bytes() -> int:
+    return int(_lib.sw_mlp_bytes())
+
+
+def sw_mlp_init(model, seed: int, stream=None) -> None:
+    _check(_lib.sw_mlp_init(_ptr(model), ctypes.c_uint64(seed), _stream(stream)), "sw_mlp_init")
+
+
+def sw_mlp_refresh(model, stream=None) -> None:
+    _check(_lib.sw_mlp_refresh(_ptr(model), _stream(stream)), "sw_mlp_refresh")
+
+
+def sw_mlp_forward(model, features, n: int, out, stream=None) -> None:
+    _check(_lib.sw_mlp_forward(_ptr(model), _ptr(features), int(n), _ptr(out), _stream(stream)), "sw_mlp_forward")
+
+
+def sw_mlp_grad(model, features, target, idx, n: int, stream=None) -> None:
+    _check(_lib.sw_mlp_grad(_ptr(model), _ptr(features), _ptr(target), _ptr(idx), int(n), _stream(stream)),
+           "sw_mlp_grad")
+
+
+def sw_mlp_adam(model, lr: float, step: int, stream=None) -> None:
+    _check(_lib.sw_mlp_adam(_ptr(model), ctypes.c_float(lr), int(step), _stream(stream)), "sw_mlp_adam")
+
+
+def sw_filter_select(pred, cand_offsets, n_reads: int, k: int, tau: float, pair_mask, stream=None) -> None:
+    _check(_lib.sw_filter_select(_ptr(pred), _ptr(cand_offsets), int(n_reads), int(k), ctypes.c_float(tau),
+                                 _ptr(pair_mask), _stream(stream)), "sw_filter_select")
+
+
+def sw_best_per_read(score, cand_offsets, n_reads: int, pair_mask, best_score, best_cand, stream=None) -> None:
+    _check(_lib.sw_best_per_read(_ptr(score), _ptr(cand_offsets), int(n_reads), _ptr(pair_mask), _ptr(best_score),
+                                 _ptr(best_cand), _stream(stream)), "sw_best_per_read")

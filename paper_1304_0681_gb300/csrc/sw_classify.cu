@@ -30,6 +30,12 @@ __global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring
         int32_t key = -1;
         if (bad) {
             atomicOr(&info->status, ST_BAD_INPUT);
+        } else if (ps.mask && !ps.mask[p]) {
+            // not selected: no alignment
+            out_score[p] = -1;
+            out_end[2 * p] = -1;
+            out_end[2 * p + 1] = -1;
+            if (cig_n) cig_n[p] = 0;
         } else if (n == 0) {
             // an empty window aligns nothing: score 0, no end cell, no CIGAR
             out_score[p] = 0;
@@ -39,7 +45,7 @@ __global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring
         } else {
             const int64_t hmax = (int64_t)sc.ma * (m < n ? m : n);
             int mode = MODE_I32;
-            if (hmax <= 1022) mode = MODE_I16;
+            if (hmax <= 510) mode = MODE_I16;  // (H << 6) | 63 fits 15 bits
             else if (hmax <= 32000) mode = MODE_I16W;
             const int cls = mode * N_MCLASS + mclass_of((int32_t)m);
             int nb = (int)((n - 1) >> 5);

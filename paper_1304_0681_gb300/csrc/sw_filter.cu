@@ -1,0 +1,632 @@
+// sw_filter.cu -- the learned candidate filter in front of Smith-Waterman.
+//
+// The paper's Stage E runs SW on every extended CAL of a read.  The filter
+// ranks a read's candidates by a small network's prediction of the SW score
+// so that only the top ones are aligned; reads whose ranking is not clear-cut
+// fall back to aligning every candidate.  It never changes a reported score:
+// the score of a read is the SW score of its best aligned candidate.
+//
+// Features: for pair (read of length m, window), the 4-mers q = 64 b0 + 16 b1
+// + 4 b2 + b3 of both strings are counted; per 3-base prefix k = q >> 2 the
+// shared counts min(c_read, c_window) are summed over the last base and
+// divided by m - 3, giving 64 values stored as bf16.
+//
+// Network 64 -> 256 -> 64 -> 1 with ReLU: y = w3 . relu(W2^T relu(W1^T f +
+// b1) + b2) + b3.  Serving runs on the tensor cores (mma.sync bf16 with fp32
+// accumulation, weights in shared memory); training uses an fp32 forward and
+// backward on the CUDA cores (mean squared error against SW score / (match m))
+// and Adam.
+#include <algorithm>
+
+#include <cuda_bf16.h>
+
+#include "sw_device.cuh"
+#include "swgb_internal.h"
+
+namespace swgb {
+
+constexpr unsigned FM = 0xffffffffu;
+
+// ---------------------------------------------------------------- features
+
+// Count the 4-mers of bases [s, s+len) into hist (shared, 256 x uint32).
+__device__ __forceinline__ void count_kmers(const uint32_t *__restrict__ buf, int64_t s, int32_t len,
+                                            uint32_t *hist, int lane)
+{
+    const int nk = len - 3;  // number of 4-mers
+    for (int base = lane * 16; base < nk; base += 32 * 16) {
+        // 16 k-mers starting at positions base .. base+15 need bases base .. base+18
+        const int avail = min(19, len - base);
+        const uint32_t lo = load_bases(buf, s + base, min(16, avail));
+        const uint32_t hi = avail > 16 ? load_bases(buf, s + base + 16, avail - 16) : 0u;
+        const uint64_t v = (uint64_t)lo | ((uint64_t)hi << 32);
+        const int cnt = min(16, nk - base);
+        for (int t = 0; t < cnt; ++t) {
+            const uint32_t w = (uint32_t)(v >> (2 * t)) & 0xFFu;  // b0 in bits 0-1 ... b3 in bits 6-7
+            const uint32_t q = ((w & 3u) << 6) | (((w >> 2) & 3u) << 4) | (((w >> 4) & 3u) << 2) | (w >> 6);
+            atomicAdd(&hist[q], 1u);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_features(FeatureParams P)
+{
+    __shared__ uint32_t hist[8][2][256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *hr = hist[warp][0], *hw = hist[warp][1];
+    for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < P.n_reads; r += (int64_t)gridDim.x * 8) {
+        const int64_t c0 = P.cand_off[r], c1 = P.cand_off[r + 1];
+        if (c0 >= c1) continue;
+        const int64_t rs = P.read_off[r];
+        const int32_t m = (int32_t)(P.read_off[r + 1] - rs);
+        for (int q = lane; q < 256; q += 32) hr[q] = 0;
+        __syncwarp();
+        if (m >= 4) count_kmers(P.reads, rs, m, hr, lane);
+        __syncwarp();
+        const float inv = m >= 4 ? 1.f / (float)(m - 3) : 0.f;
+        for (int64_t p = c0; p < c1; ++p) {
+            const int64_t ws = P.win_off[p];
+            const int32_t n = (int32_t)(P.win_off[p + 1] - ws);
+            for (int q = lane; q < 256; q += 32) hw[q] = 0;
+            __syncwarp();
+            if (n >= 4 && m >= 4) count_kmers(P.wins, ws, n, hw, lane);
+            __syncwarp();
+            // lane: prefixes 2*lane and 2*lane + 1 (4-mer codes 8*lane .. 8*lane+7)
+            uint32_t s0 = 0, s1 = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                s0 += min(hr[8 * lane + b], hw[8 * lane + b]);
+                s1 += min(hr[8 * lane + 4 + b], hw[8 * lane + 4 + b]);
+            }
+            const __nv_bfloat162 f = __floats2bfloat162_rn((float)s0 * inv, (float)s1 * inv);
+            reinterpret_cast<__nv_bfloat162 *>(P.out)[p * 32 + lane] = f;
+            __syncwarp();
+        }
+    }
+}
+
+// --------------------------------------------------------- model layout
+
+// fp32 offsets into the model buffer (see include/swgb.h)
+constexpr int64_t MD_W1 = 0, MD_B1 = 16384, MD_W2 = 16640, MD_B2 = 33024, MD_W3 = 33088, MD_B3 = 33152;
+constexpr int64_t MD_NP = 33153;
+constexpr int64_t MD_M = MD_NP, MD_V = 2 * MD_NP, MD_G = 3 * MD_NP, MD_STEP = 4 * MD_NP;
+constexpr int64_t MD_W1T = 132616;          // bf16 [256][64], 16-byte aligned
+constexpr int64_t MD_W2T = MD_W1T + 8192;   // bf16 [64][256]
+constexpr int64_t MD_TOTAL = MD_W2T + 8192;
+
+// bf16 copies of the weights, transposed for the tensor-core B operands
+__global__ void k_mlp_refresh(float *model)
+{
+    const float *W1 = model + MD_W1, *W2 = model + MD_W2;
+    __nv_bfloat16 *w1t = reinterpret_cast<__nv_bfloat16 *>(model + MD_W1T);
+    __nv_bfloat16 *w2t = reinterpret_cast<__nv_bfloat16 *>(model + MD_W2T);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 16384; i += gridDim.x * blockDim.x) {
+        const int a = i / 256, b = i % 256;      // W1[a][b] -> w1t[b][a]
+        w1t[b * 64 + a] = __float2bfloat16_rn(W1[i]);
+        const int j = i / 64, k = i % 64;        // W2[j][k] -> w2t[k][j]
+        w2t[k * 256 + j] = __float2bfloat16_rn(W2[i]);
+    }
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// He-scaled uniform weights from a counter-based generator; zero biases,
+// Adam state and step; the output bias starts at 0.5 (mid-range target)
+__global__ void k_mlp_init(float *model, uint64_t seed)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < MD_STEP + 1;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        if (i < MD_NP) {
+            const double u = (double)(mix64(seed * 0xD1B54A32D192ED03ULL ^ mix64((uint64_t)i)) >> 11) *
+                                 (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+            if (i < MD_B1) v = (float)(u * sqrt(6.0 / 64.0));
+            else if (i >= MD_W2 && i < MD_B2) v = (float)(u * sqrt(6.0 / 256.0));
+            else if (i >= MD_W3 && i < MD_B3) v = (float)(u * sqrt(6.0 / 64.0) * 0.1);
+            else if (i == MD_B3) v = 0.5f;
+        }
+        model[i] = v;
+    }
+}
+
+// ------------------------------------------------------- forward (bf16 mma)
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+constexpr int W1S = 72;   // padded row of w1t in shared memory (bf16)
+constexpr int W2S = 264;  // padded row of w2t
+
+// Each warp takes 16 pairs at a time.  Layer 1 is computed in four blocks of
+// 64 hidden units; each block's ReLU output is repacked in registers as the
+// A operand of layer 2 (the accumulator layout of two n8 tiles is the A
+// layout of one k16 step), so hidden activations never leave registers.
+__global__ void __launch_bounds__(128) k_mlp_forward(const float *__restrict__ model,
+                                                     const __nv_bfloat16 *__restrict__ feat, int64_t n,
+                                                     float *__restrict__ out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __nv_bfloat16 *w1 = reinterpret_cast<__nv_bfloat16 *>(smem);            // [256][W1S]
+    __nv_bfloat16 *w2 = w1 + 256 * W1S;                                      // [64][W2S]
+    float *b1 = reinterpret_cast<float *>(w2 + 64 * W2S);                    // [256]
+    float *b2 = b1 + 256;                                                    // [64]
+    float *w3 = b2 + 64;                                                     // [64]
+    {
+        const __nv_bfloat16 *g1 = reinterpret_cast<const __nv_bfloat16 *>(model + MD_W1T);
+        const __nv_bfloat16 *g2 = reinterpret_cast<const __nv_bfloat16 *>(model + MD_W2T);
+        for (int i = threadIdx.x; i < 256 * 64; i += blockDim.x) {
+            w1[(i / 64) * W1S + i % 64] = g1[i];
+            w2[(i / 256) * W2S + i % 256] = g2[i];
+        }
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) b1[i] = model[MD_B1 + i];
+        for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+            b2[i] = model[MD_B2 + i];
+            w3[i] = model[MD_W3 + i];
+        }
+        __syncthreads();
+    }
+    const float b3 = model[MD_B3];
+    const int lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const uint32_t *X = reinterpret_cast<const uint32_t *>(feat);  // bf16 pairs: row stride 32 words
+    for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile * 16 < n;
+         tile += warps) {
+        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+        uint32_t xa[4][4];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int c = kk * 8 + tig;  // word column (2 bf16)
+            xa[kk][0] = r0 < n ? X[r0 * 32 + c] : 0u;
+            xa[kk][1] = r1 < n ? X[r1 * 32 + c] : 0u;
+            xa[kk][2] = r0 < n ? X[r0 * 32 + c + 4] : 0u;
+            xa[kk][3] = r1 < n ? X[r1 * 32 + c + 4] : 0u;
+        }
+        float acc2[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const float c0 = b2[nt * 8 + tig * 2], c1 = b2[nt * 8 + tig * 2 + 1];
+            acc2[nt][0] = c0; acc2[nt][1] = c1; acc2[nt][2] = c0; acc2[nt][3] = c1;
+        }
+#pragma unroll 1
+        for (int nb = 0; nb < 4; ++nb) {
+            float acc1[8][4];
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int col = nb * 64 + nt * 8 + tig * 2;
+                acc1[nt][0] = b1[col]; acc1[nt][1] = b1[col + 1]; acc1[nt][2] = b1[col]; acc1[nt][3] = b1[col + 1];
+            }
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt) {
+                    const __nv_bfloat16 *row = w1 + (nb * 64 + nt * 8 + g) * W1S + kk * 16 + tig * 2;
+                    const uint32_t bb0 = *reinterpret_cast<const uint32_t *>(row);
+                    const uint32_t bb1 = *reinterpret_cast<const uint32_t *>(row + 8);
+                    mma_bf16(acc1[nt], xa[kk][0], xa[kk][1], xa[kk][2], xa[kk][3], bb0, bb1);
+                }
+            }
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const float *t0 = acc1[2 * ks], *t1 = acc1[2 * ks + 1];
+                const uint32_t a0 = pack_bf16(fmaxf(t0[0], 0.f), fmaxf(t0[1], 0.f));
+                const uint32_t a1 = pack_bf16(fmaxf(t0[2], 0.f), fmaxf(t0[3], 0.f));
+                const uint32_t a2 = pack_bf16(fmaxf(t1[0], 0.f), fmaxf(t1[1], 0.f));
+                const uint32_t a3 = pack_bf16(fmaxf(t1[2], 0.f), fmaxf(t1[3], 0.f));
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt) {
+                    const __nv_bfloat16 *row = w2 + (nt * 8 + g) * W2S + nb * 64 + ks * 16 + tig * 2;
+                    const uint32_t bb0 = *reinterpret_cast<const uint32_t *>(row);
+                    const uint32_t bb1 = *reinterpret_cast<const uint32_t *>(row + 8);
+                    mma_bf16(acc2[nt], a0, a1, a2, a3, bb0, bb1);
+                }
+            }
+        }
+        float y0 = 0.f, y1 = 0.f;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const float wa = w3[nt * 8 + tig * 2], wb = w3[nt * 8 + tig * 2 + 1];
+            y0 += fmaxf(acc2[nt][0], 0.f) * wa + fmaxf(acc2[nt][1], 0.f) * wb;
+            y1 += fmaxf(acc2[nt][2], 0.f) * wa + fmaxf(acc2[nt][3], 0.f) * wb;
+        }
+        y0 += __shfl_xor_sync(FM, y0, 1);
+        y0 += __shfl_xor_sync(FM, y0, 2);
+        y1 += __shfl_xor_sync(FM, y1, 1);
+        y1 += __shfl_xor_sync(FM, y1, 2);
+        if (tig == 0) {
+            if (r0 < n) out[r0] = y0 + b3;
+            if (r1 < n) out[r1] = y1 + b3;
+        }
+    }
+}
+
+// ------------------------------------------------- training (fp32, CUDA cores)
+
+constexpr int GR_THREADS = 256;
+constexpr int W2TS = 257;  // padded row of the transposed fp32 W2 in shared memory
+
+// Mean-squared-error gradient over samples [s0, s1) of the batch, added
+// into G.  Thread j owns hidden unit j of layer 1: its column of dW1 and its
+// row of dW2 stay in registers for the whole chunk.
+__global__ void __launch_bounds__(GR_THREADS, 1)
+    k_mlp_grad(float *model, const __nv_bfloat16 *__restrict__ feat, const float *__restrict__ target,
+               const int32_t *__restrict__ idx, int64_t n, int64_t per_block)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *W1 = reinterpret_cast<float *>(smem);        // [64][256]
+    float *W2T = W1 + 64 * 256;                         // [64][W2TS]  (W2T[k][j] = W2[j][k])
+    float *x = W2T + 64 * W2TS;                         // [64]
+    float *a1 = x + 64;                                 // [256]
+    float *part = a1 + 256;                             // [4][64]
+    float *dz2 = part + 256;                            // [64]
+    float *red = dz2 + 64;                              // [8]
+    const int j = threadIdx.x;
+    for (int i = j; i < 64 * 256; i += GR_THREADS) {
+        W1[i] = model[MD_W1 + i];
+        const int jj = i / 64, k = i % 64;
+        W2T[k * W2TS + jj] = model[MD_W2 + i];
+    }
+    __syncthreads();
+    const float b1j = model[MD_B1 + j];
+    const float b2k = j < 64 ? model[MD_B2 + j] : 0.f;
+    const float w3k = j < 64 ? model[MD_W3 + j] : 0.f;
+    const float b3 = model[MD_B3];
+    float gW1[64], gW2[64];
+#pragma unroll
+    for (int q = 0; q < 64; ++q) {
+        gW1[q] = 0.f;
+        gW2[q] = 0.f;
+    }
+    float gb1 = 0.f, gb2 = 0.f, gw3 = 0.f, gb3 = 0.f;
+    const int64_t s0 = blockIdx.x * per_block, s1 = min(n, s0 + per_block);
+    const float scale = 2.f / (float)n;
+    for (int64_t s = s0; s < s1; ++s) {
+        const int64_t row = idx ? idx[s] : s;
+        if (j < 64) x[j] = __bfloat162float(feat[row * 64 + j]);
+        __syncthreads();
+        float z1 = b1j;
+#pragma unroll 8
+        for (int i = 0; i < 64; ++i) z1 += x[i] * W1[i * 256 + j];
+        const float a = fmaxf(z1, 0.f);
+        a1[j] = a;
+        __syncthreads();
+        {   // z2[k], four partial sums per output
+            const int k = j & 63, pr = j >> 6;
+            float z = 0.f;
+#pragma unroll 8
+            for (int jj = pr * 64; jj < pr * 64 + 64; ++jj) z += a1[jj] * W2T[k * W2TS + jj];
+            part[pr * 64 + k] = z;
+        }
+        __syncthreads();
+        float z2 = 0.f, a2 = 0.f;
+        if (j < 64) {
+            z2 = b2k + part[j] + part[64 + j] + part[128 + j] + part[192 + j];
+            a2 = fmaxf(z2, 0.f);
+            float yp = a2 * w3k;
+            for (int o = 16; o > 0; o >>= 1) yp += __shfl_xor_sync(FM, yp, o);
+            if ((j & 31) == 0) red[j >> 5] = yp;
+        }
+        __syncthreads();
+        const float y = red[0] + red[1] + b3;
+        const float dy = scale * (y - target[row]);
+        if (j < 64) {
+            const float d = z2 > 0.f ? dy * w3k : 0.f;
+            dz2[j] = d;
+            gw3 += a2 * dy;
+            gb2 += d;
+        }
+        if (j == 0) gb3 += dy;
+        __syncthreads();
+        float da1 = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < 64; ++k) {
+            const float d = dz2[k];
+            da1 += d * W2T[k * W2TS + j];
+            gW2[k] += a * d;
+        }
+        const float dz1 = z1 > 0.f ? da1 : 0.f;
+        gb1 += dz1;
+#pragma unroll
+        for (int i = 0; i < 64; ++i) gW1[i] += x[i] * dz1;
+        __syncthreads();
+    }
+    float *G = model + MD_G;
+#pragma unroll
+    for (int i = 0; i < 64; ++i) atomicAdd(&G[MD_W1 + i * 256 + j], gW1[i]);
+#pragma unroll
+    for (int k = 0; k < 64; ++k) atomicAdd(&G[MD_W2 + j * 64 + k], gW2[k]);
+    atomicAdd(&G[MD_B1 + j], gb1);
+    if (j < 64) {
+        atomicAdd(&G[MD_B2 + j], gb2);
+        atomicAdd(&G[MD_W3 + j], gw3);
+    }
+    if (j == 0) atomicAdd(&G[MD_B3], gb3);
+}
+
+// One Adam step (Kingma & Ba) on the fp32 parameters from the gradient in G.
+__global__ void k_mlp_adam(float *model, float lr, int32_t step)
+{
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < MD_NP; i += (int64_t)gridDim.x * blockDim.x) {
+        const float g = model[MD_G + i];
+        const float m = b1 * model[MD_M + i] + (1.f - b1) * g;
+        const float v = b2 * model[MD_V + i] + (1.f - b2) * g * g;
+        model[MD_M + i] = m;
+        model[MD_V + i] = v;
+        model[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+    }
+}
+
+// ---------------------------------------------------- selection and best hit
+
+// Per read: the k best predictions (ties: lower candidate index first); if
+// the k-th and the (k+1)-th are closer than tau, every candidate.
+__global__ void k_select(const float *__restrict__ pred, const int64_t *__restrict__ cand_off, int64_t n_reads,
+                         int32_t k, float tau, uint8_t *__restrict__ mask)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_reads;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = cand_off[r], b = cand_off[r + 1];
+        const int64_t c = b - a;
+        if (c <= k) {
+            for (int64_t p = a; p < b; ++p) mask[p] = 1;
+            continue;
+        }
+        // the (k+1) best (value, index) kept sorted, best first
+        float bv[SW_FILTER_MAX_K + 1];
+        int64_t bi[SW_FILTER_MAX_K + 1];
+        int cnt = 0;
+        for (int64_t p = a; p < b; ++p) {
+            const float v = pred[p];
+            int pos = cnt;
+            while (pos > 0 && bv[pos - 1] < v) --pos;  // strictly better moves up: ties keep index order
+            if (pos > k) continue;
+            const int last = cnt < k + 1 ? cnt : k;
+            for (int q = last; q > pos; --q) {
+                bv[q] = bv[q - 1];
+                bi[q] = bi[q - 1];
+            }
+            bv[pos] = v;
+            bi[pos] = p;
+            if (cnt < k + 1) ++cnt;
+        }
+        const bool all = bv[k - 1] - bv[k] < tau;
+        for (int64_t p = a; p < b; ++p) mask[p] = all ? 1 : 0;
+        if (!all)
+            for (int q = 0; q < k; ++q) mask[bi[q]] = 1;
+    }
+}
+
+__global__ void k_best_per_read(const int32_t *__restrict__ score, const int64_t *__restrict__ cand_off,
+                                int64_t n_reads, const uint8_t *__restrict__ mask, int32_t *__restrict__ best,
+                                int32_t *__restrict__ best_cand)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_reads;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t bs = -1, bc = -1;
+        for (int64_t p = cand_off[r]; p < cand_off[r + 1]; ++p) {
+            if (mask && !mask[p]) continue;
+            if (score[p] > bs) {
+                bs = score[p];
+                bc = (int32_t)(p - cand_off[r]);
+            }
+        }
+        best[r] = bs;
+        if (best_cand) best_cand[r] = bc;
+    }
+}
+
+// ------------------------------------------------------------ launchers
+
+static int grid_for(int64_t items, int threads, int cap)
+{
+    int64_t b = (items + threads - 1) / threads;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+int launch_features(const FeatureParams &P, cudaStream_t st)
+{
+    k_features<<<grid_for(P.n_reads, 8, 152 * 16), 256, 0, st>>>(P);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
+int64_t mlp_floats() { return MD_TOTAL; }
+
+int launch_mlp_init(float *model, uint64_t seed, cudaStream_t st)
+{
+    k_mlp_init<<<grid_for(MD_STEP + 1, 256, 152 * 4), 256, 0, st>>>(model, seed);
+    k_mlp_refresh<<<64, 256, 0, st>>>(model);
+    count_launch(2);
+    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
+int launch_mlp_refresh(float *model, cudaStream_t st)
+{
+    k_mlp_refresh<<<64, 256, 0, st>>>(model);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
+static size_t forward_smem() { return (size_t)(256 * W1S + 64 * W2S) * 2 + (256 + 64 + 64) * 4; }
+static size_t grad_smem() { return (size_t)(64 * 256 + 64 * W2TS + 64 + 256 + 256 + 64 + 8) * 4; }
+
+int launch_mlp_forward(const float *model, const uint16_t *feat, int64_t n, float *out, int sm_count,
+                       cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)forward_smem()) !=
+            cudaSuccess)
+            return SW_ERR_CUDA;
+        attr = true;
+    }
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_mlp_forward, 128, forward_smem()) != cudaSuccess)
+        return SW_ERR_CUDA;
+    const int64_t tiles = (n + 15) / 16;
+    int64_t blocks = (tiles + 3) / 4;
+    blocks = std::min<int64_t>(blocks, (int64_t)std::max(bps, 1) * sm_count);
+    k_mlp_forward<<<(unsigned)std::max<int64_t>(blocks, 1), 128, forward_smem(), st>>>(
+        model, reinterpret_cast<const __nv_bfloat16 *>(feat), n, out);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
+int launch_mlp_grad(float *model, const uint16_t *feat, const float *target, const int32_t *idx, int64_t n,
+                    int sm_count, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem()) !=
+            cudaSuccess)
+            return SW_ERR_CUDA;
+        attr = true;
+    }
+    if (cudaMemsetAsync(model + MD_G, 0, sizeof(float) * MD_NP, st) != cudaSuccess) return SW_ERR_CUDA;
+    // enough samples per block that the per-block gradient flush stays small
+    const int64_t per_block = std::max<int64_t>(64, (n + sm_count - 1) / sm_count);
+    const int64_t blocks = (n + per_block - 1) / per_block;
+    k_mlp_grad<<<(unsigned)std::max<int64_t>(blocks, 1), GR_THREADS, grad_smem(), st>>>(
+        model, reinterpret_cast<const __nv_bfloat16 *>(feat), target, idx, n, per_block);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
+int launch_mlp_adam(float *model, float lr, int32_t step, cudaStream_t st)
+{
+    k_mlp_adam<<<grid_for(MD_NP, 256, 152 * 2), 256, 0, st>>>(model, lr, step);
+    k_mlp_refresh<<<64, 256, 0, st>>>(model);
+    count_launch(2);
+    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
+int launch_select(const float *pred, const int64_t *cand_off, int64_t n_reads, int32_t k, float tau, uint8_t *mask,
+                  cudaStream_t st)
+{
+    k_select<<<grid_for(n_reads, 128, 152 * 32), 128, 0, st>>>(pred, cand_off, n_reads, k, tau, mask);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
+int launch_best_per_read(const int32_t *score, const int64_t *cand_off, int64_t n_reads, const uint8_t *mask,
+                         int32_t *best, int32_t *best_cand, cudaStream_t st)
+{
+    k_best_per_read<<<grid_for(n_reads, 128, 152 * 32), 128, 0, st>>>(score, cand_off, n_reads, mask, best,
+                                                                       best_cand);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
+}  // namespace swgb
+
+// ------------------------------------------------------------------ C ABI
+
+using namespace swgb;
+
+static int sm_count_now(int *sms)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SW_ERR_NO_DEVICE;
+    if (cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SW_ERR_CUDA;
+    return SW_OK;
+}
+
+extern "C" {
+
+int sw_filter_features(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads, const uint8_t *windows,
+                       const int64_t *window_offsets, const int64_t *cand_offsets, uint16_t *out_features,
+                       sw_stream_t stream)
+{
+    if (n_reads < 0) return SW_ERR_INVALID_ARG;
+    if (n_reads == 0) return SW_OK;
+    if (!reads || !read_offsets || !windows || !window_offsets || !cand_offsets || !out_features)
+        return SW_ERR_INVALID_ARG;
+    if (((uintptr_t)reads & 15u) || ((uintptr_t)windows & 15u) || ((uintptr_t)out_features & 3u))
+        return SW_ERR_INVALID_ARG;
+    FeatureParams P{(const uint32_t *)reads, read_offsets, n_reads, (const uint32_t *)windows, window_offsets,
+                    cand_offsets, out_features};
+    return launch_features(P, (cudaStream_t)stream);
+}
+
+int64_t sw_mlp_bytes(void) { return mlp_floats() * (int64_t)sizeof(float); }
+
+int sw_mlp_init(float *model, uint64_t seed, sw_stream_t stream)
+{
+    if (!model || ((uintptr_t)model & 15u)) return SW_ERR_INVALID_ARG;
+    return launch_mlp_init(model, seed, (cudaStream_t)stream);
+}
+
+int sw_mlp_refresh(float *model, sw_stream_t stream)
+{
+    if (!model || ((uintptr_t)model & 15u)) return SW_ERR_INVALID_ARG;
+    return launch_mlp_refresh(model, (cudaStream_t)stream);
+}
+
+int sw_mlp_forward(const float *model, const uint16_t *features, int64_t n, float *out, sw_stream_t stream)
+{
+    if (n < 0 || !model || ((uintptr_t)model & 15u)) return SW_ERR_INVALID_ARG;
+    if (n == 0) return SW_OK;
+    if (!features || !out || ((uintptr_t)features & 3u)) return SW_ERR_INVALID_ARG;
+    int sms = 0;
+    int rc = sm_count_now(&sms);
+    if (rc) return rc;
+    return launch_mlp_forward(model, features, n, out, sms, (cudaStream_t)stream);
+}
+
+int sw_mlp_grad(float *model, const uint16_t *features, const float *target, const int32_t *idx, int64_t n,
+                sw_stream_t stream)
+{
+    if (n < 1 || !model || !features || !target || ((uintptr_t)model & 15u)) return SW_ERR_INVALID_ARG;
+    int sms = 0;
+    int rc = sm_count_now(&sms);
+    if (rc) return rc;
+    return launch_mlp_grad(model, features, target, idx, n, sms, (cudaStream_t)stream);
+}
+
+int sw_mlp_adam(float *model, float lr, int32_t step, sw_stream_t stream)
+{
+    if (!model || step < 1 || !(lr > 0.f)) return SW_ERR_INVALID_ARG;
+    return launch_mlp_adam(model, lr, step, (cudaStream_t)stream);
+}
+
+int sw_filter_select(const float *pred, const int64_t *cand_offsets, int64_t n_reads, int32_t k, float tau,
+                     uint8_t *pair_mask, sw_stream_t stream)
+{
+    if (n_reads < 0 || k < 1 || k > SW_FILTER_MAX_K) return SW_ERR_INVALID_ARG;
+    if (n_reads == 0) return SW_OK;
+    if (!pred || !cand_offsets || !pair_mask) return SW_ERR_INVALID_ARG;
+    return launch_select(pred, cand_offsets, n_reads, k, tau, pair_mask, (cudaStream_t)stream);
+}
+
+int sw_best_per_read(const int32_t *score, const int64_t *cand_offsets, int64_t n_reads, const uint8_t *pair_mask,
+                     int32_t *best_score, int32_t *best_cand, sw_stream_t stream)
+{
+    if (n_reads < 0) return SW_ERR_INVALID_ARG;
+    if (n_reads == 0) return SW_OK;
+    if (!score || !cand_offsets || !best_score) return SW_ERR_INVALID_ARG;
+    return launch_best_per_read(score, cand_offsets, n_reads, pair_mask, best_score, best_cand,
+                                (cudaStream_t)stream);
+}
+
+}  // extern "C"

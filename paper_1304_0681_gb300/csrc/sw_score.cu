@@ -39,11 +39,12 @@
 // constraint, so with `x = __vibmax_s16x2(x, ...)` the compiler may alias the
 // two and the predicates then compare the max with itself.)
 //
-// Best cell.  Every cell's H is turned into a key H*32 + (31-r) (r = row in
+// Best cell.  Every cell's H is turned into a key (H << TAGB) + (TAGM - r) (r = row in
 // the lane's block, so equal H prefers the smaller row); a three-way-max tree
 // gives the column's best key, and the lane's running best is replaced only
 // when the column's H is strictly larger (so the smallest column wins).  The
-// 16-bit keys need H <= 1022; pairs with larger possible scores use 32-bit
+// 16-bit keys need (H << 6) + 63 < 32768, i.e. H <= 510 (6-bit row tags
+// for up to 64 rows per lane); pairs with larger possible scores use 32-bit
 // keys built from each half (MODE_I16W) or the int32 mode.
 #include "sw_device.cuh"
 #include "swgb_internal.h"
@@ -141,6 +142,11 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
     typedef typename A::V V;
     constexpr bool PAIR2 = MODE != MODE_I32;
     constexpr int NW = (R + 7) / 8;
+    // row tag in the low bits of a key: TAGM - r, so equal H prefers the
+    // smaller row; 5 bits cover 32 rows, 6 bits 64
+    constexpr uint32_t TAGB = R <= 32 ? 5u : 6u;
+    constexpr uint32_t TAGM = (1u << TAGB) - 1u;
+    static_assert(R <= 64, "row tags cover at most 64 rows");
 
     // column tables: s_tab[w] byte x = s(x, w) - o; s_tab[4] = 0 (padding)
     __shared__ uint32_t s_tab[8];
@@ -221,7 +227,7 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
             V diag_in = 0;             // H(i0-1, j-1)
             V out_h = 0, out_f = 0;    // bottom row (H, F - o) handed to the next lane
             // running best of this chunk
-            uint32_t bk0 = PAIR2 && MODE == MODE_I16 ? 0x001F001Fu : 0u, bk1 = 0u;
+            uint32_t bk0 = PAIR2 && MODE == MODE_I16 ? TAGM * 0x10001u : 0u, bk1 = 0u;
             uint32_t rowA = 0, rowB = 0;
             int32_t jA = 0, jB = 0;
             // window stream: 2-bit codes of the next columns (up to 16)
@@ -275,12 +281,12 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
                     hu = hn;
                     uint32_t k0, k1 = 0;
                     if (MODE == MODE_I32) {
-                        k0 = mad_add((uint32_t)hn, 32u, (uint32_t)(31 - r));
+                        k0 = mad_add((uint32_t)hn, 1u << TAGB, TAGM - (uint32_t)r);
                     } else if (MODE == MODE_I16) {
-                        k0 = mad_add((uint32_t)hn, 32u, (uint32_t)(31 - r) * 0x10001u);
+                        k0 = mad_add((uint32_t)hn, 1u << TAGB, (TAGM - (uint32_t)r) * 0x10001u);
                     } else {
-                        k0 = mad_add((uint32_t)hn, 65536u, (uint32_t)(31 - r));
-                        k1 = ((uint32_t)hn & 0xFFFF0000u) | (uint32_t)(31 - r);
+                        k0 = mad_add((uint32_t)hn, 65536u, TAGM - (uint32_t)r);
+                        k1 = ((uint32_t)hn & 0xFFFF0000u) | (TAGM - (uint32_t)r);
                     }
                     // three-way max over pairs of rows
                     if (r % 2 == 0) {
@@ -311,14 +317,14 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
                 }
                 // strict improvement of H keeps the first (smallest) column
                 if (MODE == MODE_I32) {
-                    if (ck0 > (bk0 | 31u)) {
+                    if (ck0 > (bk0 | TAGM)) {
                         bk0 = ck0;
                         jA = j;
                     }
                 } else if (MODE == MODE_I16) {
-                    // per-half max of H*32+31; a half that rose is a strict
-                    // improvement of H (keys are >= 0, so the relu max is exact)
-                    const uint32_t nb = __vimax_s16x2_relu(bk0, ck0 | 0x001F001Fu);
+                    // per-half max of (H << TAGB) | TAGM; a half that rose is a
+                    // strict improvement of H (keys are >= 0, so relu max is exact)
+                    const uint32_t nb = __vimax_s16x2_relu(bk0, ck0 | (TAGM * 0x10001u));
                     const uint32_t up = nb ^ bk0;
                     bk0 = nb;
                     if (up & 0xFFFFu) { rowA = ck0; jA = j; }
@@ -331,16 +337,16 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
             // fold the chunk's best into the 64-bit per-lane best
             const int rbase = c * rows_per_chunk + k * R;
             if (MODE == MODE_I32) {
-                const uint32_t hb = bk0 >> 5;
-                if (hb) bestA = max(bestA, cell_key(hb, jA, rbase + 31 - (int)(bk0 & 31u)));
+                const uint32_t hb = bk0 >> TAGB;
+                if (hb) bestA = max(bestA, cell_key(hb, jA, rbase + (int)TAGM - (int)(bk0 & TAGM)));
             } else if (MODE == MODE_I16) {
-                const uint32_t ha = (bk0 & 0xFFFFu) >> 5, hb = (bk0 >> 16) >> 5;
-                if (ha) bestA = max(bestA, cell_key(ha, jA, rbase + 31 - (int)(rowA & 31u)));
-                if (hb) bestB = max(bestB, cell_key(hb, jB, rbase + 31 - (int)((rowB >> 16) & 31u)));
+                const uint32_t ha = (bk0 & 0xFFFFu) >> TAGB, hb = (bk0 >> 16) >> TAGB;
+                if (ha) bestA = max(bestA, cell_key(ha, jA, rbase + (int)TAGM - (int)(rowA & TAGM)));
+                if (hb) bestB = max(bestB, cell_key(hb, jB, rbase + (int)TAGM - (int)((rowB >> 16) & TAGM)));
             } else {
                 const uint32_t ha = bk0 >> 16, hb = bk1 >> 16;
-                if (ha) bestA = max(bestA, cell_key(ha, jA, rbase + 31 - (int)(bk0 & 0xFFFFu)));
-                if (hb) bestB = max(bestB, cell_key(hb, jB, rbase + 31 - (int)(bk1 & 0xFFFFu)));
+                if (ha) bestA = max(bestA, cell_key(ha, jA, rbase + (int)TAGM - (int)(bk0 & 0xFFFFu)));
+                if (hb) bestB = max(bestB, cell_key(hb, jB, rbase + (int)TAGM - (int)(bk1 & 0xFFFFu)));
             }
             __syncwarp();
         }
@@ -367,7 +373,7 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
     }
 }
 
-const int kScoreRows[N_SCORE_ROWS] = {8, 16, 20, 25, 32};
+const int kScoreRows[N_SCORE_ROWS] = {8, 16, 20, 25, 32, 50};
 
 template <int R>
 static int launch_r(int mode, bool fma, const ScoreLaunch &L, int blocks, int threads, cudaStream_t st)
@@ -395,6 +401,7 @@ int launch_score(int rows, int mode, const ScoreLaunch &L, int blocks, int threa
     case 20: return launch_r<20>(mode, fma, L, blocks, threads, st);
     case 25: return launch_r<25>(mode, fma, L, blocks, threads, st);
     case 32: return launch_r<32>(mode, fma, L, blocks, threads, st);
+    case 50: return launch_r<50>(mode, fma, L, blocks, threads, st);
     default: return SW_ERR_INVALID_ARG;
     }
 }
@@ -419,6 +426,7 @@ int score_kernel_regs(int rows, int mode, int *regs, int *max_blocks_per_sm, int
     case 20: fn = kernel_ptr<20>(mode); break;
     case 25: fn = kernel_ptr<25>(mode); break;
     case 32: fn = kernel_ptr<32>(mode); break;
+    case 50: fn = kernel_ptr<50>(mode); break;
     default: return SW_ERR_INVALID_ARG;
     }
     if (!fn) return SW_ERR_INVALID_ARG;

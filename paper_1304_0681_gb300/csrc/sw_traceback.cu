@@ -118,6 +118,8 @@ struct RevCigar {
     }
 };
 
+__device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
+
 // Band window of chunk c (rows c*rc .. c*rc+rc-1) in rectangle columns.
 __device__ __forceinline__ void chunk_window(const TbPair &q, int c, int rc, int &lo, int &hi)
 {
@@ -159,8 +161,10 @@ __global__ void k_tb_keys(TbParams P, const int32_t *__restrict__ order, int64_t
         tb_keys[p] = key;
         atomicAdd(&hist[key], 1);
         if (need > 0) {
+            const bool big = need > P.small_slab_words;
             atomicMax(&info->max_need[cls], (int32_t)(need < (int64_t)INT32_MAX ? need : (int64_t)INT32_MAX));
-            if (need > P.small_slab_words) atomicAdd(&info->n_big[cls], 1);
+            atomicMax(&info->max_wcap[big ? 0 : 1][cls], min(t.W, 8 * T + (t.b - t.a)));
+            if (big) atomicAdd(&info->n_big[cls], 1);
         }
     }
 }
@@ -168,6 +172,14 @@ __global__ void k_tb_keys(TbParams P, const int32_t *__restrict__ order, int64_t
 __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
 {
     const TbParams &P = L.P;
+    // column tables: s_tab[w] byte x = s(x, w) - o
+    __shared__ uint32_t s_tab[4];
+    {
+        const uint32_t mis4 = ((uint32_t)(uint8_t)(int8_t)(P.sc.mi - P.sc.go)) * 0x01010101u;
+        const uint32_t ma4 = ((uint32_t)(uint8_t)(int8_t)(P.sc.ma - P.sc.go)) * 0x01010101u;
+        if (threadIdx.x < 4) s_tab[threadIdx.x] = prmt(mis4, ma4, 0x3210u + (4u << (4u * threadIdx.x)));
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const int T = L.lanes;
     const int G = 32 / T;
@@ -179,7 +191,7 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
     uint32_t *slab = on ? L.slab + (warp_global * G + g) * L.slab_group_words : nullptr;
     int32_t *bnd = on ? L.boundary + (warp_global * G + g) * L.boundary_group_ints : nullptr;
     const int64_t bnd_half = L.boundary_group_ints / 2;
-    const int32_t ma = P.sc.ma, mi = P.sc.mi, go = P.sc.go, ge = P.sc.ge;
+    const int32_t go = P.sc.go, ge = P.sc.ge;
 
     for (;;) {
         int base = 0;
@@ -189,8 +201,10 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
         const int64_t item = base + g;
         const int32_t p = (on && item < L.n_items) ? L.order[item] : -1;
         TbPair q = tb_pair(P, p, L.status);
-        if (q.score > 0 && slab_need(q, T) > L.slab_group_words) {
-            // the launch was sized from the class maximum; never overrun a slab
+        if (q.score > 0 && (slab_need(q, T) > L.slab_group_words ||
+                            (q.rows > rc && 4 * (int64_t)min(q.W, rc + (q.b - q.a)) > L.boundary_group_ints))) {
+            // the launch was sized from the class maxima; never overrun a slab
+            // or a boundary row
             atomicOr(L.status, ST_INTERNAL);
             q.score = 0;
             q.rows = 0;
@@ -207,8 +221,11 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
             const int width = hi - lo + 1;
             const int steps = __reduce_max_sync(FULLMASK, (unsigned)max(width, 0)) + T - 1;
             const int i0 = c * rc + k * TB_ROWS;
-            uint32_t codes = 0x44444444u;  // 4 bits per row, 4 = no base
+            // per-row selectors into the column table (sign-extended byte);
+            // rows past the end row are never read by the walk
+            uint32_t sel[TB_ROWS];
             {
+                uint32_t codes = 0x44444444u;  // 4 bits per row, 4 = no base
                 const int cnt = min(TB_ROWS, q.rows - i0);
                 if (q.score > 0 && cnt > 0) {
                     const uint32_t w = load_bases(P.ps.reads, q.rs + i0, cnt);
@@ -216,21 +233,53 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
                     for (int r = 0; r < TB_ROWS; ++r)
                         if (r < cnt) codes = (codes & ~(0xFu << (4 * r))) | (((w >> (2 * r)) & 3u) << (4 * r));
                 }
+#pragma unroll
+                for (int r = 0; r < TB_ROWS; ++r) {
+                    const uint32_t x = (codes >> (4 * r)) & 0xFu;
+                    sel[r] = x < 4u ? x * 0x1111u + 0x8880u : 0x8888u;
+                }
             }
+            // per row: E - o and H of the previous column.  E - o is floored
+            // at 0: since H >= 0 the floor never changes max(H + o, E + e) or
+            // which of the two is larger, so E, F and the open bits the walk
+            // reads are exact.
             int32_t E[TB_ROWS], Hp[TB_ROWS];
 #pragma unroll
             for (int r = 0; r < TB_ROWS; ++r) {
-                E[r] = TB_NEG;
+                E[r] = 0;
                 Hp[r] = 0;
             }
+            // boundary rows are indexed relative to the writing chunk's window
             const int32_t *bin = (bnd && c > 0) ? bnd + (c & 1) * bnd_half : nullptr;
             int32_t *bout = (bnd && c + 1 < chunks) ? bnd + ((c + 1) & 1) * bnd_half : nullptr;
             // diagonal into the chunk's first column: the previous chunk's
             // bottom row one column to the left, if it computed it
             int32_t diag_in = 0;
-            if (k == 0 && bin && lo - 1 >= prev_lo && lo - 1 <= prev_hi) diag_in = bin[2 * (lo - 1)];
-            int32_t out_h = 0, out_f = TB_NEG;
-            uint32_t ww = 0;
+            if (k == 0 && bin && lo - 1 >= prev_lo && lo - 1 <= prev_hi) diag_in = bin[2 * (lo - 1 - prev_lo)];
+            int32_t out_h = 0, out_f = 0;
+            // the first lane reads the row above from the previous chunk two
+            // columns ahead, so the loads are in flight while columns compute
+            int32_t nb_h = 0, nb_f = 0, nc_h = 0, nc_f = 0;
+            if (k == 0 && bin) {
+                if (lo >= prev_lo && lo <= prev_hi) {
+                    nb_h = bin[2 * (lo - prev_lo)];
+                    nb_f = bin[2 * (lo - prev_lo) + 1];
+                }
+                if (lo + 1 >= prev_lo && lo + 1 <= prev_hi) {
+                    nc_h = bin[2 * (lo + 1 - prev_lo)];
+                    nc_f = bin[2 * (lo + 1 - prev_lo) + 1];
+                }
+            }
+            // window bases: ww holds the current word's remaining bases, wn the
+            // next 16-base word (requested 16 columns before it is needed)
+            const int64_t abs_lo = q.ws + q.jlo + lo, abs_hi = q.ws + q.jlo + hi;
+            uint32_t ww = 0, wn = 0;
+            int64_t apos = abs_lo;
+            if (width > 0) {
+                const int64_t a1 = (abs_lo & ~(int64_t)15) + 16;
+                ww = load_bases(P.ps.wins, abs_lo, (int)lmin(a1 - abs_lo, abs_hi - abs_lo + 1));
+                wn = a1 <= abs_hi ? load_bases(P.ps.wins, a1, (int)lmin(16, abs_hi - a1 + 1)) : 0u;
+            }
 
             for (int t = 0; t < steps; ++t) {
                 const int jl = t - k;       // column within the window
@@ -238,32 +287,42 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
                 int32_t up_h = __shfl_up_sync(FULLMASK, out_h, 1);
                 int32_t up_f = __shfl_up_sync(FULLMASK, out_f, 1);
                 if (k == 0) {
-                    if (bin && jj >= prev_lo && jj <= prev_hi) {
-                        up_h = bin[2 * jj];
-                        up_f = bin[2 * jj + 1];
+                    up_h = nb_h;
+                    up_f = nb_f;
+                    nb_h = nc_h;
+                    nb_f = nc_f;
+                    const int nx = jj + 2;
+                    if (bin && nx >= prev_lo && nx <= prev_hi) {
+                        nc_h = bin[2 * (nx - prev_lo)];
+                        nc_f = bin[2 * (nx - prev_lo) + 1];
                     } else {
-                        up_h = 0;
-                        up_f = TB_NEG;
+                        nc_h = 0;
+                        nc_f = 0;
                     }
                 }
                 if (jl >= 0 && jl < width) {
-                    if (jl == 0 || (((q.jlo + jj) & 15) == 0))
-                        ww = load_bases(P.ps.wins, q.ws + q.jlo + jj, min(16 - ((q.jlo + jj) & 15), hi - jj + 1));
-                    const uint32_t w = ww & 3u;
+                    const uint32_t tw = s_tab[ww & 3u];
                     ww >>= 2;
+                    if (((++apos) & 15) == 0) {
+                        ww = wn;
+                        const int64_t a2 = apos + 16;
+                        wn = a2 <= abs_hi ? load_bases(P.ps.wins, a2, (int)lmin(16, abs_hi - a2 + 1)) : 0u;
+                    }
                     int32_t d0 = diag_in, hu = up_h, f = up_f;
                     uint32_t word = 0;
 #pragma unroll
                     for (int r = 0; r < TB_ROWS; ++r) {
-                        const uint32_t x = (codes >> (4 * r)) & 0xFu;
-                        const int32_t s = x == w ? ma : mi;
-                        bool eopen, fopen;
-                        const int32_t e = __vibmax_s32(Hp[r] + go, E[r] + ge, &eopen);
-                        f = __vibmax_s32(hu + go, f + ge, &fopen);
-                        const int32_t d = d0 + s;
-                        const int32_t h = __vimax3_s32_relu(d, e, f);
-                        const uint32_t src = h == 0 ? 0u : (h == d ? 1u : (h == e ? 2u : 3u));
-                        word |= (src | ((uint32_t)eopen << 2) | ((uint32_t)fopen << 3)) << (4 * r);
+                        const int32_t sp = (int32_t)prmt(tw, 0u, sel[r]);  // s - o
+                        const int32_t eext = E[r] + ge;
+                        const int32_t e = max(Hp[r], eext);
+                        const int32_t fext = f + ge;
+                        f = max(hu, fext);
+                        const int32_t d = d0 + sp;
+                        const int32_t u = __vimax3_s32(d, e, f);
+                        const int32_t h = max(u + go, 0);
+                        uint32_t code = h == 0 ? 0u : (u == d ? 1u : (u == e ? 2u : 3u));
+                        code |= (Hp[r] >= eext ? 4u : 0u) | (hu >= fext ? 8u : 0u);
+                        word |= code << (4 * r);
                         d0 = Hp[r];
                         Hp[r] = h;
                         E[r] = e;
@@ -273,8 +332,8 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
                     out_h = hu;
                     out_f = f;
                     if (bout && k == T - 1) {
-                        bout[2 * jj] = out_h;
-                        bout[2 * jj + 1] = out_f;
+                        bout[2 * jl] = out_h;
+                        bout[2 * jl + 1] = out_f;
                     }
                 }
                 diag_in = up_h;

@@ -294,7 +294,8 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
                 t.count = cnt;
                 t.slab_words = part == 0 ? max_need : std::min<int64_t>(max_need, kSmallSlabWords);
                 const int chunks = (r.max_m + kTbLanes * TB_ROWS - 1) / (kTbLanes * TB_ROWS);
-                t.bnd_ints = chunks > 1 ? (int64_t)2 * 2 * r.max_n : 0;
+                const int64_t wcap = std::max<int64_t>(ti.max_wcap[part][r.cls], 1);
+                t.bnd_ints = chunks > 1 ? (int64_t)2 * 2 * wcap : 0;
                 const size_t per_block = (size_t)wpb * G * (t.slab_words + t.bnd_ints) * 4;
                 int64_t blocks = std::min<int64_t>(((cnt + G - 1) / G + wpb - 1) / wpb,
                                                    (int64_t)std::max(tbps, 1) * ds->sm_count);
@@ -389,6 +390,20 @@ int sw_batch_align_indexed(const uint8_t *reads, const int64_t *read_offsets, in
     if (rc || n_pairs == 0) return rc;
     if (!pair_read || n_reads < 1) return SW_ERR_INVALID_ARG;
     PairSet ps{(const uint32_t *)reads, read_offsets, pair_read, (const uint32_t *)windows, window_offsets};
+    return run_batch(ps, n_reads, n_pairs, scoring, out_score, out_end, out_cigar, (cudaStream_t)stream);
+}
+
+int sw_batch_align_masked(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads,
+                          const uint8_t *windows, const int64_t *window_offsets, const int64_t *pair_read,
+                          const uint8_t *pair_mask, int64_t n_pairs, const sw_scoring_t *scoring, int32_t *out_score,
+                          int32_t *out_end, sw_cigar_t *out_cigar, sw_stream_t stream)
+{
+    int rc = check_common(reads, read_offsets, windows, window_offsets, n_pairs, scoring, out_score, out_end,
+                          out_cigar);
+    if (rc || n_pairs == 0) return rc;
+    if (!pair_read || !pair_mask || n_reads < 1) return SW_ERR_INVALID_ARG;
+    PairSet ps{(const uint32_t *)reads, read_offsets, pair_read, (const uint32_t *)windows, window_offsets,
+               pair_mask};
     return run_batch(ps, n_reads, n_pairs, scoring, out_score, out_end, out_cigar, (cudaStream_t)stream);
 }
 

@@ -14,6 +14,17 @@ struct PairSet {
     const int64_t *pair_read;   // n_pairs, or nullptr: pair p uses read p
     const uint32_t *wins;       // packed windows (words)
     const int64_t *win_off;     // n_pairs + 1
+    const uint8_t *mask = nullptr;  // n_pairs, or nullptr: align every pair
+};
+
+struct FeatureParams {
+    const uint32_t *reads;
+    const int64_t *read_off;
+    int64_t n_reads;
+    const uint32_t *wins;
+    const int64_t *win_off;
+    const int64_t *cand_off;   // n_reads + 1
+    uint16_t *out;             // bf16 [n_pairs][64]
 };
 
 struct Scoring {
@@ -63,6 +74,7 @@ struct ScoreLaunch {
     int64_t boundary_group_bytes;
     int32_t *work_counter;
     int32_t *status;
+    int32_t one = 1;         // a multiplier the compiler cannot fold
 };
 
 // What every traceback kernel needs about the batch.
@@ -82,6 +94,7 @@ struct TbParams {
 struct TbClassInfo {
     int32_t max_need[N_CLASS];  // largest slab (words) a pair of the class needs
     int32_t n_big[N_CLASS];     // pairs needing more than small_slab_words
+    int32_t max_wcap[2][N_CLASS];  // widest chunk window: [0] big-slab launch, [1] main launch
 };
 
 struct TracebackLaunch {
@@ -98,7 +111,7 @@ struct TracebackLaunch {
 };
 
 // Row counts compiled for the score kernels.
-constexpr int N_SCORE_ROWS = 5;
+constexpr int N_SCORE_ROWS = 6;
 extern const int kScoreRows[N_SCORE_ROWS];
 constexpr int TB_ROWS = 8;
 
@@ -115,6 +128,20 @@ int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, int32_t *hist, int
 int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStream_t st);
 int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads);
 int launch_alu_probe(int kind, int64_t iters, int blocks, int threads, uint32_t *out, cudaStream_t st);
+
+int launch_features(const FeatureParams &P, cudaStream_t st);
+int64_t mlp_floats();
+int launch_mlp_init(float *model, uint64_t seed, cudaStream_t st);
+int launch_mlp_refresh(float *model, cudaStream_t st);
+int launch_mlp_forward(const float *model, const uint16_t *feat, int64_t n, float *out, int sm_count,
+                       cudaStream_t st);
+int launch_mlp_grad(float *model, const uint16_t *feat, const float *target, const int32_t *idx, int64_t n,
+                    int sm_count, cudaStream_t st);
+int launch_mlp_adam(float *model, float lr, int32_t step, cudaStream_t st);
+int launch_select(const float *pred, const int64_t *cand_off, int64_t n_reads, int32_t k, float tau, uint8_t *mask,
+                  cudaStream_t st);
+int launch_best_per_read(const int32_t *score, const int64_t *cand_off, int64_t n_reads, const uint8_t *mask,
+                         int32_t *best, int32_t *best_cand, cudaStream_t st);
 
 void count_launch(int n = 1);
 

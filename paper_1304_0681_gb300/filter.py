@@ -1,0 +1,158 @@
+"""Learned candidate filter over the C ABI.
+
+The paper aligns each read against every extended CAL.  Here a small network
+predicts each candidate's SW score from 4-mer features, only the top-k
+candidates of a read are aligned, and reads whose top predictions are too
+close to call (margin below tau) fall back to aligning every candidate.
+Reported scores are always SW scores of aligned candidates.
+
+Every computation runs in libswgb kernels; this module only allocates the
+device buffers and sequences the calls.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _swgb
+from .device import DeviceBatch
+
+N_FEAT = 64
+
+
+class FilterModel:
+    """A model buffer (fp32 parameters, Adam state, gradient, bf16 copies)."""
+
+    def __init__(self, seed: int = 0, device="cuda"):
+        self.buf = torch.zeros(_swgb.sw_mlp_bytes() // 4, dtype=torch.float32, device=device)
+        self.step = 0
+        _swgb.sw_mlp_init(self.buf, seed)
+
+    # parameter views in the documented layout
+    def params(self) -> torch.Tensor:
+        return self.buf[:33153]
+
+    def set_params(self, flat) -> None:
+        self.buf[:33153].copy_(torch.as_tensor(flat, dtype=torch.float32))
+        _swgb.sw_mlp_refresh(self.buf)
+
+    def gradient(self) -> torch.Tensor:
+        return self.buf[3 * 33153:4 * 33153]
+
+    def forward(self, features: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        n = features.shape[0]
+        out = torch.empty(n, dtype=torch.float32, device=features.device) if out is None else out
+        _swgb.sw_mlp_forward(self.buf, features, n, out)
+        return out
+
+    def grad(self, features, target, idx=None) -> None:
+        n = idx.numel() if idx is not None else features.shape[0]
+        _swgb.sw_mlp_grad(self.buf, features, target, idx, n)
+
+    def adam(self, lr: float) -> None:
+        self.step += 1
+        _swgb.sw_mlp_adam(self.buf, lr, self.step)
+
+    def train(self, features: torch.Tensor, target: torch.Tensor, epochs: int = 4, batch: int = 8192,
+              lr: float = 2e-3, seed: int = 0) -> list:
+        """Minibatch Adam on the mean squared error; returns the mean loss of
+        each epoch measured with the serving forward."""
+        n = features.shape[0]
+        gen = torch.Generator(device=features.device)
+        gen.manual_seed(seed)
+        losses = []
+        for _ in range(epochs):
+            perm = torch.randperm(n, generator=gen, device=features.device).to(torch.int32)
+            for s in range(0, n - batch + 1, batch):
+                self.grad(features, target, perm[s:s + batch])
+                self.adam(lr)
+            pred = self.forward(features)
+            losses.append(float(torch.mean((pred - target) ** 2)))
+        return losses
+
+
+def features(batch: DeviceBatch, cand_offsets: torch.Tensor) -> torch.Tensor:
+    """bf16 features (as int16 storage) of every pair of a read-grouped batch."""
+    out = torch.empty((batch.n_pairs, N_FEAT), dtype=torch.int16, device=batch.reads.device)
+    _swgb.sw_filter_features(batch.reads, batch.read_offsets, batch.n_reads, batch.windows, batch.window_offsets,
+                             cand_offsets, out)
+    return out
+
+
+@dataclass
+class FilteredResult:
+    best_score: torch.Tensor   # int32 per read
+    best_cand: torch.Tensor    # int32 per read (index within the read's candidates)
+    mask: torch.Tensor         # uint8 per pair: aligned or not
+    pred: torch.Tensor         # float per pair
+
+
+def filtered_best(batch: DeviceBatch, cand_offsets: torch.Tensor, model: FilterModel, k: int, tau: float, scoring,
+                  feats: torch.Tensor | None = None) -> FilteredResult:
+    """Features -> network -> top-k / fallback selection -> SW on the
+    selected pairs -> best hit per read (score and end only)."""
+    feats = features(batch, cand_offsets) if feats is None else feats
+    pred = model.forward(feats)
+    mask = torch.empty(batch.n_pairs, dtype=torch.uint8, device=pred.device)
+    _swgb.sw_filter_select(pred, cand_offsets, batch.n_reads, k, tau, mask)
+    _swgb.sw_batch_align_masked(batch.reads, batch.read_offsets, batch.n_reads, batch.windows, batch.window_offsets,
+                                batch.pair_read, mask, batch.n_pairs, scoring, batch.score, batch.end, None)
+    best = torch.empty(batch.n_reads, dtype=torch.int32, device=pred.device)
+    cand = torch.empty(batch.n_reads, dtype=torch.int32, device=pred.device)
+    _swgb.sw_best_per_read(batch.score, cand_offsets, batch.n_reads, mask, best, cand)
+    return FilteredResult(best, cand, mask, pred)
+
+
+def exhaustive_best(batch: DeviceBatch, cand_offsets: torch.Tensor, scoring):
+    """SW on every candidate, best hit per read."""
+    _swgb.sw_batch_align_indexed(batch.reads, batch.read_offsets, batch.n_reads, batch.windows, batch.window_offsets,
+                                 batch.pair_read, batch.n_pairs, scoring, batch.score, batch.end, None)
+    best = torch.empty(batch.n_reads, dtype=torch.int32, device=batch.score.device)
+    cand = torch.empty(batch.n_reads, dtype=torch.int32, device=batch.score.device)
+    _swgb.sw_best_per_read(batch.score, cand_offsets, batch.n_reads, None, best, cand)
+    return best, cand
+
+
+def targets(score: torch.Tensor, read_len: torch.Tensor, match: int) -> torch.Tensor:
+    """Training target of a pair: SW score / (match * read length)."""
+    return score.to(torch.float32) / (float(match) * read_len.to(torch.float32))
+
+
+def calibrate(pred: np.ndarray, score: np.ndarray, cand_offsets: np.ndarray, recall_target: float,
+              ks=(1, 2, 3, 4, 6, 8), taus=None):
+    """Pick (k, tau) with the fewest aligned pairs whose best-hit recall on
+    a held-out set reaches recall_target.  Host-side bookkeeping over
+    predictions and exhaustive scores already computed on the GPU."""
+    taus = taus if taus is not None else [0.0, 0.005, 0.01, 0.02, 0.03, 0.05, 0.08, 0.12, 0.2]
+    nr = len(cand_offsets) - 1
+    counts = np.diff(cand_offsets)
+    rid = np.repeat(np.arange(nr), counts)
+    true_best = np.full(nr, -1, np.int64)
+    np.maximum.at(true_best, rid, score)
+    # rank of each candidate within its read by prediction (desc), ties by index
+    order = np.lexsort((np.arange(len(pred)), -pred, rid))
+    rank = np.empty(len(pred), np.int64)
+    rank[order] = np.arange(len(pred)) - np.repeat(cand_offsets[:-1], counts)[order]
+    best = None
+    for k in ks:
+        sel_pred = np.full(nr, -np.inf, np.float32)
+        nxt_pred = np.full(nr, -np.inf, np.float32)
+        m_k = rank == k - 1
+        m_k1 = rank == k
+        sel_pred[rid[m_k]] = pred[m_k]
+        nxt_pred[rid[m_k1]] = pred[m_k1]
+        topk_best = np.full(nr, -1, np.int64)
+        sel = rank < k
+        np.maximum.at(topk_best, rid[sel], score[sel])
+        with np.errstate(invalid="ignore"):  # reads with <= k candidates: -inf - -inf
+            gap = sel_pred.astype(np.float32) - nxt_pred.astype(np.float32)
+        for tau in taus:
+            fall = (counts <= k) | (gap < np.float32(tau))
+            got = np.where(fall, true_best, topk_best)
+            recall = float(np.mean(got == true_best))
+            aligned = int(np.sum(np.where(fall, counts, np.minimum(counts, k))))
+            if recall >= recall_target and (best is None or aligned < best[2]):
+                best = (k, float(tau), aligned, recall)
+    return best

@@ -33,7 +33,7 @@ def test_binding_covers_declarations_and_loads():
     assert _swgb.sw_packed_bytes(64) == 16
     assert _swgb.sw_packed_bytes(65) == 32
     assert _swgb.sw_strerror(-2) == "CIGAR slot too small"
-    assert _swgb.sw_plan_rows() == [8, 16, 20, 25, 32]
+    assert _swgb.sw_plan_rows() == [8, 16, 20, 25, 32, 50]
 
 
 def test_packing_agrees_with_generator():

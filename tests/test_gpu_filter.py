@@ -1,0 +1,189 @@
+"""GPU parity of the learned candidate filter against oracle/filter_oracle.py.
+
+Tolerances (derived from the arithmetic):
+- features: the kernel multiplies the shared count by 1/(m-3) in fp32 and
+  rounds to bf16; the oracle divides in fp64 and rounds to bf16.  The fp32
+  and fp64 values differ by at most ~1 fp32 ulp, so the bf16 results agree
+  except where that ulp crosses a bf16 rounding boundary: at most one bf16
+  ulp (2^-8 relative) apart.
+- forward: the kernel reads bf16 features and bf16 weights, accumulates in
+  fp32 and rounds the 256 first-layer activations to bf16 before layer 2.
+  The oracle here does the same roundings in fp64, so what remains is fp32
+  accumulation order and activations whose fp32 value sits next to a bf16
+  rounding boundary (one bf16 ulp, 2^-8 relative, on a few of 256 terms);
+  1e-2 relative plus 1e-3 absolute covers that with margin.
+- gradient: fp32 forward and backward against fp64: relative 1e-3 of the
+  largest gradient component.
+- Adam: fp32 against fp64, 1e-5 relative.
+- selection and best hit: bit-exact (the margin decision is taken in fp32 on
+  both sides).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import filter_oracle as fo
+
+pytestmark = pytest.mark.gpu
+SCORING = (5, -4, -10, -1)
+
+
+def _batch(wl, cigar=False):
+    from paper_1304_0681_gb300 import DeviceBatch
+    return DeviceBatch.from_packed(wl.packed_reads(), wl.read_offsets, wl.packed_windows(), wl.window_offsets,
+                                   pair_read=wl.pair_read, cigar=cigar)
+
+
+def _bf16_to_f64(t):
+    import torch
+    return t.view(torch.bfloat16).float().cpu().numpy().astype(np.float64)
+
+
+def test_features_match_oracle():
+    import torch
+    from paper_1304_0681_gb300 import filter as flt
+    wl = synth.generate("filter", seed=5, n_reads=120)
+    b = _batch(wl)
+    co = torch.from_numpy(wl.cand_offsets).cuda()
+    got = _bf16_to_f64(flt.features(b, co))
+    ref = fo.bf16_round(fo.features_batch(wl.reads, wl.read_offsets, wl.windows, wl.window_offsets, wl.pair_read))
+    assert got.shape == ref.shape
+    np.testing.assert_allclose(got, ref, rtol=2 ** -8, atol=0)
+    # edge cases: reads and windows shorter than a 4-mer
+    edge = synth.random_pairs(200, (1, 9), (0, 9), seed=7)
+    b2 = _batch(edge)
+    co2 = torch.arange(edge.n_pairs + 1, dtype=torch.int64, device="cuda")
+    got2 = _bf16_to_f64(flt.features(b2, co2))
+    ref2 = fo.bf16_round(fo.features_batch(edge.reads, edge.read_offsets, edge.windows, edge.window_offsets,
+                                           edge.pair_read))
+    np.testing.assert_allclose(got2, ref2, rtol=2 ** -8, atol=0)
+
+
+def _model_params(model):
+    return fo.Params.from_flat(model.params().cpu().numpy().astype(np.float64))
+
+
+def test_forward_matches_oracle():
+    import torch
+    from paper_1304_0681_gb300 import filter as flt
+    rng = np.random.default_rng(0)
+    model = flt.FilterModel(seed=3)
+    n = 1000 + 13  # several 16-row tiles and a ragged tail
+    x = rng.uniform(0, 0.4, (n, 64))
+    xb = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).cuda().view(torch.int16)
+    got = model.forward(xb).cpu().numpy()
+    P = _model_params(model)
+    Pb = fo.Params(fo.bf16_round(P.W1), P.b1, fo.bf16_round(P.W2), P.b2, P.w3, P.b3)
+    X = fo.bf16_round(x)
+    a1 = fo.bf16_round(np.maximum(X @ Pb.W1 + Pb.b1, 0))
+    ref = np.maximum(a1 @ Pb.W2 + Pb.b2, 0) @ Pb.w3 + Pb.b3
+    np.testing.assert_allclose(got, ref, rtol=1e-2, atol=1e-3)
+
+
+def test_gradient_matches_oracle():
+    import torch
+    from paper_1304_0681_gb300 import filter as flt
+    rng = np.random.default_rng(1)
+    model = flt.FilterModel(seed=4)
+    n = 300
+    x = fo.bf16_round(rng.uniform(0, 0.4, (n, 64)))
+    t = rng.uniform(0, 1, n)
+    xb = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).cuda().view(torch.int16)
+    tt = torch.from_numpy(t.astype(np.float32)).cuda()
+    idx = torch.from_numpy(rng.permutation(n).astype(np.int32)).cuda()
+    model.grad(xb, tt, idx)
+    got = model.gradient().cpu().numpy().astype(np.float64)
+    P = _model_params(model)
+    ref = fo.backward(P, x, np.asarray(t, np.float32).astype(np.float64))
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(got, ref, atol=1e-3 * scale, rtol=0)
+
+
+def test_adam_matches_oracle():
+    import torch
+    from paper_1304_0681_gb300 import filter as flt
+    rng = np.random.default_rng(2)
+    model = flt.FilterModel(seed=5)
+    theta0 = model.params().cpu().numpy().astype(np.float64)
+    m = np.zeros_like(theta0)
+    v = np.zeros_like(theta0)
+    th = theta0.copy()
+    for step in (1, 2, 3):
+        g = rng.normal(0, 1e-2, theta0.shape).astype(np.float32)
+        model.gradient().copy_(torch.from_numpy(g))
+        model.adam(1e-3)
+        th, m, v = fo.adam_step(th, g.astype(np.float64), m, v, step, 1e-3)
+    got = model.params().cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got, th, rtol=1e-5, atol=1e-7)
+
+
+def test_select_and_best_match_oracle():
+    import torch
+    import paper_1304_0681_gb300 as sw
+    rng = np.random.default_rng(3)
+    counts = rng.integers(1, 40, 500)
+    off = np.zeros(501, np.int64)
+    np.cumsum(counts, out=off[1:])
+    n = int(off[-1])
+    pred = np.round(rng.uniform(0, 1, n), 2).astype(np.float32)  # many exact ties
+    score = rng.integers(0, 500, n).astype(np.int32)
+    dpred, doff = torch.from_numpy(pred).cuda(), torch.from_numpy(off).cuda()
+    for k, tau in ((1, 0.0), (1, 0.05), (3, 0.02), (8, 0.1), (16, 0.0)):
+        mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        sw._swgb.sw_filter_select(dpred, doff, 500, k, tau, mask)
+        ref = fo.select_candidates(pred.astype(np.float64), off, k, tau)
+        np.testing.assert_array_equal(mask.cpu().numpy().astype(bool), ref)
+        best = torch.zeros(500, dtype=torch.int32, device="cuda")
+        cand = torch.zeros(500, dtype=torch.int32, device="cuda")
+        sw._swgb.sw_best_per_read(torch.from_numpy(score).cuda(), doff, 500, mask, best, cand)
+        np.testing.assert_array_equal(best.cpu().numpy(), fo.best_per_read(score, off, ref))
+
+
+def test_masked_alignment():
+    import torch
+    import paper_1304_0681_gb300 as sw
+    from gpu_helpers import oracle_subset
+    wl = synth.generate("filter", seed=6, n_reads=60)
+    b = _batch(wl)
+    rng = np.random.default_rng(4)
+    mask = (rng.uniform(0, 1, wl.n_pairs) < 0.3).astype(np.uint8)
+    sw._swgb.sw_batch_align_masked(b.reads, b.read_offsets, b.n_reads, b.windows, b.window_offsets, b.pair_read,
+                                   torch.from_numpy(mask).cuda(), b.n_pairs, SCORING, b.score, b.end, None)
+    sw.sw_sync_status()
+    score = b.score.cpu().numpy()
+    assert (score[mask == 0] == -1).all()
+    sel = np.nonzero(mask)[0]
+    ref = oracle_subset(wl, sel, SCORING, cigar=False)
+    np.testing.assert_array_equal(score[sel], ref["score"])
+
+
+def test_training_lowers_loss_and_ranks_true_hits():
+    """What the trained network gains over the method without it: against
+    the untrained network (same features, same selection) the true candidate
+    lands in the top 4 for nearly every read, and the loss drops."""
+    import torch
+    from paper_1304_0681_gb300 import filter as flt
+    wl = synth.generate("filter", seed=8, n_reads=3000)
+    b = _batch(wl)
+    co = torch.from_numpy(wl.cand_offsets).cuda()
+    flt.exhaustive_best(b, co, SCORING)
+    feats = flt.features(b, co)
+    rl = torch.from_numpy(wl.pair_read_lengths).cuda()
+    tgt = flt.targets(b.score, rl, SCORING[0])
+    model = flt.FilterModel(seed=1)
+    off = wl.cand_offsets
+
+    def top_rank_of_true(pred):
+        ranks = []
+        for r in range(wl.n_reads):
+            p = pred[off[r]:off[r + 1]]
+            ranks.append(int(np.sum(p > p[wl.true_cand[r]])))
+        return np.array(ranks)
+
+    untrained = top_rank_of_true(model.forward(feats).cpu().numpy())
+    before = float(torch.mean((model.forward(feats) - tgt) ** 2))
+    losses = model.train(feats, tgt, epochs=10, batch=2048, lr=3e-3)
+    assert losses[-1] < 0.5 * before, (before, losses)
+    trained = top_rank_of_true(model.forward(feats).cpu().numpy())
+    assert np.mean(trained < 4) > 0.97, np.mean(trained < 4)
+    assert np.mean(trained < 4) > np.mean(untrained < 4) + 0.3, (np.mean(trained < 4), np.mean(untrained < 4))

@@ -10,7 +10,7 @@ from gpu_helpers import assert_parity, run_gpu
 pytestmark = pytest.mark.gpu
 
 DEFAULT = (5, -4, -10, -1)
-# match*min(m,n) decides the arithmetic: <= 1022 -> 16-bit lanes with 16-bit
+# match*min(m,n) decides the arithmetic: <= 510 -> 16-bit lanes with 16-bit
 # keys, <= 32000 -> 16-bit lanes with 32-bit keys, else int32 lanes
 WIDE16 = (50, -30, -60, -5)
 INT32 = (120, -60, -7, -3)
