@@ -45,7 +45,7 @@ __global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring
         } else {
             const int64_t hmax = (int64_t)sc.ma * (m < n ? m : n);
             int mode = MODE_I32;
-            if (hmax <= 510) mode = MODE_I16;  // (H << 6) | 63 fits 15 bits
+            if (hmax <= 1022) mode = MODE_I16;  // (H << 5) | 31 fits 15 bits
             else if (hmax <= 32000) mode = MODE_I16W;
             const int cls = mode * N_MCLASS + mclass_of((int32_t)m);
             int nb = (int)((n - 1) >> 5);

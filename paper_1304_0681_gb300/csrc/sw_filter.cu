@@ -29,25 +29,43 @@ constexpr unsigned FM = 0xffffffffu;
 
 // ---------------------------------------------------------------- features
 
-// Count the 4-mers of bases [s, s+len) into hist (shared, 256 x uint32).
-__device__ __forceinline__ void count_kmers(const uint32_t *__restrict__ buf, int64_t s, int32_t len,
-                                            uint32_t *hist, int lane)
+// Count the 4-mers of bases [s, s+len) into hist (shared, 256 x uint32);
+// lane l takes positions 8l .. 8l+7 of every 256.
+__device__ __forceinline__ void count_kmers32(const uint32_t *__restrict__ buf, int64_t s, int32_t len,
+                                              uint32_t *hist, int lane)
 {
     const int nk = len - 3;  // number of 4-mers
-    for (int base = lane * 16; base < nk; base += 32 * 16) {
-        // 16 k-mers starting at positions base .. base+15 need bases base .. base+18
-        const int avail = min(19, len - base);
-        const uint32_t lo = load_bases(buf, s + base, min(16, avail));
-        const uint32_t hi = avail > 16 ? load_bases(buf, s + base + 16, avail - 16) : 0u;
-        const uint64_t v = (uint64_t)lo | ((uint64_t)hi << 32);
-        const int cnt = min(16, nk - base);
+    for (int base = lane * 8; base < nk; base += 32 * 8) {
+        // 8 k-mers starting at base .. base+7 need bases base .. base+10
+        const uint32_t v = load_bases(buf, s + base, min(11, len - base));
+        const int cnt = min(8, nk - base);
         for (int t = 0; t < cnt; ++t) {
-            const uint32_t w = (uint32_t)(v >> (2 * t)) & 0xFFu;  // b0 in bits 0-1 ... b3 in bits 6-7
+            const uint32_t w = (v >> (2 * t)) & 0xFFu;  // b0 in bits 0-1 ... b3 in bits 6-7
             const uint32_t q = ((w & 3u) << 6) | (((w >> 2) & 3u) << 4) | (((w >> 4) & 3u) << 2) | (w >> 6);
             atomicAdd(&hist[q], 1u);
         }
     }
 }
+
+// Same counts as bytes, four per word: word q >> 2 (the 3-base prefix), byte
+// q & 3 (the last base).  Exact while no 4-mer occurs more than 255 times,
+// i.e. for sequences of at most 258 bases.
+__device__ __forceinline__ void count_kmers8(const uint32_t *__restrict__ buf, int64_t s, int32_t len,
+                                             uint32_t *hist, int lane)
+{
+    const int nk = len - 3;
+    for (int base = lane * 8; base < nk; base += 32 * 8) {
+        const uint32_t v = load_bases(buf, s + base, min(11, len - base));
+        const int cnt = min(8, nk - base);
+        for (int t = 0; t < cnt; ++t) {
+            const uint32_t w = (v >> (2 * t)) & 0xFFu;
+            const uint32_t pre = ((w & 3u) << 4) | (((w >> 2) & 3u) << 2) | ((w >> 4) & 3u);
+            atomicAdd(&hist[pre], 1u << (8u * (w >> 6)));
+        }
+    }
+}
+
+constexpr int kByteCountMax = 258;
 
 __global__ void __launch_bounds__(256) k_features(FeatureParams P)
 {
@@ -59,24 +77,47 @@ __global__ void __launch_bounds__(256) k_features(FeatureParams P)
         if (c0 >= c1) continue;
         const int64_t rs = P.read_off[r];
         const int32_t m = (int32_t)(P.read_off[r + 1] - rs);
+        const bool rbytes = m <= kByteCountMax;
         for (int q = lane; q < 256; q += 32) hr[q] = 0;
         __syncwarp();
-        if (m >= 4) count_kmers(P.reads, rs, m, hr, lane);
+        if (m >= 4) {
+            if (rbytes) count_kmers8(P.reads, rs, m, hr, lane);
+            else count_kmers32(P.reads, rs, m, hr, lane);
+        }
         __syncwarp();
         const float inv = m >= 4 ? 1.f / (float)(m - 3) : 0.f;
         for (int64_t p = c0; p < c1; ++p) {
             const int64_t ws = P.win_off[p];
             const int32_t n = (int32_t)(P.win_off[p + 1] - ws);
-            for (int q = lane; q < 256; q += 32) hw[q] = 0;
-            __syncwarp();
-            if (n >= 4 && m >= 4) count_kmers(P.wins, ws, n, hw, lane);
-            __syncwarp();
-            // lane: prefixes 2*lane and 2*lane + 1 (4-mer codes 8*lane .. 8*lane+7)
             uint32_t s0 = 0, s1 = 0;
+            if (rbytes && n <= kByteCountMax) {
+                // byte counters: feature k = byte sum of min(read word k, window word k)
+                hw[lane] = 0;
+                hw[lane + 32] = 0;
+                __syncwarp();
+                if (n >= 4 && m >= 4) count_kmers8(P.wins, ws, n, hw, lane);
+                __syncwarp();
+                s0 = (uint32_t)__dp4a(__vminu4(hr[2 * lane], hw[2 * lane]), 0x01010101u, 0u);
+                s1 = (uint32_t)__dp4a(__vminu4(hr[2 * lane + 1], hw[2 * lane + 1]), 0x01010101u, 0u);
+            } else {
+                for (int q = lane; q < 256; q += 32) hw[q] = 0;
+                __syncwarp();
+                if (n >= 4 && m >= 4) count_kmers32(P.wins, ws, n, hw, lane);
+                __syncwarp();
+                if (rbytes) {
+                    // read in bytes, window in words
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                s0 += min(hr[8 * lane + b], hw[8 * lane + b]);
-                s1 += min(hr[8 * lane + 4 + b], hw[8 * lane + 4 + b]);
+                    for (int b = 0; b < 4; ++b) {
+                        s0 += min((hr[2 * lane] >> (8 * b)) & 0xFFu, hw[8 * lane + b]);
+                        s1 += min((hr[2 * lane + 1] >> (8 * b)) & 0xFFu, hw[8 * lane + 4 + b]);
+                    }
+                } else {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        s0 += min(hr[8 * lane + b], hw[8 * lane + b]);
+                        s1 += min(hr[8 * lane + 4 + b], hw[8 * lane + 4 + b]);
+                    }
+                }
             }
             const __nv_bfloat162 f = __floats2bfloat162_rn((float)s0 * inv, (float)s1 * inv);
             reinterpret_cast<__nv_bfloat162 *>(P.out)[p * 32 + lane] = f;

@@ -43,8 +43,10 @@
 // the lane's block, so equal H prefers the smaller row); a three-way-max tree
 // gives the column's best key, and the lane's running best is replaced only
 // when the column's H is strictly larger (so the smallest column wins).  The
-// 16-bit keys need (H << 6) + 63 < 32768, i.e. H <= 510 (6-bit row tags
-// for up to 64 rows per lane); pairs with larger possible scores use 32-bit
+// 16-bit keys need (H << TAGB) + TAGM < 32768: H <= 1022 with 5-bit row
+// tags (up to 32 rows per lane), H <= 510 with 6-bit tags (up to 64 rows;
+// the host picks such plans only for classes whose score bound allows it);
+// pairs with larger possible scores use 32-bit
 // keys built from each half (MODE_I16W) or the int32 mode.
 #include "sw_device.cuh"
 #include "swgb_internal.h"

@@ -121,27 +121,31 @@ struct Plan {
     int lanes, rows;
 };
 
-// Lanes per group and rows per lane for reads up to m_max in a mode.
-Plan choose_plan(int mode, int32_t m_max)
+// Lanes per group and rows per lane for reads up to m_max in a mode.  In
+// the 16-bit-key mode a lane block of more than 32 rows needs 6-bit row tags,
+// which leave room for scores up to 510 only (hmax: the class's score bound).
+Plan choose_plan(int mode, int32_t m_max, int64_t hmax)
 {
+    const int max_rows = (mode == MODE_I16 && hmax > 510) ? 32 : 64;
     {
         std::lock_guard<std::mutex> lk(g_plan_mu);
         for (const PlanOverride &o : g_plans)
-            if (m_max <= o.max_read_len) return Plan{o.lanes, o.rows};
+            if (m_max <= o.max_read_len && o.rows <= max_rows) return Plan{o.lanes, o.rows};
     }
-    (void)mode;
-    // estimated issue cost per pair-column: padded rows x ~7.5 ops + ~25 ops
-    // per lane-step, scaled by the fraction of lanes a warp leaves idle
+    // estimated issue cost per pair-column: padded rows x ~6.5 ALU ops + ~40
+    // ops per lane-step (both measured), scaled by the fraction of lanes a
+    // warp leaves idle
     double best = 1e300;
     Plan bp{32, 32};
     for (int ri = 0; ri < N_SCORE_ROWS; ++ri) {
         const int R = kScoreRows[ri];
+        if (R > max_rows) continue;
         for (int T = 1; T <= 32; ++T) {
             const int chunks = (m_max + T * R - 1) / (T * R);
             if (chunks > 1 && T < 32) continue;
             const int G = 32 / T;
             const double lane_util = (double)(G * T) / 32.0;
-            const double cost = chunks * (double)T * (R * 7.5 + 25.0) / lane_util;
+            const double cost = chunks * (double)T * (R * 6.5 + 40.0) / lane_util;
             if (cost < best - 1e-9) {
                 best = cost;
                 bp = Plan{T, R};
@@ -220,7 +224,7 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         r.max_m = ci.max_m[cls];
         r.max_n = ci.max_n[cls];
         pos += cnt;
-        r.plan = choose_plan(r.mode, r.max_m);
+        r.plan = choose_plan(r.mode, r.max_m, (int64_t)sc.ma * std::min(r.max_m, r.max_n));
         int regs = 0, bps = 0;
         if ((rc = score_kernel_regs(r.plan.rows, r.mode, &regs, &bps, kThreads))) return rc;
         if (bps < 1) return SW_ERR_INTERNAL;

@@ -57,6 +57,14 @@ def test_features_match_oracle():
     ref2 = fo.bf16_round(fo.features_batch(edge.reads, edge.read_offsets, edge.windows, edge.window_offsets,
                                            edge.pair_read))
     np.testing.assert_allclose(got2, ref2, rtol=2 ** -8, atol=0)
+    # sequences longer than 258 bases use full-width counters
+    long = synth.random_pairs(150, (200, 320), (180, 420), seed=9, alphabet=2)
+    b3 = _batch(long)
+    co3 = torch.arange(long.n_pairs + 1, dtype=torch.int64, device="cuda")
+    got3 = _bf16_to_f64(flt.features(b3, co3))
+    ref3 = fo.bf16_round(fo.features_batch(long.reads, long.read_offsets, long.windows, long.window_offsets,
+                                           long.pair_read))
+    np.testing.assert_allclose(got3, ref3, rtol=2 ** -8, atol=0)
 
 
 def _model_params(model):

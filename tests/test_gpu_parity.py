@@ -10,7 +10,7 @@ from gpu_helpers import assert_parity, run_gpu
 pytestmark = pytest.mark.gpu
 
 DEFAULT = (5, -4, -10, -1)
-# match*min(m,n) decides the arithmetic: <= 510 -> 16-bit lanes with 16-bit
+# match*min(m,n) decides the arithmetic: <= 1022 -> 16-bit lanes with 16-bit
 # keys, <= 32000 -> 16-bit lanes with 32-bit keys, else int32 lanes
 WIDE16 = (50, -30, -60, -5)
 INT32 = (120, -60, -7, -3)
@@ -89,7 +89,8 @@ def _workload(reads, wins):
                           np.zeros(n, np.uint8), np.zeros(n, np.int32))
 
 
-@pytest.mark.parametrize("lanes,rows", [(1, 8), (3, 16), (4, 25), (5, 20), (7, 16), (13, 8), (32, 8), (32, 32)])
+@pytest.mark.parametrize("lanes,rows", [(1, 8), (3, 16), (4, 25), (5, 20), (7, 16), (13, 8), (32, 8), (32, 32),
+                                        (2, 50), (3, 50)])
 def test_lane_plans(lanes, rows):
     """Every (lanes, rows) plan gives the same answer, including plans that
     split a read into several row chunks (lanes * rows < read length)."""
