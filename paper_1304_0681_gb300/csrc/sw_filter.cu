@@ -188,6 +188,18 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
                  : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// Four 8x8 bf16 matrices from shared memory; lane l supplies the address of
+// row l % 8 of matrix l / 8 and receives, for every matrix, the pair of
+// elements (row l / 4, columns 2 (l % 4) and 2 (l % 4) + 1) -- the B
+// fragment layout of mma.m16n8k16 when the rows are n and the columns k.
+__device__ __forceinline__ void ldsm_x4(const void *smem_row, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem_row);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -258,11 +270,14 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const float *__restrict__ m
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
 #pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-                    const __nv_bfloat16 *row = w1 + (nb * 64 + nt * 8 + g) * W1S + kk * 16 + tig * 2;
-                    const uint32_t bb0 = *reinterpret_cast<const uint32_t *>(row);
-                    const uint32_t bb1 = *reinterpret_cast<const uint32_t *>(row + 8);
-                    mma_bf16(acc1[nt], xa[kk][0], xa[kk][1], xa[kk][2], xa[kk][3], bb0, bb1);
+                for (int np = 0; np < 4; ++np) {
+                    // n-tiles 2np, 2np+1: rows n0 .. n0+15, columns k0 .. k0+15
+                    uint32_t b00, b01, b10, b11;
+                    ldsm_x4(w1 + (nb * 64 + np * 16 + (lane >> 4) * 8 + (lane & 7)) * W1S + kk * 16 +
+                                ((lane >> 3) & 1) * 8,
+                            b00, b01, b10, b11);
+                    mma_bf16(acc1[2 * np], xa[kk][0], xa[kk][1], xa[kk][2], xa[kk][3], b00, b01);
+                    mma_bf16(acc1[2 * np + 1], xa[kk][0], xa[kk][1], xa[kk][2], xa[kk][3], b10, b11);
                 }
             }
 #pragma unroll
@@ -273,11 +288,13 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const float *__restrict__ m
                 const uint32_t a2 = pack_bf16(fmaxf(t1[0], 0.f), fmaxf(t1[1], 0.f));
                 const uint32_t a3 = pack_bf16(fmaxf(t1[2], 0.f), fmaxf(t1[3], 0.f));
 #pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-                    const __nv_bfloat16 *row = w2 + (nt * 8 + g) * W2S + nb * 64 + ks * 16 + tig * 2;
-                    const uint32_t bb0 = *reinterpret_cast<const uint32_t *>(row);
-                    const uint32_t bb1 = *reinterpret_cast<const uint32_t *>(row + 8);
-                    mma_bf16(acc2[nt], a0, a1, a2, a3, bb0, bb1);
+                for (int np = 0; np < 4; ++np) {
+                    uint32_t b00, b01, b10, b11;
+                    ldsm_x4(w2 + (np * 16 + (lane >> 4) * 8 + (lane & 7)) * W2S + nb * 64 + ks * 16 +
+                                ((lane >> 3) & 1) * 8,
+                            b00, b01, b10, b11);
+                    mma_bf16(acc2[2 * np], a0, a1, a2, a3, b00, b01);
+                    mma_bf16(acc2[2 * np + 1], a0, a1, a2, a3, b10, b11);
                 }
             }
         }

@@ -169,6 +169,12 @@ __global__ void k_tb_keys(TbParams P, const int32_t *__restrict__ order, int64_t
     }
 }
 
+// TILED (one lane per pair only): the warp's slabs and boundary rows are
+// interleaved lane-minor -- word (chunk c, column jl) of lane l at
+// [(c * WCAP + jl) * 32 + l] -- so that, all lanes being at the same chunk
+// and column at every step, each store instruction writes one full line.
+// Otherwise every group owns a packed slab of its chunks' windows.
+template <bool TILED>
 __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
 {
     const TbParams &P = L.P;
@@ -188,9 +194,15 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
     const bool on = g < G;
     const int rc = T * TB_ROWS;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    uint32_t *slab = on ? L.slab + (warp_global * G + g) * L.slab_group_words : nullptr;
-    int32_t *bnd = on ? L.boundary + (warp_global * G + g) * L.boundary_group_ints : nullptr;
-    const int64_t bnd_half = L.boundary_group_ints / 2;
+    const int WCAP = L.wcap;
+    // slab: TILED -> the warp's tile, indexed with the lane; else the group's slab
+    uint32_t *slab = !on ? nullptr
+                         : TILED ? L.slab + warp_global * 32 * L.slab_group_words
+                                 : L.slab + (warp_global * G + g) * L.slab_group_words;
+    int32_t *bnd = !on ? nullptr
+                       : TILED ? L.boundary + warp_global * 32 * L.boundary_group_ints
+                               : L.boundary + (warp_global * G + g) * L.boundary_group_ints;
+    const int64_t bnd_half = TILED ? 32 * (L.boundary_group_ints / 2) : L.boundary_group_ints / 2;
     const int32_t go = P.sc.go, ge = P.sc.ge;
 
     for (;;) {
@@ -201,8 +213,11 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
         const int64_t item = base + g;
         const int32_t p = (on && item < L.n_items) ? L.order[item] : -1;
         TbPair q = tb_pair(P, p, L.status);
-        if (q.score > 0 && (slab_need(q, T) > L.slab_group_words ||
-                            (q.rows > rc && 4 * (int64_t)min(q.W, rc + (q.b - q.a)) > L.boundary_group_ints))) {
+        const bool over = TILED ? (q.rows > (L.slab_group_words / max(WCAP, 1)) * rc ||
+                                   min(q.W, rc + (q.b - q.a)) > WCAP)
+                                : (slab_need(q, T) > L.slab_group_words ||
+                                   (q.rows > rc && 4 * (int64_t)min(q.W, rc + (q.b - q.a)) > L.boundary_group_ints));
+        if (q.score > 0 && over) {
             // the launch was sized from the class maxima; never overrun a slab
             // or a boundary row
             atomicOr(L.status, ST_INTERNAL);
@@ -255,19 +270,21 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
             // diagonal into the chunk's first column: the previous chunk's
             // bottom row one column to the left, if it computed it
             int32_t diag_in = 0;
-            if (k == 0 && bin && lo - 1 >= prev_lo && lo - 1 <= prev_hi) diag_in = bin[2 * (lo - 1 - prev_lo)];
+            // boundary element (column x of the writing chunk, value v)
+            auto bidx = [&](int x, int v) -> int64_t { return TILED ? ((int64_t)x * 2 + v) * 32 + lane : 2 * x + v; };
+            if (k == 0 && bin && lo - 1 >= prev_lo && lo - 1 <= prev_hi) diag_in = bin[bidx(lo - 1 - prev_lo, 0)];
             int32_t out_h = 0, out_f = 0;
             // the first lane reads the row above from the previous chunk two
             // columns ahead, so the loads are in flight while columns compute
             int32_t nb_h = 0, nb_f = 0, nc_h = 0, nc_f = 0;
             if (k == 0 && bin) {
                 if (lo >= prev_lo && lo <= prev_hi) {
-                    nb_h = bin[2 * (lo - prev_lo)];
-                    nb_f = bin[2 * (lo - prev_lo) + 1];
+                    nb_h = bin[bidx(lo - prev_lo, 0)];
+                    nb_f = bin[bidx(lo - prev_lo, 1)];
                 }
                 if (lo + 1 >= prev_lo && lo + 1 <= prev_hi) {
-                    nc_h = bin[2 * (lo + 1 - prev_lo)];
-                    nc_f = bin[2 * (lo + 1 - prev_lo) + 1];
+                    nc_h = bin[bidx(lo + 1 - prev_lo, 0)];
+                    nc_f = bin[bidx(lo + 1 - prev_lo, 1)];
                 }
             }
             // window bases: ww holds the current word's remaining bases, wn the
@@ -293,8 +310,8 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
                     nb_f = nc_f;
                     const int nx = jj + 2;
                     if (bin && nx >= prev_lo && nx <= prev_hi) {
-                        nc_h = bin[2 * (nx - prev_lo)];
-                        nc_f = bin[2 * (nx - prev_lo) + 1];
+                        nc_h = bin[bidx(nx - prev_lo, 0)];
+                        nc_f = bin[bidx(nx - prev_lo, 1)];
                     } else {
                         nc_h = 0;
                         nc_f = 0;
@@ -328,12 +345,13 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
                         E[r] = e;
                         hu = h;
                     }
-                    slab[slab_off + (int64_t)jl * T + k] = word;
+                    if (TILED) slab[((int64_t)c * WCAP + jl) * 32 + lane] = word;
+                    else slab[slab_off + (int64_t)jl * T + k] = word;
                     out_h = hu;
                     out_f = f;
                     if (bout && k == T - 1) {
-                        bout[2 * jl] = out_h;
-                        bout[2 * jl + 1] = out_f;
+                        bout[bidx(jl, 0)] = out_h;
+                        bout[bidx(jl, 1)] = out_f;
                     }
                 }
                 diag_in = up_h;
@@ -378,7 +396,9 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
                     }
                     if (jj < clo || jj > chi) break;  // left the band: inconsistent
                     const int kk = (i - cc * rc) / TB_ROWS, nib = i % TB_ROWS;
-                    const uint32_t code = (slab[cbase + (int64_t)(jj - clo) * T + kk] >> (4 * nib)) & 0xFu;
+                    const int64_t widx = TILED ? ((int64_t)cc * WCAP + (jj - clo)) * 32 + lane
+                                               : cbase + (int64_t)(jj - clo) * T + kk;
+                    const uint32_t code = (slab[widx] >> (4 * nib)) & 0xFu;
                     if (state == 0) {
                         const uint32_t src = code & 3u;
                         if (src == 0u) {
@@ -437,14 +457,16 @@ int launch_tb_keys(const TbParams &P, const int32_t *order, int64_t n_items, con
 
 int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStream_t st)
 {
-    k_traceback<<<blocks, threads, 0, st>>>(L);
+    if (L.tiled) k_traceback<true><<<blocks, threads, 0, st>>>(L);
+    else k_traceback<false><<<blocks, threads, 0, st>>>(L);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
 }
 
 int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback, threads, 0) == cudaSuccess
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback<false>, threads, 0) ==
+                   cudaSuccess
                ? SW_OK
                : SW_ERR_CUDA;
 }

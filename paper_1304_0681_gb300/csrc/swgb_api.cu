@@ -27,6 +27,7 @@ constexpr int kThreads = 128;
 constexpr int kTbLanes = 1;            // lanes per pair in the traceback
 constexpr int kSmallSlabWords = 4096;  // per-pair slab of the main traceback launch
 constexpr size_t kSlabBudget = (size_t)4 << 30;
+constexpr int64_t kTiledLaneWords = 4096;  // largest lane tile of a lane-interleaved traceback
 constexpr int kMaxDevices = 64;
 
 struct Buffer {
@@ -280,7 +281,9 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         const int64_t wpb = kThreads / 32;
         struct TbRun {
             int64_t start, count;
-            int64_t slab_words, bnd_ints;
+            int64_t slab_words, bnd_ints;  // per group, or per lane when tiled
+            int32_t wcap;
+            bool tiled;
             int blocks;
             int cls, part;
         };
@@ -296,11 +299,20 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
                 TbRun t{};
                 t.start = parts[part][0];
                 t.count = cnt;
-                t.slab_words = part == 0 ? max_need : std::min<int64_t>(max_need, kSmallSlabWords);
-                const int chunks = (r.max_m + kTbLanes * TB_ROWS - 1) / (kTbLanes * TB_ROWS);
-                const int64_t wcap = std::max<int64_t>(ti.max_wcap[part][r.cls], 1);
-                t.bnd_ints = chunks > 1 ? (int64_t)2 * 2 * wcap : 0;
-                const size_t per_block = (size_t)wpb * G * (t.slab_words + t.bnd_ints) * 4;
+                const int rc = kTbLanes * TB_ROWS;
+                const int64_t chunks = (r.max_m + rc - 1) / rc;
+                t.wcap = (int32_t)std::max<int64_t>(ti.max_wcap[part][r.cls], 1);
+                // lane-interleaved tiles when one lane owns a pair and a lane's
+                // tile (every chunk at the widest window) stays small
+                t.tiled = kTbLanes == 1 && chunks * t.wcap <= kTiledLaneWords;
+                if (t.tiled) {
+                    t.slab_words = chunks * t.wcap;
+                    t.bnd_ints = chunks > 1 ? (int64_t)2 * 2 * t.wcap : 0;
+                } else {
+                    t.slab_words = part == 0 ? max_need : std::min<int64_t>(max_need, kSmallSlabWords);
+                    t.bnd_ints = chunks > 1 ? (int64_t)2 * 2 * t.wcap : 0;
+                }
+                const size_t per_block = (size_t)wpb * 32 / kTbLanes * (t.slab_words + t.bnd_ints) * 4;
                 int64_t blocks = std::min<int64_t>(((cnt + G - 1) / G + wpb - 1) / wpb,
                                                    (int64_t)std::max(tbps, 1) * ds->sm_count);
                 blocks = std::min<int64_t>(blocks, (int64_t)(kSlabBudget / std::max<size_t>(per_block, 1)));
@@ -320,9 +332,11 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
             B.lanes = kTbLanes;
             B.slab = (uint32_t *)ds->dyn.ptr;
             B.slab_group_words = t.slab_words;
-            const size_t slab_total = (size_t)t.blocks * wpb * G * t.slab_words;
+            const size_t slab_total = (size_t)t.blocks * wpb * (32 / kTbLanes) * t.slab_words;
             B.boundary = (int32_t *)ds->dyn.ptr + slab_total;
             B.boundary_group_ints = t.bnd_ints;
+            B.wcap = t.wcap;
+            B.tiled = t.tiled;
             B.work_counter = counters + 2 * N_CLASS + 2 * t.cls + t.part;
             B.status = &info->status;
             if ((rc = launch_traceback(B, t.blocks, kThreads, st))) return rc;

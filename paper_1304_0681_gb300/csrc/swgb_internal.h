@@ -102,10 +102,12 @@ struct TracebackLaunch {
     const int32_t *order;
     int64_t n_items;
     int32_t lanes;
-    uint32_t *slab;          // per-group traceback bit slabs
-    int64_t slab_group_words;
-    int32_t *boundary;       // per-group chunk boundaries (2 x int32 per column, double-buffered)
-    int64_t boundary_group_ints;
+    uint32_t *slab;          // traceback bit slabs
+    int64_t slab_group_words;  // per group; tiled: per lane (chunks x wcap)
+    int32_t *boundary;       // chunk boundaries (2 x int32 per column, double-buffered)
+    int64_t boundary_group_ints;  // per group; tiled: per lane (2 x 2 x wcap)
+    int32_t wcap;            // widest chunk window of the launch
+    bool tiled;              // lane-interleaved warp tiles (one lane per pair)
     int32_t *work_counter;
     int32_t *status;
 };
