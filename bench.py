@@ -300,6 +300,7 @@ def main():
         pg = dist
     import paper_1304_0681_gb300 as sw
     from paper_1304_0681_gb300 import DeviceBatch, align
+    from paper_1304_0681_gb300.shard import reduce_run
 
     want_cigar = not args.no_cigar
     wl = synth.generate(args.workload, seed=rank)
@@ -340,13 +341,12 @@ def main():
     launches = sw.sw_launch_count() - launches0 - 0
     sw.sw_sync_status()
     sw.sw_phase_timing(False)
-    total_ms = sum(step_ms)
-    if pg:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * cells * args.steps / (total_ms * 1e-3) / 1e9
-    reads_per_s = ws * n_reads * args.steps / (total_ms * 1e-3)
+    # whole job: every rank's cells over the slowest rank's time
+    all_cells, total_s = reduce_run(cells * args.steps, sum(step_ms) * 1e-3)
+    all_reads, _ = reduce_run(n_reads * args.steps, 0.0)
+    total_ms = total_s * 1e3
+    value = all_cells / total_s / 1e9
+    reads_per_s = all_reads / total_s
 
     score_ms = statistics.mean(p[1] for p in phases)
     tb_ms = statistics.mean(p[2] for p in phases)
@@ -382,13 +382,10 @@ def main():
             t0 = time.perf_counter()
             sw.sw_batch_align_host(h_reads, h_roff, h_wins, h_woff, n, SCORING, h_score, h_end, cig)
             e_times.append(time.perf_counter() - t0)
-        e2e_s = sum(e_times) / len(e_times)
-        if pg:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": ws * cells / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "reads_per_s": ws * n_reads / e2e_s}
+        e2e_cells, e2e_s = reduce_run(cells, sum(e_times) / len(e_times))
+        e2e_reads, _ = reduce_run(n_reads, 0.0)
+        e2e = {"value": e2e_cells / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "reads_per_s": e2e_reads / e2e_s}
 
     filt = None
     if not args.no_filter:

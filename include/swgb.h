@@ -286,6 +286,27 @@ int64_t sw_launch_count(void);
  * (longer reads are then processed in chunks of 32 * r_rows rows).
  */
 int sw_set_plan(int32_t max_read_len, int32_t lanes, int32_t r_rows);
+
+/*
+ * Traceback arithmetic.  SW_TB_AUTO (the default) recomputes two pairs per
+ * lane in 16-bit halves for every length class whose score bound
+ * (match x min(m, n)) is at most 32000, and uses 32-bit arithmetic for the
+ * rest; SW_TB_INT32 uses 32-bit arithmetic for every class.  Both give the
+ * same CIGARs.  Returns SW_ERR_INVALID_ARG for any other value.  The setting
+ * is process-wide and applies to calls made after it.
+ */
+#define SW_TB_AUTO 0
+#define SW_TB_INT32 1
+int sw_set_traceback_mode(int32_t mode);
+
+/*
+ * Pairs the most recent sw_batch_align* call with a CIGAR on the current
+ * device sent to each traceback kernel: out[0] through the 16-bit kernel,
+ * out[1] through the 32-bit kernels (pairs without an alignment included).
+ * Known when the call returns, before its kernels finish.  Returns
+ * SW_ERR_INVALID_ARG for a null pointer.
+ */
+int sw_last_traceback_split(int64_t *out2);
 int sw_plan_rows(int32_t *rows, int32_t cap);
 
 /*

@@ -22,7 +22,8 @@ ERRORS = {
 
 #: every symbol include/swgb.h declares
 EXPORTS = ("sw_cigar_capacity", "sw_packed_bytes", "sw_batch_align", "sw_batch_align_indexed",
-           "sw_batch_align_host", "sw_sync_status", "sw_strerror", "sw_launch_count", "sw_set_plan",
+           "sw_batch_align_host", "sw_sync_status", "sw_strerror", "sw_launch_count", "sw_set_plan", "sw_set_traceback_mode",
+           "sw_last_traceback_split",
            "sw_plan_rows", "sw_alu_probe", "sw_phase_timing", "sw_phase_times", "sw_batch_align_noalloc",
            "sw_batch_align_masked", "sw_filter_features", "sw_mlp_bytes", "sw_mlp_init", "sw_mlp_refresh",
            "sw_mlp_forward", "sw_mlp_grad", "sw_mlp_adam", "sw_filter_select", "sw_best_per_read")
@@ -91,6 +92,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_launch_count.restype = i64
     lib.sw_set_plan.argtypes = [i32, i32, i32]
     lib.sw_set_plan.restype = ctypes.c_int
+    lib.sw_set_traceback_mode.argtypes = [i32]
+    lib.sw_set_traceback_mode.restype = ctypes.c_int
+    lib.sw_last_traceback_split.argtypes = [ctypes.c_void_p]
+    lib.sw_last_traceback_split.restype = ctypes.c_int
     lib.sw_plan_rows.argtypes = [p, i32]
     lib.sw_plan_rows.restype = ctypes.c_int
     lib.sw_phase_timing.argtypes = [i32]
@@ -187,6 +192,22 @@ def sw_launch_count() -> int:
 
 def sw_set_plan(max_read_len: int, lanes: int, rows: int) -> None:
     _check(_lib.sw_set_plan(int(max_read_len), int(lanes), int(rows)), "sw_set_plan")
+
+
+SW_TB_AUTO = 0
+SW_TB_INT32 = 1
+
+
+def sw_set_traceback_mode(mode: int) -> None:
+    _check(_lib.sw_set_traceback_mode(int(mode)), "sw_set_traceback_mode")
+
+
+def sw_last_traceback_split() -> tuple:
+    """(pairs through the 16-bit traceback, pairs through the 32-bit ones) of
+    the last call with a CIGAR on the current device."""
+    buf = (ctypes.c_int64 * 2)()
+    _check(_lib.sw_last_traceback_split(ctypes.cast(buf, ctypes.c_void_p)), "sw_last_traceback_split")
+    return int(buf[0]), int(buf[1])
 
 
 def sw_plan_rows() -> list:

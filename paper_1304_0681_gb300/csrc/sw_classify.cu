@@ -15,48 +15,62 @@ __global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring
                            int32_t *__restrict__ out_score, int32_t *__restrict__ out_end,
                            int32_t *__restrict__ cig_n)
 {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_pairs;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t rd = ps.pair_read ? ps.pair_read[p] : p;
-        bool bad = rd < 0 || rd >= n_reads;
+    // warp-strided so that every lane of a warp takes part in the key groups
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; base < n_pairs;
+         base += nwarps * 32) {
+        const int64_t p = base + lane;
+        int32_t key = -1, cls = 0;
         int64_t m = 0, n = 0;
-        if (!bad) {
-            const int64_t r0 = ps.read_off[rd], r1 = ps.read_off[rd + 1];
-            const int64_t w0 = ps.win_off[p], w1 = ps.win_off[p + 1];
-            m = r1 - r0;
-            n = w1 - w0;
-            bad = r0 < 0 || w0 < 0 || m < 1 || m > SW_MAX_READ_LEN || n < 0 || n > SW_MAX_WINDOW_LEN;
+        if (p < n_pairs) {
+            const int64_t rd = ps.pair_read ? ps.pair_read[p] : p;
+            bool bad = rd < 0 || rd >= n_reads;
+            if (!bad) {
+                const int64_t r0 = ps.read_off[rd], r1 = ps.read_off[rd + 1];
+                const int64_t w0 = ps.win_off[p], w1 = ps.win_off[p + 1];
+                m = r1 - r0;
+                n = w1 - w0;
+                bad = r0 < 0 || w0 < 0 || m < 1 || m > SW_MAX_READ_LEN || n < 0 || n > SW_MAX_WINDOW_LEN;
+            }
+            if (bad) {
+                atomicOr(&info->status, ST_BAD_INPUT);
+            } else if (ps.mask && !ps.mask[p]) {
+                // not selected: no alignment
+                out_score[p] = -1;
+                out_end[2 * p] = -1;
+                out_end[2 * p + 1] = -1;
+                if (cig_n) cig_n[p] = 0;
+            } else if (n == 0) {
+                // an empty window aligns nothing: score 0, no end cell, no CIGAR
+                out_score[p] = 0;
+                out_end[2 * p] = -1;
+                out_end[2 * p + 1] = -1;
+                if (cig_n) cig_n[p] = 0;
+            } else {
+                const int64_t hmax = (int64_t)sc.ma * (m < n ? m : n);
+                int mode = MODE_I32;
+                if (hmax <= 1022) mode = MODE_I16;  // (H << 5) | 31 fits 15 bits
+                else if (hmax <= 32000) mode = MODE_I16W;
+                cls = mode * N_MCLASS + mclass_of((int32_t)m);
+                int nb = (int)((n - 1) >> 5);
+                nb = nb > N_NBUCKET - 1 ? N_NBUCKET - 1 : nb;
+                key = cls * N_NBUCKET + (N_NBUCKET - 1 - nb);
+            }
+            keys[p] = key;
         }
-        int32_t key = -1;
-        if (bad) {
-            atomicOr(&info->status, ST_BAD_INPUT);
-        } else if (ps.mask && !ps.mask[p]) {
-            // not selected: no alignment
-            out_score[p] = -1;
-            out_end[2 * p] = -1;
-            out_end[2 * p + 1] = -1;
-            if (cig_n) cig_n[p] = 0;
-        } else if (n == 0) {
-            // an empty window aligns nothing: score 0, no end cell, no CIGAR
-            out_score[p] = 0;
-            out_end[2 * p] = -1;
-            out_end[2 * p + 1] = -1;
-            if (cig_n) cig_n[p] = 0;
-        } else {
-            const int64_t hmax = (int64_t)sc.ma * (m < n ? m : n);
-            int mode = MODE_I32;
-            if (hmax <= 1022) mode = MODE_I16;  // (H << 5) | 31 fits 15 bits
-            else if (hmax <= 32000) mode = MODE_I16W;
-            const int cls = mode * N_MCLASS + mclass_of((int32_t)m);
-            int nb = (int)((n - 1) >> 5);
-            nb = nb > N_NBUCKET - 1 ? N_NBUCKET - 1 : nb;
-            key = cls * N_NBUCKET + (N_NBUCKET - 1 - nb);
-            atomicAdd(&hist[key], 1);
-            atomicAdd(&info->count[cls], 1);
-            atomicMax(&info->max_n[cls], (int32_t)n);
-            atomicMax(&info->max_m[cls], (int32_t)m);
+        // one set of atomics per distinct key in the warp (the key fixes the class)
+        const KeyGroup g = key_group(key);
+        if (key >= 0) {
+            const unsigned mx_n = __reduce_max_sync(g.mask, (unsigned)n);
+            const unsigned mx_m = __reduce_max_sync(g.mask, (unsigned)m);
+            if (g.rank == 0) {
+                atomicAdd(&hist[key], g.size);
+                atomicAdd(&info->count[cls], g.size);
+                atomicMax(&info->max_n[cls], (int32_t)mx_n);
+                atomicMax(&info->max_m[cls], (int32_t)mx_m);
+            }
         }
-        keys[p] = key;
     }
 }
 
@@ -89,10 +103,19 @@ __global__ void k_scan(const int32_t *__restrict__ hist, int32_t *__restrict__ s
 __global__ void k_scatter(const int32_t *__restrict__ keys, int64_t n_pairs, int32_t *__restrict__ cursor,
                           int32_t *__restrict__ order)
 {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_pairs;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t k = keys[p];
-        if (k >= 0) order[atomicAdd(&cursor[k], 1)] = (int32_t)p;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; base < n_pairs;
+         base += nwarps * 32) {
+        const int64_t p = base + lane;
+        const int32_t k = p < n_pairs ? keys[p] : -1;
+        const KeyGroup g = key_group(k);
+        if (k >= 0) {
+            int32_t at = 0;
+            if (g.rank == 0) at = atomicAdd(&cursor[k], g.size);
+            at = __shfl_sync(g.mask, at, g.leader);
+            order[at + g.rank] = (int32_t)p;
+        }
     }
 }
 

@@ -32,6 +32,27 @@ __device__ __forceinline__ uint32_t load_bases(const uint32_t *__restrict__ buf,
     return __funnelshift_r(lo, hi, sh);
 }
 
+// Lanes of a converged warp that hold the same key form one group, led by
+// its lowest lane.  Per-pair atomics on a few hot counters (a batch whose
+// pairs share one length class sends every pair to the same histogram bin)
+// become one atomic per distinct key and warp.  Every lane of the warp must
+// call this.
+struct KeyGroup {
+    unsigned mask;  // lanes holding this lane's key
+    int leader;     // lowest lane of the group
+    int rank;       // this lane's position within the group
+    int size;       // lanes in the group
+};
+__device__ __forceinline__ KeyGroup key_group(int32_t key)
+{
+    KeyGroup g;
+    g.mask = __match_any_sync(0xffffffffu, key);
+    g.leader = __ffs(g.mask) - 1;
+    g.rank = __popc(g.mask & ((1u << (threadIdx.x & 31)) - 1u));
+    g.size = __popc(g.mask);
+    return g;
+}
+
 // 64-bit best-cell key: larger H first, then smaller j, then smaller i.
 __device__ __forceinline__ uint64_t cell_key(uint32_t h, int32_t j, int32_t i)
 {

@@ -33,6 +33,8 @@
 // counting sort orders each length class by cost so a warp's groups sweep
 // similar windows, and pairs whose slab exceeds the per-group slab of the
 // main launch form a separate launch with larger slabs.
+#include <algorithm>
+
 #include "sw_device.cuh"
 #include "swgb_internal.h"
 
@@ -142,29 +144,46 @@ __global__ void k_tb_keys(TbParams P, const int32_t *__restrict__ order, int64_t
                           const int32_t *__restrict__ score_keys, int32_t *__restrict__ tb_keys,
                           int32_t *__restrict__ hist, TbClassInfo *__restrict__ info)
 {
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_items;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t p = order[q];
-        const int cls = score_keys[p] / N_NBUCKET;
-        const int T = P.lanes;
-        const TbPair t = tb_pair(P, p, nullptr);
-        const int64_t need = slab_need(t, T);
-        // big slabs first, then by falling cost (~9% buckets of rows x window)
-        int32_t key;
-        if (need > P.small_slab_words) {
-            key = cls * N_NBUCKET;
-        } else {
-            const float cost = t.score > 0 ? (float)t.rows * (float)min(t.W, 8 * T + (t.b - t.a)) : 1.f;
-            const int cb = min(254, max(0, (int)(8.f * __log2f(cost))));
-            key = cls * N_NBUCKET + 1 + (254 - cb);
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; base < n_items;
+         base += nwarps * 32) {
+        const int64_t q = base + lane;
+        int32_t key = -1, cls = 0, need32 = 0, wc = 0;
+        bool big = false;
+        if (q < n_items) {
+            const int32_t p = order[q];
+            cls = score_keys[p] / N_NBUCKET;
+            const int T = P.lanes;
+            const TbPair t = tb_pair(P, p, nullptr);
+            const int64_t need = slab_need(t, T);
+            big = need > P.small_slab_words;
+            // big slabs first, then by falling cost (~9% buckets of rows x window)
+            if (big) {
+                key = cls * N_NBUCKET;
+            } else {
+                const float cost = t.score > 0 ? (float)t.rows * (float)min(t.W, 8 * T + (t.b - t.a)) : 1.f;
+                const int cb = min(254, max(0, (int)(8.f * __log2f(cost))));
+                key = cls * N_NBUCKET + 1 + (254 - cb);
+            }
+            tb_keys[p] = key;
+            need32 = (int32_t)(need < (int64_t)INT32_MAX ? need : (int64_t)INT32_MAX);
+            wc = need > 0 ? min(t.W, 8 * T + (t.b - t.a)) : 0;
         }
-        tb_keys[p] = key;
-        atomicAdd(&hist[key], 1);
-        if (need > 0) {
-            const bool big = need > P.small_slab_words;
-            atomicMax(&info->max_need[cls], (int32_t)(need < (int64_t)INT32_MAX ? need : (int64_t)INT32_MAX));
-            atomicMax(&info->max_wcap[big ? 0 : 1][cls], min(t.W, 8 * T + (t.b - t.a)));
-            if (big) atomicAdd(&info->n_big[cls], 1);
+        // the key fixes the class and whether the slab is big
+        const KeyGroup g = key_group(key);
+        if (key >= 0) {
+            const unsigned mx_need = __reduce_max_sync(g.mask, (unsigned)need32);
+            const unsigned mx_wc = __reduce_max_sync(g.mask, (unsigned)wc);
+            const unsigned n_big = __reduce_add_sync(g.mask, (unsigned)(big && need32 > 0));
+            if (g.rank == 0) {
+                atomicAdd(&hist[key], g.size);
+                if (mx_need > 0) {
+                    atomicMax(&info->max_need[cls], (int32_t)mx_need);
+                    atomicMax(&info->max_wcap[big ? 0 : 1][cls], (int32_t)mx_wc);
+                }
+                if (n_big) atomicAdd(&info->n_big[cls], (int32_t)n_big);
+            }
         }
     }
 }
@@ -443,6 +462,384 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
     }
 }
 
+// ---------------------------------------------------------------------------
+// 16x2 traceback.  One lane owns two pairs, A in the low and B in the high
+// half of every register, so each DPX instruction recomputes two cells.  It
+// serves the classes whose score bound keeps every value below 32768
+// (match x min(m, n) <= 32000, match - o <= 127); the layout is the tiled one
+// above with two 32-bit words per lane and column (rows 0-3 and rows 4-7,
+// pair A in bits 0-15, pair B in bits 16-31).
+//
+// Per cell four bits record which equalities fail (1 = not equal):
+//   bit 0  H != H(i-1,j-1) + s    bit 1  H != E
+//   bit 2  E != H(i,j-1) + o      bit 3  F != H(i-1,j) + o
+// so the walk takes the diagonal where bit 0 is clear, else E where bit 1
+// is clear, else F, and a gap run opens where bit 2 (3) is clear -- the same
+// preferences as the int32 kernel.  Whether H is 0 is not stored: the walk
+// carries the exact value of its current state, starting from the score,
+// and stops where H reaches 0.
+//
+// Each bit is min(x, 1) per half of a difference x that is non-negative in
+// both halves (a maximum minus one of its operands), so the differences and
+// the packing of the bits are integer multiply-adds on the FMA pipe, next to
+// the DPX maxima on the ALU pipe: per two cells 9 ALU and 9 FMA-pipe
+// instructions when s - o >= 0 for every substitution (FMA_ADD), else the
+// diagonal add and its difference move to the ALU pipe.
+//
+// Each pair keeps its own chunk windows (the clamped band boxes); both pairs
+// of a lane step through window offset t together and the warp steps to its
+// widest window.  Offsets past a pair's own window are computed as well:
+// they lie right of its box and hold values no larger than the full
+// matrix's (past the window end they see an all-(s = o) table, so nothing
+// grows there), which changes no cell the walk reads.  Boundary rows hold
+// (H | F << 16) per pair and offset, read by the next chunk at its own shift.
+//
+// The sweep leaves each task's tile (64 pairs) in place, and k_tb16_walk then
+// walks every pair with one thread: a walk is a chain of dependent loads from
+// tiles that are long out of L2, so it runs best at full occupancy, apart
+// from the register-heavy sweep.
+
+__device__ __forceinline__ uint32_t mad_u32(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t splat16(int32_t x) { return ((uint32_t)(uint16_t)(int16_t)x) * 0x10001u; }
+
+// Streams the window bases of one pair, one column per call; past the
+// window end it yields table index 4 (all s = o).
+struct WinStream {
+    uint32_t ww, wn;
+    int64_t apos, aend;
+    __device__ void start(const uint32_t *__restrict__ wins, int64_t a0, int64_t end)
+    {
+        apos = a0;
+        aend = end;
+        ww = wn = 0;
+        if (a0 < end) {
+            const int64_t a1 = (a0 & ~(int64_t)15) + 16;
+            ww = load_bases(wins, a0, (int)lmin(a1 - a0, end - a0));
+            wn = a1 < end ? load_bases(wins, a1, (int)lmin(16, end - a1)) : 0u;
+        }
+    }
+    __device__ __forceinline__ uint32_t next(const uint32_t *__restrict__ wins)
+    {
+        const uint32_t idx = apos < aend ? (ww & 3u) : 4u;
+        ww >>= 2;
+        if (((++apos) & 15) == 0) {
+            ww = wn;
+            const int64_t a2 = apos + 16;
+            wn = a2 < aend ? load_bases(wins, a2, (int)lmin(16, aend - a2)) : 0u;
+        }
+        return idx;
+    }
+};
+
+// Selector nibbles of one row for pair A (bytes 0-1) and pair B (bytes 2-3):
+// the row's base picks its byte of the column table and the high byte
+// replicates its sign; a row without a base takes the sign of byte 0 (0 or
+// -1, never above s = o).
+__device__ __forceinline__ uint32_t sel16(uint32_t xa, uint32_t xb)
+{
+    const uint32_t a = xa < 4u ? (xa | ((8u | xa) << 4)) : 0x88u;
+    const uint32_t b = xb < 4u ? ((4u + xb) | ((12u + xb) << 4)) : 0xCCu;
+    return a | (b << 8);
+}
+
+template <bool FMA_ADD>
+__global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
+{
+    const TbParams &P = L.P;
+    // s_tab[w] byte x = s(x, w) - o; s_tab[4] = 0 (s = o, past a window end)
+    __shared__ uint32_t s_tab[8];
+    {
+        const uint32_t mis4 = ((uint32_t)(uint8_t)(int8_t)(P.sc.mi - P.sc.go)) * 0x01010101u;
+        const uint32_t ma4 = ((uint32_t)(uint8_t)(int8_t)(P.sc.ma - P.sc.go)) * 0x01010101u;
+        if (threadIdx.x < 4) s_tab[threadIdx.x] = prmt(mis4, ma4, 0x3210u + (4u << (4u * threadIdx.x)));
+        else if (threadIdx.x < 8) s_tab[threadIdx.x] = 0u;
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int WCAP = L.wcap;
+    const int rc = TB_ROWS;
+    uint32_t *bnd = (uint32_t *)L.boundary + warp_global * 32 * L.boundary_group_ints;
+    const int32_t go = P.sc.go, ge = P.sc.ge;
+    const uint32_t GE2 = splat16(ge), GO2 = splat16(go);
+    const uint32_t one = (uint32_t)L.one;
+    const uint32_t m1 = 0u - one, two = one + one, four = two + two, eight = four + four;
+    const uint32_t mul1 = eight + eight, mul2 = mul1 * mul1, mul3 = mul2 * mul1;  // 16, 256, 4096
+    const uint32_t ONES = 0x00010001u;
+    const int64_t lane_chunks = L.slab_group_words / (2 * (int64_t)max(WCAP, 1));
+
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(L.work_counter, 64);
+        base = __shfl_sync(FULLMASK, base, 0);
+        if (base >= L.n_items) break;
+        TbPair q[2];
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+            const int64_t item = base + 2 * lane + x;
+            const int32_t p = item < L.n_items ? L.order[item] : -1;
+            q[x] = tb_pair(P, p, L.status);
+            const bool over = (q[x].rows + rc - 1) / rc > lane_chunks || min(q[x].W, rc + (q[x].b - q[x].a)) > WCAP;
+            if (q[x].score > 0 && over) {
+                // the launch was sized from the class maxima; never overrun
+                atomicOr(L.status, ST_INTERNAL);
+                q[x].score = 0;
+                q[x].rows = 0;
+            }
+        }
+        // the task's tile (64 pairs), kept for the walk kernel
+        uint2 *slab = (uint2 *)L.slab + (int64_t)(base / 64) * 32 * (L.slab_group_words / 2);
+        const int32_t rows_l = max(q[0].score > 0 ? q[0].rows : 0, q[1].score > 0 ? q[1].rows : 0);
+        const int32_t rows_w = __reduce_max_sync(FULLMASK, (unsigned)rows_l);
+        const int chunks = (rows_w + rc - 1) / rc;
+
+        int prev_lo[2] = {0, 0};
+        int prev_steps = 0;
+        for (int c = 0; c < chunks; ++c) {
+            int lo[2], hi[2];
+#pragma unroll
+            for (int x = 0; x < 2; ++x) {
+                lo[x] = 0;
+                hi[x] = -1;
+                if (q[x].score > 0 && c * rc < q[x].rows) chunk_window(q[x], c, rc, lo[x], hi[x]);
+            }
+            const int steps = __reduce_max_sync(FULLMASK, (unsigned)max(max(hi[0] - lo[0] + 1, hi[1] - lo[1] + 1), 0));
+            const int i0 = c * rc;
+            uint32_t sel[TB_ROWS];
+            {
+                uint32_t codes[2];
+#pragma unroll
+                for (int x = 0; x < 2; ++x) {
+                    codes[x] = 0x44444444u;  // 4 bits per row, 4 = no base
+                    const int cnt = min(TB_ROWS, q[x].rows - i0);
+                    if (q[x].score > 0 && cnt > 0) {
+                        const uint32_t w = load_bases(P.ps.reads, q[x].rs + i0, cnt);
+#pragma unroll
+                        for (int r = 0; r < TB_ROWS; ++r)
+                            if (r < cnt) codes[x] = (codes[x] & ~(0xFu << (4 * r))) | (((w >> (2 * r)) & 3u) << (4 * r));
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < TB_ROWS; ++r) sel[r] = sel16((codes[0] >> (4 * r)) & 0xFu, (codes[1] >> (4 * r)) & 0xFu);
+            }
+            uint32_t E[TB_ROWS], Hp[TB_ROWS];
+#pragma unroll
+            for (int r = 0; r < TB_ROWS; ++r) {
+                E[r] = 0u;
+                Hp[r] = 0u;
+            }
+            // one boundary row, updated in place: offset t is read (two steps
+            // ahead, at t + shift with shift >= 0) before step t overwrites it
+            const uint32_t *bin = c > 0 ? bnd : nullptr;
+            uint32_t *bout = c + 1 < chunks ? bnd : nullptr;
+            // boundary word of pair x at offset t of the previous chunk (0 past its steps)
+            int shift[2];
+            shift[0] = lo[0] - prev_lo[0];
+            shift[1] = lo[1] - prev_lo[1];
+            auto bload = [&](int x, int t) -> uint32_t {
+                return (bin && t >= 0 && t < prev_steps) ? bin[((int64_t)t * 32 + lane) * 2 + x] : 0u;
+            };
+            // the row above, two offsets ahead: packed (H | F << 16) per pair
+            uint32_t nb[2], nc[2], dg[2];
+#pragma unroll
+            for (int x = 0; x < 2; ++x) {
+                dg[x] = bload(x, shift[x] - 1);
+                nb[x] = bload(x, shift[x]);
+                nc[x] = bload(x, shift[x] + 1);
+            }
+            uint32_t diag_in = prmt(dg[0], dg[1], 0x5410u);
+            WinStream ws[2];
+#pragma unroll
+            for (int x = 0; x < 2; ++x) {
+                const int64_t a0 = q[x].ws + q[x].jlo + lo[x];
+                ws[x].start(P.ps.wins, a0, q[x].score > 0 ? q[x].ws + q[x].n : a0);
+            }
+
+            for (int t = 0; t < steps; ++t) {
+                const uint32_t up_h = prmt(nb[0], nb[1], 0x5410u);
+                const uint32_t up_f = prmt(nb[0], nb[1], 0x7632u);
+#pragma unroll
+                for (int x = 0; x < 2; ++x) {
+                    nb[x] = nc[x];
+                    nc[x] = bload(x, t + 2 + shift[x]);
+                }
+                const uint32_t tA = s_tab[ws[0].next(P.ps.wins)];
+                const uint32_t tB = s_tab[ws[1].next(P.ps.wins)];
+                uint32_t d0 = diag_in, hu = up_h, f = up_f;
+                uint32_t w0 = 0u, w1 = 0u;
+#pragma unroll
+                for (int r = 0; r < TB_ROWS; ++r) {
+                    const uint32_t sp = prmt(tA, tB, sel[r]);  // s - o, both pairs
+                    const uint32_t e = __viaddmax_s16x2(E[r], GE2, Hp[r]);
+                    f = __viaddmax_s16x2(f, GE2, hu);
+                    const uint32_t d = FMA_ADD ? mad_u32(d0, one, sp) : __viaddmax_s16x2(d0, sp, 0x80008000u);
+                    const uint32_t u = __vimax3_s16x2(d, e, f);
+                    const uint32_t h = __viaddmax_s16x2_relu(u, GO2, 0u);
+                    const uint32_t nd = FMA_ADD ? min_u16x2(mad_u32(d, m1, u), ONES) : min_u16x2(u ^ d, ONES);
+                    const uint32_t ne = min_u16x2(mad_u32(e, m1, u), ONES);
+                    const uint32_t nE = min_u16x2(mad_u32(Hp[r], m1, e), ONES);
+                    const uint32_t nF = min_u16x2(mad_u32(hu, m1, f), ONES);
+                    uint32_t code = mad_u32(ne, two, nd);
+                    code = mad_u32(nE, four, code);
+                    code = mad_u32(nF, eight, code);
+                    if (r == 0) w0 = code;
+                    else if (r == 4) w1 = code;
+                    else if (r < 4) w0 = mad_u32(code, r == 1 ? mul1 : r == 2 ? mul2 : mul3, w0);
+                    else w1 = mad_u32(code, r == 5 ? mul1 : r == 6 ? mul2 : mul3, w1);
+                    d0 = Hp[r];
+                    Hp[r] = h;
+                    E[r] = e;
+                    hu = h;
+                }
+                // streaming store: the walk reads back a few words of it
+                __stcs(slab + ((int64_t)c * WCAP + t) * 32 + lane, make_uint2(w0, w1));
+                if (bout)
+                    *(uint2 *)(bout + ((int64_t)t * 32 + lane) * 2) = make_uint2(prmt(hu, f, 0x5410u), prmt(hu, f, 0x7632u));
+                diag_in = up_h;
+            }
+            prev_lo[0] = lo[0];
+            prev_lo[1] = lo[1];
+            prev_steps = steps;
+            __syncwarp();
+        }
+
+        __syncwarp();
+    }
+}
+
+// One thread per pair: walk back from the end cell through the tile that
+// k_traceback16 wrote (item k of the launch: task k / 64, lane (k % 64) / 2,
+// half k % 2), carrying the exact value of the current state (the tile does
+// not record where H is 0).  The thread keeps the tile word it used last and
+// the word one column to its left (the next word of a diagonal or deletion
+// step within the chunk, loaded one step early), and the 16-base words of
+// read and window that hold its current row and column.
+__global__ void __launch_bounds__(256) k_tb16_walk(const TracebackLaunch L)
+{
+    const TbParams &P = L.P;
+    const int WCAP = L.wcap, rc = TB_ROWS;
+    const int32_t go = P.sc.go, ge = P.sc.ge;
+    const int64_t lane_chunks = L.slab_group_words / (2 * (int64_t)max(WCAP, 1));
+    for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < L.n_items;
+         item += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = L.order[item];
+        TbPair qq = tb_pair(P, p, nullptr);
+        // the sweep skipped (and reported) pairs that overrun the tile
+        if ((qq.rows + rc - 1) / rc > lane_chunks || min(qq.W, rc + (qq.b - qq.a)) > WCAP) qq.score = 0;
+        const int64_t off = P.cig_off[p];
+        RevCigar rcg{P.cig_ops + off, P.cig_off[p + 1] - off, 0, 0u, 0, false};
+        if (qq.score <= 0) {
+            P.cig_n[p] = 0;
+            continue;
+        }
+        const uint2 *tile = (const uint2 *)L.slab + (item / 64) * 32 * (L.slab_group_words / 2);
+        const int lane = (int)((item & 63) >> 1), hs = 16 * (int)(item & 1);
+        rcg.push(4u, qq.m - 1 - qq.ie);  // trailing soft clip
+        int32_t i = qq.ie, jj = qq.W - 1;
+        int32_t v = qq.score;  // value of the current state at (i, jj)
+        int state = 0;
+        int cc = i / rc, clo, chi;
+        chunk_window(qq, cc, rc, clo, chi);
+        int64_t key = -1, pkey = -1, rkey = -1, wkey = -1;
+        uint2 w = make_uint2(0u, 0u), pw = w;
+        uint32_t rw = 0u, ww = 0u;
+        bool ok = false;
+        // every step moves, or switches into a gap state before moving
+        const int64_t limit = 2 * ((int64_t)qq.rows + qq.W) + 4;
+        for (int64_t it = 0; it < limit; ++it) {
+            if (state == 0 && v == 0) {
+                ok = true;
+                break;
+            }
+            if (i < 0 || jj < 0 || v < 0) break;
+            if (i < cc * rc) {
+                cc = i / rc;
+                chunk_window(qq, cc, rc, clo, chi);
+            }
+            if (jj < clo || jj > chi) break;  // left the band: inconsistent
+            const int64_t k = (int64_t)cc * WCAP + (jj - clo);
+            if (k != key) {
+                w = k == pkey ? pw : tile[k * 32 + lane];
+                key = k;
+                if (jj - 1 >= clo) {
+                    pkey = k - 1;
+                    pw = tile[(k - 1) * 32 + lane];
+                }
+            }
+            const int r = i - cc * rc;
+            const uint32_t code = ((r < 4 ? w.x : w.y) >> (hs + 4 * (r & 3))) & 0xFu;
+            if (state == 0) {
+                if (!(code & 1u)) {
+                    // diagonal: H(i-1, j-1) = H(i, j) - s(r_i, w_j)
+                    const int64_t rpos = qq.rs + i, wpos = qq.ws + qq.jlo + jj;
+                    if ((rpos >> 4) != rkey) {
+                        rkey = rpos >> 4;
+                        rw = __ldg(P.ps.reads + rkey);
+                    }
+                    if ((wpos >> 4) != wkey) {
+                        wkey = wpos >> 4;
+                        ww = __ldg(P.ps.wins + wkey);
+                    }
+                    const uint32_t ri = (rw >> (2 * (rpos & 15))) & 3u;
+                    const uint32_t wj = (ww >> (2 * (wpos & 15))) & 3u;
+                    v -= ri == wj ? P.sc.ma : P.sc.mi;
+                    rcg.push(0u, 1);
+                    --i;
+                    --jj;
+                } else {
+                    state = (code & 2u) ? 2 : 1;
+                }
+            } else if (state == 1) {
+                rcg.push(2u, 1);
+                if (!(code & 4u)) {
+                    v -= go;  // E(i,j) = H(i,j-1) + o
+                    state = 0;
+                } else {
+                    v -= ge;  // E(i,j) = E(i,j-1) + e
+                }
+                --jj;
+            } else {
+                rcg.push(1u, 1);
+                if (!(code & 8u)) {
+                    v -= go;  // F(i,j) = H(i-1,j) + o
+                    state = 0;
+                } else {
+                    v -= ge;
+                }
+                --i;
+            }
+        }
+        if (!ok) atomicOr(L.status, ST_INTERNAL);
+        rcg.push(4u, i + 1);  // leading soft clip
+        rcg.flush();
+        if (rcg.overflow) {
+            P.cig_n[p] = -1;
+            atomicOr(L.status, ST_CAPACITY);
+        } else {
+            uint32_t *o = rcg.out;
+            for (int32_t a2 = 0, b2 = rcg.n - 1; a2 < b2; ++a2, --b2) {
+                const uint32_t tmp = o[a2];
+                o[a2] = o[b2];
+                o[b2] = tmp;
+            }
+            P.cig_n[p] = rcg.n;
+        }
+    }
+}
+
 int launch_tb_keys(const TbParams &P, const int32_t *order, int64_t n_items, const int32_t *score_keys,
                    int32_t *tb_keys, int32_t *hist, TbClassInfo *info, cudaStream_t st)
 {
@@ -457,18 +854,25 @@ int launch_tb_keys(const TbParams &P, const int32_t *order, int64_t n_items, con
 
 int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStream_t st)
 {
-    if (L.tiled) k_traceback<true><<<blocks, threads, 0, st>>>(L);
+    if (L.packed16) {
+        if (L.P.sc.mi >= L.P.sc.go) k_traceback16<true><<<blocks, threads, 0, st>>>(L);
+        else k_traceback16<false><<<blocks, threads, 0, st>>>(L);
+        // the walks: one thread per pair, a grid of whole waves
+        int64_t wb = (L.n_items + 255) / 256;
+        k_tb16_walk<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(wb, 152 * 8)), 256, 0, st>>>(L);
+        count_launch();
+    } else if (L.tiled) k_traceback<true><<<blocks, threads, 0, st>>>(L);
     else k_traceback<false><<<blocks, threads, 0, st>>>(L);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
 }
 
-int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads)
+int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads, bool packed16)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback<false>, threads, 0) ==
-                   cudaSuccess
-               ? SW_OK
-               : SW_ERR_CUDA;
+    const cudaError_t e =
+        packed16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback16<true>, threads, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback<false>, threads, 0);
+    return e == cudaSuccess ? SW_OK : SW_ERR_CUDA;
 }
 
 }  // namespace swgb

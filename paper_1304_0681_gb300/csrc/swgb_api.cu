@@ -19,6 +19,7 @@
 namespace swgb {
 
 static std::atomic<int64_t> g_launches{0};
+static std::atomic<int32_t> g_tb_mode{SW_TB_AUTO};
 void count_launch(int n) { g_launches += n; }
 
 namespace {
@@ -28,6 +29,8 @@ constexpr int kTbLanes = 1;            // lanes per pair in the traceback
 constexpr int kSmallSlabWords = 4096;  // per-pair slab of the main traceback launch
 constexpr size_t kSlabBudget = (size_t)4 << 30;
 constexpr int64_t kTiledLaneWords = 4096;  // largest lane tile of a lane-interleaved traceback
+constexpr int64_t kTiledLaneWords16 = 8192;  // the same for the 16-bit traceback (two pairs per lane)
+constexpr size_t kTile16Budget = (size_t)12 << 30;  // 16-bit traceback tiles kept for the walk
 constexpr int kMaxDevices = 64;
 
 struct Buffer {
@@ -52,6 +55,7 @@ struct DeviceState {
     int32_t *last_status = nullptr;  // device status word of the last call
     bool timing = false;             // record phase events (sw_phase_times)
     bool timed_cells_valid = false;
+    int64_t tb_split[2] = {0, 0};    // pairs per traceback kernel (16-bit, 32-bit) of the last call
     cudaEvent_t phase[4] = {nullptr, nullptr, nullptr, nullptr};
     std::mutex mu;
 };
@@ -275,16 +279,18 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
             return SW_ERR_CUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
         const TbClassInfo ti = *ds->tbinfo_host;
-        int tbps = 0;
-        if ((rc = traceback_kernel_occupancy(&tbps, kThreads))) return rc;
-        const int G = 32 / kTbLanes;
+        int tbps = 0, tbps16 = 0;
+        if ((rc = traceback_kernel_occupancy(&tbps, kThreads, false))) return rc;
+        if ((rc = traceback_kernel_occupancy(&tbps16, kThreads, true))) return rc;
+        const bool allow16 = g_tb_mode.load() == SW_TB_AUTO;
         const int64_t wpb = kThreads / 32;
         struct TbRun {
             int64_t start, count;
             int64_t slab_words, bnd_ints;  // per group, or per lane when tiled
             int32_t wcap;
-            bool tiled;
+            bool tiled, packed16;
             int blocks;
+            int64_t round_tasks;  // 16-bit kernel: tasks (64 pairs) per round
             int cls, part;
         };
         std::vector<TbRun> tbr;
@@ -302,44 +308,80 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
                 const int rc = kTbLanes * TB_ROWS;
                 const int64_t chunks = (r.max_m + rc - 1) / rc;
                 t.wcap = (int32_t)std::max<int64_t>(ti.max_wcap[part][r.cls], 1);
-                // lane-interleaved tiles when one lane owns a pair and a lane's
-                // tile (every chunk at the widest window) stays small
-                t.tiled = kTbLanes == 1 && chunks * t.wcap <= kTiledLaneWords;
-                if (t.tiled) {
+                // two pairs per lane in 16-bit halves where the class's score
+                // bound allows it and a lane's tile (every chunk at the widest
+                // window, two words per column) stays small; else lane-
+                // interleaved int32 tiles, or packed per-pair slabs
+                t.packed16 = allow16 && r.mode != MODE_I32 && kTbLanes == 1 && chunks * t.wcap * 2 <= kTiledLaneWords16;
+                t.tiled = !t.packed16 && kTbLanes == 1 && chunks * t.wcap <= kTiledLaneWords;
+                if (t.packed16) {
+                    t.slab_words = chunks * t.wcap * 2;
+                    t.bnd_ints = chunks > 1 ? (int64_t)2 * t.wcap : 0;  // one row, two pairs
+                } else if (t.tiled) {
                     t.slab_words = chunks * t.wcap;
                     t.bnd_ints = chunks > 1 ? (int64_t)2 * 2 * t.wcap : 0;
                 } else {
                     t.slab_words = part == 0 ? max_need : std::min<int64_t>(max_need, kSmallSlabWords);
                     t.bnd_ints = chunks > 1 ? (int64_t)2 * 2 * t.wcap : 0;
                 }
-                const size_t per_block = (size_t)wpb * 32 / kTbLanes * (t.slab_words + t.bnd_ints) * 4;
-                int64_t blocks = std::min<int64_t>(((cnt + G - 1) / G + wpb - 1) / wpb,
-                                                   (int64_t)std::max(tbps, 1) * ds->sm_count);
-                blocks = std::min<int64_t>(blocks, (int64_t)(kSlabBudget / std::max<size_t>(per_block, 1)));
-                t.blocks = (int)std::max<int64_t>(blocks, 1);
+                const int per_warp = t.packed16 ? 64 : 32 / kTbLanes;
+                if (t.packed16) {
+                    // a tile per task of 64 pairs, kept until the walk: tasks go
+                    // in rounds that fit the tile budget
+                    const size_t tile_bytes = (size_t)32 * t.slab_words * 4;
+                    const int64_t tasks = (cnt + 63) / 64;
+                    t.round_tasks = std::max<int64_t>(1, std::min<int64_t>(tasks, (int64_t)(kTile16Budget / tile_bytes)));
+                    const size_t bnd_per_block = (size_t)wpb * 32 * t.bnd_ints * 4;
+                    int64_t blocks = std::min<int64_t>((t.round_tasks + wpb - 1) / wpb,
+                                                       (int64_t)std::max(tbps16, 1) * ds->sm_count);
+                    t.blocks = (int)std::max<int64_t>(blocks, 1);
+                    need = std::max(need, tile_bytes * (size_t)t.round_tasks + bnd_per_block * (size_t)t.blocks);
+                } else {
+                    const size_t per_block = (size_t)wpb * 32 / kTbLanes * (t.slab_words + t.bnd_ints) * 4;
+                    int64_t blocks = std::min<int64_t>(((cnt + per_warp - 1) / per_warp + wpb - 1) / wpb,
+                                                       (int64_t)std::max(tbps, 1) * ds->sm_count);
+                    blocks = std::min<int64_t>(blocks, (int64_t)(kSlabBudget / std::max<size_t>(per_block, 1)));
+                    t.blocks = (int)std::max<int64_t>(blocks, 1);
+                    need = std::max(need, per_block * (size_t)t.blocks);
+                }
                 t.cls = r.cls;
                 t.part = part;
-                need = std::max(need, per_block * (size_t)t.blocks);
                 tbr.push_back(t);
             }
         }
         if ((rc = ensure(ds->dyn, std::max<size_t>(need, 256)))) return rc;
+        ds->tb_split[0] = ds->tb_split[1] = 0;
+        for (const TbRun &t : tbr) ds->tb_split[t.packed16 ? 0 : 1] += t.count;
         for (const TbRun &t : tbr) {
             TracebackLaunch B{};
             B.P = P;
-            B.order = tb_order + t.start;
-            B.n_items = t.count;
             B.lanes = kTbLanes;
             B.slab = (uint32_t *)ds->dyn.ptr;
             B.slab_group_words = t.slab_words;
-            const size_t slab_total = (size_t)t.blocks * wpb * (32 / kTbLanes) * t.slab_words;
-            B.boundary = (int32_t *)ds->dyn.ptr + slab_total;
             B.boundary_group_ints = t.bnd_ints;
             B.wcap = t.wcap;
             B.tiled = t.tiled;
+            B.packed16 = t.packed16;
             B.work_counter = counters + 2 * N_CLASS + 2 * t.cls + t.part;
             B.status = &info->status;
-            if ((rc = launch_traceback(B, t.blocks, kThreads, st))) return rc;
+            if (t.packed16) {
+                const int64_t round_items = t.round_tasks * 64;
+                const size_t tiles = (size_t)t.round_tasks * 32 * t.slab_words;
+                B.boundary = (int32_t *)ds->dyn.ptr + tiles;
+                for (int64_t r0 = 0; r0 < t.count; r0 += round_items) {
+                    B.order = tb_order + t.start + r0;
+                    B.n_items = std::min<int64_t>(round_items, t.count - r0);
+                    if (r0 > 0 && cudaMemsetAsync(B.work_counter, 0, sizeof(int32_t), st) != cudaSuccess)
+                        return SW_ERR_CUDA;
+                    if ((rc = launch_traceback(B, t.blocks, kThreads, st))) return rc;
+                }
+            } else {
+                B.order = tb_order + t.start;
+                B.n_items = t.count;
+                const size_t slab_total = (size_t)t.blocks * wpb * (32 / kTbLanes) * t.slab_words;
+                B.boundary = (int32_t *)ds->dyn.ptr + slab_total;
+                if ((rc = launch_traceback(B, t.blocks, kThreads, st))) return rc;
+            }
         }
     }
     if (ds->timing && cudaEventRecord(ds->phase[3], st) != cudaSuccess) return SW_ERR_CUDA;
@@ -524,11 +566,30 @@ int sw_set_plan(int32_t max_read_len, int32_t lanes, int32_t r_rows)
     return SW_OK;
 }
 
+int sw_set_traceback_mode(int32_t mode)
+{
+    if (mode != SW_TB_AUTO && mode != SW_TB_INT32) return SW_ERR_INVALID_ARG;
+    g_tb_mode.store(mode);
+    return SW_OK;
+}
+
 int sw_plan_rows(int32_t *rows, int32_t cap)
 {
     if (!rows) return N_SCORE_ROWS;
     for (int i = 0; i < N_SCORE_ROWS && i < cap; ++i) rows[i] = kScoreRows[i];
     return N_SCORE_ROWS;
+}
+
+int sw_last_traceback_split(int64_t *out2)
+{
+    if (!out2) return SW_ERR_INVALID_ARG;
+    DeviceState *ds = nullptr;
+    const int rc = device_state(&ds);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    out2[0] = ds->tb_split[0];
+    out2[1] = ds->tb_split[1];
+    return SW_OK;
 }
 
 int sw_phase_timing(int32_t enable)

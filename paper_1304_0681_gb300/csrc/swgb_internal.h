@@ -108,8 +108,10 @@ struct TracebackLaunch {
     int64_t boundary_group_ints;  // per group; tiled: per lane (2 x 2 x wcap)
     int32_t wcap;            // widest chunk window of the launch
     bool tiled;              // lane-interleaved warp tiles (one lane per pair)
+    bool packed16;           // 16x2 kernel: one lane per two pairs (tiled)
     int32_t *work_counter;
     int32_t *status;
+    int32_t one = 1;         // a multiplier the compiler cannot fold
 };
 
 // Row counts compiled for the score kernels.
@@ -128,7 +130,7 @@ int launch_tb_keys(const TbParams &P, const int32_t *order, int64_t n_items, con
 int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, int32_t *hist, int32_t *bucket_start,
                         int32_t *cursor, int32_t *order, cudaStream_t st);
 int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStream_t st);
-int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads);
+int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads, bool packed16);
 int launch_alu_probe(int kind, int64_t iters, int blocks, int threads, uint32_t *out, cudaStream_t st);
 
 int launch_features(const FeatureParams &P, cudaStream_t st);

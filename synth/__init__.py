@@ -232,6 +232,17 @@ class Workload:
                         np.zeros(len(pairs), np.int32))
 
 
+    def read_slice(self, lo: int, hi: int) -> "Workload":
+        """Reads lo .. hi with all of their candidate pairs (offsets rebased)."""
+        p0, p1 = int(self.cand_offsets[lo]), int(self.cand_offsets[hi])
+        r0, r1 = int(self.read_offsets[lo]), int(self.read_offsets[hi])
+        w0, w1 = int(self.window_offsets[p0]), int(self.window_offsets[p1])
+        return Workload(f"{self.name}[{lo}:{hi}]", self.reads[r0:r1].copy(), self.read_offsets[lo:hi + 1] - r0,
+                        self.windows[w0:w1].copy(), self.window_offsets[p0:p1 + 1] - w0,
+                        self.pair_read[p0:p1] - lo, self.cand_offsets[lo:hi + 1] - p0,
+                        self.kinds[p0:p1].copy(), self.true_cand[lo:hi].copy())
+
+
 def generate(name: str, seed: int = 0, n_reads: int | None = None, threads: int | None = None) -> Workload:
     """Generate a named workload deterministically (independent of threads)."""
     lib = _load()

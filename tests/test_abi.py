@@ -41,3 +41,14 @@ def test_packing_agrees_with_generator():
     from paper_1304_0681_gb300 import _swgb
     for n in (0, 1, 63, 64, 65, 1000, 4097):
         assert synth.packed_nbytes(n) == _swgb.sw_packed_bytes(n)
+
+
+def test_traceback_mode_setting_is_validated():
+    import pytest
+
+    from paper_1304_0681_gb300 import _swgb
+    _swgb.sw_set_traceback_mode(_swgb.SW_TB_INT32)
+    _swgb.sw_set_traceback_mode(_swgb.SW_TB_AUTO)
+    for bad in (-1, 2, 7):
+        with pytest.raises(_swgb.SwError):
+            _swgb.sw_set_traceback_mode(bad)

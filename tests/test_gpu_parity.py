@@ -16,12 +16,17 @@ WIDE16 = (50, -30, -60, -5)
 INT32 = (120, -60, -7, -3)
 
 
-@pytest.fixture(autouse=True)
-def _reset_plans():
+@pytest.fixture(autouse=True, params=["tb_auto", "tb_int32"])
+def _reset_plans(request):
+    """Every test runs twice: with the default traceback (16-bit halves, two
+    pairs per lane, wherever the score bound allows) and with 32-bit
+    arithmetic for every class."""
     import paper_1304_0681_gb300 as sw
     sw.sw_set_plan(0, 1, 8)
+    sw.sw_set_traceback_mode(sw.SW_TB_INT32 if request.param == "tb_int32" else sw.SW_TB_AUTO)
     yield
     sw.sw_set_plan(0, 1, 8)
+    sw.sw_set_traceback_mode(sw.SW_TB_AUTO)
 
 
 def test_parity_workload_full():
@@ -30,11 +35,28 @@ def test_parity_workload_full():
     assert_parity(wl, got, DEFAULT)
 
 
-@pytest.mark.parametrize("scoring", [WIDE16, (2, -3, -5, -2), (1, -1, -2, -1)])
+# mismatch < gap_open makes s - o negative for mismatches: the 16-bit
+# traceback then adds on the ALU pipe instead of with multiply-adds
+@pytest.mark.parametrize("scoring", [WIDE16, (2, -3, -5, -2), (1, -1, -2, -1), (5, -30, -3, -1), (2, -9, -4, -1)])
 def test_parity_workload_other_scorings(scoring):
     wl = synth.generate("parity", seed=1, n_reads=400)
     got = run_gpu(wl, scoring)
     assert_parity(wl, got, scoring)
+
+
+def test_traceback_kernel_split(request):
+    """The default mode sends every pair of the 100/150-bp workload through
+    the 16-bit traceback; the int32 mode sends none."""
+    import paper_1304_0681_gb300 as sw
+    wl = synth.generate("parity")
+    got = run_gpu(wl, DEFAULT)
+    s16, s32 = sw.sw_last_traceback_split()
+    assert s16 + s32 == wl.n_pairs
+    if request.node.callspec.params["_reset_plans"] == "tb_int32":
+        assert s16 == 0
+    else:
+        assert s16 == wl.n_pairs
+    assert_parity(wl, got, DEFAULT)
 
 
 def test_int32_path_long_reads():
@@ -185,11 +207,14 @@ def test_errors_are_reported():
     assert_parity(wl, got, DEFAULT)
 
 
-def test_throughput_full_size_sampled():
+def test_throughput_full_size_sampled(request):
     """The bench workload at full size (1M pairs), in the bench's launch
     configuration, checked on a sample of pairs."""
+    import paper_1304_0681_gb300 as sw
     wl = synth.generate("throughput")
     got = run_gpu(wl, DEFAULT)
+    if request.node.callspec.params["_reset_plans"] == "tb_auto":
+        assert sw.sw_last_traceback_split() == (wl.n_pairs, 0)
     rng = np.random.default_rng(3)
     pairs = np.sort(rng.choice(wl.n_pairs, 3000, replace=False))
     assert_parity(wl, got, DEFAULT, pairs=pairs)
