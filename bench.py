@@ -118,7 +118,8 @@ def _cpu_baseline(wl, budget_s: float) -> dict:
     import oracle
     cores = os.cpu_count() or 1
     rng = np.random.default_rng(12345)
-    probe = np.sort(rng.choice(wl.n_pairs, min(wl.n_pairs, 4 * cores), replace=False))
+    # a probe large enough that thread start-up does not dominate the rate
+    probe = np.sort(rng.choice(wl.n_pairs, min(wl.n_pairs, 256 * cores), replace=False))
     sub = wl.pair_slice(probe)
     t = time.perf_counter()
     oracle.align_batch(sub.reads, sub.read_offsets, sub.windows, sub.window_offsets,

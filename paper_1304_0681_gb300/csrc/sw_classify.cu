@@ -74,30 +74,44 @@ __global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring
     }
 }
 
-// Exclusive scan of the key histogram (one block).
-__global__ void k_scan(const int32_t *__restrict__ hist, int32_t *__restrict__ start, int32_t *__restrict__ cursor,
-                       int n)
+// Exclusive scan of the key histogram.  Keys are class-major (N_NBUCKET
+// buckets per class) and the per-class counts are known, so block c scans
+// class c's buckets after the counts of the classes before it; empty classes
+// return at once.
+__global__ void __launch_bounds__(N_NBUCKET) k_scan(const int32_t *__restrict__ hist,
+                                                    const int32_t *__restrict__ class_count,
+                                                    int32_t *__restrict__ start, int32_t *__restrict__ cursor)
 {
-    __shared__ int32_t part[1024];
-    const int t = threadIdx.x, nt = blockDim.x;
-    const int per = (n + nt - 1) / nt;
-    const int b = t * per, e = min(n, b + per);
-    int32_t s = 0;
-    for (int i = b; i < e; ++i) s += hist[i];
-    part[t] = s;
+    const int cls = blockIdx.x, t = threadIdx.x;
+    if (class_count[cls] == 0) return;
+    __shared__ int32_t part[N_NBUCKET / 32];
+    __shared__ int32_t base_s;
+    // classes before this one
+    int32_t pre = 0;
+    for (int c = t; c < cls; c += N_NBUCKET) pre += class_count[c];
+    pre = __reduce_add_sync(0xffffffffu, pre);
+    if ((t & 31) == 0) part[t >> 5] = pre;
     __syncthreads();
-    for (int d = 1; d < nt; d <<= 1) {
-        int32_t v = t >= d ? part[t - d] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    if (t == 0) {
+        int32_t b = 0;
+        for (int w = 0; w < N_NBUCKET / 32; ++w) b += part[w];
+        base_s = b;
     }
-    int32_t run = part[t] - s;
-    for (int i = b; i < e; ++i) {
-        start[i] = run;
-        cursor[i] = run;
-        run += hist[i];
+    __syncthreads();
+    // block scan of this class's buckets
+    const int32_t v = hist[cls * N_NBUCKET + t];
+    int32_t x = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if ((t & 31) >= d) x += y;
     }
+    if ((t & 31) == 31) part[t >> 5] = x;
+    __syncthreads();
+    int32_t wpre = base_s;
+    for (int w = 0; w < (t >> 5); ++w) wpre += part[w];
+    const int32_t s = wpre + x - v;
+    start[cls * N_NBUCKET + t] = s;
+    cursor[cls * N_NBUCKET + t] = s;
 }
 
 __global__ void k_scatter(const int32_t *__restrict__ keys, int64_t n_pairs, int32_t *__restrict__ cursor,
@@ -130,20 +144,20 @@ int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring
     if (blocks < 1) blocks = 1;
     k_classify<<<(unsigned)blocks, threads, 0, st>>>(ps, n_reads, n_pairs, sc, keys, hist, info, out_score,
                                                      out_end, cig_n);
-    k_scan<<<1, 1024, 0, st>>>(hist, bucket_start, cursor, N_CLASS * N_NBUCKET);
+    k_scan<<<N_CLASS, N_NBUCKET, 0, st>>>(hist, info->count, bucket_start, cursor);
     k_scatter<<<(unsigned)blocks, threads, 0, st>>>(keys, n_pairs, cursor, order);
     count_launch(3);
     return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
 }
 
-int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, int32_t *hist, int32_t *bucket_start,
-                        int32_t *cursor, int32_t *order, cudaStream_t st)
+int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, const int32_t *class_count, int32_t *hist,
+                        int32_t *bucket_start, int32_t *cursor, int32_t *order, cudaStream_t st)
 {
     const int threads = 256;
     int64_t blocks = (n_pairs + threads - 1) / threads;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_scan<<<1, 1024, 0, st>>>(hist, bucket_start, cursor, N_CLASS * N_NBUCKET);
+    k_scan<<<N_CLASS, N_NBUCKET, 0, st>>>(hist, class_count, bucket_start, cursor);
     k_scatter<<<(unsigned)blocks, threads, 0, st>>>(keys, n_pairs, cursor, order);
     count_launch(2);
     return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;

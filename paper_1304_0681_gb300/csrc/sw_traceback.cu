@@ -140,20 +140,22 @@ __device__ __forceinline__ int64_t slab_need(const TbPair &q, int T)
 }
 
 // Cost key per pair: class-major, most expensive first within a class.
-__global__ void k_tb_keys(TbParams P, const int32_t *__restrict__ order, int64_t n_items,
-                          const int32_t *__restrict__ score_keys, int32_t *__restrict__ tb_keys,
-                          int32_t *__restrict__ hist, TbClassInfo *__restrict__ info)
+// Pairs are visited in index order (coalesced reads of their offsets, score
+// and end cell); pairs the classification left out (key -1) get no key.
+__global__ void k_tb_keys(TbParams P, int64_t n_pairs, const int32_t *__restrict__ score_keys,
+                          int32_t *__restrict__ tb_keys, int32_t *__restrict__ hist, TbClassInfo *__restrict__ info)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; base < n_items;
+    for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; base < n_pairs;
          base += nwarps * 32) {
-        const int64_t q = base + lane;
+        const int64_t pp = base + lane;
+        const int32_t sk = pp < n_pairs ? score_keys[pp] : -1;
         int32_t key = -1, cls = 0, need32 = 0, wc = 0;
         bool big = false;
-        if (q < n_items) {
-            const int32_t p = order[q];
-            cls = score_keys[p] / N_NBUCKET;
+        if (sk >= 0) {
+            const int32_t p = (int32_t)pp;
+            cls = sk / N_NBUCKET;
             const int T = P.lanes;
             const TbPair t = tb_pair(P, p, nullptr);
             const int64_t need = slab_need(t, T);
@@ -166,10 +168,10 @@ __global__ void k_tb_keys(TbParams P, const int32_t *__restrict__ order, int64_t
                 const int cb = min(254, max(0, (int)(8.f * __log2f(cost))));
                 key = cls * N_NBUCKET + 1 + (254 - cb);
             }
-            tb_keys[p] = key;
             need32 = (int32_t)(need < (int64_t)INT32_MAX ? need : (int64_t)INT32_MAX);
             wc = need > 0 ? min(t.W, 8 * T + (t.b - t.a)) : 0;
         }
+        if (pp < n_pairs) tb_keys[pp] = key;
         // the key fixes the class and whether the slab is big
         const KeyGroup g = key_group(key);
         if (key >= 0) {
@@ -392,7 +394,8 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
                 rcg.push(4u, q.m - 1 - q.ie);  // trailing soft clip
                 int32_t i = q.ie, jj = q.W - 1;
                 int state = 0;
-                const int64_t limit = (int64_t)q.rows + q.W + 4;
+                // every step moves, or switches into a gap state before moving
+                const int64_t limit = 2 * ((int64_t)q.rows + q.W) + 4;
                 // words of chunk cc start after the windows of chunks 0..cc-1
                 int cc = i / rc, clo, chi;
                 int64_t cbase = 0;
@@ -466,9 +469,12 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
 // 16x2 traceback.  One lane owns two pairs, A in the low and B in the high
 // half of every register, so each DPX instruction recomputes two cells.  It
 // serves the classes whose score bound keeps every value below 32768
-// (match x min(m, n) <= 32000, match - o <= 127); the layout is the tiled one
-// above with two 32-bit words per lane and column (rows 0-3 and rows 4-7,
-// pair A in bits 0-15, pair B in bits 16-31).
+// (match x min(m, n) <= 32000, match - o <= 127).  A lane stores two 32-bit
+// words per window offset (rows 0-3 and rows 4-7; pair A in bits 0-15, pair
+// B in bits 16-31), and its words of four consecutive offsets share one
+// 32-byte sector: uint2 [((chunk x WCAP4 + t / 4) x 32 + lane) x 4 + t % 4].
+// The warp's stores fill each sector over four steps, and a walk moving
+// left along a chunk reads one sector per four offsets.
 //
 // Per cell four bits record which equalities fail (1 = not equal):
 //   bit 0  H != H(i-1,j-1) + s    bit 1  H != E
@@ -579,7 +585,8 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
     const uint32_t m1 = 0u - one, two = one + one, four = two + two, eight = four + four;
     const uint32_t mul1 = eight + eight, mul2 = mul1 * mul1, mul3 = mul2 * mul1;  // 16, 256, 4096
     const uint32_t ONES = 0x00010001u;
-    const int64_t lane_chunks = L.slab_group_words / (2 * (int64_t)max(WCAP, 1));
+    const int WCAP4 = (WCAP + 3) >> 2;  // groups of four offsets per chunk
+    const int64_t lane_chunks = L.slab_group_words / (8 * (int64_t)max(WCAP4, 1));
 
     for (;;) {
         int base = 0;
@@ -704,8 +711,9 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
                     E[r] = e;
                     hu = h;
                 }
-                // streaming store: the walk reads back a few words of it
-                __stcs(slab + ((int64_t)c * WCAP + t) * 32 + lane, make_uint2(w0, w1));
+                // streaming store (the walk reads back a few words of it); a
+                // lane's four consecutive offsets share one 32-byte sector
+                __stcs(slab + ((((int64_t)c * WCAP4 + (t >> 2)) * 32 + lane) << 2) + (t & 3), make_uint2(w0, w1));
                 if (bout)
                     *(uint2 *)(bout + ((int64_t)t * 32 + lane) * 2) = make_uint2(prmt(hu, f, 0x5410u), prmt(hu, f, 0x7632u));
                 diag_in = up_h;
@@ -720,19 +728,78 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
     }
 }
 
+// Collects a CIGAR as the walk emits it (its last run first) and writes it
+// forward into the pair's slot.  The first LB runs emitted -- the whole CIGAR
+// in the common case -- stay in a per-thread buffer and are stored at the
+// end; runs past those are parked at the end of the slot and moved down in
+// batches of loads before stores.  No run is read back from global memory
+// unless the CIGAR has more than LB runs.
+struct FwdCigar {
+    static constexpr int LB = 16;
+    uint32_t *out;
+    int64_t cap;
+    int32_t n;
+    uint32_t op;
+    int32_t len;
+    bool overflow;
+    uint32_t buf[LB];
+    __device__ void push(uint32_t o, int32_t l)
+    {
+        if (l <= 0) return;
+        if (len > 0 && o == op) {
+            len += l;
+            return;
+        }
+        flush();
+        op = o;
+        len = l;
+    }
+    __device__ void flush()
+    {
+        if (len > 0) {
+            const uint32_t run = ((uint32_t)len << 4) | op;
+            if (n >= cap) overflow = true;
+            else if (n < LB) buf[n] = run;
+            else out[cap - 1 - (n - LB)] = run;
+            ++n;
+        }
+        len = 0;
+    }
+    // run e (in emission order) goes to position n - 1 - e
+    __device__ void finish()
+    {
+        if (overflow) return;
+        const int32_t parked = n - LB;
+        if (parked > 0) {
+            const int64_t src = cap - n + LB;  // > 0: every source lies above its target
+            for (int32_t k = 0; k < parked; k += 4) {
+                uint32_t v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (k + u < parked) v[u] = out[src + k + u];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (k + u < parked) out[k + u] = v[u];
+            }
+        }
+        const int32_t nb = n < LB ? n : LB;
+        for (int32_t e = 0; e < nb; ++e) out[n - 1 - e] = buf[e];
+    }
+};
+
 // One thread per pair: walk back from the end cell through the tile that
 // k_traceback16 wrote (item k of the launch: task k / 64, lane (k % 64) / 2,
 // half k % 2), carrying the exact value of the current state (the tile does
-// not record where H is 0).  The thread keeps the tile word it used last and
-// the word one column to its left (the next word of a diagonal or deletion
-// step within the chunk, loaded one step early), and the 16-base words of
-// read and window that hold its current row and column.
+// not record where H is 0).  The thread keeps the sector of four offsets it
+// read last, and the 16-base words of read and window that hold its current
+// row and column.
 __global__ void __launch_bounds__(256) k_tb16_walk(const TracebackLaunch L)
 {
     const TbParams &P = L.P;
     const int WCAP = L.wcap, rc = TB_ROWS;
+    const int WCAP4 = (WCAP + 3) >> 2;
     const int32_t go = P.sc.go, ge = P.sc.ge;
-    const int64_t lane_chunks = L.slab_group_words / (2 * (int64_t)max(WCAP, 1));
+    const int64_t lane_chunks = L.slab_group_words / (8 * (int64_t)max(WCAP4, 1));
     for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < L.n_items;
          item += (int64_t)gridDim.x * blockDim.x) {
         const int32_t p = L.order[item];
@@ -740,21 +807,27 @@ __global__ void __launch_bounds__(256) k_tb16_walk(const TracebackLaunch L)
         // the sweep skipped (and reported) pairs that overrun the tile
         if ((qq.rows + rc - 1) / rc > lane_chunks || min(qq.W, rc + (qq.b - qq.a)) > WCAP) qq.score = 0;
         const int64_t off = P.cig_off[p];
-        RevCigar rcg{P.cig_ops + off, P.cig_off[p + 1] - off, 0, 0u, 0, false};
         if (qq.score <= 0) {
             P.cig_n[p] = 0;
             continue;
         }
+        FwdCigar cg;
+        cg.out = P.cig_ops + off;
+        cg.cap = P.cig_off[p + 1] - off;
+        cg.n = 0;
+        cg.op = 0u;
+        cg.len = 0;
+        cg.overflow = false;
         const uint2 *tile = (const uint2 *)L.slab + (item / 64) * 32 * (L.slab_group_words / 2);
         const int lane = (int)((item & 63) >> 1), hs = 16 * (int)(item & 1);
-        rcg.push(4u, qq.m - 1 - qq.ie);  // trailing soft clip
+        cg.push(4u, qq.m - 1 - qq.ie);  // trailing soft clip
         int32_t i = qq.ie, jj = qq.W - 1;
         int32_t v = qq.score;  // value of the current state at (i, jj)
         int state = 0;
         int cc = i / rc, clo, chi;
         chunk_window(qq, cc, rc, clo, chi);
-        int64_t key = -1, pkey = -1, rkey = -1, wkey = -1;
-        uint2 w = make_uint2(0u, 0u), pw = w;
+        int64_t gkey = -1, rkey = -1, wkey = -1;
+        uint4 ga = make_uint4(0u, 0u, 0u, 0u), gb = ga;
         uint32_t rw = 0u, ww = 0u;
         bool ok = false;
         // every step moves, or switches into a gap state before moving
@@ -770,17 +843,19 @@ __global__ void __launch_bounds__(256) k_tb16_walk(const TracebackLaunch L)
                 chunk_window(qq, cc, rc, clo, chi);
             }
             if (jj < clo || jj > chi) break;  // left the band: inconsistent
-            const int64_t k = (int64_t)cc * WCAP + (jj - clo);
-            if (k != key) {
-                w = k == pkey ? pw : tile[k * 32 + lane];
-                key = k;
-                if (jj - 1 >= clo) {
-                    pkey = k - 1;
-                    pw = tile[(k - 1) * 32 + lane];
-                }
+            const int oc = jj - clo;
+            const int64_t g = (int64_t)cc * WCAP4 + (oc >> 2);
+            if (g != gkey) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(tile + ((g * 32 + lane) << 2));
+                ga = __ldg(src);
+                gb = __ldg(src + 1);
+                gkey = g;
             }
+            const int sl = oc & 3;
+            const uint32_t wlo = sl == 0 ? ga.x : sl == 1 ? ga.z : sl == 2 ? gb.x : gb.z;
+            const uint32_t whi = sl == 0 ? ga.y : sl == 1 ? ga.w : sl == 2 ? gb.y : gb.w;
             const int r = i - cc * rc;
-            const uint32_t code = ((r < 4 ? w.x : w.y) >> (hs + 4 * (r & 3))) & 0xFu;
+            const uint32_t code = ((r < 4 ? wlo : whi) >> (hs + 4 * (r & 3))) & 0xFu;
             if (state == 0) {
                 if (!(code & 1u)) {
                     // diagonal: H(i-1, j-1) = H(i, j) - s(r_i, w_j)
@@ -796,14 +871,14 @@ __global__ void __launch_bounds__(256) k_tb16_walk(const TracebackLaunch L)
                     const uint32_t ri = (rw >> (2 * (rpos & 15))) & 3u;
                     const uint32_t wj = (ww >> (2 * (wpos & 15))) & 3u;
                     v -= ri == wj ? P.sc.ma : P.sc.mi;
-                    rcg.push(0u, 1);
+                    cg.push(0u, 1);
                     --i;
                     --jj;
                 } else {
                     state = (code & 2u) ? 2 : 1;
                 }
             } else if (state == 1) {
-                rcg.push(2u, 1);
+                cg.push(2u, 1);
                 if (!(code & 4u)) {
                     v -= go;  // E(i,j) = H(i,j-1) + o
                     state = 0;
@@ -812,7 +887,7 @@ __global__ void __launch_bounds__(256) k_tb16_walk(const TracebackLaunch L)
                 }
                 --jj;
             } else {
-                rcg.push(1u, 1);
+                cg.push(1u, 1);
                 if (!(code & 8u)) {
                     v -= go;  // F(i,j) = H(i-1,j) + o
                     state = 0;
@@ -823,31 +898,26 @@ __global__ void __launch_bounds__(256) k_tb16_walk(const TracebackLaunch L)
             }
         }
         if (!ok) atomicOr(L.status, ST_INTERNAL);
-        rcg.push(4u, i + 1);  // leading soft clip
-        rcg.flush();
-        if (rcg.overflow) {
+        cg.push(4u, i + 1);  // leading soft clip
+        cg.flush();
+        if (cg.overflow) {
             P.cig_n[p] = -1;
             atomicOr(L.status, ST_CAPACITY);
         } else {
-            uint32_t *o = rcg.out;
-            for (int32_t a2 = 0, b2 = rcg.n - 1; a2 < b2; ++a2, --b2) {
-                const uint32_t tmp = o[a2];
-                o[a2] = o[b2];
-                o[b2] = tmp;
-            }
-            P.cig_n[p] = rcg.n;
+            cg.finish();
+            P.cig_n[p] = cg.n;
         }
     }
 }
 
-int launch_tb_keys(const TbParams &P, const int32_t *order, int64_t n_items, const int32_t *score_keys,
-                   int32_t *tb_keys, int32_t *hist, TbClassInfo *info, cudaStream_t st)
+int launch_tb_keys(const TbParams &P, int64_t n_pairs, const int32_t *score_keys, int32_t *tb_keys, int32_t *hist,
+                   TbClassInfo *info, cudaStream_t st)
 {
     const int threads = 256;
-    int64_t blocks = (n_items + threads - 1) / threads;
+    int64_t blocks = (n_pairs + threads - 1) / threads;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_tb_keys<<<(unsigned)blocks, threads, 0, st>>>(P, order, n_items, score_keys, tb_keys, hist, info);
+    k_tb_keys<<<(unsigned)blocks, threads, 0, st>>>(P, n_pairs, score_keys, tb_keys, hist, info);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
 }

@@ -267,13 +267,11 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
     if (cig) {
         // order each class by traceback cost, then size the slabs from the
         // per-class maxima (a second, small read-back)
-        const int64_t n_items = pos;
         TbParams P{ps, sc, out_score, out_end, cig->ops, cig->offsets, cig->n_ops, kTbLanes, kSmallSlabWords};
         if (cudaMemsetAsync(hist, 0, sizeof(int32_t) * nh, st) != cudaSuccess) return SW_ERR_CUDA;
         if (cudaMemsetAsync(tbinfo, 0, sizeof(TbClassInfo), st) != cudaSuccess) return SW_ERR_CUDA;
-        if (cudaMemsetAsync(tb_keys, 0xFF, sizeof(int32_t) * n_pairs, st) != cudaSuccess) return SW_ERR_CUDA;
-        if ((rc = launch_tb_keys(P, order, n_items, keys, tb_keys, hist, tbinfo, st))) return rc;
-        if ((rc = launch_scan_scatter(tb_keys, n_pairs, hist, bstart, cursor, tb_order, st))) return rc;
+        if ((rc = launch_tb_keys(P, n_pairs, keys, tb_keys, hist, tbinfo, st))) return rc;
+        if ((rc = launch_scan_scatter(tb_keys, n_pairs, info->count, hist, bstart, cursor, tb_order, st))) return rc;
         if (cudaMemcpyAsync(ds->tbinfo_host, tbinfo, sizeof(TbClassInfo), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess)
             return SW_ERR_CUDA;
@@ -291,6 +289,7 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
             bool tiled, packed16;
             int blocks;
             int64_t round_tasks;  // 16-bit kernel: tasks (64 pairs) per round
+            int lanes;            // int32 kernels: lanes per pair
             int cls, part;
         };
         std::vector<TbRun> tbr;
@@ -312,19 +311,32 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
                 // bound allows it and a lane's tile (every chunk at the widest
                 // window, two words per column) stays small; else lane-
                 // interleaved int32 tiles, or packed per-pair slabs
-                t.packed16 = allow16 && r.mode != MODE_I32 && kTbLanes == 1 && chunks * t.wcap * 2 <= kTiledLaneWords16;
+                const int64_t wcap4 = (t.wcap + 3) / 4 * 4;  // the 16-bit tiles group offsets by four
+                t.packed16 = allow16 && r.mode != MODE_I32 && kTbLanes == 1 && chunks * wcap4 * 2 <= kTiledLaneWords16;
                 t.tiled = !t.packed16 && kTbLanes == 1 && chunks * t.wcap <= kTiledLaneWords;
+                t.lanes = kTbLanes;
                 if (t.packed16) {
-                    t.slab_words = chunks * t.wcap * 2;
+                    t.slab_words = chunks * wcap4 * 2;
                     t.bnd_ints = chunks > 1 ? (int64_t)2 * t.wcap : 0;  // one row, two pairs
                 } else if (t.tiled) {
                     t.slab_words = chunks * t.wcap;
                     t.bnd_ints = chunks > 1 ? (int64_t)2 * 2 * t.wcap : 0;
                 } else {
-                    t.slab_words = part == 0 ? max_need : std::min<int64_t>(max_need, kSmallSlabWords);
-                    t.bnd_ints = chunks > 1 ? (int64_t)2 * 2 * t.wcap : 0;
+                    // long reads or wide windows: T lanes share a pair (a power
+                    // of two covering the longest read in about four chunks),
+                    // so one pair's cells do not run on a single lane.  A
+                    // T-lane chunk window is at most 8 (T - 1) wider than the
+                    // one-lane windows the key pass measured.
+                    int T = 1;
+                    while (T < 32 && (int64_t)T * 32 < r.max_m) T *= 2;
+                    t.lanes = T;
+                    const int64_t chunks_t = (r.max_m + 8 * T - 1) / (8 * T);
+                    const int64_t wcap_t = t.wcap + 8 * (T - 1);
+                    t.slab_words = T == 1 ? (part == 0 ? max_need : std::min<int64_t>(max_need, kSmallSlabWords))
+                                          : chunks_t * wcap_t * T;
+                    t.bnd_ints = chunks_t > 1 ? (int64_t)2 * 2 * wcap_t : 0;
                 }
-                const int per_warp = t.packed16 ? 64 : 32 / kTbLanes;
+                const int per_warp = t.packed16 ? 64 : 32 / t.lanes;
                 if (t.packed16) {
                     // a tile per task of 64 pairs, kept until the walk: tasks go
                     // in rounds that fit the tile budget
@@ -337,7 +349,7 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
                     t.blocks = (int)std::max<int64_t>(blocks, 1);
                     need = std::max(need, tile_bytes * (size_t)t.round_tasks + bnd_per_block * (size_t)t.blocks);
                 } else {
-                    const size_t per_block = (size_t)wpb * 32 / kTbLanes * (t.slab_words + t.bnd_ints) * 4;
+                    const size_t per_block = (size_t)wpb * (32 / t.lanes) * (t.slab_words + t.bnd_ints) * 4;
                     int64_t blocks = std::min<int64_t>(((cnt + per_warp - 1) / per_warp + wpb - 1) / wpb,
                                                        (int64_t)std::max(tbps, 1) * ds->sm_count);
                     blocks = std::min<int64_t>(blocks, (int64_t)(kSlabBudget / std::max<size_t>(per_block, 1)));
@@ -355,7 +367,8 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         for (const TbRun &t : tbr) {
             TracebackLaunch B{};
             B.P = P;
-            B.lanes = kTbLanes;
+            B.P.lanes = t.lanes;
+            B.lanes = t.lanes;
             B.slab = (uint32_t *)ds->dyn.ptr;
             B.slab_group_words = t.slab_words;
             B.boundary_group_ints = t.bnd_ints;
@@ -378,7 +391,7 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
             } else {
                 B.order = tb_order + t.start;
                 B.n_items = t.count;
-                const size_t slab_total = (size_t)t.blocks * wpb * (32 / kTbLanes) * t.slab_words;
+                const size_t slab_total = (size_t)t.blocks * wpb * (32 / t.lanes) * t.slab_words;
                 B.boundary = (int32_t *)ds->dyn.ptr + slab_total;
                 if ((rc = launch_traceback(B, t.blocks, kThreads, st))) return rc;
             }

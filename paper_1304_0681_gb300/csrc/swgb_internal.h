@@ -125,10 +125,10 @@ int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring
                     int32_t *cig_n, cudaStream_t st);
 int launch_score(int rows, int mode, const ScoreLaunch &L, int blocks, int threads, cudaStream_t st);
 int score_kernel_regs(int rows, int mode, int *regs, int *max_blocks_per_sm, int threads);
-int launch_tb_keys(const TbParams &P, const int32_t *order, int64_t n_items, const int32_t *score_keys,
-                   int32_t *tb_keys, int32_t *hist, TbClassInfo *info, cudaStream_t st);
-int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, int32_t *hist, int32_t *bucket_start,
-                        int32_t *cursor, int32_t *order, cudaStream_t st);
+int launch_tb_keys(const TbParams &P, int64_t n_pairs, const int32_t *score_keys, int32_t *tb_keys, int32_t *hist,
+                   TbClassInfo *info, cudaStream_t st);
+int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, const int32_t *class_count, int32_t *hist,
+                        int32_t *bucket_start, int32_t *cursor, int32_t *order, cudaStream_t st);
 int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStream_t st);
 int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads, bool packed16);
 int launch_alu_probe(int kind, int64_t iters, int blocks, int threads, uint32_t *out, cudaStream_t st);

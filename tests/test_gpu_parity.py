@@ -142,10 +142,15 @@ def test_multichunk_long_reads():
 
 
 def test_uneven_sample():
+    """Uneven lengths: a random sample plus every long read and every wide
+    (spliced) window, which take the several-lanes-per-pair traceback."""
     wl = synth.generate("uneven", seed=2, n_reads=3000)
     got = run_gpu(wl, DEFAULT)
     rng = np.random.default_rng(1)
-    assert_parity(wl, got, DEFAULT, pairs=np.sort(rng.choice(wl.n_pairs, 600, replace=False)))
+    long_or_wide = np.nonzero((wl.pair_read_lengths >= 250) | (wl.window_lengths >= 1000))[0]
+    assert len(long_or_wide) > 100
+    pairs = np.union1d(rng.choice(wl.n_pairs, 600, replace=False), long_or_wide)
+    assert_parity(wl, got, DEFAULT, pairs=pairs)
 
 
 def test_indexed_candidates():
