@@ -55,6 +55,8 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-filter", action="store_true", help="skip the learned-filter comparison")
     ap.add_argument("--filter-reads", type=int, default=500_000)
+    ap.add_argument("--pairs", type=int, default=None,
+                    help="smaller case of the workload (profiling); default: the full workload")
     return ap.parse_args()
 
 
@@ -304,7 +306,7 @@ def main():
     from paper_1304_0681_gb300.shard import reduce_run
 
     want_cigar = not args.no_cigar
-    wl = synth.generate(args.workload, seed=rank)
+    wl = synth.generate(args.workload, seed=rank, n_reads=args.pairs)
     batch = DeviceBatch.from_packed(wl.packed_reads(), wl.read_offsets, wl.packed_windows(), wl.window_offsets,
                                     cigar=want_cigar)
     cells, n_reads = wl.cells(), wl.n_reads
