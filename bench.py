@@ -55,6 +55,8 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-filter", action="store_true", help="skip the learned-filter comparison")
     ap.add_argument("--filter-reads", type=int, default=500_000)
+    ap.add_argument("--fullmix-reads", type=int, default=150_000, help="reads of the full-mix sample")
+    ap.add_argument("--no-extra", action="store_true", help="skip the uneven and full-mix sections")
     ap.add_argument("--pairs", type=int, default=None,
                     help="smaller case of the workload (profiling); default: the full workload")
     return ap.parse_args()
@@ -134,10 +136,19 @@ def _cpu_baseline(wl, budget_s: float) -> dict:
     oracle.align_batch(sub.reads, sub.read_offsets, sub.windows, sub.window_offsets,
                        scoring=oracle.Scoring(*SCORING), threads=cores)
     dt = time.perf_counter() - t
+    # one core: a smaller sample of the same batch
+    n1 = max(1, min(n, int(n / cores / 2)))
+    sub1 = wl.pair_slice(pairs[:n1])
+    t = time.perf_counter()
+    oracle.align_batch(sub1.reads, sub1.read_offsets, sub1.windows, sub1.window_offsets,
+                       scoring=oracle.Scoring(*SCORING), threads=1)
+    dt1 = time.perf_counter() - t
     return {"value": sub.cells() / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
             "sample": f"{n} of {wl.n_pairs} pairs drawn uniformly (seed 12345), score + end + CIGAR, "
                       f"{sub.cells():.3e} cells in {dt:.1f} s",
-            "reads_per_s": n / dt}
+            "reads_per_s": n / dt,
+            "one_core": {"value": sub1.cells() / dt1 / 1e9, "unit": "GCUPS", "cores": 1,
+                         "sample": f"the first {n1} pairs of that sample, {sub1.cells():.3e} cells in {dt1:.1f} s"}}
 
 
 def _traffic_record(kernel_file: str):
@@ -153,11 +164,20 @@ def _traffic_record(kernel_file: str):
     return rec
 
 
-def _filter_section(args, rank, steps: int) -> dict:
-    """Plain vs learned-filtered best-hit search on the candidate workload:
-    500k reads of 150 bp, U{1..64} candidate windows of 250 bp (one true at
-    1-3% divergence, paralog decoys at 5-20% or random).  The network is
-    trained on SW scores of ~5M pairs from another seed, and (k, tau) are
+FILTER_WORKLOADS = {
+    "filter": "learned filter: 500k reads 150 bp, U{1..64} candidates of 250 bp, 16.25M pairs; "
+              "best hit per read, score + end",
+    "fullmix": "full mix (sample): reads 75-800 bp as the uneven workload, U{1..32} candidates, 15% spliced, "
+               "true hit at 1-5% divergence; best hit per read, score + end",
+}
+
+
+def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int = 500_000,
+                    n_train: int = 150_000, n_cal: int = 40_000, epochs: int = 4) -> dict:
+    """Plain vs learned-filtered best-hit search on a candidate workload
+    (default: 500k reads of 150 bp, U{1..64} candidate windows of 250 bp, one
+    true at 1-3% divergence, paralog decoys at 5-20% or random).  The network
+    is trained on SW scores of pairs from another seed, and (k, tau) are
     picked on a held-out seed for >= 99.6% best-hit recall; neither is timed.
     A step is one whole search over the batch (score and end, no CIGAR)."""
     import numpy as np
@@ -175,16 +195,16 @@ def _filter_section(args, rank, steps: int) -> dict:
 
     # training set: SW scores from the method itself are the targets
     t0 = time.perf_counter()
-    wl_tr, b_tr, co_tr = load("filter", 1000 + rank, 150_000)
+    wl_tr, b_tr, co_tr = load(name, 1000 + rank, n_train)
     flt.exhaustive_best(b_tr, co_tr, SCORING)
     feats_tr = flt.features(b_tr, co_tr)
     tgt = flt.targets(b_tr.score, torch.from_numpy(wl_tr.pair_read_lengths).cuda(), SCORING[0])
     model = flt.FilterModel(seed=1)
-    losses = model.train(feats_tr, tgt, epochs=4, batch=8192, lr=2e-3)
-    n_train = wl_tr.n_pairs
+    losses = model.train(feats_tr, tgt, epochs=epochs, batch=8192, lr=2e-3)
+    n_train_pairs = wl_tr.n_pairs
     del b_tr, feats_tr, tgt
     # calibration on a held-out seed
-    wl_cal, b_cal, co_cal = load("filter", 2000 + rank, 40_000)
+    wl_cal, b_cal, co_cal = load(name, 2000 + rank, n_cal)
     flt.exhaustive_best(b_cal, co_cal, SCORING)
     pred_cal = model.forward(flt.features(b_cal, co_cal)).cpu().numpy()
     cal = flt.calibrate(pred_cal, b_cal.score.cpu().numpy().astype(np.int64), wl_cal.cand_offsets, 0.996)
@@ -192,7 +212,7 @@ def _filter_section(args, rank, steps: int) -> dict:
     del b_cal
     setup_s = time.perf_counter() - t0
 
-    wl, b, co = load("filter", rank, args.filter_reads)
+    wl, b, co = load(name, rank, n_reads)
     cells = wl.cells()
     stream = torch.cuda.current_stream()
 
@@ -227,8 +247,7 @@ def _filter_section(args, rank, steps: int) -> dict:
     e2.record(stream)
     e2.synchronize()
     recall = float(np.mean(best_filt == best_plain))
-    return {"workload": "learned filter: 500k reads 150 bp, U{1..64} candidates of 250 bp, 16.25M pairs; "
-                        "best hit per read, score + end",
+    return {"workload": FILTER_WORKLOADS[name],
             "reads": wl.n_reads, "pairs": wl.n_pairs, "cells_exhaustive": cells,
             "plain": {"ms_per_step": ms_plain, "reads_per_s": wl.n_reads / (ms_plain * 1e-3),
                       "gcups": cells / (ms_plain * 1e-3) / 1e9},
@@ -238,8 +257,48 @@ def _filter_section(args, rank, steps: int) -> dict:
                          "gcups_aligned": sel_cells / (ms_filt * 1e-3) / 1e9},
             "speedup_reads_per_s": ms_plain / ms_filt, "best_hit_recall": recall, "k": k, "tau": tau,
             "calibration_recall": cal[3] if cal else None,
-            "training": {"pairs": n_train, "epochs": 4, "loss_per_epoch": losses, "setup_s": setup_s},
+            "training": {"pairs": n_train_pairs, "epochs": epochs, "loss_per_epoch": losses, "setup_s": setup_s},
             "steps": steps}
+
+
+def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
+    """The batched uneven workload (2M pairs, reads 75-800 bp, 10% spliced),
+    score + end + CIGAR in one call per step, L2 flushed between steps."""
+    import torch
+
+    import paper_1304_0681_gb300 as sw
+    import synth
+    from paper_1304_0681_gb300 import DeviceBatch, align
+
+    wl = synth.generate("uneven", seed=rank)
+    b = DeviceBatch.from_packed(wl.packed_reads(), wl.read_offsets, wl.packed_windows(), wl.window_offsets,
+                                cigar=True)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        align(b, SCORING, cigar=True)
+    torch.cuda.synchronize()
+    sw.sw_phase_timing(True)
+    ms, phases = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        align(b, SCORING, cigar=True, sync=False)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        phases.append(sw.sw_phase_times())
+    sw.sw_sync_status()
+    sw.sw_phase_timing(False)
+    cells = wl.cells()
+    t = sum(ms) / len(ms)
+    score_ms = statistics.mean(p[1] for p in phases)
+    return {"workload": WORKLOADS["uneven"], "pairs": wl.n_pairs, "cells": cells, "steps": steps,
+            "ms_per_step": t, "gcups": cells / (t * 1e-3) / 1e9, "reads_per_s": wl.n_reads / (t * 1e-3),
+            "phase_ms": {"classify": statistics.mean(p[0] for p in phases), "score": score_ms,
+                         "traceback": statistics.mean(p[2] for p in phases)},
+            "score_roofline_frac": cells / (score_ms * 1e-3) / 1e9 / peak_gcups}
 
 
 def run_reference(args, ws, rank):
@@ -355,7 +414,10 @@ def main():
     tb_ms = statistics.mean(p[2] for p in phases)
     cls_ms = statistics.mean(p[0] for p in phases)
     achieved = cells / (score_ms * 1e-3) / 1e9
-    traffic = _traffic_record(os.path.join(ROOT, "paper_1304_0681_gb300", "csrc", "sw_score.cu"))
+    # the recorded DRAM traffic is for the full throughput batch only
+    traffic = (_traffic_record(os.path.join(ROOT, "paper_1304_0681_gb300", "csrc", "sw_score.cu"))
+               if args.workload == "throughput" and args.pairs is None else None)
+    in_mb = (len(wl.packed_reads()) + len(wl.packed_windows())) / 1e6
 
     # end to end through the host entry point: pinned inputs in, results out
     e2e = None
@@ -392,7 +454,15 @@ def main():
 
     filt = None
     if not args.no_filter:
-        filt = _filter_section(args, rank, steps=max(2, min(args.steps, 5)))
+        filt = _filter_section(args, rank, steps=max(2, min(args.steps, 5)), n_reads=args.filter_reads)
+    uneven = fullmix = None
+    if not args.no_extra and args.workload == "throughput":
+        del batch
+        torch.cuda.empty_cache()
+        uneven = _uneven_section(args, rank, steps=max(2, min(args.steps, 3)), peak_gcups=peak_gcups)
+        if not args.no_filter:
+            fullmix = _filter_section(args, rank, steps=max(2, min(args.steps, 3)), name="fullmix",
+                                      n_reads=args.fullmix_reads, n_train=40_000, n_cal=15_000, epochs=8)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
@@ -400,7 +470,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "i16x2+i32", "data": "synthetic",
                 "config": {"workload": WORKLOADS[args.workload], "pairs_per_gpu": wl.n_pairs,
                            "cells_per_gpu": cells, "cigar": want_cigar, "scoring": list(SCORING),
-                           "l2": "256 MB buffer written between timed steps (inputs 75 MB < L2)"},
+                           "l2": f"256 MB buffer written between timed steps (packed inputs {in_mb:.0f} MB)"},
                 "reads_per_s": reads_per_s,
                 "phase_ms": {"classify": cls_ms, "score": score_ms, "traceback": tb_ms},
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gcups, "unit": "GCUPS",
@@ -409,7 +479,8 @@ def main():
                              "kernel": "k_score (score + end-cell pass)",
                              "peak_basis": f"measured 16x2 DPX add-max rate {dpx_ops / 1e12:.2f} Tops/s "
                                            f"x 2 cells / {OPS_PER_CELL:g} ops per cell"},
-                "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "learned_filter": filt}
+                "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "learned_filter": filt,
+                "uneven": uneven, "fullmix_sample": fullmix}
         if rank == 0 and not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
         print(json.dumps(line), flush=True)
