@@ -160,13 +160,15 @@ __global__ void k_tb_keys(TbParams P, int64_t n_pairs, const int32_t *__restrict
             const TbPair t = tb_pair(P, p, nullptr);
             const int64_t need = slab_need(t, T);
             big = need > P.small_slab_words;
-            // big slabs first, then by falling cost (~9% buckets of rows x window)
+            // big slabs first, each group by falling cost (rows x window, in
+            // ~19% and ~9% buckets) so that the longest tasks start first
+            const float cost = t.score > 0 ? (float)t.rows * (float)min(t.W, 8 * T + (t.b - t.a)) : 1.f;
             if (big) {
-                key = cls * N_NBUCKET;
+                const int cb = min(63, max(0, (int)(4.f * __log2f(cost)) - 40));
+                key = cls * N_NBUCKET + (63 - cb);
             } else {
-                const float cost = t.score > 0 ? (float)t.rows * (float)min(t.W, 8 * T + (t.b - t.a)) : 1.f;
-                const int cb = min(254, max(0, (int)(8.f * __log2f(cost))));
-                key = cls * N_NBUCKET + 1 + (254 - cb);
+                const int cb = min(191, max(0, (int)(8.f * __log2f(cost))));
+                key = cls * N_NBUCKET + 64 + (191 - cb);
             }
             need32 = (int32_t)(need < (int64_t)INT32_MAX ? need : (int64_t)INT32_MAX);
             wc = need > 0 ? min(t.W, 8 * T + (t.b - t.a)) : 0;
@@ -561,9 +563,21 @@ __device__ __forceinline__ uint32_t sel16(uint32_t xa, uint32_t xb)
     return a | (b << 8);
 }
 
-template <bool FMA_ADD>
+// Tile geometry of a 16-bit traceback launch: T lanes per group (two pairs),
+// G = 32 / T groups and 2G pairs per task.  Word (chunk c, step t, lane)
+// of a task's tile: uint2 [((c * S4 + t / 4) * 32 + lane) * 4 + t % 4],
+// S4 = ceil((WCAP + T - 1) / 4) groups of four steps per chunk; lane k of a
+// group computes window offset t - k at step t.
+__device__ __forceinline__ int64_t tb16_word(int c, int t, int lane, int S4)
+{
+    return ((((int64_t)c * S4 + (t >> 2)) * 32 + lane) << 2) + (t & 3);
+}
+
+template <int T, bool FMA_ADD>
 __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
 {
+    constexpr int G = 32 / T;       // groups per warp, two pairs each
+    constexpr int PAIRS = 2 * G;    // pairs per task
     const TbParams &P = L.P;
     // s_tab[w] byte x = s(x, w) - o; s_tab[4] = 0 (s = o, past a window end)
     __shared__ uint32_t s_tab[8];
@@ -575,46 +589,49 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
+    const int g = lane / T, k = lane % T;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int WCAP = L.wcap;
-    const int rc = TB_ROWS;
-    uint32_t *bnd = (uint32_t *)L.boundary + warp_global * 32 * L.boundary_group_ints;
+    const int S4 = (WCAP + T - 1 + 3) >> 2;
+    const int rc = T * TB_ROWS;
+    // one boundary row per group, updated in place: (H | F << 16) of pair x at
+    // offset j in word (j * G + g) * 2 + x
+    uint32_t *bnd = (uint32_t *)L.boundary + warp_global * L.boundary_group_ints;
     const int32_t go = P.sc.go, ge = P.sc.ge;
     const uint32_t GE2 = splat16(ge), GO2 = splat16(go);
     const uint32_t one = (uint32_t)L.one;
     const uint32_t m1 = 0u - one, two = one + one, four = two + two, eight = four + four;
     const uint32_t mul1 = eight + eight, mul2 = mul1 * mul1, mul3 = mul2 * mul1;  // 16, 256, 4096
     const uint32_t ONES = 0x00010001u;
-    const int WCAP4 = (WCAP + 3) >> 2;  // groups of four offsets per chunk
-    const int64_t lane_chunks = L.slab_group_words / (8 * (int64_t)max(WCAP4, 1));
+    const int64_t lane_chunks = L.slab_group_words / (8 * (int64_t)max(S4, 1));
 
     for (;;) {
         int base = 0;
-        if (lane == 0) base = atomicAdd(L.work_counter, 64);
+        if (lane == 0) base = atomicAdd(L.work_counter, PAIRS);
         base = __shfl_sync(FULLMASK, base, 0);
         if (base >= L.n_items) break;
         TbPair q[2];
 #pragma unroll
         for (int x = 0; x < 2; ++x) {
-            const int64_t item = base + 2 * lane + x;
+            const int64_t item = base + 2 * g + x;
             const int32_t p = item < L.n_items ? L.order[item] : -1;
-            q[x] = tb_pair(P, p, L.status);
+            q[x] = tb_pair(P, p, k == 0 ? L.status : nullptr);
             const bool over = (q[x].rows + rc - 1) / rc > lane_chunks || min(q[x].W, rc + (q[x].b - q[x].a)) > WCAP;
             if (q[x].score > 0 && over) {
                 // the launch was sized from the class maxima; never overrun
-                atomicOr(L.status, ST_INTERNAL);
+                if (k == 0) atomicOr(L.status, ST_INTERNAL);
                 q[x].score = 0;
                 q[x].rows = 0;
             }
         }
-        // the task's tile (64 pairs), kept for the walk kernel
-        uint2 *slab = (uint2 *)L.slab + (int64_t)(base / 64) * 32 * (L.slab_group_words / 2);
+        // the task's tile, kept for the walk kernel
+        uint2 *slab = (uint2 *)L.slab + (int64_t)(base / PAIRS) * 32 * (L.slab_group_words / 2);
         const int32_t rows_l = max(q[0].score > 0 ? q[0].rows : 0, q[1].score > 0 ? q[1].rows : 0);
         const int32_t rows_w = __reduce_max_sync(FULLMASK, (unsigned)rows_l);
         const int chunks = (rows_w + rc - 1) / rc;
 
         int prev_lo[2] = {0, 0};
-        int prev_steps = 0;
+        int prev_width = 0;  // offsets the previous chunk's last lanes wrote
         for (int c = 0; c < chunks; ++c) {
             int lo[2], hi[2];
 #pragma unroll
@@ -623,8 +640,9 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
                 hi[x] = -1;
                 if (q[x].score > 0 && c * rc < q[x].rows) chunk_window(q[x], c, rc, lo[x], hi[x]);
             }
-            const int steps = __reduce_max_sync(FULLMASK, (unsigned)max(max(hi[0] - lo[0] + 1, hi[1] - lo[1] + 1), 0));
-            const int i0 = c * rc;
+            const int width = __reduce_max_sync(FULLMASK, (unsigned)max(max(hi[0] - lo[0] + 1, hi[1] - lo[1] + 1), 0));
+            const int steps = width + T - 1;
+            const int i0 = c * rc + k * TB_ROWS;
             uint32_t sel[TB_ROWS];
             {
                 uint32_t codes[2];
@@ -648,16 +666,16 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
                 E[r] = 0u;
                 Hp[r] = 0u;
             }
-            // one boundary row, updated in place: offset t is read (two steps
-            // ahead, at t + shift with shift >= 0) before step t overwrites it
-            const uint32_t *bin = c > 0 ? bnd : nullptr;
-            uint32_t *bout = c + 1 < chunks ? bnd : nullptr;
-            // boundary word of pair x at offset t of the previous chunk (0 past its steps)
+            // one boundary row, updated in place: the first lane reads offset
+            // j (two steps ahead, at j + shift, shift >= 0) at step j - 2, the
+            // last lane overwrites it at step j + T - 1
+            const uint32_t *bin = (c > 0 && k == 0) ? bnd : nullptr;
+            uint32_t *bout = (c + 1 < chunks && k == T - 1) ? bnd : nullptr;
             int shift[2];
             shift[0] = lo[0] - prev_lo[0];
             shift[1] = lo[1] - prev_lo[1];
-            auto bload = [&](int x, int t) -> uint32_t {
-                return (bin && t >= 0 && t < prev_steps) ? bin[((int64_t)t * 32 + lane) * 2 + x] : 0u;
+            auto bload = [&](int x, int j) -> uint32_t {
+                return (bin && j >= 0 && j < prev_width) ? bin[((int64_t)j * G + g) * 2 + x] : 0u;
             };
             // the row above, two offsets ahead: packed (H | F << 16) per pair
             uint32_t nb[2], nc[2], dg[2];
@@ -674,57 +692,67 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
                 const int64_t a0 = q[x].ws + q[x].jlo + lo[x];
                 ws[x].start(P.ps.wins, a0, q[x].score > 0 ? q[x].ws + q[x].n : a0);
             }
+            uint32_t out_h = 0u, out_f = 0u;
 
             for (int t = 0; t < steps; ++t) {
-                const uint32_t up_h = prmt(nb[0], nb[1], 0x5410u);
-                const uint32_t up_f = prmt(nb[0], nb[1], 0x7632u);
+                // the row above: from the lane before (its last step), or the
+                // previous chunk's boundary row for the group's first lane
+                uint32_t up_h = T > 1 ? __shfl_up_sync(FULLMASK, out_h, 1) : 0u;
+                uint32_t up_f = T > 1 ? __shfl_up_sync(FULLMASK, out_f, 1) : 0u;
+                if (k == 0) {
+                    up_h = prmt(nb[0], nb[1], 0x5410u);
+                    up_f = prmt(nb[0], nb[1], 0x7632u);
 #pragma unroll
-                for (int x = 0; x < 2; ++x) {
-                    nb[x] = nc[x];
-                    nc[x] = bload(x, t + 2 + shift[x]);
+                    for (int x = 0; x < 2; ++x) {
+                        nb[x] = nc[x];
+                        nc[x] = bload(x, t + 2 + shift[x]);
+                    }
                 }
-                const uint32_t tA = s_tab[ws[0].next(P.ps.wins)];
-                const uint32_t tB = s_tab[ws[1].next(P.ps.wins)];
-                uint32_t d0 = diag_in, hu = up_h, f = up_f;
-                uint32_t w0 = 0u, w1 = 0u;
+                const int jl = t - k;  // this lane's window offset
+                if (jl >= 0) {
+                    const uint32_t tA = s_tab[ws[0].next(P.ps.wins)];
+                    const uint32_t tB = s_tab[ws[1].next(P.ps.wins)];
+                    uint32_t d0 = diag_in, hu = up_h, f = up_f;
+                    uint32_t w0 = 0u, w1 = 0u;
 #pragma unroll
-                for (int r = 0; r < TB_ROWS; ++r) {
-                    const uint32_t sp = prmt(tA, tB, sel[r]);  // s - o, both pairs
-                    const uint32_t e = __viaddmax_s16x2(E[r], GE2, Hp[r]);
-                    f = __viaddmax_s16x2(f, GE2, hu);
-                    const uint32_t d = FMA_ADD ? mad_u32(d0, one, sp) : __viaddmax_s16x2(d0, sp, 0x80008000u);
-                    const uint32_t u = __vimax3_s16x2(d, e, f);
-                    const uint32_t h = __viaddmax_s16x2_relu(u, GO2, 0u);
-                    const uint32_t nd = FMA_ADD ? min_u16x2(mad_u32(d, m1, u), ONES) : min_u16x2(u ^ d, ONES);
-                    const uint32_t ne = min_u16x2(mad_u32(e, m1, u), ONES);
-                    const uint32_t nE = min_u16x2(mad_u32(Hp[r], m1, e), ONES);
-                    const uint32_t nF = min_u16x2(mad_u32(hu, m1, f), ONES);
-                    uint32_t code = mad_u32(ne, two, nd);
-                    code = mad_u32(nE, four, code);
-                    code = mad_u32(nF, eight, code);
-                    if (r == 0) w0 = code;
-                    else if (r == 4) w1 = code;
-                    else if (r < 4) w0 = mad_u32(code, r == 1 ? mul1 : r == 2 ? mul2 : mul3, w0);
-                    else w1 = mad_u32(code, r == 5 ? mul1 : r == 6 ? mul2 : mul3, w1);
-                    d0 = Hp[r];
-                    Hp[r] = h;
-                    E[r] = e;
-                    hu = h;
+                    for (int r = 0; r < TB_ROWS; ++r) {
+                        const uint32_t sp = prmt(tA, tB, sel[r]);  // s - o, both pairs
+                        const uint32_t e = __viaddmax_s16x2(E[r], GE2, Hp[r]);
+                        f = __viaddmax_s16x2(f, GE2, hu);
+                        const uint32_t d = FMA_ADD ? mad_u32(d0, one, sp) : __viaddmax_s16x2(d0, sp, 0x80008000u);
+                        const uint32_t u = __vimax3_s16x2(d, e, f);
+                        const uint32_t h = __viaddmax_s16x2_relu(u, GO2, 0u);
+                        const uint32_t nd = FMA_ADD ? min_u16x2(mad_u32(d, m1, u), ONES) : min_u16x2(u ^ d, ONES);
+                        const uint32_t ne = min_u16x2(mad_u32(e, m1, u), ONES);
+                        const uint32_t nE = min_u16x2(mad_u32(Hp[r], m1, e), ONES);
+                        const uint32_t nF = min_u16x2(mad_u32(hu, m1, f), ONES);
+                        uint32_t code = mad_u32(ne, two, nd);
+                        code = mad_u32(nE, four, code);
+                        code = mad_u32(nF, eight, code);
+                        if (r == 0) w0 = code;
+                        else if (r == 4) w1 = code;
+                        else if (r < 4) w0 = mad_u32(code, r == 1 ? mul1 : r == 2 ? mul2 : mul3, w0);
+                        else w1 = mad_u32(code, r == 5 ? mul1 : r == 6 ? mul2 : mul3, w1);
+                        d0 = Hp[r];
+                        Hp[r] = h;
+                        E[r] = e;
+                        hu = h;
+                    }
+                    // streaming store (the walk reads back a few words of it); a
+                    // lane's four consecutive steps share one 32-byte sector
+                    __stcs(slab + tb16_word(c, t, lane, S4), make_uint2(w0, w1));
+                    out_h = hu;
+                    out_f = f;
+                    if (bout)
+                        *(uint2 *)(bout + ((int64_t)jl * G + g) * 2) = make_uint2(prmt(hu, f, 0x5410u), prmt(hu, f, 0x7632u));
+                    diag_in = up_h;
                 }
-                // streaming store (the walk reads back a few words of it); a
-                // lane's four consecutive offsets share one 32-byte sector
-                __stcs(slab + ((((int64_t)c * WCAP4 + (t >> 2)) * 32 + lane) << 2) + (t & 3), make_uint2(w0, w1));
-                if (bout)
-                    *(uint2 *)(bout + ((int64_t)t * 32 + lane) * 2) = make_uint2(prmt(hu, f, 0x5410u), prmt(hu, f, 0x7632u));
-                diag_in = up_h;
             }
             prev_lo[0] = lo[0];
             prev_lo[1] = lo[1];
-            prev_steps = steps;
+            prev_width = width;
             __syncwarp();
         }
-
-        __syncwarp();
     }
 }
 
@@ -788,18 +816,20 @@ struct FwdCigar {
 };
 
 // One thread per pair: walk back from the end cell through the tile that
-// k_traceback16 wrote (item k of the launch: task k / 64, lane (k % 64) / 2,
-// half k % 2), carrying the exact value of the current state (the tile does
-// not record where H is 0).  The thread keeps the sector of four offsets it
-// read last, and the 16-base words of read and window that hold its current
-// row and column.
+// k_traceback16<T> wrote (item k of the launch: task k / 2G, group
+// (k % 2G) / 2, half k % 2), carrying the exact value of the current state
+// (the tile does not record where H is 0).  The thread keeps the sector of
+// four steps it read last, and the 16-base words of read and window that
+// hold its current row and column.
+template <int T>
 __global__ void __launch_bounds__(256) k_tb16_walk(const TracebackLaunch L)
 {
+    constexpr int G = 32 / T, PAIRS = 2 * G;
     const TbParams &P = L.P;
-    const int WCAP = L.wcap, rc = TB_ROWS;
-    const int WCAP4 = (WCAP + 3) >> 2;
+    const int WCAP = L.wcap, rc = T * TB_ROWS;
+    const int S4 = (WCAP + T - 1 + 3) >> 2;
     const int32_t go = P.sc.go, ge = P.sc.ge;
-    const int64_t lane_chunks = L.slab_group_words / (8 * (int64_t)max(WCAP4, 1));
+    const int64_t lane_chunks = L.slab_group_words / (8 * (int64_t)max(S4, 1));
     for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < L.n_items;
          item += (int64_t)gridDim.x * blockDim.x) {
         const int32_t p = L.order[item];
@@ -818,8 +848,8 @@ __global__ void __launch_bounds__(256) k_tb16_walk(const TracebackLaunch L)
         cg.op = 0u;
         cg.len = 0;
         cg.overflow = false;
-        const uint2 *tile = (const uint2 *)L.slab + (item / 64) * 32 * (L.slab_group_words / 2);
-        const int lane = (int)((item & 63) >> 1), hs = 16 * (int)(item & 1);
+        const uint2 *tile = (const uint2 *)L.slab + (item / PAIRS) * 32 * (L.slab_group_words / 2);
+        const int g = (int)((item % PAIRS) >> 1), hs = 16 * (int)(item & 1);
         cg.push(4u, qq.m - 1 - qq.ie);  // trailing soft clip
         int32_t i = qq.ie, jj = qq.W - 1;
         int32_t v = qq.score;  // value of the current state at (i, jj)
@@ -843,18 +873,18 @@ __global__ void __launch_bounds__(256) k_tb16_walk(const TracebackLaunch L)
                 chunk_window(qq, cc, rc, clo, chi);
             }
             if (jj < clo || jj > chi) break;  // left the band: inconsistent
-            const int oc = jj - clo;
-            const int64_t g = (int64_t)cc * WCAP4 + (oc >> 2);
-            if (g != gkey) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(tile + ((g * 32 + lane) << 2));
+            const int kk = (i - cc * rc) >> 3, r = i & 7;
+            const int t = (jj - clo) + kk;
+            const int64_t sector = ((int64_t)cc * S4 + (t >> 2)) * 32 + g * T + kk;
+            if (sector != gkey) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(tile + (sector << 2));
                 ga = __ldg(src);
                 gb = __ldg(src + 1);
-                gkey = g;
+                gkey = sector;
             }
-            const int sl = oc & 3;
+            const int sl = t & 3;
             const uint32_t wlo = sl == 0 ? ga.x : sl == 1 ? ga.z : sl == 2 ? gb.x : gb.z;
             const uint32_t whi = sl == 0 ? ga.y : sl == 1 ? ga.w : sl == 2 ? gb.y : gb.w;
-            const int r = i - cc * rc;
             const uint32_t code = ((r < 4 ? wlo : whi) >> (hs + 4 * (r & 3))) & 0xFu;
             if (state == 0) {
                 if (!(code & 1u)) {
@@ -925,11 +955,27 @@ int launch_tb_keys(const TbParams &P, int64_t n_pairs, const int32_t *score_keys
 int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStream_t st)
 {
     if (L.packed16) {
-        if (L.P.sc.mi >= L.P.sc.go) k_traceback16<true><<<blocks, threads, 0, st>>>(L);
-        else k_traceback16<false><<<blocks, threads, 0, st>>>(L);
-        // the walks: one thread per pair, a grid of whole waves
+        const bool fma = L.P.sc.mi >= L.P.sc.go;
         int64_t wb = (L.n_items + 255) / 256;
-        k_tb16_walk<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(wb, 152 * 8)), 256, 0, st>>>(L);
+        const unsigned wblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(wb, 152 * 8));
+        switch (L.lanes) {
+#define SWGB_TB16(TT)                                                                              \
+    case TT:                                                                                       \
+        if (fma) k_traceback16<TT, true><<<blocks, threads, 0, st>>>(L);                           \
+        else k_traceback16<TT, false><<<blocks, threads, 0, st>>>(L);                              \
+        /* the walks: one thread per pair */                                                       \
+        k_tb16_walk<TT><<<wblocks, 256, 0, st>>>(L);                                                \
+        break;
+            SWGB_TB16(1)
+            SWGB_TB16(2)
+            SWGB_TB16(4)
+            SWGB_TB16(8)
+            SWGB_TB16(16)
+            SWGB_TB16(32)
+#undef SWGB_TB16
+        default:
+            return SW_ERR_INTERNAL;
+        }
         count_launch();
     } else if (L.tiled) k_traceback<true><<<blocks, threads, 0, st>>>(L);
     else k_traceback<false><<<blocks, threads, 0, st>>>(L);
@@ -937,11 +983,22 @@ int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStre
     return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
 }
 
-int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads, bool packed16)
+int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads, bool packed16, int lanes)
 {
-    const cudaError_t e =
-        packed16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback16<true>, threads, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback<false>, threads, 0);
+    cudaError_t e = cudaErrorInvalidValue;
+    if (!packed16) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback<false>, threads, 0);
+    } else {
+        switch (lanes) {
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback16<1, true>, threads, 0); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback16<2, true>, threads, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback16<4, true>, threads, 0); break;
+        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback16<8, true>, threads, 0); break;
+        case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback16<16, true>, threads, 0); break;
+        case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback16<32, true>, threads, 0); break;
+        default: break;
+        }
+    }
     return e == cudaSuccess ? SW_OK : SW_ERR_CUDA;
 }
 

@@ -30,7 +30,10 @@ constexpr int kSmallSlabWords = 4096;  // per-pair slab of the main traceback la
 constexpr size_t kSlabBudget = (size_t)4 << 30;
 constexpr int64_t kTiledLaneWords = 4096;  // largest lane tile of a lane-interleaved traceback
 constexpr int64_t kTiledLaneWords16 = 8192;  // the same for the 16-bit traceback (two pairs per lane)
-constexpr size_t kTile16Budget = (size_t)12 << 30;  // 16-bit traceback tiles kept for the walk
+// 16-bit traceback tiles kept for the walk: up to this share of the free
+// device memory, at most kTile16Cap; larger batches go in rounds
+constexpr double kTile16FreeShare = 0.4;
+constexpr size_t kTile16Cap = (size_t)64 << 30;
 constexpr int kMaxDevices = 64;
 
 struct Buffer {
@@ -277,10 +280,18 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
             return SW_ERR_CUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
         const TbClassInfo ti = *ds->tbinfo_host;
-        int tbps = 0, tbps16 = 0;
-        if ((rc = traceback_kernel_occupancy(&tbps, kThreads, false))) return rc;
-        if ((rc = traceback_kernel_occupancy(&tbps16, kThreads, true))) return rc;
+        int tbps = 0;
+        if ((rc = traceback_kernel_occupancy(&tbps, kThreads, false, 1))) return rc;
         const bool allow16 = g_tb_mode.load() == SW_TB_AUTO;
+        size_t tile16_budget = (size_t)4 << 30;
+        {
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+                // what the dynamic buffer already holds is reusable
+                const size_t usable = free_b + ds->dyn.bytes;
+                tile16_budget = std::max(tile16_budget, std::min(kTile16Cap, (size_t)(kTile16FreeShare * usable)));
+            }
+        }
         const int64_t wpb = kThreads / 32;
         struct TbRun {
             int64_t start, count;
@@ -307,45 +318,51 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
                 const int rc = kTbLanes * TB_ROWS;
                 const int64_t chunks = (r.max_m + rc - 1) / rc;
                 t.wcap = (int32_t)std::max<int64_t>(ti.max_wcap[part][r.cls], 1);
-                // two pairs per lane in 16-bit halves where the class's score
-                // bound allows it and a lane's tile (every chunk at the widest
-                // window, two words per column) stays small; else lane-
-                // interleaved int32 tiles, or packed per-pair slabs
-                const int64_t wcap4 = (t.wcap + 3) / 4 * 4;  // the 16-bit tiles group offsets by four
-                t.packed16 = allow16 && r.mode != MODE_I32 && kTbLanes == 1 && chunks * wcap4 * 2 <= kTiledLaneWords16;
-                t.tiled = !t.packed16 && kTbLanes == 1 && chunks * t.wcap <= kTiledLaneWords;
-                t.lanes = kTbLanes;
+                // 16-bit halves (two pairs per lane group) wherever the class's
+                // score bound allows it; else int32 lanes.  T lanes share a
+                // pair: one where a lane's tile (every chunk at the widest
+                // window) stays small, else a power of two covering the
+                // longest read in about four chunks, so that one pair's cells
+                // do not run on a single lane.  A T-lane chunk window is at
+                // most 8 (T - 1) wider than the one-lane windows the key pass
+                // measured.
+                const int64_t wcap4 = (t.wcap + 3) / 4 * 4;
+                int Tl = 1;
+                while (Tl < 32 && (int64_t)Tl * 32 < r.max_m) Tl *= 2;
+                t.packed16 = allow16 && r.mode != MODE_I32;
+                const bool one_lane16 = chunks * wcap4 * 2 <= kTiledLaneWords16;
+                t.tiled = !t.packed16 && chunks * t.wcap <= kTiledLaneWords;
+                t.lanes = (t.packed16 && one_lane16) || t.tiled ? 1 : Tl;
                 if (t.packed16) {
-                    t.slab_words = chunks * wcap4 * 2;
-                    t.bnd_ints = chunks > 1 ? (int64_t)2 * t.wcap : 0;  // one row, two pairs
+                    const int T = t.lanes;
+                    const int64_t chunks_t = (r.max_m + 8 * T - 1) / (8 * T);
+                    t.wcap = (int32_t)(t.wcap + 8 * (T - 1));
+                    const int64_t s4 = (t.wcap + T - 1 + 3) / 4;
+                    t.slab_words = chunks_t * s4 * 8;                                      // per lane
+                    t.bnd_ints = chunks_t > 1 ? (int64_t)(32 / T) * 2 * t.wcap : 0;        // per warp
                 } else if (t.tiled) {
                     t.slab_words = chunks * t.wcap;
                     t.bnd_ints = chunks > 1 ? (int64_t)2 * 2 * t.wcap : 0;
                 } else {
-                    // long reads or wide windows: T lanes share a pair (a power
-                    // of two covering the longest read in about four chunks),
-                    // so one pair's cells do not run on a single lane.  A
-                    // T-lane chunk window is at most 8 (T - 1) wider than the
-                    // one-lane windows the key pass measured.
-                    int T = 1;
-                    while (T < 32 && (int64_t)T * 32 < r.max_m) T *= 2;
-                    t.lanes = T;
+                    const int T = t.lanes;
                     const int64_t chunks_t = (r.max_m + 8 * T - 1) / (8 * T);
                     const int64_t wcap_t = t.wcap + 8 * (T - 1);
                     t.slab_words = T == 1 ? (part == 0 ? max_need : std::min<int64_t>(max_need, kSmallSlabWords))
                                           : chunks_t * wcap_t * T;
                     t.bnd_ints = chunks_t > 1 ? (int64_t)2 * 2 * wcap_t : 0;
                 }
-                const int per_warp = t.packed16 ? 64 : 32 / t.lanes;
+                const int per_warp = t.packed16 ? 64 / t.lanes : 32 / t.lanes;
                 if (t.packed16) {
-                    // a tile per task of 64 pairs, kept until the walk: tasks go
-                    // in rounds that fit the tile budget
+                    // a tile per task, kept until the walk: tasks go in rounds
+                    // that fit the tile budget
+                    int occ = 0;
+                    const int orc = traceback_kernel_occupancy(&occ, kThreads, true, t.lanes);
+                    if (orc) return orc;
                     const size_t tile_bytes = (size_t)32 * t.slab_words * 4;
-                    const int64_t tasks = (cnt + 63) / 64;
-                    t.round_tasks = std::max<int64_t>(1, std::min<int64_t>(tasks, (int64_t)(kTile16Budget / tile_bytes)));
-                    const size_t bnd_per_block = (size_t)wpb * 32 * t.bnd_ints * 4;
-                    int64_t blocks = std::min<int64_t>((t.round_tasks + wpb - 1) / wpb,
-                                                       (int64_t)std::max(tbps16, 1) * ds->sm_count);
+                    const int64_t tasks = (cnt + per_warp - 1) / per_warp;
+                    t.round_tasks = std::max<int64_t>(1, std::min<int64_t>(tasks, (int64_t)(tile16_budget / tile_bytes)));
+                    const size_t bnd_per_block = (size_t)wpb * t.bnd_ints * 4;
+                    int64_t blocks = std::min<int64_t>((t.round_tasks + wpb - 1) / wpb, (int64_t)std::max(occ, 1) * ds->sm_count);
                     t.blocks = (int)std::max<int64_t>(blocks, 1);
                     need = std::max(need, tile_bytes * (size_t)t.round_tasks + bnd_per_block * (size_t)t.blocks);
                 } else {
@@ -378,7 +395,7 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
             B.work_counter = counters + 2 * N_CLASS + 2 * t.cls + t.part;
             B.status = &info->status;
             if (t.packed16) {
-                const int64_t round_items = t.round_tasks * 64;
+                const int64_t round_items = t.round_tasks * (64 / t.lanes);
                 const size_t tiles = (size_t)t.round_tasks * 32 * t.slab_words;
                 B.boundary = (int32_t *)ds->dyn.ptr + tiles;
                 for (int64_t r0 = 0; r0 < t.count; r0 += round_items) {

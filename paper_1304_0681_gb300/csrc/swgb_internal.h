@@ -130,7 +130,7 @@ int launch_tb_keys(const TbParams &P, int64_t n_pairs, const int32_t *score_keys
 int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, const int32_t *class_count, int32_t *hist,
                         int32_t *bucket_start, int32_t *cursor, int32_t *order, cudaStream_t st);
 int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStream_t st);
-int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads, bool packed16);
+int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads, bool packed16, int lanes);
 int launch_alu_probe(int kind, int64_t iters, int blocks, int threads, uint32_t *out, cudaStream_t st);
 
 int launch_features(const FeatureParams &P, cudaStream_t st);
