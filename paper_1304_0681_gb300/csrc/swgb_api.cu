@@ -35,6 +35,8 @@ constexpr int64_t kTiledLaneWords16 = 8192;  // the same for the 16-bit tracebac
 constexpr double kTile16FreeShare = 0.4;
 constexpr size_t kTile16Cap = (size_t)64 << 30;
 constexpr int kMaxDevices = 64;
+constexpr int kAuxStreams = 4;
+constexpr bool kConcurrentTbParts = false;
 
 struct Buffer {
     void *ptr = nullptr;
@@ -59,7 +61,13 @@ struct DeviceState {
     bool timing = false;             // record phase events (sw_phase_times)
     bool timed_cells_valid = false;
     int64_t tb_split[2] = {0, 0};    // pairs per traceback kernel (16-bit, 32-bit) of the last call
+    size_t tile16_budget = 0;        // 16-bit traceback tile budget (set at the first traceback)
     cudaEvent_t phase[4] = {nullptr, nullptr, nullptr, nullptr};
+    // independent launches (length classes, traceback parts) fork onto these
+    // streams and join back, so one launch's tail overlaps the next
+    cudaStream_t aux[kAuxStreams] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kAuxStreams] = {};
     std::mutex mu;
 };
 
@@ -69,6 +77,26 @@ std::vector<PlanOverride> g_plans;
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Fork: the first n auxiliary streams wait for everything enqueued on st so
+// far.  Join: st waits for all of their work.  (The pattern is legal under
+// stream capture.)
+int fork_streams(DeviceState *ds, cudaStream_t st, int n)
+{
+    if (cudaEventRecord(ds->fork_ev, st) != cudaSuccess) return SW_ERR_CUDA;
+    for (int k = 0; k < n; ++k)
+        if (cudaStreamWaitEvent(ds->aux[k], ds->fork_ev, 0) != cudaSuccess) return SW_ERR_CUDA;
+    return SW_OK;
+}
+
+int join_streams(DeviceState *ds, cudaStream_t st, int n)
+{
+    for (int k = 0; k < n; ++k) {
+        if (cudaEventRecord(ds->join_ev[k], ds->aux[k]) != cudaSuccess) return SW_ERR_CUDA;
+        if (cudaStreamWaitEvent(st, ds->join_ev[k], 0) != cudaSuccess) return SW_ERR_CUDA;
+    }
+    return SW_OK;
+}
+
 int ensure(Buffer &b, size_t bytes)
 {
     if (b.bytes >= bytes) return SW_OK;
@@ -77,7 +105,7 @@ int ensure(Buffer &b, size_t bytes)
     if (b.ptr) cudaFree(b.ptr);
     b.ptr = nullptr;
     b.bytes = 0;
-    const size_t want = align_up(bytes + bytes / 4, 1 << 20);
+    const size_t want = align_up(bytes + std::min<size_t>(bytes / 4, (size_t)256 << 20), 1 << 20);
     if (cudaMalloc(&b.ptr, want) != cudaSuccess) {
         cudaGetLastError();
         return SW_ERR_CUDA;
@@ -102,6 +130,11 @@ int device_state(DeviceState **out)
         if (cudaEventCreateWithFlags(&s.last_done, cudaEventDisableTiming) != cudaSuccess) return SW_ERR_CUDA;
         for (cudaEvent_t &e : s.phase)
             if (cudaEventCreate(&e) != cudaSuccess) return SW_ERR_CUDA;
+        for (int k = 0; k < kAuxStreams; ++k) {
+            if (cudaStreamCreateWithFlags(&s.aux[k], cudaStreamNonBlocking) != cudaSuccess) return SW_ERR_CUDA;
+            if (cudaEventCreateWithFlags(&s.join_ev[k], cudaEventDisableTiming) != cudaSuccess) return SW_ERR_CUDA;
+        }
+        if (cudaEventCreateWithFlags(&s.fork_ev, cudaEventDisableTiming) != cudaSuccess) return SW_ERR_CUDA;
         s.ready = true;
     }
     *out = &s;
@@ -217,6 +250,7 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         Plan plan;
         int score_blocks;
         size_t bnd_bytes_group;
+        size_t bnd_offset;  // of this class's boundary scratch in the dynamic buffer
     };
     std::vector<ClassRun> runs;
     int64_t pos = 0;
@@ -244,14 +278,20 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         r.score_blocks = (int)std::max<int64_t>(blocks, 1);
         const int chunks = (r.max_m + r.plan.lanes * r.plan.rows - 1) / (r.plan.lanes * r.plan.rows);
         r.bnd_bytes_group = chunks > 1 ? (size_t)2 * r.max_n * 2 * sizeof(uint32_t) : 0;
-        size_t need = r.bnd_bytes_group * (size_t)r.score_blocks * wpb * G;
-        need_dyn = std::max(need_dyn, need);
+        // classes run concurrently: each gets its own boundary scratch
+        r.bnd_offset = need_dyn;
+        need_dyn += align_up(r.bnd_bytes_group * (size_t)r.score_blocks * wpb * G, 256);
         runs.push_back(r);
     }
     if ((rc = ensure(ds->dyn, std::max<size_t>(need_dyn, 256)))) return rc;
 
     if (ds->timing && cudaEventRecord(ds->phase[1], st) != cudaSuccess) return SW_ERR_CUDA;
-    for (const ClassRun &r : runs) {
+    // one launch per class; several classes fork onto the auxiliary streams
+    const int n_aux_score = runs.size() > 1 ? (int)std::min<size_t>(runs.size(), kAuxStreams) : 0;
+    if (n_aux_score && (rc = fork_streams(ds, st, n_aux_score))) return rc;
+    for (size_t ri = 0; ri < runs.size(); ++ri) {
+        const ClassRun &r = runs[ri];
+        const cudaStream_t cs = n_aux_score ? ds->aux[ri % n_aux_score] : st;
         ScoreLaunch L{};
         L.ps = ps;
         L.sc = sc;
@@ -260,12 +300,13 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         L.lanes = r.plan.lanes;
         L.out_score = out_score;
         L.out_end = out_end;
-        L.boundary = r.bnd_bytes_group ? (uint8_t *)ds->dyn.ptr : nullptr;
+        L.boundary = r.bnd_bytes_group ? (uint8_t *)ds->dyn.ptr + r.bnd_offset : nullptr;
         L.boundary_group_bytes = (int64_t)r.bnd_bytes_group;
         L.work_counter = counters + r.cls;
         L.status = &info->status;
-        if ((rc = launch_score(r.plan.rows, r.mode, L, r.score_blocks, kThreads, st))) return rc;
+        if ((rc = launch_score(r.plan.rows, r.mode, L, r.score_blocks, kThreads, cs))) return rc;
     }
+    if (n_aux_score && (rc = join_streams(ds, st, n_aux_score))) return rc;
     if (ds->timing && cudaEventRecord(ds->phase[2], st) != cudaSuccess) return SW_ERR_CUDA;
     if (cig) {
         // order each class by traceback cost, then size the slabs from the
@@ -283,15 +324,16 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         int tbps = 0;
         if ((rc = traceback_kernel_occupancy(&tbps, kThreads, false, 1))) return rc;
         const bool allow16 = g_tb_mode.load() == SW_TB_AUTO;
-        size_t tile16_budget = (size_t)4 << 30;
-        {
+        if (!ds->tile16_budget) {
+            // once per device: a share of the memory free at the first call
+            // (plus what the dynamic buffer already holds)
             size_t free_b = 0, total_b = 0;
-            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-                // what the dynamic buffer already holds is reusable
-                const size_t usable = free_b + ds->dyn.bytes;
-                tile16_budget = std::max(tile16_budget, std::min(kTile16Cap, (size_t)(kTile16FreeShare * usable)));
-            }
+            ds->tile16_budget = (size_t)4 << 30;
+            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+                ds->tile16_budget = std::max(ds->tile16_budget,
+                                             std::min(kTile16Cap, (size_t)(kTile16FreeShare * (free_b + ds->dyn.bytes))));
         }
+        const size_t tile16_budget = ds->tile16_budget;
         const int64_t wpb = kThreads / 32;
         struct TbRun {
             int64_t start, count;
@@ -301,6 +343,9 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
             int blocks;
             int64_t round_tasks;  // 16-bit kernel: tasks (64 pairs) per round
             int lanes;            // int32 kernels: lanes per pair
+            size_t need;          // scratch bytes of one round
+            size_t offset;        // of its scratch in the dynamic buffer
+            bool one_round;
             int cls, part;
         };
         std::vector<TbRun> tbr;
@@ -364,29 +409,53 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
                     const size_t bnd_per_block = (size_t)wpb * t.bnd_ints * 4;
                     int64_t blocks = std::min<int64_t>((t.round_tasks + wpb - 1) / wpb, (int64_t)std::max(occ, 1) * ds->sm_count);
                     t.blocks = (int)std::max<int64_t>(blocks, 1);
-                    need = std::max(need, tile_bytes * (size_t)t.round_tasks + bnd_per_block * (size_t)t.blocks);
+                    t.need = tile_bytes * (size_t)t.round_tasks + bnd_per_block * (size_t)t.blocks;
+                    t.one_round = t.round_tasks == tasks;
                 } else {
                     const size_t per_block = (size_t)wpb * (32 / t.lanes) * (t.slab_words + t.bnd_ints) * 4;
                     int64_t blocks = std::min<int64_t>(((cnt + per_warp - 1) / per_warp + wpb - 1) / wpb,
                                                        (int64_t)std::max(tbps, 1) * ds->sm_count);
                     blocks = std::min<int64_t>(blocks, (int64_t)(kSlabBudget / std::max<size_t>(per_block, 1)));
                     t.blocks = (int)std::max<int64_t>(blocks, 1);
-                    need = std::max(need, per_block * (size_t)t.blocks);
+                    t.need = per_block * (size_t)t.blocks;
+                    t.one_round = true;
                 }
                 t.cls = r.cls;
                 t.part = part;
                 tbr.push_back(t);
             }
         }
-        if ((rc = ensure(ds->dyn, std::max<size_t>(need, 256)))) return rc;
+        // Parts run concurrently on the auxiliary streams, each in its own
+        // scratch region, when all of them fit one round of the budget;
+        // otherwise one after another, each from the start of the buffer.
+        size_t total = 0;
+        bool all_one_round = true;
+        for (TbRun &t : tbr) {
+            t.offset = total;
+            total += align_up(t.need, 256);
+            all_one_round = all_one_round && t.one_round;
+            need = std::max(need, t.need);
+        }
+        // (measured: on a one-class batch the big and main parts slowed each
+        // other down, on the uneven batch it gained 0.1 %, so parts run in order)
+        const bool concurrent = kConcurrentTbParts && tbr.size() > 1 && all_one_round &&
+                                total <= std::max(tile16_budget, need);
+        if (!concurrent)
+            for (TbRun &t : tbr) t.offset = 0;
+        if ((rc = ensure(ds->dyn, std::max<size_t>(concurrent ? total : need, 256)))) return rc;
         ds->tb_split[0] = ds->tb_split[1] = 0;
         for (const TbRun &t : tbr) ds->tb_split[t.packed16 ? 0 : 1] += t.count;
-        for (const TbRun &t : tbr) {
+        const int n_aux_tb = concurrent ? (int)std::min<size_t>(tbr.size(), kAuxStreams) : 0;
+        if (n_aux_tb && (rc = fork_streams(ds, st, n_aux_tb))) return rc;
+        for (size_t ti2 = 0; ti2 < tbr.size(); ++ti2) {
+            const TbRun &t = tbr[ti2];
+            const cudaStream_t ts = n_aux_tb ? ds->aux[ti2 % n_aux_tb] : st;
+            uint8_t *region = (uint8_t *)ds->dyn.ptr + t.offset;
             TracebackLaunch B{};
             B.P = P;
             B.P.lanes = t.lanes;
             B.lanes = t.lanes;
-            B.slab = (uint32_t *)ds->dyn.ptr;
+            B.slab = (uint32_t *)region;
             B.slab_group_words = t.slab_words;
             B.boundary_group_ints = t.bnd_ints;
             B.wcap = t.wcap;
@@ -397,22 +466,23 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
             if (t.packed16) {
                 const int64_t round_items = t.round_tasks * (64 / t.lanes);
                 const size_t tiles = (size_t)t.round_tasks * 32 * t.slab_words;
-                B.boundary = (int32_t *)ds->dyn.ptr + tiles;
+                B.boundary = (int32_t *)region + tiles;
                 for (int64_t r0 = 0; r0 < t.count; r0 += round_items) {
                     B.order = tb_order + t.start + r0;
                     B.n_items = std::min<int64_t>(round_items, t.count - r0);
-                    if (r0 > 0 && cudaMemsetAsync(B.work_counter, 0, sizeof(int32_t), st) != cudaSuccess)
+                    if (r0 > 0 && cudaMemsetAsync(B.work_counter, 0, sizeof(int32_t), ts) != cudaSuccess)
                         return SW_ERR_CUDA;
-                    if ((rc = launch_traceback(B, t.blocks, kThreads, st))) return rc;
+                    if ((rc = launch_traceback(B, t.blocks, kThreads, ts))) return rc;
                 }
             } else {
                 B.order = tb_order + t.start;
                 B.n_items = t.count;
                 const size_t slab_total = (size_t)t.blocks * wpb * (32 / t.lanes) * t.slab_words;
-                B.boundary = (int32_t *)ds->dyn.ptr + slab_total;
-                if ((rc = launch_traceback(B, t.blocks, kThreads, st))) return rc;
+                B.boundary = (int32_t *)region + slab_total;
+                if ((rc = launch_traceback(B, t.blocks, kThreads, ts))) return rc;
             }
         }
+        if (n_aux_tb && (rc = join_streams(ds, st, n_aux_tb))) return rc;
     }
     if (ds->timing && cudaEventRecord(ds->phase[3], st) != cudaSuccess) return SW_ERR_CUDA;
     ds->timed_cells_valid = ds->timing;
