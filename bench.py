@@ -301,6 +301,54 @@ def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
             "score_roofline_frac": cells / (score_ms * 1e-3) / 1e9 / peak_gcups}
 
 
+def _graph_section(rank, n_pairs: int = 16384, reps: int = 50) -> dict:
+    """Small batches, where per-call host work matters: the throughput
+    workload's pair mix at n_pairs pairs, score + end + CIGAR, through
+    sw_batch_align (two host synchronisations per call) and as a CUDA graph
+    captured from a plan (sw_plan_align) and replayed.  Wall time per batch,
+    host included, over reps back-to-back batches."""
+    import torch
+
+    import synth
+    from paper_1304_0681_gb300 import BatchPlan, DeviceBatch, align
+
+    wl = synth.generate("throughput", seed=100 + rank, n_reads=n_pairs)
+    b = DeviceBatch.from_packed(wl.packed_reads(), wl.read_offsets, wl.packed_windows(), wl.window_offsets,
+                                cigar=True)
+    for _ in range(3):
+        align(b, SCORING, cigar=True)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        align(b, SCORING, cigar=True, sync=False)
+    torch.cuda.synchronize()
+    direct_s = (time.perf_counter() - t) / reps
+    plan = BatchPlan(b, SCORING)
+    plan.align()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(graph, stream=side):
+        plan.align()
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        graph.replay()
+    torch.cuda.synchronize()
+    graph_s = (time.perf_counter() - t) / reps
+    plan.status()
+    cells = wl.cells()
+    del graph
+    plan.close()
+    return {"workload": f"{n_pairs} pairs of the throughput mix (100 x 200 bp, 20% decoys), score + end + CIGAR",
+            "batches": reps, "direct_ms_per_batch": direct_s * 1e3, "graph_ms_per_batch": graph_s * 1e3,
+            "direct_gcups": cells / direct_s / 1e9, "graph_gcups": cells / graph_s / 1e9,
+            "speedup": direct_s / graph_s}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -455,8 +503,9 @@ def main():
     filt = None
     if not args.no_filter:
         filt = _filter_section(args, rank, steps=max(2, min(args.steps, 5)), n_reads=args.filter_reads)
-    uneven = fullmix = None
+    uneven = fullmix = graph = None
     if not args.no_extra and args.workload == "throughput":
+        graph = _graph_section(rank)
         del batch
         torch.cuda.empty_cache()
         uneven = _uneven_section(args, rank, steps=max(2, min(args.steps, 3)), peak_gcups=peak_gcups)
@@ -480,7 +529,7 @@ def main():
                              "peak_basis": f"measured 16x2 DPX add-max rate {dpx_ops / 1e12:.2f} Tops/s "
                                            f"x 2 cells / {OPS_PER_CELL:g} ops per cell"},
                 "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "learned_filter": filt,
-                "uneven": uneven, "fullmix_sample": fullmix}
+                "uneven": uneven, "fullmix_sample": fullmix, "small_batch_graph": graph}
         if rank == 0 and not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
         print(json.dumps(line), flush=True)

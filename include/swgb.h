@@ -269,6 +269,44 @@ int sw_batch_align_noalloc(const uint8_t *reads, const int64_t *read_offsets,
                            int64_t n_pairs, const sw_scoring_t *scoring,
                            int32_t *out_score, int32_t *out_end, sw_stream_t stream);
 
+/*
+ * Capturable execution of a fixed-shape batch (pattern: one plan, many
+ * replays).  sw_batch_align synchronises with the host twice per call (to
+ * size its launches from the batch) and allocates on growth, so it cannot be
+ * captured into a CUDA graph.  A plan takes those decisions once:
+ *
+ *   sw_plan_create classifies the batch given by its offsets (device
+ *   pointers, as for sw_batch_align_indexed; pair_read may be NULL for one
+ *   read per pair), picks the lane plans, sizes the traceback for the worst
+ *   case (every window fully inside the band) and allocates all scratch the
+ *   plan will use.  It synchronises `stream` once.  with_cigar = 0 plans
+ *   score and end cell only.
+ *
+ *   sw_plan_align enqueues the whole path on `stream` for the plan's shape
+ *   and the given packed bases and outputs: no allocation, no host
+ *   synchronisation, a fixed sequence of kernel launches and memsets.  So it
+ *   can be captured into a CUDA graph and replayed; the bases and outputs
+ *   may change between calls or replays (the arrays the captured call named
+ *   are the ones a replay uses), the offsets must not.  The device compares
+ *   the batch's class counts with the plan's and reports a mismatch as
+ *   SW_ERR_DEVICE_INPUT through sw_plan_status.
+ *
+ *   sw_plan_status waits for `stream` and returns the status the plan's
+ *   last execution (or replay) recorded.  sw_plan_destroy waits for the
+ *   device and frees the plan.  A plan belongs to the device current at its
+ *   creation; executions of one plan must not overlap.
+ *
+ * The paper has no counterpart: its batches go to OpenMP threads (§3.4).
+ */
+typedef struct sw_plan sw_plan_t;
+int sw_plan_create(const int64_t *read_offsets, int64_t n_reads, const int64_t *window_offsets,
+                   const int64_t *pair_read, int64_t n_pairs, const sw_scoring_t *scoring, int32_t with_cigar,
+                   sw_stream_t stream, sw_plan_t **out_plan);
+int sw_plan_align(sw_plan_t *plan, const uint8_t *reads, const uint8_t *windows, int32_t *out_score,
+                  int32_t *out_end, sw_cigar_t *out_cigar, sw_stream_t stream);
+int sw_plan_status(sw_plan_t *plan, sw_stream_t stream);
+int sw_plan_destroy(sw_plan_t *plan);
+
 /* Text of an SW_* code (static storage). */
 const char *sw_strerror(int code);
 

@@ -11,10 +11,10 @@ from ._swgb import (SwError, sw_alu_probe, sw_batch_align, sw_batch_align_host, 
                     sw_cigar_capacity, sw_launch_count, sw_packed_bytes, sw_phase_times, sw_phase_timing,
                     sw_plan_rows, sw_set_plan, sw_set_traceback_mode, sw_last_traceback_split, sw_strerror, sw_sync_status,
                     SW_TB_AUTO, SW_TB_INT32)
-from .device import DeviceBatch, align
+from .device import BatchPlan, DeviceBatch, align
 
 __all__ = ["SwError", "sw_alu_probe", "sw_batch_align", "sw_batch_align_host", "sw_batch_align_indexed",
            "sw_batch_align_noalloc",
            "sw_cigar_capacity", "sw_launch_count", "sw_packed_bytes", "sw_phase_times", "sw_phase_timing",
            "sw_plan_rows", "sw_set_plan", "sw_set_traceback_mode", "sw_last_traceback_split", "SW_TB_AUTO", "SW_TB_INT32", "sw_strerror",
-           "sw_sync_status", "DeviceBatch", "align", "_swgb"]
+           "sw_sync_status", "DeviceBatch", "BatchPlan", "align", "_swgb"]

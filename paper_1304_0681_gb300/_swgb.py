@@ -23,7 +23,7 @@ ERRORS = {
 #: every symbol include/swgb.h declares
 EXPORTS = ("sw_cigar_capacity", "sw_packed_bytes", "sw_batch_align", "sw_batch_align_indexed",
            "sw_batch_align_host", "sw_sync_status", "sw_strerror", "sw_launch_count", "sw_set_plan", "sw_set_traceback_mode",
-           "sw_last_traceback_split",
+           "sw_last_traceback_split", "sw_plan_create", "sw_plan_align", "sw_plan_status", "sw_plan_destroy",
            "sw_plan_rows", "sw_alu_probe", "sw_phase_timing", "sw_phase_times", "sw_batch_align_noalloc",
            "sw_batch_align_masked", "sw_filter_features", "sw_mlp_bytes", "sw_mlp_init", "sw_mlp_refresh",
            "sw_mlp_forward", "sw_mlp_grad", "sw_mlp_adam", "sw_filter_select", "sw_best_per_read")
@@ -96,6 +96,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_set_traceback_mode.restype = ctypes.c_int
     lib.sw_last_traceback_split.argtypes = [ctypes.c_void_p]
     lib.sw_last_traceback_split.restype = ctypes.c_int
+    lib.sw_plan_create.argtypes = [p, i64, p, p, i64, ctypes.POINTER(Scoring), i32, p, ctypes.POINTER(ctypes.c_void_p)]
+    lib.sw_plan_create.restype = ctypes.c_int
+    lib.sw_plan_align.argtypes = [p, p, p, p, p, ctypes.POINTER(Cigar), p]
+    lib.sw_plan_align.restype = ctypes.c_int
+    lib.sw_plan_status.argtypes = [p, p]
+    lib.sw_plan_status.restype = ctypes.c_int
+    lib.sw_plan_destroy.argtypes = [p]
+    lib.sw_plan_destroy.restype = ctypes.c_int
     lib.sw_plan_rows.argtypes = [p, i32]
     lib.sw_plan_rows.restype = ctypes.c_int
     lib.sw_phase_timing.argtypes = [i32]
@@ -176,6 +184,33 @@ def sw_batch_align_noalloc(reads, read_offsets, windows, window_offsets, n_pairs
     _check(_lib.sw_batch_align_noalloc(_ptr(reads), _ptr(read_offsets), _ptr(windows), _ptr(window_offsets),
                                        int(n_pairs), ctypes.byref(sc), _ptr(out_score), _ptr(out_end),
                                        _stream(stream)), "sw_batch_align_noalloc")
+
+
+def sw_plan_create(read_offsets, n_reads: int, window_offsets, pair_read, n_pairs: int, scoring,
+                   with_cigar: bool = True, stream=None) -> int:
+    """Plan a fixed-shape batch; returns the plan handle (see include/swgb.h)."""
+    sc = _scoring(scoring)
+    h = ctypes.c_void_p()
+    _check(_lib.sw_plan_create(_ptr(read_offsets), int(n_reads), _ptr(window_offsets), _ptr(pair_read),
+                               int(n_pairs), ctypes.byref(sc), int(bool(with_cigar)), _stream(stream),
+                               ctypes.byref(h)), "sw_plan_create")
+    return h.value
+
+
+def sw_plan_align(plan: int, reads, windows, out_score, out_end, cigar=None, stream=None) -> None:
+    """Enqueue one execution of a plan (capturable: no allocation, no host
+    synchronisation)."""
+    cg = Cigar(*(t.data_ptr() for t in cigar)) if cigar is not None else None
+    _check(_lib.sw_plan_align(ctypes.c_void_p(plan), _ptr(reads), _ptr(windows), _ptr(out_score), _ptr(out_end),
+                              ctypes.byref(cg) if cg is not None else None, _stream(stream)), "sw_plan_align")
+
+
+def sw_plan_status(plan: int, stream=None) -> None:
+    _check(_lib.sw_plan_status(ctypes.c_void_p(plan), _stream(stream)), "sw_plan_status")
+
+
+def sw_plan_destroy(plan: int) -> None:
+    _check(_lib.sw_plan_destroy(ctypes.c_void_p(plan)), "sw_plan_destroy")
 
 
 def sw_sync_status(stream=None) -> None:

@@ -133,6 +133,26 @@ __global__ void k_scatter(const int32_t *__restrict__ keys, int64_t n_pairs, int
     }
 }
 
+// A planned batch must classify into the class counts its plan was made for,
+// with no read or window longer than the plan's for its class (the plan's
+// scratch is sized from those maxima).  expect: counts, then longest read,
+// then longest window, N_CLASS each.
+__global__ void k_check_counts(const ClassInfo *__restrict__ info, const int32_t *__restrict__ expect,
+                               int32_t *__restrict__ status)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N_CLASS; c += gridDim.x * blockDim.x)
+        if (info->count[c] != expect[c] || info->max_m[c] > expect[N_CLASS + c] ||
+            info->max_n[c] > expect[2 * N_CLASS + c])
+            atomicOr(status, ST_BAD_INPUT);
+}
+
+int launch_check_counts(const ClassInfo *info, const int32_t *expect, int32_t *status, cudaStream_t st)
+{
+    k_check_counts<<<(N_CLASS + 255) / 256, 256, 0, st>>>(info, expect, status);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
 int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring sc,
                     int32_t *keys, int32_t *hist, int32_t *bucket_start, int32_t *cursor,
                     ClassInfo *info, int32_t *order, int32_t *out_score, int32_t *out_end,

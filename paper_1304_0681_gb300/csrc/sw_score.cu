@@ -174,6 +174,9 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
 
     uint8_t *bnd = (on && L.boundary) ? L.boundary + (warp_global * G + g) * L.boundary_group_bytes : nullptr;
     const int64_t bnd_half = L.boundary_group_bytes / 2;  // bytes per buffer of the double buffer
+    // input already found invalid (a planned batch whose shape changed): the
+    // scratch may be too small for it, so do nothing
+    if (*(volatile const int32_t *)L.status & ST_BAD_INPUT) return;
 
     for (;;) {
         int base = 0;

@@ -227,6 +227,8 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
                                : L.boundary + (warp_global * G + g) * L.boundary_group_ints;
     const int64_t bnd_half = TILED ? 32 * (L.boundary_group_ints / 2) : L.boundary_group_ints / 2;
     const int32_t go = P.sc.go, ge = P.sc.ge;
+    // input already found invalid (a planned batch whose shape changed)
+    if (*(volatile const int32_t *)L.status & ST_BAD_INPUT) return;
 
     for (;;) {
         int base = 0;
@@ -604,6 +606,8 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
     const uint32_t mul1 = eight + eight, mul2 = mul1 * mul1, mul3 = mul2 * mul1;  // 16, 256, 4096
     const uint32_t ONES = 0x00010001u;
     const int64_t lane_chunks = L.slab_group_words / (8 * (int64_t)max(S4, 1));
+    // input already found invalid (a planned batch whose shape changed)
+    if (*(volatile const int32_t *)L.status & ST_BAD_INPUT) return;
 
     for (;;) {
         int base = 0;
@@ -830,6 +834,7 @@ __global__ void __launch_bounds__(256) k_tb16_walk(const TracebackLaunch L)
     const int S4 = (WCAP + T - 1 + 3) >> 2;
     const int32_t go = P.sc.go, ge = P.sc.ge;
     const int64_t lane_chunks = L.slab_group_words / (8 * (int64_t)max(S4, 1));
+    if (*(volatile const int32_t *)L.status & ST_BAD_INPUT) return;
     for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < L.n_items;
          item += (int64_t)gridDim.x * blockDim.x) {
         const int32_t p = L.order[item];

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "sw_device.cuh"
@@ -514,6 +515,266 @@ int check_common(const void *reads, const int64_t *roff, const void *wins, const
     return SW_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Plans: the launch decisions of one batch shape, taken once, so that the
+// execution itself is a fixed sequence of launches (capturable).
+
+struct PlanScoreRun {
+    int cls, mode, rows, lanes, blocks;
+    int64_t start, count;
+    size_t bnd_bytes_group, bnd_offset;
+};
+
+struct PlanTbRun {
+    int cls, lanes, blocks;
+    bool packed16, tiled;
+    int64_t start, count, slab_words, bnd_ints, round_tasks;
+    int32_t wcap;
+};
+
+}  // namespace
+}  // namespace swgb
+
+struct sw_plan {
+    int device = -1;
+    swgb::PairSet ps{};  // offsets and pair map (bases bound per execution)
+    int64_t n_reads = 0, n_pairs = 0;
+    swgb::Scoring sc{};
+    bool cigar = false;
+    swgb::Buffer fixed, dyn;  // owned: a captured graph keeps pointing here
+    int32_t *keys = nullptr, *order = nullptr, *hist = nullptr, *bstart = nullptr, *cursor = nullptr;
+    int32_t *counters = nullptr, *tb_keys = nullptr, *tb_order = nullptr, *expect = nullptr;
+    swgb::ClassInfo *info = nullptr;
+    swgb::TbClassInfo *tbinfo = nullptr;
+    std::vector<swgb::PlanScoreRun> sruns;
+    std::vector<swgb::PlanTbRun> truns;
+    size_t tb_tiles_bytes = 0;  // offset of the traceback boundary rows in dyn
+};
+
+namespace swgb {
+namespace {
+
+int plan_build(sw_plan *pl, DeviceState *ds, cudaStream_t st)
+{
+    int rc = SW_OK;
+    const size_t nh = (size_t)N_CLASS * N_NBUCKET;
+    const int64_t n_pairs = pl->n_pairs;
+    size_t off = 0;
+    const size_t o_keys = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
+    const size_t o_order = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
+    const size_t o_hist = off; off = align_up(off + sizeof(int32_t) * nh, 256);
+    const size_t o_bstart = off; off = align_up(off + sizeof(int32_t) * nh, 256);
+    const size_t o_cursor = off; off = align_up(off + sizeof(int32_t) * nh, 256);
+    const size_t o_info = off; off = align_up(off + sizeof(ClassInfo), 256);
+    const size_t o_counters = off; off = align_up(off + sizeof(int32_t) * 4 * N_CLASS, 256);
+    const size_t o_tbkeys = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
+    const size_t o_tborder = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
+    const size_t o_tbinfo = off; off = align_up(off + sizeof(TbClassInfo), 256);
+    const size_t o_expect = off; off = align_up(off + sizeof(int32_t) * 3 * N_CLASS, 256);
+    if ((rc = ensure(pl->fixed, off))) return rc;
+    uint8_t *fx = (uint8_t *)pl->fixed.ptr;
+    pl->keys = (int32_t *)(fx + o_keys);
+    pl->order = (int32_t *)(fx + o_order);
+    pl->hist = (int32_t *)(fx + o_hist);
+    pl->bstart = (int32_t *)(fx + o_bstart);
+    pl->cursor = (int32_t *)(fx + o_cursor);
+    pl->info = (ClassInfo *)(fx + o_info);
+    pl->counters = (int32_t *)(fx + o_counters);
+    pl->tb_keys = (int32_t *)(fx + o_tbkeys);
+    pl->tb_order = (int32_t *)(fx + o_tborder);
+    pl->tbinfo = (TbClassInfo *)(fx + o_tbinfo);
+    pl->expect = (int32_t *)(fx + o_expect);
+
+    // classify once (it reads offsets only) and read the class table back
+    if (cudaMemsetAsync(pl->hist, 0, sizeof(int32_t) * nh, st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cudaMemsetAsync(pl->info, 0, sizeof(ClassInfo), st) != cudaSuccess) return SW_ERR_CUDA;
+    int32_t *tmp_score = pl->tb_keys, *tmp_end = nullptr;  // empty-window outputs go to scratch
+    if ((rc = ensure(pl->dyn, sizeof(int32_t) * 2 * std::max<int64_t>(n_pairs, 1)))) return rc;
+    tmp_end = (int32_t *)pl->dyn.ptr;
+    if ((rc = launch_classify(pl->ps, pl->n_reads, n_pairs, pl->sc, pl->keys, pl->hist, pl->bstart, pl->cursor,
+                              pl->info, pl->order, tmp_score, tmp_end, nullptr, st)))
+        return rc;
+    ClassInfo ci;
+    if (cudaMemcpyAsync(&ci, pl->info, sizeof(ClassInfo), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SW_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
+    if (ci.status) return status_to_code(ci.status);
+    {
+        std::vector<int32_t> ex(3 * N_CLASS);
+        std::memcpy(ex.data(), ci.count, sizeof(int32_t) * N_CLASS);
+        std::memcpy(ex.data() + N_CLASS, ci.max_m, sizeof(int32_t) * N_CLASS);
+        std::memcpy(ex.data() + 2 * N_CLASS, ci.max_n, sizeof(int32_t) * N_CLASS);
+        if (cudaMemcpy(pl->expect, ex.data(), sizeof(int32_t) * 3 * N_CLASS, cudaMemcpyHostToDevice) != cudaSuccess)
+            return SW_ERR_CUDA;
+    }
+
+    // score launches, as sw_batch_align plans them
+    const int64_t wpb = kThreads / 32;
+    int64_t pos = 0;
+    size_t score_scratch = 0;
+    for (int cls = 0; cls < N_CLASS; ++cls) {
+        const int32_t cnt = ci.count[cls];
+        if (!cnt) continue;
+        PlanScoreRun r{};
+        r.cls = cls;
+        r.mode = cls / N_MCLASS;
+        r.start = pos;
+        r.count = cnt;
+        pos += cnt;
+        const int32_t max_m = ci.max_m[cls], max_n = ci.max_n[cls];
+        const Plan plan = choose_plan(r.mode, max_m, (int64_t)pl->sc.ma * std::min(max_m, max_n));
+        r.rows = plan.rows;
+        r.lanes = plan.lanes;
+        int regs = 0, bps = 0;
+        if ((rc = score_kernel_regs(r.rows, r.mode, &regs, &bps, kThreads))) return rc;
+        if (bps < 1) return SW_ERR_INTERNAL;
+        const int G = 32 / r.lanes;
+        const int per_warp = G * (r.mode == MODE_I32 ? 1 : 2);
+        const int64_t warps_needed = (cnt + per_warp - 1) / per_warp;
+        r.blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps_needed + wpb - 1) / wpb, (int64_t)bps * ds->sm_count));
+        const int chunks = (max_m + r.lanes * r.rows - 1) / (r.lanes * r.rows);
+        r.bnd_bytes_group = chunks > 1 ? (size_t)2 * max_n * 2 * sizeof(uint32_t) : 0;
+        r.bnd_offset = score_scratch;
+        score_scratch += align_up(r.bnd_bytes_group * (size_t)r.blocks * wpb * G, 256);
+        pl->sruns.push_back(r);
+    }
+
+    // traceback launches for the worst case: any window may be inside the
+    // band, so a chunk window is at most the class's longest window
+    size_t tb_need = 0;
+    if (pl->cigar) {
+        if (!ds->tile16_budget) {
+            size_t free_b = 0, total_b = 0;
+            ds->tile16_budget = (size_t)4 << 30;
+            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+                ds->tile16_budget = std::max(ds->tile16_budget,
+                                             std::min(kTile16Cap, (size_t)(kTile16FreeShare * (free_b + ds->dyn.bytes))));
+        }
+        int tbps = 0;
+        if ((rc = traceback_kernel_occupancy(&tbps, kThreads, false, 1))) return rc;
+        const bool allow16 = g_tb_mode.load() == SW_TB_AUTO;
+        for (const PlanScoreRun &r : pl->sruns) {
+            PlanTbRun t{};
+            t.cls = r.cls;
+            t.start = r.start;
+            t.count = r.count;
+            const int32_t max_m = ci.max_m[r.cls], max_n = ci.max_n[r.cls];
+            const int64_t chunks = (max_m + TB_ROWS - 1) / TB_ROWS;
+            const int64_t wcap1 = max_n;
+            const int64_t wcap4 = (wcap1 + 3) / 4 * 4;
+            int Tl = 1;
+            while (Tl < 32 && (int64_t)Tl * 32 < max_m) Tl *= 2;
+            t.packed16 = allow16 && r.mode != MODE_I32;
+            t.tiled = !t.packed16 && chunks * wcap1 <= kTiledLaneWords;
+            t.lanes = (t.packed16 && chunks * wcap4 * 2 <= kTiledLaneWords16) || t.tiled ? 1 : Tl;
+            const int T = t.lanes;
+            const int64_t chunks_t = (max_m + 8 * T - 1) / (8 * T);
+            const int64_t wcap_t = wcap1 + 8 * (T - 1);
+            t.wcap = (int32_t)(t.packed16 ? wcap_t : wcap1);
+            if (t.packed16) {
+                const int64_t s4 = (wcap_t + T - 1 + 3) / 4;
+                t.slab_words = chunks_t * s4 * 8;
+                t.bnd_ints = chunks_t > 1 ? (int64_t)(32 / T) * 2 * wcap_t : 0;
+                int occ = 0;
+                if ((rc = traceback_kernel_occupancy(&occ, kThreads, true, T))) return rc;
+                const size_t tile_bytes = (size_t)32 * t.slab_words * 4;
+                const int per_warp = 64 / T;
+                const int64_t tasks = (t.count + per_warp - 1) / per_warp;
+                t.round_tasks = std::max<int64_t>(1, std::min<int64_t>(tasks, (int64_t)(ds->tile16_budget / tile_bytes)));
+                t.blocks = (int)std::max<int64_t>(1, std::min<int64_t>((t.round_tasks + wpb - 1) / wpb, (int64_t)std::max(occ, 1) * ds->sm_count));
+                tb_need = std::max(tb_need, tile_bytes * (size_t)t.round_tasks + (size_t)wpb * t.bnd_ints * 4 * t.blocks);
+            } else {
+                if (t.tiled) {
+                    t.slab_words = chunks * wcap1;
+                    t.bnd_ints = chunks > 1 ? 4 * wcap1 : 0;
+                } else {
+                    t.slab_words = chunks_t * wcap_t * T;
+                    t.bnd_ints = chunks_t > 1 ? 4 * wcap_t : 0;
+                }
+                const int per_warp = 32 / T;
+                const size_t per_block = (size_t)wpb * per_warp * (t.slab_words + t.bnd_ints) * 4;
+                int64_t blocks = std::min<int64_t>(((t.count + per_warp - 1) / per_warp + wpb - 1) / wpb,
+                                                   (int64_t)std::max(tbps, 1) * ds->sm_count);
+                blocks = std::min<int64_t>(blocks, (int64_t)(kSlabBudget / std::max<size_t>(per_block, 1)));
+                t.blocks = (int)std::max<int64_t>(blocks, 1);
+                t.round_tasks = 0;
+                tb_need = std::max(tb_need, per_block * (size_t)t.blocks);
+            }
+            pl->truns.push_back(t);
+        }
+    }
+    return ensure(pl->dyn, std::max<size_t>(std::max(score_scratch, tb_need), 256));
+}
+
+int plan_execute(sw_plan *pl, int32_t *out_score, int32_t *out_end, const sw_cigar_t *cig, cudaStream_t st)
+{
+    int rc = SW_OK;
+    const size_t nh = (size_t)N_CLASS * N_NBUCKET;
+    const PairSet &ps = pl->ps;
+    if (cudaMemsetAsync(pl->hist, 0, sizeof(int32_t) * nh, st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cudaMemsetAsync(pl->info, 0, sizeof(ClassInfo), st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cudaMemsetAsync(pl->counters, 0, sizeof(int32_t) * 4 * N_CLASS, st) != cudaSuccess) return SW_ERR_CUDA;
+    if ((rc = launch_classify(ps, pl->n_reads, pl->n_pairs, pl->sc, pl->keys, pl->hist, pl->bstart, pl->cursor,
+                              pl->info, pl->order, out_score, out_end, cig ? cig->n_ops : nullptr, st)))
+        return rc;
+    if ((rc = launch_check_counts(pl->info, pl->expect, &pl->info->status, st))) return rc;
+    for (const PlanScoreRun &r : pl->sruns) {
+        ScoreLaunch L{};
+        L.ps = ps;
+        L.sc = pl->sc;
+        L.order = pl->order + r.start;
+        L.n_items = r.count;
+        L.lanes = r.lanes;
+        L.out_score = out_score;
+        L.out_end = out_end;
+        L.boundary = r.bnd_bytes_group ? (uint8_t *)pl->dyn.ptr + r.bnd_offset : nullptr;
+        L.boundary_group_bytes = (int64_t)r.bnd_bytes_group;
+        L.work_counter = pl->counters + r.cls;
+        L.status = &pl->info->status;
+        if ((rc = launch_score(r.rows, r.mode, L, r.blocks, kThreads, st))) return rc;
+    }
+    if (!pl->cigar || !cig) return SW_OK;
+    TbParams P{ps, pl->sc, out_score, out_end, cig->ops, cig->offsets, cig->n_ops, 1, kSmallSlabWords};
+    if (cudaMemsetAsync(pl->hist, 0, sizeof(int32_t) * nh, st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cudaMemsetAsync(pl->tbinfo, 0, sizeof(TbClassInfo), st) != cudaSuccess) return SW_ERR_CUDA;
+    if ((rc = launch_tb_keys(P, pl->n_pairs, pl->keys, pl->tb_keys, pl->hist, pl->tbinfo, st))) return rc;
+    if ((rc = launch_scan_scatter(pl->tb_keys, pl->n_pairs, pl->info->count, pl->hist, pl->bstart, pl->cursor,
+                                  pl->tb_order, st)))
+        return rc;
+    const int64_t wpb = kThreads / 32;
+    for (const PlanTbRun &t : pl->truns) {
+        TracebackLaunch B{};
+        B.P = P;
+        B.P.lanes = t.lanes;
+        B.lanes = t.lanes;
+        B.slab = (uint32_t *)pl->dyn.ptr;
+        B.slab_group_words = t.slab_words;
+        B.boundary_group_ints = t.bnd_ints;
+        B.wcap = t.wcap;
+        B.tiled = t.tiled;
+        B.packed16 = t.packed16;
+        B.work_counter = pl->counters + 2 * N_CLASS + 2 * t.cls;
+        B.status = &pl->info->status;
+        if (t.packed16) {
+            const int64_t round_items = t.round_tasks * (64 / t.lanes);
+            B.boundary = (int32_t *)pl->dyn.ptr + (size_t)t.round_tasks * 32 * t.slab_words;
+            for (int64_t r0 = 0; r0 < t.count; r0 += round_items) {
+                B.order = pl->tb_order + t.start + r0;
+                B.n_items = std::min<int64_t>(round_items, t.count - r0);
+                if (r0 > 0 && cudaMemsetAsync(B.work_counter, 0, sizeof(int32_t), st) != cudaSuccess)
+                    return SW_ERR_CUDA;
+                if ((rc = launch_traceback(B, t.blocks, kThreads, st))) return rc;
+            }
+        } else {
+            B.order = pl->tb_order + t.start;
+            B.n_items = t.count;
+            B.boundary = (int32_t *)pl->dyn.ptr + (size_t)t.blocks * wpb * (32 / t.lanes) * t.slab_words;
+            if ((rc = launch_traceback(B, t.blocks, kThreads, st))) return rc;
+        }
+    }
+    return SW_OK;
+}
+
 }  // namespace
 }  // namespace swgb
 
@@ -741,6 +1002,75 @@ int sw_alu_probe(int32_t kind, int64_t iters, double *ops_per_s, sw_stream_t str
     cudaFree(out);
     if (rc) return rc;
     *ops_per_s = (double)blocks * threads * 8.0 * (double)iters / (ms * 1e-3);
+    return SW_OK;
+}
+
+int sw_plan_create(const int64_t *read_offsets, int64_t n_reads, const int64_t *window_offsets,
+                   const int64_t *pair_read, int64_t n_pairs, const sw_scoring_t *scoring, int32_t with_cigar,
+                   sw_stream_t stream, sw_plan_t **out_plan)
+{
+    if (!out_plan) return SW_ERR_INVALID_ARG;
+    *out_plan = nullptr;
+    if (!read_offsets || !window_offsets || n_pairs < 1 || !scoring_ok(scoring)) return SW_ERR_INVALID_ARG;
+    if (pair_read && n_reads < 1) return SW_ERR_INVALID_ARG;
+    if (n_pairs > (int64_t)INT32_MAX - 64) return SW_ERR_UNSUPPORTED;
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    sw_plan *pl = new (std::nothrow) sw_plan();
+    if (!pl) return SW_ERR_INVALID_ARG;
+    cudaGetDevice(&pl->device);
+    pl->ps = PairSet{nullptr, read_offsets, pair_read, nullptr, window_offsets};
+    pl->n_reads = pair_read ? n_reads : n_pairs;
+    pl->n_pairs = n_pairs;
+    pl->sc = Scoring{scoring->match, scoring->mismatch, scoring->gap_open, scoring->gap_extend};
+    pl->cigar = with_cigar != 0;
+    {
+        std::lock_guard<std::mutex> lk(ds->mu);
+        rc = plan_build(pl, ds, (cudaStream_t)stream);
+    }
+    if (rc) {
+        sw_plan_destroy(pl);
+        return rc;
+    }
+    *out_plan = pl;
+    return SW_OK;
+}
+
+int sw_plan_align(sw_plan_t *plan, const uint8_t *reads, const uint8_t *windows, int32_t *out_score,
+                  int32_t *out_end, sw_cigar_t *out_cigar, sw_stream_t stream)
+{
+    if (!plan || !reads || !windows || !out_score || !out_end) return SW_ERR_INVALID_ARG;
+    if (((uintptr_t)reads & 15u) || ((uintptr_t)windows & 15u)) return SW_ERR_INVALID_ARG;
+    if (out_cigar && (!out_cigar->ops || !out_cigar->offsets || !out_cigar->n_ops)) return SW_ERR_INVALID_ARG;
+    if (out_cigar && !plan->cigar) return SW_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return SW_ERR_INVALID_ARG;
+    plan->ps.reads = (const uint32_t *)reads;
+    plan->ps.wins = (const uint32_t *)windows;
+    return plan_execute(plan, out_score, out_end, out_cigar, (cudaStream_t)stream);
+}
+
+int sw_plan_status(sw_plan_t *plan, sw_stream_t stream)
+{
+    if (!plan) return SW_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return SW_ERR_CUDA;
+    int32_t v = 0;
+    if (cudaMemcpy(&v, &plan->info->status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return SW_ERR_CUDA;
+    return status_to_code(v);
+}
+
+int sw_plan_destroy(sw_plan_t *plan)
+{
+    if (!plan) return SW_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (plan->device >= 0) cudaSetDevice(plan->device);
+    cudaDeviceSynchronize();
+    if (plan->fixed.ptr) cudaFree(plan->fixed.ptr);
+    if (plan->dyn.ptr) cudaFree(plan->dyn.ptr);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete plan;
     return SW_OK;
 }
 

@@ -127,6 +127,7 @@ int launch_score(int rows, int mode, const ScoreLaunch &L, int blocks, int threa
 int score_kernel_regs(int rows, int mode, int *regs, int *max_blocks_per_sm, int threads);
 int launch_tb_keys(const TbParams &P, int64_t n_pairs, const int32_t *score_keys, int32_t *tb_keys, int32_t *hist,
                    TbClassInfo *info, cudaStream_t st);
+int launch_check_counts(const ClassInfo *info, const int32_t *expect, int32_t *status, cudaStream_t st);
 int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, const int32_t *class_count, int32_t *hist,
                         int32_t *bucket_start, int32_t *cursor, int32_t *order, cudaStream_t st);
 int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStream_t st);

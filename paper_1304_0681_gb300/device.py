@@ -90,3 +90,36 @@ def align(batch: DeviceBatch, scoring, cigar: bool = True, stream=None, sync: bo
     if sync:
         _swgb.sw_sync_status(stream)
     return batch
+
+
+class BatchPlan:
+    """A plan for the shape of one DeviceBatch (its offsets and pair map):
+    launch decisions and scratch fixed once, so that align() is a fixed
+    sequence of launches that a CUDA graph can capture and replay.  The
+    batch's bases may change between calls; its offsets must not."""
+
+    def __init__(self, batch: DeviceBatch, scoring, cigar: bool = True, stream=None):
+        self.batch = batch
+        self.cigar = bool(cigar)
+        self.handle = _swgb.sw_plan_create(batch.read_offsets, batch.n_reads, batch.window_offsets,
+                                           batch.pair_read, batch.n_pairs, scoring, self.cigar, stream)
+
+    def align(self, stream=None) -> DeviceBatch:
+        b = self.batch
+        _swgb.sw_plan_align(self.handle, b.reads, b.windows, b.score, b.end,
+                            b.cigar_tuple() if self.cigar else None, stream)
+        return b
+
+    def status(self, stream=None) -> None:
+        _swgb.sw_plan_status(self.handle, stream)
+
+    def close(self) -> None:
+        if self.handle:
+            _swgb.sw_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
