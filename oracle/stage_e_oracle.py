@@ -1,0 +1,114 @@
+"""Reference of Stage E, task iv: alignment records and splice junctions.
+TEST INFRASTRUCTURE ONLY: only tests, the smoke check and the benchmark's
+CPU leg may use it.
+
+The paper (§2, Stage E) turns every SW alignment whose score passes a
+threshold into an alignment record: where the read lies on the reference
+(chromosome, first and last position), which part of the read aligned, and
+the strand.  The same task looks for splice junctions: a long run of
+consecutive deletions in the alignment marks a candidate intron, and the
+candidate is kept when the intron starts and ends with the marks GT ... AG
+or CT ... AC.  Junctions are counted over all batches.
+
+Readings (the paper gives no numbers or formats for these):
+- "above a given threshold" is read as score >= min_score, and score > 0
+  (an empty alignment is never a record);
+- "a large number of consecutive deletions" is a D run of at least
+  min_intron window bases;
+- a window's reference coordinates are given per window: chromosome, the
+  position of its first base, and its strand; the alignment covers window
+  columns j_start..j_end with j_start = j_end + 1 - (M + D bases);
+- a junction is (chromosome, first intron base, last intron base, strand),
+  all in reference coordinates; GT...AG gives strand '+' (0), CT...AC
+  strand '-' (1); other marks are not junctions.
+
+Every function here is a plain loop over the definition.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+OP_M, OP_I, OP_D, OP_S = 0, 1, 2, 4
+A, C, G, T = 0, 1, 2, 3
+
+
+def runs(ops):
+    """(length, op) of each BAM-encoded CIGAR run."""
+    return [(int(x) >> 4, int(x) & 0xF) for x in ops]
+
+
+def alignment_span(ops, i_end: int, j_end: int):
+    """(i_start, j_start): first read row and first window column of the
+    alignment, from its CIGAR and end cell."""
+    rr = runs(ops)
+    i_start = rr[0][0] if rr and rr[0][1] == OP_S else 0
+    ref_len = sum(n for n, op in rr if op in (OP_M, OP_D))
+    return i_start, j_end + 1 - ref_len
+
+
+def record(pair, score, i_end, j_end, ops, chrom, pos, strand):
+    """The alignment record of one pair, as a tuple (pair, score, chrom,
+    ref_start, ref_end, read_start, read_end, strand)."""
+    i_start, j_start = alignment_span(ops, i_end, j_end)
+    return (int(pair), int(score), int(chrom), int(pos) + j_start, int(pos) + j_end, i_start, int(i_end),
+            int(strand))
+
+
+def records(score, i_end, j_end, cigars, window_chrom, window_pos, window_strand, min_score):
+    """Records of every pair with score >= min_score (and > 0), in pair order."""
+    out = []
+    for p in range(len(score)):
+        if score[p] > 0 and score[p] >= min_score:
+            out.append(record(p, score[p], i_end[p], j_end[p], cigars[p], window_chrom[p], window_pos[p],
+                              window_strand[p]))
+    return out
+
+
+def intron_strand(window, j: int, length: int):
+    """0 for GT...AG, 1 for CT...AC, None otherwise (window base codes,
+    intron = window[j : j + length])."""
+    if length < 4:
+        return None
+    first = (int(window[j]), int(window[j + 1]))
+    last = (int(window[j + length - 2]), int(window[j + length - 1]))
+    if first == (G, T) and last == (A, G):
+        return 0
+    if first == (C, T) and last == (A, C):
+        return 1
+    return None
+
+
+def pair_junctions(window, ops, j_end: int, chrom: int, pos: int, min_intron: int):
+    """Junctions of one alignment: (chrom, first intron base, last intron
+    base, strand) for each qualifying D run, in CIGAR order."""
+    _, j = alignment_span(ops, 0, j_end)
+    out = []
+    for n, op in runs(ops):
+        if op == OP_D:
+            if n >= min_intron:
+                s = intron_strand(window, j, n)
+                if s is not None:
+                    out.append((int(chrom), int(pos) + j, int(pos) + j + n - 1, s))
+            j += n
+        elif op == OP_M:
+            j += n
+    return out
+
+
+def junction_counts(windows, window_offsets, score, j_end, cigars, window_chrom, window_pos, min_score,
+                    min_intron, counts=None):
+    """Add the junctions of every pair with score >= min_score (and > 0) to
+    a dict {(chrom, start, end, strand): count} and return it."""
+    counts = {} if counts is None else counts
+    for p in range(len(score)):
+        if score[p] > 0 and score[p] >= min_score:
+            w = windows[window_offsets[p]:window_offsets[p + 1]]
+            for key in pair_junctions(w, cigars[p], j_end[p], window_chrom[p], window_pos[p], min_intron):
+                counts[key] = counts.get(key, 0) + 1
+    return counts
+
+
+def cigars_of(res):
+    """Per-pair CIGAR op arrays from an oracle.align_batch result."""
+    off, n = res["cigar_offsets"], res["n_ops"]
+    return [res["ops"][off[p]:off[p] + n[p]] for p in range(len(n))]
