@@ -291,6 +291,38 @@ def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
         phases.append(sw.sw_phase_times())
     sw.sw_sync_status()
     sw.sw_phase_timing(False)
+    # Stage E task iv on the aligned batch: records above a score threshold
+    # and GT-AG / CT-AC junctions (synthetic reference coordinates: one
+    # contig per 100k windows, windows back to back)
+    from paper_1304_0681_gb300 import stage_e
+    pid = torch.arange(wl.n_pairs, device="cuda")
+    chrom = (pid // 100_000).to(torch.int32)
+    pos = b.window_offsets[:-1].clone()
+    strand = (pid % 2).to(torch.int8)
+    table = stage_e.JunctionTable(1 << 22)
+    rec_out = torch.empty((wl.n_pairs, 6), dtype=torch.int64, device="cuda")
+    rec_n = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def stage_e_step():
+        sw._swgb.sw_records(b.score, b.end, b.cigar_tuple(), wl.n_pairs, chrom, pos, strand, 100, rec_out, rec_n)
+        table.detect(b, chrom, pos, 100, 20)
+
+    stage_e_step()
+    torch.cuda.synchronize()
+    table.clear()
+    e_ms = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stage_e_step()
+        e1.record(stream)
+        e1.synchronize()
+        e_ms.append(e0.elapsed_time(e1))
+    sw.sw_sync_status()
+    jn = table.export()
+    stage_e_res = {"ms": statistics.mean(e_ms), "records": int(rec_n.item()), "min_score": 100, "min_intron": 20,
+                   "distinct_junctions": int(len(jn["count"])), "junction_hits": int(jn["count"].sum()),
+                   "steps_counted": steps}
     cells = wl.cells()
     t = sum(ms) / len(ms)
     score_ms = statistics.mean(p[1] for p in phases)
@@ -298,7 +330,8 @@ def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
             "ms_per_step": t, "gcups": cells / (t * 1e-3) / 1e9, "reads_per_s": wl.n_reads / (t * 1e-3),
             "phase_ms": {"classify": statistics.mean(p[0] for p in phases), "score": score_ms,
                          "traceback": statistics.mean(p[2] for p in phases)},
-            "score_roofline_frac": cells / (score_ms * 1e-3) / 1e9 / peak_gcups}
+            "score_roofline_frac": cells / (score_ms * 1e-3) / 1e9 / peak_gcups,
+            "stage_e_records_junctions": stage_e_res}
 
 
 def _graph_section(rank, n_pairs: int = 16384, reps: int = 50) -> dict:

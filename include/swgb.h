@@ -307,6 +307,70 @@ int sw_plan_align(sw_plan_t *plan, const uint8_t *reads, const uint8_t *windows,
 int sw_plan_status(sw_plan_t *plan, sw_stream_t stream);
 int sw_plan_destroy(sw_plan_t *plan);
 
+/*
+ * Stage E, task iv (§2): records and splice junctions from the alignments.
+ * All pointers are device pointers; every call is stream-ordered and
+ * asynchronous, and device-detected errors are read with sw_sync_status.
+ *
+ * Records.  A pair whose score is >= min_score (and > 0) becomes a record;
+ * records are written in pair order to out_records (room for n_pairs) and
+ * their number to *out_count.  The window's reference coordinates come from
+ * the caller per pair: window_chrom, window_pos (reference position of the
+ * window's first base) and window_strand (copied into the record).  The
+ * aligned window columns are j_start..j_end with j_start = j_end + 1 -
+ * (M + D bases of the CIGAR); the record holds ref_start = window_pos +
+ * j_start, ref_end = window_pos + j_end, read_start = the leading soft clip,
+ * read_end = i_end.  Pairs whose CIGAR overflowed (n_ops < 0) are skipped.
+ */
+typedef struct {
+    int64_t pair;
+    int64_t ref_start;
+    int64_t ref_end;
+    int32_t chrom;
+    int32_t score;
+    int32_t read_start;
+    int32_t read_end;
+    int32_t strand;
+    int32_t n_ops;
+} sw_record_t; /* 48 bytes */
+int sw_records(const int32_t *score, const int32_t *end, const sw_cigar_t *cigar, int64_t n_pairs,
+               const int32_t *window_chrom, const int64_t *window_pos, const int8_t *window_strand,
+               int32_t min_score, sw_record_t *out_records, int64_t *out_count, sw_stream_t stream);
+
+/*
+ * Splice junctions.  Every D run of at least min_intron window bases in the
+ * CIGAR of a record (score >= min_score, > 0) is a candidate intron
+ * window[j .. j+len-1]; it is a junction when it starts with GT and ends
+ * with AG (strand 0) or starts with CT and ends with AC (strand 1).  The
+ * junction (chrom, window_pos + j, window_pos + j + len - 1, strand) is
+ * counted in a caller-owned open-addressing table that persists across
+ * calls (the role of the paper's AVL tree).
+ *
+ * The table holds `capacity` slots (a power of two, >= 64) in
+ * sw_junction_table_words(capacity) 64-bit words: keys, then counts.
+ * sw_junction_table_clear empties it.  A full table sets SW_ERR_CAPACITY;
+ * a chromosome >= 4096, a position >= 2^32 - 1 or an intron longer than
+ * 2^19 bases sets SW_ERR_UNSUPPORTED (those junctions are not counted).
+ * sw_junctions_export writes up to max_out junctions (in slot order) and
+ * their number to *out_count (the number in the table, which may exceed
+ * max_out).  Requires min_intron >= 4.
+ */
+typedef struct {
+    int64_t start;
+    int64_t end;
+    int64_t count;
+    int32_t chrom;
+    int32_t strand;
+} sw_junction_t; /* 32 bytes */
+int64_t sw_junction_table_words(int64_t capacity);
+int sw_junction_table_clear(uint64_t *table, int64_t capacity, sw_stream_t stream);
+int sw_junctions_detect(const uint8_t *windows, const int64_t *window_offsets, const int32_t *score,
+                        const int32_t *end, const sw_cigar_t *cigar, int64_t n_pairs, const int32_t *window_chrom,
+                        const int64_t *window_pos, int32_t min_score, int32_t min_intron, uint64_t *table,
+                        int64_t capacity, sw_stream_t stream);
+int sw_junctions_export(const uint64_t *table, int64_t capacity, sw_junction_t *out, int64_t max_out,
+                        int64_t *out_count, sw_stream_t stream);
+
 /* Text of an SW_* code (static storage). */
 const char *sw_strerror(int code);
 

@@ -24,6 +24,8 @@ ERRORS = {
 EXPORTS = ("sw_cigar_capacity", "sw_packed_bytes", "sw_batch_align", "sw_batch_align_indexed",
            "sw_batch_align_host", "sw_sync_status", "sw_strerror", "sw_launch_count", "sw_set_plan", "sw_set_traceback_mode",
            "sw_last_traceback_split", "sw_plan_create", "sw_plan_align", "sw_plan_status", "sw_plan_destroy",
+           "sw_records", "sw_junction_table_words", "sw_junction_table_clear", "sw_junctions_detect",
+           "sw_junctions_export",
            "sw_plan_rows", "sw_alu_probe", "sw_phase_timing", "sw_phase_times", "sw_batch_align_noalloc",
            "sw_batch_align_masked", "sw_filter_features", "sw_mlp_bytes", "sw_mlp_init", "sw_mlp_refresh",
            "sw_mlp_forward", "sw_mlp_grad", "sw_mlp_adam", "sw_filter_select", "sw_best_per_read")
@@ -104,6 +106,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_plan_status.restype = ctypes.c_int
     lib.sw_plan_destroy.argtypes = [p]
     lib.sw_plan_destroy.restype = ctypes.c_int
+    lib.sw_records.argtypes = [p, p, ctypes.POINTER(Cigar), i64, p, p, p, i32, p, p, p]
+    lib.sw_records.restype = ctypes.c_int
+    lib.sw_junction_table_words.argtypes = [i64]
+    lib.sw_junction_table_words.restype = i64
+    lib.sw_junction_table_clear.argtypes = [p, i64, p]
+    lib.sw_junction_table_clear.restype = ctypes.c_int
+    lib.sw_junctions_detect.argtypes = [p, p, p, p, ctypes.POINTER(Cigar), i64, p, p, i32, i32, p, i64, p]
+    lib.sw_junctions_detect.restype = ctypes.c_int
+    lib.sw_junctions_export.argtypes = [p, i64, p, i64, p, p]
+    lib.sw_junctions_export.restype = ctypes.c_int
     lib.sw_plan_rows.argtypes = [p, i32]
     lib.sw_plan_rows.restype = ctypes.c_int
     lib.sw_phase_timing.argtypes = [i32]
@@ -211,6 +223,41 @@ def sw_plan_status(plan: int, stream=None) -> None:
 
 def sw_plan_destroy(plan: int) -> None:
     _check(_lib.sw_plan_destroy(ctypes.c_void_p(plan)), "sw_plan_destroy")
+
+
+RECORD_BYTES = 48
+JUNCTION_BYTES = 32
+
+
+def sw_records(score, end, cigar, n_pairs: int, window_chrom, window_pos, window_strand, min_score: int,
+               out_records, out_count, stream=None) -> None:
+    """out_records: a device buffer of >= n_pairs * 48 bytes; out_count: int64[1]."""
+    cg = Cigar(*(t.data_ptr() for t in cigar))
+    _check(_lib.sw_records(_ptr(score), _ptr(end), ctypes.byref(cg), int(n_pairs), _ptr(window_chrom),
+                           _ptr(window_pos), _ptr(window_strand), int(min_score), _ptr(out_records), _ptr(out_count),
+                           _stream(stream)), "sw_records")
+
+
+def sw_junction_table_words(capacity: int) -> int:
+    return int(_lib.sw_junction_table_words(int(capacity)))
+
+
+def sw_junction_table_clear(table, capacity: int, stream=None) -> None:
+    _check(_lib.sw_junction_table_clear(_ptr(table), int(capacity), _stream(stream)), "sw_junction_table_clear")
+
+
+def sw_junctions_detect(windows, window_offsets, score, end, cigar, n_pairs: int, window_chrom, window_pos,
+                        min_score: int, min_intron: int, table, capacity: int, stream=None) -> None:
+    cg = Cigar(*(t.data_ptr() for t in cigar))
+    _check(_lib.sw_junctions_detect(_ptr(windows), _ptr(window_offsets), _ptr(score), _ptr(end), ctypes.byref(cg),
+                                    int(n_pairs), _ptr(window_chrom), _ptr(window_pos), int(min_score),
+                                    int(min_intron), _ptr(table), int(capacity), _stream(stream)),
+           "sw_junctions_detect")
+
+
+def sw_junctions_export(table, capacity: int, out, max_out: int, out_count, stream=None) -> None:
+    _check(_lib.sw_junctions_export(_ptr(table), int(capacity), _ptr(out), int(max_out), _ptr(out_count),
+                                    _stream(stream)), "sw_junctions_export")
 
 
 def sw_sync_status(stream=None) -> None:

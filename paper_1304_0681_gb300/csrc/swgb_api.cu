@@ -63,6 +63,7 @@ struct DeviceState {
     bool timed_cells_valid = false;
     int64_t tb_split[2] = {0, 0};    // pairs per traceback kernel (16-bit, 32-bit) of the last call
     size_t tile16_budget = 0;        // 16-bit traceback tile budget (set at the first traceback)
+    Buffer misc;                     // Stage E task iv: status word and record scan scratch
     cudaEvent_t phase[4] = {nullptr, nullptr, nullptr, nullptr};
     // independent launches (length classes, traceback parts) fork onto these
     // streams and join back, so one launch's tail overlaps the next
@@ -1072,6 +1073,87 @@ int sw_plan_destroy(sw_plan_t *plan)
     if (prev >= 0) cudaSetDevice(prev);
     delete plan;
     return SW_OK;
+}
+
+// ---- Stage E, task iv ---------------------------------------------------
+
+static int stage_e_status(DeviceState *ds, size_t extra, cudaStream_t st, int32_t **status, uint8_t **scratch)
+{
+    // a status word in front of the scratch, cleared by each call
+    int rc = ensure(ds->misc, 256 + extra);
+    if (rc) return rc;
+    *status = (int32_t *)ds->misc.ptr;
+    *scratch = (uint8_t *)ds->misc.ptr + 256;
+    if (cudaMemsetAsync(*status, 0, sizeof(int32_t), st) != cudaSuccess) return SW_ERR_CUDA;
+    ds->last_status = *status;
+    return SW_OK;
+}
+
+int sw_records(const int32_t *score, const int32_t *end, const sw_cigar_t *cigar, int64_t n_pairs,
+               const int32_t *window_chrom, const int64_t *window_pos, const int8_t *window_strand,
+               int32_t min_score, sw_record_t *out_records, int64_t *out_count, sw_stream_t stream)
+{
+    if (n_pairs < 0 || !out_count) return SW_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_pairs == 0) return cudaMemsetAsync(out_count, 0, sizeof(int64_t), st) == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    if (!score || !end || !cigar || !cigar->ops || !cigar->offsets || !cigar->n_ops || !window_chrom ||
+        !window_pos || !window_strand || !out_records)
+        return SW_ERR_INVALID_ARG;
+    if (n_pairs > (int64_t)INT32_MAX - 64) return SW_ERR_UNSUPPORTED;
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    const int64_t n_blk = (n_pairs + 255) / 256;
+    int32_t *status = nullptr;
+    uint8_t *scratch = nullptr;
+    if ((rc = stage_e_status(ds, align_up(4 * n_blk, 256) + 8 * n_blk, st, &status, &scratch))) return rc;
+    int32_t *blk_count = (int32_t *)scratch;
+    int64_t *blk_off = (int64_t *)(scratch + align_up(4 * n_blk, 256));
+    return launch_records(score, end, *cigar, n_pairs, window_chrom, window_pos, window_strand, min_score,
+                          out_records, out_count, blk_count, blk_off, st);
+}
+
+int64_t sw_junction_table_words(int64_t capacity) { return capacity < 0 ? 0 : 2 * capacity; }
+
+static bool table_ok(const uint64_t *table, int64_t capacity)
+{
+    return table && capacity >= 64 && (capacity & (capacity - 1)) == 0 && capacity <= ((int64_t)1 << 40);
+}
+
+int sw_junction_table_clear(uint64_t *table, int64_t capacity, sw_stream_t stream)
+{
+    if (!table_ok(table, capacity)) return SW_ERR_INVALID_ARG;
+    return launch_table_clear(table, capacity, (cudaStream_t)stream);
+}
+
+int sw_junctions_detect(const uint8_t *windows, const int64_t *window_offsets, const int32_t *score,
+                        const int32_t *end, const sw_cigar_t *cigar, int64_t n_pairs, const int32_t *window_chrom,
+                        const int64_t *window_pos, int32_t min_score, int32_t min_intron, uint64_t *table,
+                        int64_t capacity, sw_stream_t stream)
+{
+    if (n_pairs < 0 || min_intron < 4 || !table_ok(table, capacity)) return SW_ERR_INVALID_ARG;
+    if (n_pairs == 0) return SW_OK;
+    if (!windows || ((uintptr_t)windows & 15u) || !window_offsets || !score || !end || !cigar || !cigar->ops ||
+        !cigar->offsets || !cigar->n_ops || !window_chrom || !window_pos)
+        return SW_ERR_INVALID_ARG;
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *status = nullptr;
+    uint8_t *scratch = nullptr;
+    if ((rc = stage_e_status(ds, 0, st, &status, &scratch))) return rc;
+    return launch_junctions((const uint32_t *)windows, window_offsets, score, end, *cigar, n_pairs, window_chrom,
+                            window_pos, min_score, min_intron, table, capacity, status, st);
+}
+
+int sw_junctions_export(const uint64_t *table, int64_t capacity, sw_junction_t *out, int64_t max_out,
+                        int64_t *out_count, sw_stream_t stream)
+{
+    if (!table_ok(table, capacity) || max_out < 0 || !out_count || (max_out > 0 && !out)) return SW_ERR_INVALID_ARG;
+    return launch_table_export(table, capacity, out, max_out, out_count, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -148,6 +148,17 @@ int launch_select(const float *pred, const int64_t *cand_off, int64_t n_reads, i
 int launch_best_per_read(const int32_t *score, const int64_t *cand_off, int64_t n_reads, const uint8_t *mask,
                          int32_t *best, int32_t *best_cand, cudaStream_t st);
 
+int launch_records(const int32_t *score, const int32_t *end, const sw_cigar_t &cig, int64_t n_pairs,
+                   const int32_t *chrom, const int64_t *pos, const int8_t *strand, int32_t min_score,
+                   sw_record_t *out, int64_t *out_count, int32_t *blk_count, int64_t *blk_off, cudaStream_t st);
+int launch_junctions(const uint32_t *wins, const int64_t *win_off, const int32_t *score, const int32_t *end,
+                     const sw_cigar_t &cig, int64_t n_pairs, const int32_t *chrom, const int64_t *pos,
+                     int32_t min_score, int32_t min_intron, uint64_t *table, int64_t capacity, int32_t *status,
+                     cudaStream_t st);
+int launch_table_clear(uint64_t *table, int64_t capacity, cudaStream_t st);
+int launch_table_export(const uint64_t *table, int64_t capacity, sw_junction_t *out, int64_t max_out,
+                        int64_t *out_count, cudaStream_t st);
+
 void count_launch(int n = 1);
 
 }  // namespace swgb
