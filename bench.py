@@ -501,6 +501,7 @@ def main():
     in_mb = (len(wl.packed_reads()) + len(wl.packed_windows())) / 1e6
 
     # end to end through the host entry point: pinned inputs in, results out
+    # (sw_batch_align_host_dense: scores, end cells and the CIGARs packed)
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -509,29 +510,32 @@ def main():
         n = wl.n_pairs
         h_score = torch.zeros(n, dtype=torch.int32).pin_memory()
         h_end = torch.zeros(2 * n, dtype=torch.int32).pin_memory()
-        cig = None
         h2d = sum(t.numel() * t.element_size() for t in (h_reads, h_wins, h_roff, h_woff))
         d2h = (h_score.numel() + h_end.numel()) * 4
+
         if want_cigar:
-            cap = 2 * wl.pair_read_lengths + 3
-            coff = np.zeros(n + 1, np.int64)
-            np.cumsum(cap, out=coff[1:])
-            h_coff = pin(coff)
-            h_ops = torch.zeros(int(coff[-1]), dtype=torch.int32).pin_memory()
-            h_nops = torch.zeros(n, dtype=torch.int32).pin_memory()
-            cig = (h_ops, h_coff, h_nops)
-            h2d += h_coff.numel() * 8
-            d2h += (h_ops.numel() + h_nops.numel()) * 4
-        sw.sw_batch_align_host(h_reads, h_roff, h_wins, h_woff, n, SCORING, h_score, h_end, cig)
+            h_ops = torch.zeros(int(2 * wl.read_offsets[-1] + 3 * n), dtype=torch.int32).pin_memory()
+            h_offs = torch.zeros(n + 1, dtype=torch.int64).pin_memory()
+
+            def call():
+                sw.sw_batch_align_host_dense(h_reads, h_roff, h_wins, h_woff, n, SCORING, h_score, h_end, h_ops,
+                                             h_offs)
+        else:
+            def call():
+                sw.sw_batch_align_host(h_reads, h_roff, h_wins, h_woff, n, SCORING, h_score, h_end, None)
+        call()
+        if want_cigar:
+            d2h += h_offs.numel() * 8 + int(h_offs[-1]) * 4
         e_times = []
         for _ in range(max(3, min(args.steps, 5))):
             t0 = time.perf_counter()
-            sw.sw_batch_align_host(h_reads, h_roff, h_wins, h_woff, n, SCORING, h_score, h_end, cig)
+            call()
             e_times.append(time.perf_counter() - t0)
         e2e_cells, e2e_s = reduce_run(cells, sum(e_times) / len(e_times))
         e2e_reads, _ = reduce_run(n_reads, 0.0)
         e2e = {"value": e2e_cells / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "reads_per_s": e2e_reads / e2e_s}
+               "d2h_bytes_per_step": int(d2h), "reads_per_s": e2e_reads / e2e_s,
+               "api": "sw_batch_align_host_dense" if want_cigar else "sw_batch_align_host"}
 
     filt = None
     if not args.no_filter:

@@ -143,7 +143,11 @@ int sw_batch_align_indexed(const uint8_t *reads, const int64_t *read_offsets, in
  * score, end and CIGAR back to the host buffers and waits for `stream`.
  * Pointers are host memory (pinned memory makes the copies asynchronous);
  * out_cigar's members are host pointers too.  Returns after the results are
- * in host memory.
+ * in host memory.  Large batches go in two chunks whose copies overlap the
+ * other chunk's kernels.  When out_cigar->ops is pinned host memory the
+ * device can address, the device writes each pair's used runs straight into
+ * its slot and leaves the rest of the slot untouched; otherwise whole slots
+ * are copied back.
  */
 int sw_batch_align_host(const uint8_t *reads, const int64_t *read_offsets,
                         const uint8_t *windows, const int64_t *window_offsets,
@@ -268,6 +272,23 @@ int sw_batch_align_noalloc(const uint8_t *reads, const int64_t *read_offsets,
                            const uint8_t *windows, const int64_t *window_offsets,
                            int64_t n_pairs, const sw_scoring_t *scoring,
                            int32_t *out_score, int32_t *out_end, sw_stream_t stream);
+
+/*
+ * sw_batch_align_host_dense -- sw_batch_align_host with the CIGARs packed
+ * densely for the host: pair p's runs come back in ops_out[offsets_out[p] ..
+ * offsets_out[p+1]), offsets_out has n_pairs + 1 entries and
+ * offsets_out[n_pairs] is the total.  The library sizes the device-side
+ * CIGAR slots itself (2m + 3 runs per pair) and compacts them on the device,
+ * so only the runs cross the host link.  ops_cap is the room in ops_out;
+ * when the runs need more, ops_out holds the first ops_cap of them,
+ * offsets_out is complete and the call returns SW_ERR_CAPACITY.  All
+ * pointers are host memory (pinned for asynchronous copies).  Returns after
+ * the results are in host memory.
+ */
+int sw_batch_align_host_dense(const uint8_t *reads, const int64_t *read_offsets, const uint8_t *windows,
+                              const int64_t *window_offsets, int64_t n_pairs, const sw_scoring_t *scoring,
+                              int32_t *out_score, int32_t *out_end, uint32_t *ops_out, int64_t ops_cap,
+                              int64_t *offsets_out, sw_stream_t stream);
 
 /*
  * Capturable execution of a fixed-shape batch (pattern: one plan, many

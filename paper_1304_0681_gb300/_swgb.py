@@ -24,7 +24,7 @@ ERRORS = {
 EXPORTS = ("sw_cigar_capacity", "sw_packed_bytes", "sw_batch_align", "sw_batch_align_indexed",
            "sw_batch_align_host", "sw_sync_status", "sw_strerror", "sw_launch_count", "sw_set_plan", "sw_set_traceback_mode",
            "sw_last_traceback_split", "sw_plan_create", "sw_plan_align", "sw_plan_status", "sw_plan_destroy",
-           "sw_records", "sw_junction_table_words", "sw_junction_table_clear", "sw_junctions_detect",
+           "sw_batch_align_host_dense", "sw_records", "sw_junction_table_words", "sw_junction_table_clear", "sw_junctions_detect",
            "sw_junctions_export",
            "sw_plan_rows", "sw_alu_probe", "sw_phase_timing", "sw_phase_times", "sw_batch_align_noalloc",
            "sw_batch_align_masked", "sw_filter_features", "sw_mlp_bytes", "sw_mlp_init", "sw_mlp_refresh",
@@ -106,6 +106,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_plan_status.restype = ctypes.c_int
     lib.sw_plan_destroy.argtypes = [p]
     lib.sw_plan_destroy.restype = ctypes.c_int
+    lib.sw_batch_align_host_dense.argtypes = [p, p, p, p, i64, ctypes.POINTER(Scoring), p, p, p, i64, p, p]
+    lib.sw_batch_align_host_dense.restype = ctypes.c_int
     lib.sw_records.argtypes = [p, p, ctypes.POINTER(Cigar), i64, p, p, p, i32, p, p, p]
     lib.sw_records.restype = ctypes.c_int
     lib.sw_junction_table_words.argtypes = [i64]
@@ -186,6 +188,17 @@ def sw_batch_align_host(reads, read_offsets, windows, window_offsets, n_pairs: i
                                     int(n_pairs), ctypes.byref(sc), _ptr(out_score), _ptr(out_end),
                                     ctypes.byref(cg) if cg is not None else None, _stream(stream)),
            "sw_batch_align_host")
+
+
+def sw_batch_align_host_dense(reads, read_offsets, windows, window_offsets, n_pairs: int, scoring, out_score,
+                              out_end, ops_out, offsets_out, stream=None) -> None:
+    """Host tensors; CIGARs come back packed: pair p's runs are
+    ops_out[offsets_out[p]:offsets_out[p+1]]."""
+    sc = _scoring(scoring)
+    _check(_lib.sw_batch_align_host_dense(_ptr(reads), _ptr(read_offsets), _ptr(windows), _ptr(window_offsets),
+                                          int(n_pairs), ctypes.byref(sc), _ptr(out_score), _ptr(out_end),
+                                          _ptr(ops_out), int(ops_out.numel()), _ptr(offsets_out), _stream(stream)),
+           "sw_batch_align_host_dense")
 
 
 def sw_batch_align_noalloc(reads, read_offsets, windows, window_offsets, n_pairs: int, scoring, out_score, out_end,

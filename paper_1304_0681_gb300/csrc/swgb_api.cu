@@ -37,6 +37,8 @@ constexpr double kTile16FreeShare = 0.4;
 constexpr size_t kTile16Cap = (size_t)64 << 30;
 constexpr int kMaxDevices = 64;
 constexpr int kAuxStreams = 4;
+constexpr int kHostChunks = 2;                 // sw_batch_align_host pipelines a batch in this many chunks
+constexpr int64_t kHostChunkMin = 65536;       // ... of at least this many pairs
 constexpr bool kConcurrentTbParts = false;
 
 struct Buffer {
@@ -70,6 +72,10 @@ struct DeviceState {
     cudaStream_t aux[kAuxStreams] = {};
     cudaEvent_t fork_ev = nullptr;
     cudaEvent_t join_ev[kAuxStreams] = {};
+    // sw_batch_align_host: copy streams and per-chunk events
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    cudaEvent_t host_in_ev[kHostChunks] = {};
+    cudaEvent_t host_out_ev = nullptr;
     std::mutex mu;
 };
 
@@ -137,6 +143,11 @@ int device_state(DeviceState **out)
             if (cudaEventCreateWithFlags(&s.join_ev[k], cudaEventDisableTiming) != cudaSuccess) return SW_ERR_CUDA;
         }
         if (cudaEventCreateWithFlags(&s.fork_ev, cudaEventDisableTiming) != cudaSuccess) return SW_ERR_CUDA;
+        if (cudaStreamCreateWithFlags(&s.copy_in, cudaStreamNonBlocking) != cudaSuccess) return SW_ERR_CUDA;
+        if (cudaStreamCreateWithFlags(&s.copy_out, cudaStreamNonBlocking) != cudaSuccess) return SW_ERR_CUDA;
+        for (cudaEvent_t &e : s.host_in_ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SW_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&s.host_out_ev, cudaEventDisableTiming) != cudaSuccess) return SW_ERR_CUDA;
         s.ready = true;
     }
     *out = &s;
@@ -857,30 +868,90 @@ int sw_batch_align_host(const uint8_t *reads, const int64_t *read_offsets, const
         if ((rc = ensure(ds->stage, off))) return rc;
     }
     uint8_t *b = (uint8_t *)ds->stage.ptr;
+    // The batch goes in chunks of pairs through one device copy of it: chunk
+    // c+1's inputs are copied in (copy stream) while chunk c computes (the
+    // caller's stream) and chunk c-1's outputs are copied out (a second copy
+    // stream).  Every chunk uses the batch's own offsets into the shared copy.
+    // (with a CIGAR one chunk: measured, the chunks' copies slowed the kernels
+    // more than the overlap saved)
+    const int64_t n_split = out_cigar ? 1 : kHostChunks;
+    const int64_t chunk = std::max<int64_t>(kHostChunkMin, (n_pairs + n_split - 1) / n_split);
+    const int64_t n_chunks = (n_pairs + chunk - 1) / chunk;
     auto h2d = [&](size_t o, const void *src, size_t n) {
-        return n == 0 || cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, st) == cudaSuccess;
+        return n == 0 || cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, ds->copy_in) == cudaSuccess;
     };
     auto d2h = [&](void *dst, size_t o, size_t n) {
-        return n == 0 || cudaMemcpyAsync(dst, b + o, n, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+        return n == 0 || cudaMemcpyAsync(dst, b + o, n, cudaMemcpyDeviceToHost, ds->copy_out) == cudaSuccess;
     };
-    if (!h2d(o_r, reads, rb) || !h2d(o_w, windows, wb) || !h2d(o_ro, read_offsets, 8 * (n_pairs + 1)) ||
-        !h2d(o_wo, window_offsets, 8 * (n_pairs + 1)))
-        return SW_ERR_CUDA;
-    sw_cigar_t dc{};
+    // the whole words holding bases [q0, q1)
+    auto word_bytes = [](int64_t q0, int64_t q1, int64_t total, int64_t &lo, int64_t &n) {
+        lo = (q0 >> 4) * 4;
+        n = std::min<int64_t>(total, ((q1 + 15) >> 4) * 4) - lo;
+        if (n < 0) n = 0;
+    };
+    auto copy_in = [&](int64_t c) -> bool {
+        const int64_t p0 = c * chunk, p1 = std::min<int64_t>(n_pairs, p0 + chunk);
+        int64_t lo = 0, n = 0;
+        word_bytes(read_offsets[p0], read_offsets[p1], rb, lo, n);
+        if (!h2d(o_r + lo, reads + lo, n)) return false;
+        word_bytes(window_offsets[p0], window_offsets[p1], wb, lo, n);
+        if (!h2d(o_w + lo, windows + lo, n)) return false;
+        if (!h2d(o_ro + 8 * p0, read_offsets + p0, 8 * (p1 - p0 + 1))) return false;
+        if (!h2d(o_wo + 8 * p0, window_offsets + p0, 8 * (p1 - p0 + 1))) return false;
+        if (out_cigar && !h2d(o_co + 8 * p0, out_cigar->offsets + p0, 8 * (p1 - p0 + 1))) return false;
+        return cudaEventRecord(ds->host_in_ev[c % kHostChunks], ds->copy_in) == cudaSuccess;
+    };
+    // CIGAR runs go straight into the caller's slots when its op buffer is
+    // pinned host memory the device can address; else the slots are copied
+    uint32_t *host_ops_dev = nullptr;
     if (out_cigar) {
-        if (!h2d(o_co, out_cigar->offsets, 8 * (n_pairs + 1))) return SW_ERR_CUDA;
-        dc.ops = (uint32_t *)(b + o_ops);
-        dc.offsets = (const int64_t *)(b + o_co);
-        dc.n_ops = (int32_t *)(b + o_cn);
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, out_cigar->ops) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+            at.devicePointer)
+            host_ops_dev = (uint32_t *)at.devicePointer;
+        cudaGetLastError();  // a pageable pointer is not an error here
     }
-    PairSet ps{(const uint32_t *)(b + o_r), (const int64_t *)(b + o_ro), nullptr, (const uint32_t *)(b + o_w),
-               (const int64_t *)(b + o_wo)};
-    rc = run_batch(ps, n_pairs, n_pairs, scoring, (int32_t *)(b + o_s), (int32_t *)(b + o_e),
-                   out_cigar ? &dc : nullptr, st);
-    if (rc) return rc;
-    if (!d2h(out_score, o_s, 4 * n_pairs) || !d2h(out_end, o_e, 8 * n_pairs)) return SW_ERR_CUDA;
-    if (out_cigar && (!d2h(out_cigar->n_ops, o_cn, 4 * n_pairs) || !d2h(out_cigar->ops, o_ops, 4 * n_cig)))
-        return SW_ERR_CUDA;
+    // the copy streams start after what the caller enqueued on st
+    if (cudaEventRecord(ds->fork_ev, st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cudaStreamWaitEvent(ds->copy_in, ds->fork_ev, 0) != cudaSuccess) return SW_ERR_CUDA;
+    if (cudaStreamWaitEvent(ds->copy_out, ds->fork_ev, 0) != cudaSuccess) return SW_ERR_CUDA;
+    if (!copy_in(0)) return SW_ERR_CUDA;
+    for (int64_t c = 0; c < n_chunks; ++c) {
+        const int64_t p0 = c * chunk, p1 = std::min<int64_t>(n_pairs, p0 + chunk), np = p1 - p0;
+        // the next chunk's inputs, queued before this chunk's host waits
+        if (c + 1 < n_chunks) {
+            // its event slot must be free: the chunk kHostChunks back has started
+            if (!copy_in(c + 1)) return SW_ERR_CUDA;
+        }
+        if (cudaStreamWaitEvent(st, ds->host_in_ev[c % kHostChunks], 0) != cudaSuccess) return SW_ERR_CUDA;
+        sw_cigar_t dc{};
+        if (out_cigar) {
+            dc.ops = (uint32_t *)(b + o_ops);
+            dc.offsets = (const int64_t *)(b + o_co) + p0;
+            dc.n_ops = (int32_t *)(b + o_cn) + p0;
+        }
+        PairSet ps{(const uint32_t *)(b + o_r), (const int64_t *)(b + o_ro) + p0, nullptr,
+                   (const uint32_t *)(b + o_w), (const int64_t *)(b + o_wo) + p0};
+        rc = run_batch(ps, np, np, scoring, (int32_t *)(b + o_s) + p0, (int32_t *)(b + o_e) + 2 * p0,
+                       out_cigar ? &dc : nullptr, st);
+        if (rc) return rc;
+        if (host_ops_dev &&
+            (rc = launch_cigar_to_host(dc.ops, dc.offsets, dc.n_ops, np, host_ops_dev, st)))
+            return rc;
+        // this chunk's outputs, once its kernels are done
+        if (cudaEventRecord(ds->host_out_ev, st) != cudaSuccess) return SW_ERR_CUDA;
+        if (cudaStreamWaitEvent(ds->copy_out, ds->host_out_ev, 0) != cudaSuccess) return SW_ERR_CUDA;
+        if (!d2h(out_score + p0, o_s + 4 * p0, 4 * np) || !d2h(out_end + 2 * p0, o_e + 8 * p0, 8 * np))
+            return SW_ERR_CUDA;
+        if (out_cigar) {
+            const int64_t c0 = out_cigar->offsets[p0], c1 = out_cigar->offsets[p1];
+            if (!d2h(out_cigar->n_ops + p0, o_cn + 4 * p0, 4 * np)) return SW_ERR_CUDA;
+            if (!host_ops_dev && !d2h(out_cigar->ops + c0, o_ops + 4 * c0, 4 * (c1 - c0))) return SW_ERR_CUDA;
+        }
+    }
+    // st ends after the last copy out
+    if (cudaEventRecord(ds->host_out_ev, ds->copy_out) != cudaSuccess) return SW_ERR_CUDA;
+    if (cudaStreamWaitEvent(st, ds->host_out_ev, 0) != cudaSuccess) return SW_ERR_CUDA;
     return read_status(ds, st);
 }
 
@@ -1073,6 +1144,79 @@ int sw_plan_destroy(sw_plan_t *plan)
     if (prev >= 0) cudaSetDevice(prev);
     delete plan;
     return SW_OK;
+}
+
+int sw_batch_align_host_dense(const uint8_t *reads, const int64_t *read_offsets, const uint8_t *windows,
+                              const int64_t *window_offsets, int64_t n_pairs, const sw_scoring_t *scoring,
+                              int32_t *out_score, int32_t *out_end, uint32_t *ops_out, int64_t ops_cap,
+                              int64_t *offsets_out, sw_stream_t stream)
+{
+    int rc = check_common(reads, read_offsets, windows, window_offsets, n_pairs, scoring, out_score, out_end,
+                          nullptr);
+    if (rc) return rc;
+    if (!offsets_out || ops_cap < 0 || (ops_cap > 0 && !ops_out)) return SW_ERR_INVALID_ARG;
+    if (n_pairs == 0) {
+        offsets_out[0] = 0;
+        return SW_OK;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    DeviceState *ds = nullptr;
+    if ((rc = device_state(&ds))) return rc;
+    const int64_t rb = sw_packed_bytes(read_offsets[n_pairs]);
+    const int64_t wb = sw_packed_bytes(window_offsets[n_pairs]);
+    // device slots of 2m + 3 runs per pair
+    const int64_t n_slots = 2 * (read_offsets[n_pairs] - read_offsets[0]) + 3 * n_pairs;
+    const int64_t dense_cap = std::min<int64_t>(std::max<int64_t>(ops_cap, 1), n_slots);
+    const int64_t n_blk = (n_pairs + 255) / 256;
+    size_t off = 0;
+    const size_t o_r = off; off = align_up(off + rb, 256);
+    const size_t o_w = off; off = align_up(off + wb, 256);
+    const size_t o_ro = off; off = align_up(off + 8 * (n_pairs + 1), 256);
+    const size_t o_wo = off; off = align_up(off + 8 * (n_pairs + 1), 256);
+    const size_t o_s = off; off = align_up(off + 4 * n_pairs, 256);
+    const size_t o_e = off; off = align_up(off + 8 * n_pairs, 256);
+    const size_t o_co = off; off = align_up(off + 8 * (n_pairs + 1), 256);
+    const size_t o_cn = off; off = align_up(off + 4 * n_pairs, 256);
+    const size_t o_ops = off; off = align_up(off + 4 * n_slots, 256);
+    const size_t o_do = off; off = align_up(off + 8 * (n_pairs + 1), 256);
+    const size_t o_dense = off; off = align_up(off + 4 * dense_cap, 256);
+    const size_t o_blk = off; off = align_up(off + 8 * n_blk, 256);
+    {
+        std::lock_guard<std::mutex> lk(ds->mu);
+        if ((rc = ensure(ds->stage, off))) return rc;
+    }
+    uint8_t *b = (uint8_t *)ds->stage.ptr;
+    auto h2d = [&](size_t o, const void *src, size_t n) {
+        return n == 0 || cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    };
+    auto d2h = [&](void *dst, size_t o, size_t n) {
+        return n == 0 || cudaMemcpyAsync(dst, b + o, n, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    };
+    if (!h2d(o_r, reads, rb) || !h2d(o_w, windows, wb) || !h2d(o_ro, read_offsets, 8 * (n_pairs + 1)) ||
+        !h2d(o_wo, window_offsets, 8 * (n_pairs + 1)))
+        return SW_ERR_CUDA;
+    int64_t *cig_off = (int64_t *)(b + o_co), *blk = (int64_t *)(b + o_blk);
+    if ((rc = launch_cap_offsets((const int64_t *)(b + o_ro), n_pairs, cig_off, blk, st))) return rc;
+    // the slots are counted from the first read's start
+    sw_cigar_t dc{(uint32_t *)(b + o_ops), cig_off, (int32_t *)(b + o_cn)};
+    PairSet ps{(const uint32_t *)(b + o_r), (const int64_t *)(b + o_ro), nullptr, (const uint32_t *)(b + o_w),
+               (const int64_t *)(b + o_wo)};
+    if ((rc = run_batch(ps, n_pairs, n_pairs, scoring, (int32_t *)(b + o_s), (int32_t *)(b + o_e), &dc, st)))
+        return rc;
+    int64_t *doff = (int64_t *)(b + o_do);
+    if ((rc = launch_dense_cigar(dc.ops, cig_off, dc.n_ops, n_pairs, doff, (uint32_t *)(b + o_dense), dense_cap, blk,
+                                 st)))
+        return rc;
+    if (!d2h(out_score, o_s, 4 * n_pairs) || !d2h(out_end, o_e, 8 * n_pairs) ||
+        !d2h(offsets_out, o_do, 8 * (n_pairs + 1)))
+        return SW_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
+    const int64_t total = offsets_out[n_pairs];
+    const int64_t n_copy = std::min<int64_t>(total, ops_cap);
+    if (!d2h(ops_out, o_dense, 4 * n_copy)) return SW_ERR_CUDA;
+    rc = read_status(ds, st);
+    if (rc) return rc;
+    return total > ops_cap ? SW_ERR_CAPACITY : SW_OK;
 }
 
 // ---- Stage E, task iv ---------------------------------------------------

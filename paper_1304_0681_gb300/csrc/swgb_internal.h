@@ -159,6 +159,13 @@ int launch_table_clear(uint64_t *table, int64_t capacity, cudaStream_t st);
 int launch_table_export(const uint64_t *table, int64_t capacity, sw_junction_t *out, int64_t max_out,
                         int64_t *out_count, cudaStream_t st);
 
+int launch_cigar_to_host(const uint32_t *ops, const int64_t *off, const int32_t *n_ops, int64_t n_pairs,
+                         uint32_t *host_ops, cudaStream_t st);
+
+int launch_cap_offsets(const int64_t *read_off, int64_t n_pairs, int64_t *cig_off, int64_t *blk, cudaStream_t st);
+int launch_dense_cigar(const uint32_t *ops, const int64_t *off, const int32_t *n_ops, int64_t n_pairs,
+                       int64_t *doff, uint32_t *dense, int64_t dense_cap, int64_t *blk, cudaStream_t st);
+
 void count_launch(int n = 1);
 
 }  // namespace swgb

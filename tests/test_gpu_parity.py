@@ -160,10 +160,15 @@ def test_indexed_candidates():
     assert_parity(wl, got, DEFAULT, pairs=np.sort(rng.choice(wl.n_pairs, 800, replace=False)))
 
 
-def test_host_entry_point():
+@pytest.mark.parametrize("workload,n_reads,sample", [("parity", 300, None), ("uneven", 230_000, 2500)])
+def test_host_entry_point(workload, n_reads, sample):
+    """Host buffers in and out.  The large case runs in several pipelined
+    chunks (copies of one chunk overlapping the next chunk's kernels); it is
+    checked on a sample that includes the chunk borders, and as a whole
+    against the device entry point."""
     import torch
     import paper_1304_0681_gb300 as sw
-    wl = synth.generate("parity", seed=7, n_reads=300)
+    wl = synth.generate(workload, seed=7, n_reads=n_reads)
     n = wl.n_pairs
     cap = 2 * wl.pair_read_lengths + 3
     coff = np.zeros(n + 1, np.int64)
@@ -179,7 +184,50 @@ def test_host_entry_point():
     got = {"score": score.numpy().astype(np.int64), "i_end": e[:, 0].astype(np.int64),
            "j_end": e[:, 1].astype(np.int64), "ops": ops.numpy().view(np.uint32), "cigar_offsets": coff,
            "n_ops": nops.numpy().astype(np.int64)}
-    assert_parity(wl, got, DEFAULT)
+    if sample is None:
+        assert_parity(wl, got, DEFAULT)
+        return
+    rng = np.random.default_rng(5)
+    chunk = max(65536, (n + 3) // 4)
+    borders = np.array([c * chunk + d for c in range(1, 4) for d in (-2, -1, 0, 1) if 0 <= c * chunk + d < n])
+    pairs = np.union1d(rng.choice(n, sample, replace=False), borders)
+    assert_parity(wl, got, DEFAULT, pairs=pairs)
+    dev = run_gpu(wl, DEFAULT)
+    np.testing.assert_array_equal(got["score"], dev["score"])
+    np.testing.assert_array_equal(got["n_ops"], dev["n_ops"])
+
+
+def test_host_dense_entry_point():
+    """Host buffers in, CIGARs back packed: equal pair by pair to the
+    device entry point's (and so to the oracle's); too little room gives
+    SW_ERR_CAPACITY with complete offsets."""
+    import torch
+    import paper_1304_0681_gb300 as sw
+    wl = synth.generate("uneven", seed=8, n_reads=3000)
+    n = wl.n_pairs
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    args = (t(wl.packed_reads()), t(wl.read_offsets), t(wl.packed_windows()), t(wl.window_offsets), n, DEFAULT)
+    score = torch.zeros(n, dtype=torch.int32).pin_memory()
+    end = torch.zeros(2 * n, dtype=torch.int32).pin_memory()
+    ops = torch.zeros(40 * n, dtype=torch.int32).pin_memory()
+    offs = torch.zeros(n + 1, dtype=torch.int64).pin_memory()
+    sw.sw_batch_align_host_dense(*args, score, end, ops, offs)
+    dev = run_gpu(wl, DEFAULT)
+    np.testing.assert_array_equal(score.numpy(), dev["score"])
+    np.testing.assert_array_equal(end.numpy().reshape(-1, 2)[:, 0], dev["i_end"])
+    o = offs.numpy()
+    np.testing.assert_array_equal(np.diff(o), dev["n_ops"])
+    flat = ops.numpy().view(np.uint32)
+    for p in range(n):
+        c0 = dev["cigar_offsets"][p]
+        np.testing.assert_array_equal(flat[o[p]:o[p + 1]], dev["ops"][c0:c0 + dev["n_ops"][p]])
+    small = torch.zeros(int(o[-1]) - 1, dtype=torch.int32).pin_memory()
+    offs2 = torch.zeros(n + 1, dtype=torch.int64).pin_memory()
+    with pytest.raises(sw.SwError) as e:
+        sw.sw_batch_align_host_dense(*args, score, end, small, offs2)
+    assert e.value.code == -2
+    np.testing.assert_array_equal(offs2.numpy(), o)
+    np.testing.assert_array_equal(small.numpy().view(np.uint32), flat[:len(small)])
 
 
 def test_errors_are_reported():
