@@ -48,6 +48,7 @@
 // the host picks such plans only for classes whose score bound allows it);
 // pairs with larger possible scores use 32-bit
 // keys built from each half (MODE_I16W) or the int32 mode.
+#include "sw_band.cuh"
 #include "sw_device.cuh"
 #include "swgb_internal.h"
 
@@ -361,19 +362,27 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
             bestA = max(bestA, __shfl_sync(FULL, bestA, src));
             if (PAIR2) bestB = max(bestB, __shfl_sync(FULL, bestB, src));
         }
-        if (on && k == 0) {
+        // outputs, and with a traceback to follow, each pair's traceback cost
+        // key (the key pass folded into this epilogue)
 #pragma unroll
-            for (int h2 = 0; h2 < (PAIR2 ? 2 : 1); ++h2) {
-                const int64_t it = item + h2;
-                if (it < L.n_items) {
-                    const uint64_t b = h2 ? bestB : bestA;
-                    const int32_t p = L.order[it];
-                    const uint32_t sc = key_h(b);
-                    L.out_score[p] = (int32_t)sc;
-                    L.out_end[2 * p] = sc ? key_i(b) : -1;
-                    L.out_end[2 * p + 1] = sc ? key_j(b) : -1;
+        for (int h2 = 0; h2 < (PAIR2 ? 2 : 1); ++h2) {
+            const int64_t it = item + h2;
+            int32_t tkey = -1, need32 = 0, wc = 0;
+            bool big = false;
+            if (on && k == 0 && it < L.n_items) {
+                const uint64_t b = h2 ? bestB : bestA;
+                const int32_t p = L.order[it];
+                const uint32_t sc = key_h(b);
+                const int32_t ie = sc ? key_i(b) : -1, je = sc ? key_j(b) : -1;
+                L.out_score[p] = (int32_t)sc;
+                L.out_end[2 * p] = ie;
+                L.out_end[2 * p + 1] = je;
+                if (L.tb_keys) {
+                    tb_cost_key(L.cls, (int32_t)sc, ie, je, L.small_slab_words, L.sc, tkey, need32, wc, big);
+                    L.tb_keys[p] = tkey;
                 }
             }
+            if (L.tb_keys) tb_key_atomics(tkey, L.cls, need32, wc, big, L.tb_hist, L.tb_info);
         }
     }
 }

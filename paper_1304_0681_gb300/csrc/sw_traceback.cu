@@ -35,6 +35,7 @@
 // main launch form a separate launch with larger slabs.
 #include <algorithm>
 
+#include "sw_band.cuh"
 #include "sw_device.cuh"
 #include "swgb_internal.h"
 
@@ -73,20 +74,12 @@ __device__ __forceinline__ TbPair tb_pair(const TbParams &P, int32_t p, int32_t 
         q.score = 0;
         return q;
     }
-    const int32_t ma = P.sc.ma, go = P.sc.go, ge = P.sc.ge;
-    const int32_t dend = q.je - q.ie;
-    int32_t dlo = -q.ie - 1;  // no lower limit when gaps are free
-    if (ge < 0) {
-        const int32_t num = ma * (q.ie + 1) + go - q.score;
-        dlo = dend - (num < 0 ? 0 : num / (-ge) + 1);
-    }
-    const int32_t inum = ma * (q.ie + 1) + go - ge - q.score;
-    const int32_t dhi = dend + (inum < 0 ? 0 : inum / (ma - ge));
-    q.jlo = max(0, dlo);
-    q.W = q.je - q.jlo + 1;
-    q.rows = q.ie + 1;
-    q.a = dlo - q.jlo;
-    q.b = dhi - q.jlo;
+    const Band bd = band_of(q.score, q.ie, q.je, P.sc);
+    q.jlo = bd.jlo;
+    q.W = bd.W;
+    q.rows = bd.rows;
+    q.a = bd.a;
+    q.b = bd.b;
     return q;
 }
 
@@ -154,41 +147,12 @@ __global__ void k_tb_keys(TbParams P, int64_t n_pairs, const int32_t *__restrict
         int32_t key = -1, cls = 0, need32 = 0, wc = 0;
         bool big = false;
         if (sk >= 0) {
-            const int32_t p = (int32_t)pp;
             cls = sk / N_NBUCKET;
-            const int T = P.lanes;
-            const TbPair t = tb_pair(P, p, nullptr);
-            const int64_t need = slab_need(t, T);
-            big = need > P.small_slab_words;
-            // big slabs first, each group by falling cost (rows x window, in
-            // ~19% and ~9% buckets) so that the longest tasks start first
-            const float cost = t.score > 0 ? (float)t.rows * (float)min(t.W, 8 * T + (t.b - t.a)) : 1.f;
-            if (big) {
-                const int cb = min(63, max(0, (int)(4.f * __log2f(cost)) - 40));
-                key = cls * N_NBUCKET + (63 - cb);
-            } else {
-                const int cb = min(191, max(0, (int)(8.f * __log2f(cost))));
-                key = cls * N_NBUCKET + 64 + (191 - cb);
-            }
-            need32 = (int32_t)(need < (int64_t)INT32_MAX ? need : (int64_t)INT32_MAX);
-            wc = need > 0 ? min(t.W, 8 * T + (t.b - t.a)) : 0;
+            const TbPair t = tb_pair(P, (int32_t)pp, nullptr);
+            tb_cost_key(cls, t.score, t.ie, t.je, P.small_slab_words, P.sc, key, need32, wc, big);
         }
         if (pp < n_pairs) tb_keys[pp] = key;
-        // the key fixes the class and whether the slab is big
-        const KeyGroup g = key_group(key);
-        if (key >= 0) {
-            const unsigned mx_need = __reduce_max_sync(g.mask, (unsigned)need32);
-            const unsigned mx_wc = __reduce_max_sync(g.mask, (unsigned)wc);
-            const unsigned n_big = __reduce_add_sync(g.mask, (unsigned)(big && need32 > 0));
-            if (g.rank == 0) {
-                atomicAdd(&hist[key], g.size);
-                if (mx_need > 0) {
-                    atomicMax(&info->max_need[cls], (int32_t)mx_need);
-                    atomicMax(&info->max_wcap[big ? 0 : 1][cls], (int32_t)mx_wc);
-                }
-                if (n_big) atomicAdd(&info->n_big[cls], (int32_t)n_big);
-            }
-        }
+        tb_key_atomics(key, cls, need32, wc, big, hist, info);
     }
 }
 

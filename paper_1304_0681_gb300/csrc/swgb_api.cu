@@ -299,6 +299,13 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
     if ((rc = ensure(ds->dyn, std::max<size_t>(need_dyn, 256)))) return rc;
 
     if (ds->timing && cudaEventRecord(ds->phase[1], st) != cudaSuccess) return SW_ERR_CUDA;
+    // with a CIGAR, the score kernels' epilogue also writes the traceback
+    // cost keys and the class table the traceback is sized from
+    if (cig) {
+        if (cudaMemsetAsync(hist, 0, sizeof(int32_t) * nh, st) != cudaSuccess) return SW_ERR_CUDA;
+        if (cudaMemsetAsync(tbinfo, 0, sizeof(TbClassInfo), st) != cudaSuccess) return SW_ERR_CUDA;
+        if (cudaMemsetAsync(tb_keys, 0xFF, sizeof(int32_t) * n_pairs, st) != cudaSuccess) return SW_ERR_CUDA;
+    }
     // one launch per class; several classes fork onto the auxiliary streams
     const int n_aux_score = runs.size() > 1 ? (int)std::min<size_t>(runs.size(), kAuxStreams) : 0;
     if (n_aux_score && (rc = fork_streams(ds, st, n_aux_score))) return rc;
@@ -317,6 +324,13 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         L.boundary_group_bytes = (int64_t)r.bnd_bytes_group;
         L.work_counter = counters + r.cls;
         L.status = &info->status;
+        if (cig) {
+            L.cls = r.cls;
+            L.tb_keys = tb_keys;
+            L.tb_hist = hist;
+            L.tb_info = tbinfo;
+            L.small_slab_words = kSmallSlabWords;
+        }
         if ((rc = launch_score(r.plan.rows, r.mode, L, r.score_blocks, kThreads, cs))) return rc;
     }
     if (n_aux_score && (rc = join_streams(ds, st, n_aux_score))) return rc;
@@ -325,9 +339,6 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         // order each class by traceback cost, then size the slabs from the
         // per-class maxima (a second, small read-back)
         TbParams P{ps, sc, out_score, out_end, cig->ops, cig->offsets, cig->n_ops, kTbLanes, kSmallSlabWords};
-        if (cudaMemsetAsync(hist, 0, sizeof(int32_t) * nh, st) != cudaSuccess) return SW_ERR_CUDA;
-        if (cudaMemsetAsync(tbinfo, 0, sizeof(TbClassInfo), st) != cudaSuccess) return SW_ERR_CUDA;
-        if ((rc = launch_tb_keys(P, n_pairs, keys, tb_keys, hist, tbinfo, st))) return rc;
         if ((rc = launch_scan_scatter(tb_keys, n_pairs, info->count, hist, bstart, cursor, tb_order, st))) return rc;
         if (cudaMemcpyAsync(ds->tbinfo_host, tbinfo, sizeof(TbClassInfo), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess)

@@ -62,6 +62,8 @@ struct ClassInfo {
     int32_t pad[3];
 };
 
+struct TbClassInfo;
+
 struct ScoreLaunch {
     PairSet ps;
     Scoring sc;
@@ -75,6 +77,12 @@ struct ScoreLaunch {
     int32_t *work_counter;
     int32_t *status;
     int32_t one = 1;         // a multiplier the compiler cannot fold
+    // traceback cost keys from the epilogue (tb_keys == nullptr: none)
+    int32_t cls = 0;         // the launch's class
+    int32_t *tb_keys = nullptr;
+    int32_t *tb_hist = nullptr;
+    TbClassInfo *tb_info = nullptr;
+    int32_t small_slab_words = 0;
 };
 
 // What every traceback kernel needs about the batch.
