@@ -639,9 +639,12 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
             // last lane overwrites it at step j + T - 1
             const uint32_t *bin = (c > 0 && k == 0) ? bnd : nullptr;
             uint32_t *bout = (c + 1 < chunks && k == T - 1) ? bnd : nullptr;
+            // a pair's window moves right by shift >= 0 from chunk to chunk; a
+            // pair without rows in this chunk reads the row at shift 0 (its
+            // values are never used)
             int shift[2];
-            shift[0] = lo[0] - prev_lo[0];
-            shift[1] = lo[1] - prev_lo[1];
+#pragma unroll
+            for (int x = 0; x < 2; ++x) shift[x] = hi[x] >= lo[x] ? max(lo[x] - prev_lo[x], 0) : 0;
             auto bload = [&](int x, int j) -> uint32_t {
                 return (bin && j >= 0 && j < prev_width) ? bin[((int64_t)j * G + g) * 2 + x] : 0u;
             };
@@ -661,6 +664,8 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
                 ws[x].start(P.ps.wins, a0, q[x].score > 0 ? q[x].ws + q[x].n : a0);
             }
             uint32_t out_h = 0u, out_f = 0u;
+            int64_t widx = tb16_word(c, 0, lane, S4);   // tile word of step t
+            int64_t bidx = ((int64_t)(0 - k) * G + g) * 2;  // boundary word of offset t - k
 
             for (int t = 0; t < steps; ++t) {
                 // the row above: from the lane before (its last step), or the
@@ -708,13 +713,14 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
                     }
                     // streaming store (the walk reads back a few words of it); a
                     // lane's four consecutive steps share one 32-byte sector
-                    __stcs(slab + tb16_word(c, t, lane, S4), make_uint2(w0, w1));
+                    __stcs(slab + widx, make_uint2(w0, w1));
                     out_h = hu;
                     out_f = f;
-                    if (bout)
-                        *(uint2 *)(bout + ((int64_t)jl * G + g) * 2) = make_uint2(prmt(hu, f, 0x5410u), prmt(hu, f, 0x7632u));
+                    if (bout) *(uint2 *)(bout + bidx) = make_uint2(prmt(hu, f, 0x5410u), prmt(hu, f, 0x7632u));
                     diag_in = up_h;
                 }
+                widx += (t & 3) == 3 ? 32 * 4 - 3 : 1;
+                bidx += 2 * G;
             }
             prev_lo[0] = lo[0];
             prev_lo[1] = lo[1];

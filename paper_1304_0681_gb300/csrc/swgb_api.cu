@@ -408,7 +408,7 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
                     t.wcap = (int32_t)(t.wcap + 8 * (T - 1));
                     const int64_t s4 = (t.wcap + T - 1 + 3) / 4;
                     t.slab_words = chunks_t * s4 * 8;                                      // per lane
-                    t.bnd_ints = chunks_t > 1 ? (int64_t)(32 / T) * 2 * t.wcap : 0;        // per warp
+                    t.bnd_ints = chunks_t > 1 ? (int64_t)(32 / T) * 2 * t.wcap : 0;  // per warp: one row
                 } else if (t.tiled) {
                     t.slab_words = chunks * t.wcap;
                     t.bnd_ints = chunks > 1 ? (int64_t)2 * 2 * t.wcap : 0;
