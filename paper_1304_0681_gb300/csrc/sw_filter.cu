@@ -67,11 +67,34 @@ __device__ __forceinline__ void count_kmers8(const uint32_t *__restrict__ buf, i
 
 constexpr int kByteCountMax = 258;
 
+// Byte counters of the 4-mers at positions first .. first + cnt - 1 of a
+// sequence (first + cnt <= len - 3): two 19-base loads, 16 k-mers each.
+__device__ __forceinline__ void count_run8(const uint32_t *__restrict__ buf, int64_t s, int32_t len, int first,
+                                           int cnt, uint32_t *hist)
+{
+    for (int h = 0; h < cnt; h += 16) {
+        const int q = first + h;
+        const int k = min(16, cnt - h);              // k-mers of this half
+        const int nb = min(k + 3, len - q);          // bases they span
+        const uint32_t lo = load_bases(buf, s + q, min(16, nb));
+        const uint32_t hi = nb > 16 ? load_bases(buf, s + q + 16, nb - 16) : 0u;
+        const uint64_t v = ((uint64_t)hi << 32) | lo;
+        for (int t = 0; t < k; ++t) {
+            const uint32_t w = (uint32_t)(v >> (2 * t)) & 0xFFu;
+            const uint32_t pre = ((w & 3u) << 4) | (((w >> 2) & 3u) << 2) | ((w >> 4) & 3u);
+            atomicAdd(&hist[pre], 1u << (8u * (w >> 6)));
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_features(FeatureParams P)
 {
     __shared__ uint32_t hist[8][2][256];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *hr = hist[warp][0], *hw = hist[warp][1];
+    // byte-counter path: four candidates at a time, 8 lanes and 64 words each
+    const int sg = lane >> 3, sl = lane & 7;
+    uint32_t *hs = hist[warp][1] + 64 * sg;
     for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < P.n_reads; r += (int64_t)gridDim.x * 8) {
         const int64_t c0 = P.cand_off[r], c1 = P.cand_off[r + 1];
         if (c0 >= c1) continue;
@@ -86,6 +109,43 @@ __global__ void __launch_bounds__(256) k_features(FeatureParams P)
         }
         __syncwarp();
         const float inv = m >= 4 ? 1.f / (float)(m - 3) : 0.f;
+        // the longest window of the read decides the path
+        int32_t nmax = 0;
+        for (int64_t p = c0 + lane; p < c1; p += 32) nmax = max(nmax, (int32_t)(P.win_off[p + 1] - P.win_off[p]));
+        nmax = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)nmax);
+        if (rbytes && nmax <= kByteCountMax) {
+            for (int64_t pb = c0; pb < c1; pb += 4) {
+                const int64_t p = pb + sg;
+                const bool live = p < c1;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) hs[8 * sl + q] = 0;
+                __syncwarp();
+                int32_t n = 0;
+                if (live) {
+                    const int64_t ws = P.win_off[p];
+                    n = (int32_t)(P.win_off[p + 1] - ws);
+                    const int nk = n - 3;
+                    // lane sl counts k-mers sl*32 .. sl*32+31
+                    if (m >= 4 && sl * 32 < nk) count_run8(P.wins, ws, n, sl * 32, min(32, nk - sl * 32), hs);
+                }
+                __syncwarp();
+                if (live) {
+                    uint32_t f2[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int k0 = 8 * sl + 2 * q;
+                        const uint32_t a = (uint32_t)__dp4a(__vminu4(hr[k0], hs[k0]), 0x01010101u, 0u);
+                        const uint32_t b = (uint32_t)__dp4a(__vminu4(hr[k0 + 1], hs[k0 + 1]), 0x01010101u, 0u);
+                        const __nv_bfloat162 f = __floats2bfloat162_rn((float)a * inv, (float)b * inv);
+                        f2[q] = *reinterpret_cast<const uint32_t *>(&f);
+                    }
+                    if (n < 4 || m < 4) f2[0] = f2[1] = f2[2] = f2[3] = 0u;
+                    reinterpret_cast<uint4 *>(P.out)[p * 8 + sl] = make_uint4(f2[0], f2[1], f2[2], f2[3]);
+                }
+                __syncwarp();
+            }
+            continue;
+        }
         for (int64_t p = c0; p < c1; ++p) {
             const int64_t ws = P.win_off[p];
             const int32_t n = (int32_t)(P.win_off[p + 1] - ws);
