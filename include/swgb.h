@@ -206,7 +206,16 @@ int sw_mlp_init(float *model, uint64_t seed, sw_stream_t stream);
 int sw_mlp_refresh(float *model, sw_stream_t stream);
 
 /* Predictions for n feature rows on the tensor cores (bf16 inputs and
- * weights, fp32 accumulation): out device float[n]. */
+ * weights, fp32 accumulation): out device float[n].  By default
+ * (SW_MLP_AUTO) the 5th-generation tensor cores compute both layers into
+ * tensor memory when `features` is 16-byte aligned; SW_MLP_MMA_SYNC (or
+ * 4-byte-aligned features) uses warp-level MMA instead.  Both round the
+ * hidden layer to bf16 and agree up to fp32 summation order.  A timed-out
+ * tensor-core wait is reported as SW_ERR_DEVICE_TIMEOUT by sw_sync_status.
+ * sw_set_mlp_kernel is process-wide; SW_ERR_INVALID_ARG for other values. */
+#define SW_MLP_AUTO 0
+#define SW_MLP_MMA_SYNC 1
+int sw_set_mlp_kernel(int32_t kind);
 int sw_mlp_forward(const float *model, const uint16_t *features, int64_t n, float *out, sw_stream_t stream);
 
 /* Gradient of mean((y - target)^2) over n samples (fp32 forward and

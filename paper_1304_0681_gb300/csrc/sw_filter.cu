@@ -20,6 +20,8 @@
 
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include "sw_device.cuh"
 #include "swgb_internal.h"
 
@@ -189,12 +191,6 @@ __global__ void __launch_bounds__(256) k_features(FeatureParams P)
 // --------------------------------------------------------- model layout
 
 // fp32 offsets into the model buffer (see include/swgb.h)
-constexpr int64_t MD_W1 = 0, MD_B1 = 16384, MD_W2 = 16640, MD_B2 = 33024, MD_W3 = 33088, MD_B3 = 33152;
-constexpr int64_t MD_NP = 33153;
-constexpr int64_t MD_M = MD_NP, MD_V = 2 * MD_NP, MD_G = 3 * MD_NP, MD_STEP = 4 * MD_NP;
-constexpr int64_t MD_W1T = 132616;          // bf16 [256][64], 16-byte aligned
-constexpr int64_t MD_W2T = MD_W1T + 8192;   // bf16 [64][256]
-constexpr int64_t MD_TOTAL = MD_W2T + 8192;
 
 // bf16 copies of the weights, transposed for the tensor-core B operands
 __global__ void k_mlp_refresh(float *model)
@@ -662,6 +658,8 @@ int launch_best_per_read(const int32_t *score, const int64_t *cand_off, int64_t 
 
 using namespace swgb;
 
+static std::atomic<int32_t> g_mlp_kind{SW_MLP_AUTO};  // set by sw_set_mlp_kernel
+
 static int sm_count_now(int *sms)
 {
     int dev = 0;
@@ -701,6 +699,13 @@ int sw_mlp_refresh(float *model, sw_stream_t stream)
     return launch_mlp_refresh(model, (cudaStream_t)stream);
 }
 
+int sw_set_mlp_kernel(int32_t kind)
+{
+    if (kind != SW_MLP_AUTO && kind != SW_MLP_MMA_SYNC) return SW_ERR_INVALID_ARG;
+    g_mlp_kind.store(kind);
+    return SW_OK;
+}
+
 int sw_mlp_forward(const float *model, const uint16_t *features, int64_t n, float *out, sw_stream_t stream)
 {
     if (n < 0 || !model || ((uintptr_t)model & 15u)) return SW_ERR_INVALID_ARG;
@@ -709,6 +714,12 @@ int sw_mlp_forward(const float *model, const uint16_t *features, int64_t n, floa
     int sms = 0;
     int rc = sm_count_now(&sms);
     if (rc) return rc;
+    // the tensor-memory kernel reads 16-byte feature rows
+    if (g_mlp_kind.load() == SW_MLP_AUTO && !((uintptr_t)features & 15u)) {
+        int32_t *status = nullptr;
+        if ((rc = aux_status_word((cudaStream_t)stream, &status))) return rc;
+        return launch_mlp_forward_tc(model, features, n, out, sms, status, (cudaStream_t)stream);
+    }
     return launch_mlp_forward(model, features, n, out, sms, (cudaStream_t)stream);
 }
 

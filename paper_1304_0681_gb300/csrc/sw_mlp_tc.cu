@@ -1,0 +1,311 @@
+// sw_mlp_tc.cu -- the candidate filter's network on the 5th-generation
+// tensor cores (tcgen05): 64 -> 256 -> 64 -> 1, bf16 operands, fp32
+// accumulation in tensor memory.
+//
+// One persistent CTA of 4 warps per SM holds both weight matrices in shared
+// memory and takes tiles of 128 pairs:
+//   1. the tile's features (128 x 64 bf16) are copied into shared memory;
+//   2. one thread issues four tcgen05.mma (M 128, N 256, K 16) into TMEM;
+//   3. each warp reads its 32 rows back with tcgen05.ld, adds b1, applies
+//      ReLU, rounds to bf16 and stores them as the next A operand;
+//   4. sixteen tcgen05.mma (M 128, N 64, K 16) compute layer 2 into TMEM;
+//   5. each thread reads its row, adds b2, applies ReLU and takes the dot
+//      product with w3 (+ b3) in fp32.
+// Operands use the K-major layout without swizzle: 8-row x 16-byte core
+// matrices, core matrices along K 128 bytes apart (leading byte offset) and
+// 8-row groups K/8 x 128 bytes apart (stride byte offset).  Completion of the
+// MMAs is signalled through an mbarrier that tcgen05.commit arrives on; every
+// wait on it is bounded and a timeout is reported, never waited out.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "sw_device.cuh"
+#include "swgb_internal.h"
+
+namespace swgb {
+
+namespace {
+
+constexpr int TC_ROWS = 128;        // pairs per tile (MMA M)
+constexpr uint32_t TC_TMEM_COLS = 512;  // the whole tensor memory (one CTA per SM)
+constexpr int64_t TC_WAIT_LIMIT = 1 << 20;  // polls of an mbarrier before giving up
+
+// shared memory layout (bytes)
+constexpr int SM_W1 = 0;                       // B of layer 1: 256 x 64 bf16
+constexpr int SM_W2 = SM_W1 + 256 * 64 * 2;    // B of layer 2: 64 x 256 bf16
+constexpr int SM_XSZ = 128 * 64 * 2;           // one X buffer
+constexpr int SM_X = SM_W2 + 64 * 256 * 2;     // A of layer 1: 2 x (128 x 64 bf16)
+constexpr int SM_H = SM_X + 2 * SM_XSZ;        // A of layer 2: 128 x 256 bf16
+constexpr int SM_B1 = SM_H + 128 * 256 * 2;    // 256 fp32
+constexpr int SM_B2 = SM_B1 + 256 * 4;         // 64 fp32
+constexpr int SM_W3 = SM_B2 + 64 * 4;          // 64 fp32
+constexpr int SM_PART = SM_W3 + 64 * 4;        // 128 fp32 partial dots
+constexpr int SM_BAR = SM_PART + 128 * 4;      // 2 mbarriers (16 B), TMEM base (4 B)
+constexpr int SM_USED = SM_BAR + 64;
+constexpr int SM_TOTAL = 227 * 1024;           // all of it: headroom past the used bytes
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (r, k) of a K-major bf16 operand with K columns
+__device__ __forceinline__ uint32_t kmajor_off(int r, int k, int K)
+{
+    return (uint32_t)((r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start, leading and stride byte offsets
+// (16-byte units), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor of kind::f16: fp32 D, bf16 A and B, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy writes to shared memory, visible to the tensor core's reads
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// bounded wait for the given phase of an mbarrier; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase)
+{
+    for (int64_t it = 0; it < TC_WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, P1;\n\t}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// 8 warps.  Tile t's layer-1 accumulator lives in TMEM columns 256 (t % 2) ..
+// +255 and its layer-2 accumulator in the first 64 of them, so the layer-1
+// MMA of tile t+1 runs on the tensor core while the warps finish tile t.
+// Features are double-buffered with asynchronous copies one tile ahead.
+__global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restrict__ model,
+                                                           const __nv_bfloat16 *__restrict__ feat, int64_t n,
+                                                           float *__restrict__ out, int32_t *status)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;  // TMEM lane quarter, column half
+    float *b1 = reinterpret_cast<float *>(smem + SM_B1);
+    float *b2 = reinterpret_cast<float *>(smem + SM_B2);
+    float *w3 = reinterpret_cast<float *>(smem + SM_W3);
+    float *part = reinterpret_cast<float *>(smem + SM_PART);  // layer-2 partial dots [128]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + SM_BAR);  // [0] layer 1, [1] layer 2
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM_BAR + 16);
+    const uint32_t s_base = smem_u32(smem);
+    const uint32_t bar1 = smem_u32(bar), bar2 = smem_u32(bar + 1);
+
+    {
+        const uint4 *g1 = reinterpret_cast<const uint4 *>(model + MD_W1T);  // [256][64] bf16
+        const uint4 *g2 = reinterpret_cast<const uint4 *>(model + MD_W2T);  // [64][256] bf16
+        for (int c = tid; c < 256 * 8; c += blockDim.x) {
+            const int r = c >> 3, k = (c & 7) * 8;
+            *reinterpret_cast<uint4 *>(smem + SM_W1 + kmajor_off(r, k, 64)) = g1[c];
+        }
+        for (int c = tid; c < 64 * 32; c += blockDim.x) {
+            const int r = c >> 5, k = (c & 31) * 8;
+            *reinterpret_cast<uint4 *>(smem + SM_W2 + kmajor_off(r, k, 256)) = g2[c];
+        }
+        for (int i = tid; i < 256; i += blockDim.x) b1[i] = model[MD_B1 + i];
+        for (int i = tid; i < 64; i += blockDim.x) {
+            b2[i] = model[MD_B2 + i];
+            w3[i] = model[MD_W3 + i];
+        }
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar2));
+    }
+    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    // the features of one tile into X buffer xb (rows past n read as zero)
+    auto load_x = [&](int64_t tile, int xb) {
+        const int64_t row0 = tile * TC_ROWS;
+        const uint4 *g = reinterpret_cast<const uint4 *>(feat);
+        for (int c = tid; c < TC_ROWS * 8; c += blockDim.x) {
+            const int r = c >> 3, k = (c & 7) * 8;
+            const bool in = row0 + r < n;
+            cp_async16(s_base + SM_X + xb * SM_XSZ + kmajor_off(r, k, 64), g + (in ? (row0 + r) * 8 + (c & 7) : 0),
+                       in ? 16u : 0u);
+        }
+        cp_async_commit();
+    };
+    int64_t tile = blockIdx.x;
+    if (tile < tiles) load_x(tile, 0);
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const float b3 = model[MD_B3];
+    uint32_t ph1 = 0, ph2 = 0;
+    bool ok = true;
+    auto layer1 = [&](int xb, uint32_t acc) {
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+            mma_bf16(acc, smem_desc(s_base + SM_X + xb * SM_XSZ + 256 * ks, 128, 1024),
+                     smem_desc(s_base + SM_W1 + 256 * ks, 128, 1024), idesc_bf16(128, 256), ks > 0);
+        mma_commit(bar1);
+    };
+    auto wait_all = [&](uint32_t bar, uint32_t &ph) -> bool {
+        const bool got = mbar_wait(bar, ph);
+        ph ^= 1u;
+        return __syncthreads_and(got) != 0;
+    };
+
+    // tile `tile` uses X buffer xb and accumulator columns 256 * xb
+    int xb = 0;
+    if (tile < tiles) {
+        cp_async_wait_all();
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) layer1(0, tmem);
+    }
+    for (; tile < tiles && ok; tile += gridDim.x, xb ^= 1) {
+        const int64_t next = tile + gridDim.x;
+        const uint32_t acc = tmem + 256u * (uint32_t)xb;
+        // the next tile's features, while this one computes
+        if (next < tiles) load_x(next, xb ^ 1);
+        ok = wait_all(bar1, ph1);  // layer 1 of this tile
+        fence_after_sync();
+        if (!ok) break;
+        // h = bf16(relu(D + b1)): warp (quarter, half) takes 32 rows x 128 columns
+        {
+            const int r = 32 * quarter + lane;
+            const uint32_t la = acc + ((uint32_t)(32 * quarter) << 16);
+            for (int c0 = 128 * half; c0 < 128 * half + 128; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(la + (uint32_t)c0, v);
+                tmem_wait_ld();
+                uint32_t pk[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float x0 = fmaxf(__uint_as_float(v[2 * j]) + b1[c0 + 2 * j], 0.f);
+                    const float x1 = fmaxf(__uint_as_float(v[2 * j + 1]) + b1[c0 + 2 * j + 1], 0.f);
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+                    pk[j] = *reinterpret_cast<const uint32_t *>(&h);
+                }
+                *reinterpret_cast<uint4 *>(smem + SM_H + kmajor_off(r, c0, 256)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4 *>(smem + SM_H + kmajor_off(r, c0 + 8, 256)) =
+                    make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+        }
+        // the next tile's features have landed (each thread waits for its own
+        // copies; the barrier below publishes them)
+        cp_async_wait_all();
+        fence_async_smem();
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+        if (tid == 0) {
+            // layer 2 of this tile (first 64 columns of its accumulator), then
+            // layer 1 of the next tile into the other accumulator
+#pragma unroll
+            for (int ks = 0; ks < 16; ++ks)
+                mma_bf16(acc, smem_desc(s_base + SM_H + 256 * ks, 128, 4096),
+                         smem_desc(s_base + SM_W2 + 256 * ks, 128, 4096), idesc_bf16(128, 64), ks > 0);
+            mma_commit(bar2);
+            if (next < tiles) layer1(xb ^ 1, tmem + 256u * (uint32_t)(xb ^ 1));
+        }
+        ok = wait_all(bar2, ph2);
+        fence_after_sync();
+        if (!ok) break;
+        // y = w3 . relu(D + b2) + b3: warp (quarter, half) sums 32 of the 64 columns
+        {
+            float accv = 0.f;
+            const uint32_t la = acc + ((uint32_t)(32 * quarter) << 16);
+            for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(la + (uint32_t)c0, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) accv += fmaxf(__uint_as_float(v[j]) + b2[c0 + j], 0.f) * w3[c0 + j];
+            }
+            const int r = 32 * quarter + lane;
+            if (half == 1) part[r] = accv;
+            fence_before_sync();
+            __syncthreads();
+            fence_after_sync();
+            const int64_t row = tile * TC_ROWS + r;
+            if (half == 0 && row < n) out[row] = accv + part[r] + b3;
+        }
+    }
+    if (!ok && tid == 0) atomicOr(status, ST_TIMEOUT);
+    cp_async_wait_all();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
+}  // namespace
+
+int launch_mlp_forward_tc(const float *model, const uint16_t *feat, int64_t n, float *out, int sm_count,
+                          int32_t *status, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL) !=
+            cudaSuccess)
+            return SW_ERR_CUDA;
+        attr = true;
+    }
+    static_assert(SM_USED <= SM_TOTAL, "shared memory layout");
+    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, sm_count));
+    k_mlp_forward_tc<<<grid, 256, SM_TOTAL, st>>>(model, reinterpret_cast<const __nv_bfloat16 *>(feat), n, out,
+                                                   status);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+}
+
+}  // namespace swgb

@@ -42,7 +42,6 @@
 namespace swgb {
 
 constexpr unsigned FULLMASK = 0xffffffffu;
-constexpr int32_t TB_NEG = -(1 << 28);
 
 struct TbPair {
     int64_t rs, ws;

@@ -473,7 +473,7 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         if (n_aux_tb && (rc = fork_streams(ds, st, n_aux_tb))) return rc;
         for (size_t ti2 = 0; ti2 < tbr.size(); ++ti2) {
             const TbRun &t = tbr[ti2];
-            const cudaStream_t ts = n_aux_tb ? ds->aux[ti2 % n_aux_tb] : st;
+            const cudaStream_t ts = n_aux_tb ? ds->aux[ti2 % std::max(n_aux_tb, 1)] : st;
             uint8_t *region = (uint8_t *)ds->dyn.ptr + t.offset;
             TracebackLaunch B{};
             B.P = P;
@@ -1231,6 +1231,25 @@ int sw_batch_align_host_dense(const uint8_t *reads, const int64_t *read_offsets,
 }
 
 // ---- Stage E, task iv ---------------------------------------------------
+
+}  // extern "C"
+
+namespace swgb {
+int aux_status_word(cudaStream_t st, int32_t **status)
+{
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    if ((rc = ensure(ds->misc, 256))) return rc;
+    *status = (int32_t *)ds->misc.ptr;
+    if (cudaMemsetAsync(*status, 0, sizeof(int32_t), st) != cudaSuccess) return SW_ERR_CUDA;
+    ds->last_status = *status;
+    return SW_OK;
+}
+}  // namespace swgb
+
+extern "C" {
 
 static int stage_e_status(DeviceState *ds, size_t extra, cudaStream_t st, int32_t **status, uint8_t **scratch)
 {

@@ -174,6 +174,21 @@ int launch_cap_offsets(const int64_t *read_off, int64_t n_pairs, int64_t *cig_of
 int launch_dense_cigar(const uint32_t *ops, const int64_t *off, const int32_t *n_ops, int64_t n_pairs,
                        int64_t *doff, uint32_t *dense, int64_t dense_cap, int64_t *blk, cudaStream_t st);
 
+int launch_mlp_forward_tc(const float *model, const uint16_t *feat, int64_t n, float *out, int sm_count,
+                          int32_t *status, cudaStream_t st);
+// A device status word for calls outside the alignment path: cleared on
+// `st`, and the word sw_sync_status reads until the next call sets another.
+int aux_status_word(cudaStream_t st, int32_t **status);
+
+// Layout of the filter's model buffer (floats): parameters, Adam moments,
+// gradient, step, then bf16 copies of W1 and W2 transposed (K-major).
+constexpr int64_t MD_W1 = 0, MD_B1 = 16384, MD_W2 = 16640, MD_B2 = 33024, MD_W3 = 33088, MD_B3 = 33152;
+constexpr int64_t MD_NP = 33153;
+constexpr int64_t MD_M = MD_NP, MD_V = 2 * MD_NP, MD_G = 3 * MD_NP, MD_STEP = 4 * MD_NP;
+constexpr int64_t MD_W1T = 132616;          // bf16 [256][64], 16-byte aligned
+constexpr int64_t MD_W2T = MD_W1T + 8192;   // bf16 [64][256]
+constexpr int64_t MD_TOTAL = MD_W2T + 8192;
+
 void count_launch(int n = 1);
 
 }  // namespace swgb

@@ -195,3 +195,32 @@ def test_training_lowers_loss_and_ranks_true_hits():
     trained = top_rank_of_true(model.forward(feats).cpu().numpy())
     assert np.mean(trained < 4) > 0.97, np.mean(trained < 4)
     assert np.mean(trained < 4) > np.mean(untrained < 4) + 0.3, (np.mean(trained < 4), np.mean(untrained < 4))
+
+
+def test_tensor_memory_forward_matches_warp_mma():
+    """The tcgen05 (tensor-memory) forward and the warp-level MMA forward
+    compute the same network: equal up to fp32 summation order, on a batch
+    with a ragged last tile; and both match the oracle."""
+    import torch
+    from paper_1304_0681_gb300 import _swgb
+    from paper_1304_0681_gb300 import filter as flt
+    rng = np.random.default_rng(9)
+    model = flt.FilterModel(seed=6)
+    n = 128 * 37 + 55
+    x = rng.uniform(0, 0.5, (n, 64))
+    xb = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).cuda().view(torch.int16)
+    try:
+        _swgb.sw_set_mlp_kernel(_swgb.SW_MLP_MMA_SYNC)
+        a = model.forward(xb).cpu().numpy()
+        _swgb.sw_set_mlp_kernel(_swgb.SW_MLP_AUTO)
+        b = model.forward(xb).cpu().numpy()
+        _swgb.sw_sync_status()
+    finally:
+        _swgb.sw_set_mlp_kernel(_swgb.SW_MLP_AUTO)
+    np.testing.assert_allclose(b, a, rtol=1e-2, atol=1e-3)
+    P = _model_params(model)
+    Pb = fo.Params(fo.bf16_round(P.W1), P.b1, fo.bf16_round(P.W2), P.b2, P.w3, P.b3)
+    X = fo.bf16_round(x)
+    a1 = fo.bf16_round(np.maximum(X @ Pb.W1 + Pb.b1, 0))
+    ref = np.maximum(a1 @ Pb.W2 + Pb.b2, 0) @ Pb.w3 + Pb.b3
+    np.testing.assert_allclose(b, ref, rtol=1e-2, atol=1e-3)
