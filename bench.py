@@ -57,6 +57,8 @@ def _args():
     ap.add_argument("--filter-reads", type=int, default=500_000)
     ap.add_argument("--fullmix-reads", type=int, default=150_000, help="reads of the full-mix sample")
     ap.add_argument("--no-extra", action="store_true", help="skip the uneven and full-mix sections")
+    ap.add_argument("--only-mlp", type=int, default=0, metavar="ROWS",
+                    help="time only the filter network's forward on ROWS random feature rows (both kernels)")
     ap.add_argument("--pairs", type=int, default=None,
                     help="smaller case of the workload (profiling); default: the full workload")
     return ap.parse_args()
@@ -382,6 +384,38 @@ def _graph_section(rank, n_pairs: int = 16384, reps: int = 50) -> dict:
             "speedup": direct_s / graph_s}
 
 
+def run_mlp_only(args) -> None:
+    """The filter network's forward alone: ROWS random bf16 feature rows
+    through the tensor-memory kernel and the warp-MMA kernel."""
+    import torch
+
+    from paper_1304_0681_gb300 import _swgb
+    from paper_1304_0681_gb300 import filter as flt
+    n = args.only_mlp
+    model = flt.FilterModel(seed=1)
+    x = (torch.rand(n, 64, device="cuda", generator=torch.Generator(device="cuda").manual_seed(0)) * 0.5)
+    x = x.to(torch.bfloat16).view(torch.int16)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    flops = n * 2 * (64 * 256 + 256 * 64 + 64)
+    res = {}
+    for kind, name in ((_swgb.SW_MLP_AUTO, "tcgen05"), (_swgb.SW_MLP_MMA_SYNC, "mma_sync")):
+        _swgb.sw_set_mlp_kernel(kind)
+        for _ in range(args.warmup):
+            model.forward(x, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            model.forward(x, out)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[name] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}
+    _swgb.sw_set_mlp_kernel(_swgb.SW_MLP_AUTO)
+    _swgb.sw_sync_status()
+    print(json.dumps({"section": "filter network forward", "rows": n, "flop_per_row": flops // n, **res}), flush=True)
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -428,6 +462,8 @@ def main():
     ws, rank, local = _dist()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.only_mlp:
+        return run_mlp_only(args)
 
     import numpy as np
     import torch
