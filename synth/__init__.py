@@ -292,3 +292,201 @@ def random_pairs(n_pairs: int, m_range, n_range, seed: int = 0, alphabet: int = 
     return Workload("random", reads, roff, wins, woff, np.arange(n_pairs, dtype=np.int64),
                     np.arange(n_pairs + 1, dtype=np.int64), np.full(n_pairs, KIND_RANDOM, np.uint8),
                     np.zeros(n_pairs, np.int32))
+
+
+# --------------------------------------------------------------------------
+# Reference genomes and reads sampled from them (the inputs of seeding).
+
+class GenomeSpec(ctypes.Structure):
+    _fields_ = [
+        ("seed", ctypes.c_uint64),
+        ("n_chrom", ctypes.c_int32),
+        ("pad0", ctypes.c_int32),
+        ("repeat_share", ctypes.c_double),
+        ("rep_len_min", ctypes.c_int32),
+        ("rep_len_max", ctypes.c_int32),
+        ("rep_copies_min", ctypes.c_int32),
+        ("rep_copies_max", ctypes.c_int32),
+        ("rep_div_lo", ctypes.c_double),
+        ("rep_div_hi", ctypes.c_double),
+        ("n_introns", ctypes.c_int64),
+        ("intron_min", ctypes.c_int32),
+        ("intron_max", ctypes.c_int32),
+        ("margin", ctypes.c_int32),
+        ("pad1", ctypes.c_int32),
+    ]
+
+
+class ReadsSpec(ctypes.Structure):
+    _fields_ = [
+        ("seed", ctypes.c_uint64),
+        ("n_reads", ctypes.c_int64),
+        ("n_len", ctypes.c_int32),
+        ("len_val", ctypes.c_int32 * 8),
+        ("pad0", ctypes.c_int32),
+        ("len_w", ctypes.c_double * 8),
+        ("eps", ctypes.c_double),
+        ("indel_share", ctypes.c_double),
+        ("splice_frac", ctypes.c_double),
+        ("min_exon", ctypes.c_int32),
+        ("pad1", ctypes.c_int32),
+    ]
+
+
+#: Chromosome lengths (Mb) of a human-sized genome: 22 autosomes, X and Y.
+HUMAN_MB = (249, 243, 198, 191, 181, 171, 159, 146, 141, 136, 135, 134, 115, 107, 102, 90, 81, 78, 59, 63, 48, 51,
+            155, 59)
+
+GENOMES = {
+    # 3.1 Gb in 24 chromosomes; 5% in repeat families of 300-6,000 bp with
+    # 2-20 copies at 0-8% divergence; 200,000 introns of 50-2,000 bp.
+    "human": dict(chrom_len=[x * 1_000_000 for x in HUMAN_MB], repeat_share=0.05, rep_len=(300, 6000),
+                  rep_copies=(2, 20), rep_div=(0.0, 0.08), n_introns=200_000, intron=(50, 2000)),
+    # 64 Mb in 8 chromosomes, same feature mix (full-size sampled parity
+    # checks that the oracle can still scan).
+    "medium": dict(chrom_len=[8_000_000] * 8, repeat_share=0.05, rep_len=(300, 6000), rep_copies=(2, 20),
+                   rep_div=(0.0, 0.08), n_introns=4000, intron=(50, 2000)),
+    # 2 Mb in 4 chromosomes: every-read parity against the oracle.
+    "small": dict(chrom_len=[300_000, 500_000, 700_000, 500_000], repeat_share=0.05, rep_len=(200, 2000),
+                  rep_copies=(2, 10), rep_div=(0.0, 0.08), n_introns=400, intron=(50, 2000)),
+}
+
+#: The paper's simulated read sets: 2M single-end reads of 100 or 250 nt at
+#: 0.1% or 1% error; indels are 30% of the errors.  10% of the reads span a
+#: splice junction (RNA-seq).
+READ_SETS = {
+    "T1": dict(lengths=((100, 1.0),), eps=0.001),
+    "T2": dict(lengths=((100, 1.0),), eps=0.01),
+    "T3": dict(lengths=((250, 1.0),), eps=0.001),
+    "T4": dict(lengths=((250, 1.0),), eps=0.01),
+}
+
+
+@dataclass
+class Genome:
+    """A reference of chromosomes back to back: ``packed`` 2-bit bases,
+    ``chrom_offsets`` (n_chrom + 1, in bases), and the planted introns as
+    rows (chrom, global start, length, strand: 0 GT..AG, 1 CT..AC)."""
+    name: str
+    packed: np.ndarray
+    chrom_offsets: np.ndarray
+    introns: np.ndarray
+    _codes: np.ndarray | None = field(default=None, repr=False)
+
+    @property
+    def n_bases(self) -> int:
+        return int(self.chrom_offsets[-1])
+
+    @property
+    def n_chrom(self) -> int:
+        return len(self.chrom_offsets) - 1
+
+    def codes(self) -> np.ndarray:
+        if self._codes is None:
+            self._codes = unpack(self.packed, self.n_bases)
+        return self._codes
+
+
+@dataclass
+class ReadSet:
+    """Reads (codes, CSR offsets) and where each came from: chromosome,
+    forward-strand chromosome position of its first template base, strand,
+    and the intron it spans (-1 for none)."""
+    name: str
+    reads: np.ndarray
+    read_offsets: np.ndarray
+    chrom: np.ndarray
+    pos: np.ndarray
+    strand: np.ndarray
+    intron: np.ndarray
+    _packed: np.ndarray | None = field(default=None, repr=False)
+
+    @property
+    def n_reads(self) -> int:
+        return len(self.read_offsets) - 1
+
+    def packed_reads(self) -> np.ndarray:
+        if self._packed is None:
+            self._packed = pack(self.reads)
+        return self._packed
+
+    def read(self, r: int) -> np.ndarray:
+        return self.reads[self.read_offsets[r]:self.read_offsets[r + 1]]
+
+
+def _load_genome_fns(lib):
+    p, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    if not hasattr(lib, "_genome_ready"):
+        lib.synth_genome.argtypes = [ctypes.POINTER(GenomeSpec), p, p, p, ctypes.c_int]
+        lib.synth_read_lengths.argtypes = [ctypes.POINTER(ReadsSpec), p, ctypes.c_int]
+        lib.synth_sample_reads.argtypes = [ctypes.POINTER(ReadsSpec), p, i32, p, p, i64, p, p, p, p, p, p,
+                                           ctypes.c_int]
+        lib._genome_ready = True
+    return lib
+
+
+def genome(name: str = "small", seed: int = 0, threads: int | None = None, **over) -> Genome:
+    """Generate a named reference genome (keyword arguments override the
+    recipe: chrom_len, repeat_share, rep_len, rep_copies, rep_div, n_introns,
+    intron, margin)."""
+    lib = _load_genome_fns(_load())
+    g = dict(GENOMES[name], margin=4096)
+    g.update(over)
+    clen = np.asarray(g["chrom_len"], np.int64)
+    off = np.zeros(len(clen) + 1, np.int64)
+    np.cumsum(clen, out=off[1:])
+    s = GenomeSpec()
+    s.seed = seed
+    s.n_chrom = len(clen)
+    s.repeat_share = g["repeat_share"]
+    s.rep_len_min, s.rep_len_max = g["rep_len"]
+    s.rep_copies_min, s.rep_copies_max = g["rep_copies"]
+    s.rep_div_lo, s.rep_div_hi = g["rep_div"]
+    s.n_introns = g["n_introns"]
+    s.intron_min, s.intron_max = g["intron"]
+    s.margin = g["margin"]
+    packed = np.zeros(packed_nbytes(int(off[-1])), np.uint8)
+    introns = np.zeros((int(s.n_introns), 4), np.int64)
+    rc = lib.synth_genome(ctypes.byref(s), _ptr(off), _ptr(packed), _ptr(introns),
+                          threads or min(os.cpu_count() or 1, 32))
+    if rc:
+        raise RuntimeError(f"synth_genome failed: {rc}")
+    return Genome(name, packed, off, introns)
+
+
+def sample_reads(g: Genome, name: str = "T2", n_reads: int = 2_000_000, seed: int = 1, splice: float = 0.10,
+                 indel_share: float = 0.3, min_exon: int = 20, threads: int | None = None, **over) -> ReadSet:
+    """Sample a named read set from a genome (keyword arguments override:
+    lengths, eps)."""
+    lib = _load_genome_fns(_load())
+    rs = dict(READ_SETS[name])
+    rs.update(over)
+    s = ReadsSpec()
+    s.seed = seed
+    s.n_reads = n_reads
+    s.n_len = len(rs["lengths"])
+    for k, (v, w) in enumerate(rs["lengths"]):
+        s.len_val[k] = v
+        s.len_w[k] = w
+    s.eps = rs["eps"]
+    s.indel_share = indel_share
+    s.splice_frac = splice
+    s.min_exon = min_exon
+    nt = threads or min(os.cpu_count() or 1, 32)
+    ln = np.zeros(n_reads, np.int32)
+    if lib.synth_read_lengths(ctypes.byref(s), _ptr(ln), nt):
+        raise RuntimeError("synth_read_lengths failed")
+    roff = np.zeros(n_reads + 1, np.int64)
+    np.cumsum(ln, out=roff[1:])
+    codes = np.zeros(int(roff[-1]), np.uint8)
+    chrom = np.zeros(n_reads, np.int32)
+    pos = np.zeros(n_reads, np.int64)
+    strand = np.zeros(n_reads, np.int8)
+    intron = np.zeros(n_reads, np.int32)
+    introns = np.ascontiguousarray(g.introns, np.int64)
+    rc = lib.synth_sample_reads(ctypes.byref(s), _ptr(g.chrom_offsets), g.n_chrom, _ptr(g.packed), _ptr(introns),
+                                len(introns), _ptr(roff), _ptr(codes), _ptr(chrom), _ptr(pos), _ptr(strand),
+                                _ptr(intron), nt)
+    if rc:
+        raise RuntimeError(f"synth_sample_reads failed: {rc}")
+    return ReadSet(name, codes, roff, chrom, pos, strand, intron)
