@@ -28,7 +28,10 @@ EXPORTS = ("sw_cigar_capacity", "sw_packed_bytes", "sw_batch_align", "sw_batch_a
            "sw_junctions_export",
            "sw_plan_rows", "sw_alu_probe", "sw_phase_timing", "sw_phase_times", "sw_batch_align_noalloc",
            "sw_batch_align_masked", "sw_filter_features", "sw_mlp_bytes", "sw_mlp_init", "sw_mlp_refresh",
-           "sw_mlp_forward", "sw_set_mlp_kernel", "sw_mlp_grad", "sw_mlp_adam", "sw_filter_select", "sw_best_per_read")
+           "sw_mlp_forward", "sw_set_mlp_kernel", "sw_mlp_grad", "sw_mlp_adam", "sw_filter_select", "sw_best_per_read",
+           # include/swgb_seed.h
+           "sw_index_table_words", "sw_index_build", "sw_seed_windows", "sw_reads_two_strands",
+           "sw_extract_windows")
 
 
 class SwError(RuntimeError):
@@ -44,6 +47,23 @@ class Scoring(ctypes.Structure):
 
 class Cigar(ctypes.Structure):
     _fields_ = [("ops", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("n_ops", ctypes.c_void_p)]
+
+
+class SeedParams(ctypes.Structure):
+    """sw_seed_params_t; the defaults are the paper's where it states them
+    (k = 15, second phase at the eighth base, 12-base spacing giving 8 + 7
+    seeds for 100 bases, 30-base flanks) and readings elsewhere."""
+    _fields_ = [(n, ctypes.c_int32) for n in ("k", "stride", "phase", "max_hits", "merge_dist", "min_cal_len",
+                                              "flank", "max_intron", "max_window")]
+
+    def __init__(self, k=15, stride=12, phase=7, max_hits=64, merge_dist=30, min_cal_len=20, flank=30,
+                 max_intron=2000, max_window=16384):
+        super().__init__(k, stride, phase, max_hits, merge_dist, min_cal_len, flank, max_intron, max_window)
+
+
+class Windows(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("start", "length", "chrom", "pos", "strand", "pair_read",
+                                               "cand_offsets")]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -88,6 +108,17 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_filter_select.restype = ctypes.c_int
     lib.sw_best_per_read.argtypes = [p, p, i64, p, p, p, p]
     lib.sw_best_per_read.restype = ctypes.c_int
+    lib.sw_index_table_words.argtypes = [i32]
+    lib.sw_index_table_words.restype = i64
+    lib.sw_index_build.argtypes = [p, i64, p, i32, i32, p, p, p, p]
+    lib.sw_index_build.restype = ctypes.c_int
+    lib.sw_seed_windows.argtypes = [p, p, p, i32, ctypes.POINTER(SeedParams), p, p, i64, ctypes.POINTER(Windows),
+                                    i64, p, p]
+    lib.sw_seed_windows.restype = ctypes.c_int
+    lib.sw_reads_two_strands.argtypes = [p, p, i64, p, i64, p, p]
+    lib.sw_reads_two_strands.restype = ctypes.c_int
+    lib.sw_extract_windows.argtypes = [p, i64, p, p, i64, p, i64, p, p]
+    lib.sw_extract_windows.restype = ctypes.c_int
     lib.sw_sync_status.argtypes = [p]
     lib.sw_sync_status.restype = ctypes.c_int
     lib.sw_strerror.argtypes = [ctypes.c_int]
@@ -390,3 +421,35 @@ def sw_filter_select(pred, cand_offsets, n_reads: int, k: int, tau: float, pair_
 def sw_best_per_read(score, cand_offsets, n_reads: int, pair_mask, best_score, best_cand, stream=None) -> None:
     _check(_lib.sw_best_per_read(_ptr(score), _ptr(cand_offsets), int(n_reads), _ptr(pair_mask), _ptr(best_score),
                                  _ptr(best_cand), _stream(stream)), "sw_best_per_read")
+
+
+def sw_index_table_words(k: int) -> int:
+    return int(_lib.sw_index_table_words(int(k)))
+
+
+def sw_index_build(genome, n_bases: int, chrom_offsets, n_chrom: int, k: int, table, positions, out_n,
+                   stream=None) -> None:
+    _check(_lib.sw_index_build(_ptr(genome), int(n_bases), _ptr(chrom_offsets), int(n_chrom), int(k), _ptr(table),
+                               _ptr(positions), _ptr(out_n), _stream(stream)), "sw_index_build")
+
+
+def sw_seed_windows(table, positions, chrom_offsets, n_chrom: int, params: SeedParams, reads, read_offsets,
+                    n_reads: int, out: dict, capacity: int, out_count, stream=None) -> None:
+    """out: tensors start, length, chrom, pos, strand, pair_read (capacity
+    entries) and cand_offsets (n_reads + 1)."""
+    w = Windows(*(out[n].data_ptr() for n in ("start", "length", "chrom", "pos", "strand", "pair_read",
+                                               "cand_offsets")))
+    _check(_lib.sw_seed_windows(_ptr(table), _ptr(positions), _ptr(chrom_offsets), int(n_chrom),
+                                ctypes.byref(params), _ptr(reads), _ptr(read_offsets), int(n_reads), ctypes.byref(w),
+                                int(capacity), _ptr(out_count), _stream(stream)), "sw_seed_windows")
+
+
+def sw_reads_two_strands(reads, read_offsets, n_reads: int, out, cap_bases: int, out_offsets, stream=None) -> None:
+    _check(_lib.sw_reads_two_strands(_ptr(reads), _ptr(read_offsets), int(n_reads), _ptr(out), int(cap_bases),
+                                     _ptr(out_offsets), _stream(stream)), "sw_reads_two_strands")
+
+
+def sw_extract_windows(genome, n_bases: int, start, length, n_windows: int, out, cap_bases: int, out_offsets,
+                       stream=None) -> None:
+    _check(_lib.sw_extract_windows(_ptr(genome), int(n_bases), _ptr(start), _ptr(length), int(n_windows), _ptr(out),
+                                   int(cap_bases), _ptr(out_offsets), _stream(stream)), "sw_extract_windows")

@@ -21,7 +21,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
 
 def _deps():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
-        os.path.join(INCLUDE, "swgb.h")]
+        os.path.join(INCLUDE, "swgb.h"), os.path.join(INCLUDE, "swgb_seed.h")]
 
 
 def _compile(src: str, obj: str, verbose: bool) -> str:

@@ -118,6 +118,11 @@ struct CapOf {  // CIGAR capacity of pair p: 2 m + 3 runs
     __device__ int64_t operator()(int64_t p) const { return 2 * (roff[p + 1] - roff[p]) + 3; }
 };
 
+struct I32Of {  // a plain int32 array
+    const int32_t *v;
+    __device__ int64_t operator()(int64_t p) const { return v[p]; }
+};
+
 struct RunsOf {  // runs pair p's CIGAR holds (an overflowed slot holds none)
     const int32_t *n_ops;
     __device__ int64_t operator()(int64_t p) const { return n_ops[p] > 0 ? n_ops[p] : 0; }
@@ -146,6 +151,12 @@ __global__ void k_dense_copy(const uint32_t *__restrict__ ops, const int64_t *__
 int launch_cap_offsets(const int64_t *read_off, int64_t n_pairs, int64_t *cig_off, int64_t *blk, cudaStream_t st)
 {
     return exclusive_scan(CapOf{read_off}, n_pairs, cig_off, blk, st);
+}
+
+int launch_scan_i32(const int32_t *v, int64_t n, int64_t *out, int64_t *blk, cudaStream_t st)
+{
+    if (n == 0) return cudaMemsetAsync(out, 0, sizeof(int64_t), st) == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return exclusive_scan(I32Of{v}, n, out, blk, st);
 }
 
 int launch_dense_cigar(const uint32_t *ops, const int64_t *off, const int32_t *n_ops, int64_t n_pairs,

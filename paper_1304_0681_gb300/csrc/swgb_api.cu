@@ -16,6 +16,7 @@
 
 #include "sw_device.cuh"
 #include "swgb_internal.h"
+#include "swgb_seed.h"
 
 namespace swgb {
 
@@ -1328,6 +1329,127 @@ int sw_junctions_export(const uint64_t *table, int64_t capacity, sw_junction_t *
 {
     if (!table_ok(table, capacity) || max_out < 0 || !out_count || (max_out > 0 && !out)) return SW_ERR_INVALID_ARG;
     return launch_table_export(table, capacity, out, max_out, out_count, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ---- seeding (Stages C, D, E i-ii) ----------------------------------------
+
+extern "C" {
+
+int64_t sw_index_table_words(int32_t k) { return (k < 8 || k > 16) ? 0 : (int64_t)1 << (2 * k); }
+
+int sw_index_build(const uint8_t *genome, int64_t n_bases, const int64_t *chrom_offsets, int32_t n_chrom,
+                   int32_t k, uint32_t *table, uint32_t *positions, int64_t *out_n_positions, sw_stream_t stream)
+{
+    if (!genome || ((uintptr_t)genome & 15u) || !chrom_offsets || !table || !positions || !out_n_positions ||
+        k < 8 || k > 16 || n_chrom < 1 || n_bases < 0)
+        return SW_ERR_INVALID_ARG;
+    if (n_bases >= (int64_t)UINT32_MAX) return SW_ERR_UNSUPPORTED;
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n_blk = ((size_t)1 << (2 * k)) / 4096;
+    int32_t *status = nullptr;
+    uint8_t *scratch = nullptr;
+    if ((rc = stage_e_status(ds, 4 * n_blk, st, &status, &scratch))) return rc;
+    return launch_index_build((const uint32_t *)genome, n_bases, chrom_offsets, n_chrom, k, table, positions,
+                              out_n_positions, (uint32_t *)scratch, ds->sm_count, status, st);
+}
+
+static int seed_params_check(const sw_seed_params_t *p, SeedKParams *kp, int *block_hits)
+{
+    if (!p || p->k < 8 || p->k > 16 || p->stride < 1 || p->phase < 0 || p->phase > SW_SEED_MAX_READ_LEN ||
+        p->max_hits < 1 || p->max_hits > SW_SEED_MAX_HITS || p->merge_dist < 0 || p->min_cal_len < p->k ||
+        p->flank < 0 || p->max_intron < 0 || p->max_window < 1 || p->max_window > SW_MAX_WINDOW_LEN)
+        return SW_ERR_INVALID_ARG;
+    *kp = SeedKParams{p->k, p->stride, p->phase, p->max_hits, p->merge_dist, p->min_cal_len, p->flank,
+                      p->max_intron, p->max_window};
+    const int64_t bound = (int64_t)seed_count_per_read(SW_SEED_MAX_READ_LEN, *kp) * p->max_hits;
+    int64_t n = 32;
+    while (n < bound) n <<= 1;
+    if (n > SW_SEED_MAX_LIST) return SW_ERR_UNSUPPORTED;
+    *block_hits = (int)n;
+    return SW_OK;
+}
+
+int sw_seed_windows(const uint32_t *table, const uint32_t *positions, const int64_t *chrom_offsets,
+                    int32_t n_chrom, const sw_seed_params_t *params, const uint8_t *reads,
+                    const int64_t *read_offsets, int64_t n_reads, const sw_windows_t *out, int64_t capacity,
+                    int64_t *out_count, sw_stream_t stream)
+{
+    SeedKParams kp;
+    int block_hits = 0;
+    int rc = seed_params_check(params, &kp, &block_hits);
+    if (rc) return rc;
+    if (n_reads < 0 || capacity < 0 || !out || !out_count || !out->cand_offsets || !table || !positions ||
+        !chrom_offsets || n_chrom < 1)
+        return SW_ERR_INVALID_ARG;
+    if (n_reads > (int64_t)INT32_MAX / 2 - 1 || capacity >= (int64_t)UINT32_MAX) return SW_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_reads == 0) {
+        if (cudaMemsetAsync(out_count, 0, sizeof(int64_t), st) != cudaSuccess ||
+            cudaMemsetAsync(out->cand_offsets, 0, sizeof(int64_t), st) != cudaSuccess)
+            return SW_ERR_CUDA;
+        return SW_OK;
+    }
+    if (!reads || ((uintptr_t)reads & 15u) || !read_offsets || !out->start || !out->length || !out->chrom ||
+        !out->pos || !out->strand || !out->pair_read)
+        return SW_ERR_INVALID_ARG;
+    DeviceState *ds = nullptr;
+    if ((rc = device_state(&ds))) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    int32_t *status = nullptr;
+    uint8_t *scratch = nullptr;
+    if ((rc = stage_e_status(ds, seed_scratch_bytes(n_reads, capacity), st, &status, &scratch))) return rc;
+    SeedOutPtrs o{out->start, out->length, out->chrom, out->pos, out->strand, out->pair_read, out->cand_offsets,
+                  out_count};
+    return launch_seed_windows((const uint32_t *)reads, read_offsets, n_reads, table, positions, chrom_offsets,
+                               n_chrom, kp, SW_SEED_MAX_READ_LEN, block_hits, o, capacity, scratch, ds->sm_count,
+                               status, st);
+}
+
+int sw_reads_two_strands(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads, uint8_t *out,
+                         int64_t cap_bases, int64_t *out_offsets, sw_stream_t stream)
+{
+    if (n_reads < 0 || cap_bases < 0 || !out_offsets) return SW_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_reads == 0)
+        return cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), st) == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    if (!reads || ((uintptr_t)reads & 15u) || !read_offsets || !out || ((uintptr_t)out & 15u))
+        return SW_ERR_INVALID_ARG;
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    int32_t *status = nullptr;
+    uint8_t *scratch = nullptr;
+    if ((rc = stage_e_status(ds, 0, st, &status, &scratch))) return rc;
+    return launch_two_strands((const uint32_t *)reads, read_offsets, n_reads, (uint32_t *)out, cap_bases,
+                              out_offsets, ds->sm_count, status, st);
+}
+
+int sw_extract_windows(const uint8_t *genome, int64_t n_bases, const int64_t *start, const int32_t *length,
+                       int64_t n_windows, uint8_t *out, int64_t cap_bases, int64_t *out_offsets,
+                       sw_stream_t stream)
+{
+    if (n_windows < 0 || cap_bases < 0 || n_bases < 0 || !out_offsets) return SW_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_windows == 0)
+        return cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), st) == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    if (!genome || ((uintptr_t)genome & 15u) || !start || !length || !out || ((uintptr_t)out & 15u))
+        return SW_ERR_INVALID_ARG;
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    int32_t *status = nullptr;
+    uint8_t *scratch = nullptr;
+    if ((rc = stage_e_status(ds, 8 * ((size_t)(n_windows + 255) / 256 + 1), st, &status, &scratch))) return rc;
+    return launch_extract_windows((const uint32_t *)genome, n_bases, start, length, n_windows, (uint32_t *)out,
+                                  cap_bases, out_offsets, (int64_t *)scratch, ds->sm_count, status, st);
 }
 
 }  // extern "C"

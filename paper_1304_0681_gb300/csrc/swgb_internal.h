@@ -191,4 +191,37 @@ constexpr int64_t MD_TOTAL = MD_W2T + 8192;
 
 void count_launch(int n = 1);
 
+// Exclusive scan of int32 values v[0 .. n) into out[0 .. n] (out[n] = the
+// total); blk holds (n + 255) / 256 + 1 int64 words.
+int launch_scan_i32(const int32_t *v, int64_t n, int64_t *out, int64_t *blk, cudaStream_t st);
+
+// ---- seeding (reads to candidate windows) ----
+struct SeedKParams {
+    int32_t k, stride, phase, max_hits, merge_dist, min_cal_len, flank, max_intron, max_window;
+};
+struct SeedOutPtrs {
+    int64_t *start;
+    int32_t *length;
+    int32_t *chrom;
+    int64_t *pos;
+    int8_t *strand;
+    int64_t *pair_read;
+    int64_t *cand_offsets;
+    int64_t *count;
+};
+int seed_count_per_read(int m, const SeedKParams &p);
+int launch_index_build(const uint32_t *genome, int64_t n_bases, const int64_t *chrom_off, int n_chrom, int k,
+                       uint32_t *table, uint32_t *positions, int64_t *out_n, uint32_t *blk, int sm_count,
+                       int32_t *status, cudaStream_t st);
+size_t seed_scratch_bytes(int64_t n_reads, int64_t capacity);
+int launch_seed_windows(const uint32_t *reads, const int64_t *roff, int64_t n_reads, const uint32_t *table,
+                        const uint32_t *positions, const int64_t *chrom_off, int n_chrom, const SeedKParams &p,
+                        int max_read, int block_hits, SeedOutPtrs out, int64_t capacity, uint8_t *scratch,
+                        int sm_count, int32_t *status, cudaStream_t st);
+int launch_extract_windows(const uint32_t *genome, int64_t n_bases, const int64_t *start, const int32_t *len,
+                           int64_t n, uint32_t *dst, int64_t cap_bases, int64_t *woff, int64_t *blk, int sm_count,
+                           int32_t *status, cudaStream_t st);
+int launch_two_strands(const uint32_t *reads, const int64_t *roff, int64_t n, uint32_t *dst, int64_t cap_bases,
+                       int64_t *doff, int sm_count, int32_t *status, cudaStream_t st);
+
 }  // namespace swgb

@@ -1,0 +1,169 @@
+"""Seeding over the C ABI (include/swgb_seed.h): the k-mer index of a
+reference, reads to candidate windows (the paper's Stages C and D and Stage E
+tasks i-ii), and the map of a whole batch: seed, extract the windows' bases,
+align every read against its windows (Stage E task iii), keep the records
+and the best hit per read (task iv).
+
+The kernels do all the work; this module allocates buffers, reads back the
+counts that size the next step, and retries once with a larger buffer when
+a capacity was too small.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _swgb
+from ._swgb import SeedParams, SwError
+
+CAPACITY = -2
+
+
+def _dev(a, device, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return (t if dtype is None else t.to(dtype)).to(device)
+
+
+def packed_bytes(n_bases: int) -> int:
+    return int(_swgb.sw_packed_bytes(int(n_bases)))
+
+
+class KmerIndex:
+    """The direct-address k-mer index of a packed reference (chromosomes
+    back to back, chrom_offsets in bases), built on the device."""
+
+    def __init__(self, packed, chrom_offsets, k: int = 15, device="cuda", stream=None):
+        chrom_offsets = np.asarray(chrom_offsets, np.int64)
+        self.k = int(k)
+        self.n_bases = int(chrom_offsets[-1])
+        self.n_chrom = len(chrom_offsets) - 1
+        self.chrom_offsets_host = chrom_offsets
+        if isinstance(packed, torch.Tensor):
+            self.genome = packed.to(device)
+        else:
+            buf = np.zeros(packed_bytes(self.n_bases), np.uint8)
+            buf[:min(len(packed), len(buf))] = np.asarray(packed, np.uint8)[:len(buf)]
+            self.genome = _dev(buf, device)
+        self.chrom_offsets = _dev(chrom_offsets, device)
+        words = _swgb.sw_index_table_words(self.k)
+        if words == 0:
+            raise ValueError(f"k = {k} outside 8..16")
+        self.table = torch.empty(words, dtype=torch.int32, device=device)
+        self.positions = torch.empty(max(self.n_bases, 1), dtype=torch.int32, device=device)
+        self.n_positions_dev = torch.zeros(1, dtype=torch.int64, device=device)
+        _swgb.sw_index_build(self.genome, self.n_bases, self.chrom_offsets, self.n_chrom, self.k, self.table,
+                             self.positions, self.n_positions_dev, stream)
+        _swgb.sw_sync_status(stream)
+        self.n_positions = int(self.n_positions_dev.item())
+
+    def bucket(self, code: int) -> np.ndarray:
+        """Positions of k-mer `code` (first base in the low bits), sorted."""
+        lo = int(self.table[code - 1].item()) & 0xFFFFFFFF if code else 0
+        hi = int(self.table[code].item()) & 0xFFFFFFFF
+        return np.sort(self.positions[lo:hi].cpu().numpy().view(np.uint32).astype(np.int64))
+
+
+_WIN_FIELDS = (("start", torch.int64), ("length", torch.int32), ("chrom", torch.int32), ("pos", torch.int64),
+               ("strand", torch.int8), ("pair_read", torch.int64))
+
+
+def seed_windows(index: KmerIndex, reads, read_offsets, n_reads: int, params: SeedParams | None = None,
+                 capacity: int | None = None, stream=None) -> dict:
+    """Windows of every read as device tensors (trimmed to the count):
+    start, length, chrom, pos, strand, pair_read, cand_offsets, and count."""
+    params = params or SeedParams(k=index.k)
+    if params.k != index.k:
+        raise ValueError("params.k differs from the index's k")
+    dev = index.table.device
+    cap = int(capacity if capacity is not None else 4 * n_reads + 1024)
+    for attempt in range(2):
+        out = {n: torch.empty(max(cap, 1), dtype=t, device=dev) for n, t in _WIN_FIELDS}
+        out["cand_offsets"] = torch.empty(n_reads + 1, dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        _swgb.sw_seed_windows(index.table, index.positions, index.chrom_offsets, index.n_chrom, params, reads,
+                              read_offsets, n_reads, out, cap, cnt, stream)
+        try:
+            _swgb.sw_sync_status(stream)
+        except SwError as e:
+            if e.code != CAPACITY or attempt:
+                raise
+            cap = int(cnt.item())
+            continue
+        n = int(cnt.item())
+        res = {k: v[:n] for k, v in out.items() if k != "cand_offsets"}
+        res["cand_offsets"] = out["cand_offsets"]
+        res["count"] = n
+        return res
+    raise AssertionError("unreachable")
+
+
+def two_strands(reads, read_offsets, n_reads: int, stream=None):
+    """(packed reads, offsets) holding each read and then every reverse
+    complement: read r's strand s is index r + s * n_reads."""
+    total = int(read_offsets[n_reads].item()) if n_reads else 0
+    out = torch.zeros(packed_bytes(2 * total), dtype=torch.uint8, device=read_offsets.device)
+    off = torch.empty(2 * n_reads + 1, dtype=torch.int64, device=read_offsets.device)
+    _swgb.sw_reads_two_strands(reads, read_offsets, n_reads, out, 2 * total, off, stream)
+    return out, off
+
+
+def extract_windows(index: KmerIndex, start, length, n_windows: int, stream=None):
+    """(packed window bases, offsets) of the given reference spans."""
+    total = int(length[:n_windows].to(torch.int64).sum().item()) if n_windows else 0
+    out = torch.empty(packed_bytes(total), dtype=torch.uint8, device=index.genome.device)
+    off = torch.empty(n_windows + 1, dtype=torch.int64, device=index.genome.device)
+    _swgb.sw_extract_windows(index.genome, index.n_bases, start, length, n_windows, out, total, off, stream)
+    return out, off
+
+
+@dataclass
+class Mapped:
+    windows: dict          # seed_windows() output
+    reads2: torch.Tensor   # both strands of the reads
+    reads2_offsets: torch.Tensor
+    win_bases: torch.Tensor
+    win_offsets: torch.Tensor
+    score: torch.Tensor    # per window
+    end: torch.Tensor
+    cigar: tuple | None
+    best_score: torch.Tensor   # per read
+    best_cand: torch.Tensor
+
+    def cigar_tuple(self):
+        return self.cigar
+
+
+def map_reads(index: KmerIndex, reads, read_offsets, n_reads: int, scoring, params: SeedParams | None = None,
+              cigar: bool = True, stream=None) -> Mapped:
+    """Seed, extract, align every (read strand, window) pair, and pick each
+    read's best window (first on ties)."""
+    win = seed_windows(index, reads, read_offsets, n_reads, params, stream=stream)
+    n = win["count"]
+    # each call clears the status word the next one reuses: check in between
+    reads2, roff2 = two_strands(reads, read_offsets, n_reads, stream)
+    _swgb.sw_sync_status(stream)
+    wb, woff = extract_windows(index, win["start"], win["length"], n, stream)
+    _swgb.sw_sync_status(stream)
+    dev = reads.device
+    score = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    end = torch.empty(2 * max(n, 1), dtype=torch.int32, device=dev)
+    cg = None
+    if cigar and n:
+        rl = (read_offsets[1:] - read_offsets[:-1]).repeat(2)
+        cap = 2 * rl[win["pair_read"]] + 3
+        coff = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+        torch.cumsum(cap, 0, out=coff[1:])
+        cg = (torch.empty(int(coff[-1].item()), dtype=torch.int32, device=dev), coff,
+              torch.empty(n, dtype=torch.int32, device=dev))
+    if n:
+        _swgb.sw_batch_align_indexed(reads2, roff2, 2 * n_reads, wb, woff, win["pair_read"], n, scoring, score, end,
+                                     cg, stream)
+        _swgb.sw_sync_status(stream)
+    best = torch.empty(max(n_reads, 1), dtype=torch.int32, device=dev)
+    bcand = torch.empty(max(n_reads, 1), dtype=torch.int32, device=dev)
+    if n_reads:
+        _swgb.sw_best_per_read(score, win["cand_offsets"], n_reads, None, best, bcand, stream)
+    _swgb.sw_sync_status(stream)
+    return Mapped(win, reads2, roff2, wb, woff, score[:n], end[:2 * n], cg, best[:n_reads], bcand[:n_reads])

@@ -1,5 +1,5 @@
-"""The C-ABI library builds, loads and exports every symbol include/swgb.h
-declares (no compute calls: runs without a GPU)."""
+"""The C-ABI library builds, loads and exports every symbol the headers
+under include/ declare (no compute calls: runs without a GPU)."""
 import os
 import re
 import subprocess
@@ -8,9 +8,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    text = open(os.path.join(ROOT, "include", "swgb.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(sw_[a-z0-9_]+)\s*\(", text)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            text = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, h)).read(), flags=re.S)
+            names.update(re.findall(r"\b(sw_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_library_exports_declared_symbols():
