@@ -57,6 +57,11 @@ def _args():
     ap.add_argument("--filter-reads", type=int, default=500_000)
     ap.add_argument("--fullmix-reads", type=int, default=150_000, help="reads of the full-mix sample")
     ap.add_argument("--no-extra", action="store_true", help="skip the uneven and full-mix sections")
+    ap.add_argument("--no-seeding", action="store_true", help="skip the seeding section")
+    ap.add_argument("--only-seeding", action="store_true", help="run the seeding section alone")
+    ap.add_argument("--seed-ref", default="human", help="reference recipe of the seeding section")
+    ap.add_argument("--seed-k", type=int, default=15, help="seed length of the seeding section")
+    ap.add_argument("--seed-sets", default="T2,T4", help="read sets of the seeding section")
     ap.add_argument("--only-mlp", type=int, default=0, metavar="ROWS",
                     help="time only the filter network's forward on ROWS random feature rows (both kernels)")
     ap.add_argument("--pairs", type=int, default=None,
@@ -336,6 +341,106 @@ def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
             "stage_e_records_junctions": stage_e_res}
 
 
+def _seeding_section(args, rank, steps: int) -> dict:
+    """Reads to windows on the GPU (Stages C, D, E i-ii) over a human-sized
+    reference (3.1 Gb, 24 chromosomes, 5% repeat families, 200k introns) for
+    the paper's read sets T2 (2M x 100 nt, 1% error) and T4 (2M x 250 nt):
+    seeding kernels timed alone (L2 flushed between steps), then the whole
+    map of T2 (seed, both strands, extract, SW with CIGAR, best hit per
+    read) with its host round trips, and its mapping accuracy."""
+    import numpy as np
+    import torch
+
+    import paper_1304_0681_gb300 as sw
+    import synth
+    from paper_1304_0681_gb300 import seed as sd
+
+    t0 = time.perf_counter()
+    g = synth.genome(args.seed_ref, seed=rank)
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    genome_dev = torch.from_numpy(g.packed).cuda()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    idx = sd.KmerIndex(genome_dev, g.chrom_offsets, k=args.seed_k)
+    e1.record(stream)
+    e1.synchronize()
+    index_ms = e0.elapsed_time(e1)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    p = sw._swgb.SeedParams(k=args.seed_k)
+    res = {"reference": {"recipe": args.seed_ref, "bases": g.n_bases, "chromosomes": g.n_chrom, "repeat_share": 0.05,
+                         "introns": int(len(g.introns)), "host_generate_s": gen_s},
+           "index": {"k": args.seed_k, "build_ms": index_ms, "positions": idx.n_positions,
+                     "table_gb": idx.table.numel() * 4 / 1e9, "positions_gb": idx.positions.numel() * 4 / 1e9},
+           "params": {f: getattr(p, f) for f, _ in p._fields_},
+           "paper_context": "stages C + D in isolation, 20 threads of a 64-core Opteron: T2 59.55 + 18.00 s, "
+                            "T4 265.31 (10 thr) ... see BASELINE.md; those stages only see reads stage B left "
+                            "unmapped, these kernels seed every read"}
+    for name in args.seed_sets.split(","):
+        rs = synth.sample_reads(g, name, n_reads=2_000_000, seed=rank + 1)
+        rd = torch.from_numpy(rs.packed_reads()).cuda()
+        ro = torch.from_numpy(rs.read_offsets).cuda()
+        w = sd.seed_windows(idx, rd, ro, rs.n_reads, p)
+        cap = int(w["count"] * 1.1) + 1024
+        out = {n: torch.empty(cap, dtype=t, device="cuda") for n, t in sd._WIN_FIELDS}
+        out["cand_offsets"] = torch.empty(rs.n_reads + 1, dtype=torch.int64, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        ms = []
+        for it in range(steps + 1):
+            flush.zero_()
+            e0.record(stream)
+            sw._swgb.sw_seed_windows(idx.table, idx.positions, idx.chrom_offsets, idx.n_chrom, p, rd, ro, rs.n_reads,
+                                     out, cap, cnt)
+            e1.record(stream)
+            e1.synchronize()
+            if it:
+                ms.append(e0.elapsed_time(e1))
+        sw.sw_sync_status()
+        n_win = int(cnt.item())
+        t = statistics.mean(ms)
+        sec = {"reads": rs.n_reads, "read_len": int(rs.read_offsets[1]), "eps": synth.READ_SETS[name]["eps"],
+               "spliced_share": 0.10, "windows": n_win, "windows_per_read": n_win / rs.n_reads,
+               "seed_ms": t, "seed_reads_per_s": rs.n_reads / (t * 1e-3), "steps": steps}
+        if name == "T2":
+            sd.map_reads(idx, rd, ro, rs.n_reads, SCORING)  # warm
+            torch.cuda.synchronize()
+            walls = []
+            for _ in range(steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                mp = sd.map_reads(idx, rd, ro, rs.n_reads, SCORING)
+                torch.cuda.synchronize()
+                walls.append(time.perf_counter() - t0)
+            wt = statistics.mean(walls)
+            wv = mp.windows
+            n = wv["count"]
+            rl = np.diff(rs.read_offsets)
+            pr = wv["pair_read"].cpu().numpy()
+            wlen = wv["length"].cpu().numpy().astype(np.int64)
+            cells = int(np.sum(np.concatenate([rl, rl])[pr] * wlen))
+            bc = mp.best_cand.cpu().numpy().astype(np.int64)
+            co = wv["cand_offsets"].cpu().numpy()
+            ok = bc >= 0
+            i = np.where(ok, co[:-1] + np.maximum(bc, 0), 0)
+            st = wv["start"].cpu().numpy()[i]
+            en = st + wlen[i] - 1
+            ws_ = wv["strand"].cpu().numpy()[i]
+            a = g.chrom_offsets[rs.chrom] + rs.pos
+            hit = ok & (ws_ == rs.strand) & (st <= a) & (a <= en)
+            sec["map"] = {"ms_per_step": wt * 1e3, "reads_per_s": rs.n_reads / wt, "pairs": n, "cells": cells,
+                          "gcups_incl_seeding": cells / wt / 1e9, "mapped_share": float(ok.mean()),
+                          "best_window_holds_origin": float(hit.mean()),
+                          "includes": "seed, two-strand reads, extract, SW score+end+CIGAR, best per read, "
+                                      "host count read-backs and buffer allocation"}
+            del mp
+        res[name] = sec
+        del rd, ro, out, w
+        torch.cuda.empty_cache()
+    return res
+
+
 def _graph_section(rank, n_pairs: int = 16384, reps: int = 50) -> dict:
     """Small batches, where per-call host work matters: the throughput
     workload's pair mix at n_pairs pairs, score + end + CIGAR, through
@@ -472,6 +577,11 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device")
     torch.cuda.set_device(local)
+    if args.only_seeding:
+        sec = _seeding_section(args, rank, steps=max(2, min(args.steps, 3)))
+        if rank == 0:
+            print(json.dumps({"seeding": sec}), flush=True)
+        return
     pg = None
     if ws > 1:
         import torch.distributed as dist
@@ -576,7 +686,7 @@ def main():
     filt = None
     if not args.no_filter:
         filt = _filter_section(args, rank, steps=max(2, min(args.steps, 5)), n_reads=args.filter_reads)
-    uneven = fullmix = graph = None
+    uneven = fullmix = graph = seeding = None
     if not args.no_extra and args.workload == "throughput":
         graph = _graph_section(rank)
         del batch
@@ -585,6 +695,9 @@ def main():
         if not args.no_filter:
             fullmix = _filter_section(args, rank, steps=max(2, min(args.steps, 3)), name="fullmix",
                                       n_reads=args.fullmix_reads, n_train=40_000, n_cal=15_000, epochs=8)
+        if not args.no_seeding:
+            torch.cuda.empty_cache()
+            seeding = _seeding_section(args, rank, steps=max(2, min(args.steps, 3)))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
@@ -602,7 +715,7 @@ def main():
                              "peak_basis": f"measured 16x2 DPX add-max rate {dpx_ops / 1e12:.2f} Tops/s "
                                            f"x 2 cells / {OPS_PER_CELL:g} ops per cell"},
                 "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "learned_filter": filt,
-                "uneven": uneven, "fullmix_sample": fullmix, "small_batch_graph": graph}
+                "uneven": uneven, "fullmix_sample": fullmix, "small_batch_graph": graph, "seeding": seeding}
         if rank == 0 and not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
         print(json.dumps(line), flush=True)

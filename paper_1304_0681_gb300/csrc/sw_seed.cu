@@ -28,7 +28,7 @@ namespace swgb {
 
 namespace {
 
-constexpr int kWarpHits = 1024;           // hit list of one warp (4 KB of shared memory)
+constexpr int kWarpHits = 512;            // hit list of one warp (2 KB of shared memory)
 constexpr int kSeedWarps = 8;             // warps per block of the main kernel
 constexpr int kTabTile = 4096;            // table entries per block of the table scan
 
@@ -222,21 +222,6 @@ __device__ __forceinline__ void bucket(const uint32_t *__restrict__ table, uint3
     hi = __ldg(table + code);
 }
 
-// Hits of a read-strand that pass the repeat filter (warp-uniform result).
-__device__ int64_t seed_hit_count(const uint32_t *reads, int64_t r0, int m, int strand, const uint32_t *table,
-                                  const SeedCfg &c, int lane)
-{
-    const int ns0 = n_phase(m, 0, c.p), ns = ns0 + n_phase(m, c.p.phase, c.p);
-    int64_t h = 0;
-    for (int t = lane; t < ns; t += 32) {
-        uint32_t lo, hi;
-        bucket(table, seed_code(reads, r0, m, seed_start(t, ns0, c.p), strand, c), lo, hi);
-        if (hi - lo <= (uint32_t)c.p.max_hits) h += hi - lo;
-    }
-    for (int d = 16; d > 0; d >>= 1) h += __shfl_xor_sync(0xffffffffu, h, d);
-    return h;
-}
-
 // Copy the hits of seeds tid, tid + nthreads, ... into list[] at slots taken
 // from *fill (a shared-memory counter).
 __device__ void seed_gather(const uint32_t *reads, int64_t r0, int m, int strand, const uint32_t *table,
@@ -275,6 +260,46 @@ __device__ void bitonic_sort(uint32_t *list, int n, int tid, int nthreads)
     }
 }
 
+// Ascending bitonic sort of list[0 .. 32 E) held in registers: lane l holds
+// elements l + 32 e.  Partners less than 32 apart sit in other lanes
+// (shuffles), those 32 or more apart in the same lane.
+template <int E>
+__device__ void sort_in_registers(uint32_t *list, int H, int lane)
+{
+    uint32_t x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = lane + 32 * e < H ? list[lane + 32 * e] : 0xFFFFFFFFu;
+#pragma unroll
+    for (int size = 2; size <= 32 * E; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int d = stride >> 5;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if (e & d) continue;
+                    const bool up = (((lane + 32 * e) & size) == 0);
+                    const uint32_t a = x[e], b = x[e | d];
+                    x[e] = up ? min(a, b) : max(a, b);
+                    x[e | d] = up ? max(a, b) : min(a, b);
+                }
+            } else {
+                const bool lower = (lane & stride) == 0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const uint32_t y = __shfl_xor_sync(0xffffffffu, x[e], stride);
+                    const bool up = (((lane + 32 * e) & size) == 0);
+                    x[e] = (lower == up) ? min(x[e], y) : max(x[e], y);
+                }
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < E; ++e) list[lane + 32 * e] = x[e];
+    __syncwarp();
+}
+
 // Regions -> merged regions -> CALs -> extended CALs, by one warp over the
 // sorted hits list[0 .. H).  Extended CAL c is written to list[2c],
 // list[2c + 1] (start, end); a CAL spans more than min_cal_len >= k bases,
@@ -286,17 +311,20 @@ __device__ int cal_pass(uint32_t *list, int H, const int64_t *__restrict__ off, 
     const SeedKParams &p = c.p;
     int ncal = 0;
     int64_t carry_s = -1;       // last hit of the previous chunk
-    int carry_c = -1;           // its chromosome
     int64_t carry_start = -1;   // start of the region open at the end of the previous chunk
     for (int base = 0; base < H; base += 32) {
         const int i = base + lane;
         const bool valid = i < H;
         const int64_t s = valid ? (int64_t)list[i] : 0;
-        const int ch = valid ? chrom_of(off, n_chrom, s) : -1;
         int64_t prev_s = __shfl_up_sync(0xffffffffu, s, 1);
-        int prev_c = __shfl_up_sync(0xffffffffu, ch, 1);
-        if (lane == 0) { prev_s = carry_s; prev_c = carry_c; }
-        const bool starts = valid && (i == 0 || s - prev_s - p.k >= p.merge_dist || ch != prev_c);
+        if (lane == 0) prev_s = carry_s;
+        // a hit close to the one before starts a region only across a
+        // chromosome border: the chromosome is looked up only then
+        bool starts = false;
+        if (valid) {
+            starts = i == 0 || s - prev_s - p.k >= p.merge_dist;
+            if (!starts) starts = chrom_of(off, n_chrom, s) != chrom_of(off, n_chrom, prev_s);
+        }
         const unsigned F = __ballot_sync(0xffffffffu, starts);
         // does the region of hit i end at i?
         bool next_starts = __shfl_down_sync(0xffffffffu, starts, 1);
@@ -304,7 +332,8 @@ __device__ int cal_pass(uint32_t *list, int H, const int64_t *__restrict__ off, 
             next_starts = true;
             if (i + 1 < H) {
                 const int64_t s1 = (int64_t)list[i + 1];
-                next_starts = s1 - s - p.k >= p.merge_dist || chrom_of(off, n_chrom, s1) != ch;
+                next_starts = s1 - s - p.k >= p.merge_dist ||
+                              chrom_of(off, n_chrom, s1) != chrom_of(off, n_chrom, s);
             }
         }
         const bool ends = valid && (i == H - 1 || next_starts);
@@ -316,6 +345,7 @@ __device__ int cal_pass(uint32_t *list, int H, const int64_t *__restrict__ off, 
         const bool is_cal = ends && rend - rstart + 1 > p.min_cal_len;
         int64_t es = 0, ee = 0;
         if (is_cal) {
+            const int ch = chrom_of(off, n_chrom, s);
             const int64_t lo = __ldg(off + ch), hi = __ldg(off + ch + 1);
             es = rstart - p.flank < lo ? lo : rstart - p.flank;
             ee = rend + p.flank > hi - 1 ? hi - 1 : rend + p.flank;
@@ -331,7 +361,6 @@ __device__ int cal_pass(uint32_t *list, int H, const int64_t *__restrict__ off, 
         }
         ncal += __popc(C);
         carry_s = __shfl_sync(0xffffffffu, s, 31);
-        carry_c = __shfl_sync(0xffffffffu, ch, 31);
         carry_start = __shfl_sync(0xffffffffu, rstart, 31);
         __syncwarp();
     }
@@ -432,7 +461,20 @@ k_seed(const uint32_t *__restrict__ reads, const int64_t *__restrict__ roff, int
             continue;
         }
         const int m = (int)m64;
-        const int64_t H = seed_hit_count(reads, r0, m, strand, table, c, lane);
+        // one lookup per seed: the buckets of seeds lane and lane + 32 stay
+        // in registers; seeds beyond the 64th (reads over about 390 bases)
+        // are looked up again when their hits are copied
+        const int ns0 = n_phase(m, 0, c.p), ns = ns0 + n_phase(m, c.p.phase, c.p);
+        uint32_t lo0 = 0, n0 = 0, lo1 = 0, n1 = 0;
+        int64_t H = 0;
+        for (int t = lane; t < ns; t += 32) {
+            uint32_t lo, hi;
+            bucket(table, seed_code(reads, r0, m, seed_start(t, ns0, c.p), strand, c), lo, hi);
+            const uint32_t cnt = hi - lo <= (uint32_t)c.p.max_hits ? hi - lo : 0u;
+            if (t < 32) { lo0 = lo; n0 = cnt; } else if (t < 64) { lo1 = lo; n1 = cnt; }
+            H += cnt;
+        }
+        for (int d = 16; d > 0; d >>= 1) H += __shfl_xor_sync(0xffffffffu, H, d);
         if (H == 0) {
             if (lane == 0) {
                 S.wcount[rs] = 0;
@@ -444,14 +486,36 @@ k_seed(const uint32_t *__restrict__ reads, const int64_t *__restrict__ roff, int
             if (lane == 0) S.ovf[atomicAdd(S.n_ovf, 1u)] = (int32_t)rs;
             continue;
         }
-        if (lane == 0) fills[wib] = 0;
-        __syncwarp();
-        seed_gather(reads, r0, m, strand, table, positions, c, list, &fills[wib], lane, 32);
+        uint32_t own = n0 + n1, at = own;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, at, d);
+            if (lane >= d) at += y;
+        }
+        at -= own;
+        for (uint32_t j = 0; j < n0; ++j) list[at + j] = __ldg(positions + lo0 + j);
+        for (uint32_t j = 0; j < n1; ++j) list[at + n0 + j] = __ldg(positions + lo1 + j);
+        if (ns > 64) {
+            if (lane == 31) fills[wib] = (int)(at + own);
+            __syncwarp();
+            for (int t = 64 + lane; t < ns; t += 32) {
+                uint32_t lo, hi;
+                bucket(table, seed_code(reads, r0, m, seed_start(t, ns0, c.p), strand, c), lo, hi);
+                if (hi - lo > (uint32_t)c.p.max_hits || hi == lo) continue;
+                const int a = atomicAdd(&fills[wib], (int)(hi - lo));
+                for (uint32_t j = lo; j < hi; ++j) list[a + (j - lo)] = __ldg(positions + j);
+            }
+        }
         __syncwarp();
         const int n = pow2_at_least((int)H);
-        for (int i = (int)H + lane; i < n && i < kWarpHits; i += 32) list[i] = 0xFFFFFFFFu;
-        __syncwarp();
-        bitonic_sort<false>(list, n, lane, 32);
+        if (n == 32) sort_in_registers<1>(list, (int)H, lane);
+        else if (n == 64) sort_in_registers<2>(list, (int)H, lane);
+        else if (n == 128) sort_in_registers<4>(list, (int)H, lane);
+        else if (n == 256) sort_in_registers<8>(list, (int)H, lane);
+        else {
+            for (int i = (int)H + lane; i < n; i += 32) list[i] = 0xFFFFFFFFu;
+            __syncwarp();
+            bitonic_sort<false>(list, n, lane, 32);
+        }
         finish_read_strand(list, (int)H, rs, off, n_chrom, c, S, lane);
         __syncwarp();
     }

@@ -342,6 +342,11 @@ GENOMES = {
     # 2-20 copies at 0-8% divergence; 200,000 introns of 50-2,000 bp.
     "human": dict(chrom_len=[x * 1_000_000 for x in HUMAN_MB], repeat_share=0.05, rep_len=(300, 6000),
                   rep_copies=(2, 20), rep_div=(0.0, 0.08), n_introns=200_000, intron=(50, 2000)),
+    # a quarter of "human" (774 Mb, same 24 chromosomes scaled, 50k introns):
+    # with k = 14 seeds it gives the random hits per seed of "human" with
+    # k = 15, in a quarter of the device memory (profiling captures)
+    "quarter": dict(chrom_len=[x * 250_000 for x in HUMAN_MB], repeat_share=0.05, rep_len=(300, 6000),
+                    rep_copies=(2, 20), rep_div=(0.0, 0.08), n_introns=50_000, intron=(50, 2000)),
     # 64 Mb in 8 chromosomes, same feature mix (full-size sampled parity
     # checks that the oracle can still scan).
     "medium": dict(chrom_len=[8_000_000] * 8, repeat_share=0.05, rep_len=(300, 6000), rep_copies=(2, 20),
