@@ -374,8 +374,8 @@ def _seeding_section(args, rank, steps: int) -> dict:
            "index": {"k": args.seed_k, "build_ms": index_ms, "positions": idx.n_positions,
                      "table_gb": idx.table.numel() * 4 / 1e9, "positions_gb": idx.positions.numel() * 4 / 1e9},
            "params": {f: getattr(p, f) for f, _ in p._fields_},
-           "paper_context": "stages C + D in isolation, 20 threads of a 64-core Opteron: T2 59.55 + 18.00 s, "
-                            "T4 265.31 (10 thr) ... see BASELINE.md; those stages only see reads stage B left "
+           "paper_context": "stages C + D in isolation, 20 threads of a 64-core Opteron (Table 1): T2 59.55 + "
+                            "18.00 s, T4 223.02 + 49.01 s per 2M reads; those stages only see reads stage B left "
                             "unmapped, these kernels seed every read"}
     for name in args.seed_sets.split(","):
         rs = synth.sample_reads(g, name, n_reads=2_000_000, seed=rank + 1)
