@@ -429,6 +429,33 @@ def _seeding_section(args, rank, steps: int) -> dict:
             ws_ = wv["strand"].cpu().numpy()[i]
             a = g.chrom_offsets[rs.chrom] + rs.pos
             hit = ok & (ws_ == rs.strand) & (st <= a) & (a <= en)
+            # the same reads from pinned host memory in 8 batches of 250k, by
+            # one worker stream and by two and three overlapping ones
+            n_b = 8
+            bnd = np.linspace(0, rs.n_reads, n_b + 1).astype(np.int64)
+            hb = []
+            for lo_, hi_ in zip(bnd[:-1], bnd[1:]):
+                sub = rs.reads[rs.read_offsets[lo_]:rs.read_offsets[hi_]]
+                hb.append((torch.from_numpy(synth.pack(sub)).pin_memory(),
+                           torch.from_numpy(rs.read_offsets[lo_:hi_ + 1] - rs.read_offsets[lo_]).pin_memory()))
+            pipe = {}
+            for ns in (1, 2, 3):
+                sd.map_batches(idx, hb, SCORING, n_streams=ns)  # warm each stream's scratch
+                torch.cuda.synchronize()
+                pw = []
+                for _ in range(steps):
+                    flush.zero_()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    sd.map_batches(idx, hb, SCORING, n_streams=ns)
+                    torch.cuda.synchronize()
+                    pw.append(time.perf_counter() - t0)
+                pipe[f"streams_{ns}"] = {"ms_per_2M_reads": statistics.mean(pw) * 1e3,
+                                         "reads_per_s": rs.n_reads / statistics.mean(pw)}
+            pipe["batches"] = n_b
+            pipe["includes"] = ("pinned host reads in, best hit per read out; each worker thread drives its own "
+                                "stream through seed, extract, SW + CIGAR, best")
+            sec["map_pipelined_from_host"] = pipe
             sec["map"] = {"ms_per_step": wt * 1e3, "reads_per_s": rs.n_reads / wt, "pairs": n, "cells": cells,
                           "gcups_incl_seeding": cells / wt / 1e9, "mapped_share": float(ok.mean()),
                           "best_window_holds_origin": float(hit.mean()),

@@ -243,13 +243,35 @@ int sw_best_per_read(const int32_t *score, const int64_t *cand_offsets, int64_t 
                      const uint8_t *pair_mask, int32_t *best_score, int32_t *best_cand, sw_stream_t stream);
 
 /*
- * Wait for `stream` and report problems the alignment kernels of the last
- * call on this device detected on the device (SW_ERR_CAPACITY when a CIGAR
- * slot overflowed, SW_ERR_INTERNAL when a consistency check failed).
+ * Wait for `stream` and report problems the kernels of the last call on
+ * `stream` detected on the device (SW_ERR_CAPACITY when a CIGAR slot
+ * overflowed, SW_ERR_INTERNAL when a consistency check failed, ...).
  * sw_batch_align returns once its kernels are enqueued, so a caller that
  * wants those errors calls this after it.
+ *
+ * Streams: the library keeps its scratch, status word and read-back slots
+ * per (device, stream).  Calls on one stream run in stream order; calls on
+ * different streams share no scratch, so batches on two streams may be in
+ * flight at once (each stream's scratch is grown on demand and kept until
+ * the process exits).  The queries below that take no stream
+ * (sw_last_traceback_split, sw_phase_times) refer to the device's most
+ * recent call; sw_phase_timing applies to every stream of the device.
  */
 int sw_sync_status(sw_stream_t stream);
+
+/*
+ * Free the library's scratch of `stream` on the current device (after
+ * waiting for the stream).  The next call on the stream allocates it again.
+ * The caller makes sure no other thread uses the stream meanwhile.
+ */
+int sw_stream_release(sw_stream_t stream);
+
+/*
+ * The CUDA error (cudaError_t value) behind the last SW_ERR_CUDA returned
+ * on this host thread, 0 if none; *name (if not NULL) receives its name
+ * (static storage).
+ */
+int sw_last_cuda_error(const char **name);
 
 /*
  * sw_batch_align_noalloc -- score and end cell of pair p = (read p, window p),

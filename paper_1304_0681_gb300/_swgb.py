@@ -21,7 +21,7 @@ ERRORS = {
 }
 
 #: every symbol include/swgb.h declares
-EXPORTS = ("sw_cigar_capacity", "sw_packed_bytes", "sw_batch_align", "sw_batch_align_indexed",
+EXPORTS = ("sw_cigar_capacity", "sw_packed_bytes", "sw_batch_align", "sw_stream_release", "sw_last_cuda_error", "sw_batch_align_indexed",
            "sw_batch_align_host", "sw_sync_status", "sw_strerror", "sw_launch_count", "sw_set_plan", "sw_set_traceback_mode",
            "sw_last_traceback_split", "sw_plan_create", "sw_plan_align", "sw_plan_status", "sw_plan_destroy",
            "sw_batch_align_host_dense", "sw_records", "sw_junction_table_words", "sw_junction_table_clear", "sw_junctions_detect",
@@ -35,9 +35,11 @@ EXPORTS = ("sw_cigar_capacity", "sw_packed_bytes", "sw_batch_align", "sw_batch_a
 
 
 class SwError(RuntimeError):
-    def __init__(self, code: int, what: str):
-        super().__init__(f"{what}: {ERRORS.get(code, code)} ({code})")
+    def __init__(self, code: int, what: str, cuda: str | None = None):
+        tail = f" [{cuda}]" if cuda else ""
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({code}){tail}")
         self.code = code
+        self.cuda = cuda
 
 
 class Scoring(ctypes.Structure):
@@ -108,6 +110,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_filter_select.restype = ctypes.c_int
     lib.sw_best_per_read.argtypes = [p, p, i64, p, p, p, p]
     lib.sw_best_per_read.restype = ctypes.c_int
+    lib.sw_stream_release.argtypes = [p]
+    lib.sw_stream_release.restype = ctypes.c_int
+    lib.sw_last_cuda_error.argtypes = [ctypes.POINTER(ctypes.c_char_p)]
+    lib.sw_last_cuda_error.restype = ctypes.c_int
     lib.sw_index_table_words.argtypes = [i32]
     lib.sw_index_table_words.restype = i64
     lib.sw_index_build.argtypes = [p, i64, p, i32, i32, p, p, p, p]
@@ -167,7 +173,12 @@ _lib = load()
 
 def _check(rc: int, what: str):
     if rc != SW_OK:
-        raise SwError(rc, what)
+        cuda = None
+        if rc == -3:  # SW_ERR_CUDA: name the CUDA error behind it
+            name = ctypes.c_char_p()
+            code = _lib.sw_last_cuda_error(ctypes.byref(name))
+            cuda = f"{name.value.decode() if name.value else '?'} ({code})"
+        raise SwError(rc, what, cuda)
 
 
 def _ptr(t):
@@ -453,3 +464,13 @@ def sw_extract_windows(genome, n_bases: int, start, length, n_windows: int, out,
                        stream=None) -> None:
     _check(_lib.sw_extract_windows(_ptr(genome), int(n_bases), _ptr(start), _ptr(length), int(n_windows), _ptr(out),
                                    int(cap_bases), _ptr(out_offsets), _stream(stream)), "sw_extract_windows")
+
+
+def sw_stream_release(stream=None) -> None:
+    _check(_lib.sw_stream_release(_stream(stream)), "sw_stream_release")
+
+
+def sw_last_cuda_error() -> tuple:
+    name = ctypes.c_char_p()
+    code = _lib.sw_last_cuda_error(ctypes.byref(name))
+    return code, (name.value.decode() if name.value else "")

@@ -54,7 +54,7 @@ int launch_alu_probe(int kind, int64_t iters, int blocks, int threads, uint32_t 
     default: return SW_ERR_INVALID_ARG;
     }
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 }  // namespace swgb

@@ -150,7 +150,7 @@ int launch_check_counts(const ClassInfo *info, const int32_t *expect, int32_t *s
 {
     k_check_counts<<<(N_CLASS + 255) / 256, 256, 0, st>>>(info, expect, status);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring sc,
@@ -167,7 +167,7 @@ int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring
     k_scan<<<N_CLASS, N_NBUCKET, 0, st>>>(hist, info->count, bucket_start, cursor);
     k_scatter<<<(unsigned)blocks, threads, 0, st>>>(keys, n_pairs, cursor, order);
     count_launch(3);
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, const int32_t *class_count, int32_t *hist,
@@ -180,7 +180,7 @@ int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, const int32_t *cla
     k_scan<<<N_CLASS, N_NBUCKET, 0, st>>>(hist, class_count, bucket_start, cursor);
     k_scatter<<<(unsigned)blocks, threads, 0, st>>>(keys, n_pairs, cursor, order);
     count_launch(2);
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 }  // namespace swgb

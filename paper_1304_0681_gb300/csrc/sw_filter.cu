@@ -562,7 +562,7 @@ int launch_features(const FeatureParams &P, cudaStream_t st)
 {
     k_features<<<grid_for(P.n_reads, 8, 152 * 16), 256, 0, st>>>(P);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int64_t mlp_floats() { return MD_TOTAL; }
@@ -572,14 +572,14 @@ int launch_mlp_init(float *model, uint64_t seed, cudaStream_t st)
     k_mlp_init<<<grid_for(MD_STEP + 1, 256, 152 * 4), 256, 0, st>>>(model, seed);
     k_mlp_refresh<<<64, 256, 0, st>>>(model);
     count_launch(2);
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int launch_mlp_refresh(float *model, cudaStream_t st)
 {
     k_mlp_refresh<<<64, 256, 0, st>>>(model);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 static size_t forward_smem() { return (size_t)(256 * W1S + 64 * W2S) * 2 + (256 + 64 + 64) * 4; }
@@ -590,13 +590,12 @@ int launch_mlp_forward(const float *model, const uint16_t *feat, int64_t n, floa
 {
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)forward_smem()) !=
-            cudaSuccess)
+        if (cuda_failed(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)forward_smem())))
             return SW_ERR_CUDA;
         attr = true;
     }
     int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_mlp_forward, 128, forward_smem()) != cudaSuccess)
+    if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_mlp_forward, 128, forward_smem())))
         return SW_ERR_CUDA;
     const int64_t tiles = (n + 15) / 16;
     int64_t blocks = (tiles + 3) / 4;
@@ -604,7 +603,7 @@ int launch_mlp_forward(const float *model, const uint16_t *feat, int64_t n, floa
     k_mlp_forward<<<(unsigned)std::max<int64_t>(blocks, 1), 128, forward_smem(), st>>>(
         model, reinterpret_cast<const __nv_bfloat16 *>(feat), n, out);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int launch_mlp_grad(float *model, const uint16_t *feat, const float *target, const int32_t *idx, int64_t n,
@@ -612,19 +611,18 @@ int launch_mlp_grad(float *model, const uint16_t *feat, const float *target, con
 {
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem()) !=
-            cudaSuccess)
+        if (cuda_failed(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem())))
             return SW_ERR_CUDA;
         attr = true;
     }
-    if (cudaMemsetAsync(model + MD_G, 0, sizeof(float) * MD_NP, st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(model + MD_G, 0, sizeof(float) * MD_NP, st))) return SW_ERR_CUDA;
     // enough samples per block that the per-block gradient flush stays small
     const int64_t per_block = std::max<int64_t>(64, (n + sm_count - 1) / sm_count);
     const int64_t blocks = (n + per_block - 1) / per_block;
     k_mlp_grad<<<(unsigned)std::max<int64_t>(blocks, 1), GR_THREADS, grad_smem(), st>>>(
         model, reinterpret_cast<const __nv_bfloat16 *>(feat), target, idx, n, per_block);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int launch_mlp_adam(float *model, float lr, int32_t step, cudaStream_t st)
@@ -632,7 +630,7 @@ int launch_mlp_adam(float *model, float lr, int32_t step, cudaStream_t st)
     k_mlp_adam<<<grid_for(MD_NP, 256, 152 * 2), 256, 0, st>>>(model, lr, step);
     k_mlp_refresh<<<64, 256, 0, st>>>(model);
     count_launch(2);
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int launch_select(const float *pred, const int64_t *cand_off, int64_t n_reads, int32_t k, float tau, uint8_t *mask,
@@ -640,7 +638,7 @@ int launch_select(const float *pred, const int64_t *cand_off, int64_t n_reads, i
 {
     k_select<<<grid_for(n_reads, 128, 152 * 32), 128, 0, st>>>(pred, cand_off, n_reads, k, tau, mask);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int launch_best_per_read(const int32_t *score, const int64_t *cand_off, int64_t n_reads, const uint8_t *mask,
@@ -649,7 +647,7 @@ int launch_best_per_read(const int32_t *score, const int64_t *cand_off, int64_t 
     k_best_per_read<<<grid_for(n_reads, 128, 152 * 32), 128, 0, st>>>(score, cand_off, n_reads, mask, best,
                                                                        best_cand);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 }  // namespace swgb
@@ -663,8 +661,8 @@ static std::atomic<int32_t> g_mlp_kind{SW_MLP_AUTO};  // set by sw_set_mlp_kerne
 static int sm_count_now(int *sms)
 {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return SW_ERR_NO_DEVICE;
-    if (cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaGetDevice(&dev))) return SW_ERR_NO_DEVICE;
+    if (cuda_failed(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev))) return SW_ERR_CUDA;
     return SW_OK;
 }
 

@@ -30,7 +30,7 @@ int launch_cigar_to_host(const uint32_t *ops, const int64_t *off, const int32_t 
     if (blocks < 1) blocks = 1;
     k_cigar_to_host<<<(unsigned)blocks, 256, 0, st>>>(ops, off, n_ops, n_pairs, host_ops);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 }  // namespace swgb
@@ -110,7 +110,7 @@ int exclusive_scan(F v, int64_t n, int64_t *out, int64_t *blk, cudaStream_t st)
     k_scan_blocks<<<1, 1024, 0, st>>>(blk, n_blk, out + n);
     k_scan_write<<<(unsigned)n_blk, 256, 0, st>>>(v, n, blk, out);
     count_launch(3);
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 struct CapOf {  // CIGAR capacity of pair p: 2 m + 3 runs
@@ -155,7 +155,7 @@ int launch_cap_offsets(const int64_t *read_off, int64_t n_pairs, int64_t *cig_of
 
 int launch_scan_i32(const int32_t *v, int64_t n, int64_t *out, int64_t *blk, cudaStream_t st)
 {
-    if (n == 0) return cudaMemsetAsync(out, 0, sizeof(int64_t), st) == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    if (n == 0) return !cuda_failed(cudaMemsetAsync(out, 0, sizeof(int64_t), st)) ? SW_OK : SW_ERR_CUDA;
     return exclusive_scan(I32Of{v}, n, out, blk, st);
 }
 
@@ -169,7 +169,7 @@ int launch_dense_cigar(const uint32_t *ops, const int64_t *off, const int32_t *n
     if (blocks < 1) blocks = 1;
     k_dense_copy<<<(unsigned)blocks, 256, 0, st>>>(ops, off, n_ops, doff, n_pairs, dense, dense_cap);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 }  // namespace swgb

@@ -294,8 +294,7 @@ int launch_mlp_forward_tc(const float *model, const uint16_t *feat, int64_t n, f
 {
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL) !=
-            cudaSuccess)
+        if (cuda_failed(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL)))
             return SW_ERR_CUDA;
         attr = true;
     }
@@ -305,7 +304,7 @@ int launch_mlp_forward_tc(const float *model, const uint16_t *feat, int64_t n, f
     k_mlp_forward_tc<<<grid, 256, SM_TOTAL, st>>>(model, reinterpret_cast<const __nv_bfloat16 *>(feat), n, out,
                                                    status);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 }  // namespace swgb

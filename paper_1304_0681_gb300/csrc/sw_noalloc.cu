@@ -65,14 +65,14 @@ extern "C" int sw_batch_align_noalloc(const uint8_t *reads, const int64_t *read_
     if (((uintptr_t)reads & 15u) || ((uintptr_t)windows & 15u)) return SW_ERR_INVALID_ARG;
 
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return SW_ERR_NO_DEVICE;
+    if (cuda_failed(cudaGetDevice(&dev)) || dev < 0 || dev >= kNaMaxDevices) return SW_ERR_NO_DEVICE;
     int32_t *scratch = nullptr;
     {
         // first call on this device: look up the array's device address
         std::lock_guard<std::mutex> lk(g_na_mu);
         if (!g_na_ptr[dev]) {
             void *ptr = nullptr;
-            if (cudaGetSymbolAddress(&ptr, g_sw_noalloc_scratch) != cudaSuccess || !ptr) {
+            if (cuda_failed(cudaGetSymbolAddress(&ptr, g_sw_noalloc_scratch)) || !ptr) {
                 cudaGetLastError();
                 return SW_ERR_CUDA;
             }
@@ -84,14 +84,14 @@ extern "C" int sw_batch_align_noalloc(const uint8_t *reads, const int64_t *read_
     const PairSet ps{(const uint32_t *)reads, read_offsets, nullptr, (const uint32_t *)windows, window_offsets};
 
     // the array keeps the previous call's contents: clear counter, status, max
-    if (cudaMemsetAsync(scratch, 0, kNaHeader * sizeof(int32_t), st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(scratch, 0, kNaHeader * sizeof(int32_t), st))) return SW_ERR_CUDA;
     const int64_t pblocks = std::min<int64_t>((n_pairs + 255) / 256, 152 * 8);
     k_noalloc_prepare<<<(unsigned)pblocks, 256, 0, st>>>(ps, n_pairs, scratch);
     count_launch();
-    if (cudaGetLastError() != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaGetLastError())) return SW_ERR_CUDA;
     int32_t hdr[3] = {0, 0, 0};
-    if (cudaMemcpyAsync(hdr, scratch, sizeof(hdr), cudaMemcpyDeviceToHost, st) != cudaSuccess) return SW_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemcpyAsync(hdr, scratch, sizeof(hdr), cudaMemcpyDeviceToHost, st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaStreamSynchronize(st))) return SW_ERR_CUDA;
     if (hdr[1] & ST_BAD_INPUT) return SW_ERR_DEVICE_INPUT;
     if (hdr[1] & ST_UNSUPPORTED) return SW_ERR_UNSUPPORTED;
 
@@ -113,7 +113,7 @@ extern "C" int sw_batch_align_noalloc(const uint8_t *reads, const int64_t *read_
     L.status = scratch + 1;
     int regs = 0, bps = 0, sms = 0;
     if (score_kernel_regs(rows, MODE_I32, &regs, &bps, 128) != SW_OK || bps < 1) return SW_ERR_INTERNAL;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return SW_ERR_CUDA;
     const int64_t groups = 32 / lanes;
     const int64_t warps = (n_pairs + groups - 1) / groups;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((warps + 3) / 4, (int64_t)bps * sms));

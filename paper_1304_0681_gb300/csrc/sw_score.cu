@@ -399,7 +399,7 @@ static int launch_r(int mode, bool fma, const ScoreLaunch &L, int blocks, int th
     else if (mode == MODE_I16W) k_score<R, MODE_I16W, false><<<blocks, threads, 0, st>>>(L);
     else return SW_ERR_INTERNAL;
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 // The FMA-pipe diagonal add needs every substitution score minus gap_open
@@ -445,9 +445,9 @@ int score_kernel_regs(int rows, int mode, int *regs, int *max_blocks_per_sm, int
     }
     if (!fn) return SW_ERR_INVALID_ARG;
     cudaFuncAttributes a;
-    if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaFuncGetAttributes(&a, fn))) return SW_ERR_CUDA;
     *regs = a.numRegs;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, fn, threads, 0) != cudaSuccess)
+    if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, fn, threads, 0)))
         return SW_ERR_CUDA;
     return SW_OK;
 }

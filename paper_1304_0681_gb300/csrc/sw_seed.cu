@@ -713,7 +713,7 @@ int launch_index_build(const uint32_t *genome, int64_t n_bases, const int64_t *c
                        int32_t *status, cudaStream_t st)
 {
     const uint64_t n_tab = 1ull << (2 * k);
-    if (cudaMemsetAsync(table, 0, n_tab * sizeof(uint32_t), st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(table, 0, n_tab * sizeof(uint32_t), st))) return SW_ERR_CUDA;
     k_check_offsets<<<grid_for(n_chrom, 256, sm_count, 4), 256, 0, st>>>(chrom_off, n_chrom, 0, n_bases, status);
     const int g = grid_for((n_bases + 15) / 16, 256, sm_count, 8);
     k_index_pass<true><<<g, 256, 0, st>>>(genome, n_bases, chrom_off, n_chrom, k, table, positions, status);
@@ -723,7 +723,7 @@ int launch_index_build(const uint32_t *genome, int64_t n_bases, const int64_t *c
     k_tab_write<<<(unsigned)n_blk, 256, 0, st>>>((uint4 *)table, blk);
     k_index_pass<false><<<g, 256, 0, st>>>(genome, n_bases, chrom_off, n_chrom, k, table, positions, status);
     count_launch(6);
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 size_t seed_scratch_bytes(int64_t n_reads, int64_t capacity)
@@ -760,9 +760,8 @@ int launch_seed_windows(const uint32_t *reads, const int64_t *roff, int64_t n_re
     c.mask = p.k >= 16 ? 0xFFFFFFFFu : ((1u << (2 * p.k)) - 1u);
     c.max_read = max_read;
     c.block_hits = block_hits;
-    if (cudaMemsetAsync(scratch, 0, 16, st) != cudaSuccess) return SW_ERR_CUDA;
-    if (cudaFuncSetAttribute(k_seed_large, cudaFuncAttributeMaxDynamicSharedMemorySize, block_hits * 4) !=
-        cudaSuccess)
+    if (cuda_failed(cudaMemsetAsync(scratch, 0, 16, st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaFuncSetAttribute(k_seed_large, cudaFuncAttributeMaxDynamicSharedMemorySize, block_hits * 4)))
         return SW_ERR_CUDA;
     k_check_offsets<<<grid_for(n_reads, 256, sm_count, 4), 256, 0, st>>>(roff, n_reads, -1, -1, status);
     k_seed<<<grid_for(n_rs * 32, kSeedWarps * 32, sm_count, 8), kSeedWarps * 32, 0, st>>>(
@@ -774,7 +773,7 @@ int launch_seed_windows(const uint32_t *reads, const int64_t *roff, int64_t n_re
     if (rc) return rc;
     k_seed_place<<<grid_for(n_rs + 1, 256, sm_count, 8), 256, 0, st>>>(S, woff, n_reads, chrom_off, n_chrom, out);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int launch_extract_windows(const uint32_t *genome, int64_t n_bases, const int64_t *start, const int32_t *len,
@@ -788,7 +787,7 @@ int launch_extract_windows(const uint32_t *genome, int64_t n_bases, const int64_
     k_extract<<<grid_for(n * 32, 256, sm_count, 8), 256, 0, st>>>(genome, n_bases, start, len, woff, n, dst,
                                                                   cap_bases, status);
     count_launch(2);
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int launch_two_strands(const uint32_t *reads, const int64_t *roff, int64_t n, uint32_t *dst, int64_t cap_bases,
@@ -800,7 +799,7 @@ int launch_two_strands(const uint32_t *reads, const int64_t *roff, int64_t n, ui
     k_two_strands<<<grid_for(2 * n * 32, 256, sm_count, 8), 256, 0, st>>>(reads, roff, n, dst, cap_bases, doff,
                                                                           status);
     count_launch(3);
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 }  // namespace swgb

@@ -220,7 +220,7 @@ int launch_records(const int32_t *score, const int32_t *end, const sw_cigar_t &c
     k_record_write<<<(unsigned)n_blk, threads, 0, st>>>(score, end, cig.ops, cig.offsets, cig.n_ops, n_pairs, chrom,
                                                          pos, strand, min_score, blk_off, out);
     count_launch(3);
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int launch_junctions(const uint32_t *wins, const int64_t *win_off, const int32_t *score, const int32_t *end,
@@ -235,24 +235,24 @@ int launch_junctions(const uint32_t *wins, const int64_t *win_off, const int32_t
                                                          (unsigned long long *)(table + capacity), capacity, log2cap,
                                                          status);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int launch_table_clear(uint64_t *table, int64_t capacity, cudaStream_t st)
 {
     k_table_clear<<<grid_for(capacity, 256), 256, 0, st>>>(table, (unsigned long long *)(table + capacity), capacity);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int launch_table_export(const uint64_t *table, int64_t capacity, sw_junction_t *out, int64_t max_out,
                         int64_t *out_count, cudaStream_t st)
 {
-    if (cudaMemsetAsync(out_count, 0, sizeof(int64_t), st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(out_count, 0, sizeof(int64_t), st))) return SW_ERR_CUDA;
     k_table_export<<<grid_for(capacity, 256), 256, 0, st>>>(table, (const unsigned long long *)(table + capacity),
                                                              capacity, out, max_out, (unsigned long long *)out_count);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 }  // namespace swgb

@@ -923,7 +923,7 @@ int launch_tb_keys(const TbParams &P, int64_t n_pairs, const int32_t *score_keys
     if (blocks < 1) blocks = 1;
     k_tb_keys<<<(unsigned)blocks, threads, 0, st>>>(P, n_pairs, score_keys, tb_keys, hist, info);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStream_t st)
@@ -954,7 +954,7 @@ int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStre
     } else if (L.tiled) k_traceback<true><<<blocks, threads, 0, st>>>(L);
     else k_traceback<false><<<blocks, threads, 0, st>>>(L);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return launch_status();
 }
 
 int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads, bool packed16, int lanes)
@@ -973,7 +973,7 @@ int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads, bool packed1
         default: break;
         }
     }
-    return e == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return cuda_failed(e) ? SW_ERR_CUDA : SW_OK;
 }
 
 }  // namespace swgb

@@ -24,6 +24,9 @@ static std::atomic<int64_t> g_launches{0};
 static std::atomic<int32_t> g_tb_mode{SW_TB_AUTO};
 void count_launch(int n) { g_launches += n; }
 
+thread_local int g_cuda_error = 0;
+void note_cuda_error(cudaError_t e) { g_cuda_error = (int)e; }
+
 namespace {
 
 constexpr int kThreads = 128;
@@ -51,8 +54,14 @@ struct PlanOverride {
     int32_t max_read_len, lanes, rows;
 };
 
+// Library state of one (device, stream): scratch buffers, the status word
+// of the stream's last call, pinned read-back slots, events and auxiliary
+// streams.  Calls on one stream are ordered by the stream; calls on two
+// streams get two states, so their work may overlap on the GPU without
+// sharing scratch.
 struct DeviceState {
     bool ready = false;
+    int dev = 0;
     int sm_count = 0;
     int cc_major = 0, cc_minor = 0;
     Buffer fixed, dyn;
@@ -80,7 +89,10 @@ struct DeviceState {
     std::mutex mu;
 };
 
-DeviceState g_dev[kMaxDevices];
+std::mutex g_state_mu;
+std::vector<std::pair<std::pair<int, cudaStream_t>, DeviceState *>> g_states;  // never freed
+DeviceState *g_last_state[kMaxDevices] = {};   // the state of the device's most recent call
+bool g_timing[kMaxDevices] = {};               // sw_phase_timing, per device
 std::mutex g_plan_mu;
 std::vector<PlanOverride> g_plans;
 
@@ -91,17 +103,17 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // stream capture.)
 int fork_streams(DeviceState *ds, cudaStream_t st, int n)
 {
-    if (cudaEventRecord(ds->fork_ev, st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaEventRecord(ds->fork_ev, st))) return SW_ERR_CUDA;
     for (int k = 0; k < n; ++k)
-        if (cudaStreamWaitEvent(ds->aux[k], ds->fork_ev, 0) != cudaSuccess) return SW_ERR_CUDA;
+        if (cuda_failed(cudaStreamWaitEvent(ds->aux[k], ds->fork_ev, 0))) return SW_ERR_CUDA;
     return SW_OK;
 }
 
 int join_streams(DeviceState *ds, cudaStream_t st, int n)
 {
     for (int k = 0; k < n; ++k) {
-        if (cudaEventRecord(ds->join_ev[k], ds->aux[k]) != cudaSuccess) return SW_ERR_CUDA;
-        if (cudaStreamWaitEvent(st, ds->join_ev[k], 0) != cudaSuccess) return SW_ERR_CUDA;
+        if (cuda_failed(cudaEventRecord(ds->join_ev[k], ds->aux[k]))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaStreamWaitEvent(st, ds->join_ev[k], 0))) return SW_ERR_CUDA;
     }
     return SW_OK;
 }
@@ -110,12 +122,12 @@ int ensure(Buffer &b, size_t bytes)
 {
     if (b.bytes >= bytes) return SW_OK;
     // pending work may still use the old buffer
-    if (cudaDeviceSynchronize() != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaDeviceSynchronize())) return SW_ERR_CUDA;
     if (b.ptr) cudaFree(b.ptr);
     b.ptr = nullptr;
     b.bytes = 0;
     const size_t want = align_up(bytes + std::min<size_t>(bytes / 4, (size_t)256 << 20), 1 << 20);
-    if (cudaMalloc(&b.ptr, want) != cudaSuccess) {
+    if (cuda_failed(cudaMalloc(&b.ptr, want))) {
         cudaGetLastError();
         return SW_ERR_CUDA;
     }
@@ -123,36 +135,89 @@ int ensure(Buffer &b, size_t bytes)
     return SW_OK;
 }
 
-int device_state(DeviceState **out)
+int device_state(DeviceState **out, cudaStream_t st)
 {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SW_ERR_NO_DEVICE;
-    DeviceState &s = g_dev[dev];
+    if (cuda_failed(cudaGetDevice(&dev)) || dev < 0 || dev >= kMaxDevices) return SW_ERR_NO_DEVICE;
+    std::lock_guard<std::mutex> glk(g_state_mu);
+    DeviceState *found = nullptr;
+    for (auto &e : g_states)
+        if (e.first.first == dev && e.first.second == st) found = e.second;
+    if (!found) {
+        found = new (std::nothrow) DeviceState;
+        if (!found) return SW_ERR_CUDA;
+        found->dev = dev;
+        g_states.push_back({{dev, st}, found});
+    }
+    DeviceState &s = *found;
     if (!s.ready) {
         cudaDeviceProp prop;
-        if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return SW_ERR_NO_DEVICE;
+        if (cuda_failed(cudaGetDeviceProperties(&prop, dev))) return SW_ERR_NO_DEVICE;
         s.sm_count = prop.multiProcessorCount;
         s.cc_major = prop.major;
         s.cc_minor = prop.minor;
-        if (cudaMallocHost(&s.info_host, sizeof(ClassInfo)) != cudaSuccess) return SW_ERR_CUDA;
-        if (cudaMallocHost(&s.tbinfo_host, sizeof(TbClassInfo)) != cudaSuccess) return SW_ERR_CUDA;
-        if (cudaEventCreateWithFlags(&s.last_done, cudaEventDisableTiming) != cudaSuccess) return SW_ERR_CUDA;
+        if (cuda_failed(cudaMallocHost(&s.info_host, sizeof(ClassInfo)))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaMallocHost(&s.tbinfo_host, sizeof(TbClassInfo)))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaEventCreateWithFlags(&s.last_done, cudaEventDisableTiming))) return SW_ERR_CUDA;
         for (cudaEvent_t &e : s.phase)
-            if (cudaEventCreate(&e) != cudaSuccess) return SW_ERR_CUDA;
+            if (cuda_failed(cudaEventCreate(&e))) return SW_ERR_CUDA;
         for (int k = 0; k < kAuxStreams; ++k) {
-            if (cudaStreamCreateWithFlags(&s.aux[k], cudaStreamNonBlocking) != cudaSuccess) return SW_ERR_CUDA;
-            if (cudaEventCreateWithFlags(&s.join_ev[k], cudaEventDisableTiming) != cudaSuccess) return SW_ERR_CUDA;
+            if (cuda_failed(cudaStreamCreateWithFlags(&s.aux[k], cudaStreamNonBlocking))) return SW_ERR_CUDA;
+            if (cuda_failed(cudaEventCreateWithFlags(&s.join_ev[k], cudaEventDisableTiming))) return SW_ERR_CUDA;
         }
-        if (cudaEventCreateWithFlags(&s.fork_ev, cudaEventDisableTiming) != cudaSuccess) return SW_ERR_CUDA;
-        if (cudaStreamCreateWithFlags(&s.copy_in, cudaStreamNonBlocking) != cudaSuccess) return SW_ERR_CUDA;
-        if (cudaStreamCreateWithFlags(&s.copy_out, cudaStreamNonBlocking) != cudaSuccess) return SW_ERR_CUDA;
+        if (cuda_failed(cudaEventCreateWithFlags(&s.fork_ev, cudaEventDisableTiming))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaStreamCreateWithFlags(&s.copy_in, cudaStreamNonBlocking))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaStreamCreateWithFlags(&s.copy_out, cudaStreamNonBlocking))) return SW_ERR_CUDA;
         for (cudaEvent_t &e : s.host_in_ev)
-            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SW_ERR_CUDA;
-        if (cudaEventCreateWithFlags(&s.host_out_ev, cudaEventDisableTiming) != cudaSuccess) return SW_ERR_CUDA;
+            if (cuda_failed(cudaEventCreateWithFlags(&e, cudaEventDisableTiming))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaEventCreateWithFlags(&s.host_out_ev, cudaEventDisableTiming))) return SW_ERR_CUDA;
         s.ready = true;
     }
+    s.timing = g_timing[dev];
+    g_last_state[dev] = &s;
     *out = &s;
     return SW_OK;
+}
+
+void free_state(DeviceState *s)
+{
+    for (Buffer *b : {&s->fixed, &s->dyn, &s->stage, &s->misc})
+        if (b->ptr) {
+            cudaFree(b->ptr);
+            b->ptr = nullptr;
+            b->bytes = 0;
+        }
+    if (s->info_host) cudaFreeHost(s->info_host);
+    if (s->tbinfo_host) cudaFreeHost(s->tbinfo_host);
+    if (s->last_done) cudaEventDestroy(s->last_done);
+    for (cudaEvent_t e : s->phase)
+        if (e) cudaEventDestroy(e);
+    for (int k = 0; k < kAuxStreams; ++k) {
+        if (s->aux[k]) cudaStreamDestroy(s->aux[k]);
+        if (s->join_ev[k]) cudaEventDestroy(s->join_ev[k]);
+    }
+    if (s->fork_ev) cudaEventDestroy(s->fork_ev);
+    if (s->copy_in) cudaStreamDestroy(s->copy_in);
+    if (s->copy_out) cudaStreamDestroy(s->copy_out);
+    for (cudaEvent_t e : s->host_in_ev)
+        if (e) cudaEventDestroy(e);
+    if (s->host_out_ev) cudaEventDestroy(s->host_out_ev);
+}
+
+// The state of the device's most recent call (for the queries that take no
+// stream), or the default stream's.
+int last_state(DeviceState **out)
+{
+    int dev = 0;
+    if (cuda_failed(cudaGetDevice(&dev)) || dev < 0 || dev >= kMaxDevices) return SW_ERR_NO_DEVICE;
+    {
+        std::lock_guard<std::mutex> glk(g_state_mu);
+        if (g_last_state[dev]) {
+            *out = g_last_state[dev];
+            return SW_OK;
+        }
+    }
+    return device_state(out, 0);
 }
 
 bool scoring_ok(const sw_scoring_t *s)
@@ -214,10 +279,10 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
               int32_t *out_score, int32_t *out_end, const sw_cigar_t *cig, cudaStream_t st)
 {
     DeviceState *ds = nullptr;
-    int rc = device_state(&ds);
+    int rc = device_state(&ds, st);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(ds->mu);
-    if (ds->last_recorded && cudaStreamWaitEvent(st, ds->last_done, 0) != cudaSuccess) return SW_ERR_CUDA;
+    if (ds->last_recorded && cuda_failed(cudaStreamWaitEvent(st, ds->last_done, 0))) return SW_ERR_CUDA;
 
     const Scoring sc{scoring->match, scoring->mismatch, scoring->gap_open, scoring->gap_extend};
     const size_t nh = (size_t)N_CLASS * N_NBUCKET;
@@ -243,16 +308,16 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
     ds->last_status = &info->status;
 
     ds->timed_cells_valid = false;
-    if (ds->timing && cudaEventRecord(ds->phase[0], st) != cudaSuccess) return SW_ERR_CUDA;
-    if (cudaMemsetAsync(hist, 0, sizeof(int32_t) * nh, st) != cudaSuccess) return SW_ERR_CUDA;
-    if (cudaMemsetAsync(info, 0, sizeof(ClassInfo), st) != cudaSuccess) return SW_ERR_CUDA;
-    if (cudaMemsetAsync(counters, 0, sizeof(int32_t) * 4 * N_CLASS, st) != cudaSuccess) return SW_ERR_CUDA;
+    if (ds->timing && cuda_failed(cudaEventRecord(ds->phase[0], st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(info, 0, sizeof(ClassInfo), st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(counters, 0, sizeof(int32_t) * 4 * N_CLASS, st))) return SW_ERR_CUDA;
     if ((rc = launch_classify(ps, n_reads, n_pairs, sc, keys, hist, bstart, cursor, info, order, out_score,
                               out_end, cig ? cig->n_ops : nullptr, st)))
         return rc;
-    if (cudaMemcpyAsync(ds->info_host, info, sizeof(ClassInfo), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    if (cuda_failed(cudaMemcpyAsync(ds->info_host, info, sizeof(ClassInfo), cudaMemcpyDeviceToHost, st)))
         return SW_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaStreamSynchronize(st))) return SW_ERR_CUDA;
     const ClassInfo ci = *ds->info_host;
     if (ci.status) return status_to_code(ci.status);
 
@@ -299,13 +364,13 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
     }
     if ((rc = ensure(ds->dyn, std::max<size_t>(need_dyn, 256)))) return rc;
 
-    if (ds->timing && cudaEventRecord(ds->phase[1], st) != cudaSuccess) return SW_ERR_CUDA;
+    if (ds->timing && cuda_failed(cudaEventRecord(ds->phase[1], st))) return SW_ERR_CUDA;
     // with a CIGAR, the score kernels' epilogue also writes the traceback
     // cost keys and the class table the traceback is sized from
     if (cig) {
-        if (cudaMemsetAsync(hist, 0, sizeof(int32_t) * nh, st) != cudaSuccess) return SW_ERR_CUDA;
-        if (cudaMemsetAsync(tbinfo, 0, sizeof(TbClassInfo), st) != cudaSuccess) return SW_ERR_CUDA;
-        if (cudaMemsetAsync(tb_keys, 0xFF, sizeof(int32_t) * n_pairs, st) != cudaSuccess) return SW_ERR_CUDA;
+        if (cuda_failed(cudaMemsetAsync(hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaMemsetAsync(tbinfo, 0, sizeof(TbClassInfo), st))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaMemsetAsync(tb_keys, 0xFF, sizeof(int32_t) * n_pairs, st))) return SW_ERR_CUDA;
     }
     // one launch per class; several classes fork onto the auxiliary streams
     const int n_aux_score = runs.size() > 1 ? (int)std::min<size_t>(runs.size(), kAuxStreams) : 0;
@@ -335,16 +400,15 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         if ((rc = launch_score(r.plan.rows, r.mode, L, r.score_blocks, kThreads, cs))) return rc;
     }
     if (n_aux_score && (rc = join_streams(ds, st, n_aux_score))) return rc;
-    if (ds->timing && cudaEventRecord(ds->phase[2], st) != cudaSuccess) return SW_ERR_CUDA;
+    if (ds->timing && cuda_failed(cudaEventRecord(ds->phase[2], st))) return SW_ERR_CUDA;
     if (cig) {
         // order each class by traceback cost, then size the slabs from the
         // per-class maxima (a second, small read-back)
         TbParams P{ps, sc, out_score, out_end, cig->ops, cig->offsets, cig->n_ops, kTbLanes, kSmallSlabWords};
         if ((rc = launch_scan_scatter(tb_keys, n_pairs, info->count, hist, bstart, cursor, tb_order, st))) return rc;
-        if (cudaMemcpyAsync(ds->tbinfo_host, tbinfo, sizeof(TbClassInfo), cudaMemcpyDeviceToHost, st) !=
-            cudaSuccess)
+        if (cuda_failed(cudaMemcpyAsync(ds->tbinfo_host, tbinfo, sizeof(TbClassInfo), cudaMemcpyDeviceToHost, st)))
             return SW_ERR_CUDA;
-        if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
+        if (cuda_failed(cudaStreamSynchronize(st))) return SW_ERR_CUDA;
         const TbClassInfo ti = *ds->tbinfo_host;
         int tbps = 0;
         if ((rc = traceback_kernel_occupancy(&tbps, kThreads, false, 1))) return rc;
@@ -495,7 +559,7 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
                 for (int64_t r0 = 0; r0 < t.count; r0 += round_items) {
                     B.order = tb_order + t.start + r0;
                     B.n_items = std::min<int64_t>(round_items, t.count - r0);
-                    if (r0 > 0 && cudaMemsetAsync(B.work_counter, 0, sizeof(int32_t), ts) != cudaSuccess)
+                    if (r0 > 0 && cuda_failed(cudaMemsetAsync(B.work_counter, 0, sizeof(int32_t), ts)))
                         return SW_ERR_CUDA;
                     if ((rc = launch_traceback(B, t.blocks, kThreads, ts))) return rc;
                 }
@@ -509,20 +573,20 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
         }
         if (n_aux_tb && (rc = join_streams(ds, st, n_aux_tb))) return rc;
     }
-    if (ds->timing && cudaEventRecord(ds->phase[3], st) != cudaSuccess) return SW_ERR_CUDA;
+    if (ds->timing && cuda_failed(cudaEventRecord(ds->phase[3], st))) return SW_ERR_CUDA;
     ds->timed_cells_valid = ds->timing;
-    if (cudaEventRecord(ds->last_done, st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaEventRecord(ds->last_done, st))) return SW_ERR_CUDA;
     ds->last_recorded = true;
     return SW_OK;
 }
 
 int read_status(DeviceState *ds, cudaStream_t st)
 {
-    if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaStreamSynchronize(st))) return SW_ERR_CUDA;
     std::lock_guard<std::mutex> lk(ds->mu);
     if (!ds->last_status) return SW_OK;
     int32_t v = 0;
-    if (cudaMemcpy(&v, ds->last_status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemcpy(&v, ds->last_status, sizeof(v), cudaMemcpyDeviceToHost))) return SW_ERR_CUDA;
     return status_to_code(v);
 }
 
@@ -610,8 +674,8 @@ int plan_build(sw_plan *pl, DeviceState *ds, cudaStream_t st)
     pl->expect = (int32_t *)(fx + o_expect);
 
     // classify once (it reads offsets only) and read the class table back
-    if (cudaMemsetAsync(pl->hist, 0, sizeof(int32_t) * nh, st) != cudaSuccess) return SW_ERR_CUDA;
-    if (cudaMemsetAsync(pl->info, 0, sizeof(ClassInfo), st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(pl->hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(pl->info, 0, sizeof(ClassInfo), st))) return SW_ERR_CUDA;
     int32_t *tmp_score = pl->tb_keys, *tmp_end = nullptr;  // empty-window outputs go to scratch
     if ((rc = ensure(pl->dyn, sizeof(int32_t) * 2 * std::max<int64_t>(n_pairs, 1)))) return rc;
     tmp_end = (int32_t *)pl->dyn.ptr;
@@ -619,16 +683,16 @@ int plan_build(sw_plan *pl, DeviceState *ds, cudaStream_t st)
                               pl->info, pl->order, tmp_score, tmp_end, nullptr, st)))
         return rc;
     ClassInfo ci;
-    if (cudaMemcpyAsync(&ci, pl->info, sizeof(ClassInfo), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    if (cuda_failed(cudaMemcpyAsync(&ci, pl->info, sizeof(ClassInfo), cudaMemcpyDeviceToHost, st)))
         return SW_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaStreamSynchronize(st))) return SW_ERR_CUDA;
     if (ci.status) return status_to_code(ci.status);
     {
         std::vector<int32_t> ex(3 * N_CLASS);
         std::memcpy(ex.data(), ci.count, sizeof(int32_t) * N_CLASS);
         std::memcpy(ex.data() + N_CLASS, ci.max_m, sizeof(int32_t) * N_CLASS);
         std::memcpy(ex.data() + 2 * N_CLASS, ci.max_n, sizeof(int32_t) * N_CLASS);
-        if (cudaMemcpy(pl->expect, ex.data(), sizeof(int32_t) * 3 * N_CLASS, cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cuda_failed(cudaMemcpy(pl->expect, ex.data(), sizeof(int32_t) * 3 * N_CLASS, cudaMemcpyHostToDevice)))
             return SW_ERR_CUDA;
     }
 
@@ -735,9 +799,9 @@ int plan_execute(sw_plan *pl, int32_t *out_score, int32_t *out_end, const sw_cig
     int rc = SW_OK;
     const size_t nh = (size_t)N_CLASS * N_NBUCKET;
     const PairSet &ps = pl->ps;
-    if (cudaMemsetAsync(pl->hist, 0, sizeof(int32_t) * nh, st) != cudaSuccess) return SW_ERR_CUDA;
-    if (cudaMemsetAsync(pl->info, 0, sizeof(ClassInfo), st) != cudaSuccess) return SW_ERR_CUDA;
-    if (cudaMemsetAsync(pl->counters, 0, sizeof(int32_t) * 4 * N_CLASS, st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(pl->hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(pl->info, 0, sizeof(ClassInfo), st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(pl->counters, 0, sizeof(int32_t) * 4 * N_CLASS, st))) return SW_ERR_CUDA;
     if ((rc = launch_classify(ps, pl->n_reads, pl->n_pairs, pl->sc, pl->keys, pl->hist, pl->bstart, pl->cursor,
                               pl->info, pl->order, out_score, out_end, cig ? cig->n_ops : nullptr, st)))
         return rc;
@@ -759,8 +823,8 @@ int plan_execute(sw_plan *pl, int32_t *out_score, int32_t *out_end, const sw_cig
     }
     if (!pl->cigar || !cig) return SW_OK;
     TbParams P{ps, pl->sc, out_score, out_end, cig->ops, cig->offsets, cig->n_ops, 1, kSmallSlabWords};
-    if (cudaMemsetAsync(pl->hist, 0, sizeof(int32_t) * nh, st) != cudaSuccess) return SW_ERR_CUDA;
-    if (cudaMemsetAsync(pl->tbinfo, 0, sizeof(TbClassInfo), st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(pl->hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(pl->tbinfo, 0, sizeof(TbClassInfo), st))) return SW_ERR_CUDA;
     if ((rc = launch_tb_keys(P, pl->n_pairs, pl->keys, pl->tb_keys, pl->hist, pl->tbinfo, st))) return rc;
     if ((rc = launch_scan_scatter(pl->tb_keys, pl->n_pairs, pl->info->count, pl->hist, pl->bstart, pl->cursor,
                                   pl->tb_order, st)))
@@ -785,7 +849,7 @@ int plan_execute(sw_plan *pl, int32_t *out_score, int32_t *out_end, const sw_cig
             for (int64_t r0 = 0; r0 < t.count; r0 += round_items) {
                 B.order = pl->tb_order + t.start + r0;
                 B.n_items = std::min<int64_t>(round_items, t.count - r0);
-                if (r0 > 0 && cudaMemsetAsync(B.work_counter, 0, sizeof(int32_t), st) != cudaSuccess)
+                if (r0 > 0 && cuda_failed(cudaMemsetAsync(B.work_counter, 0, sizeof(int32_t), st)))
                     return SW_ERR_CUDA;
                 if ((rc = launch_traceback(B, t.blocks, kThreads, st))) return rc;
             }
@@ -861,7 +925,7 @@ int sw_batch_align_host(const uint8_t *reads, const int64_t *read_offsets, const
     if (rc || n_pairs == 0) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     DeviceState *ds = nullptr;
-    if ((rc = device_state(&ds))) return rc;
+    if ((rc = device_state(&ds, (cudaStream_t)stream))) return rc;
     const int64_t rb = sw_packed_bytes(read_offsets[n_pairs]);
     const int64_t wb = sw_packed_bytes(window_offsets[n_pairs]);
     const int64_t n_cig = out_cigar ? out_cigar->offsets[n_pairs] : 0;
@@ -890,10 +954,10 @@ int sw_batch_align_host(const uint8_t *reads, const int64_t *read_offsets, const
     const int64_t chunk = std::max<int64_t>(kHostChunkMin, (n_pairs + n_split - 1) / n_split);
     const int64_t n_chunks = (n_pairs + chunk - 1) / chunk;
     auto h2d = [&](size_t o, const void *src, size_t n) {
-        return n == 0 || cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, ds->copy_in) == cudaSuccess;
+        return n == 0 || !cuda_failed(cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, ds->copy_in));
     };
     auto d2h = [&](void *dst, size_t o, size_t n) {
-        return n == 0 || cudaMemcpyAsync(dst, b + o, n, cudaMemcpyDeviceToHost, ds->copy_out) == cudaSuccess;
+        return n == 0 || !cuda_failed(cudaMemcpyAsync(dst, b + o, n, cudaMemcpyDeviceToHost, ds->copy_out));
     };
     // the whole words holding bases [q0, q1)
     auto word_bytes = [](int64_t q0, int64_t q1, int64_t total, int64_t &lo, int64_t &n) {
@@ -911,7 +975,7 @@ int sw_batch_align_host(const uint8_t *reads, const int64_t *read_offsets, const
         if (!h2d(o_ro + 8 * p0, read_offsets + p0, 8 * (p1 - p0 + 1))) return false;
         if (!h2d(o_wo + 8 * p0, window_offsets + p0, 8 * (p1 - p0 + 1))) return false;
         if (out_cigar && !h2d(o_co + 8 * p0, out_cigar->offsets + p0, 8 * (p1 - p0 + 1))) return false;
-        return cudaEventRecord(ds->host_in_ev[c % kHostChunks], ds->copy_in) == cudaSuccess;
+        return !cuda_failed(cudaEventRecord(ds->host_in_ev[c % kHostChunks], ds->copy_in));
     };
     // CIGAR runs go straight into the caller's slots when its op buffer is
     // pinned host memory the device can address; else the slots are copied
@@ -924,9 +988,9 @@ int sw_batch_align_host(const uint8_t *reads, const int64_t *read_offsets, const
         cudaGetLastError();  // a pageable pointer is not an error here
     }
     // the copy streams start after what the caller enqueued on st
-    if (cudaEventRecord(ds->fork_ev, st) != cudaSuccess) return SW_ERR_CUDA;
-    if (cudaStreamWaitEvent(ds->copy_in, ds->fork_ev, 0) != cudaSuccess) return SW_ERR_CUDA;
-    if (cudaStreamWaitEvent(ds->copy_out, ds->fork_ev, 0) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaEventRecord(ds->fork_ev, st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaStreamWaitEvent(ds->copy_in, ds->fork_ev, 0))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaStreamWaitEvent(ds->copy_out, ds->fork_ev, 0))) return SW_ERR_CUDA;
     if (!copy_in(0)) return SW_ERR_CUDA;
     for (int64_t c = 0; c < n_chunks; ++c) {
         const int64_t p0 = c * chunk, p1 = std::min<int64_t>(n_pairs, p0 + chunk), np = p1 - p0;
@@ -935,7 +999,7 @@ int sw_batch_align_host(const uint8_t *reads, const int64_t *read_offsets, const
             // its event slot must be free: the chunk kHostChunks back has started
             if (!copy_in(c + 1)) return SW_ERR_CUDA;
         }
-        if (cudaStreamWaitEvent(st, ds->host_in_ev[c % kHostChunks], 0) != cudaSuccess) return SW_ERR_CUDA;
+        if (cuda_failed(cudaStreamWaitEvent(st, ds->host_in_ev[c % kHostChunks], 0))) return SW_ERR_CUDA;
         sw_cigar_t dc{};
         if (out_cigar) {
             dc.ops = (uint32_t *)(b + o_ops);
@@ -951,8 +1015,8 @@ int sw_batch_align_host(const uint8_t *reads, const int64_t *read_offsets, const
             (rc = launch_cigar_to_host(dc.ops, dc.offsets, dc.n_ops, np, host_ops_dev, st)))
             return rc;
         // this chunk's outputs, once its kernels are done
-        if (cudaEventRecord(ds->host_out_ev, st) != cudaSuccess) return SW_ERR_CUDA;
-        if (cudaStreamWaitEvent(ds->copy_out, ds->host_out_ev, 0) != cudaSuccess) return SW_ERR_CUDA;
+        if (cuda_failed(cudaEventRecord(ds->host_out_ev, st))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaStreamWaitEvent(ds->copy_out, ds->host_out_ev, 0))) return SW_ERR_CUDA;
         if (!d2h(out_score + p0, o_s + 4 * p0, 4 * np) || !d2h(out_end + 2 * p0, o_e + 8 * p0, 8 * np))
             return SW_ERR_CUDA;
         if (out_cigar) {
@@ -962,15 +1026,47 @@ int sw_batch_align_host(const uint8_t *reads, const int64_t *read_offsets, const
         }
     }
     // st ends after the last copy out
-    if (cudaEventRecord(ds->host_out_ev, ds->copy_out) != cudaSuccess) return SW_ERR_CUDA;
-    if (cudaStreamWaitEvent(st, ds->host_out_ev, 0) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaEventRecord(ds->host_out_ev, ds->copy_out))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaStreamWaitEvent(st, ds->host_out_ev, 0))) return SW_ERR_CUDA;
     return read_status(ds, st);
+}
+
+int sw_last_cuda_error(const char **name)
+{
+    if (name) *name = cudaGetErrorName((cudaError_t)g_cuda_error);
+    return g_cuda_error;
+}
+
+int sw_stream_release(sw_stream_t stream)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SW_ERR_NO_DEVICE;
+    const cudaStream_t st = (cudaStream_t)stream;
+    DeviceState *s = nullptr;
+    {
+        std::lock_guard<std::mutex> glk(g_state_mu);
+        for (size_t i = 0; i < g_states.size(); ++i)
+            if (g_states[i].first.first == dev && g_states[i].first.second == st) {
+                s = g_states[i].second;
+                g_states.erase(g_states.begin() + i);
+                break;
+            }
+        if (s && g_last_state[dev] == s) g_last_state[dev] = nullptr;
+    }
+    if (!s) return SW_OK;
+    const int rc = cuda_failed(cudaStreamSynchronize(st)) ? SW_ERR_CUDA : SW_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        free_state(s);
+    }
+    delete s;
+    return rc;
 }
 
 int sw_sync_status(sw_stream_t stream)
 {
     DeviceState *ds = nullptr;
-    int rc = device_state(&ds);
+    int rc = device_state(&ds, (cudaStream_t)stream);
     if (rc) return rc;
     return read_status(ds, (cudaStream_t)stream);
 }
@@ -1029,7 +1125,7 @@ int sw_last_traceback_split(int64_t *out2)
 {
     if (!out2) return SW_ERR_INVALID_ARG;
     DeviceState *ds = nullptr;
-    const int rc = device_state(&ds);
+    const int rc = last_state(&ds);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(ds->mu);
     out2[0] = ds->tb_split[0];
@@ -1039,11 +1135,10 @@ int sw_last_traceback_split(int64_t *out2)
 
 int sw_phase_timing(int32_t enable)
 {
-    DeviceState *ds = nullptr;
-    int rc = device_state(&ds);
-    if (rc) return rc;
-    std::lock_guard<std::mutex> lk(ds->mu);
-    ds->timing = enable != 0;
+    int dev = 0;
+    if (cuda_failed(cudaGetDevice(&dev)) || dev < 0 || dev >= kMaxDevices) return SW_ERR_NO_DEVICE;
+    std::lock_guard<std::mutex> glk(g_state_mu);
+    g_timing[dev] = enable != 0;
     return SW_OK;
 }
 
@@ -1051,13 +1146,13 @@ int sw_phase_times(float *ms3)
 {
     if (!ms3) return SW_ERR_INVALID_ARG;
     DeviceState *ds = nullptr;
-    int rc = device_state(&ds);
+    int rc = last_state(&ds);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(ds->mu);
     if (!ds->timed_cells_valid) return SW_ERR_INVALID_ARG;
-    if (cudaEventSynchronize(ds->phase[3]) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaEventSynchronize(ds->phase[3]))) return SW_ERR_CUDA;
     for (int i = 0; i < 3; ++i)
-        if (cudaEventElapsedTime(&ms3[i], ds->phase[i], ds->phase[i + 1]) != cudaSuccess) return SW_ERR_CUDA;
+        if (cuda_failed(cudaEventElapsedTime(&ms3[i], ds->phase[i], ds->phase[i + 1]))) return SW_ERR_CUDA;
     return SW_OK;
 }
 
@@ -1065,12 +1160,12 @@ int sw_alu_probe(int32_t kind, int64_t iters, double *ops_per_s, sw_stream_t str
 {
     if (!ops_per_s || iters < 1 || kind < 0 || kind > 6) return SW_ERR_INVALID_ARG;
     DeviceState *ds = nullptr;
-    int rc = device_state(&ds);
+    int rc = device_state(&ds, (cudaStream_t)stream);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const int threads = 256, blocks = ds->sm_count * 8;
     uint32_t *out = nullptr;
-    if (cudaMalloc(&out, sizeof(uint32_t) * threads * blocks) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMalloc(&out, sizeof(uint32_t) * threads * blocks))) return SW_ERR_CUDA;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1079,7 +1174,7 @@ int sw_alu_probe(int32_t kind, int64_t iters, double *ops_per_s, sw_stream_t str
     if (!rc) rc = launch_alu_probe(kind, iters, blocks, threads, out, st);
     cudaEventRecord(e1, st);
     float ms = 0.f;
-    if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+    if (!rc && (cuda_failed(cudaEventSynchronize(e1)) || cuda_failed(cudaEventElapsedTime(&ms, e0, e1))))
         rc = SW_ERR_CUDA;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1099,7 +1194,7 @@ int sw_plan_create(const int64_t *read_offsets, int64_t n_reads, const int64_t *
     if (pair_read && n_reads < 1) return SW_ERR_INVALID_ARG;
     if (n_pairs > (int64_t)INT32_MAX - 64) return SW_ERR_UNSUPPORTED;
     DeviceState *ds = nullptr;
-    int rc = device_state(&ds);
+    int rc = device_state(&ds, (cudaStream_t)stream);
     if (rc) return rc;
     sw_plan *pl = new (std::nothrow) sw_plan();
     if (!pl) return SW_ERR_INVALID_ARG;
@@ -1129,7 +1224,7 @@ int sw_plan_align(sw_plan_t *plan, const uint8_t *reads, const uint8_t *windows,
     if (out_cigar && (!out_cigar->ops || !out_cigar->offsets || !out_cigar->n_ops)) return SW_ERR_INVALID_ARG;
     if (out_cigar && !plan->cigar) return SW_ERR_INVALID_ARG;
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return SW_ERR_INVALID_ARG;
+    if (cuda_failed(cudaGetDevice(&dev)) || dev != plan->device) return SW_ERR_INVALID_ARG;
     plan->ps.reads = (const uint32_t *)reads;
     plan->ps.wins = (const uint32_t *)windows;
     return plan_execute(plan, out_score, out_end, out_cigar, (cudaStream_t)stream);
@@ -1138,9 +1233,9 @@ int sw_plan_align(sw_plan_t *plan, const uint8_t *reads, const uint8_t *windows,
 int sw_plan_status(sw_plan_t *plan, sw_stream_t stream)
 {
     if (!plan) return SW_ERR_INVALID_ARG;
-    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaStreamSynchronize((cudaStream_t)stream))) return SW_ERR_CUDA;
     int32_t v = 0;
-    if (cudaMemcpy(&v, &plan->info->status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemcpy(&v, &plan->info->status, sizeof(v), cudaMemcpyDeviceToHost))) return SW_ERR_CUDA;
     return status_to_code(v);
 }
 
@@ -1173,7 +1268,7 @@ int sw_batch_align_host_dense(const uint8_t *reads, const int64_t *read_offsets,
     }
     cudaStream_t st = (cudaStream_t)stream;
     DeviceState *ds = nullptr;
-    if ((rc = device_state(&ds))) return rc;
+    if ((rc = device_state(&ds, (cudaStream_t)stream))) return rc;
     const int64_t rb = sw_packed_bytes(read_offsets[n_pairs]);
     const int64_t wb = sw_packed_bytes(window_offsets[n_pairs]);
     // device slots of 2m + 3 runs per pair
@@ -1199,10 +1294,10 @@ int sw_batch_align_host_dense(const uint8_t *reads, const int64_t *read_offsets,
     }
     uint8_t *b = (uint8_t *)ds->stage.ptr;
     auto h2d = [&](size_t o, const void *src, size_t n) {
-        return n == 0 || cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, st) == cudaSuccess;
+        return n == 0 || !cuda_failed(cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, st));
     };
     auto d2h = [&](void *dst, size_t o, size_t n) {
-        return n == 0 || cudaMemcpyAsync(dst, b + o, n, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+        return n == 0 || !cuda_failed(cudaMemcpyAsync(dst, b + o, n, cudaMemcpyDeviceToHost, st));
     };
     if (!h2d(o_r, reads, rb) || !h2d(o_w, windows, wb) || !h2d(o_ro, read_offsets, 8 * (n_pairs + 1)) ||
         !h2d(o_wo, window_offsets, 8 * (n_pairs + 1)))
@@ -1222,7 +1317,7 @@ int sw_batch_align_host_dense(const uint8_t *reads, const int64_t *read_offsets,
     if (!d2h(out_score, o_s, 4 * n_pairs) || !d2h(out_end, o_e, 8 * n_pairs) ||
         !d2h(offsets_out, o_do, 8 * (n_pairs + 1)))
         return SW_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaStreamSynchronize(st))) return SW_ERR_CUDA;
     const int64_t total = offsets_out[n_pairs];
     const int64_t n_copy = std::min<int64_t>(total, ops_cap);
     if (!d2h(ops_out, o_dense, 4 * n_copy)) return SW_ERR_CUDA;
@@ -1239,12 +1334,12 @@ namespace swgb {
 int aux_status_word(cudaStream_t st, int32_t **status)
 {
     DeviceState *ds = nullptr;
-    int rc = device_state(&ds);
+    int rc = device_state(&ds, st);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(ds->mu);
     if ((rc = ensure(ds->misc, 256))) return rc;
     *status = (int32_t *)ds->misc.ptr;
-    if (cudaMemsetAsync(*status, 0, sizeof(int32_t), st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(*status, 0, sizeof(int32_t), st))) return SW_ERR_CUDA;
     ds->last_status = *status;
     return SW_OK;
 }
@@ -1259,7 +1354,7 @@ static int stage_e_status(DeviceState *ds, size_t extra, cudaStream_t st, int32_
     if (rc) return rc;
     *status = (int32_t *)ds->misc.ptr;
     *scratch = (uint8_t *)ds->misc.ptr + 256;
-    if (cudaMemsetAsync(*status, 0, sizeof(int32_t), st) != cudaSuccess) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(*status, 0, sizeof(int32_t), st))) return SW_ERR_CUDA;
     ds->last_status = *status;
     return SW_OK;
 }
@@ -1270,13 +1365,13 @@ int sw_records(const int32_t *score, const int32_t *end, const sw_cigar_t *cigar
 {
     if (n_pairs < 0 || !out_count) return SW_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    if (n_pairs == 0) return cudaMemsetAsync(out_count, 0, sizeof(int64_t), st) == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    if (n_pairs == 0) return !cuda_failed(cudaMemsetAsync(out_count, 0, sizeof(int64_t), st)) ? SW_OK : SW_ERR_CUDA;
     if (!score || !end || !cigar || !cigar->ops || !cigar->offsets || !cigar->n_ops || !window_chrom ||
         !window_pos || !window_strand || !out_records)
         return SW_ERR_INVALID_ARG;
     if (n_pairs > (int64_t)INT32_MAX - 64) return SW_ERR_UNSUPPORTED;
     DeviceState *ds = nullptr;
-    int rc = device_state(&ds);
+    int rc = device_state(&ds, (cudaStream_t)stream);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(ds->mu);
     const int64_t n_blk = (n_pairs + 255) / 256;
@@ -1313,7 +1408,7 @@ int sw_junctions_detect(const uint8_t *windows, const int64_t *window_offsets, c
         !cigar->offsets || !cigar->n_ops || !window_chrom || !window_pos)
         return SW_ERR_INVALID_ARG;
     DeviceState *ds = nullptr;
-    int rc = device_state(&ds);
+    int rc = device_state(&ds, (cudaStream_t)stream);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(ds->mu);
     cudaStream_t st = (cudaStream_t)stream;
@@ -1347,7 +1442,7 @@ int sw_index_build(const uint8_t *genome, int64_t n_bases, const int64_t *chrom_
         return SW_ERR_INVALID_ARG;
     if (n_bases >= (int64_t)UINT32_MAX) return SW_ERR_UNSUPPORTED;
     DeviceState *ds = nullptr;
-    int rc = device_state(&ds);
+    int rc = device_state(&ds, (cudaStream_t)stream);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(ds->mu);
     cudaStream_t st = (cudaStream_t)stream;
@@ -1390,8 +1485,8 @@ int sw_seed_windows(const uint32_t *table, const uint32_t *positions, const int6
     if (n_reads > (int64_t)INT32_MAX / 2 - 1 || capacity >= (int64_t)UINT32_MAX) return SW_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     if (n_reads == 0) {
-        if (cudaMemsetAsync(out_count, 0, sizeof(int64_t), st) != cudaSuccess ||
-            cudaMemsetAsync(out->cand_offsets, 0, sizeof(int64_t), st) != cudaSuccess)
+        if (cuda_failed(cudaMemsetAsync(out_count, 0, sizeof(int64_t), st)) ||
+            cuda_failed(cudaMemsetAsync(out->cand_offsets, 0, sizeof(int64_t), st)))
             return SW_ERR_CUDA;
         return SW_OK;
     }
@@ -1399,7 +1494,7 @@ int sw_seed_windows(const uint32_t *table, const uint32_t *positions, const int6
         !out->pos || !out->strand || !out->pair_read)
         return SW_ERR_INVALID_ARG;
     DeviceState *ds = nullptr;
-    if ((rc = device_state(&ds))) return rc;
+    if ((rc = device_state(&ds, (cudaStream_t)stream))) return rc;
     std::lock_guard<std::mutex> lk(ds->mu);
     int32_t *status = nullptr;
     uint8_t *scratch = nullptr;
@@ -1417,11 +1512,11 @@ int sw_reads_two_strands(const uint8_t *reads, const int64_t *read_offsets, int6
     if (n_reads < 0 || cap_bases < 0 || !out_offsets) return SW_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     if (n_reads == 0)
-        return cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), st) == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+        return !cuda_failed(cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), st)) ? SW_OK : SW_ERR_CUDA;
     if (!reads || ((uintptr_t)reads & 15u) || !read_offsets || !out || ((uintptr_t)out & 15u))
         return SW_ERR_INVALID_ARG;
     DeviceState *ds = nullptr;
-    int rc = device_state(&ds);
+    int rc = device_state(&ds, (cudaStream_t)stream);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(ds->mu);
     int32_t *status = nullptr;
@@ -1438,11 +1533,11 @@ int sw_extract_windows(const uint8_t *genome, int64_t n_bases, const int64_t *st
     if (n_windows < 0 || cap_bases < 0 || n_bases < 0 || !out_offsets) return SW_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     if (n_windows == 0)
-        return cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), st) == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+        return !cuda_failed(cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), st)) ? SW_OK : SW_ERR_CUDA;
     if (!genome || ((uintptr_t)genome & 15u) || !start || !length || !out || ((uintptr_t)out & 15u))
         return SW_ERR_INVALID_ARG;
     DeviceState *ds = nullptr;
-    int rc = device_state(&ds);
+    int rc = device_state(&ds, (cudaStream_t)stream);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(ds->mu);
     int32_t *status = nullptr;

@@ -191,6 +191,16 @@ constexpr int64_t MD_TOTAL = MD_W2T + 8192;
 
 void count_launch(int n = 1);
 
+// The CUDA error behind the last SW_ERR_CUDA of this host thread.
+void note_cuda_error(cudaError_t e);
+inline bool cuda_failed(cudaError_t e)
+{
+    if (e == cudaSuccess) return false;
+    note_cuda_error(e);
+    return true;
+}
+inline int launch_status() { return cuda_failed(cudaGetLastError()) ? SW_ERR_CUDA : SW_OK; }
+
 // Exclusive scan of int32 values v[0 .. n) into out[0 .. n] (out[n] = the
 // total); blk holds (n + 255) / 256 + 1 int64 words.
 int launch_scan_i32(const int32_t *v, int64_t n, int64_t *out, int64_t *blk, cudaStream_t st);

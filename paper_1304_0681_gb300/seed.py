@@ -167,3 +167,96 @@ def map_reads(index: KmerIndex, reads, read_offsets, n_reads: int, scoring, para
         _swgb.sw_best_per_read(score, win["cand_offsets"], n_reads, None, best, bcand, stream)
     _swgb.sw_sync_status(stream)
     return Mapped(win, reads2, roff2, wb, woff, score[:n], end[:2 * n], cg, best[:n_reads], bcand[:n_reads])
+
+
+@dataclass
+class BatchResult:
+    best_score: np.ndarray   # per read, -1 when no window
+    best_cand: np.ndarray    # index of the best window within the read's windows
+    best_start: np.ndarray   # its reference start (-1 when none)
+    best_strand: np.ndarray
+    n_windows: int
+
+
+def _map_host_batch(index: KmerIndex, packed: torch.Tensor, offsets: torch.Tensor, scoring, params, cigar,
+                    stream) -> BatchResult:
+    dev = index.table.device
+    rd = packed.to(dev, non_blocking=True)
+    ro = offsets.to(dev, non_blocking=True)
+    n_reads = offsets.numel() - 1
+    mp = map_reads(index, rd, ro, n_reads, scoring, params, cigar=cigar)
+    w = mp.windows
+    bc = mp.best_cand.to(torch.int64)
+    ok = bc >= 0
+    i = torch.where(ok, w["cand_offsets"][:-1] + bc.clamp(min=0), torch.zeros_like(bc))
+    if w["count"]:
+        start = torch.where(ok, w["start"][i], torch.full_like(bc, -1))
+        strand = torch.where(ok, w["strand"][i].to(torch.int64), torch.full_like(bc, -1))
+    else:
+        start = strand = torch.full_like(bc, -1)
+    out = torch.stack([mp.best_score.to(torch.int64), bc, start, strand]).cpu()
+    return BatchResult(out[0].numpy().astype(np.int32), out[1].numpy().astype(np.int32), out[2].numpy(),
+                       out[3].numpy().astype(np.int8), w["count"])
+
+
+_STREAMS: dict = {}
+
+
+def _worker_streams(dev, n: int) -> list:
+    """The same n worker streams on every call (the library keeps scratch
+    per stream: new streams on each call would each grow their own)."""
+    key = str(dev)
+    pool = _STREAMS.setdefault(key, [])
+    while len(pool) < n:
+        pool.append(torch.cuda.Stream(device=dev))
+    return pool[:n]
+
+
+def map_batches(index: KmerIndex, batches, scoring, params: SeedParams | None = None, cigar: bool = True,
+                n_streams: int = 2) -> list:
+    """Map a sequence of host batches, each (packed reads, read offsets) as
+    pinned CPU tensors: copy in, seed, extract, align, best hit, copy the
+    best hits back.  With n_streams > 1, that many worker threads each drive
+    their own CUDA stream, so one batch's host round trips and kernel tails
+    overlap other batches' kernels (the library keeps separate scratch per
+    stream).  Returns one BatchResult per batch, in order."""
+    import threading
+
+    batches = list(batches)
+    results = [None] * len(batches)
+    errors = []
+    dev = index.table.device
+    next_item = [0]
+    lock = threading.Lock()
+
+    streams = _worker_streams(dev, max(n_streams, 1))
+
+    def worker(w):
+        torch.cuda.set_device(dev)
+        s = streams[w]
+        with torch.cuda.stream(s):
+            while True:
+                with lock:
+                    if errors or next_item[0] >= len(batches):
+                        return
+                    k = next_item[0]
+                    next_item[0] += 1
+                try:
+                    packed, offsets = batches[k]
+                    results[k] = _map_host_batch(index, packed, offsets, scoring, params, cigar, s)
+                except BaseException as e:  # reported to the caller below
+                    with lock:
+                        errors.append(e)
+                    return
+
+    if n_streams <= 1:
+        worker(0)
+    else:
+        threads = [threading.Thread(target=worker, args=(w,)) for w in range(n_streams)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+    if errors:
+        raise errors[0]
+    return results

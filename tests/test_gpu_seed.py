@@ -258,3 +258,80 @@ def test_full_size_sampled_parity():
         np.testing.assert_array_equal(got["length"][lo:hi], ref["end"][rlo:rhi] - ref["start"][rlo:rhi] + 1)
         np.testing.assert_array_equal(got["strand"][lo:hi], ref["strand"][rlo:rhi])
         np.testing.assert_array_equal(got["pos"][lo:hi], ref["pos"][rlo:rhi])
+
+
+def test_pipelined_batches_match_one_map():
+    """Batches mapped by three workers on three streams give, read for
+    read, the best hits of one map over all reads (and of the oracle)."""
+    torch = _torch()
+    from paper_1304_0681_gb300.seed import map_batches, map_reads
+    g = synth.genome("small", seed=17)
+    rs = synth.sample_reads(g, "T2", n_reads=3000, seed=18, splice=0.1,
+                            lengths=((100, .6), (250, .3), (40, .1)))
+    idx = _index(g)
+    bounds = [0, 500, 1200, 1201, 2000, 3000]
+    batches = []
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        sub = rs.reads[rs.read_offsets[a]:rs.read_offsets[b]]
+        off = rs.read_offsets[a:b + 1] - rs.read_offsets[a]
+        batches.append((torch.from_numpy(synth.pack(sub)).pin_memory(), torch.from_numpy(off).pin_memory()))
+    rd, ro = _reads_dev(rs)
+    whole = map_reads(idx, rd, ro, rs.n_reads, SC)
+    want_score = whole.best_score.cpu().numpy()
+    want_cand = whole.best_cand.cpu().numpy()
+    for ns in (1, 3):
+        res = map_batches(idx, batches, SC, n_streams=ns)
+        np.testing.assert_array_equal(np.concatenate([r.best_score for r in res]), want_score)
+        np.testing.assert_array_equal(np.concatenate([r.best_cand for r in res]), want_cand)
+    ref = so.seed_windows(g.packed, g.chrom_offsets, rs.reads, rs.read_offsets, _oparams(_params()),
+                          read_ids=range(0, 3000, 97))
+    c = g.codes()
+    for j, r in enumerate(range(0, 3000, 97)):
+        best = -1
+        for i in range(ref["cand_offsets"][j], ref["cand_offsets"][j + 1]):
+            seq = rs.read(r) if ref["strand"][i] == 0 else so.revcomp(rs.read(r))
+            s, _, _, _ = oracle.align(seq, c[ref["start"][i]:ref["end"][i] + 1], oracle.Scoring(*SC), cigar=False)
+            best = max(best, s)
+        assert want_score[r] == best, r
+
+
+def test_status_is_per_stream():
+    """A capacity error on one stream is reported there and not on another."""
+    import paper_1304_0681_gb300 as sw
+    from paper_1304_0681_gb300.seed import _WIN_FIELDS
+    torch = _torch()
+    g = synth.genome("small", seed=19)
+    rs = synth.sample_reads(g, "T2", n_reads=200, seed=20)
+    idx = _index(g)
+    rd, ro = _reads_dev(rs)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Stream(), torch.cuda.Stream()
+    out = {n: torch.empty(4, dtype=t, device="cuda") for n, t in _WIN_FIELDS}
+    out["cand_offsets"] = torch.empty(rs.n_reads + 1, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    sw._swgb.sw_seed_windows(idx.table, idx.positions, idx.chrom_offsets, idx.n_chrom, _params(), rd, ro,
+                             rs.n_reads, out, 4, cnt, stream=a)
+    sw._swgb.sw_sync_status(stream=b)
+    with pytest.raises(sw.SwError) as e:
+        sw._swgb.sw_sync_status(stream=a)
+    assert e.value.code == -2
+    assert int(cnt.item()) > 4
+
+
+def test_stream_release_frees_and_reallocates():
+    import paper_1304_0681_gb300 as sw
+    from paper_1304_0681_gb300.seed import map_reads
+    torch = _torch()
+    g = synth.genome("small", seed=21)
+    rs = synth.sample_reads(g, "T2", n_reads=300, seed=22)
+    idx = _index(g)
+    rd, ro = _reads_dev(rs)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        a = map_reads(idx, rd, ro, rs.n_reads, SC).best_score.cpu().numpy()
+        sw._swgb.sw_stream_release(s)
+        b = map_reads(idx, rd, ro, rs.n_reads, SC).best_score.cpu().numpy()
+        sw._swgb.sw_stream_release(s)
+    np.testing.assert_array_equal(a, b)
+    assert sw._swgb.sw_last_cuda_error()[0] == 0
