@@ -271,6 +271,7 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
 def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
     """The batched uneven workload (2M pairs, reads 75-800 bp, 10% spliced),
     score + end + CIGAR in one call per step, L2 flushed between steps."""
+    import numpy as np
     import torch
 
     import paper_1304_0681_gb300 as sw
@@ -330,6 +331,28 @@ def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
     stage_e_res = {"ms": statistics.mean(e_ms), "records": int(rec_n.item()), "min_score": 100, "min_intron": 20,
                    "distinct_junctions": int(len(jn["count"])), "junction_hits": int(jn["count"].sum()),
                    "steps_counted": steps}
+    if not args.no_cpu_baseline and rank == 0:
+        # the oracle's records and junction counts over a sample of pairs,
+        # on its own alignments (computed first, untimed)
+        import oracle
+        from oracle import stage_e_oracle as seo
+        rng = np.random.default_rng(7)
+        samp = np.sort(rng.choice(wl.n_pairs, 20_000, replace=False))
+        sub = wl.pair_slice(samp)
+        res_o = oracle.align_batch(sub.reads, sub.read_offsets, sub.windows, sub.window_offsets,
+                                   scoring=oracle.Scoring(*SCORING), cigar=True, threads=os.cpu_count() or 1)
+        cig = seo.cigars_of(res_o)
+        ch = (samp // 100_000).astype(np.int32)
+        ps = wl.window_offsets[:-1][samp]
+        stn = (samp % 2).astype(np.int8)
+        t0 = time.perf_counter()
+        seo.records(res_o["score"], res_o["i_end"], res_o["j_end"], cig, ch, ps, stn, 100)
+        seo.junction_counts(sub.windows, sub.window_offsets, res_o["score"], res_o["j_end"], cig, ch, ps, 100, 20)
+        dt = time.perf_counter() - t0
+        stage_e_res["cpu_baseline"] = {"value": len(samp) / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                                       "sample": f"{len(samp)} of {wl.n_pairs} pairs (seed 7): records and junction "
+                                                 f"counts in {dt:.2f} s, on the oracle's own alignments"}
+        stage_e_res["gpu_pairs_per_s"] = wl.n_pairs / (stage_e_res["ms"] * 1e-3)
     cells = wl.cells()
     t = sum(ms) / len(ms)
     score_ms = statistics.mean(p[1] for p in phases)
@@ -462,6 +485,18 @@ def _seeding_section(args, rank, steps: int) -> dict:
                           "includes": "seed, two-strand reads, extract, SW score+end+CIGAR, best per read, "
                                       "host count read-backs and buffer allocation"}
             del mp
+        if not args.no_cpu_baseline and rank == 0 and name == "T2":
+            # the oracle as it stands: one scan of the whole reference for the
+            # sample's seeds, then every read's steps in plain Python
+            from oracle import seed_oracle as so
+            ids = np.arange(0, rs.n_reads, rs.n_reads // 2000)[:2000]
+            op = so.SeedParams(**{f: getattr(p, f) for f, _ in p._fields_})
+            t0 = time.perf_counter()
+            so.seed_windows(g.packed, g.chrom_offsets, rs.reads, rs.read_offsets, op, read_ids=ids)
+            dt = time.perf_counter() - t0
+            sec["cpu_baseline"] = {"value": len(ids) / dt, "unit": "reads/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"{len(ids)} evenly spaced reads of the 2M: seeds to windows in "
+                                             f"{dt:.1f} s (a scan of the whole reference, no index)"}
         res[name] = sec
         del rd, ro, out, w
         torch.cuda.empty_cache()
