@@ -158,6 +158,28 @@ def _cpu_baseline(wl, budget_s: float) -> dict:
                          "sample": f"the first {n1} pairs of that sample, {sub1.cells():.3e} cells in {dt1:.1f} s"}}
 
 
+def _oracle_sample(wl, frac: float = 0.01, seed: int = 3, cigar: bool = True) -> dict:
+    """The oracle on a seeded sample of a large workload's pairs, on all host
+    cores, with the time the whole workload would take at that rate."""
+    import numpy as np
+
+    import oracle
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    n = max(1, int(wl.n_pairs * frac))
+    pairs = np.sort(rng.choice(wl.n_pairs, n, replace=False))
+    sub = wl.pair_slice(pairs)
+    t = time.perf_counter()
+    oracle.align_batch(sub.reads, sub.read_offsets, sub.windows, sub.window_offsets,
+                       scoring=oracle.Scoring(*SCORING), cigar=cigar, threads=cores)
+    dt = time.perf_counter() - t
+    rate = sub.cells() / dt
+    return {"value": rate / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{n} of {wl.n_pairs} pairs drawn uniformly (seed {seed}), "
+                      f"{'score + end + CIGAR' if cigar else 'score + end'}, {sub.cells():.3e} cells in {dt:.1f} s",
+            "extrapolated_full_s": wl.cells() / rate, "extrapolated": True}
+
+
 def _traffic_record(kernel_file: str):
     """DRAM bytes per launch of the score kernel from the committed ncu
     summary, if it was captured from the current kernel source."""
@@ -254,7 +276,8 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
     e2.record(stream)
     e2.synchronize()
     recall = float(np.mean(best_filt == best_plain))
-    return {"workload": FILTER_WORKLOADS[name],
+    oracle_sw = _oracle_sample(wl, 0.01, cigar=False) if (not args.no_cpu_baseline and rank == 0) else None
+    return {"workload": FILTER_WORKLOADS[name], "cpu_baseline": oracle_sw,
             "reads": wl.n_reads, "pairs": wl.n_pairs, "cells_exhaustive": cells,
             "plain": {"ms_per_step": ms_plain, "reads_per_s": wl.n_reads / (ms_plain * 1e-3),
                       "gcups": cells / (ms_plain * 1e-3) / 1e9},
@@ -331,6 +354,7 @@ def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
     stage_e_res = {"ms": statistics.mean(e_ms), "records": int(rec_n.item()), "min_score": 100, "min_intron": 20,
                    "distinct_junctions": int(len(jn["count"])), "junction_hits": int(jn["count"].sum()),
                    "steps_counted": steps}
+    oracle_sw = _oracle_sample(wl, 0.01, cigar=True) if (not args.no_cpu_baseline and rank == 0) else None
     if not args.no_cpu_baseline and rank == 0:
         # the oracle's records and junction counts over a sample of pairs,
         # on its own alignments (computed first, untimed)
@@ -361,7 +385,7 @@ def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
             "phase_ms": {"classify": statistics.mean(p[0] for p in phases), "score": score_ms,
                          "traceback": statistics.mean(p[2] for p in phases)},
             "score_roofline_frac": cells / (score_ms * 1e-3) / 1e9 / peak_gcups,
-            "stage_e_records_junctions": stage_e_res}
+            "stage_e_records_junctions": stage_e_res, "cpu_baseline": oracle_sw}
 
 
 def _seeding_section(args, rank, steps: int) -> dict:

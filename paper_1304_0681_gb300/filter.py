@@ -56,21 +56,52 @@ class FilterModel:
         _swgb.sw_mlp_adam(self.buf, lr, self.step)
 
     def train(self, features: torch.Tensor, target: torch.Tensor, epochs: int = 4, batch: int = 8192,
-              lr: float = 2e-3, seed: int = 0) -> list:
+              lr: float = 2e-3, seed: int = 0, group=None) -> list:
         """Minibatch Adam on the mean squared error; returns the mean loss of
-        each epoch measured with the serving forward."""
+        each epoch measured with the serving forward.
+
+        With a process group, every rank holds the same training set and the
+        same seed: each takes its share of every minibatch, and the gradients
+        are combined by an all-reduce before the (identical) Adam step, so
+        all ranks keep the same parameters as one rank training alone."""
         n = features.shape[0]
         gen = torch.Generator(device=features.device)
         gen.manual_seed(seed)
+        rank, world = 0, 1
+        if group is not None:
+            import torch.distributed as dist
+            rank, world = dist.get_rank(group), dist.get_world_size(group)
         losses = []
         for _ in range(epochs):
             perm = torch.randperm(n, generator=gen, device=features.device).to(torch.int32)
             for s in range(0, n - batch + 1, batch):
-                self.grad(features, target, perm[s:s + batch])
+                if world == 1:
+                    self.grad(features, target, perm[s:s + batch])
+                else:
+                    lo, hi = minibatch_share(batch, rank, world)
+                    if hi > lo:
+                        self.grad(features, target, perm[s + lo:s + hi])
+                    else:
+                        self.gradient().zero_()
+                    allreduce_mean_gradient(self.gradient(), hi - lo, batch, group)
                 self.adam(lr)
             pred = self.forward(features)
             losses.append(float(torch.mean((pred - target) ** 2)))
         return losses
+
+
+def minibatch_share(n: int, rank: int, world: int) -> tuple:
+    """Rank's contiguous share [lo, hi) of an n-sample minibatch."""
+    return n * rank // world, n * (rank + 1) // world
+
+
+def allreduce_mean_gradient(grad: torch.Tensor, n_local: int, n_total: int, group=None) -> None:
+    """In place: a rank's mean gradient over its n_local samples becomes the
+    mean over all n_total samples of every rank (weight n_local / n_total,
+    then a sum over ranks)."""
+    import torch.distributed as dist
+    grad.mul_(n_local / n_total)
+    dist.all_reduce(grad, op=dist.ReduceOp.SUM, group=group)
 
 
 def features(batch: DeviceBatch, cand_offsets: torch.Tensor) -> torch.Tensor:

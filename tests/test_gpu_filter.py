@@ -107,6 +107,31 @@ def test_gradient_matches_oracle():
     np.testing.assert_allclose(got, ref, atol=1e-3 * scale, rtol=0)
 
 
+def test_gradient_shares_combine_to_the_full_batch():
+    """The data-parallel step: each rank's mean gradient over its share of a
+    minibatch, weighted by its share and summed (what the all-reduce does),
+    equals the gradient of the whole minibatch; three shares, one empty."""
+    import torch
+    from paper_1304_0681_gb300 import filter as flt
+    rng = np.random.default_rng(6)
+    model = flt.FilterModel(seed=7)
+    n = 257
+    x = fo.bf16_round(rng.uniform(0, 0.4, (n, 64)))
+    t = rng.uniform(0, 1, n)
+    xb = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).cuda().view(torch.int16)
+    tt = torch.from_numpy(t.astype(np.float32)).cuda()
+    idx = torch.from_numpy(rng.permutation(n).astype(np.int32)).cuda()
+    model.grad(xb, tt, idx)
+    full = model.gradient().clone()
+    acc = torch.zeros_like(full)
+    for lo, hi in ((0, 100), (100, 100), (100, n)):
+        if hi > lo:
+            model.grad(xb, tt, idx[lo:hi])
+            acc += model.gradient() * ((hi - lo) / n)
+    scale = float(full.abs().max())
+    np.testing.assert_allclose(acc.cpu().numpy(), full.cpu().numpy(), atol=1e-5 * scale, rtol=0)
+
+
 def test_adam_matches_oracle():
     import torch
     from paper_1304_0681_gb300 import filter as flt

@@ -105,3 +105,46 @@ def test_two_rank_shards_match_unsharded(tmp_path):
     assert cig == ref
     assert out["units"] == wl.cells()
     assert out["secs"] == 1.5
+
+
+def _grad_worker(rank, world, port, out_dir):
+    """Each rank takes its share of one minibatch, computes the mean
+    gradient of its share (the fp64 oracle stands in for the GPU kernel on
+    this CPU test) and combines it with the filter's all-reduce."""
+    import torch
+    import torch.distributed as dist
+
+    from oracle import filter_oracle as fo
+    from paper_1304_0681_gb300.filter import allreduce_mean_gradient, minibatch_share
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rng = np.random.default_rng(5)
+        X = rng.random((37, fo.N_FEAT))
+        t = rng.random(37)
+        P = fo.Params.init(3)
+        lo, hi = minibatch_share(len(t), rank, world)
+        g = torch.from_numpy(fo.backward(P, X[lo:hi], t[lo:hi]) if hi > lo else np.zeros(fo.N_PARAMS))
+        allreduce_mean_gradient(g, hi - lo, len(t))
+        if rank == 0:
+            np.save(os.path.join(out_dir, "grad.npy"), g.numpy())
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_filter_gradient_allreduce_equals_one_rank(tmp_path, world):
+    import torch.multiprocessing as mp
+
+    from oracle import filter_oracle as fo
+    from paper_1304_0681_gb300.filter import minibatch_share
+    mp.spawn(_grad_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    rng = np.random.default_rng(5)
+    X = rng.random((37, fo.N_FEAT))
+    t = rng.random(37)
+    want = fo.backward(fo.Params.init(3), X, t)
+    np.testing.assert_allclose(np.load(tmp_path / "grad.npy"), want, rtol=1e-12, atol=1e-14)
+    shares = [minibatch_share(37, r, world) for r in range(world)]
+    assert shares[0][0] == 0 and shares[-1][1] == 37
+    assert all(a[1] == b[0] for a, b in zip(shares, shares[1:]))
