@@ -599,15 +599,17 @@ __global__ void k_seed_place(const SeedScratch S, const int64_t *__restrict__ wo
 // ---- copies of base ranges ----------------------------------------------
 
 // Bases [s0, s0 + L) of src to bases [d0, d0 + L) of dst, reverse
-// complemented when rev; one warp, a destination word per lane.  Words the
-// range shares with a neighbour are merged with atomicOr into a zeroed
-// destination.
+// complemented when rev; a group of kCopyLanes lanes, a destination word per
+// lane and step.  Words the range shares with a neighbour are merged with
+// atomicOr into a zeroed destination.
+constexpr int kCopyLanes = 8;  // a 100-base read spans 7 words
+
 __device__ void copy_range(const uint32_t *__restrict__ src, int64_t s0, int64_t L, uint32_t *dst, int64_t d0,
-                           bool rev, int lane)
+                           bool rev, int gl)
 {
     if (L <= 0) return;
     const int64_t w0 = d0 >> 4, w1 = (d0 + L - 1) >> 4;
-    for (int64_t w = w0 + lane; w <= w1; w += 32) {
+    for (int64_t w = w0 + gl; w <= w1; w += kCopyLanes) {
         const int64_t b0 = w << 4 > d0 ? w << 4 : d0;                       // first base of the range in w
         const int64_t b1 = (w << 4) + 16 < d0 + L ? (w << 4) + 16 : d0 + L;  // one past the last
         const int cnt = (int)(b1 - b0);
@@ -639,43 +641,43 @@ __global__ void k_extract(const uint32_t *__restrict__ g, int64_t n_bases, const
                           const int32_t *__restrict__ len, const int64_t *__restrict__ woff, int64_t n,
                           uint32_t *dst, int64_t cap_bases, int32_t *status)
 {
-    const int lane = threadIdx.x & 31;
-    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < n;
-         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int gl = threadIdx.x % kCopyLanes;
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kCopyLanes; w < n;
+         w += ((int64_t)gridDim.x * blockDim.x) / kCopyLanes) {
         const int64_t d0 = woff[w], L = len[w], s0 = start[w];
         if (L < 0 || s0 < 0 || s0 + L > n_bases) {
-            if (lane == 0) atomicOr(status, ST_BAD_INPUT);
+            if (gl == 0) atomicOr(status, ST_BAD_INPUT);
             continue;
         }
         if (d0 + L > cap_bases) {
-            if (lane == 0) atomicOr(status, ST_CAPACITY);
+            if (gl == 0) atomicOr(status, ST_CAPACITY);
             continue;
         }
-        copy_range(g, s0, L, dst, d0, false, lane);
+        copy_range(g, s0, L, dst, d0, false, gl);
     }
 }
 
 __global__ void k_two_strands(const uint32_t *__restrict__ reads, const int64_t *__restrict__ roff, int64_t n,
                               uint32_t *dst, int64_t cap_bases, int64_t *__restrict__ doff, int32_t *status)
 {
-    const int lane = threadIdx.x & 31;
+    const int gl = threadIdx.x % kCopyLanes;
     if (*(volatile const int32_t *)status & ST_BAD_INPUT) return;
     const int64_t total = roff[n];
     if (2 * total > cap_bases) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_CAPACITY);
         return;
     }
-    for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; it < 2 * n;
-         it += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kCopyLanes; it < 2 * n;
+         it += ((int64_t)gridDim.x * blockDim.x) / kCopyLanes) {
         const int64_t r = it < n ? it : it - n;
         const bool rev = it >= n;
         const int64_t s0 = roff[r], L = roff[r + 1] - s0;
         const int64_t d0 = rev ? total + s0 : s0;
-        if (lane == 0) {
+        if (gl == 0) {
             doff[it] = d0;
             if (it == 2 * n - 1) doff[2 * n] = 2 * total;
         }
-        copy_range(reads, s0, L, dst, d0, rev, lane);
+        copy_range(reads, s0, L, dst, d0, rev, gl);
     }
 }
 
@@ -784,7 +786,7 @@ int launch_extract_windows(const uint32_t *genome, int64_t n_bases, const int64_
     if (rc) return rc;
     const int64_t cap_words = (cap_bases + 15) / 16;
     k_zero_words<<<grid_for(cap_words, 256, sm_count, 8), 256, 0, st>>>(dst, woff + n, 1, cap_words);
-    k_extract<<<grid_for(n * 32, 256, sm_count, 8), 256, 0, st>>>(genome, n_bases, start, len, woff, n, dst,
+    k_extract<<<grid_for(n * kCopyLanes, 256, sm_count, 8), 256, 0, st>>>(genome, n_bases, start, len, woff, n, dst,
                                                                   cap_bases, status);
     count_launch(2);
     return launch_status();
@@ -796,7 +798,7 @@ int launch_two_strands(const uint32_t *reads, const int64_t *roff, int64_t n, ui
     const int64_t cap_words = (cap_bases + 15) / 16;
     k_check_offsets<<<grid_for(n, 256, sm_count, 4), 256, 0, st>>>(roff, n, 0, -1, status);
     k_zero_words<<<grid_for(cap_words, 256, sm_count, 8), 256, 0, st>>>(dst, roff + n, 2, cap_words);
-    k_two_strands<<<grid_for(2 * n * 32, 256, sm_count, 8), 256, 0, st>>>(reads, roff, n, dst, cap_bases, doff,
+    k_two_strands<<<grid_for(2 * n * kCopyLanes, 256, sm_count, 8), 256, 0, st>>>(reads, roff, n, dst, cap_bases, doff,
                                                                           status);
     count_launch(3);
     return launch_status();
