@@ -503,6 +503,38 @@ def _seeding_section(args, rank, steps: int) -> dict:
             pipe["includes"] = ("pinned host reads in, best hit per read out; each worker thread drives its own "
                                 "stream through seed, extract, SW + CIGAR, best")
             sec["map_pipelined_from_host"] = pipe
+            # the same map with Stage E task iv: records (score >= 200) and
+            # splice junctions (deletion runs >= 20 with intron marks)
+            from paper_1304_0681_gb300 import stage_e
+            tab = stage_e.JunctionTable(1 << 22)
+            sd.map_reads(idx, rd, ro, rs.n_reads, SCORING, min_score=200, junctions=tab)
+            jw = []
+            for _ in range(steps):
+                tab.clear()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                mpj = sd.map_reads(idx, rd, ro, rs.n_reads, SCORING, min_score=200, junctions=tab)
+                torch.cuda.synchronize()
+                jw.append(time.perf_counter() - t0)
+            jn = tab.export()
+            found = {(int(c_), int(a_), int(b_), int(t_)) for c_, a_, b_, t_ in
+                     zip(jn["chrom"], jn["start"], jn["end"], jn["strand"])}
+            planted = {(int(ch), int(st - g.chrom_offsets[ch]), int(st - g.chrom_offsets[ch] + L - 1), int(t_))
+                       for ch, st, L, t_ in g.introns}
+            spanned = {tuple(planted_row) for planted_row in
+                       [(int(g.introns[i][0]), int(g.introns[i][1] - g.chrom_offsets[g.introns[i][0]]),
+                         int(g.introns[i][1] - g.chrom_offsets[g.introns[i][0]] + g.introns[i][2] - 1),
+                         int(g.introns[i][3])) for i in np.unique(rs.intron[rs.intron >= 0])]}
+            short = {x for x in spanned if x[2] - x[1] + 1 <= 150}
+            sec["map_with_records_junctions"] = {
+                "ms_per_step": statistics.mean(jw) * 1e3, "records": int(mpj.n_records),
+                "junctions_found": len(found), "found_that_are_planted": len(found & planted) / max(len(found), 1),
+                "planted_introns_spanned_by_reads": len(spanned),
+                "spanned_found": len(found & spanned) / max(len(spanned), 1),
+                "spanned_of_at_most_150_bp_found": len(found & short) / max(len(short), 1),
+                "note": "a linear gap costs 10 + (L - 1): SW bridges an intron of L bases only when the shorter "
+                        "exon part scores more than that, so long introns stay unbridged"}
+            del mpj
             sec["map"] = {"ms_per_step": wt * 1e3, "reads_per_s": rs.n_reads / wt, "pairs": n, "cells": cells,
                           "gcups_incl_seeding": cells / wt / 1e9, "mapped_share": float(ok.mean()),
                           "best_window_holds_origin": float(hit.mean()),

@@ -121,6 +121,8 @@ def extract_windows(index: KmerIndex, start, length, n_windows: int, stream=None
 @dataclass
 class Mapped:
     windows: dict          # seed_windows() output
+    records_dev: torch.Tensor | None   # sw_record_t rows on the device (min_score given)
+    n_records: int
     reads2: torch.Tensor   # both strands of the reads
     reads2_offsets: torch.Tensor
     win_bases: torch.Tensor
@@ -134,11 +136,27 @@ class Mapped:
     def cigar_tuple(self):
         return self.cigar
 
+    @property
+    def records(self) -> dict | None:
+        """The records as numpy fields (stage_e.records() layout), copied to
+        the host on first use."""
+        if self.records_dev is None:
+            return None
+        if not hasattr(self, "_records"):
+            from .stage_e import _decode_records
+            self._records = _decode_records(self.records_dev, self.n_records)
+        return self._records
+
 
 def map_reads(index: KmerIndex, reads, read_offsets, n_reads: int, scoring, params: SeedParams | None = None,
-              cigar: bool = True, stream=None) -> Mapped:
+              cigar: bool = True, stream=None, min_score: int | None = None, junctions=None,
+              min_intron: int = 20) -> Mapped:
     """Seed, extract, align every (read strand, window) pair, and pick each
-    read's best window (first on ties)."""
+    read's best window (first on ties).  With min_score (and a CIGAR), the
+    alignments scoring at least min_score also become records in reference
+    coordinates, and, given a stage_e.JunctionTable, their deletion runs of
+    at least min_intron bases with intron marks are counted in it
+    (Stage E, task iv)."""
     win = seed_windows(index, reads, read_offsets, n_reads, params, stream=stream)
     n = win["count"]
     # each call clears the status word the next one reuses: check in between
@@ -161,12 +179,24 @@ def map_reads(index: KmerIndex, reads, read_offsets, n_reads: int, scoring, para
         _swgb.sw_batch_align_indexed(reads2, roff2, 2 * n_reads, wb, woff, win["pair_read"], n, scoring, score, end,
                                      cg, stream)
         _swgb.sw_sync_status(stream)
+    rec_out, n_rec = None, 0
+    if min_score is not None and cg is not None and n:
+        rec_out = torch.empty((n, 6), dtype=torch.int64, device=dev)
+        rec_n = torch.zeros(1, dtype=torch.int64, device=dev)
+        _swgb.sw_records(score, end, cg, n, win["chrom"], win["pos"], win["strand"], min_score, rec_out, rec_n, stream)
+        _swgb.sw_sync_status(stream)
+        n_rec = int(rec_n.item())
+        if junctions is not None:
+            _swgb.sw_junctions_detect(wb, woff, score, end, cg, n, win["chrom"], win["pos"], min_score, min_intron,
+                                      junctions.table, junctions.capacity, stream)
+            _swgb.sw_sync_status(stream)
     best = torch.empty(max(n_reads, 1), dtype=torch.int32, device=dev)
     bcand = torch.empty(max(n_reads, 1), dtype=torch.int32, device=dev)
     if n_reads:
         _swgb.sw_best_per_read(score, win["cand_offsets"], n_reads, None, best, bcand, stream)
     _swgb.sw_sync_status(stream)
-    return Mapped(win, reads2, roff2, wb, woff, score[:n], end[:2 * n], cg, best[:n_reads], bcand[:n_reads])
+    return Mapped(win, rec_out, n_rec, reads2, roff2, wb, woff, score[:n], end[:2 * n], cg, best[:n_reads],
+                  bcand[:n_reads])
 
 
 @dataclass

@@ -25,7 +25,11 @@ def records(batch: DeviceBatch, window_chrom, window_pos, window_strand, min_sco
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
     _swgb.sw_records(batch.score, batch.end, batch.cigar_tuple(), n, window_chrom, window_pos, window_strand,
                      min_score, out, cnt, stream)
-    k = int(cnt.item())
+    return _decode_records(out, int(cnt.item()))
+
+
+def _decode_records(out: torch.Tensor, k: int) -> dict:
+    """numpy fields of the first k sw_record_t rows of a device buffer."""
     a = out[:k].cpu().numpy()
     i32 = a.view(np.int32).reshape(k, 12)
     return {"pair": a[:, 0], "ref_start": a[:, 1], "ref_end": a[:, 2], "chrom": i32[:, 6], "score": i32[:, 7],

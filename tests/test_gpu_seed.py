@@ -335,3 +335,45 @@ def test_stream_release_frees_and_reallocates():
         sw._swgb.sw_stream_release(s)
     np.testing.assert_array_equal(a, b)
     assert sw._swgb.sw_last_cuda_error()[0] == 0
+
+
+def test_map_records_and_junctions_match_the_oracle_pipeline():
+    """Seeded windows carry reference coordinates: the records and splice
+    junctions of the whole GPU map equal the oracle pipeline's (seeding
+    oracle -> SW oracle -> Stage E oracle), and the junctions are the planted
+    introns the spliced reads span."""
+    from oracle import stage_e_oracle as se
+    from paper_1304_0681_gb300 import stage_e
+    from paper_1304_0681_gb300.seed import map_reads
+    g = synth.genome("small", seed=23, n_introns=300, intron=(50, 150))
+    rs = synth.sample_reads(g, "T1", n_reads=1200, seed=24, splice=0.5, min_exon=35)
+    idx = _index(g)
+    rd, ro = _reads_dev(rs)
+    tab = stage_e.JunctionTable(1 << 14)
+    mp = map_reads(idx, rd, ro, rs.n_reads, SC, min_score=200, junctions=tab, min_intron=20)
+    jn = tab.export()
+    got_j = {(int(c), int(a), int(b), int(t)): int(k)
+             for c, a, b, t, k in zip(jn["chrom"], jn["start"], jn["end"], jn["strand"], jn["count"])}
+    ref = so.seed_windows(g.packed, g.chrom_offsets, rs.reads, rs.read_offsets, _oparams(_params()))
+    c = g.codes()
+    scores, ie, je, cig, wins = [], [], [], [], []
+    for i in range(len(ref["start"])):
+        r = int(ref["read"][i])
+        seq = rs.read(r) if ref["strand"][i] == 0 else so.revcomp(rs.read(r))
+        w = c[ref["start"][i]:ref["end"][i] + 1]
+        s, a, b, ops = oracle.align(seq, w, oracle.Scoring(*SC))
+        scores.append(s); ie.append(a); je.append(b); cig.append(ops); wins.append(w)
+    woff = np.zeros(len(wins) + 1, np.int64)
+    np.cumsum([len(w) for w in wins], out=woff[1:])
+    recs = np.array(se.records(scores, ie, je, cig, ref["chrom"], ref["pos"], ref["strand"], 200),
+                    np.int64).reshape(-1, 8)
+    got = mp.records
+    for k, col in (("pair", 0), ("score", 1), ("chrom", 2), ("ref_start", 3), ("ref_end", 4), ("read_start", 5),
+                   ("read_end", 6), ("strand", 7)):
+        np.testing.assert_array_equal(got[k], recs[:, col], err_msg=k)
+    want_j = se.junction_counts(np.concatenate(wins), woff, scores, je, cig, ref["chrom"], ref["pos"], 200, 20)
+    assert got_j == want_j
+    # the junctions are planted introns: (chrom, local start, local end, strand)
+    planted = {(int(ch), int(st - g.chrom_offsets[ch]), int(st - g.chrom_offsets[ch] + L - 1), int(t))
+               for ch, st, L, t in g.introns}
+    assert len(got_j) > 50 and set(got_j) <= planted
