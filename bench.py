@@ -446,9 +446,18 @@ def _seeding_section(args, rank, steps: int) -> dict:
         sw.sw_sync_status()
         n_win = int(cnt.item())
         t = statistics.mean(ms)
+        lookups, hits_kept, sectors = sw._swgb.sw_seed_stats()
+        if "gather_probe_loads_per_s" not in res:
+            res["gather_probe_loads_per_s"] = sw._swgb.sw_gather_probe(32, 64)
         sec = {"reads": rs.n_reads, "read_len": int(rs.read_offsets[1]), "eps": synth.READ_SETS[name]["eps"],
                "spliced_share": 0.10, "windows": n_win, "windows_per_read": n_win / rs.n_reads,
-               "seed_ms": t, "seed_reads_per_s": rs.n_reads / (t * 1e-3), "steps": steps}
+               "seed_ms": t, "seed_reads_per_s": rs.n_reads / (t * 1e-3), "steps": steps,
+               "lookups": lookups, "hits_kept": hits_kept, "sectors": sectors,
+               "roofline": {"bound": "scattered 32-byte sectors", "kernel": "k_seed (+ k_seed_large, place)",
+                            "achieved": sectors / (t * 1e-3), "peak": res["gather_probe_loads_per_s"],
+                            "unit": "sectors/s", "frac": sectors / (t * 1e-3) / res["gather_probe_loads_per_s"],
+                            "peak_basis": "measured random 4-byte loads/s over a 16 GiB buffer (sw_gather_probe)",
+                            "per_unit": "table sectors of each seed lookup + sectors of its kept bucket"}}
         if name == "T2":
             sd.map_reads(idx, rd, ro, rs.n_reads, SCORING)  # warm
             torch.cuda.synchronize()

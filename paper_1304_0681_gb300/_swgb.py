@@ -31,7 +31,7 @@ EXPORTS = ("sw_cigar_capacity", "sw_packed_bytes", "sw_batch_align", "sw_stream_
            "sw_mlp_forward", "sw_set_mlp_kernel", "sw_mlp_grad", "sw_mlp_adam", "sw_filter_select", "sw_best_per_read",
            # include/swgb_seed.h
            "sw_index_table_words", "sw_index_build", "sw_seed_windows", "sw_reads_two_strands",
-           "sw_extract_windows")
+           "sw_extract_windows", "sw_seed_stats", "sw_gather_probe")
 
 
 class SwError(RuntimeError):
@@ -114,6 +114,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_stream_release.restype = ctypes.c_int
     lib.sw_last_cuda_error.argtypes = [ctypes.POINTER(ctypes.c_char_p)]
     lib.sw_last_cuda_error.restype = ctypes.c_int
+    lib.sw_seed_stats.argtypes = [p, p]
+    lib.sw_seed_stats.restype = ctypes.c_int
+    lib.sw_gather_probe.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_double), p]
+    lib.sw_gather_probe.restype = ctypes.c_int
     lib.sw_index_table_words.argtypes = [i32]
     lib.sw_index_table_words.restype = i64
     lib.sw_index_build.argtypes = [p, i64, p, i32, i32, p, p, p, p]
@@ -474,3 +478,18 @@ def sw_last_cuda_error() -> tuple:
     name = ctypes.c_char_p()
     code = _lib.sw_last_cuda_error(ctypes.byref(name))
     return code, (name.value.decode() if name.value else "")
+
+
+def sw_seed_stats(stream=None) -> tuple:
+    """(seed lookups, hits kept, 32-byte sectors read) of the stream's last
+    sw_seed_windows call."""
+    buf = (ctypes.c_int64 * 3)()
+    _check(_lib.sw_seed_stats(_stream(stream), ctypes.cast(buf, ctypes.c_void_p)), "sw_seed_stats")
+    return int(buf[0]), int(buf[1]), int(buf[2])
+
+
+def sw_gather_probe(log2_words: int = 32, rounds: int = 64, stream=None) -> float:
+    """Random 4-byte loads per second (one 32-byte sector each)."""
+    out = ctypes.c_double(0.0)
+    _check(_lib.sw_gather_probe(int(log2_words), int(rounds), ctypes.byref(out), _stream(stream)), "sw_gather_probe")
+    return out.value

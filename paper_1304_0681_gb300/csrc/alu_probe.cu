@@ -40,6 +40,37 @@ __global__ void __launch_bounds__(256) k_alu_probe(int64_t iters, uint32_t seed,
     out[tid] = x;
 }
 
+// Random 4-byte loads over a buffer much larger than L2: each thread keeps 8
+// independent loads in flight, at addresses from a 64-bit LCG, and folds the
+// values so that no load is dead.  The rate, in loads per second, is the
+// ceiling for kernels whose traffic is scattered 32-byte sectors.
+__global__ void __launch_bounds__(256) k_gather_probe(const uint32_t *__restrict__ buf, uint64_t mask,
+                                                     int64_t rounds, uint32_t *out)
+{
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    uint64_t x = tid * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    uint32_t acc = 0;
+    for (int64_t i = 0; i < rounds; ++i) {
+        uint32_t v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            x = x * 6364136223846793005ull + 1442695040888963407ull;
+            v[q] = __ldg(buf + ((x >> 17) & mask));
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc ^= v[q];
+    }
+    out[tid] = acc;
+}
+
+int launch_gather_probe(const uint32_t *buf, uint64_t mask, int64_t rounds, int blocks, int threads, uint32_t *out,
+                        cudaStream_t st)
+{
+    k_gather_probe<<<blocks, threads, 0, st>>>(buf, mask, rounds, out);
+    count_launch();
+    return launch_status();
+}
+
 int launch_alu_probe(int kind, int64_t iters, int blocks, int threads, uint32_t *out, cudaStream_t st)
 {
     const uint32_t seed = 12345u;

@@ -178,6 +178,7 @@ __global__ void k_tab_write(uint4 *tab, const uint32_t *__restrict__ blk)
 // ---- seeding -------------------------------------------------------------
 
 struct SeedScratch {
+    unsigned long long *stats;   // table lookups, hits kept, 32-byte sectors the lookups touch
     uint32_t *wstart, *wend;     // windows in reservation order (capacity entries)
     int64_t capacity;
     unsigned long long *n_win;   // windows reserved so far
@@ -215,6 +216,29 @@ __device__ __forceinline__ uint32_t seed_code(const uint32_t *reads, int64_t r0,
     return revcomp_bits(load_bases(reads, r0 + m - s - c.p.k, c.p.k) & c.mask, c.p.k);
 }
 
+// 32-byte sectors a lookup of code x reads: table[x - 1 .. x], and the kept
+// bucket positions[lo .. lo + cnt).
+__device__ __forceinline__ uint32_t lookup_sectors(uint32_t x, uint32_t lo, uint32_t cnt)
+{
+    uint32_t n = x ? ((x >> 3) - ((x - 1) >> 3) + 1) : 1u;
+    if (cnt) n += ((lo + cnt - 1) >> 3) - (lo >> 3) + 1;
+    return n;
+}
+
+__device__ __forceinline__ void add_stats(unsigned long long *stats, uint64_t a, uint64_t b, uint64_t c)
+{
+    for (int d = 16; d > 0; d >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, d);
+        b += __shfl_xor_sync(0xffffffffu, b, d);
+        c += __shfl_xor_sync(0xffffffffu, c, d);
+    }
+    if ((threadIdx.x & 31) == 0 && (a | b | c)) {
+        atomicAdd(stats, (unsigned long long)a);
+        atomicAdd(stats + 1, (unsigned long long)b);
+        atomicAdd(stats + 2, (unsigned long long)c);
+    }
+}
+
 // Bucket of a code: [lo, hi) in positions.
 __device__ __forceinline__ void bucket(const uint32_t *__restrict__ table, uint32_t code, uint32_t &lo, uint32_t &hi)
 {
@@ -226,13 +250,18 @@ __device__ __forceinline__ void bucket(const uint32_t *__restrict__ table, uint3
 // from *fill (a shared-memory counter).
 __device__ void seed_gather(const uint32_t *reads, int64_t r0, int m, int strand, const uint32_t *table,
                             const uint32_t *__restrict__ positions, const SeedCfg &c, uint32_t *list,
-                            int *fill, int tid, int nthreads)
+                            int *fill, int tid, int nthreads, uint64_t *st)
 {
     const int ns0 = n_phase(m, 0, c.p), ns = ns0 + n_phase(m, c.p.phase, c.p);
     for (int t = tid; t < ns; t += nthreads) {
         uint32_t lo, hi;
-        bucket(table, seed_code(reads, r0, m, seed_start(t, ns0, c.p), strand, c), lo, hi);
-        if (hi - lo > (uint32_t)c.p.max_hits || hi == lo) continue;
+        const uint32_t x = seed_code(reads, r0, m, seed_start(t, ns0, c.p), strand, c);
+        bucket(table, x, lo, hi);
+        const uint32_t cnt = hi - lo <= (uint32_t)c.p.max_hits ? hi - lo : 0u;
+        st[0] += 1;
+        st[1] += cnt;
+        st[2] += lookup_sectors(x, lo, cnt);
+        if (cnt == 0) continue;
         const int at = atomicAdd(fill, (int)(hi - lo));
         for (uint32_t j = lo; j < hi; ++j) list[at + (j - lo)] = __ldg(positions + j);
     }
@@ -446,6 +475,7 @@ k_seed(const uint32_t *__restrict__ reads, const int64_t *__restrict__ roff, int
     if (*(volatile const int32_t *)S.status & ST_BAD_INPUT) return;
     uint32_t *list = lists[wib];
     const int64_t n_rs = 2 * n_reads;
+    uint64_t st[3] = {0, 0, 0};  // this lane's lookups, hits kept, sectors read
     for (int64_t rs = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; rs < n_rs;
          rs += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int64_t r = rs >> 1;
@@ -469,10 +499,13 @@ k_seed(const uint32_t *__restrict__ reads, const int64_t *__restrict__ roff, int
         int64_t H = 0;
         for (int t = lane; t < ns; t += 32) {
             uint32_t lo, hi;
-            bucket(table, seed_code(reads, r0, m, seed_start(t, ns0, c.p), strand, c), lo, hi);
+            const uint32_t x = seed_code(reads, r0, m, seed_start(t, ns0, c.p), strand, c);
+            bucket(table, x, lo, hi);
             const uint32_t cnt = hi - lo <= (uint32_t)c.p.max_hits ? hi - lo : 0u;
             if (t < 32) { lo0 = lo; n0 = cnt; } else if (t < 64) { lo1 = lo; n1 = cnt; }
             H += cnt;
+            st[0] += 1;
+            st[2] += lookup_sectors(x, lo, 0);
         }
         for (int d = 16; d > 0; d >>= 1) H += __shfl_xor_sync(0xffffffffu, H, d);
         if (H == 0) {
@@ -486,6 +519,8 @@ k_seed(const uint32_t *__restrict__ reads, const int64_t *__restrict__ roff, int
             if (lane == 0) S.ovf[atomicAdd(S.n_ovf, 1u)] = (int32_t)rs;
             continue;
         }
+        st[1] += n0 + n1;
+        st[2] += (n0 ? ((lo0 + n0 - 1) >> 3) - (lo0 >> 3) + 1 : 0) + (n1 ? ((lo1 + n1 - 1) >> 3) - (lo1 >> 3) + 1 : 0);
         uint32_t own = n0 + n1, at = own;
         for (int d = 1; d < 32; d <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, at, d);
@@ -499,8 +534,15 @@ k_seed(const uint32_t *__restrict__ reads, const int64_t *__restrict__ roff, int
             __syncwarp();
             for (int t = 64 + lane; t < ns; t += 32) {
                 uint32_t lo, hi;
-                bucket(table, seed_code(reads, r0, m, seed_start(t, ns0, c.p), strand, c), lo, hi);
-                if (hi - lo > (uint32_t)c.p.max_hits || hi == lo) continue;
+                const uint32_t x = seed_code(reads, r0, m, seed_start(t, ns0, c.p), strand, c);
+                bucket(table, x, lo, hi);
+                st[0] += 1;
+                if (hi - lo > (uint32_t)c.p.max_hits || hi == lo) {
+                    st[2] += lookup_sectors(x, lo, 0);
+                    continue;
+                }
+                st[1] += hi - lo;
+                st[2] += lookup_sectors(x, lo, hi - lo);
                 const int a = atomicAdd(&fills[wib], (int)(hi - lo));
                 for (uint32_t j = lo; j < hi; ++j) list[a + (j - lo)] = __ldg(positions + j);
             }
@@ -519,6 +561,7 @@ k_seed(const uint32_t *__restrict__ reads, const int64_t *__restrict__ roff, int
         finish_read_strand(list, (int)H, rs, off, n_chrom, c, S, lane);
         __syncwarp();
     }
+    add_stats(S.stats, st[0], st[1], st[2]);
 }
 
 // Large cases: one block per read-strand with a list of c.block_hits
@@ -532,6 +575,7 @@ k_seed_large(const uint32_t *__restrict__ reads, const int64_t *__restrict__ rof
     extern __shared__ uint32_t big[];
     __shared__ int fill;
     if (*(volatile const int32_t *)S.status & ST_BAD_INPUT) return;
+    uint64_t st[3] = {0, 0, 0};
     const unsigned n_items = *(volatile unsigned *)S.n_ovf;
     for (unsigned it = blockIdx.x; it < n_items; it += gridDim.x) {
         const int64_t rs = S.ovf[it];
@@ -541,7 +585,7 @@ k_seed_large(const uint32_t *__restrict__ reads, const int64_t *__restrict__ rof
         const int m = (int)(roff[r + 1] - r0);
         if (threadIdx.x == 0) fill = 0;
         __syncthreads();
-        seed_gather(reads, r0, m, strand, table, positions, c, big, &fill, threadIdx.x, blockDim.x);
+        seed_gather(reads, r0, m, strand, table, positions, c, big, &fill, threadIdx.x, blockDim.x, st);
         __syncthreads();
         const int H = fill;
         const int n = pow2_at_least(H);
@@ -560,6 +604,7 @@ k_seed_large(const uint32_t *__restrict__ reads, const int64_t *__restrict__ rof
         if (threadIdx.x < 32) finish_read_strand(big, H, rs, off, n_chrom, c, S, threadIdx.x);
         __syncthreads();
     }
+    add_stats(S.stats, st[0], st[1], st[2]);
 }
 
 // Windows from reservation order into (read, strand, reference) order, with
@@ -732,14 +777,14 @@ size_t seed_scratch_bytes(int64_t n_reads, int64_t capacity)
 {
     const int64_t n_rs = 2 * n_reads;
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-    return up(16) + up(4 * (size_t)n_rs) + up(8 * (size_t)n_rs) + up(4 * (size_t)n_rs) + up(8 * (size_t)(n_rs + 1)) +
+    return up(64) + up(4 * (size_t)n_rs) + up(8 * (size_t)n_rs) + up(4 * (size_t)n_rs) + up(8 * (size_t)(n_rs + 1)) +
            up(8 * (size_t)((n_rs + 255) / 256 + 1)) + 2 * up(4 * (size_t)std::max<int64_t>(capacity, 1));
 }
 
 int launch_seed_windows(const uint32_t *reads, const int64_t *roff, int64_t n_reads, const uint32_t *table,
                         const uint32_t *positions, const int64_t *chrom_off, int n_chrom, const SeedKParams &p,
                         int max_read, int block_hits, SeedOutPtrs out, int64_t capacity, uint8_t *scratch,
-                        int sm_count, int32_t *status, cudaStream_t st)
+                        int64_t *stats_host, int sm_count, int32_t *status, cudaStream_t st)
 {
     const int64_t n_rs = 2 * n_reads;
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
@@ -747,7 +792,8 @@ int launch_seed_windows(const uint32_t *reads, const int64_t *roff, int64_t n_re
     SeedScratch S;
     S.n_win = (unsigned long long *)q;
     S.n_ovf = (unsigned int *)(q + 8);
-    q += up(16);
+    S.stats = (unsigned long long *)(q + 16);
+    q += up(64);
     S.wcount = (int32_t *)q; q += up(4 * (size_t)n_rs);
     S.wbase = (int64_t *)q; q += up(8 * (size_t)n_rs);
     S.ovf = (int32_t *)q; q += up(4 * (size_t)n_rs);
@@ -762,7 +808,7 @@ int launch_seed_windows(const uint32_t *reads, const int64_t *roff, int64_t n_re
     c.mask = p.k >= 16 ? 0xFFFFFFFFu : ((1u << (2 * p.k)) - 1u);
     c.max_read = max_read;
     c.block_hits = block_hits;
-    if (cuda_failed(cudaMemsetAsync(scratch, 0, 16, st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(scratch, 0, 64, st))) return SW_ERR_CUDA;
     if (cuda_failed(cudaFuncSetAttribute(k_seed_large, cudaFuncAttributeMaxDynamicSharedMemorySize, block_hits * 4)))
         return SW_ERR_CUDA;
     k_check_offsets<<<grid_for(n_reads, 256, sm_count, 4), 256, 0, st>>>(roff, n_reads, -1, -1, status);
@@ -775,7 +821,11 @@ int launch_seed_windows(const uint32_t *reads, const int64_t *roff, int64_t n_re
     if (rc) return rc;
     k_seed_place<<<grid_for(n_rs + 1, 256, sm_count, 8), 256, 0, st>>>(S, woff, n_reads, chrom_off, n_chrom, out);
     count_launch();
-    return launch_status();
+    if ((rc = launch_status())) return rc;
+    // the counters, into a pinned slot that later calls on the stream leave alone
+    return cuda_failed(cudaMemcpyAsync(stats_host, S.stats, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st))
+               ? SW_ERR_CUDA
+               : SW_OK;
 }
 
 int launch_extract_windows(const uint32_t *genome, int64_t n_bases, const int64_t *start, const int32_t *len,

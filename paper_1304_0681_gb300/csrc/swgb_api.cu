@@ -76,6 +76,7 @@ struct DeviceState {
     int64_t tb_split[2] = {0, 0};    // pairs per traceback kernel (16-bit, 32-bit) of the last call
     size_t tile16_budget = 0;        // 16-bit traceback tile budget (set at the first traceback)
     Buffer misc;                     // Stage E task iv: status word and record scan scratch
+    int64_t *seed_stats_host = nullptr;  // pinned: counters of the stream's last sw_seed_windows
     cudaEvent_t phase[4] = {nullptr, nullptr, nullptr, nullptr};
     // independent launches (length classes, traceback parts) fork onto these
     // streams and join back, so one launch's tail overlaps the next
@@ -188,6 +189,7 @@ void free_state(DeviceState *s)
             b->bytes = 0;
         }
     if (s->info_host) cudaFreeHost(s->info_host);
+    if (s->seed_stats_host) cudaFreeHost(s->seed_stats_host);
     if (s->tbinfo_host) cudaFreeHost(s->tbinfo_host);
     if (s->last_done) cudaEventDestroy(s->last_done);
     for (cudaEvent_t e : s->phase)
@@ -1499,11 +1501,13 @@ int sw_seed_windows(const uint32_t *table, const uint32_t *positions, const int6
     int32_t *status = nullptr;
     uint8_t *scratch = nullptr;
     if ((rc = stage_e_status(ds, seed_scratch_bytes(n_reads, capacity), st, &status, &scratch))) return rc;
+    if (!ds->seed_stats_host && cuda_failed(cudaMallocHost(&ds->seed_stats_host, 4 * sizeof(int64_t))))
+        return SW_ERR_CUDA;
     SeedOutPtrs o{out->start, out->length, out->chrom, out->pos, out->strand, out->pair_read, out->cand_offsets,
                   out_count};
     return launch_seed_windows((const uint32_t *)reads, read_offsets, n_reads, table, positions, chrom_offsets,
-                               n_chrom, kp, SW_SEED_MAX_READ_LEN, block_hits, o, capacity, scratch, ds->sm_count,
-                               status, st);
+                               n_chrom, kp, SW_SEED_MAX_READ_LEN, block_hits, o, capacity, scratch,
+                               ds->seed_stats_host, ds->sm_count, status, st);
 }
 
 int sw_reads_two_strands(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads, uint8_t *out,
@@ -1545,6 +1549,57 @@ int sw_extract_windows(const uint8_t *genome, int64_t n_bases, const int64_t *st
     if ((rc = stage_e_status(ds, 8 * ((size_t)(n_windows + 255) / 256 + 1), st, &status, &scratch))) return rc;
     return launch_extract_windows((const uint32_t *)genome, n_bases, start, length, n_windows, (uint32_t *)out,
                                   cap_bases, out_offsets, (int64_t *)scratch, ds->sm_count, status, st);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int sw_seed_stats(sw_stream_t stream, int64_t *out3)
+{
+    if (!out3) return SW_ERR_INVALID_ARG;
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds, (cudaStream_t)stream);
+    if (rc) return rc;
+    if (cuda_failed(cudaStreamSynchronize((cudaStream_t)stream))) return SW_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    if (!ds->seed_stats_host) return SW_ERR_INVALID_ARG;
+    for (int i = 0; i < 3; ++i) out3[i] = ds->seed_stats_host[i];
+    return SW_OK;
+}
+
+int sw_gather_probe(int32_t log2_words, int64_t rounds, double *loads_per_s, sw_stream_t stream)
+{
+    if (!loads_per_s || log2_words < 20 || log2_words > 34 || rounds < 1) return SW_ERR_INVALID_ARG;
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds, (cudaStream_t)stream);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t words = (size_t)1 << log2_words;
+    const int threads = 256, blocks = ds->sm_count * 8;
+    uint32_t *buf = nullptr, *out = nullptr;
+    if (cuda_failed(cudaMalloc(&buf, words * sizeof(uint32_t)))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMalloc(&out, sizeof(uint32_t) * threads * blocks))) {
+        cudaFree(buf);
+        return SW_ERR_CUDA;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.f;
+    rc = cuda_failed(cudaMemsetAsync(buf, 0x5A, words * sizeof(uint32_t), st)) ? SW_ERR_CUDA : SW_OK;
+    if (!rc && (cuda_failed(cudaEventCreate(&e0)) || cuda_failed(cudaEventCreate(&e1)))) rc = SW_ERR_CUDA;
+    if (!rc) rc = launch_gather_probe(buf, words - 1, rounds / 8 + 1, blocks, threads, out, st);  // warm-up
+    if (!rc && cuda_failed(cudaEventRecord(e0, st))) rc = SW_ERR_CUDA;
+    if (!rc) rc = launch_gather_probe(buf, words - 1, rounds, blocks, threads, out, st);
+    if (!rc && cuda_failed(cudaEventRecord(e1, st))) rc = SW_ERR_CUDA;
+    if (!rc && (cuda_failed(cudaEventSynchronize(e1)) || cuda_failed(cudaEventElapsedTime(&ms, e0, e1))))
+        rc = SW_ERR_CUDA;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    cudaFree(buf);
+    if (rc) return rc;
+    *loads_per_s = (double)blocks * threads * 8.0 * (double)rounds / (ms * 1e-3);
+    return SW_OK;
 }
 
 }  // extern "C"

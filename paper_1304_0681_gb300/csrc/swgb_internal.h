@@ -227,7 +227,9 @@ size_t seed_scratch_bytes(int64_t n_reads, int64_t capacity);
 int launch_seed_windows(const uint32_t *reads, const int64_t *roff, int64_t n_reads, const uint32_t *table,
                         const uint32_t *positions, const int64_t *chrom_off, int n_chrom, const SeedKParams &p,
                         int max_read, int block_hits, SeedOutPtrs out, int64_t capacity, uint8_t *scratch,
-                        int sm_count, int32_t *status, cudaStream_t st);
+                        int64_t *stats_host, int sm_count, int32_t *status, cudaStream_t st);
+int launch_gather_probe(const uint32_t *buf, uint64_t mask, int64_t rounds, int blocks, int threads, uint32_t *out,
+                        cudaStream_t st);
 int launch_extract_windows(const uint32_t *genome, int64_t n_bases, const int64_t *start, const int32_t *len,
                            int64_t n, uint32_t *dst, int64_t cap_bases, int64_t *woff, int64_t *blk, int sm_count,
                            int32_t *status, cudaStream_t st);

@@ -377,3 +377,30 @@ def test_map_records_and_junctions_match_the_oracle_pipeline():
     planted = {(int(ch), int(st - g.chrom_offsets[ch]), int(st - g.chrom_offsets[ch] + L - 1), int(t))
                for ch, st, L, t in g.introns}
     assert len(got_j) > 50 and set(got_j) <= planted
+
+
+def test_seed_stats_count_lookups_and_hits():
+    """The seeding counters: one lookup per seed of each read-strand, and
+    the hits of every seed with at most max_hits of them (from the oracle's
+    exact-match scan); each lookup reads at least one sector."""
+    import paper_1304_0681_gb300 as sw
+    g = synth.genome("small", seed=25)
+    rs = synth.sample_reads(g, "T2", n_reads=700, seed=26, lengths=((40, .2), (100, .5), (250, .3)))
+    idx = _index(g)
+    p = _params(max_hits=8)
+    _gpu_windows(idx, rs, p)
+    lookups, hits, sectors = sw._swgb.sw_seed_stats()
+    op = _oparams(p)
+    want_lookups, want_hits, codes = 0, 0, []
+    for r in range(rs.n_reads):
+        for seq in (rs.read(r), so.revcomp(rs.read(r))):
+            cs = so.read_seed_codes(seq, op)
+            want_lookups += len(cs)
+            codes.append(cs)
+    table = so.kmer_hits(g.packed, g.chrom_offsets, op.k, {c for cs in codes for c in cs})
+    for cs in codes:
+        for c in cs:
+            h = len(table.get(c, ()))
+            want_hits += h if h <= op.max_hits else 0
+    assert (lookups, hits) == (want_lookups, want_hits)
+    assert sectors >= lookups
