@@ -30,6 +30,7 @@ namespace {
 
 constexpr int kWarpHits = 512;            // hit list of one warp (2 KB of shared memory)
 constexpr int kSeedWarps = 8;             // warps per block of the main kernel
+constexpr int kBinWords = 512;            // 1024 16-bit bin counters per warp (2 KB)
 constexpr int kTabTile = 4096;            // table entries per block of the table scan
 
 __device__ __forceinline__ uint32_t kmask(int k) { return k >= 16 ? 0xFFFFFFFFu : ((1u << (2 * k)) - 1u); }
@@ -191,6 +192,7 @@ struct SeedScratch {
 
 struct SeedCfg {
     SeedKParams p;
+    int bin_shift;               // bins of 2^bin_shift >= k + merge_dist bases
     uint32_t mask;
     int max_read;                // longest read seeding accepts
     int block_hits;              // hit list of the large-case kernel
@@ -456,6 +458,53 @@ __device__ void finish_read_strand(uint32_t *list, int H, int64_t rs, const int6
     }
 }
 
+__device__ __forceinline__ uint32_t bin_slot(uint32_t b) { return (b * 0x9E3779B1u) >> 22; }
+
+__device__ __forceinline__ uint32_t bin_count(const uint32_t *bins, uint32_t b)
+{
+    const uint32_t s = bin_slot(b);
+    return (bins[s >> 1] >> (16 * (s & 1))) & 0xFFFFu;
+}
+
+// Drops, in place, the hits of list[0 .. H) that no other hit lies close
+// to, and returns how many remain (in their old order).  Two hits share a
+// region only when fewer than k + merge_dist bases separate their starts,
+// so they lie in the same or adjacent bins of 2^bin_shift >= k + merge_dist
+// bases; a hit alone in its bin and both neighbours forms a region of its
+// own, k <= min_cal_len bases long: never a CAL, and it never joins another
+// region.  Bins are counted in a hashed table, where a collision can only
+// keep a hit that could have gone.  One warp.
+__device__ int drop_isolated_hits(uint32_t *list, int H, uint32_t *bins, int sh, int lane)
+{
+    for (int i = lane; i < kBinWords; i += 32) bins[i] = 0u;
+    __syncwarp();
+    for (int i = lane; i < H; i += 32) {
+        const uint32_t sl = bin_slot(list[i] >> sh);
+        atomicAdd(bins + (sl >> 1), 1u << (16 * (sl & 1)));
+    }
+    __syncwarp();
+    int nk = 0;
+    for (int base = 0; base < H; base += 32) {
+        const int i = base + lane;
+        uint32_t v = 0u;
+        bool keep = false;
+        if (i < H) {
+            v = list[i];
+            const uint32_t b = v >> sh;
+            const uint32_t tot = bin_count(bins, b) + bin_count(bins, b + 1) + (b ? bin_count(bins, b - 1) : 0u);
+            keep = tot >= 2;
+        }
+        const unsigned K = __ballot_sync(0xffffffffu, keep);
+        // the chunk is read before any of it is overwritten; earlier chunks
+        // kept at most as many hits as they held
+        __syncwarp();
+        if (keep) list[nk + __popc(K & ((1u << lane) - 1u))] = v;
+        nk += __popc(K);
+        __syncwarp();
+    }
+    return nk;
+}
+
 __device__ __forceinline__ int pow2_at_least(int h)
 {
     int n = 32;
@@ -470,6 +519,7 @@ k_seed(const uint32_t *__restrict__ reads, const int64_t *__restrict__ roff, int
        int n_chrom, SeedCfg c, SeedScratch S)
 {
     __shared__ uint32_t lists[kSeedWarps][kWarpHits];
+    __shared__ uint32_t binss[kSeedWarps][kBinWords];
     __shared__ int fills[kSeedWarps];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (*(volatile const int32_t *)S.status & ST_BAD_INPUT) return;
@@ -548,6 +598,14 @@ k_seed(const uint32_t *__restrict__ reads, const int64_t *__restrict__ roff, int
             }
         }
         __syncwarp();
+        H = drop_isolated_hits(list, (int)H, binss[wib], c.bin_shift, lane);
+        if (H == 0) {
+            if (lane == 0) {
+                S.wcount[rs] = 0;
+                S.wbase[rs] = 0;
+            }
+            continue;
+        }
         const int n = pow2_at_least((int)H);
         if (n == 32) sort_in_registers<1>(list, (int)H, lane);
         else if (n == 64) sort_in_registers<2>(list, (int)H, lane);
@@ -808,6 +866,8 @@ int launch_seed_windows(const uint32_t *reads, const int64_t *roff, int64_t n_re
     c.mask = p.k >= 16 ? 0xFFFFFFFFu : ((1u << (2 * p.k)) - 1u);
     c.max_read = max_read;
     c.block_hits = block_hits;
+    c.bin_shift = 0;
+    while (((int64_t)1 << c.bin_shift) < (int64_t)p.k + p.merge_dist) ++c.bin_shift;
     if (cuda_failed(cudaMemsetAsync(scratch, 0, 64, st))) return SW_ERR_CUDA;
     if (cuda_failed(cudaFuncSetAttribute(k_seed_large, cudaFuncAttributeMaxDynamicSharedMemorySize, block_hits * 4)))
         return SW_ERR_CUDA;
