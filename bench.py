@@ -276,7 +276,7 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
     e2.record(stream)
     e2.synchronize()
     recall = float(np.mean(best_filt == best_plain))
-    oracle_sw = _oracle_sample(wl, 0.01, cigar=False) if (not args.no_cpu_baseline and rank == 0) else None
+    oracle_sw = _oracle_sample(wl, 0.01, cigar=False) if (not args.no_cpu_baseline and rank == 0 and args.gpus == 1) else None
     return {"workload": FILTER_WORKLOADS[name], "cpu_baseline": oracle_sw,
             "reads": wl.n_reads, "pairs": wl.n_pairs, "cells_exhaustive": cells,
             "plain": {"ms_per_step": ms_plain, "reads_per_s": wl.n_reads / (ms_plain * 1e-3),
@@ -354,8 +354,8 @@ def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
     stage_e_res = {"ms": statistics.mean(e_ms), "records": int(rec_n.item()), "min_score": 100, "min_intron": 20,
                    "distinct_junctions": int(len(jn["count"])), "junction_hits": int(jn["count"].sum()),
                    "steps_counted": steps}
-    oracle_sw = _oracle_sample(wl, 0.01, cigar=True) if (not args.no_cpu_baseline and rank == 0) else None
-    if not args.no_cpu_baseline and rank == 0:
+    oracle_sw = _oracle_sample(wl, 0.01, cigar=True) if (not args.no_cpu_baseline and rank == 0 and args.gpus == 1) else None
+    if not args.no_cpu_baseline and rank == 0 and args.gpus == 1:
         # the oracle's records and junction counts over a sample of pairs,
         # on its own alignments (computed first, untimed)
         import oracle
@@ -550,7 +550,7 @@ def _seeding_section(args, rank, steps: int) -> dict:
                           "includes": "seed, two-strand reads, extract, SW score+end+CIGAR, best per read, "
                                       "host count read-backs and buffer allocation"}
             del mp
-        if not args.no_cpu_baseline and rank == 0 and name == "T2":
+        if not args.no_cpu_baseline and rank == 0 and args.gpus == 1 and name == "T2":
             # the oracle as it stands: one scan of the whole reference for the
             # sample's seeds, then every read's steps in plain Python
             from oracle import seed_oracle as so
