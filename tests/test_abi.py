@@ -56,3 +56,28 @@ def test_traceback_mode_setting_is_validated():
     for bad in (-1, 2, 7):
         with pytest.raises(_swgb.SwError):
             _swgb.sw_set_traceback_mode(bad)
+
+
+def test_seeding_arguments_are_checked_before_any_device_work():
+    """Host-side validation of the seeding entry points (no GPU needed)."""
+    import ctypes
+
+    from paper_1304_0681_gb300 import _swgb
+    lib = _swgb._lib
+    assert _swgb.sw_index_table_words(15) == 4 ** 15
+    assert _swgb.sw_index_table_words(7) == 0 and _swgb.sw_index_table_words(17) == 0
+    bad = [dict(k=7), dict(k=17), dict(min_cal_len=14), dict(stride=0), dict(phase=-1), dict(max_hits=0),
+           dict(max_hits=2000), dict(merge_dist=-1), dict(max_window=0), dict(max_window=1 << 21)]
+    for kw in bad:
+        rc = lib.sw_seed_windows(None, None, None, 1, ctypes.byref(_swgb.SeedParams(**kw)), None, None, 1, None, 0,
+                                 None, None)
+        assert rc == -1, kw
+    # a read of 1,024 bases could keep more hits than the block path holds
+    rc = lib.sw_seed_windows(None, None, None, 1, ctypes.byref(_swgb.SeedParams(stride=4, max_hits=200)), None,
+                             None, 1, None, 0, None, None)
+    assert rc == -5
+    assert lib.sw_seed_stats(None, None) == -1
+    out = ctypes.c_double()
+    assert lib.sw_gather_probe(10, 4, ctypes.byref(out), None) == -1
+    assert lib.sw_gather_probe(32, 0, ctypes.byref(out), None) == -1
+    assert lib.sw_gather_probe(32, 4, None, None) == -1
