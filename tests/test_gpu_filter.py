@@ -249,3 +249,32 @@ def test_tensor_memory_forward_matches_warp_mma():
     a1 = fo.bf16_round(np.maximum(X @ Pb.W1 + Pb.b1, 0))
     ref = np.maximum(a1 @ Pb.W2 + Pb.b2, 0) @ Pb.w3 + Pb.b3
     np.testing.assert_allclose(b, ref, rtol=1e-2, atol=1e-3)
+
+
+def test_filter_workload_full_size_sampled():
+    """The filter workload at its benchmark size (500k reads, 16.25M
+    candidate pairs), scored exhaustively as the benchmark's plain arm does
+    (score and end, indexed reads), checked on a sample of pairs."""
+    import torch
+
+    import oracle
+    from paper_1304_0681_gb300 import filter as flt
+    wl = synth.generate("filter", seed=0)
+    b = _batch(wl)
+    co = torch.from_numpy(wl.cand_offsets).cuda()
+    best, cand = flt.exhaustive_best(b, co, SCORING)
+    score = b.score.cpu().numpy()
+    end = b.end.cpu().numpy().reshape(-1, 2)
+    rng = np.random.default_rng(5)
+    pairs = np.sort(rng.choice(wl.n_pairs, 2000, replace=False))
+    sub = wl.pair_slice(pairs)
+    ref = oracle.align_batch(sub.reads, sub.read_offsets, sub.windows, sub.window_offsets,
+                             scoring=oracle.Scoring(*SCORING), cigar=False)
+    np.testing.assert_array_equal(score[pairs], ref["score"])
+    np.testing.assert_array_equal(end[pairs, 0], ref["i_end"])
+    np.testing.assert_array_equal(end[pairs, 1], ref["j_end"])
+    # the best hit per read is the maximum over its candidates
+    reads = rng.choice(wl.n_reads, 500, replace=False)
+    bs = best.cpu().numpy()
+    for r in reads:
+        assert bs[r] == score[wl.cand_offsets[r]:wl.cand_offsets[r + 1]].max()

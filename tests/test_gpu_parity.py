@@ -274,3 +274,21 @@ def test_throughput_full_size_sampled(request):
     # every decoy-free pair aligns most of the read
     true = wl.kinds == synth.KIND_TRUE
     assert np.median(got["score"][true]) > 400
+
+
+def test_uneven_full_size_sampled(request):
+    """The uneven workload at its benchmark size (2M pairs, reads 75-800 bp,
+    10% spliced), in one call as the benchmark makes it, checked on a sample
+    of pairs that includes long reads and spliced (wide) windows."""
+    if request.node.callspec.params["_reset_plans"] != "tb_auto":
+        pytest.skip("the benchmark's configuration only")
+    wl = synth.generate("uneven", seed=0)
+    got = run_gpu(wl, DEFAULT)
+    rng = np.random.default_rng(4)
+    m, n = wl.pair_read_lengths, wl.window_lengths
+    long_reads = np.nonzero(m == 800)[0]
+    spliced = np.nonzero(n - m > 200)[0]
+    pairs = np.unique(np.concatenate([rng.choice(wl.n_pairs, 1500, replace=False),
+                                      rng.choice(long_reads, 150, replace=False),
+                                      rng.choice(spliced, 300, replace=False)]))
+    assert_parity(wl, got, DEFAULT, pairs=pairs)
