@@ -292,3 +292,51 @@ def test_uneven_full_size_sampled(request):
                                       rng.choice(long_reads, 150, replace=False),
                                       rng.choice(spliced, 300, replace=False)]))
     assert_parity(wl, got, DEFAULT, pairs=pairs)
+
+
+def test_host_calls_on_two_streams_at_once(request):
+    """Two host threads, each with its own stream, run host-buffer calls on
+    different batches at the same time, several times over: every result
+    equals the oracle's (the library's scratch and staging are per stream)."""
+    if request.node.callspec.params["_reset_plans"] != "tb_auto":
+        pytest.skip("one traceback mode is enough")
+    import threading
+
+    import torch
+    import paper_1304_0681_gb300 as sw
+    wls = [synth.generate("uneven", seed=21, n_reads=1500), synth.generate("throughput", seed=22, n_reads=4000)]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    jobs = []
+    for wl in wls:
+        n = wl.n_pairs
+        jobs.append({"wl": wl, "args": (t(wl.packed_reads()), t(wl.read_offsets), t(wl.packed_windows()),
+                                        t(wl.window_offsets), n, DEFAULT),
+                     "score": torch.zeros(n, dtype=torch.int32).pin_memory(),
+                     "end": torch.zeros(2 * n, dtype=torch.int32).pin_memory(),
+                     "ops": torch.zeros(int(2 * wl.read_offsets[-1] + 3 * n), dtype=torch.int32).pin_memory(),
+                     "offs": torch.zeros(n + 1, dtype=torch.int64).pin_memory(), "stream": torch.cuda.Stream()})
+    errors = []
+
+    def work(j):
+        try:
+            with torch.cuda.stream(j["stream"]):
+                for _ in range(4):
+                    sw.sw_batch_align_host_dense(*j["args"], j["score"], j["end"], j["ops"], j["offs"])
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(j,)) for j in jobs]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    for j in jobs:
+        wl = j["wl"]
+        o = j["offs"].numpy()
+        flat = j["ops"].numpy().view(np.uint32)
+        got = {"score": j["score"].numpy().astype(np.int64), "i_end": j["end"].numpy().reshape(-1, 2)[:, 0],
+               "j_end": j["end"].numpy().reshape(-1, 2)[:, 1], "ops": flat, "cigar_offsets": o[:-1],
+               "n_ops": np.diff(o)}
+        rng = np.random.default_rng(0)
+        assert_parity(wl, got, DEFAULT, pairs=np.sort(rng.choice(wl.n_pairs, 600, replace=False)))
