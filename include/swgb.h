@@ -90,6 +90,14 @@ typedef struct {
  * M/I runs, a D run between or around each, two soft clips). */
 int64_t sw_cigar_capacity(int64_t read_len);
 
+/* CSR offsets of CIGAR slots for a batch, on the device: out_offsets[p] =
+ * sum over pairs q < p of sw_cigar_capacity(length of q's read), and
+ * out_offsets[n_pairs] the total.  read_offsets, pair_read (NULL: pair p
+ * uses read p) and out_offsets (int64[n_pairs + 1]) are device memory.
+ * Stream-ordered. */
+int sw_cigar_offsets(const int64_t *read_offsets, const int64_t *pair_read, int64_t n_pairs, int64_t *out_offsets,
+                     sw_stream_t stream);
+
 /* Bytes of a packed buffer holding n_bases: ceil(n_bases / 4) rounded up to
  * a multiple of 16. */
 int64_t sw_packed_bytes(int64_t n_bases);

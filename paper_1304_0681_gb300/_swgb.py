@@ -21,7 +21,7 @@ ERRORS = {
 }
 
 #: every symbol include/swgb.h declares
-EXPORTS = ("sw_cigar_capacity", "sw_packed_bytes", "sw_batch_align", "sw_stream_release", "sw_last_cuda_error", "sw_batch_align_indexed",
+EXPORTS = ("sw_cigar_capacity", "sw_cigar_offsets", "sw_packed_bytes", "sw_batch_align", "sw_stream_release", "sw_last_cuda_error", "sw_batch_align_indexed",
            "sw_batch_align_host", "sw_sync_status", "sw_strerror", "sw_launch_count", "sw_set_plan", "sw_set_traceback_mode",
            "sw_last_traceback_split", "sw_plan_create", "sw_plan_align", "sw_plan_status", "sw_plan_destroy",
            "sw_batch_align_host_dense", "sw_records", "sw_junction_table_words", "sw_junction_table_clear", "sw_junctions_detect",
@@ -110,6 +110,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_filter_select.restype = ctypes.c_int
     lib.sw_best_per_read.argtypes = [p, p, i64, p, p, p, p]
     lib.sw_best_per_read.restype = ctypes.c_int
+    lib.sw_cigar_offsets.argtypes = [p, p, i64, p, p]
+    lib.sw_cigar_offsets.restype = ctypes.c_int
     lib.sw_stream_release.argtypes = [p]
     lib.sw_stream_release.restype = ctypes.c_int
     lib.sw_last_cuda_error.argtypes = [ctypes.POINTER(ctypes.c_char_p)]
@@ -493,3 +495,8 @@ def sw_gather_probe(log2_words: int = 32, rounds: int = 64, stream=None) -> floa
     out = ctypes.c_double(0.0)
     _check(_lib.sw_gather_probe(int(log2_words), int(rounds), ctypes.byref(out), _stream(stream)), "sw_gather_probe")
     return out.value
+
+
+def sw_cigar_offsets(read_offsets, pair_read, n_pairs: int, out_offsets, stream=None) -> None:
+    _check(_lib.sw_cigar_offsets(_ptr(read_offsets), _ptr(pair_read), int(n_pairs), _ptr(out_offsets),
+                                 _stream(stream)), "sw_cigar_offsets")

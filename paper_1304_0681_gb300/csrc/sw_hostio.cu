@@ -123,6 +123,16 @@ struct I32Of {  // a plain int32 array
     __device__ int64_t operator()(int64_t p) const { return v[p]; }
 };
 
+struct CapOfIndexed {  // capacity of pair p whose read is pair_read[p]
+    const int64_t *roff;
+    const int64_t *pair_read;
+    __device__ int64_t operator()(int64_t p) const
+    {
+        const int64_t r = pair_read[p];
+        return 2 * (roff[r + 1] - roff[r]) + 3;
+    }
+};
+
 struct RunsOf {  // runs pair p's CIGAR holds (an overflowed slot holds none)
     const int32_t *n_ops;
     __device__ int64_t operator()(int64_t p) const { return n_ops[p] > 0 ? n_ops[p] : 0; }
@@ -151,6 +161,15 @@ __global__ void k_dense_copy(const uint32_t *__restrict__ ops, const int64_t *__
 int launch_cap_offsets(const int64_t *read_off, int64_t n_pairs, int64_t *cig_off, int64_t *blk, cudaStream_t st)
 {
     return exclusive_scan(CapOf{read_off}, n_pairs, cig_off, blk, st);
+}
+
+int launch_cap_offsets_indexed(const int64_t *read_off, const int64_t *pair_read, int64_t n_pairs, int64_t *cig_off,
+                               int64_t *blk, cudaStream_t st)
+{
+    if (n_pairs == 0)
+        return cuda_failed(cudaMemsetAsync(cig_off, 0, sizeof(int64_t), st)) ? SW_ERR_CUDA : SW_OK;
+    if (!pair_read) return exclusive_scan(CapOf{read_off}, n_pairs, cig_off, blk, st);
+    return exclusive_scan(CapOfIndexed{read_off, pair_read}, n_pairs, cig_off, blk, st);
 }
 
 int launch_scan_i32(const int32_t *v, int64_t n, int64_t *out, int64_t *blk, cudaStream_t st)

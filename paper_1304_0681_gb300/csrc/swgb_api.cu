@@ -1603,3 +1603,22 @@ int sw_gather_probe(int32_t log2_words, int64_t rounds, double *loads_per_s, sw_
 }
 
 }  // extern "C"
+
+extern "C" {
+
+int sw_cigar_offsets(const int64_t *read_offsets, const int64_t *pair_read, int64_t n_pairs, int64_t *out_offsets,
+                     sw_stream_t stream)
+{
+    if (n_pairs < 0 || !out_offsets || (n_pairs > 0 && !read_offsets)) return SW_ERR_INVALID_ARG;
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds, (cudaStream_t)stream);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *status = nullptr;
+    uint8_t *scratch = nullptr;
+    if ((rc = stage_e_status(ds, 8 * ((size_t)(n_pairs + 255) / 256 + 1), st, &status, &scratch))) return rc;
+    return launch_cap_offsets_indexed(read_offsets, pair_read, n_pairs, out_offsets, (int64_t *)scratch, st);
+}
+
+}  // extern "C"

@@ -171,6 +171,8 @@ int launch_cigar_to_host(const uint32_t *ops, const int64_t *off, const int32_t 
                          uint32_t *host_ops, cudaStream_t st);
 
 int launch_cap_offsets(const int64_t *read_off, int64_t n_pairs, int64_t *cig_off, int64_t *blk, cudaStream_t st);
+int launch_cap_offsets_indexed(const int64_t *read_off, const int64_t *pair_read, int64_t n_pairs, int64_t *cig_off,
+                               int64_t *blk, cudaStream_t st);
 int launch_dense_cigar(const uint32_t *ops, const int64_t *off, const int32_t *n_ops, int64_t n_pairs,
                        int64_t *doff, uint32_t *dense, int64_t dense_cap, int64_t *blk, cudaStream_t st);
 

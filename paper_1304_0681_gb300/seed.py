@@ -169,10 +169,8 @@ def map_reads(index: KmerIndex, reads, read_offsets, n_reads: int, scoring, para
     end = torch.empty(2 * max(n, 1), dtype=torch.int32, device=dev)
     cg = None
     if cigar and n:
-        rl = (read_offsets[1:] - read_offsets[:-1]).repeat(2)
-        cap = 2 * rl[win["pair_read"]] + 3
-        coff = torch.zeros(n + 1, dtype=torch.int64, device=dev)
-        torch.cumsum(cap, 0, out=coff[1:])
+        coff = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        _swgb.sw_cigar_offsets(roff2, win["pair_read"], n, coff, stream)
         cg = (torch.empty(int(coff[-1].item()), dtype=torch.int32, device=dev), coff,
               torch.empty(n, dtype=torch.int32, device=dev))
     if n:

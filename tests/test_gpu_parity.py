@@ -340,3 +340,25 @@ def test_host_calls_on_two_streams_at_once(request):
                "n_ops": np.diff(o)}
         rng = np.random.default_rng(0)
         assert_parity(wl, got, DEFAULT, pairs=np.sort(rng.choice(wl.n_pairs, 600, replace=False)))
+
+
+def test_cigar_offsets_on_the_device(request):
+    """sw_cigar_offsets: slot offsets of 2 m + 3 runs per pair, with and
+    without a pair -> read index, and for an empty batch."""
+    if request.node.callspec.params["_reset_plans"] != "tb_auto":
+        pytest.skip("independent of the traceback mode")
+    import torch
+    import paper_1304_0681_gb300 as sw
+    wl = synth.generate("filter", seed=4, n_reads=300)
+    roff = torch.from_numpy(wl.read_offsets).cuda()
+    pr = torch.from_numpy(wl.pair_read).cuda()
+    out = torch.empty(wl.n_pairs + 1, dtype=torch.int64, device="cuda")
+    sw._swgb.sw_cigar_offsets(roff, pr, wl.n_pairs, out)
+    cap = 2 * wl.read_lengths[wl.pair_read] + 3
+    np.testing.assert_array_equal(out.cpu().numpy(), np.concatenate([[0], np.cumsum(cap)]))
+    out2 = torch.empty(wl.n_reads + 1, dtype=torch.int64, device="cuda")
+    sw._swgb.sw_cigar_offsets(roff, None, wl.n_reads, out2)
+    np.testing.assert_array_equal(out2.cpu().numpy(), np.concatenate([[0], np.cumsum(2 * wl.read_lengths + 3)]))
+    out3 = torch.full((1,), 7, dtype=torch.int64, device="cuda")
+    sw._swgb.sw_cigar_offsets(roff, None, 0, out3)
+    assert out3.item() == 0
