@@ -68,7 +68,9 @@ def _flip(code, k):
 @pytest.mark.parametrize("k", [8, 11, 15])
 def test_index_buckets_match_oracle(k):
     torch = _torch()
-    g = synth.genome("small", seed=5, chrom_len=[20_000, 1, 7, 30_000, 15_000], n_introns=20, rep_len=(100, 800))
+    # tiny and empty chromosomes: k-mers never span a border, offsets repeat
+    g = synth.genome("small", seed=5, chrom_len=[20_000, 1, 0, 7, 30_000, 0, 15_000], n_introns=20,
+                     rep_len=(100, 800))
     idx = _index(g, k)
     ref = so.index_buckets(g.packed, g.chrom_offsets, k)
     valid = sum(max(0, int(b - a) - k + 1) for a, b in zip(g.chrom_offsets[:-1], g.chrom_offsets[1:]))
@@ -142,6 +144,17 @@ def test_long_hit_lists_take_the_block_path():
     ref = so.seed_windows(packed, g.chrom_offsets, rs.reads, rs.read_offsets, _oparams(p))
     _compare(got, ref, rs.n_reads)
     assert np.all(np.diff(got["cand_offsets"])[:20] >= 41)
+
+
+def test_empty_chromosomes():
+    """Chromosomes of length 0 between others: windows, chromosomes and
+    chromosome positions as the oracle's."""
+    g = synth.genome("small", seed=27, chrom_len=[0, 150_000, 0, 0, 120_000, 0], n_introns=30)
+    rs = synth.sample_reads(g, "T2", n_reads=600, seed=28, splice=0.2)
+    idx = _index(g)
+    p = _params()
+    _compare(_gpu_windows(idx, rs, p), so.seed_windows(g.packed, g.chrom_offsets, rs.reads, rs.read_offsets,
+                                                        _oparams(p)), rs.n_reads)
 
 
 def test_edge_cases_and_capacity_retry():
