@@ -241,6 +241,19 @@ __device__ __forceinline__ void add_stats(unsigned long long *stats, uint64_t a,
     }
 }
 
+// Asynchronous 4-byte copies from global to shared memory: all of a warp's
+// bucket reads are in flight together instead of one dependent load (and
+// store) after another per lane.
+__device__ __forceinline__ void cp_async4(uint32_t *dst_smem, const uint32_t *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Bucket of a code: [lo, hi) in positions.
 __device__ __forceinline__ void bucket(const uint32_t *__restrict__ table, uint32_t code, uint32_t &lo, uint32_t &hi)
 {
@@ -265,8 +278,9 @@ __device__ void seed_gather(const uint32_t *reads, int64_t r0, int m, int strand
         st[2] += lookup_sectors(x, lo, cnt);
         if (cnt == 0) continue;
         const int at = atomicAdd(fill, (int)(hi - lo));
-        for (uint32_t j = lo; j < hi; ++j) list[at + (j - lo)] = __ldg(positions + j);
+        for (uint32_t j = lo; j < hi; ++j) cp_async4(list + at + (j - lo), positions + j);
     }
+    cp_async_wait_all();
 }
 
 // Ascending bitonic sort of list[0 .. n) (n a power of two) by the threads
@@ -577,8 +591,8 @@ k_seed(const uint32_t *__restrict__ reads, const int64_t *__restrict__ roff, int
             if (lane >= d) at += y;
         }
         at -= own;
-        for (uint32_t j = 0; j < n0; ++j) list[at + j] = __ldg(positions + lo0 + j);
-        for (uint32_t j = 0; j < n1; ++j) list[at + n0 + j] = __ldg(positions + lo1 + j);
+        for (uint32_t j = 0; j < n0; ++j) cp_async4(list + at + j, positions + lo0 + j);
+        for (uint32_t j = 0; j < n1; ++j) cp_async4(list + at + n0 + j, positions + lo1 + j);
         if (ns > 64) {
             if (lane == 31) fills[wib] = (int)(at + own);
             __syncwarp();
@@ -594,9 +608,10 @@ k_seed(const uint32_t *__restrict__ reads, const int64_t *__restrict__ roff, int
                 st[1] += hi - lo;
                 st[2] += lookup_sectors(x, lo, hi - lo);
                 const int a = atomicAdd(&fills[wib], (int)(hi - lo));
-                for (uint32_t j = lo; j < hi; ++j) list[a + (j - lo)] = __ldg(positions + j);
+                for (uint32_t j = lo; j < hi; ++j) cp_async4(list + a + (j - lo), positions + j);
             }
         }
+        cp_async_wait_all();
         __syncwarp();
         H = drop_isolated_hits(list, (int)H, binss[wib], c.bin_shift, lane);
         if (H == 0) {
