@@ -57,7 +57,7 @@ def _args():
                     help="host threads, each driving its own stream, that run the end-to-end calls")
     ap.add_argument("--no-filter", action="store_true", help="skip the learned-filter comparison")
     ap.add_argument("--filter-reads", type=int, default=500_000)
-    ap.add_argument("--fullmix-reads", type=int, default=150_000, help="reads of the full-mix sample")
+    ap.add_argument("--fullmix-reads", type=int, default=10_000_000, help="reads of the full-mix workload")
     ap.add_argument("--no-extra", action="store_true", help="skip the uneven and full-mix sections")
     ap.add_argument("--no-seeding", action="store_true", help="skip the seeding section")
     ap.add_argument("--only-seeding", action="store_true", help="run the seeding section alone")
@@ -160,9 +160,11 @@ def _cpu_baseline(wl, budget_s: float) -> dict:
                          "sample": f"the first {n1} pairs of that sample, {sub1.cells():.3e} cells in {dt1:.1f} s"}}
 
 
-def _oracle_sample(wl, frac: float = 0.01, seed: int = 3, cigar: bool = True) -> dict:
+def _oracle_sample(wl, frac: float = 0.01, seed: int = 3, cigar: bool = True, full_cells: int | None = None,
+                   of: str = "") -> dict:
     """The oracle on a seeded sample of a large workload's pairs, on all host
-    cores, with the time the whole workload would take at that rate."""
+    cores, with the time the whole workload (full_cells, default wl's) would
+    take at that rate."""
     import numpy as np
 
     import oracle
@@ -177,9 +179,9 @@ def _oracle_sample(wl, frac: float = 0.01, seed: int = 3, cigar: bool = True) ->
     dt = time.perf_counter() - t
     rate = sub.cells() / dt
     return {"value": rate / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{n} of {wl.n_pairs} pairs drawn uniformly (seed {seed}), "
+            "sample": f"{n} of {wl.n_pairs} pairs{of} drawn uniformly (seed {seed}), "
                       f"{'score + end + CIGAR' if cigar else 'score + end'}, {sub.cells():.3e} cells in {dt:.1f} s",
-            "extrapolated_full_s": wl.cells() / rate, "extrapolated": True}
+            "extrapolated_full_s": (full_cells or wl.cells()) / rate, "extrapolated": True}
 
 
 def _traffic_record(kernel_file: str):
@@ -198,19 +200,22 @@ def _traffic_record(kernel_file: str):
 FILTER_WORKLOADS = {
     "filter": "learned filter: 500k reads 150 bp, U{1..64} candidates of 250 bp, 16.25M pairs; "
               "best hit per read, score + end",
-    "fullmix": "full mix (sample): reads 75-800 bp as the uneven workload, U{1..32} candidates, 15% spliced, "
-               "true hit at 1-5% divergence; best hit per read, score + end",
+    "fullmix": "full mix: 10M reads of 75-800 bp as the uneven workload, U{1..32} candidates (about 165M pairs), "
+               "15% spliced, true hit at 1-5% divergence; best hit per read, score + end; generated on the GPU",
 }
 
 
 def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int = 500_000,
-                    n_train: int = 150_000, n_cal: int = 40_000, epochs: int = 4) -> dict:
+                    n_train: int = 150_000, n_cal: int = 40_000, epochs: int = 4, on_device: bool = False) -> dict:
     """Plain vs learned-filtered best-hit search on a candidate workload
     (default: 500k reads of 150 bp, U{1..64} candidate windows of 250 bp, one
     true at 1-3% divergence, paralog decoys at 5-20% or random).  The network
     is trained on SW scores of pairs from another seed, and (k, tau) are
     picked on a held-out seed for >= 99.6% best-hit recall; neither is timed.
-    A step is one whole search over the batch (score and end, no CIGAR)."""
+    A step is one whole search over the batch (score and end, no CIGAR).
+    With on_device the timed batch is generated on the GPU (the same
+    workload as the host generator's) and the oracle is timed on a prefix of
+    it generated on the host."""
     import numpy as np
     import torch
 
@@ -243,8 +248,18 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
     del b_cal
     setup_s = time.perf_counter() - t0
 
-    wl, b, co = load(name, rank, n_reads)
-    cells = wl.cells()
+    if on_device:
+        wl = synth.generate_device(name, seed=rank, n_reads=n_reads)
+        np_ = wl.n_pairs
+        b = DeviceBatch(wl.reads, wl.read_offsets, wl.windows, wl.window_offsets, wl.pair_read,
+                        torch.zeros(np_, dtype=torch.int32, device="cuda"),
+                        torch.zeros(2 * np_, dtype=torch.int32, device="cuda"), None, None, None)
+        co = wl.cand_offsets
+        pair_cells = (wl.window_offsets[1:] - wl.window_offsets[:-1]) * wl.pair_read_lengths()
+    else:
+        wl, b, co = load(name, rank, n_reads)
+        pair_cells = torch.from_numpy(wl.pair_read_lengths.astype(np.int64) * wl.window_lengths).cuda()
+    cells = int(pair_cells.sum().item())
     stream = torch.cuda.current_stream()
 
     def timed(fn):
@@ -266,7 +281,7 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
     res, ms_filt = timed(lambda: flt.filtered_best(b, co, model, k, tau, SCORING))
     best_filt = res.best_score.cpu().numpy()
     aligned = int(res.mask.sum().item())
-    sel_cells = int(np.sum((wl.pair_read_lengths.astype(np.int64) * wl.window_lengths)[res.mask.cpu().numpy() > 0]))
+    sel_cells = int(pair_cells[res.mask > 0].sum().item())
     # phase split of one filtered step (features + network, then the rest)
     torch.cuda.synchronize()
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -278,7 +293,14 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
     e2.record(stream)
     e2.synchronize()
     recall = float(np.mean(best_filt == best_plain))
-    oracle_sw = _oracle_sample(wl, 0.01, cigar=False) if (not args.no_cpu_baseline and rank == 0 and args.gpus == 1) else None
+    oracle_sw = None
+    if not args.no_cpu_baseline and rank == 0 and args.gpus == 1:
+        if on_device:   # the first reads of the same set, generated on the host
+            n_host = min(wl.n_reads, 200_000)
+            oracle_sw = _oracle_sample(synth.generate(name, seed=rank, n_reads=n_host), 0.01, cigar=False,
+                                       full_cells=cells, of=f" of the first {n_host} reads")
+        else:
+            oracle_sw = _oracle_sample(wl, 0.01, cigar=False)
     return {"workload": FILTER_WORKLOADS[name], "cpu_baseline": oracle_sw,
             "reads": wl.n_reads, "pairs": wl.n_pairs, "cells_exhaustive": cells,
             "plain": {"ms_per_step": ms_plain, "reads_per_s": wl.n_reads / (ms_plain * 1e-3),
@@ -846,8 +868,10 @@ def main():
         torch.cuda.empty_cache()
         uneven = _uneven_section(args, rank, steps=max(2, min(args.steps, 3)), peak_gcups=peak_gcups)
         if not args.no_filter:
+            torch.cuda.empty_cache()
             fullmix = _filter_section(args, rank, steps=max(2, min(args.steps, 3)), name="fullmix",
-                                      n_reads=args.fullmix_reads, n_train=40_000, n_cal=15_000, epochs=8)
+                                      n_reads=args.fullmix_reads, n_train=40_000, n_cal=15_000, epochs=8,
+                                      on_device=True)
         if not args.no_seeding:
             torch.cuda.empty_cache()
             seeding = _seeding_section(args, rank, steps=max(2, min(args.steps, 3)))
@@ -868,7 +892,7 @@ def main():
                              "peak_basis": f"measured 16x2 DPX add-max rate {dpx_ops / 1e12:.2f} Tops/s "
                                            f"x 2 cells / {OPS_PER_CELL:g} ops per cell"},
                 "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "learned_filter": filt,
-                "uneven": uneven, "fullmix_sample": fullmix, "small_batch_graph": graph, "seeding": seeding}
+                "uneven": uneven, "fullmix": fullmix, "small_batch_graph": graph, "seeding": seeding}
         if rank == 0 and not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
         print(json.dumps(line), flush=True)

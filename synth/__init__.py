@@ -37,6 +37,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "synth.c")
+_CORE = os.path.join(_HERE, "synth_core.h")
 _LIB_PATH = os.path.join(_HERE, "libsynth.so")
 
 KIND_TRUE, KIND_PARALOG, KIND_RANDOM = 0, 1, 2
@@ -64,6 +65,7 @@ class SynthSpec(ctypes.Structure):
         ("splice_frac", ctypes.c_double),
         ("intron_min", ctypes.c_int32),
         ("intron_max", ctypes.c_int32),
+        ("first_read", ctypes.c_int64),
     ]
 
 
@@ -115,10 +117,17 @@ def spec_for(name: str, seed: int = 0, n_reads: int | None = None) -> SynthSpec:
 _lib = None
 
 
+def _stale(lib: str, *srcs: str) -> bool:
+    return not os.path.exists(lib) or any(os.path.getmtime(lib) < os.path.getmtime(s) for s in srcs)
+
+
 def build(force: bool = False) -> str:
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    """Compile the host generator (gcc; no contraction of floating-point
+    expressions, so its uniforms compare as the device generator's do)."""
+    if force or _stale(_LIB_PATH, _SRC, _CORE):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lpthread"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp, _SRC,
+                               "-lpthread"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -243,10 +252,16 @@ class Workload:
                         self.kinds[p0:p1].copy(), self.true_cand[lo:hi].copy())
 
 
-def generate(name: str, seed: int = 0, n_reads: int | None = None, threads: int | None = None) -> Workload:
-    """Generate a named workload deterministically (independent of threads)."""
+def generate(name: str, seed: int = 0, n_reads: int | None = None, threads: int | None = None,
+             first_read: int = 0) -> Workload:
+    """Generate a named workload deterministically (independent of threads).
+
+    Every read and its candidates depend only on (seed, read index), so
+    ``first_read=R, n_reads=n`` gives reads R .. R+n-1 of any larger set of
+    the same seed (offsets rebased to 0)."""
     lib = _load()
     spec = spec_for(name, seed, n_reads)
+    spec.first_read = first_read
     nt = threads or min(os.cpu_count() or 1, 32)
     nr = int(spec.n_reads)
     read_len = np.zeros(nr, np.int32)
@@ -275,6 +290,116 @@ def generate(name: str, seed: int = 0, n_reads: int | None = None, threads: int 
         raise RuntimeError(f"synth_fill failed: {rc}")
     pair_read = np.repeat(np.arange(nr, dtype=np.int64), n_cand)
     return Workload(name, reads, read_off, wins, win_off, pair_read, cand_off, kinds, true_cand)
+
+
+# --------------------------------------------------------------------------
+# The same generator on the device (synth_gpu.cu includes synth_core.h as
+# synth.c does), for workloads too large to generate on the host.
+
+_GPU_SRC = os.path.join(_HERE, "synth_gpu.cu")
+_GPU_LIB_PATH = os.path.join(_HERE, "libsynth_gpu.so")
+_gpu_lib = None
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile the device generator (nvcc, sm_103a, -fmad=false so that its
+    double expressions round as the host generator's do)."""
+    if force or _stale(_GPU_LIB_PATH, _GPU_SRC, _CORE):
+        tmp = _GPU_LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call([os.environ.get("NVCC", "nvcc"), "-gencode", "arch=compute_103a,code=sm_103a",
+                               "-O3", "-fmad=false", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
+                               "-o", tmp, _GPU_SRC])
+        os.replace(tmp, _GPU_LIB_PATH)
+    return _GPU_LIB_PATH
+
+
+def _load_gpu():
+    global _gpu_lib
+    if _gpu_lib is None:
+        lib = ctypes.CDLL(build_gpu())
+        p, sp = ctypes.c_void_p, ctypes.POINTER(SynthSpec)
+        lib.synth_gpu_headers.argtypes = [sp, p, p, p]
+        lib.synth_gpu_reads.argtypes = [sp, p, p, p, p]
+        lib.synth_gpu_windows.argtypes = [sp, p, p, ctypes.c_int64, p, p, p, p, p]
+        _gpu_lib = lib
+    return _gpu_lib
+
+
+@dataclass
+class DeviceWorkload:
+    """A workload generated on the device: the arrays of Workload as CUDA
+    tensors, reads and windows 2-bit packed (synth_pack's layout)."""
+    name: str
+    reads: "torch.Tensor"           # uint8, packed, packed_nbytes(total read bases)
+    read_offsets: "torch.Tensor"    # int64, n_reads + 1
+    windows: "torch.Tensor"         # uint8, packed
+    window_offsets: "torch.Tensor"  # int64, n_pairs + 1
+    pair_read: "torch.Tensor"       # int64, n_pairs
+    cand_offsets: "torch.Tensor"    # int64, n_reads + 1
+    kinds: "torch.Tensor"           # uint8, n_pairs
+    true_cand: "torch.Tensor"       # int32, n_reads
+
+    @property
+    def n_reads(self) -> int:
+        return self.read_offsets.numel() - 1
+
+    @property
+    def n_pairs(self) -> int:
+        return self.window_offsets.numel() - 1
+
+    def pair_read_lengths(self):
+        return (self.read_offsets[1:] - self.read_offsets[:-1])[self.pair_read]
+
+    def cells(self) -> int:
+        """Sum of m * n over pairs."""
+        return int(((self.window_offsets[1:] - self.window_offsets[:-1]) * self.pair_read_lengths()).sum().item())
+
+
+def generate_device(name: str, seed: int = 0, n_reads: int | None = None, device="cuda",
+                    first_read: int = 0) -> DeviceWorkload:
+    """generate() on the device: the same workload, packed, without a host
+    copy."""
+    import torch
+
+    lib = _load_gpu()
+    spec = spec_for(name, seed, n_reads)
+    spec.first_read = first_read
+    nr = int(spec.n_reads)
+    dev = torch.device(device)
+    st = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+    def call(rc, what):
+        if rc:
+            raise RuntimeError(f"{what} failed: {rc}")
+
+    def cumsum0(x):
+        out = torch.zeros(x.numel() + 1, dtype=torch.int64, device=dev)
+        torch.cumsum(x.to(torch.int64), 0, out=out[1:])
+        return out
+
+    read_len = torch.empty(nr, dtype=torch.int32, device=dev)
+    n_cand = torch.empty(nr, dtype=torch.int32, device=dev)
+    call(lib.synth_gpu_headers(ctypes.byref(spec), read_len.data_ptr(), n_cand.data_ptr(), st), "synth_gpu_headers")
+    cand_off = cumsum0(n_cand)
+    read_off = cumsum0(read_len)
+    n_pairs = int(cand_off[-1].item())
+    pair_read = torch.repeat_interleave(torch.arange(nr, dtype=torch.int64, device=dev), n_cand.to(torch.int64),
+                                        output_size=n_pairs)
+    win_len = torch.empty(n_pairs, dtype=torch.int32, device=dev)
+    call(lib.synth_gpu_windows(ctypes.byref(spec), pair_read.data_ptr(), cand_off.data_ptr(), n_pairs, None,
+                               win_len.data_ptr(), None, None, st), "synth_gpu_windows (lengths)")
+    win_off = cumsum0(win_len)
+    del win_len
+    reads = torch.zeros(packed_nbytes(int(read_off[-1].item())), dtype=torch.uint8, device=dev)
+    wins = torch.zeros(packed_nbytes(int(win_off[-1].item())), dtype=torch.uint8, device=dev)
+    kinds = torch.empty(n_pairs, dtype=torch.uint8, device=dev)
+    true_cand = torch.empty(nr, dtype=torch.int32, device=dev)
+    call(lib.synth_gpu_reads(ctypes.byref(spec), read_off.data_ptr(), reads.data_ptr(), true_cand.data_ptr(), st),
+         "synth_gpu_reads")
+    call(lib.synth_gpu_windows(ctypes.byref(spec), pair_read.data_ptr(), cand_off.data_ptr(), n_pairs,
+                               win_off.data_ptr(), None, wins.data_ptr(), kinds.data_ptr(), st),
+         "synth_gpu_windows (fill)")
+    return DeviceWorkload(name, reads, read_off, wins, win_off, pair_read, cand_off, kinds, true_cand)
 
 
 def random_pairs(n_pairs: int, m_range, n_range, seed: int = 0, alphabet: int = 4) -> Workload:

@@ -32,181 +32,20 @@
 #include <string.h>
 #include <pthread.h>
 
-typedef struct {
-    uint64_t seed;
-    int64_t n_reads;
-    int32_t n_len;            /* read length mix: n_len (value, weight) pairs */
-    int32_t len_val[8];
-    double len_w[8];
-    int32_t cand_min, cand_max; /* candidates per read, uniform */
-    int32_t win_len;          /* > 0: fixed window length; 0: flanks */
-    int32_t flank_min, flank_max;
-    double div_lo, div_hi;    /* true window: per-base mutation event probability */
-    double indel_share;       /* share of mutation events that are indels */
-    double decoy_random;      /* single-candidate reads: P(window is a random decoy) */
-    double paralog_share;     /* multi-candidate reads: share of decoys that are paralogs */
-    double par_lo, par_hi;    /* paralog divergence */
-    double splice_frac;       /* P(read spans a splice junction) */
-    int32_t intron_min, intron_max;
-} synth_spec_t;
-
-enum { KIND_TRUE = 0, KIND_PARALOG = 1, KIND_RANDOM = 2 };
-
-static inline uint64_t mix64(uint64_t z)
+/* Host sink of make_window: stores bases at p (count only when p is NULL). */
+struct synth_sink { uint8_t *p; };
+#define SYNTH_FN static inline
+typedef struct synth_sink synth_sink_t;
+SYNTH_FN void synth_put(synth_sink_t *o, uint8_t b)
 {
-    z += 0x9E3779B97F4A7C15ULL;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    return z ^ (z >> 31);
+    if (o->p) *o->p++ = b;
 }
+#include "synth_core.h"
 
-typedef struct { uint64_t key, ctr; uint64_t bits; int nbits; } rng_t;
-
-static inline uint64_t rnext(rng_t *g) { return mix64(g->key ^ mix64(g->ctr++)); }
-static inline double runif(rng_t *g) { return (double)(rnext(g) >> 11) * (1.0 / 9007199254740992.0); }
-static inline int64_t rint_in(rng_t *g, int64_t lo, int64_t hi) /* inclusive */
-{
-    return lo + (int64_t)(rnext(g) % (uint64_t)(hi - lo + 1));
-}
-static inline uint8_t rbase(rng_t *g)
-{
-    if (g->nbits == 0) { g->bits = rnext(g); g->nbits = 32; }
-    uint8_t b = (uint8_t)(g->bits & 3u);
-    g->bits >>= 2; g->nbits--;
-    return b;
-}
-
-static rng_t read_rng(const synth_spec_t *s, int64_t r)
-{
-    rng_t g = {mix64(s->seed * 0xD1B54A32D192ED03ULL ^ mix64((uint64_t)r)), 0, 0, 0};
-    return g;
-}
-static rng_t cand_rng(const rng_t *rg, int64_t k)
-{
-    rng_t g = {mix64(rg->key + 0x632BE59BD9B4E019ULL * (uint64_t)(k + 1)), 0, 0, 0};
-    return g;
-}
-
-/* Per-read header draws, in a fixed order. */
-typedef struct { int32_t m, c, t, spliced; } read_hdr_t;
-
-static read_hdr_t read_header(const synth_spec_t *s, rng_t *g)
-{
-    read_hdr_t h;
-    double u = runif(g), tot = 0.0, acc = 0.0;
-    for (int k = 0; k < s->n_len; ++k) tot += s->len_w[k];
-    h.m = s->len_val[s->n_len - 1];
-    for (int k = 0; k < s->n_len; ++k) {
-        acc += s->len_w[k] / tot;
-        if (u < acc) { h.m = s->len_val[k]; break; }
-    }
-    h.c = (int32_t)rint_in(g, s->cand_min, s->cand_max);
-    h.t = (int32_t)rint_in(g, 0, h.c - 1);
-    h.spliced = runif(g) < s->splice_frac;
-    return h;
-}
-
-static void read_bases(rng_t *g, int32_t m, uint8_t *out)
-{
-    for (int32_t i = 0; i < m; ++i) out[i] = rbase(g);
-}
-
-/* Mutate read[0..m) at per-base event probability d; returns the length. */
-static int64_t mutate(rng_t *g, const uint8_t *read, int32_t m, double d, double indel_share, uint8_t *out)
-{
-    int64_t n = 0;
-    const double p_indel = d * indel_share;
-    for (int32_t i = 0; i < m; ++i) {
-        const double u = runif(g);
-        if (u < p_indel) {
-            const int32_t len = (int32_t)rint_in(g, 1, 3);
-            if (rnext(g) & 1u) {               /* insertion after this base */
-                out[n++] = read[i];
-                for (int32_t k = 0; k < len; ++k) out[n++] = rbase(g);
-            } else {                           /* deletion of len read bases */
-                i += len - 1;
-            }
-        } else if (u < d) {
-            out[n++] = (uint8_t)((read[i] + 1 + rint_in(g, 0, 2)) & 3);
-        } else {
-            out[n++] = read[i];
-        }
-    }
-    return n;
-}
-
-/*
- * Make candidate window k of a read into out (capacity checked by caller).
- * Returns its length and writes its kind.
- */
-static int64_t make_window(const synth_spec_t *s, const rng_t *rg, const read_hdr_t *h,
-                           const uint8_t *read, int64_t k, uint8_t *out, uint8_t *tmp, uint8_t *kind)
-{
-    rng_t g = cand_rng(rg, k);
-    int kd;
-    if (h->c == 1 && s->cand_max == 1)
-        kd = runif(&g) < s->decoy_random ? KIND_RANDOM : KIND_TRUE;
-    else if (k == h->t)
-        kd = KIND_TRUE;
-    else
-        kd = runif(&g) < s->paralog_share ? KIND_PARALOG : KIND_RANDOM;
-    *kind = (uint8_t)kd;
-
-    int64_t body = 0;
-    if (kd != KIND_RANDOM) {
-        const double lo = kd == KIND_TRUE ? s->div_lo : s->par_lo;
-        const double hi = kd == KIND_TRUE ? s->div_hi : s->par_hi;
-        const double d = lo + (hi - lo) * runif(&g);
-        body = mutate(&g, read, h->m, d, s->indel_share, tmp);
-        if (kd == KIND_TRUE && h->spliced) {
-            const int64_t il = rint_in(&g, s->intron_min, s->intron_max);
-            const int64_t half = body / 2;
-            memmove(tmp + half + il, tmp + half, (size_t)(body - half));
-            for (int64_t q = 0; q < il; ++q) tmp[half + q] = rbase(&g);
-            tmp[half] = 2; tmp[half + 1] = 3;             /* G T ... */
-            tmp[half + il - 2] = 0; tmp[half + il - 1] = 2; /* ... A G */
-            body += il;
-        }
-    }
-    int64_t n;
-    if (s->win_len > 0) {
-        n = s->win_len;
-        if (kd == KIND_RANDOM) {
-            for (int64_t q = 0; q < n; ++q) out[q] = rbase(&g);
-        } else if (body >= n) {
-            memcpy(out, tmp, (size_t)n);
-        } else {
-            const int64_t off = rint_in(&g, 0, n - body);
-            for (int64_t q = 0; q < off; ++q) out[q] = rbase(&g);
-            memcpy(out + off, tmp, (size_t)body);
-            for (int64_t q = off + body; q < n; ++q) out[q] = rbase(&g);
-        }
-    } else {
-        const int64_t f1 = rint_in(&g, s->flank_min, s->flank_max);
-        const int64_t f2 = rint_in(&g, s->flank_min, s->flank_max);
-        if (kd == KIND_RANDOM) {
-            n = h->m + f1 + f2;
-            for (int64_t q = 0; q < n; ++q) out[q] = rbase(&g);
-        } else {
-            n = f1 + body + f2;
-            for (int64_t q = 0; q < f1; ++q) out[q] = rbase(&g);
-            memcpy(out + f1, tmp, (size_t)body);
-            for (int64_t q = f1 + body; q < n; ++q) out[q] = rbase(&g);
-        }
-    }
-    return n;
-}
-
-static int32_t max_read_len(const synth_spec_t *s)
-{
-    int32_t mx = 0;
-    for (int k = 0; k < s->n_len; ++k) if (s->len_val[k] > mx) mx = s->len_val[k];
-    return mx;
-}
 static int64_t max_window_len(const synth_spec_t *s)
 {
     const int64_t mm = max_read_len(s);
-    int64_t body = 4 * mm + s->intron_max + 4;
+    const int64_t body = max_body_len(s);
     int64_t w = s->win_len > 0 ? s->win_len : body + 2 * (int64_t)s->flank_max + mm;
     return w > body ? w : body;
 }
@@ -230,12 +69,11 @@ static void *worker(void *arg)
     job_t *jb = (job_t *)arg;
     const synth_spec_t *s = jb->s;
     const int64_t wmax = max_window_len(s);
-    uint8_t *rb = NULL, *wb = NULL, *tb = NULL;
+    uint8_t *rb = NULL, *tb = NULL;
     if (jb->mode >= 1) {
         rb = (uint8_t *)malloc((size_t)max_read_len(s) + 16);
-        wb = (uint8_t *)malloc((size_t)wmax + 16);
         tb = (uint8_t *)malloc((size_t)wmax + 16);
-        if (!rb || !wb || !tb) { jb->rc = -3; free(rb); free(wb); free(tb); return NULL; }
+        if (!rb || !tb) { jb->rc = -3; free(rb); free(tb); return NULL; }
     }
     for (int64_t r = jb->r0; r < jb->r1; ++r) {
         rng_t g = read_rng(s, r);
@@ -248,15 +86,17 @@ static void *worker(void *arg)
             const int64_t p = jb->cand_off[r] + k;
             uint8_t kind;
             if (jb->mode == 1) {
-                jb->win_len[p] = (int32_t)make_window(s, &g, &h, rdst, k, wb, tb, &kind);
+                synth_sink_t count = {NULL};
+                jb->win_len[p] = (int32_t)make_window(s, &g, &h, rdst, k, &count, tb, &kind);
             } else {
-                const int64_t n = make_window(s, &g, &h, rdst, k, jb->win_codes + jb->win_off[p], tb, &kind);
+                synth_sink_t store = {jb->win_codes + jb->win_off[p]};
+                const int64_t n = make_window(s, &g, &h, rdst, k, &store, tb, &kind);
                 if (n != jb->win_off[p + 1] - jb->win_off[p]) jb->rc = -2;
                 jb->kinds[p] = kind;
             }
         }
     }
-    free(rb); free(wb); free(tb);
+    free(rb); free(tb);
     return NULL;
 }
 

@@ -278,3 +278,52 @@ def test_filter_workload_full_size_sampled():
     bs = best.cpu().numpy()
     for r in reads:
         assert bs[r] == score[wl.cand_offsets[r]:wl.cand_offsets[r + 1]].max()
+
+
+def test_fullmix_workload_full_size_sampled():
+    """The full-mix workload at its full size: 10M reads of 75-800 bases with
+    U{1..32} candidates (about 165M pairs), generated on the device.  Both
+    benchmark arms run on the whole set: exhaustive SW (score and end) and
+    the filtered search (features, network, selection, masked SW; an
+    untrained network, so the selection is arbitrary but exercised).  Three
+    ranges of reads (first, middle, last), generated on the host, are aligned
+    by the oracle: every pair's score and end cell, the best hit per read, and
+    the filtered best hit (the maximum over the selected candidates) must
+    match."""
+    import os
+
+    import torch
+
+    import oracle
+    from paper_1304_0681_gb300 import DeviceBatch
+    from paper_1304_0681_gb300 import filter as flt
+    dw = synth.generate_device("fullmix", seed=0)
+    assert dw.n_reads == 10_000_000 and dw.n_pairs > 150_000_000
+    n = dw.n_pairs
+    b = DeviceBatch(dw.reads, dw.read_offsets, dw.windows, dw.window_offsets, dw.pair_read,
+                    torch.zeros(n, dtype=torch.int32, device="cuda"), torch.zeros(2 * n, dtype=torch.int32, device="cuda"),
+                    None, None, None)
+    best, cand = flt.exhaustive_best(b, dw.cand_offsets, SCORING)
+    score = b.score.cpu().numpy()
+    end = b.end.cpu().numpy().reshape(-1, 2)
+    best = best.cpu().numpy()
+    model = flt.FilterModel(seed=3)
+    res = flt.filtered_best(b, dw.cand_offsets, model, 3, 0.02, SCORING)
+    fbest, mask = res.best_score.cpu().numpy(), res.mask.cpu().numpy()
+    co = dw.cand_offsets.cpu().numpy()
+    span = 1200
+    for r0 in (0, dw.n_reads // 2 - span // 2, dw.n_reads - span):
+        h = synth.generate("fullmix", seed=0, n_reads=span, first_read=r0)
+        p0, p1 = int(co[r0]), int(co[r0 + span])
+        np.testing.assert_array_equal(co[r0:r0 + span + 1] - p0, h.cand_offsets)
+        sub = h.pair_slice(np.arange(h.n_pairs))
+        ref = oracle.align_batch(sub.reads, sub.read_offsets, sub.windows, sub.window_offsets,
+                                 scoring=oracle.Scoring(*SCORING), cigar=False, threads=os.cpu_count() or 1)
+        np.testing.assert_array_equal(score[p0:p1], ref["score"])
+        np.testing.assert_array_equal(end[p0:p1, 0], ref["i_end"])
+        np.testing.assert_array_equal(end[p0:p1, 1], ref["j_end"])
+        for r in range(span):
+            a, z = h.cand_offsets[r], h.cand_offsets[r + 1]
+            assert best[r0 + r] == ref["score"][a:z].max()
+            sel = mask[p0 + a:p0 + z] > 0
+            assert sel.any() and fbest[r0 + r] == ref["score"][a:z][sel].max()

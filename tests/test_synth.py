@@ -60,3 +60,37 @@ def test_filter_candidates():
         assert ks[w.true_cand[r]] == synth.KIND_TRUE
     assert set(w.window_lengths) == {250}
     np.testing.assert_array_equal(w.pair_read, np.repeat(np.arange(2000), nc))
+
+
+def test_read_range_equals_slice_of_larger_set():
+    """Reads R .. R+n-1 generated alone equal that slice of a larger set of
+    the same seed (what lets a host range stand beside a device-generated
+    set of 10M reads)."""
+    for name in ("uneven", "filter", "fullmix", "throughput"):
+        big = synth.generate(name, seed=4, n_reads=400)
+        part = synth.generate(name, seed=4, n_reads=150, first_read=200)
+        ref = big.read_slice(200, 350)
+        for f in ("reads", "read_offsets", "windows", "window_offsets", "pair_read", "cand_offsets", "kinds",
+                  "true_cand"):
+            np.testing.assert_array_equal(getattr(part, f), getattr(ref, f), err_msg=f"{name}.{f}")
+    head = synth.generate("fullmix", seed=4, n_reads=100)
+    np.testing.assert_array_equal(head.windows, synth.generate("fullmix", seed=4, n_reads=400).read_slice(0, 100).windows)
+
+
+def test_device_generator_rejects_specs_beyond_its_buffers():
+    """The device generator keeps a read and a window body in fixed per-thread
+    buffers; a spec that could overflow them is refused on the host, before
+    any launch (so this runs without a GPU)."""
+    import ctypes
+    lib = synth._load_gpu()
+    for tweak in ({"len_val": 2000}, {"intron_max": 9000}, {"cand_min": 0}, {"n_len": 0}):
+        s = synth.spec_for("uneven", 0, 10)
+        for k, v in tweak.items():
+            if k == "len_val":
+                s.len_val[s.n_len - 1] = v
+            else:
+                setattr(s, k, v)
+        assert lib.synth_gpu_headers(ctypes.byref(s), None, None, None) == -1, tweak
+    s = synth.spec_for("fullmix", 0, 10)
+    s.n_reads = 0                         # in range and empty: nothing to launch
+    assert lib.synth_gpu_headers(ctypes.byref(s), None, None, None) == 0
