@@ -35,6 +35,14 @@ constexpr int kSmallSlabWords = 4096;  // per-pair slab of the main traceback la
 constexpr size_t kSlabBudget = (size_t)4 << 30;
 constexpr int64_t kTiledLaneWords = 4096;  // largest lane tile of a lane-interleaved traceback
 constexpr int64_t kTiledLaneWords16 = 8192;  // the same for the 16-bit traceback (two pairs per lane)
+// Lanes per pair of a multi-lane traceback: the smallest power of two T with
+// the class's longest read in at most this many chunks of 8T rows.  A chunk
+// sweeps its rows' band box, 8T - 1 columns wider than the band, so smaller T
+// wastes fewer cells per pair and larger T keeps fewer pairs per warp waiting.
+// Measured on the uneven batch (2M pairs, reads 75-800 bp), 16-bit sweep:
+// 4 chunks 57.0 ms, 8 chunks 49.6 ms, 16 chunks 64.5 ms of traceback.
+constexpr int kTbChunks32 = 4;
+constexpr int kTbChunks16 = 8;
 // 16-bit traceback tiles kept for the walk: up to this share of the free
 // device memory, at most kTile16Cap; larger batches go in rounds
 constexpr double kTile16FreeShare = 0.4;
@@ -458,14 +466,14 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
                 // score bound allows it; else int32 lanes.  T lanes share a
                 // pair: one where a lane's tile (every chunk at the widest
                 // window) stays small, else a power of two covering the
-                // longest read in about four chunks, so that one pair's cells
-                // do not run on a single lane.  A T-lane chunk window is at
-                // most 8 (T - 1) wider than the one-lane windows the key pass
-                // measured.
+                // longest read in a few chunks (kTbChunks16, kTbChunks32), so
+                // that one pair's cells do not run on a single lane.  A T-lane
+                // chunk window is at most 8 (T - 1) wider than the one-lane
+                // windows the key pass measured.
                 const int64_t wcap4 = (t.wcap + 3) / 4 * 4;
-                int Tl = 1;
-                while (Tl < 32 && (int64_t)Tl * 32 < r.max_m) Tl *= 2;
                 t.packed16 = allow16 && r.mode != MODE_I32;
+                int Tl = 1;
+                while (Tl < 32 && (int64_t)Tl * 8 * (t.packed16 ? kTbChunks16 : kTbChunks32) < r.max_m) Tl *= 2;
                 const bool one_lane16 = chunks * wcap4 * 2 <= kTiledLaneWords16;
                 t.tiled = !t.packed16 && chunks * t.wcap <= kTiledLaneWords;
                 t.lanes = (t.packed16 && one_lane16) || t.tiled ? 1 : Tl;
@@ -752,9 +760,9 @@ int plan_build(sw_plan *pl, DeviceState *ds, cudaStream_t st)
             const int64_t chunks = (max_m + TB_ROWS - 1) / TB_ROWS;
             const int64_t wcap1 = max_n;
             const int64_t wcap4 = (wcap1 + 3) / 4 * 4;
-            int Tl = 1;
-            while (Tl < 32 && (int64_t)Tl * 32 < max_m) Tl *= 2;
             t.packed16 = allow16 && r.mode != MODE_I32;
+            int Tl = 1;
+            while (Tl < 32 && (int64_t)Tl * 8 * (t.packed16 ? kTbChunks16 : kTbChunks32) < max_m) Tl *= 2;
             t.tiled = !t.packed16 && chunks * wcap1 <= kTiledLaneWords;
             t.lanes = (t.packed16 && chunks * wcap4 * 2 <= kTiledLaneWords16) || t.tiled ? 1 : Tl;
             const int T = t.lanes;
