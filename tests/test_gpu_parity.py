@@ -11,7 +11,8 @@ pytestmark = pytest.mark.gpu
 
 DEFAULT = (5, -4, -10, -1)
 # match*min(m,n) decides the arithmetic: <= 1022 -> 16-bit lanes with 16-bit
-# keys, <= 32000 -> 16-bit lanes with 32-bit keys, else int32 lanes
+# keys (at most 32 rows per lane above 510), <= 32000 -> 16-bit lanes with
+# 32-bit keys, else int32 lanes
 WIDE16 = (50, -30, -60, -5)
 INT32 = (120, -60, -7, -3)
 
@@ -109,6 +110,29 @@ def _workload(reads, wins):
                           np.concatenate(wins) if sum(len(w) for w in wins) else np.zeros(0, np.uint8), woff,
                           np.arange(n, dtype=np.int64), np.arange(n + 1, dtype=np.int64),
                           np.zeros(n, np.uint8), np.zeros(n, np.int32))
+
+
+def test_key_mode_boundaries():
+    """Reads around the limits of the arithmetic modes: match * min(m, n) at
+    and just above 510 (6-bit row tags) and 1022 (the end of 16-bit keys),
+    with three scorings.  Planted copies of the read score at the top of each
+    range, and 2-letter alphabets make rows tie, which the row tags decide."""
+    rng = np.random.default_rng(7)
+    reads, wins = [], []
+    for m in (101, 102, 103, 203, 204, 205, 206, 300, 408, 409, 410, 411, 510, 511, 512, 513, 1022, 1023, 1024):
+        for alphabet, plant in ((4, True), (2, False), (2, True)):
+            r = rng.integers(0, alphabet, m).astype(np.uint8)
+            w = rng.integers(0, alphabet, m + 60).astype(np.uint8)
+            if plant:
+                w[30:30 + m] = r
+            reads.append(r)
+            wins.append(w)
+    wl = _workload(reads, wins)
+    for sc in (DEFAULT, (2, -3, -5, -2), (3, -2, -4, -1)):
+        got = run_gpu(wl, sc)
+        assert_parity(wl, got, sc)
+        planted = np.arange(0, wl.n_pairs, 3)
+        np.testing.assert_array_equal(got["score"][planted], sc[0] * wl.read_lengths[planted])
 
 
 @pytest.mark.parametrize("lanes,rows", [(1, 8), (3, 16), (4, 25), (5, 20), (7, 16), (13, 8), (32, 8), (32, 32),
