@@ -3,7 +3,7 @@
 The paper's Stage E aligns every read against all of its extended CALs; the
 filter is an addition that ranks the candidates of a read so that only the
 best-looking ones get full Smith-Waterman, with exhaustive SW as fallback
-and as the judge of best-hit recall.  This module is the plain fp64
+and as the reference that best-hit recall is measured against.  This module is the plain fp64
 definition the CUDA kernels are checked against; only tests, the smoke check
 and the benchmark's CPU leg may use it.
 
