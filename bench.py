@@ -250,12 +250,12 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
 
     if on_device:
         wl = synth.generate_device(name, seed=rank, n_reads=n_reads)
-        np_ = wl.n_pairs
+        n_pairs = wl.n_pairs
         b = DeviceBatch(wl.reads, wl.read_offsets, wl.windows, wl.window_offsets, wl.pair_read,
-                        torch.zeros(np_, dtype=torch.int32, device="cuda"),
-                        torch.zeros(2 * np_, dtype=torch.int32, device="cuda"), None, None, None)
+                        torch.zeros(n_pairs, dtype=torch.int32, device="cuda"),
+                        torch.zeros(2 * n_pairs, dtype=torch.int32, device="cuda"), None, None, None)
         co = wl.cand_offsets
-        pair_cells = (wl.window_offsets[1:] - wl.window_offsets[:-1]) * wl.pair_read_lengths()
+        pair_cells = (wl.window_offsets[1:] - wl.window_offsets[:-1]) * wl.pair_read_lengths
     else:
         wl, b, co = load(name, rank, n_reads)
         pair_cells = torch.from_numpy(wl.pair_read_lengths.astype(np.int64) * wl.window_lengths).cuda()

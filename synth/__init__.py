@@ -347,12 +347,13 @@ class DeviceWorkload:
     def n_pairs(self) -> int:
         return self.window_offsets.numel() - 1
 
+    @property
     def pair_read_lengths(self):
         return (self.read_offsets[1:] - self.read_offsets[:-1])[self.pair_read]
 
     def cells(self) -> int:
         """Sum of m * n over pairs."""
-        return int(((self.window_offsets[1:] - self.window_offsets[:-1]) * self.pair_read_lengths()).sum().item())
+        return int(((self.window_offsets[1:] - self.window_offsets[:-1]) * self.pair_read_lengths).sum().item())
 
 
 def generate_device(name: str, seed: int = 0, n_reads: int | None = None, device="cuda",
