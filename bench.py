@@ -509,6 +509,8 @@ def _seeding_section(args, rank, steps: int) -> dict:
             ws_ = wv["strand"].cpu().numpy()[i]
             a = g.chrom_offsets[rs.chrom] + rs.pos
             hit = ok & (ws_ == rs.strand) & (st <= a) & (a <= en)
+            mq = mp.mapq.cpu().numpy()
+            hi_q = ok & (mq >= 20)
             # the same reads from pinned host memory in 8 batches of 250k, by
             # one worker stream and by two and three overlapping ones
             n_b = 8
@@ -571,8 +573,13 @@ def _seeding_section(args, rank, steps: int) -> dict:
             sec["map"] = {"ms_per_step": wt * 1e3, "reads_per_s": rs.n_reads / wt, "pairs": n, "cells": cells,
                           "gcups_incl_seeding": cells / wt / 1e9, "mapped_share": float(ok.mean()),
                           "best_window_holds_origin": float(hit.mean()),
-                          "includes": "seed, two-strand reads, extract, SW score+end+CIGAR, best per read, "
-                                      "host count read-backs and buffer allocation"}
+                          "mapq": {"mean": float(mq[ok].mean()) if ok.any() else None,
+                                   "share_ge_20": float(hi_q.mean()),
+                                   "origin_share_at_ge_20": float(hit[hi_q].mean()) if hi_q.any() else None,
+                                   "origin_share_below_20": float(hit[ok & ~hi_q].mean()) if (ok & ~hi_q).any()
+                                   else None},
+                          "includes": "seed, two-strand reads, extract, SW score+end+CIGAR, top hit and mapping "
+                                      "quality per read, host count read-backs and buffer allocation"}
             del mp
         if not args.no_cpu_baseline and rank == 0 and args.gpus == 1 and name == "T2":
             # the oracle as it stands: one scan of the whole reference for the

@@ -398,6 +398,23 @@ int sw_records(const int32_t *score, const int32_t *end, const sw_cigar_t *cigar
                int32_t min_score, sw_record_t *out_records, int64_t *out_count, sw_stream_t stream);
 
 /*
+ * Top hits.  The SW task reports statistics of each alignment, "e.g. quality
+ * score" (§2, Stage E), without defining one.  Per read r, over its
+ * candidates p = cand_offsets[r] .. cand_offsets[r+1]-1 with pair_mask[p] != 0
+ * (pair_mask may be NULL: all):
+ *   best_score[r]   S1, the largest score
+ *   best_cand[r]    its candidate index within the read (first on ties)
+ *   second_score[r] S2, the largest score of the other candidates (so a tie
+ *                   gives S2 = S1), 0 when there is no other candidate
+ *   mapq[r]         min(60, floor(60 (S1 - S2) / S1)), 0 when S1 <= 0
+ * A read without candidates gets -1, -1, -1 and 0.  best_cand, second_score
+ * and mapq may be NULL.  All arrays are device memory (int32[n_reads];
+ * cand_offsets int64[n_reads + 1]).
+ */
+int sw_top_hits(const int32_t *score, const int64_t *cand_offsets, int64_t n_reads, const uint8_t *pair_mask,
+                int32_t *best_score, int32_t *best_cand, int32_t *second_score, int32_t *mapq, sw_stream_t stream);
+
+/*
  * Splice junctions.  Every D run of at least min_intron window bases in the
  * CIGAR of a record (score >= min_score, > 0) is a candidate intron
  * window[j .. j+len-1]; it is a junction when it starts with GT and ends

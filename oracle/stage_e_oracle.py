@@ -20,7 +20,12 @@ Readings (the paper gives no numbers or formats for these):
   columns j_start..j_end with j_start = j_end + 1 - (M + D bases);
 - a junction is (chromosome, first intron base, last intron base, strand),
   all in reference coordinates; GT...AG gives strand '+' (0), CT...AC
-  strand '-' (1); other marks are not junctions.
+  strand '-' (1); other marks are not junctions;
+- the alignment's "quality score" (listed among the SW task's statistics,
+  not defined) is read per read as a mapping quality: S1 the best score of
+  its candidates (the first candidate reaching it is the top hit), S2 the
+  best score of the other candidates (0 without one), and quality
+  min(60, floor(60 (S1 - S2) / S1)), 0 when S1 <= 0.
 
 Every function here is a plain loop over the definition.
 """
@@ -106,6 +111,26 @@ def junction_counts(windows, window_offsets, score, j_end, cigars, window_chrom,
             for key in pair_junctions(w, cigars[p], j_end[p], window_chrom[p], window_pos[p], min_intron):
                 counts[key] = counts.get(key, 0) + 1
     return counts
+
+
+def top_hits(score, cand_offsets, mask=None):
+    """Per read: (best score, its candidate index, second-best score, mapping
+    quality), over candidates with mask[p] != 0 (all without a mask); a read
+    without candidates gives (-1, -1, -1, 0)."""
+    out = []
+    for r in range(len(cand_offsets) - 1):
+        p0, p1 = int(cand_offsets[r]), int(cand_offsets[r + 1])
+        cands = [(int(score[p]), p - p0) for p in range(p0, p1) if mask is None or mask[p]]
+        if not cands:
+            out.append((-1, -1, -1, 0))
+            continue
+        s1 = max(s for s, _ in cands)
+        c1 = min(c for s, c in cands if s == s1)
+        others = [s for s, c in cands if c != c1]
+        s2 = max(others) if others else 0
+        q = 0 if s1 <= 0 else min(60, (60 * (s1 - s2)) // s1)
+        out.append((s1, c1, s2, q))
+    return out
 
 
 def cigars_of(res):

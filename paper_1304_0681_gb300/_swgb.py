@@ -29,6 +29,7 @@ EXPORTS = ("sw_cigar_capacity", "sw_cigar_offsets", "sw_packed_bytes", "sw_batch
            "sw_plan_rows", "sw_alu_probe", "sw_phase_timing", "sw_phase_times", "sw_batch_align_noalloc",
            "sw_batch_align_masked", "sw_filter_features", "sw_mlp_bytes", "sw_mlp_init", "sw_mlp_refresh",
            "sw_mlp_forward", "sw_set_mlp_kernel", "sw_mlp_grad", "sw_mlp_adam", "sw_filter_select", "sw_best_per_read",
+           "sw_top_hits",
            # include/swgb_seed.h
            "sw_index_table_words", "sw_index_build", "sw_seed_windows", "sw_reads_two_strands",
            "sw_extract_windows", "sw_seed_stats", "sw_gather_probe")
@@ -110,6 +111,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_filter_select.restype = ctypes.c_int
     lib.sw_best_per_read.argtypes = [p, p, i64, p, p, p, p]
     lib.sw_best_per_read.restype = ctypes.c_int
+    lib.sw_top_hits.argtypes = [p, p, i64, p, p, p, p, p, p]
+    lib.sw_top_hits.restype = ctypes.c_int
     lib.sw_cigar_offsets.argtypes = [p, p, i64, p, p]
     lib.sw_cigar_offsets.restype = ctypes.c_int
     lib.sw_stream_release.argtypes = [p]
@@ -438,6 +441,12 @@ def sw_filter_select(pred, cand_offsets, n_reads: int, k: int, tau: float, pair_
 def sw_best_per_read(score, cand_offsets, n_reads: int, pair_mask, best_score, best_cand, stream=None) -> None:
     _check(_lib.sw_best_per_read(_ptr(score), _ptr(cand_offsets), int(n_reads), _ptr(pair_mask), _ptr(best_score),
                                  _ptr(best_cand), _stream(stream)), "sw_best_per_read")
+
+
+def sw_top_hits(score, cand_offsets, n_reads: int, pair_mask, best_score, best_cand, second_score, mapq,
+                stream=None) -> None:
+    _check(_lib.sw_top_hits(_ptr(score), _ptr(cand_offsets), int(n_reads), _ptr(pair_mask), _ptr(best_score),
+                            _ptr(best_cand), _ptr(second_score), _ptr(mapq), _stream(stream)), "sw_top_hits")
 
 
 def sw_index_table_words(k: int) -> int:

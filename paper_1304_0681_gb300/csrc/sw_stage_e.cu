@@ -4,6 +4,9 @@
 // record (reference position, strand, ...) and looks in its CIGAR for long
 // deletion runs whose ends carry the intron marks GT ... AG or CT ... AC;
 // such a run is a splice junction, counted over all batches (§2, Stage E).
+// The SW task also reports statistics of each alignment, a quality score
+// among them, which the paper does not define; here a read's top hit and a
+// mapping quality from the gap between its best and second-best scores.
 //
 // Records: one thread per pair computes the aligned span from its CIGAR;
 // a block count, a scan of the block counts and a second pass write the
@@ -206,7 +209,65 @@ __global__ void k_table_export(const uint64_t *keys, const unsigned long long *c
 
 int grid_for(int64_t n, int threads) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 32)); }
 
+// Top hit per read: best score S1 and its candidate (first on ties), the best
+// score S2 of the other candidates (0 when there are none), and the mapping
+// quality min(60, floor(60 (S1 - S2) / S1)), 0 when S1 <= 0.  Masked-out
+// candidates are skipped; a read without candidates gets -1, -1, -1, 0.
+__global__ void k_top_hits(const int32_t *__restrict__ score, const int64_t *__restrict__ cand_off, int64_t n_reads,
+                           const uint8_t *__restrict__ mask, int32_t *__restrict__ best, int32_t *__restrict__ best_cand,
+                           int32_t *__restrict__ second, int32_t *__restrict__ mapq)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_reads;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p0 = cand_off[r], p1 = cand_off[r + 1];
+        int32_t s1 = 0, s2 = 0, c1 = -1;
+        bool any = false, two = false;
+        for (int64_t p = p0; p < p1; ++p) {
+            if (mask && !mask[p]) continue;
+            const int32_t s = score[p];
+            if (!any) {
+                s1 = s;
+                c1 = (int32_t)(p - p0);
+                any = true;
+            } else if (s > s1) {
+                s2 = s1;  // the old best is now the best of the others
+                s1 = s;
+                c1 = (int32_t)(p - p0);
+                two = true;
+            } else {
+                s2 = two ? max(s2, s) : s;
+                two = true;
+            }
+        }
+        int32_t q = 0;
+        if (!any) {
+            s1 = -1;
+            s2 = -1;
+        } else {
+            if (!two) s2 = 0;
+            if (s1 > 0) {
+                const int64_t g = 60 * ((int64_t)s1 - s2) / s1;
+                q = (int32_t)(g < 60 ? g : 60);
+            }
+        }
+        best[r] = s1;
+        if (best_cand) best_cand[r] = c1;
+        if (second) second[r] = s2;
+        if (mapq) mapq[r] = q;
+    }
+}
+
 }  // namespace
+
+int launch_top_hits(const int32_t *score, const int64_t *cand_off, int64_t n_reads, const uint8_t *mask, int32_t *best,
+                    int32_t *best_cand, int32_t *second, int32_t *mapq, cudaStream_t st)
+{
+    int64_t blocks = (n_reads + 127) / 128;
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 32));
+    k_top_hits<<<(unsigned)blocks, 128, 0, st>>>(score, cand_off, n_reads, mask, best, best_cand, second, mapq);
+    count_launch();
+    return launch_status();
+}
 
 int launch_records(const int32_t *score, const int32_t *end, const sw_cigar_t &cig, int64_t n_pairs,
                    const int32_t *chrom, const int64_t *pos, const int8_t *strand, int32_t min_score,

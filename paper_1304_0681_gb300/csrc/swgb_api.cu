@@ -1394,6 +1394,16 @@ int sw_records(const int32_t *score, const int32_t *end, const sw_cigar_t *cigar
                           out_records, out_count, blk_count, blk_off, st);
 }
 
+int sw_top_hits(const int32_t *score, const int64_t *cand_offsets, int64_t n_reads, const uint8_t *pair_mask,
+                int32_t *best_score, int32_t *best_cand, int32_t *second_score, int32_t *mapq, sw_stream_t stream)
+{
+    if (n_reads < 0) return SW_ERR_INVALID_ARG;
+    if (n_reads == 0) return SW_OK;
+    if (!score || !cand_offsets || !best_score) return SW_ERR_INVALID_ARG;
+    return launch_top_hits(score, cand_offsets, n_reads, pair_mask, best_score, best_cand, second_score, mapq,
+                           (cudaStream_t)stream);
+}
+
 int64_t sw_junction_table_words(int64_t capacity) { return capacity < 0 ? 0 : 2 * capacity; }
 
 static bool table_ok(const uint64_t *table, int64_t capacity)

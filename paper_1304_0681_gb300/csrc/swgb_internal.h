@@ -156,6 +156,8 @@ int launch_select(const float *pred, const int64_t *cand_off, int64_t n_reads, i
 int launch_best_per_read(const int32_t *score, const int64_t *cand_off, int64_t n_reads, const uint8_t *mask,
                          int32_t *best, int32_t *best_cand, cudaStream_t st);
 
+int launch_top_hits(const int32_t *score, const int64_t *cand_off, int64_t n_reads, const uint8_t *mask, int32_t *best,
+                    int32_t *best_cand, int32_t *second, int32_t *mapq, cudaStream_t st);
 int launch_records(const int32_t *score, const int32_t *end, const sw_cigar_t &cig, int64_t n_pairs,
                    const int32_t *chrom, const int64_t *pos, const int8_t *strand, int32_t min_score,
                    sw_record_t *out, int64_t *out_count, int32_t *blk_count, int64_t *blk_off, cudaStream_t st);

@@ -132,6 +132,8 @@ class Mapped:
     cigar: tuple | None
     best_score: torch.Tensor   # per read
     best_cand: torch.Tensor
+    second_score: torch.Tensor  # per read: best score of the read's other windows
+    mapq: torch.Tensor          # per read: min(60, 60 (best - second) // best)
 
     def cigar_tuple(self):
         return self.cigar
@@ -152,7 +154,8 @@ def map_reads(index: KmerIndex, reads, read_offsets, n_reads: int, scoring, para
               cigar: bool = True, stream=None, min_score: int | None = None, junctions=None,
               min_intron: int = 20) -> Mapped:
     """Seed, extract, align every (read strand, window) pair, and pick each
-    read's best window (first on ties).  With min_score (and a CIGAR), the
+    read's best window (first on ties) with its second-best score and
+    mapping quality (sw_top_hits).  With min_score (and a CIGAR), the
     alignments scoring at least min_score also become records in reference
     coordinates, and, given a stage_e.JunctionTable, their deletion runs of
     at least min_intron bases with intron marks are counted in it
@@ -188,13 +191,12 @@ def map_reads(index: KmerIndex, reads, read_offsets, n_reads: int, scoring, para
             _swgb.sw_junctions_detect(wb, woff, score, end, cg, n, win["chrom"], win["pos"], min_score, min_intron,
                                       junctions.table, junctions.capacity, stream)
             _swgb.sw_sync_status(stream)
-    best = torch.empty(max(n_reads, 1), dtype=torch.int32, device=dev)
-    bcand = torch.empty(max(n_reads, 1), dtype=torch.int32, device=dev)
+    best, bcand, second, mapq = (torch.empty(max(n_reads, 1), dtype=torch.int32, device=dev) for _ in range(4))
     if n_reads:
-        _swgb.sw_best_per_read(score, win["cand_offsets"], n_reads, None, best, bcand, stream)
+        _swgb.sw_top_hits(score, win["cand_offsets"], n_reads, None, best, bcand, second, mapq, stream)
     _swgb.sw_sync_status(stream)
     return Mapped(win, rec_out, n_rec, reads2, roff2, wb, woff, score[:n], end[:2 * n], cg, best[:n_reads],
-                  bcand[:n_reads])
+                  bcand[:n_reads], second[:n_reads], mapq[:n_reads])
 
 
 @dataclass
@@ -203,6 +205,7 @@ class BatchResult:
     best_cand: np.ndarray    # index of the best window within the read's windows
     best_start: np.ndarray   # its reference start (-1 when none)
     best_strand: np.ndarray
+    mapq: np.ndarray         # mapping quality (sw_top_hits)
     n_windows: int
 
 
@@ -222,9 +225,9 @@ def _map_host_batch(index: KmerIndex, packed: torch.Tensor, offsets: torch.Tenso
         strand = torch.where(ok, w["strand"][i].to(torch.int64), torch.full_like(bc, -1))
     else:
         start = strand = torch.full_like(bc, -1)
-    out = torch.stack([mp.best_score.to(torch.int64), bc, start, strand]).cpu()
+    out = torch.stack([mp.best_score.to(torch.int64), bc, start, strand, mp.mapq.to(torch.int64)]).cpu()
     return BatchResult(out[0].numpy().astype(np.int32), out[1].numpy().astype(np.int32), out[2].numpy(),
-                       out[3].numpy().astype(np.int8), w["count"])
+                       out[3].numpy().astype(np.int8), out[4].numpy().astype(np.int32), w["count"])
 
 
 _STREAMS: dict = {}

@@ -3,7 +3,8 @@
 Records are the alignments whose score passes a threshold, with their
 reference coordinates; junctions are long deletion runs whose intron starts
 and ends with GT ... AG (strand 0) or CT ... AC (strand 1), counted across
-batches in a device hash table.  The kernels do all the work; this module
+batches in a device hash table; top hits are each read's best candidate with
+a mapping quality from its best and second-best scores.  The kernels do all the work; this module
 allocates buffers and decodes the packed outputs.
 """
 from __future__ import annotations
@@ -26,6 +27,18 @@ def records(batch: DeviceBatch, window_chrom, window_pos, window_strand, min_sco
     _swgb.sw_records(batch.score, batch.end, batch.cigar_tuple(), n, window_chrom, window_pos, window_strand,
                      min_score, out, cnt, stream)
     return _decode_records(out, int(cnt.item()))
+
+
+def top_hits(score: torch.Tensor, cand_offsets: torch.Tensor, n_reads: int, mask: torch.Tensor | None = None,
+             stream=None) -> dict:
+    """Per read (device int32 tensors): best score, its candidate index,
+    second-best score and mapping quality min(60, 60 (S1 - S2) // S1)."""
+    dev = score.device
+    out = {k: torch.empty(max(n_reads, 1), dtype=torch.int32, device=dev)[:n_reads]
+           for k in ("best_score", "best_cand", "second_score", "mapq")}
+    _swgb.sw_top_hits(score, cand_offsets, n_reads, mask, out["best_score"], out["best_cand"], out["second_score"],
+                      out["mapq"], stream)
+    return out
 
 
 def _decode_records(out: torch.Tensor, k: int) -> dict:

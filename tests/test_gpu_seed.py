@@ -231,15 +231,23 @@ def test_map_reads_matches_oracle_alignment():
     c = g.codes()
     score = mp.score.cpu().numpy()
     end = mp.end.cpu().numpy().reshape(-1, 2)
+    oscore = np.zeros(len(ref["start"]), np.int64)
     for i in range(len(ref["start"])):
         r = int(ref["read"][i])
         seq = rs.read(r) if ref["strand"][i] == 0 else so.revcomp(rs.read(r))
         s, ie, je, _ = oracle.align(seq, c[ref["start"][i]:ref["end"][i] + 1], oracle.Scoring(*SC), cigar=False)
         assert (score[i], end[i, 0], end[i, 1]) == (s, ie, je), i
+        oscore[i] = s
     best = mp.best_score.cpu().numpy()
     for r in range(rs.n_reads):
         lo, hi = ref["cand_offsets"][r], ref["cand_offsets"][r + 1]
         assert best[r] == (score[lo:hi].max() if hi > lo else -1)
+    # top hit, second-best score and mapping quality of every read, from the
+    # oracle's own scores
+    from oracle import stage_e_oracle as se
+    top = np.array(se.top_hits(oscore, ref["cand_offsets"]), np.int64).reshape(-1, 4)
+    for k, f in enumerate(("best_score", "best_cand", "second_score", "mapq")):
+        np.testing.assert_array_equal(getattr(mp, f).cpu().numpy(), top[:, k], err_msg=f)
     # mapping accuracy: the best window of most reads holds their origin
     bc = mp.best_cand.cpu().numpy()
     hit = 0
@@ -296,6 +304,7 @@ def test_pipelined_batches_match_one_map():
         res = map_batches(idx, batches, SC, n_streams=ns)
         np.testing.assert_array_equal(np.concatenate([r.best_score for r in res]), want_score)
         np.testing.assert_array_equal(np.concatenate([r.best_cand for r in res]), want_cand)
+        np.testing.assert_array_equal(np.concatenate([r.mapq for r in res]), whole.mapq.cpu().numpy())
     ref = so.seed_windows(g.packed, g.chrom_offsets, rs.reads, rs.read_offsets, _oparams(_params()),
                           read_ids=range(0, 3000, 97))
     c = g.codes()

@@ -155,3 +155,65 @@ def test_full_table_and_unsupported_keys_are_reported():
     assert e.value.code == -5  # SW_ERR_UNSUPPORTED
     with pytest.raises(sw.SwError):
         stage_e.JunctionTable(100)  # not a power of two
+
+
+def _top_hits_gpu(score, off, mask, outputs=True):
+    import torch
+    from paper_1304_0681_gb300 import _swgb
+    n = len(off) - 1
+    s = torch.from_numpy(np.asarray(score, np.int32)).cuda()
+    o = torch.from_numpy(np.asarray(off, np.int64)).cuda()
+    m = None if mask is None else torch.from_numpy(np.asarray(mask, np.uint8)).cuda()
+    out = [torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda") for _ in range(4)]
+    _swgb.sw_top_hits(s, o, n, m, out[0], out[1] if outputs else None, out[2] if outputs else None,
+                      out[3] if outputs else None)
+    torch.cuda.synchronize()
+    return [x[:n].cpu().numpy() for x in out]
+
+
+def test_top_hits_random_scores():
+    """Seeded scores over a narrow range (ties everywhere), 0-40 candidates
+    per read (empty reads included), with and without a mask, and with the
+    optional outputs left out: bit-exact against the oracle."""
+    rng = np.random.default_rng(9)
+    counts = rng.integers(0, 41, 20000)
+    counts[::97] = 0
+    off = np.zeros(len(counts) + 1, np.int64)
+    np.cumsum(counts, out=off[1:])
+    score = rng.integers(0, 20, int(off[-1]))
+    score[::11] = rng.integers(0, 2000, len(score[::11]))
+    mask = (rng.random(int(off[-1])) < 0.6).astype(np.uint8)
+    for m in (None, mask):
+        ref = np.array(se.top_hits(score, off, m), np.int64).reshape(-1, 4)
+        got = _top_hits_gpu(score, off, m)
+        for k in range(4):
+            np.testing.assert_array_equal(got[k], ref[:, k], err_msg=f"output {k}")
+        best_only = _top_hits_gpu(score, off, m, outputs=False)
+        np.testing.assert_array_equal(best_only[0], ref[:, 0])
+        assert (best_only[1] == -7).all() and (best_only[3] == -7).all()
+
+
+def test_top_hits_of_aligned_candidates():
+    """The candidate workload (U{1..64} windows per read) aligned on each
+    side: the GPU's top hits of its scores equal the oracle's of its own."""
+    import torch
+    from paper_1304_0681_gb300 import DeviceBatch, _swgb
+    from paper_1304_0681_gb300 import stage_e
+    wl = synth.generate("filter", seed=8, n_reads=250)
+    b = DeviceBatch.from_packed(wl.packed_reads(), wl.read_offsets, wl.packed_windows(), wl.window_offsets,
+                                pair_read=wl.pair_read, cigar=False)
+    _swgb.sw_batch_align_indexed(b.reads, b.read_offsets, b.n_reads, b.windows, b.window_offsets, b.pair_read,
+                                 b.n_pairs, DEFAULT, b.score, b.end, None)
+    co = torch.from_numpy(wl.cand_offsets).cuda()
+    top = stage_e.top_hits(b.score, co, wl.n_reads)
+    sub = wl.pair_slice(np.arange(wl.n_pairs))
+    res = oracle.align_batch(sub.reads, sub.read_offsets, sub.windows, sub.window_offsets,
+                             scoring=oracle.Scoring(*DEFAULT), cigar=False)
+    ref = np.array(se.top_hits(res["score"], wl.cand_offsets), np.int64).reshape(-1, 4)
+    for k, name in enumerate(("best_score", "best_cand", "second_score", "mapq")):
+        np.testing.assert_array_equal(top[name].cpu().numpy(), ref[:, k], err_msg=name)
+    # the top hit is mostly the true window, and a wrong top hit comes with
+    # a lower quality (a paralog decoy scores close to the true window)
+    right = ref[:, 1] == wl.true_cand
+    assert right.mean() > 0.8
+    assert ref[right, 3].mean() > 2 * ref[~right, 3].mean()

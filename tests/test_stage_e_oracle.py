@@ -128,3 +128,57 @@ def test_span_and_intron_position_with_other_gaps():
     assert oracle.cigar_string(ops) == f"25M3I25M{L}D50M"
     assert se.alignment_span(ops, ie, je) == (0, 20)
     assert se.pair_junctions(encode(w_i), ops, je, CHROM, POS, L) == [(CHROM, POS + 70, POS + 70 + L - 1, 0)]
+
+
+# Top hits and mapping quality.  Hand-derived rows: (scores, mask, expected
+# (best, candidate, second, quality)); quality = min(60, floor(60 (S1 - S2) / S1)).
+TOP_HITS_CASES = [
+    ([50], None, (50, 0, 0, 60)),                    # one candidate: no competitor
+    ([50, 50], None, (50, 0, 50, 0)),                # a tie: the first wins, quality 0
+    ([40, 100, 70], None, (100, 1, 70, 18)),         # 60 * 30 / 100
+    ([0, 0], None, (0, 0, 0, 0)),                    # nothing aligned: quality 0
+    ([], None, (-1, -1, -1, 0)),                     # no candidate
+    ([100, 90, 80], [0, 1, 1], (90, 1, 80, 6)),      # masked best; 600 / 90 = 6.67
+    ([100, 90], [0, 0], (-1, -1, -1, 0)),            # every candidate masked
+    ([3, 1], None, (3, 0, 1, 40)),
+    ([6, 7], None, (7, 1, 6, 8)),                    # 60 / 7 = 8.57
+    ([9, 3, 9, 9], None, (9, 0, 9, 0)),
+    ([12, 30, 29, 30], [1, 0, 1, 1], (30, 3, 29, 2)),  # 60 / 30 = 2
+]
+
+
+@pytest.mark.parametrize("scores,mask,expected", TOP_HITS_CASES)
+def test_top_hits_hand_cases(scores, mask, expected):
+    off = np.array([0, len(scores)], np.int64)
+    m = None if mask is None else np.array(mask, np.uint8)
+    assert se.top_hits(np.array(scores, np.int64), off, m) == [expected]
+
+
+def test_top_hits_against_sorting():
+    """Brute force by sorting: S1 and S2 are the two largest of the kept
+    scores, the candidate is the first index of S1 (numpy's argmax), and the
+    quality moves with the gap only."""
+    rng = np.random.default_rng(4)
+    counts = rng.integers(0, 9, 3000)
+    off = np.zeros(len(counts) + 1, np.int64)
+    np.cumsum(counts, out=off[1:])
+    score = rng.integers(0, 12, int(off[-1]))   # a narrow range: many ties
+    mask = (rng.random(int(off[-1])) < 0.7).astype(np.uint8)
+    for use_mask in (False, True):
+        got = se.top_hits(score, off, mask if use_mask else None)
+        for r in range(len(counts)):
+            idx = np.arange(off[r], off[r + 1])
+            if use_mask:
+                idx = idx[mask[idx] > 0]
+            if len(idx) == 0:
+                assert got[r] == (-1, -1, -1, 0)
+                continue
+            s = score[idx]
+            desc = np.sort(s)[::-1]
+            s1, s2 = int(desc[0]), int(desc[1]) if len(desc) > 1 else 0
+            c1 = int(idx[np.argmax(s)] - off[r])
+            assert got[r][:3] == (s1, c1, s2), r
+            q = got[r][3]
+            assert 0 <= q <= 60
+            assert (q == 0) == (s1 == 0 or s1 == s2 or 60 * (s1 - s2) < s1)
+            assert (q == 60) == (s1 > 0 and 60 * (s1 - s2) >= 60 * s1)
