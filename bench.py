@@ -293,6 +293,33 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
     e2.record(stream)
     e2.synchronize()
     recall = float(np.mean(best_filt == best_plain))
+    pipe = None
+    if not on_device:
+        # the same reads from pinned host memory in 8 batches, by 1, 2 and 3
+        # worker streams: copy in, features, network, selection, SW, top hits
+        n_b = 8
+        bnd = np.linspace(0, wl.n_reads, n_b + 1).astype(np.int64)
+        hb = []
+        for lo_, hi_ in zip(bnd[:-1], bnd[1:]):
+            sub = wl.read_slice(int(lo_), int(hi_))
+            hb.append(tuple(torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+                            for x in (sub.packed_reads(), sub.read_offsets, sub.packed_windows(), sub.window_offsets,
+                                      sub.pair_read, sub.cand_offsets)))
+        pipe = {"batches": n_b, "includes": "copies in and out, features, network, selection, SW on the selected "
+                                            "pairs, top hit and mapping quality per read; wall clock"}
+        for ns in (1, 2, 3):
+            flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns)  # warm each stream's scratch
+            torch.cuda.synchronize()
+            walls = []
+            for _ in range(steps):
+                t0 = time.perf_counter()
+                outs = flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns)
+                torch.cuda.synchronize()
+                walls.append(time.perf_counter() - t0)
+            wt = statistics.mean(walls)
+            pipe[f"streams_{ns}"] = {"ms": wt * 1e3, "reads_per_s": wl.n_reads / wt}
+        pipe["best_hit_recall"] = float(np.mean(np.concatenate([o.best_score for o in outs]) == best_plain))
+        del hb
     oracle_sw = None
     if not args.no_cpu_baseline and rank == 0 and args.gpus == 1:
         if on_device:   # the first reads of the same set, generated on the host
@@ -310,6 +337,7 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
                          "features_and_mlp_ms": e0.elapsed_time(e1), "select_align_best_ms": e1.elapsed_time(e2),
                          "gcups_aligned": sel_cells / (ms_filt * 1e-3) / 1e9},
             "speedup_reads_per_s": ms_plain / ms_filt, "best_hit_recall": recall, "k": k, "tau": tau,
+            "filtered_pipelined_from_host": pipe,
             "calibration_recall": cal[3] if cal else None,
             "training": {"pairs": n_train_pairs, "epochs": epochs, "loss_per_epoch": losses, "setup_s": setup_s},
             "steps": steps}

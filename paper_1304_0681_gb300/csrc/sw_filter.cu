@@ -588,12 +588,11 @@ static size_t grad_smem() { return (size_t)(64 * 256 + 64 * W2TS + 64 + 256 + 25
 int launch_mlp_forward(const float *model, const uint16_t *feat, int64_t n, float *out, int sm_count,
                        cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
-        if (cuda_failed(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)forward_smem())))
-            return SW_ERR_CUDA;
-        attr = true;
-    }
+    // per call: the attribute belongs to the current device, and calls may
+    // come from several host threads at once
+    if (cuda_failed(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)forward_smem())))
+        return SW_ERR_CUDA;
     int bps = 0;
     if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_mlp_forward, 128, forward_smem())))
         return SW_ERR_CUDA;
@@ -609,12 +608,11 @@ int launch_mlp_forward(const float *model, const uint16_t *feat, int64_t n, floa
 int launch_mlp_grad(float *model, const uint16_t *feat, const float *target, const int32_t *idx, int64_t n,
                     int sm_count, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
-        if (cuda_failed(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem())))
-            return SW_ERR_CUDA;
-        attr = true;
-    }
+    // per call: the attribute belongs to the current device, and calls may
+    // come from several host threads at once
+    if (cuda_failed(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)grad_smem())))
+        return SW_ERR_CUDA;
     if (cuda_failed(cudaMemsetAsync(model + MD_G, 0, sizeof(float) * MD_NP, st))) return SW_ERR_CUDA;
     // enough samples per block that the per-block gradient flush stays small
     const int64_t per_block = std::max<int64_t>(64, (n + sm_count - 1) / sm_count);

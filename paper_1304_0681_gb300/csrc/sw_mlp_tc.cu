@@ -292,12 +292,11 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
 int launch_mlp_forward_tc(const float *model, const uint16_t *feat, int64_t n, float *out, int sm_count,
                           int32_t *status, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
-        if (cuda_failed(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL)))
-            return SW_ERR_CUDA;
-        attr = true;
-    }
+    // per call: the attribute belongs to the current device, and calls may
+    // come from several host threads at once
+    if (cuda_failed(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SM_TOTAL)))
+        return SW_ERR_CUDA;
     static_assert(SM_USED <= SM_TOTAL, "shared memory layout");
     const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, sm_count));

@@ -146,6 +146,47 @@ def exhaustive_best(batch: DeviceBatch, cand_offsets: torch.Tensor, scoring):
     return best, cand
 
 
+@dataclass
+class FilterBatchResult:
+    best_score: np.ndarray   # per read, over the aligned candidates (-1: none)
+    best_cand: np.ndarray    # its index within the read's candidates
+    mapq: np.ndarray         # mapping quality of the top hit (sw_top_hits)
+    aligned_pairs: int
+
+
+def _filter_host_batch(model: FilterModel, batch, k: int, tau: float, scoring) -> FilterBatchResult:
+    """One host batch (packed reads, read offsets, packed windows, window
+    offsets, pair -> read, candidate offsets; pinned CPU tensors) through the
+    filtered search on the current stream, results copied back."""
+    from .stage_e import top_hits
+    dev = model.buf.device
+    reads, roff, wins, woff, pair_read, coff = (t.to(dev, non_blocking=True) for t in batch)
+    n_reads, n_pairs = roff.numel() - 1, woff.numel() - 1
+    b = DeviceBatch(reads, roff, wins, woff, pair_read, torch.empty(n_pairs, dtype=torch.int32, device=dev),
+                    torch.empty(2 * n_pairs, dtype=torch.int32, device=dev), None, None, None)
+    pred = model.forward(features(b, coff))
+    mask = torch.empty(n_pairs, dtype=torch.uint8, device=dev)
+    _swgb.sw_filter_select(pred, coff, n_reads, k, tau, mask)
+    _swgb.sw_batch_align_masked(b.reads, b.read_offsets, n_reads, b.windows, b.window_offsets, b.pair_read, mask,
+                                n_pairs, scoring, b.score, b.end, None)
+    top = top_hits(b.score, coff, n_reads, mask)
+    out = torch.cat([top["best_score"], top["best_cand"], top["mapq"],
+                     mask.sum(dtype=torch.int64).to(torch.int32).reshape(1)]).cpu().numpy()
+    return FilterBatchResult(out[:n_reads], out[n_reads:2 * n_reads], out[2 * n_reads:3 * n_reads],
+                             int(out[3 * n_reads]))
+
+
+def filtered_batches(model: FilterModel, batches, k: int, tau: float, scoring, n_streams: int = 2) -> list:
+    """The filtered search over a sequence of host batches (see
+    _filter_host_batch for their layout): copy in, features, network,
+    selection, SW on the selected pairs, top hits, copy out, with n_streams
+    batches in flight on their own streams.  One FilterBatchResult per
+    batch, in order."""
+    from .seed import run_on_worker_streams
+    return run_on_worker_streams(model.buf.device, list(batches),
+                                 lambda bt, s: _filter_host_batch(model, bt, k, tau, scoring), n_streams)
+
+
 def targets(score: torch.Tensor, read_len: torch.Tensor, match: int) -> torch.Tensor:
     """Training target of a pair: SW score / (match * read length)."""
     return score.to(torch.float32) / (float(match) * read_len.to(torch.float32))

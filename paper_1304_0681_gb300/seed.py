@@ -243,23 +243,18 @@ def _worker_streams(dev, n: int) -> list:
     return pool[:n]
 
 
-def map_batches(index: KmerIndex, batches, scoring, params: SeedParams | None = None, cigar: bool = True,
-                n_streams: int = 2) -> list:
-    """Map a sequence of host batches, each (packed reads, read offsets) as
-    pinned CPU tensors: copy in, seed, extract, align, best hit, copy the
-    best hits back.  With n_streams > 1, that many worker threads each drive
-    their own CUDA stream, so one batch's host round trips and kernel tails
-    overlap other batches' kernels (the library keeps separate scratch per
-    stream).  Returns one BatchResult per batch, in order."""
+def run_on_worker_streams(dev, items: list, fn, n_streams: int = 2) -> list:
+    """fn(item, stream) for every item, by n_streams worker threads that each
+    drive their own CUDA stream from a pool reused across calls (the library
+    keeps separate scratch per stream, so the workers' kernels and host
+    round trips overlap).  Returns the results in item order; the first
+    exception of any worker is raised after all have stopped."""
     import threading
 
-    batches = list(batches)
-    results = [None] * len(batches)
+    results = [None] * len(items)
     errors = []
-    dev = index.table.device
     next_item = [0]
     lock = threading.Lock()
-
     streams = _worker_streams(dev, max(n_streams, 1))
 
     def worker(w):
@@ -268,13 +263,12 @@ def map_batches(index: KmerIndex, batches, scoring, params: SeedParams | None = 
         with torch.cuda.stream(s):
             while True:
                 with lock:
-                    if errors or next_item[0] >= len(batches):
+                    if errors or next_item[0] >= len(items):
                         return
                     k = next_item[0]
                     next_item[0] += 1
                 try:
-                    packed, offsets = batches[k]
-                    results[k] = _map_host_batch(index, packed, offsets, scoring, params, cigar, s)
+                    results[k] = fn(items[k], s)
                 except BaseException as e:  # reported to the caller below
                     with lock:
                         errors.append(e)
@@ -291,3 +285,14 @@ def map_batches(index: KmerIndex, batches, scoring, params: SeedParams | None = 
     if errors:
         raise errors[0]
     return results
+
+
+def map_batches(index: KmerIndex, batches, scoring, params: SeedParams | None = None, cigar: bool = True,
+                n_streams: int = 2) -> list:
+    """Map a sequence of host batches, each (packed reads, read offsets) as
+    pinned CPU tensors: copy in, seed, extract, align, top hit, copy the
+    results back, with n_streams batches in flight on their own streams
+    (run_on_worker_streams).  Returns one BatchResult per batch, in order."""
+    return run_on_worker_streams(
+        index.table.device, list(batches),
+        lambda b, s: _map_host_batch(index, b[0], b[1], scoring, params, cigar, s), n_streams)

@@ -327,3 +327,41 @@ def test_fullmix_workload_full_size_sampled():
             assert best[r0 + r] == ref["score"][a:z].max()
             sel = mask[p0 + a:p0 + z] > 0
             assert sel.any() and fbest[r0 + r] == ref["score"][a:z][sel].max()
+
+
+def test_filtered_batches_pipelined():
+    """Host batches of the candidate workload (one of a single read) through
+    the filtered search on 1 and 3 worker streams: read for read the top hit,
+    its candidate and mapping quality of the single-call search over all
+    reads, and the same number of aligned pairs."""
+    import torch
+
+    from paper_1304_0681_gb300 import filter as flt
+    from paper_1304_0681_gb300 import stage_e
+    wl = synth.generate("filter", seed=12, n_reads=1200)
+    model = flt.FilterModel(seed=2)   # untrained: an arbitrary but fixed selection
+    torch.cuda.synchronize()
+    # tau = 0: no margin fallback (an untrained network's predictions lie too
+    # close together for any positive margin), so reads with more than k
+    # candidates align only k of them
+    k, tau = 3, 0.0
+    bounds = [0, 300, 301, 700, 1200]
+    batches = []
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        sub = wl.read_slice(a, b)
+        batches.append(tuple(torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+                             for x in (sub.packed_reads(), sub.read_offsets, sub.packed_windows(),
+                                       sub.window_offsets, sub.pair_read, sub.cand_offsets)))
+    whole = _batch(wl)
+    co = torch.from_numpy(wl.cand_offsets).cuda()
+    res = flt.filtered_best(whole, co, model, k, tau, SCORING)
+    top = stage_e.top_hits(whole.score, co, wl.n_reads, res.mask)
+    torch.cuda.synchronize()
+    want = {f: top[f].cpu().numpy() for f in ("best_score", "best_cand", "mapq")}
+    n_aligned = int(res.mask.sum().item())
+    assert 0 < n_aligned < wl.n_pairs
+    for ns in (1, 3):
+        out = flt.filtered_batches(model, batches, k, tau, SCORING, n_streams=ns)
+        for f in ("best_score", "best_cand", "mapq"):
+            np.testing.assert_array_equal(np.concatenate([getattr(o, f) for o in out]), want[f], err_msg=f)
+        assert sum(o.aligned_pairs for o in out) == n_aligned
