@@ -77,6 +77,9 @@ def test_forward_closed_forms():
     # negative pre-activations are cut by the ReLU
     P.b1[3] = -10.0
     np.testing.assert_array_equal(fo.forward(P, X)[0], np.zeros(5))
+    # the output layer is linear: a negative bias comes through
+    n = fo.Params(np.zeros((64, 256)), np.zeros(256), np.zeros((256, 64)), np.zeros(64), np.zeros(64), -0.25)
+    np.testing.assert_array_equal(fo.forward(n, X)[0], np.full(5, -0.25))
 
 
 def test_adam_first_step_is_lr_times_sign():
@@ -86,12 +89,17 @@ def test_adam_first_step_is_lr_times_sign():
 
 
 def test_bf16_round():
-    v = np.array([1.0, 1.0 + 2 ** -9, 1.0 + 3 * 2 ** -9, -2.5, 3.140625, 1e-40])
+    # bf16 keeps 7 fraction bits: next to 1.0 the spacing is 2^-7
+    v = np.array([1.0, 1.0 + 2 ** -9, 1.0 + 3 * 2 ** -9, -2.5, 3.140625, 1e-40,
+                  1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -(1.0 + 2 ** -8)])
     r = fo.bf16_round(v)
     assert r[0] == 1.0
-    assert r[1] == 1.0                   # halfway, ties to even
-    assert r[2] == 1.0 + 2 ** -7         # halfway, ties to even (up)
+    assert r[1] == 1.0                   # a quarter step: down
+    assert r[2] == 1.0 + 2 ** -7         # three quarters: up
     assert r[3] == -2.5 and r[4] == 3.140625
+    assert r[6] == 1.0                   # exactly halfway: ties to the even neighbour (down)
+    assert r[7] == 1.0 + 2 ** -6         # exactly halfway: the even neighbour is above
+    assert r[8] == -1.0
 
 
 def test_select_candidates():
@@ -105,3 +113,21 @@ def test_select_candidates():
     np.testing.assert_array_equal(sel, [True, False, True, False, False, True, True, False])
     best = fo.best_per_read(np.array([5, 9, 1, 2, 7, 3, 8, 0]), off, sel)
     np.testing.assert_array_equal(best, [5, 8])
+
+
+def test_select_candidates_edges():
+    """Exactly k candidates (all kept), a margin equal to tau (only a
+    smaller one falls back) and tied predictions (the lower index first);
+    predictions exact in fp32."""
+    off = np.array([0, 2, 5, 8])
+    pred = np.array([0.1, 0.7,            # read 0: two candidates, k = 2
+                     0.5, 0.25, 0.0,      # read 1: margin 0.25 between first and second
+                     0.5, 0.5, 0.5])      # read 2: three-way tie
+    sel = fo.select_candidates(pred, off, k=2, tau=0.0)
+    np.testing.assert_array_equal(sel[:2], [True, True])
+    np.testing.assert_array_equal(sel[5:], [True, True, False])
+    sel = fo.select_candidates(pred, off, k=1, tau=0.25)
+    np.testing.assert_array_equal(sel[2:5], [True, False, False])
+    np.testing.assert_array_equal(sel[5:], [True, True, True])   # margin 0 < tau: all
+    sel = fo.select_candidates(pred, off, k=1, tau=0.0)
+    np.testing.assert_array_equal(sel[5:], [True, False, False])
