@@ -81,3 +81,16 @@ def test_seeding_arguments_are_checked_before_any_device_work():
     assert lib.sw_gather_probe(10, 4, ctypes.byref(out), None) == -1
     assert lib.sw_gather_probe(32, 0, ctypes.byref(out), None) == -1
     assert lib.sw_gather_probe(32, 4, None, None) == -1
+
+
+def test_top_hits_arguments_are_checked_before_any_device_work():
+    """sw_top_hits: a negative read count or a missing required array is
+    SW_ERR_INVALID_ARG; an empty batch succeeds without touching a device."""
+    from paper_1304_0681_gb300 import _swgb
+    lib = _swgb._lib
+    assert lib.sw_top_hits(None, None, -1, None, None, None, None, None, None) == -1
+    assert lib.sw_top_hits(None, None, 0, None, None, None, None, None, None) == 0
+    for missing in range(3):   # score, cand_offsets, best_score
+        args = [1, 1, 5, None, 1, None, None, None, None]
+        args[(0, 1, 4)[missing]] = None
+        assert lib.sw_top_hits(*args) == -1, missing
