@@ -398,8 +398,9 @@ int sw_records(const int32_t *score, const int32_t *end, const sw_cigar_t *cigar
                int32_t min_score, sw_record_t *out_records, int64_t *out_count, sw_stream_t stream);
 
 /*
- * Top hits.  The SW task reports statistics of each alignment, "e.g. quality
- * score" (§2, Stage E), without defining one.  Per read r, over its
+ * Top hits.  Among the statistics the SW task reports for an alignment is a
+ * quality score, which the paper leaves undefined (§2, Stage E); it is read
+ * here as a mapping quality.  Per read r, over its
  * candidates p = cand_offsets[r] .. cand_offsets[r+1]-1 with pair_mask[p] != 0
  * (pair_mask may be NULL: all):
  *   best_score[r]   S1, the largest score

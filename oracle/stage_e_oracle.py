@@ -21,8 +21,8 @@ Readings (the paper gives no numbers or formats for these):
 - a junction is (chromosome, first intron base, last intron base, strand),
   all in reference coordinates; GT...AG gives strand '+' (0), CT...AC
   strand '-' (1); other marks are not junctions;
-- the alignment's "quality score" (listed among the SW task's statistics,
-  not defined) is read per read as a mapping quality: S1 the best score of
+- the alignment's quality score (one of the SW task's statistics, left
+  undefined) is read per read as a mapping quality: S1 the best score of
   its candidates (the first candidate reaching it is the top hit), S2 the
   best score of the other candidates (0 without one), and quality
   min(60, floor(60 (S1 - S2) / S1)), 0 when S1 <= 0.
