@@ -11,10 +11,10 @@ candidate is kept when the intron starts and ends with the marks GT ... AG
 or CT ... AC.  Junctions are counted over all batches.
 
 Readings (the paper gives no numbers or formats for these):
-- "above a given threshold" is read as score >= min_score, and score > 0
-  (an empty alignment is never a record);
-- "a large number of consecutive deletions" is a D run of at least
-  min_intron window bases;
+- the score threshold for a record is read as score >= min_score, and
+  score > 0 (an empty alignment is never a record);
+- a long run of consecutive deletions is a D run of at least min_intron
+  window bases;
 - a window's reference coordinates are given per window: chromosome, the
   position of its first base, and its strand; the alignment covers window
   columns j_start..j_end with j_start = j_end + 1 - (M + D bases);
