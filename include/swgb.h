@@ -251,6 +251,33 @@ int sw_best_per_read(const int32_t *score, const int64_t *cand_offsets, int64_t 
                      const uint8_t *pair_mask, int32_t *best_score, int32_t *best_cand, sw_stream_t stream);
 
 /*
+ * sw_filter_align -- the filtered search in one call: sw_filter_features,
+ * sw_mlp_forward, sw_filter_select (k, tau), sw_batch_align_masked (score
+ * and end; unselected pairs get score -1 and end (-1, -1)) and
+ * sw_best_per_read over the selected pairs.  Reads, windows and offsets as
+ * sw_batch_align_indexed; pair_read (device int64[n_pairs]) must agree with
+ * cand_offsets (pair p belongs to read r when cand_offsets[r] <= p <
+ * cand_offsets[r+1]).  pair_mask (device uint8[n_pairs]) receives the
+ * selection, or NULL: the library keeps it in its scratch.  best_score and
+ * best_cand: device int32[n_reads] (best_cand may be NULL).  Features and
+ * predictions live in library scratch of this stream (132 bytes per pair).
+ * A read count of 0 needs n_pairs == 0; with no pairs every read gets -1.
+ * Device-detected errors of every step (a timed-out tensor-core wait, an
+ * input the alignment rejects) are read with sw_sync_status.
+ */
+int sw_filter_align(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads, const uint8_t *windows,
+                    const int64_t *window_offsets, const int64_t *pair_read, const int64_t *cand_offsets,
+                    int64_t n_pairs, const float *model, int32_t k, float tau, const sw_scoring_t *scoring,
+                    int32_t *out_score, int32_t *out_end, uint8_t *pair_mask, int32_t *best_score,
+                    int32_t *best_cand, sw_stream_t stream);
+
+/* One training step: sw_mlp_grad over the n samples (idx may be NULL), then
+ * sw_mlp_adam with lr and step (from 1).  SW_ERR_INVALID_ARG for n < 1, a
+ * missing array, step < 1 or lr <= 0. */
+int sw_filter_train_step(float *model, const uint16_t *features, const float *target, const int32_t *idx, int64_t n,
+                         float lr, int32_t step, sw_stream_t stream);
+
+/*
  * Wait for `stream` and report problems the kernels of the last call on
  * `stream` detected on the device (SW_ERR_CAPACITY when a CIGAR slot
  * overflowed, SW_ERR_INTERNAL when a consistency check failed, ...).
@@ -266,6 +293,8 @@ int sw_best_per_read(const int32_t *score, const int64_t *cand_offsets, int64_t 
  * recent call; sw_phase_timing applies to every stream of the device.
  */
 int sw_sync_status(sw_stream_t stream);
+/* The same as sw_sync_status. */
+int sw_get_status(sw_stream_t stream);
 
 /*
  * Free the library's scratch of `stream` on the current device (after

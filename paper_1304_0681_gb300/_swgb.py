@@ -29,7 +29,7 @@ EXPORTS = ("sw_cigar_capacity", "sw_cigar_offsets", "sw_packed_bytes", "sw_batch
            "sw_plan_rows", "sw_alu_probe", "sw_phase_timing", "sw_phase_times", "sw_batch_align_noalloc",
            "sw_batch_align_masked", "sw_filter_features", "sw_mlp_bytes", "sw_mlp_init", "sw_mlp_refresh",
            "sw_mlp_forward", "sw_set_mlp_kernel", "sw_mlp_grad", "sw_mlp_adam", "sw_filter_select", "sw_best_per_read",
-           "sw_top_hits",
+           "sw_top_hits", "sw_filter_align", "sw_filter_train_step", "sw_get_status",
            # include/swgb_seed.h
            "sw_index_table_words", "sw_index_build", "sw_seed_windows", "sw_reads_two_strands",
            "sw_extract_windows", "sw_seed_stats", "sw_gather_probe")
@@ -113,6 +113,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_best_per_read.restype = ctypes.c_int
     lib.sw_top_hits.argtypes = [p, p, i64, p, p, p, p, p, p]
     lib.sw_top_hits.restype = ctypes.c_int
+    lib.sw_filter_align.argtypes = [p, p, i64, p, p, p, p, i64, p, i32, ctypes.c_float, ctypes.POINTER(Scoring),
+                                    p, p, p, p, p, p]
+    lib.sw_filter_align.restype = ctypes.c_int
+    lib.sw_filter_train_step.argtypes = [p, p, p, p, i64, ctypes.c_float, i32, p]
+    lib.sw_filter_train_step.restype = ctypes.c_int
+    lib.sw_get_status.argtypes = [p]
+    lib.sw_get_status.restype = ctypes.c_int
     lib.sw_cigar_offsets.argtypes = [p, p, i64, p, p]
     lib.sw_cigar_offsets.restype = ctypes.c_int
     lib.sw_stream_release.argtypes = [p]
@@ -330,6 +337,10 @@ def sw_sync_status(stream=None) -> None:
     _check(_lib.sw_sync_status(_stream(stream)), "sw_sync_status")
 
 
+def sw_get_status(stream=None) -> None:
+    _check(_lib.sw_get_status(_stream(stream)), "sw_get_status")
+
+
 def sw_strerror(code: int) -> str:
     return _lib.sw_strerror(int(code)).decode()
 
@@ -441,6 +452,21 @@ def sw_filter_select(pred, cand_offsets, n_reads: int, k: int, tau: float, pair_
 def sw_best_per_read(score, cand_offsets, n_reads: int, pair_mask, best_score, best_cand, stream=None) -> None:
     _check(_lib.sw_best_per_read(_ptr(score), _ptr(cand_offsets), int(n_reads), _ptr(pair_mask), _ptr(best_score),
                                  _ptr(best_cand), _stream(stream)), "sw_best_per_read")
+
+
+def sw_filter_align(reads, read_offsets, n_reads: int, windows, window_offsets, pair_read, cand_offsets,
+                    n_pairs: int, model, k: int, tau: float, scoring, out_score, out_end, pair_mask, best_score,
+                    best_cand, stream=None) -> None:
+    sc = _scoring(scoring)
+    _check(_lib.sw_filter_align(_ptr(reads), _ptr(read_offsets), int(n_reads), _ptr(windows), _ptr(window_offsets),
+                                _ptr(pair_read), _ptr(cand_offsets), int(n_pairs), _ptr(model), int(k),
+                                ctypes.c_float(tau), ctypes.byref(sc), _ptr(out_score), _ptr(out_end), _ptr(pair_mask),
+                                _ptr(best_score), _ptr(best_cand), _stream(stream)), "sw_filter_align")
+
+
+def sw_filter_train_step(model, features, target, idx, n: int, lr: float, step: int, stream=None) -> None:
+    _check(_lib.sw_filter_train_step(_ptr(model), _ptr(features), _ptr(target), _ptr(idx), int(n),
+                                     ctypes.c_float(lr), int(step), _stream(stream)), "sw_filter_train_step")
 
 
 def sw_top_hits(score, cand_offsets, n_reads: int, pair_mask, best_score, best_cand, second_score, mapq,

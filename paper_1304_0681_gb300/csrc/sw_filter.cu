@@ -549,6 +549,16 @@ __global__ void k_best_per_read(const int32_t *__restrict__ score, const int64_t
     }
 }
 
+// One thread: fold a status word into another (errors of one step of a
+// composite call stay visible through the status word of its last step).
+__global__ void k_or_status(int32_t *dst, const int32_t *src)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int32_t v = *src;
+        if (v) atomicOr(dst, v);
+    }
+}
+
 // ------------------------------------------------------------ launchers
 
 static int grid_for(int64_t items, int threads, int cap)
@@ -561,6 +571,13 @@ static int grid_for(int64_t items, int threads, int cap)
 int launch_features(const FeatureParams &P, cudaStream_t st)
 {
     k_features<<<grid_for(P.n_reads, 8, 152 * 16), 256, 0, st>>>(P);
+    count_launch();
+    return launch_status();
+}
+
+int launch_or_status(int32_t *dst, const int32_t *src, cudaStream_t st)
+{
+    k_or_status<<<1, 32, 0, st>>>(dst, src);
     count_launch();
     return launch_status();
 }
@@ -752,6 +769,62 @@ int sw_best_per_read(const int32_t *score, const int64_t *cand_offsets, int64_t 
     if (!score || !cand_offsets || !best_score) return SW_ERR_INVALID_ARG;
     return launch_best_per_read(score, cand_offsets, n_reads, pair_mask, best_score, best_cand,
                                 (cudaStream_t)stream);
+}
+
+int sw_filter_align(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads, const uint8_t *windows,
+                    const int64_t *window_offsets, const int64_t *pair_read, const int64_t *cand_offsets,
+                    int64_t n_pairs, const float *model, int32_t k, float tau, const sw_scoring_t *scoring,
+                    int32_t *out_score, int32_t *out_end, uint8_t *pair_mask, int32_t *best_score,
+                    int32_t *best_cand, sw_stream_t stream)
+{
+    if (n_reads < 0 || n_pairs < 0 || k < 1 || k > SW_FILTER_MAX_K) return SW_ERR_INVALID_ARG;
+    if (n_reads == 0) return n_pairs == 0 ? SW_OK : SW_ERR_INVALID_ARG;
+    if (!cand_offsets || !best_score) return SW_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_pairs == 0) {  // no candidates: every read gets -1, -1 (all bytes 0xFF)
+        if (cuda_failed(cudaMemsetAsync(best_score, 0xFF, sizeof(int32_t) * (size_t)n_reads, st))) return SW_ERR_CUDA;
+        if (best_cand && cuda_failed(cudaMemsetAsync(best_cand, 0xFF, sizeof(int32_t) * (size_t)n_reads, st)))
+            return SW_ERR_CUDA;
+        return SW_OK;
+    }
+    if (!reads || !read_offsets || !windows || !window_offsets || !pair_read || !model || !scoring || !out_score ||
+        !out_end)
+        return SW_ERR_INVALID_ARG;
+    // library scratch of this stream: bf16 features (16-byte rows for the
+    // tensor-core network), predictions, and the selection when the caller
+    // passes no mask
+    constexpr size_t kFeatures = 64;  // bf16 features per pair
+    const size_t fb = ((size_t)n_pairs * kFeatures * 2 + 255) / 256 * 256;
+    const size_t pb = ((size_t)n_pairs * 4 + 255) / 256 * 256;
+    uint8_t *scr = nullptr;
+    int rc = filter_scratch(st, fb + pb + (pair_mask ? 0 : (size_t)n_pairs), &scr);
+    if (rc) return rc;
+    uint16_t *feat = reinterpret_cast<uint16_t *>(scr);
+    float *pred = reinterpret_cast<float *>(scr + fb);
+    uint8_t *mask = pair_mask ? pair_mask : scr + fb + pb;
+    // the network's status word, cleared here whichever kernel runs it
+    int32_t *net_status = nullptr;
+    if ((rc = aux_status_word(st, &net_status))) return rc;
+    if ((rc = sw_filter_features(reads, read_offsets, n_reads, windows, window_offsets, cand_offsets, feat, stream)))
+        return rc;
+    if ((rc = sw_mlp_forward(model, feat, n_pairs, pred, stream))) return rc;
+    if ((rc = sw_filter_select(pred, cand_offsets, n_reads, k, tau, mask, stream))) return rc;
+    if ((rc = sw_batch_align_masked(reads, read_offsets, n_reads, windows, window_offsets, pair_read, mask, n_pairs,
+                                    scoring, out_score, out_end, nullptr, stream)))
+        return rc;
+    int32_t *align_status = nullptr;
+    if ((rc = stream_status_word(st, &align_status))) return rc;
+    if (align_status && align_status != net_status && (rc = launch_or_status(align_status, net_status, st)))
+        return rc;
+    return launch_best_per_read(out_score, cand_offsets, n_reads, mask, best_score, best_cand, st);
+}
+
+int sw_filter_train_step(float *model, const uint16_t *features, const float *target, const int32_t *idx, int64_t n,
+                         float lr, int32_t step, sw_stream_t stream)
+{
+    if (n < 1 || !model || !features || !target || step < 1 || !(lr > 0.f)) return SW_ERR_INVALID_ARG;
+    const int rc = sw_mlp_grad(model, features, target, idx, n, stream);
+    return rc ? rc : sw_mlp_adam(model, lr, step, stream);
 }
 
 }  // extern "C"

@@ -84,6 +84,7 @@ struct DeviceState {
     int64_t tb_split[2] = {0, 0};    // pairs per traceback kernel (16-bit, 32-bit) of the last call
     size_t tile16_budget = 0;        // 16-bit traceback tile budget (set at the first traceback)
     Buffer misc;                     // Stage E task iv: status word and record scan scratch
+    Buffer filt;                     // sw_filter_align: features, predictions, selection
     int64_t *seed_stats_host = nullptr;  // pinned: counters of the stream's last sw_seed_windows
     cudaEvent_t phase[4] = {nullptr, nullptr, nullptr, nullptr};
     // independent launches (length classes, traceback parts) fork onto these
@@ -190,7 +191,7 @@ int device_state(DeviceState **out, cudaStream_t st)
 
 void free_state(DeviceState *s)
 {
-    for (Buffer *b : {&s->fixed, &s->dyn, &s->stage, &s->misc})
+    for (Buffer *b : {&s->fixed, &s->dyn, &s->stage, &s->misc, &s->filt})
         if (b->ptr) {
             cudaFree(b->ptr);
             b->ptr = nullptr;
@@ -1081,6 +1082,8 @@ int sw_sync_status(sw_stream_t stream)
     return read_status(ds, (cudaStream_t)stream);
 }
 
+int sw_get_status(sw_stream_t stream) { return sw_sync_status(stream); }
+
 const char *sw_strerror(int code)
 {
     switch (code) {
@@ -1351,6 +1354,28 @@ int aux_status_word(cudaStream_t st, int32_t **status)
     *status = (int32_t *)ds->misc.ptr;
     if (cuda_failed(cudaMemsetAsync(*status, 0, sizeof(int32_t), st))) return SW_ERR_CUDA;
     ds->last_status = *status;
+    return SW_OK;
+}
+// Scratch of sw_filter_align on this stream (grown on demand).
+int filter_scratch(cudaStream_t st, size_t bytes, uint8_t **ptr)
+{
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds, st);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    if ((rc = ensure(ds->filt, bytes))) return rc;
+    *ptr = (uint8_t *)ds->filt.ptr;
+    return SW_OK;
+}
+
+// The status word sw_sync_status will read for this stream's last call.
+int stream_status_word(cudaStream_t st, int32_t **status)
+{
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds, st);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    *status = ds->last_status;
     return SW_OK;
 }
 }  // namespace swgb

@@ -183,6 +183,9 @@ int launch_mlp_forward_tc(const float *model, const uint16_t *feat, int64_t n, f
 // A device status word for calls outside the alignment path: cleared on
 // `st`, and the word sw_sync_status reads until the next call sets another.
 int aux_status_word(cudaStream_t st, int32_t **status);
+int filter_scratch(cudaStream_t st, size_t bytes, uint8_t **ptr);
+int stream_status_word(cudaStream_t st, int32_t **status);
+int launch_or_status(int32_t *dst, const int32_t *src, cudaStream_t st);
 
 // Layout of the filter's model buffer (floats): parameters, Adam moments,
 // gradient, step, then bf16 copies of W1 and W2 transposed (K-major).

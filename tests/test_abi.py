@@ -94,3 +94,29 @@ def test_top_hits_arguments_are_checked_before_any_device_work():
         args = [1, 1, 5, None, 1, None, None, None, None]
         args[(0, 1, 4)[missing]] = None
         assert lib.sw_top_hits(*args) == -1, missing
+
+
+def test_filter_entry_points_check_arguments_before_any_device_work():
+    """sw_filter_align and sw_filter_train_step reject bad counts, k outside
+    1..SW_FILTER_MAX_K and missing arrays before touching a device."""
+    import ctypes
+
+    from paper_1304_0681_gb300 import _swgb
+    lib = _swgb._lib
+    sc = ctypes.byref(_swgb.Scoring(5, -4, -10, -1))
+    f = ctypes.c_float
+
+    def align(n_reads, n_pairs, k=3, cand=1, model=1, best=1):
+        return lib.sw_filter_align(1, 1, n_reads, 1, 1, 1, cand, n_pairs, model, k, f(0.0), sc, 1, 1, None, best,
+                                   None, None)
+    assert align(-1, 0) == -1
+    assert align(2, 5, k=0) == -1 and align(2, 5, k=17) == -1
+    assert align(0, 0) == 0
+    assert align(0, 5) == -1
+    assert align(3, 5, cand=None) == -1 and align(3, 5, best=None) == -1
+    assert align(3, 5, model=None) == -1
+    step = lib.sw_filter_train_step
+    assert step(1, 1, 1, None, 0, f(1e-3), 1, None) == -1
+    assert step(1, 1, 1, None, 8, f(1e-3), 0, None) == -1
+    assert step(1, 1, 1, None, 8, f(0.0), 1, None) == -1
+    assert step(None, 1, 1, None, 8, f(1e-3), 1, None) == -1

@@ -365,3 +365,65 @@ def test_filtered_batches_pipelined():
         for f in ("best_score", "best_cand", "mapq"):
             np.testing.assert_array_equal(np.concatenate([getattr(o, f) for o in out]), want[f], err_msg=f)
         assert sum(o.aligned_pairs for o in out) == n_aligned
+
+
+def test_filter_align_in_one_call():
+    """sw_filter_align gives the selection, scores, end cells and best hits
+    of the step-by-step filtered search (features, network, selection,
+    masked SW, best hit), with the caller's mask and with the library's."""
+    import torch
+
+    from paper_1304_0681_gb300 import _swgb
+    from paper_1304_0681_gb300 import filter as flt
+    wl = synth.generate("filter", seed=14, n_reads=600)
+    model = flt.FilterModel(seed=6)
+    k, tau = 3, 0.0
+    co = torch.from_numpy(wl.cand_offsets).cuda()
+    b = _batch(wl)
+    res = flt.filtered_best(b, co, model, k, tau, SCORING)
+    torch.cuda.synchronize()
+    assert 0 < int(res.mask.sum().item()) < wl.n_pairs
+    for own_mask in (True, False):
+        b2 = _batch(wl)
+        mask = torch.full((wl.n_pairs,), 7, dtype=torch.uint8, device="cuda") if own_mask else None
+        best = torch.full((wl.n_reads,), -7, dtype=torch.int32, device="cuda")
+        cand = torch.full_like(best, -7)
+        _swgb.sw_filter_align(b2.reads, b2.read_offsets, wl.n_reads, b2.windows, b2.window_offsets, b2.pair_read, co,
+                              wl.n_pairs, model.buf, k, tau, SCORING, b2.score, b2.end, mask, best, cand)
+        _swgb.sw_get_status()
+        assert torch.equal(b2.score, b.score) and torch.equal(b2.end, b.end)
+        assert torch.equal(best, res.best_score) and torch.equal(cand, res.best_cand)
+        if own_mask:
+            assert torch.equal(mask, res.mask)
+    # no candidates at all: every read gets -1, -1
+    zero = torch.zeros(4, dtype=torch.int64, device="cuda")
+    best = torch.full((3,), 5, dtype=torch.int32, device="cuda")
+    cand = torch.full_like(best, 5)
+    _swgb.sw_filter_align(b.reads, b.read_offsets, 3, b.windows, b.window_offsets, b.pair_read, zero, 0, model.buf,
+                          k, tau, SCORING, b.score, b.end, None, best, cand)
+    torch.cuda.synchronize()
+    assert (best == -1).all() and (cand == -1).all()
+
+
+def test_filter_train_step_in_one_call():
+    """sw_filter_train_step leaves the model buffer (parameters, moments,
+    gradient, serving copies) bit for bit as sw_mlp_grad then sw_mlp_adam.
+    60 samples fit one block of the gradient kernel, so its float sums run in
+    one fixed order (several blocks add their shares with atomics)."""
+    import torch
+
+    from paper_1304_0681_gb300 import _swgb
+    from paper_1304_0681_gb300 import filter as flt
+    wl = synth.generate("filter", seed=15, n_reads=60)
+    b = _batch(wl)
+    feats = flt.features(b, torch.from_numpy(wl.cand_offsets).cuda())
+    tgt = torch.rand(wl.n_pairs, generator=torch.Generator().manual_seed(3)).cuda()
+    assert wl.n_pairs >= 180
+    idx = torch.arange(0, 180, 3, dtype=torch.int32, device="cuda")
+    m1, m2 = flt.FilterModel(seed=9), flt.FilterModel(seed=9)
+    for step in (1, 2):
+        m1.grad(feats, tgt, idx)
+        m1.adam(1e-3)
+        _swgb.sw_filter_train_step(m2.buf, feats, tgt, idx, idx.numel(), 1e-3, step)
+    torch.cuda.synchronize()
+    assert m1.step == 2 and torch.equal(m1.buf, m2.buf)
