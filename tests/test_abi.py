@@ -120,3 +120,33 @@ def test_filter_entry_points_check_arguments_before_any_device_work():
     assert step(1, 1, 1, None, 8, f(1e-3), 0, None) == -1
     assert step(1, 1, 1, None, 8, f(0.0), 1, None) == -1
     assert step(None, 1, 1, None, 8, f(1e-3), 1, None) == -1
+
+
+def test_headers_are_plain_c_and_link(tmp_path):
+    """Both headers compile as strict C99 with warnings as errors, and a C
+    program links against the library and calls its host-only entry points
+    (no device needed)."""
+    import os
+
+    from paper_1304_0681_gb300 import _swgb
+    lib = os.path.abspath(_swgb.LIB_PATH)
+    src = tmp_path / "abi_check.c"
+    src.write_text(
+        '#include "swgb.h"\n#include "swgb_seed.h"\n#include <stdio.h>\n'
+        "int main(void) {\n"
+        "    sw_scoring_t sc = {5, -4, -10, -1};\n"
+        "    sw_seed_params_t sp = {15, 12, 7, 64, 30, 20, 30, 2000, 16384};\n"
+        "    (void)sc; (void)sp;\n"
+        "    if (sw_cigar_capacity(100) < 203) return 1;\n"
+        "    if (sw_index_table_words(15) != (int64_t)1 << 30) return 2;\n"
+        "    if (sw_top_hits(0, 0, -1, 0, 0, 0, 0, 0, 0) != SW_ERR_INVALID_ARG) return 3;\n"
+        '    printf("%s\\n", sw_strerror(SW_ERR_CAPACITY));\n'
+        "    return 0;\n"
+        "}\n")
+    exe = tmp_path / "abi_check"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc, str(src), "-o", str(exe),
+                    lib, "-Wl,-rpath," + os.path.dirname(lib)], check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert out.stdout.strip() == _swgb.sw_strerror(-2)
