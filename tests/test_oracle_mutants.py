@@ -39,6 +39,12 @@ MUTANTS = {
                                         "if (E[i * ld + j] == H[i * ld + j - 1] + go && j == 1) state = 0;"),
     "trailing clip off by one": ("m - 1 - i_end0", "m - i_end0"),
     "I and D swapped": ("rev[nrev++] = (uint8_t)OP_D;", "rev[nrev++] = (uint8_t)OP_I;"),
+    # the bounds behind the rectangle and band tracebacks
+    "deletion bound one short": ("return num < 0 ? 0 : num / (-ge) + 1;", "return num < 0 ? 0 : num / (-ge);"),
+    "band one diagonal short of the deletions": ("const int64_t dlo = dmax < 0 ? -(i_end + 1) - 1 : dend - dmax;",
+                                                 "const int64_t dlo = dmax < 0 ? -(i_end + 1) - 1 : dend - dmax + 1;"),
+    "band one diagonal short of the insertions": ("const int64_t dhi = dend + imax;",
+                                                  "const int64_t dhi = dend + imax - 1;"),
 }
 
 
@@ -85,6 +91,26 @@ def run_pins(lib) -> list:
                     break
     except Exception:
         failed.append("rescore(crash)")
+    try:
+        # rectangle and band against the full matrix: the golden rows (one
+        # of them an exact split read, whose single deletion run makes the
+        # deletion bound tight) and tie-heavy random pairs
+        cases = [(encode(row["read"]), encode(row["window"]), oracle.Scoring(*row["scoring"]))
+                 for row in load_golden("sw_worked_examples.txt")]
+        for t in range(150):
+            cases.append((rng.integers(0, 2, rng.integers(1, 40)).astype(np.uint8),
+                          rng.integers(0, 2, rng.integers(1, 60)).astype(np.uint8), scorings[t % 3]))
+        for r, w, sc in cases:
+            s, ie, je, ops = oracle.align(r, w, sc, lib=lib)
+            if s <= 0:
+                continue
+            band = oracle.band_traceback(r, w, s, ie, je, sc, lib=lib)
+            rect, _ = oracle.rect_traceback(r, w, s, ie, je, sc, lib=lib)
+            if not (np.array_equal(band, ops) and np.array_equal(rect, ops)):
+                failed.append("band-rectangle")
+                break
+    except Exception:
+        failed.append("band-rectangle(crash)")
     return failed
 
 
