@@ -88,6 +88,60 @@ def test_adam_first_step_is_lr_times_sign():
     np.testing.assert_allclose(th, -0.01 * np.sign(g), rtol=1e-4)
 
 
+def _adam_run(grads, lr=0.01):
+    th = np.zeros(len(grads[0]))
+    m, v = np.zeros_like(th), np.zeros_like(th)
+    out = []
+    for t, g in enumerate(grads, start=1):
+        th, m, v = fo.adam_step(th, np.asarray(g, dtype=np.float64), m, v, t, lr)
+        out.append((th.copy(), m.copy(), v.copy()))
+    return out
+
+
+def test_adam_constant_gradient_steps_lr_times_sign():
+    """Kingma & Ba (2015), Algorithm 1, with g_t = g for every t: the moment
+    recursions sum geometric series, m_t = (1 - b1^t) g and v_t = (1 - b2^t)
+    g^2, so the bias-corrected estimates are exactly g and g^2 at every step
+    and each step moves theta by lr * g / (|g| + eps) ~ lr * sign(g)."""
+    g = np.array([0.5, -2.0, 3.0])
+    for t, (th, m, v) in enumerate(_adam_run([g] * 4), start=1):
+        np.testing.assert_allclose(m, (1 - 0.9 ** t) * g, rtol=1e-12)
+        np.testing.assert_allclose(v, (1 - 0.999 ** t) * g * g, rtol=1e-12)
+        np.testing.assert_allclose(th, -0.01 * t * np.sign(g), rtol=1e-6)
+
+
+def test_adam_alternating_gradient_shows_the_carry_over():
+    """g, -g, g: by hand from Algorithm 1 (b1 = 0.9, b2 = 0.999).
+    Step 2: m_2 = 0.9 * 0.1 g - 0.1 g = -0.01 g, m_2 / (1 - 0.81) = -g / 19;
+    v_2 = (1 - b2^2) g^2, so v_2 / (1 - b2^2) = g^2.  The step is -lr * (-g/19)
+    / |g| = +lr sign(g) / 19.
+    Step 3: m_3 = 0.9 * (-0.01 g) + 0.1 g = 0.091 g, over 1 - 0.729 = 0.271
+    gives 91 g / 271; v_3 / (1 - b2^3) = g^2.  The step is -lr * 91/271 sign(g).
+    A dropped carry-over (m_t = 0.1 g_t) would give -lr sign(g) * 0.1/0.19 at
+    step 2."""
+    g = np.array([0.25, -4.0])
+    runs = _adam_run([g, -g, g])
+    s = np.sign(g)
+    np.testing.assert_allclose(runs[0][0], -0.01 * s, rtol=1e-6)
+    np.testing.assert_allclose(runs[1][1], -0.01 * g, rtol=1e-12)
+    np.testing.assert_allclose(runs[1][0], -0.01 * s + 0.01 * s / 19, rtol=1e-6)
+    np.testing.assert_allclose(runs[2][1], 0.091 * g, rtol=1e-12)
+    np.testing.assert_allclose(runs[2][0], -0.01 * s + 0.01 * s / 19 - 0.01 * s * 91 / 271, rtol=1e-6)
+
+
+def test_adam_changing_magnitude():
+    """g_1 = 1, g_2 = 3 (one parameter), by hand: m_2 = 0.1 (0.9 * 1 + 3) =
+    0.39, bias-corrected 0.39 / 0.19 = 39/19; v_2 = 0.001 (0.999 * 1 + 9) =
+    0.009999, bias-corrected 0.009999 / 0.001999 = 9999/1999.  Step 2 moves
+    theta by -lr (39/19) / sqrt(9999/1999)."""
+    runs = _adam_run([[1.0], [3.0]])
+    th2, m2, v2 = runs[1]
+    np.testing.assert_allclose(m2, [0.39], rtol=1e-12)
+    np.testing.assert_allclose(v2, [0.009999], rtol=1e-12)
+    step2 = -0.01 * (39 / 19) / np.sqrt(9999 / 1999)
+    np.testing.assert_allclose(th2, [-0.01 + step2], rtol=1e-7)
+
+
 def test_bf16_round():
     # bf16 keeps 7 fraction bits: next to 1.0 the spacing is 2^-7
     v = np.array([1.0, 1.0 + 2 ** -9, 1.0 + 3 * 2 ** -9, -2.5, 3.140625, 1e-40,

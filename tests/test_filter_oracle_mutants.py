@@ -27,6 +27,9 @@ MUTANTS = {
     # Adam
     "adam_no_bias_correction": ("mh = m / (1 - beta1 ** step)", "mh = m"),
     "adam_no_sqrt": ("np.sqrt(vh) + eps", "vh + eps"),
+    "adam_no_momentum_carry": ("m = beta1 * m + (1 - beta1) * grad", "m = (1 - beta1) * grad"),
+    "adam_beta1_in_v": ("v = beta2 * v + (1 - beta2) * grad * grad", "v = beta1 * v + (1 - beta2) * grad * grad"),
+    "adam_no_v_carry": ("v = beta2 * v + (1 - beta2) * grad * grad", "v = (1 - beta2) * grad * grad"),
     # bf16
     "bf16_truncates": ("u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000", "u = u & 0xFFFF0000"),
     "bf16_ties_up": ("u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000", "u = (u + 0x8000) & 0xFFFF0000"),
