@@ -326,8 +326,9 @@ int sw_last_cuda_error(const char **name);
  * bases (else SW_ERR_UNSUPPORTED, detected on the device).  Arguments,
  * layouts, scoring requirements and outputs are those of sw_batch_align.
  *
- * The first call on a device looks up the array's device address, so make it
- * before any other work that must not be interrupted by that set-up.  Every
+ * Each call looks up the array's device address on the current device (no
+ * allocation).  The first call on a device may also load the library's device
+ * code there: make it before any stream capture.  Every
  * call on a device uses the same array (it keeps the previous call's
  * contents; the call clears what must start at zero), so calls whose GPU
  * work overlaps -- on different streams or from different threads -- race;
@@ -507,6 +508,19 @@ int sw_set_plan(int32_t max_read_len, int32_t lanes, int32_t r_rows);
 #define SW_TB_AUTO 0
 #define SW_TB_INT32 1
 int sw_set_traceback_mode(int32_t mode);
+
+/*
+ * Score-pass arithmetic.  SW_SCORE_AUTO (the default) gives each pair the
+ * narrowest exact mode its score bound match x min(m, n) allows: two pairs
+ * per lane in 16-bit halves up to 32000, 32-bit lanes above.  SW_SCORE_INT32
+ * runs every pair in 32-bit lanes (and so, with a CIGAR, through the 32-bit
+ * traceback kernels).  Both give the same scores, end cells and CIGARs.
+ * Returns SW_ERR_INVALID_ARG for any other value.  Process-wide; applies to
+ * calls made after it, and a plan keeps the setting it was created under.
+ */
+#define SW_SCORE_AUTO 0
+#define SW_SCORE_INT32 1
+int sw_set_score_mode(int32_t mode);
 
 /*
  * Pairs the most recent sw_batch_align* call with a CIGAR on the current

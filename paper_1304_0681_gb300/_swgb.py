@@ -22,7 +22,7 @@ ERRORS = {
 
 #: every symbol include/swgb.h declares
 EXPORTS = ("sw_cigar_capacity", "sw_cigar_offsets", "sw_packed_bytes", "sw_batch_align", "sw_stream_release", "sw_last_cuda_error", "sw_batch_align_indexed",
-           "sw_batch_align_host", "sw_sync_status", "sw_strerror", "sw_launch_count", "sw_set_plan", "sw_set_traceback_mode",
+           "sw_batch_align_host", "sw_sync_status", "sw_strerror", "sw_launch_count", "sw_set_plan", "sw_set_traceback_mode", "sw_set_score_mode",
            "sw_last_traceback_split", "sw_plan_create", "sw_plan_align", "sw_plan_status", "sw_plan_destroy",
            "sw_batch_align_host_dense", "sw_records", "sw_junction_table_words", "sw_junction_table_clear", "sw_junctions_detect",
            "sw_junctions_export",
@@ -151,6 +151,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_set_plan.restype = ctypes.c_int
     lib.sw_set_traceback_mode.argtypes = [i32]
     lib.sw_set_traceback_mode.restype = ctypes.c_int
+    lib.sw_set_score_mode.argtypes = [i32]
+    lib.sw_set_score_mode.restype = ctypes.c_int
     lib.sw_last_traceback_split.argtypes = [ctypes.c_void_p]
     lib.sw_last_traceback_split.restype = ctypes.c_int
     lib.sw_plan_create.argtypes = [p, i64, p, p, i64, ctypes.POINTER(Scoring), i32, p, ctypes.POINTER(ctypes.c_void_p)]
@@ -359,6 +361,14 @@ SW_TB_INT32 = 1
 
 def sw_set_traceback_mode(mode: int) -> None:
     _check(_lib.sw_set_traceback_mode(int(mode)), "sw_set_traceback_mode")
+
+
+SW_SCORE_AUTO = 0
+SW_SCORE_INT32 = 1
+
+
+def sw_set_score_mode(mode: int) -> None:
+    _check(_lib.sw_set_score_mode(int(mode)), "sw_set_score_mode")
 
 
 def sw_last_traceback_split() -> tuple:

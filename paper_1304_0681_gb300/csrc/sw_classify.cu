@@ -10,7 +10,7 @@
 
 namespace swgb {
 
-__global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring sc,
+__global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring sc, bool force_i32,
                            int32_t *__restrict__ keys, int32_t *__restrict__ hist, ClassInfo *__restrict__ info,
                            int32_t *__restrict__ out_score, int32_t *__restrict__ out_end,
                            int32_t *__restrict__ cig_n)
@@ -50,7 +50,8 @@ __global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring
             } else {
                 const int64_t hmax = (int64_t)sc.ma * (m < n ? m : n);
                 int mode = MODE_I32;
-                if (hmax <= 1022) mode = MODE_I16;  // (H << 5) | 31 fits 15 bits
+                if (force_i32) mode = MODE_I32;
+                else if (hmax <= 1022) mode = MODE_I16;  // (H << 5) | 31 fits 15 bits
                 else if (hmax <= 32000) mode = MODE_I16W;
                 cls = mode * N_MCLASS + mclass_of((int32_t)m);
                 int nb = (int)((n - 1) >> 5);
@@ -153,7 +154,7 @@ int launch_check_counts(const ClassInfo *info, const int32_t *expect, int32_t *s
     return launch_status();
 }
 
-int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring sc,
+int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring sc, bool force_i32,
                     int32_t *keys, int32_t *hist, int32_t *bucket_start, int32_t *cursor,
                     ClassInfo *info, int32_t *order, int32_t *out_score, int32_t *out_end,
                     int32_t *cig_n, cudaStream_t st)
@@ -162,7 +163,7 @@ int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring
     int64_t blocks = (n_pairs + threads - 1) / threads;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_classify<<<(unsigned)blocks, threads, 0, st>>>(ps, n_reads, n_pairs, sc, keys, hist, info, out_score,
+    k_classify<<<(unsigned)blocks, threads, 0, st>>>(ps, n_reads, n_pairs, sc, force_i32, keys, hist, info, out_score,
                                                      out_end, cig_n);
     k_scan<<<N_CLASS, N_NBUCKET, 0, st>>>(hist, info->count, bucket_start, cursor);
     k_scatter<<<(unsigned)blocks, threads, 0, st>>>(keys, n_pairs, cursor, order);

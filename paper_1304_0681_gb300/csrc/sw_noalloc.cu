@@ -9,7 +9,6 @@
 // order -- lives in one file-scope device array of fixed size instead of in
 // library-allocated buffers.
 #include <algorithm>
-#include <mutex>
 
 #include "sw_device.cuh"
 #include "swgb_internal.h"
@@ -22,10 +21,6 @@ constexpr int kNaHeader = 64;
 static __device__ __align__(256) int32_t g_sw_noalloc_scratch[kNaHeader + SW_NOALLOC_MAX_PAIRS];
 
 namespace {
-
-constexpr int kNaMaxDevices = 64;
-int32_t *g_na_ptr[kNaMaxDevices];  // device address of the array, per device
-std::mutex g_na_mu;
 
 // Validation and identity order.  Pairs with an empty window simply run as
 // all-padding columns in the score kernel and come out with score 0.
@@ -64,28 +59,32 @@ extern "C" int sw_batch_align_noalloc(const uint8_t *reads, const int64_t *read_
     if (!reads || !read_offsets || !windows || !window_offsets || !out_score || !out_end) return SW_ERR_INVALID_ARG;
     if (((uintptr_t)reads & 15u) || ((uintptr_t)windows & 15u)) return SW_ERR_INVALID_ARG;
 
-    int dev = 0;
-    if (cuda_failed(cudaGetDevice(&dev)) || dev < 0 || dev >= kNaMaxDevices) return SW_ERR_NO_DEVICE;
+    int dev = 0, sms = 0;
+    if (cuda_failed(cudaGetDevice(&dev))) return SW_ERR_NO_DEVICE;
+    if (cuda_failed(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) || sms < 1)
+        return SW_ERR_CUDA;
+    // The array's device address on the current device.  In host code the
+    // array's name is only a host-side stand-in, so the address is looked up
+    // with the device current.  The first call on a device also loads the
+    // library's device code there (set-up: make it before any stream
+    // capture).  The lookup allocates nothing and is cheap once the code is
+    // loaded, so it is repeated on every call: after a device reset the code
+    // is loaded again at another address, and a cached pointer would be stale.
     int32_t *scratch = nullptr;
     {
-        // first call on this device: look up the array's device address
-        std::lock_guard<std::mutex> lk(g_na_mu);
-        if (!g_na_ptr[dev]) {
-            void *ptr = nullptr;
-            if (cuda_failed(cudaGetSymbolAddress(&ptr, g_sw_noalloc_scratch)) || !ptr) {
-                cudaGetLastError();
-                return SW_ERR_CUDA;
-            }
-            g_na_ptr[dev] = (int32_t *)ptr;
+        void *ptr = nullptr;
+        if (cuda_failed(cudaGetSymbolAddress(&ptr, g_sw_noalloc_scratch)) || !ptr) {
+            cudaGetLastError();
+            return SW_ERR_CUDA;
         }
-        scratch = g_na_ptr[dev];
+        scratch = (int32_t *)ptr;
     }
     cudaStream_t st = (cudaStream_t)stream;
     const PairSet ps{(const uint32_t *)reads, read_offsets, nullptr, (const uint32_t *)windows, window_offsets};
 
     // the array keeps the previous call's contents: clear counter, status, max
     if (cuda_failed(cudaMemsetAsync(scratch, 0, kNaHeader * sizeof(int32_t), st))) return SW_ERR_CUDA;
-    const int64_t pblocks = std::min<int64_t>((n_pairs + 255) / 256, 152 * 8);
+    const int64_t pblocks = std::min<int64_t>((n_pairs + 255) / 256, (int64_t)sms * 8);
     k_noalloc_prepare<<<(unsigned)pblocks, 256, 0, st>>>(ps, n_pairs, scratch);
     count_launch();
     if (cuda_failed(cudaGetLastError())) return SW_ERR_CUDA;
@@ -111,9 +110,8 @@ extern "C" int sw_batch_align_noalloc(const uint8_t *reads, const int64_t *read_
     L.boundary_group_bytes = 0;
     L.work_counter = scratch;
     L.status = scratch + 1;
-    int regs = 0, bps = 0, sms = 0;
+    int regs = 0, bps = 0;
     if (score_kernel_regs(rows, MODE_I32, &regs, &bps, 128) != SW_OK || bps < 1) return SW_ERR_INTERNAL;
-    if (cuda_failed(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return SW_ERR_CUDA;
     const int64_t groups = 32 / lanes;
     const int64_t warps = (n_pairs + groups - 1) / groups;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((warps + 3) / 4, (int64_t)bps * sms));

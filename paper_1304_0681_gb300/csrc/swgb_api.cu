@@ -22,6 +22,7 @@ namespace swgb {
 
 static std::atomic<int64_t> g_launches{0};
 static std::atomic<int32_t> g_tb_mode{SW_TB_AUTO};
+static std::atomic<int32_t> g_score_mode{SW_SCORE_AUTO};
 void count_launch(int n) { g_launches += n; }
 
 thread_local int g_cuda_error = 0;
@@ -323,7 +324,8 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
     if (cuda_failed(cudaMemsetAsync(hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
     if (cuda_failed(cudaMemsetAsync(info, 0, sizeof(ClassInfo), st))) return SW_ERR_CUDA;
     if (cuda_failed(cudaMemsetAsync(counters, 0, sizeof(int32_t) * 4 * N_CLASS, st))) return SW_ERR_CUDA;
-    if ((rc = launch_classify(ps, n_reads, n_pairs, sc, keys, hist, bstart, cursor, info, order, out_score,
+    if ((rc = launch_classify(ps, n_reads, n_pairs, sc, g_score_mode.load() == SW_SCORE_INT32, keys, hist, bstart,
+                              cursor, info, order, out_score,
                               out_end, cig ? cig->n_ops : nullptr, st)))
         return rc;
     if (cuda_failed(cudaMemcpyAsync(ds->info_host, info, sizeof(ClassInfo), cudaMemcpyDeviceToHost, st)))
@@ -640,6 +642,7 @@ struct sw_plan {
     int64_t n_reads = 0, n_pairs = 0;
     swgb::Scoring sc{};
     bool cigar = false;
+    bool force_i32 = false;   // the score mode setting at creation
     swgb::Buffer fixed, dyn;  // owned: a captured graph keeps pointing here
     int32_t *keys = nullptr, *order = nullptr, *hist = nullptr, *bstart = nullptr, *cursor = nullptr;
     int32_t *counters = nullptr, *tb_keys = nullptr, *tb_order = nullptr, *expect = nullptr;
@@ -690,7 +693,8 @@ int plan_build(sw_plan *pl, DeviceState *ds, cudaStream_t st)
     int32_t *tmp_score = pl->tb_keys, *tmp_end = nullptr;  // empty-window outputs go to scratch
     if ((rc = ensure(pl->dyn, sizeof(int32_t) * 2 * std::max<int64_t>(n_pairs, 1)))) return rc;
     tmp_end = (int32_t *)pl->dyn.ptr;
-    if ((rc = launch_classify(pl->ps, pl->n_reads, n_pairs, pl->sc, pl->keys, pl->hist, pl->bstart, pl->cursor,
+    if ((rc = launch_classify(pl->ps, pl->n_reads, n_pairs, pl->sc, pl->force_i32, pl->keys, pl->hist, pl->bstart,
+                              pl->cursor,
                               pl->info, pl->order, tmp_score, tmp_end, nullptr, st)))
         return rc;
     ClassInfo ci;
@@ -813,7 +817,8 @@ int plan_execute(sw_plan *pl, int32_t *out_score, int32_t *out_end, const sw_cig
     if (cuda_failed(cudaMemsetAsync(pl->hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
     if (cuda_failed(cudaMemsetAsync(pl->info, 0, sizeof(ClassInfo), st))) return SW_ERR_CUDA;
     if (cuda_failed(cudaMemsetAsync(pl->counters, 0, sizeof(int32_t) * 4 * N_CLASS, st))) return SW_ERR_CUDA;
-    if ((rc = launch_classify(ps, pl->n_reads, pl->n_pairs, pl->sc, pl->keys, pl->hist, pl->bstart, pl->cursor,
+    if ((rc = launch_classify(ps, pl->n_reads, pl->n_pairs, pl->sc, pl->force_i32, pl->keys, pl->hist, pl->bstart,
+                              pl->cursor,
                               pl->info, pl->order, out_score, out_end, cig ? cig->n_ops : nullptr, st)))
         return rc;
     if ((rc = launch_check_counts(pl->info, pl->expect, &pl->info->status, st))) return rc;
@@ -1127,6 +1132,13 @@ int sw_set_traceback_mode(int32_t mode)
     return SW_OK;
 }
 
+int sw_set_score_mode(int32_t mode)
+{
+    if (mode != SW_SCORE_AUTO && mode != SW_SCORE_INT32) return SW_ERR_INVALID_ARG;
+    g_score_mode.store(mode);
+    return SW_OK;
+}
+
 int sw_plan_rows(int32_t *rows, int32_t cap)
 {
     if (!rows) return N_SCORE_ROWS;
@@ -1217,6 +1229,7 @@ int sw_plan_create(const int64_t *read_offsets, int64_t n_reads, const int64_t *
     pl->n_pairs = n_pairs;
     pl->sc = Scoring{scoring->match, scoring->mismatch, scoring->gap_open, scoring->gap_extend};
     pl->cigar = with_cigar != 0;
+    pl->force_i32 = g_score_mode.load() == SW_SCORE_INT32;
     {
         std::lock_guard<std::mutex> lk(ds->mu);
         rc = plan_build(pl, ds, (cudaStream_t)stream);

@@ -127,7 +127,9 @@ constexpr int N_SCORE_ROWS = 6;
 extern const int kScoreRows[N_SCORE_ROWS];
 constexpr int TB_ROWS = 8;
 
-int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring sc,
+// force_i32: every pair takes the int32 score mode (else the narrowest
+// mode its score bound allows)
+int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring sc, bool force_i32,
                     int32_t *keys, int32_t *hist, int32_t *bucket_start, int32_t *cursor,
                     ClassInfo *info, int32_t *order, int32_t *out_score, int32_t *out_end,
                     int32_t *cig_n, cudaStream_t st);

@@ -45,6 +45,36 @@ def test_parity_workload_other_scorings(scoring):
     assert_parity(wl, got, scoring)
 
 
+def test_parity_workload_int32_score_kernel():
+    """The 1,000-pair parity workload (100-bp reads, 150-bp windows) through
+    the int32 score kernel: every pair in 32-bit lanes, so with a CIGAR every
+    pair also takes the 32-bit traceback.  Score, end cell and CIGAR of each
+    pair against the oracle, bit-exact."""
+    import paper_1304_0681_gb300 as sw
+    wl = synth.generate("parity")
+    sw.sw_set_score_mode(sw.SW_SCORE_INT32)
+    try:
+        got = run_gpu(wl, DEFAULT)
+        s16, s32 = sw.sw_last_traceback_split()
+    finally:
+        sw.sw_set_score_mode(sw.SW_SCORE_AUTO)
+    assert (s16, s32) == (0, wl.n_pairs)
+    assert_parity(wl, got, DEFAULT)
+    # and score and end alone (no traceback kernels behind the score pass)
+    sw.sw_set_score_mode(sw.SW_SCORE_INT32)
+    try:
+        got = run_gpu(wl, DEFAULT, cigar=False)
+    finally:
+        sw.sw_set_score_mode(sw.SW_SCORE_AUTO)
+    assert_parity(wl, got, DEFAULT, cigar=False)
+
+
+def test_score_mode_setting_rejects_other_values():
+    import paper_1304_0681_gb300 as sw
+    with pytest.raises(sw.SwError):
+        sw.sw_set_score_mode(2)
+
+
 def test_traceback_kernel_split(request):
     """The default mode sends every pair of the 100/150-bp workload through
     the 16-bit traceback; the int32 mode sends none."""

@@ -3,15 +3,17 @@ library allocate device memory (their memory belongs to their own pool, or
 cudaMalloc's device synchronisation is unacceptable to them).  It keeps its
 scratch in a fixed static device array, so the test checks that two calls in
 a row -- the second one inheriting the first one's leftover scratch contents
--- each give exactly what sw_batch_align gives for the same batch (scores and
-end cells are integers: the tolerance is zero), and that sizes beyond the
-array's limits are refused with a clear error.
+-- each give exactly what sw_batch_align gives for the same batch, and what
+the CPU oracle gives (scores and end cells are integers: the tolerance is
+zero), and that sizes beyond the array's limits are refused with a clear
+error.
 
 This file is collected last so that a run stopping at the first failure has
 already run every other test."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -59,7 +61,13 @@ def _mixed(seed, n):
     return wl
 
 
-def test_two_calls_match_sw_batch_align():
+def _oracle(wl):
+    o = oracle.align_batch(wl.reads, wl.read_offsets, wl.windows, wl.window_offsets,
+                           scoring=oracle.Scoring(*SCORING), cigar=False)
+    return o["score"], np.stack([o["i_end"], o["j_end"]], axis=1).ravel()
+
+
+def test_two_calls_match_sw_batch_align_and_the_oracle():
     first = _mixed(1, 3000)
     second = synth.generate("parity", seed=9, n_reads=700)  # smaller batch after a larger one
     for wl in (first, second):
@@ -67,6 +75,9 @@ def test_two_calls_match_sw_batch_align():
         got_s, got_e = _noalloc(wl)
         np.testing.assert_array_equal(got_s, ref_s)
         np.testing.assert_array_equal(got_e, ref_e)
+        orc_s, orc_e = _oracle(wl)
+        np.testing.assert_array_equal(got_s, orc_s)
+        np.testing.assert_array_equal(got_e, orc_e)
     assert (ref_s > 0).all()
 
 
