@@ -1,16 +1,27 @@
 #!/usr/bin/env python
 """Benchmark of the batched Smith-Waterman hot path (one JSON line).
 
-A step aligns one whole batch -- classification, score pass and traceback to
-CIGAR -- through the C ABI with the inputs already resident in device memory.
-Default workload: 1,000,000 (read, window) pairs, reads 100 bp, windows 200 bp,
-2% substitutions + 0.5% indels, 20% random decoy windows (2.0e10 DP cells).
+Headline (default): the full-mix workload -- 10M reads of 75-800 bp, each
+with U{1..32} candidate windows (about 165M (read, window) pairs, 1.2e13 DP
+cells, 15% spliced), generated on the GPU.  A step is one learned-filtered
+search over the whole batch through the C ABI (sw_filter_align: 4-mer
+features, the bf16 network on the tensor cores, top-k / fallback selection,
+Smith-Waterman score and end cell of the selected pairs, best hit per read)
+with the inputs resident in device memory; `value` is reads/s.  Beside it:
+the plain exhaustive search of the same batch (every candidate aligned), the
+best-hit recall of the filtered search against it, the roofline of the score
+kernel, an end-to-end figure from pinned host memory, and the CPU oracle.
+
+A compact summary of the other workloads -- the 1M-pair throughput batch
+(score + end + CIGAR, GCUPS), the 2M-pair uneven batch, the 500k-read filter
+workload, small-batch graph replay, and seeding -- is printed last.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload fullmix|throughput|uneven]
 
-Under torchrun (N > 1) every rank aligns its own batch of the same size
+Under torchrun (N > 1) every rank searches its own batch of the same size
 (weak scaling, no collective on the data path); the reported value is the
-cells of all ranks over the slowest rank's time.
+reads of all ranks over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -30,6 +41,9 @@ sys.path.insert(0, ROOT)
 METRIC = "SW GCUPS & reads/s, plain vs learned-filtered at ≥99.5% best-hit recall"
 SCORING = (5, -4, -10, -1)
 WORKLOADS = {
+    "fullmix": "full mix: 10M reads of 75-800 bp as the uneven workload, U{1..32} candidate windows per read "
+               "(about 165M pairs), 15% spliced, true hit at 1-5% divergence, the rest 5-20% or random; "
+               "learned-filtered vs exhaustive best hit per read, score + end; generated on the GPU",
     "throughput": "plain SW, 1M pairs: reads 100 bp, windows 200 bp (2% subst, 0.5% indels 1-3 bp), "
                   "20% random decoys; score + end + CIGAR",
     "uneven": "batched uneven SW, 2M pairs: reads 75-800 bp, windows read + 2 x U(20,100) flanks, "
@@ -48,7 +62,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="throughput")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="fullmix",
+                    help="headline workload: fullmix (filtered reads/s) or a plain-SW batch (GCUPS)")
     ap.add_argument("--no-cigar", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -58,6 +73,8 @@ def _args():
     ap.add_argument("--no-filter", action="store_true", help="skip the learned-filter comparison")
     ap.add_argument("--filter-reads", type=int, default=500_000)
     ap.add_argument("--fullmix-reads", type=int, default=10_000_000, help="reads of the full-mix workload")
+    ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain exhaustive arm")
+    ap.add_argument("--e2e-batches", type=int, default=8, help="host batches of the full-mix end-to-end leg")
     ap.add_argument("--no-extra", action="store_true", help="skip the uneven and full-mix sections")
     ap.add_argument("--no-seeding", action="store_true", help="skip the seeding section")
     ap.add_argument("--only-seeding", action="store_true", help="run the seeding section alone")
@@ -205,6 +222,50 @@ FILTER_WORKLOADS = {
 }
 
 
+def _train_filter(name: str, rank: int, n_train: int, n_cal: int, epochs: int):
+    """The filter network trained on the GPU by the library's own forward,
+    backward and Adam kernels, on SW scores the method itself computes for
+    the pairs of another seed of the workload; then (k, tau) picked on a
+    held-out seed for >= 99.6% best-hit recall.  Not timed as part of a
+    step.  Returns (model, k, tau, facts)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1304_0681_gb300 import DeviceBatch
+    from paper_1304_0681_gb300 import filter as flt
+
+    def load(seed, n_reads):
+        wl = synth.generate(name, seed=seed, n_reads=n_reads)
+        b = DeviceBatch.from_packed(wl.packed_reads(), wl.read_offsets, wl.packed_windows(), wl.window_offsets,
+                                    pair_read=wl.pair_read, cigar=False)
+        return wl, b, torch.from_numpy(wl.cand_offsets).cuda()
+
+    t0 = time.perf_counter()
+    wl_tr, b_tr, co_tr = load(1000 + rank, n_train)
+    flt.exhaustive_best(b_tr, co_tr, SCORING)
+    feats_tr = flt.features(b_tr, co_tr)
+    tgt = flt.targets(b_tr.score, torch.from_numpy(wl_tr.pair_read_lengths).cuda(), SCORING[0])
+    model = flt.FilterModel(seed=1)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    losses = model.train(feats_tr, tgt, epochs=epochs, batch=8192, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    n_train_pairs = wl_tr.n_pairs
+    del b_tr, feats_tr, tgt
+    wl_cal, b_cal, co_cal = load(2000 + rank, n_cal)
+    flt.exhaustive_best(b_cal, co_cal, SCORING)
+    pred_cal = model.forward(flt.features(b_cal, co_cal)).cpu().numpy()
+    cal = flt.calibrate(pred_cal, b_cal.score.cpu().numpy().astype(np.int64), wl_cal.cand_offsets, 0.996)
+    k, tau = (cal[0], cal[1]) if cal else (8, 1.0)  # no setting reached the recall: align every candidate
+    del b_cal
+    facts = {"pairs": n_train_pairs, "epochs": epochs, "loss_per_epoch": losses,
+             "train_s": train_s, "train_pairs_per_s": n_train_pairs * epochs / max(train_s, 1e-9),
+             "setup_s": time.perf_counter() - t0, "calibration": cal}
+    return model, k, tau, facts
+
+
 def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int = 500_000,
                     n_train: int = 150_000, n_cal: int = 40_000, epochs: int = 4, on_device: bool = False) -> dict:
     """Plain vs learned-filtered best-hit search on a candidate workload
@@ -229,24 +290,8 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
                                     pair_read=wl.pair_read, cigar=False)
         return wl, b, torch.from_numpy(wl.cand_offsets).cuda()
 
-    # training set: SW scores from the method itself are the targets
-    t0 = time.perf_counter()
-    wl_tr, b_tr, co_tr = load(name, 1000 + rank, n_train)
-    flt.exhaustive_best(b_tr, co_tr, SCORING)
-    feats_tr = flt.features(b_tr, co_tr)
-    tgt = flt.targets(b_tr.score, torch.from_numpy(wl_tr.pair_read_lengths).cuda(), SCORING[0])
-    model = flt.FilterModel(seed=1)
-    losses = model.train(feats_tr, tgt, epochs=epochs, batch=8192, lr=2e-3)
-    n_train_pairs = wl_tr.n_pairs
-    del b_tr, feats_tr, tgt
-    # calibration on a held-out seed
-    wl_cal, b_cal, co_cal = load(name, 2000 + rank, n_cal)
-    flt.exhaustive_best(b_cal, co_cal, SCORING)
-    pred_cal = model.forward(flt.features(b_cal, co_cal)).cpu().numpy()
-    cal = flt.calibrate(pred_cal, b_cal.score.cpu().numpy().astype(np.int64), wl_cal.cand_offsets, 0.996)
-    k, tau = (cal[0], cal[1]) if cal else (8, 1.0)  # no setting reached the recall: align every candidate
-    del b_cal
-    setup_s = time.perf_counter() - t0
+    model, k, tau, training = _train_filter(name, rank, n_train, n_cal, epochs)
+    cal = training["calibration"]
 
     if on_device:
         wl = synth.generate_device(name, seed=rank, n_reads=n_reads)
@@ -338,9 +383,7 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
                          "gcups_aligned": sel_cells / (ms_filt * 1e-3) / 1e9},
             "speedup_reads_per_s": ms_plain / ms_filt, "best_hit_recall": recall, "k": k, "tau": tau,
             "filtered_pipelined_from_host": pipe,
-            "calibration_recall": cal[3] if cal else None,
-            "training": {"pairs": n_train_pairs, "epochs": epochs, "loss_per_epoch": losses, "setup_s": setup_s},
-            "steps": steps}
+            "calibration_recall": cal[3] if cal else None, "training": training, "steps": steps}
 
 
 def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
@@ -707,18 +750,495 @@ def run_mlp_only(args) -> None:
     print(json.dumps({"section": "filter network forward", "rows": n, "flop_per_row": flops // n, **res}), flush=True)
 
 
+class _OracleReads:
+    """The oracle, as it stands, on the host cores: the exhaustive best hit
+    (every candidate aligned, score and end cell) of reads of a candidate
+    workload, generated on the host (every read depends only on the seed and
+    its index, so the first n_host reads are those of the full set)."""
+
+    def __init__(self, name: str, seed: int, n_host: int):
+        import synth
+        self.wl = synth.generate(name, seed=seed, n_reads=n_host)
+        self.cores = os.cpu_count() or 1
+
+    def run(self, ids) -> dict:
+        import numpy as np
+
+        import oracle
+        wl, co = self.wl, self.wl.cand_offsets
+        pairs = np.concatenate([np.arange(co[r], co[r + 1]) for r in ids])
+        sub = wl.pair_slice(pairs)
+        t = time.perf_counter()
+        res = oracle.align_batch(sub.reads, sub.read_offsets, sub.windows, sub.window_offsets,
+                                 scoring=oracle.Scoring(*SCORING), cigar=False, threads=self.cores)
+        counts = co[np.asarray(ids) + 1] - co[np.asarray(ids)]
+        starts = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+        best = np.maximum.reduceat(res["score"], starts)
+        return {"seconds": time.perf_counter() - t, "reads": len(ids), "pairs": len(pairs), "cells": sub.cells(),
+                "best": best}
+
+    def sized(self, budget_s: float, rng=None) -> dict:
+        """A sample of about budget_s seconds: evenly spaced reads, or drawn
+        with rng."""
+        import numpy as np
+        n_all = self.wl.n_reads
+        probe = self.run(np.linspace(0, n_all - 1, 8 * self.cores).astype(np.int64))
+        n = int(min(n_all, max(8 * self.cores, budget_s * probe["reads"] / max(probe["seconds"], 1e-6))))
+        ids = (np.sort(rng.choice(n_all, n, replace=False)) if rng is not None
+               else np.linspace(0, n_all - 1, n).astype(np.int64))
+        return self.run(ids)
+
+
+def _oracle_reads(name: str, rank: int, budget_s: float, n_host: int = 200_000) -> dict:
+    """cpu_baseline of a candidate workload: the oracle's reads/s over a
+    bounded sample of about budget_s seconds of CPU work."""
+    o = _OracleReads(name, rank, n_host)
+    r = o.sized(budget_s)
+    return {"value": r["reads"] / r["seconds"], "unit": "reads/s", "cores": o.cores, "kind": "oracle",
+            "sample": f"{r['reads']} reads evenly spaced over the first {n_host} of the set (host-generated), "
+                      f"every candidate aligned ({r['pairs']} pairs, {r['cells']:.3e} cells, score + end, best "
+                      f"per read) in {r['seconds']:.1f} s", "gcups": r["cells"] / r["seconds"] / 1e9}
+
+
+def _fullmix_headline(args, rank: int, ws: int, pg, peak: dict, local: int) -> dict:
+    """The headline: the learned-filtered search vs the plain exhaustive
+    search over the full-mix workload, both on the GPU, through the C ABI.
+    The filtered arm is timed over exactly `steps` steps after `warmup`
+    untimed ones (the batch, about 12 GB of packed windows, is larger than
+    L2); the plain arm over --plain-steps steps."""
+    import numpy as np
+    import torch
+
+    import paper_1304_0681_gb300 as sw
+    import synth
+    from paper_1304_0681_gb300 import _swgb
+    from paper_1304_0681_gb300 import filter as flt
+    from paper_1304_0681_gb300.shard import reduce_run
+
+    name = "fullmix"
+    model, k, tau, training = _train_filter(name, rank, n_train=40_000, n_cal=15_000, epochs=8)
+    t0 = time.perf_counter()
+    wl = synth.generate_device(name, seed=rank, n_reads=args.fullmix_reads)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    n_reads, n_pairs = wl.n_reads, wl.n_pairs
+    dev = wl.reads.device
+    i32 = dict(dtype=torch.int32, device=dev)
+    score, end = torch.empty(n_pairs, **i32), torch.empty(2 * n_pairs, **i32)
+    mask = torch.empty(n_pairs, dtype=torch.uint8, device=dev)
+    best, cand = torch.empty(n_reads, **i32), torch.empty(n_reads, **i32)
+    best_p, cand_p = torch.empty(n_reads, **i32), torch.empty(n_reads, **i32)
+    pair_cells = (wl.window_offsets[1:] - wl.window_offsets[:-1]) * wl.pair_read_lengths
+    cells = int(pair_cells.sum().item())
+    stream = torch.cuda.current_stream()
+
+    def filtered():
+        _swgb.sw_filter_align(wl.reads, wl.read_offsets, n_reads, wl.windows, wl.window_offsets, wl.pair_read,
+                              wl.cand_offsets, n_pairs, model.buf, k, tau, SCORING, score, end, mask, best, cand)
+
+    def plain():
+        _swgb.sw_batch_align_indexed(wl.reads, wl.read_offsets, n_reads, wl.windows, wl.window_offsets,
+                                     wl.pair_read, n_pairs, SCORING, score, end, None)
+        _swgb.sw_best_per_read(score, wl.cand_offsets, n_reads, None, best_p, cand_p)
+
+    def run_timed(fn, n_steps, phases=None):
+        ms = []
+        for _ in range(n_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            if phases is not None:
+                phases.append(sw.sw_phase_times())
+        return ms
+
+    # plain arm first (its scores are the recall reference), then the filtered arm
+    plain()
+    torch.cuda.synchronize()
+    sw.sw_sync_status()
+    ms_plain = run_timed(plain, max(1, args.plain_steps))
+    sw.sw_sync_status()
+    best_plain = best_p.cpu().numpy()
+
+    for _ in range(args.warmup):
+        filtered()
+    torch.cuda.synchronize()
+    sw.sw_sync_status()
+    sw.sw_phase_timing(True)
+    clocks = Clocks(local)
+    launches0 = sw.sw_launch_count()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    phases = []
+    ms_filt = run_timed(filtered, args.steps, phases)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = sw.sw_launch_count() - launches0
+    sw.sw_sync_status()
+    sw.sw_phase_timing(False)
+    best_filt = best.cpu().numpy()
+    recall = float(np.mean(best_filt == best_plain))
+    m = mask.bool()
+    aligned = int(m.sum().item())
+    sel_cells = int(pair_cells[m].sum().item())
+
+    # phases of one filtered step: features + network (CUDA events around
+    # the same kernels), then the masked alignment's own phase events
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    feats = torch.empty((n_pairs, 64), dtype=torch.int16, device=dev)
+    _swgb.sw_filter_features(wl.reads, wl.read_offsets, n_reads, wl.windows, wl.window_offsets, wl.cand_offsets,
+                             feats)
+    e1.record(stream)
+    e1.synchronize()
+    feat_ms = e0.elapsed_time(e1)
+    pred = torch.empty(n_pairs, dtype=torch.float32, device=dev)
+    e0.record(stream)
+    _swgb.sw_mlp_forward(model.buf, feats, n_pairs, pred)
+    e1.record(stream)
+    e1.synchronize()
+    mlp_ms = e0.elapsed_time(e1)
+    del feats, pred
+    torch.cuda.empty_cache()
+
+    all_reads, total_s = reduce_run(n_reads * args.steps, sum(ms_filt) * 1e-3)
+    t_filt = statistics.mean(ms_filt)
+    t_plain = statistics.mean(ms_plain)
+    ph = {"classify": statistics.mean(p[0] for p in phases), "score": statistics.mean(p[1] for p in phases),
+          "traceback": statistics.mean(p[2] for p in phases)}
+    achieved = sel_cells / (ph["score"] * 1e-3) / 1e9
+    feat_bytes = _feature_bytes(wl)
+    out = {"value": all_reads / total_s, "ms_per_step": total_s * 1e3 / args.steps, "clocks": clk,
+           "gpu_launches": int(launches),
+           "config": {"workload": WORKLOADS[name], "reads_per_gpu": n_reads, "pairs_per_gpu": n_pairs,
+                      "cells_exhaustive_per_gpu": cells, "k": k, "tau": tau, "scoring": list(SCORING),
+                      "api": "sw_filter_align (features, network, selection, SW score + end, best per read)",
+                      "l2": "inputs larger than L2 (about 12 GB of packed windows per step)",
+                      "generated_on_gpu_s": gen_s},
+           "filtered": {"ms_per_step": t_filt, "reads_per_s": n_reads / (t_filt * 1e-3), "aligned_pairs": aligned,
+                        "aligned_share": aligned / n_pairs, "aligned_cells": sel_cells,
+                        "gcups_of_aligned_cells": sel_cells / (t_filt * 1e-3) / 1e9,
+                        "phase_ms": {"features": feat_ms, "network": mlp_ms, **{f"sw_{a}": b for a, b in ph.items()}}},
+           "plain": {"ms_per_step": t_plain, "reads_per_s": n_reads / (t_plain * 1e-3),
+                     "gcups": cells / (t_plain * 1e-3) / 1e9, "steps": len(ms_plain),
+                     "api": "sw_batch_align_indexed + sw_best_per_read"},
+           "speedup_reads_per_s": t_plain / t_filt, "best_hit_recall": recall,
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak["gcups"], "unit": "GCUPS",
+                        "frac": achieved / peak["gcups"], "traffic": None,
+                        "kernel": "k_score on the selected pairs (score + end cell), all of a step's launches",
+                        "peak_basis": peak["basis"], "frac_of_mix_peak": achieved / peak["mix_gcups"],
+                        "mix_peak": peak["mix_gcups"], "mix_peak_basis": peak["mix_basis"]},
+           "features_roofline": {"bound": "hbm", "kernel": "k_features", "achieved": feat_bytes / (feat_ms * 1e-3) / 1e9,
+                                 "peak": peak["hbm_gbs"], "unit": "GB/s",
+                                 "frac": feat_bytes / (feat_ms * 1e-3) / 1e9 / peak["hbm_gbs"],
+                                 "algorithmic_bytes": feat_bytes,
+                                 "per_unit": "packed read and window bytes of each pair + 128 B of bf16 features"},
+           "training": {key: training[key] for key in ("pairs", "epochs", "train_s", "train_pairs_per_s")}}
+
+    # end to end: the same reads from pinned host memory in batches, through
+    # filter.filtered_batches (copy in, features, network, selection, SW,
+    # top hit with mapping quality, copy out) on worker streams
+    if not args.no_e2e:
+        n_b = max(1, args.e2e_batches)
+        bnd = np.linspace(0, n_reads, n_b + 1).astype(np.int64)
+        hb, h2d = [], 0
+        for lo_, hi_ in zip(bnd[:-1], bnd[1:]):
+            sub = synth.generate_device(name, seed=rank, n_reads=int(hi_ - lo_), first_read=int(lo_))
+            parts = []
+            for t in (sub.reads, sub.read_offsets, sub.windows, sub.window_offsets, sub.pair_read, sub.cand_offsets):
+                h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+                h.copy_(t)
+                parts.append(h)
+                h2d += h.numel() * h.element_size()
+            hb.append(tuple(parts))
+            del sub
+        torch.cuda.empty_cache()
+        ns = max(1, args.e2e_streams)
+        outs = flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns)  # each stream's scratch
+        torch.cuda.synchronize()
+        reps = max(2, min(args.steps, 3))
+        walls = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            outs = flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns)
+            torch.cuda.synchronize()
+            walls.append(time.perf_counter() - t0)
+        e2e_reads, e2e_s = reduce_run(n_reads, statistics.mean(walls))
+        got = np.concatenate([o.best_score for o in outs])
+        out["e2e"] = {"value": e2e_reads / e2e_s, "unit": "reads/s", "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(n_reads * 12 + 4 * n_b),
+                      "api": "filter.filtered_batches (pinned host batches in, top hit + mapping quality out)",
+                      "batches": n_b, "streams": ns, "steps": reps,
+                      "best_hit_recall": float(np.mean(got == best_plain))}
+        del hb
+    if not args.no_cpu_baseline and rank == 0 and ws == 1:
+        out["cpu_baseline"] = _oracle_reads(name, rank, args.cpu_seconds)
+    del wl
+    torch.cuda.empty_cache()
+    return out
+
+
+def _feature_bytes(wl) -> int:
+    """Algorithmic bytes of the feature kernel over a device workload: the
+    packed read of each pair, the packed window, and the 64 bf16 features
+    written."""
+    rl = (wl.read_offsets[1:] - wl.read_offsets[:-1])
+    read_bytes = int(((rl[wl.pair_read] + 3) // 4).sum().item())
+    win_bytes = int((((wl.window_offsets[1:] - wl.window_offsets[:-1]) + 3) // 4).sum().item())
+    return read_bytes + win_bytes + 128 * wl.n_pairs
+
+
+def _throughput_section(args, rank: int, ws: int, pg, peak: dict, local: int, workload: str = "throughput",
+                        headline: bool = False) -> dict:
+    """Plain SW with CIGARs on one batch (default: the 1M-pair throughput
+    batch, 100 x 200 bp, 20% decoys): classification, score pass and
+    traceback to CIGAR in one sw_batch_align call per step, L2 flushed
+    between steps; GCUPS.  With headline, exactly --steps steps after
+    --warmup, clocks sampled; else a few steps."""
+    import numpy as np
+    import torch
+
+    import paper_1304_0681_gb300 as sw
+    import synth
+    from paper_1304_0681_gb300 import DeviceBatch, align
+    from paper_1304_0681_gb300.shard import reduce_run
+
+    want_cigar = not args.no_cigar
+    wl = synth.generate(workload, seed=rank, n_reads=args.pairs)
+    batch = DeviceBatch.from_packed(wl.packed_reads(), wl.read_offsets, wl.packed_windows(), wl.window_offsets,
+                                    cigar=want_cigar)
+    cells, n_reads = wl.cells(), wl.n_reads
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    steps = args.steps if headline else max(3, min(args.steps, 10))
+    warmup = args.warmup if headline else 3
+    for _ in range(warmup):
+        align(batch, SCORING, cigar=want_cigar)
+    torch.cuda.synchronize()
+
+    sw.sw_phase_timing(True)
+    clocks = Clocks(local)
+    launches0 = sw.sw_launch_count()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms, phases = [], []
+    for _ in range(steps):
+        flush.zero_()  # write > L2 so every step starts cold
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        align(batch, SCORING, cigar=want_cigar, sync=False)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        phases.append(sw.sw_phase_times())
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = sw.sw_launch_count() - launches0
+    sw.sw_sync_status()
+    sw.sw_phase_timing(False)
+    all_cells, total_s = reduce_run(cells * steps, sum(step_ms) * 1e-3)
+    all_reads, _ = reduce_run(n_reads * steps, 0.0)
+    score_ms = statistics.mean(p[1] for p in phases)
+    achieved = cells / (score_ms * 1e-3) / 1e9
+    traffic = (_traffic_record(os.path.join(ROOT, "paper_1304_0681_gb300", "csrc", "sw_score.cu"))
+               if workload == "throughput" and args.pairs is None else None)
+    in_mb = (len(wl.packed_reads()) + len(wl.packed_windows())) / 1e6
+    res = {"value": all_cells / total_s / 1e9, "unit": "GCUPS", "ms_per_step": total_s * 1e3 / steps,
+           "steps": steps, "reads_per_s": all_reads / total_s, "clocks": clk, "gpu_launches": int(launches),
+           "config": {"workload": WORKLOADS[workload], "pairs_per_gpu": wl.n_pairs, "cells_per_gpu": cells,
+                      "cigar": want_cigar, "scoring": list(SCORING),
+                      "l2": f"256 MB buffer written between timed steps (packed inputs {in_mb:.0f} MB)"},
+           "phase_ms": {"classify": statistics.mean(p[0] for p in phases), "score": score_ms,
+                        "traceback": statistics.mean(p[2] for p in phases)},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak["gcups"], "unit": "GCUPS",
+                        "frac": achieved / peak["gcups"],
+                        "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                        "kernel": "k_score (score + end-cell pass)", "peak_basis": peak["basis"],
+                        "frac_of_mix_peak": achieved / peak["mix_gcups"]}}
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h_reads, h_wins = pin(wl.packed_reads()), pin(wl.packed_windows())
+        h_roff, h_woff = pin(wl.read_offsets), pin(wl.window_offsets)
+        n = wl.n_pairs
+        h2d = sum(t.numel() * t.element_size() for t in (h_reads, h_wins, h_roff, h_woff))
+        d2h = 3 * n * 4  # score and end cell
+        ns = max(1, args.e2e_streams)
+
+        def outputs():
+            o = {"score": torch.zeros(n, dtype=torch.int32).pin_memory(),
+                 "end": torch.zeros(2 * n, dtype=torch.int32).pin_memory()}
+            if want_cigar:
+                o["ops"] = torch.zeros(int(2 * wl.read_offsets[-1] + 3 * n), dtype=torch.int32).pin_memory()
+                o["offs"] = torch.zeros(n + 1, dtype=torch.int64).pin_memory()
+            return o
+
+        outs = [outputs() for _ in range(ns)]
+        streams = [torch.cuda.Stream() for _ in range(ns)]
+
+        def call(w=0):
+            o = outs[w]
+            with torch.cuda.stream(streams[w]):
+                if want_cigar:
+                    sw.sw_batch_align_host_dense(h_reads, h_roff, h_wins, h_woff, n, SCORING, o["score"], o["end"],
+                                                 o["ops"], o["offs"])
+                else:
+                    sw.sw_batch_align_host(h_reads, h_roff, h_wins, h_woff, n, SCORING, o["score"], o["end"], None)
+        for w in range(ns):
+            call(w)  # each stream's library scratch and staging
+        if want_cigar:
+            d2h += outs[0]["offs"].numel() * 8 + int(outs[0]["offs"][-1]) * 4
+        reps = max(3, min(args.steps, 5))
+
+        def worker(w, kk):
+            torch.cuda.set_device(local)
+            for _ in range(kk):
+                call(w)
+
+        import threading
+        t0 = time.perf_counter()
+        threads = [threading.Thread(target=worker, args=(w, reps)) for w in range(1, ns)]
+        for t in threads:
+            t.start()
+        worker(0, reps)
+        for t in threads:
+            t.join()
+        e_s = (time.perf_counter() - t0) / (reps * ns)
+        e2e_cells, e2e_s = reduce_run(cells, e_s)
+        e2e_reads, _ = reduce_run(n_reads, 0.0)
+        res["e2e"] = {"value": e2e_cells / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h), "reads_per_s": e2e_reads / e2e_s,
+                      "api": "sw_batch_align_host_dense" if want_cigar else "sw_batch_align_host",
+                      "streams": ns, "calls": reps * ns,
+                      "note": "each call copies its batch in from pinned host memory and its results out; "
+                              f"{ns} host threads, each on its own stream, keep calls in flight together"}
+    if not args.no_cpu_baseline and rank == 0 and ws == 1:
+        res["cpu_baseline"] = _cpu_baseline(wl, min(args.cpu_seconds, 8.0))
+    del batch, flush
+    torch.cuda.empty_cache()
+    return res
+
+
+def _measure_peaks() -> dict:
+    """Integer roofline of the score kernel: the measured 16x2 DPX add-max
+    rate x 2 cells / 7 operations per cell, and beside it the measured rate
+    of the DPX + multiply-add mix the kernel issues; HBM from the measured
+    copy bandwidth of this machine's GPUs, else the fallback figure."""
+    import paper_1304_0681_gb300 as sw
+    dpx = sw.sw_alu_probe(1, 20000)
+    mix = sw.sw_alu_probe(6, 20000)
+    hbm, hbm_basis = 6800.0, "fallback 6.8 TB/s"
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            hbm = float(json.load(open(path))["hbm_gbs"])
+            hbm_basis = "measured copy bandwidth (MEASURED_PEAKS.json)"
+        except (ValueError, KeyError):
+            pass
+    return {"gcups": dpx * 2.0 / OPS_PER_CELL / 1e9, "dpx_ops": dpx,
+            "basis": f"measured 16x2 DPX add-max rate {dpx / 1e12:.2f} Tops/s x 2 cells / {OPS_PER_CELL:g} ops per cell",
+            "mix_gcups": mix * 2.0 / OPS_PER_CELL / 1e9,
+            "mix_basis": f"measured 16x2 DPX add-max + multiply-add mix {mix / 1e12:.2f} Tops/s x 2 cells / "
+                         f"{OPS_PER_CELL:g} ops per cell",
+            "hbm_gbs": hbm, "hbm_basis": hbm_basis}
+
+
+def _r(x, nd=4):
+    """A number rounded to nd significant digits (compact summary)."""
+    if x is None or isinstance(x, (int, str, bool)):
+        return x
+    return float(f"{x:.{nd}g}")
+
+
+def _summary(head, thr, unev, filt, graph, seeding) -> dict:
+    """The figures of every section in a few hundred characters; printed
+    last in the line so a record that keeps only its tail still holds them."""
+    s = {}
+    if head:
+        s["fullmix_10M"] = {"filtered_rps": _r(head["filtered"]["reads_per_s"]),
+                            "plain_rps": _r(head["plain"]["reads_per_s"]),
+                            "speedup": _r(head["speedup_reads_per_s"], 3), "recall": _r(head["best_hit_recall"], 5),
+                            "k": head["config"]["k"], "tau": head["config"]["tau"],
+                            "aligned_share": _r(head["filtered"]["aligned_share"], 3),
+                            "plain_gcups": _r(head["plain"]["gcups"]),
+                            "score_frac": _r(head["roofline"]["frac"], 3),
+                            "e2e_rps": _r(head.get("e2e", {}).get("value")),
+                            "oracle_rps": _r(head.get("cpu_baseline", {}).get("value"))}
+    if thr:
+        s["throughput_1M"] = {"gcups": _r(thr["value"]), "ms": _r(thr["ms_per_step"]),
+                              "phase_ms": [_r(v, 3) for v in thr["phase_ms"].values()],
+                              "score_frac": _r(thr["roofline"]["frac"], 3),
+                              "e2e_gcups": _r(thr.get("e2e", {}).get("value")),
+                              "oracle_gcups": _r(thr.get("cpu_baseline", {}).get("value"), 3)}
+    if unev:
+        s["uneven_2M"] = {"gcups": _r(unev["gcups"]), "ms": _r(unev["ms_per_step"]),
+                          "phase_ms": [_r(v, 3) for v in unev["phase_ms"].values()],
+                          "score_frac": _r(unev["score_roofline_frac"], 3)}
+    if filt:
+        s["filter_500k"] = {"filtered_rps": _r(filt["filtered"]["reads_per_s"]),
+                            "plain_rps": _r(filt["plain"]["reads_per_s"]),
+                            "speedup": _r(filt["speedup_reads_per_s"], 3), "recall": _r(filt["best_hit_recall"], 5),
+                            "k": filt["k"], "tau": filt["tau"]}
+    if graph:
+        s["graph_16k"] = {"direct_ms": _r(graph["direct_ms_per_batch"], 3),
+                          "graph_ms": _r(graph["graph_ms_per_batch"], 3)}
+    if seeding:
+        for nm in ("T2", "T4"):
+            if nm in seeding:
+                s[f"seed_{nm}"] = {"ms": _r(seeding[nm]["seed_ms"], 3),
+                                   "frac": _r(seeding[nm]["roofline"]["frac"], 3)}
+    return s
+
+
 def run_reference(args, ws, rank):
+    """The oracle as the reference arm, on the host cores, on the same
+    workload, metric and unit as the GPU line; each step a bounded sample
+    sized so the whole run ends within a few minutes."""
     if rank != 0:
         return
     import numpy as np
 
     import oracle
     import synth
-    wl = synth.generate(args.workload, seed=0)
     cores = os.cpu_count() or 1
-    rng = np.random.default_rng(777)
-    # size each step so the whole run stays within a few minutes
     per_step_s = max(2.0, 120.0 / max(args.steps + args.warmup, 1))
+    if args.workload == "fullmix":
+        o = _OracleReads("fullmix", 0, 50_000)
+        rng = np.random.default_rng(777)
+        per = o.sized(per_step_s, rng)  # sizes the steps
+        n = per["reads"]
+        times, reads, pairs = [], 0, 0
+        for s in range(args.warmup + args.steps):
+            r = o.run(np.sort(rng.choice(o.wl.n_reads, n, replace=False)))
+            if s >= args.warmup:
+                times.append(r["seconds"])
+                reads += r["reads"]
+                pairs += r["pairs"]
+        total = sum(times)
+        value = reads / total
+        sample = (f"{n} reads per step drawn uniformly from the first {o.wl.n_reads} reads of the set "
+                  f"(host-generated), every candidate aligned (score + end, best per read)")
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "reads/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64",
+                "data": "synthetic", "config": {"workload": WORKLOADS["fullmix"], "sample_reads_per_step": n,
+                                                "pairs_per_step": pairs / args.steps},
+                "cpu_baseline": {"value": value, "unit": "reads/s", "cores": o.cores, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": "reads/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "note": "the oracle's exhaustive search (every candidate aligned, best hit per read): the "
+                        "definition the filtered search's best-hit recall is judged against"}
+        print(json.dumps(line), flush=True)
+        return
+    wl = synth.generate(args.workload, seed=0)
+    rng = np.random.default_rng(777)
     probe = wl.pair_slice(np.sort(rng.choice(wl.n_pairs, 4 * cores, replace=False)))
     t = time.perf_counter()
     oracle.align_batch(probe.reads, probe.read_offsets, probe.windows, probe.window_offsets,
@@ -756,10 +1276,8 @@ def main():
     if args.only_mlp:
         return run_mlp_only(args)
 
-    import numpy as np
     import torch
 
-    import synth
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device")
     torch.cuda.set_device(local)
@@ -773,163 +1291,47 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
         pg = dist
-    import paper_1304_0681_gb300 as sw
-    from paper_1304_0681_gb300 import DeviceBatch, align
-    from paper_1304_0681_gb300.shard import reduce_run
 
-    want_cigar = not args.no_cigar
-    wl = synth.generate(args.workload, seed=rank, n_reads=args.pairs)
-    batch = DeviceBatch.from_packed(wl.packed_reads(), wl.read_offsets, wl.packed_windows(), wl.window_offsets,
-                                    cigar=want_cigar)
-    cells, n_reads = wl.cells(), wl.n_reads
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    # integer roofline: measured 16x2 DPX add-max throughput
-    dpx_ops = sw.sw_alu_probe(1, 20000)
-    peak_gcups = dpx_ops * 2.0 / OPS_PER_CELL / 1e9
-
-    for _ in range(args.warmup):
-        align(batch, SCORING, cigar=want_cigar)
-    torch.cuda.synchronize()
-
-    sw.sw_phase_timing(True)
-    clocks = Clocks(local)
-    launches0 = sw.sw_launch_count()
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    step_ms, phases = [], []
-    for _ in range(args.steps):
-        flush.zero_()  # write > L2 so every step starts cold
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        align(batch, SCORING, cigar=want_cigar, sync=False)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        phases.append(sw.sw_phase_times())
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    launches = sw.sw_launch_count() - launches0 - 0
-    sw.sw_sync_status()
-    sw.sw_phase_timing(False)
-    # whole job: every rank's cells over the slowest rank's time
-    all_cells, total_s = reduce_run(cells * args.steps, sum(step_ms) * 1e-3)
-    all_reads, _ = reduce_run(n_reads * args.steps, 0.0)
-    total_ms = total_s * 1e3
-    value = all_cells / total_s / 1e9
-    reads_per_s = all_reads / total_s
-
-    score_ms = statistics.mean(p[1] for p in phases)
-    tb_ms = statistics.mean(p[2] for p in phases)
-    cls_ms = statistics.mean(p[0] for p in phases)
-    achieved = cells / (score_ms * 1e-3) / 1e9
-    # the recorded DRAM traffic is for the full throughput batch only
-    traffic = (_traffic_record(os.path.join(ROOT, "paper_1304_0681_gb300", "csrc", "sw_score.cu"))
-               if args.workload == "throughput" and args.pairs is None else None)
-    in_mb = (len(wl.packed_reads()) + len(wl.packed_windows())) / 1e6
-
-    # end to end through the host entry point: pinned inputs in, results out
-    # (sw_batch_align_host_dense: scores, end cells and the CIGARs packed)
-    e2e = None
-    if not args.no_e2e:
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        h_reads, h_wins = pin(wl.packed_reads()), pin(wl.packed_windows())
-        h_roff, h_woff = pin(wl.read_offsets), pin(wl.window_offsets)
-        n = wl.n_pairs
-        h2d = sum(t.numel() * t.element_size() for t in (h_reads, h_wins, h_roff, h_woff))
-        d2h = 3 * n * 4  # score and end cell
-
-        ns = max(1, args.e2e_streams)
-
-        def outputs():
-            o = {"score": torch.zeros(n, dtype=torch.int32).pin_memory(),
-                 "end": torch.zeros(2 * n, dtype=torch.int32).pin_memory()}
-            if want_cigar:
-                o["ops"] = torch.zeros(int(2 * wl.read_offsets[-1] + 3 * n), dtype=torch.int32).pin_memory()
-                o["offs"] = torch.zeros(n + 1, dtype=torch.int64).pin_memory()
-            return o
-
-        outs = [outputs() for _ in range(ns)]
-        streams = [torch.cuda.Stream() for _ in range(ns)]
-
-        def call(w=0):
-            o = outs[w]
-            with torch.cuda.stream(streams[w]):
-                if want_cigar:
-                    sw.sw_batch_align_host_dense(h_reads, h_roff, h_wins, h_woff, n, SCORING, o["score"], o["end"],
-                                                 o["ops"], o["offs"])
-                else:
-                    sw.sw_batch_align_host(h_reads, h_roff, h_wins, h_woff, n, SCORING, o["score"], o["end"], None)
-        for w in range(ns):
-            call(w)  # each stream's library scratch and staging
-        if want_cigar:
-            d2h += outs[0]["offs"].numel() * 8 + int(outs[0]["offs"][-1]) * 4
-        reps = max(3, min(args.steps, 5))
-
-        def worker(w, k):
-            torch.cuda.set_device(local)
-            for _ in range(k):
-                call(w)
-
-        import threading
-        t0 = time.perf_counter()
-        threads = [threading.Thread(target=worker, args=(w, reps)) for w in range(1, ns)]
-        for t in threads:
-            t.start()
-        worker(0, reps)
-        for t in threads:
-            t.join()
-        e_times = [(time.perf_counter() - t0) / (reps * ns)]
-        e2e_cells, e2e_s = reduce_run(cells, sum(e_times) / len(e_times))
-        e2e_reads, _ = reduce_run(n_reads, 0.0)
-        e2e = {"value": e2e_cells / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "reads_per_s": e2e_reads / e2e_s,
-               "api": "sw_batch_align_host_dense" if want_cigar else "sw_batch_align_host",
-               "streams": ns, "calls": reps * ns,
-               "note": "each call copies its batch in from pinned host memory and its results out; "
-                       f"{ns} host threads, each on its own stream, keep calls in flight together"}
-
-    filt = None
-    if not args.no_filter:
-        filt = _filter_section(args, rank, steps=max(2, min(args.steps, 5)), n_reads=args.filter_reads)
-    uneven = fullmix = graph = seeding = None
-    if not args.no_extra and args.workload == "throughput":
+    peak = _measure_peaks()
+    head = thr = unev = filt = graph = seeding = None
+    extra = not args.no_extra and ws == 1
+    if args.workload == "fullmix":
+        head = _fullmix_headline(args, rank, ws, pg, peak, local)
+        line = {"metric": METRIC, "value": head["value"], "unit": "reads/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "i16x2+i32 (SW), bf16 (network)",
+                "data": "synthetic", "config": head["config"],
+                "reads_per_s_plain": head["plain"]["reads_per_s"],
+                "speedup_reads_per_s": head["speedup_reads_per_s"], "best_hit_recall": head["best_hit_recall"],
+                "filtered": head["filtered"], "plain": head["plain"], "roofline": head["roofline"],
+                "features_roofline": head["features_roofline"], "training": head["training"],
+                "clocks": head["clocks"], "gpu_launches": head["gpu_launches"], "e2e": head.get("e2e"),
+                "cpu_baseline": head.get("cpu_baseline")}
+        if extra:
+            thr = _throughput_section(args, rank, ws, pg, peak, local)
+    else:
+        thr = _throughput_section(args, rank, ws, pg, peak, local, workload=args.workload, headline=True)
+        line = {"metric": METRIC, "value": thr["value"], "unit": "GCUPS", "n_gpus": ws, "steps": thr["steps"],
+                "warmup": args.warmup, "ms_per_step": thr["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "i16x2+i32", "data": "synthetic",
+                "config": thr["config"], "reads_per_s": thr["reads_per_s"], "phase_ms": thr["phase_ms"],
+                "roofline": thr["roofline"], "clocks": thr["clocks"], "gpu_launches": thr["gpu_launches"],
+                "e2e": thr.get("e2e"), "cpu_baseline": thr.get("cpu_baseline")}
+    if extra:
+        import torch
         graph = _graph_section(rank)
-        del batch
         torch.cuda.empty_cache()
-        uneven = _uneven_section(args, rank, steps=max(2, min(args.steps, 3)), peak_gcups=peak_gcups)
+        unev = _uneven_section(args, rank, steps=max(2, min(args.steps, 3)), peak_gcups=peak["gcups"])
         if not args.no_filter:
             torch.cuda.empty_cache()
-            fullmix = _filter_section(args, rank, steps=max(2, min(args.steps, 3)), name="fullmix",
-                                      n_reads=args.fullmix_reads, n_train=40_000, n_cal=15_000, epochs=8,
-                                      on_device=True)
+            filt = _filter_section(args, rank, steps=max(2, min(args.steps, 5)), n_reads=args.filter_reads)
         if not args.no_seeding:
             torch.cuda.empty_cache()
             seeding = _seeding_section(args, rank, steps=max(2, min(args.steps, 3)))
-
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "i16x2+i32", "data": "synthetic",
-                "config": {"workload": WORKLOADS[args.workload], "pairs_per_gpu": wl.n_pairs,
-                           "cells_per_gpu": cells, "cigar": want_cigar, "scoring": list(SCORING),
-                           "l2": f"256 MB buffer written between timed steps (packed inputs {in_mb:.0f} MB)"},
-                "reads_per_s": reads_per_s,
-                "phase_ms": {"classify": cls_ms, "score": score_ms, "traceback": tb_ms},
-                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gcups, "unit": "GCUPS",
-                             "frac": achieved / peak_gcups,
-                             "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
-                             "kernel": "k_score (score + end-cell pass)",
-                             "peak_basis": f"measured 16x2 DPX add-max rate {dpx_ops / 1e12:.2f} Tops/s "
-                                           f"x 2 cells / {OPS_PER_CELL:g} ops per cell"},
-                "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "learned_filter": filt,
-                "uneven": uneven, "fullmix": fullmix, "small_batch_graph": graph, "seeding": seeding}
-        if rank == 0 and not args.no_cpu_baseline and ws == 1:
-            line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
+        line["detail"] = {"peaks": peak, "throughput_1M": thr if head else None, "uneven_2M": unev,
+                          "filter_500k": filt, "small_batch_graph": graph, "seeding": seeding}
+        line["summary"] = _summary(head, thr, unev, filt, graph, seeding)
         print(json.dumps(line), flush=True)
     if pg:
         pg.barrier()

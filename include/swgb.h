@@ -118,12 +118,22 @@ int64_t sw_packed_bytes(int64_t n_bases);
  *  stream                     CUDA stream
  *
  * Read length must be 1..SW_MAX_READ_LEN, window length 0..SW_MAX_WINDOW_LEN
- * (an empty window gives score 0).  The call enqueues a classification
- * kernel, waits for it on `stream` (it reads back a few hundred bytes of
- * per-class counts to size the launches), then enqueues the alignment
- * kernels and returns without waiting for them (sw_sync_status waits and
- * reports errors the alignment kernels found).  Not capturable in a CUDA
- * graph because of the mid-call wait.
+ * (an empty window gives score 0).  The call enqueues a fixed sequence of
+ * memsets and kernel launches on `stream` and returns without waiting: the
+ * batch is classified into length classes on the device, one-block planner
+ * kernels size the launches there, and every compiled kernel variant runs
+ * once as a persistent launch over the classes planned for it (launches with
+ * nothing to do exit at once).  The host never waits for the device, so the
+ * call can be captured into a CUDA graph, provided that an uncaptured call on
+ * the same stream with at least as many pairs came first: the first call of
+ * a size on a stream allocates the library's scratch for it, and a call that
+ * would have to grow scratch during a capture returns SW_ERR_UNSUPPORTED.
+ * Replays use the bases, offsets and outputs the captured call named.
+ * sw_sync_status waits and reports what the kernels found (invalid device
+ * input, an overflowing CIGAR slot, ...).  Scratch is bounded per call: a
+ * batch whose longest pair needs more than the call's scratch for one warp
+ * (far beyond the workloads of the paper, e.g. an 8,000-base read against a
+ * window of a million bases) is reported as SW_ERR_UNSUPPORTED.
  */
 int sw_batch_align(const uint8_t *reads, const int64_t *read_offsets,
                    const uint8_t *windows, const int64_t *window_offsets,
@@ -360,25 +370,26 @@ int sw_batch_align_host_dense(const uint8_t *reads, const int64_t *read_offsets,
                               int64_t *offsets_out, sw_stream_t stream);
 
 /*
- * Capturable execution of a fixed-shape batch (pattern: one plan, many
- * replays).  sw_batch_align synchronises with the host twice per call (to
- * size its launches from the batch) and allocates on growth, so it cannot be
- * captured into a CUDA graph.  A plan takes those decisions once:
+ * Fixed-shape execution with dedicated scratch (pattern: one plan, many
+ * replays).  sw_batch_align sizes its scratch from the pair count and grows
+ * it on demand; a plan instead owns scratch sized for the worst case of one
+ * batch shape, so its executions never allocate, on any stream:
  *
  *   sw_plan_create classifies the batch given by its offsets (device
  *   pointers, as for sw_batch_align_indexed; pair_read may be NULL for one
- *   read per pair), picks the lane plans, sizes the traceback for the worst
- *   case (every window fully inside the band) and allocates all scratch the
- *   plan will use.  It synchronises `stream` once.  with_cigar = 0 plans
- *   score and end cell only.
+ *   read per pair), sizes the score boundaries and the traceback for the
+ *   worst case of that shape (every window fully inside the band) and
+ *   allocates all scratch, auxiliary streams and events the plan will use.
+ *   It synchronises `stream` once.  with_cigar = 0 plans score and end
+ *   cell only.
  *
- *   sw_plan_align enqueues the whole path on `stream` for the plan's shape
- *   and the given packed bases and outputs: no allocation, no host
- *   synchronisation, a fixed sequence of kernel launches and memsets.  So it
- *   can be captured into a CUDA graph and replayed; the bases and outputs
- *   may change between calls or replays (the arrays the captured call named
- *   are the ones a replay uses), the offsets must not.  The device compares
- *   the batch's class counts with the plan's and reports a mismatch as
+ *   sw_plan_align enqueues on `stream` the same fixed sequence of memsets and
+ *   launches as sw_batch_align, for the plan's shape and the given packed
+ *   bases and outputs: no allocation, no host synchronisation.  So it can be
+ *   captured into a CUDA graph and replayed; the bases and outputs may change
+ *   between calls or replays (the arrays the captured call named are the
+ *   ones a replay uses), the offsets must not.  The device compares the
+ *   batch's class counts with the plan's and reports a mismatch as
  *   SW_ERR_DEVICE_INPUT through sw_plan_status.
  *
  *   sw_plan_status waits for `stream` and returns the status the plan's
@@ -493,7 +504,10 @@ int64_t sw_launch_count(void);
  * choice for length classes whose longest read is <= max_read_len (0 clears
  * all overrides); r_rows must be one of the compiled row counts (sw_plan_rows
  * lists them), and lanes * r_rows must cover the reads unless lanes == 32
- * (longer reads are then processed in chunks of 32 * r_rows rows).
+ * (longer reads are then processed in chunks of 32 * r_rows rows).  At most
+ * 16 overrides are held (SW_ERR_UNSUPPORTED beyond).  Process-wide; applies
+ * to calls made after it, and the planner kernels of a call read the
+ * overrides it was enqueued with.
  */
 int sw_set_plan(int32_t max_read_len, int32_t lanes, int32_t r_rows);
 
@@ -526,8 +540,8 @@ int sw_set_score_mode(int32_t mode);
  * Pairs the most recent sw_batch_align* call with a CIGAR on the current
  * device sent to each traceback kernel: out[0] through the 16-bit kernel,
  * out[1] through the 32-bit kernels (pairs without an alignment included).
- * Known when the call returns, before its kernels finish.  Returns
- * SW_ERR_INVALID_ARG for a null pointer.
+ * The split is planned on the device, so this waits for the device.
+ * Returns SW_ERR_INVALID_ARG for a null pointer.
  */
 int sw_last_traceback_split(int64_t *out2);
 int sw_plan_rows(int32_t *rows, int32_t cap);
@@ -535,8 +549,9 @@ int sw_plan_rows(int32_t *rows, int32_t cap);
 /*
  * Phase timing (measurement support).  With timing enabled, each call records
  * CUDA events on its stream around its three phases; sw_phase_times waits for
- * the last call and writes the milliseconds of (0) classification including
- * the host read-back, (1) the score kernels, (2) the traceback kernels.
+ * the last call and writes the milliseconds of (0) classification and launch
+ * planning, (1) the score kernels, (2) the traceback (its sort, planning and
+ * kernels).
  * Returns SW_ERR_INVALID_ARG if the last call was not timed.
  */
 int sw_phase_timing(int32_t enable);

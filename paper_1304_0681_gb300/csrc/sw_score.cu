@@ -61,11 +61,12 @@ struct PairRef {
     int32_t m, n;    // lengths (m == 0: no pair)
 };
 
-__device__ __forceinline__ PairRef load_pair(const ScoreLaunch &L, int64_t item, bool on)
+__device__ __forceinline__ PairRef load_pair(const ScoreLaunch &L, const int32_t *order, int64_t n_items,
+                                             int64_t item, bool on)
 {
     PairRef pr{0, 0, 0, 0};
-    if (on && item < L.n_items) {
-        const int64_t p = L.order[item];
+    if (on && item < n_items) {
+        const int64_t p = order[item];
         const int64_t rd = L.ps.pair_read ? L.ps.pair_read[p] : p;
         pr.rs = L.ps.read_off[rd];
         pr.m = (int32_t)(L.ps.read_off[rd + 1] - pr.rs);
@@ -163,31 +164,86 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
     }
 
     const int lane = threadIdx.x & 31;
-    const int T = L.lanes;
+    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t one = (uint32_t)L.one;
+    const V GO = A::splat(go), GE = A::splat(ge);
+    // input already found invalid (or a plan whose shape changed): the
+    // scratch may be too small for it, so do nothing
+    if (*(volatile const int32_t *)L.status & ST_BAD_INPUT) return;
+
+    // One class given by the host, or every class of this launch's variant
+    // in the device plan (longest reads first); the warps of the launch move
+    // on to the next class as soon as the current one has no work left.
+    // The class's order, count, counter and index live in shared memory, one
+    // record per warp, read where they are used: held in registers across
+    // the inner loops they would push the largest plans into spills.
+    struct ClassCtx {
+        const int32_t *order;
+        int32_t *work_counter;
+        int64_t n_items;
+        uint8_t *bnd_warp;       // the warp's boundary slot (nullptr: one row chunk)
+        int64_t bnd_group_bytes;
+        int32_t cls, ci, n_cls;
+    };
+    __shared__ ClassCtx s_cc[4];  // 128 threads: 4 warps
+    volatile ClassCtx *const cc = &s_cc[threadIdx.x >> 5];
+    const bool planned = L.dp != nullptr;
+    if (lane == 0) {
+        cc->ci = 0;
+        cc->n_cls = planned ? L.dp->var_n[L.variant] : 1;
+    }
+    __syncwarp();
+    for (; cc->ci < cc->n_cls; __syncwarp(), cc->ci = cc->ci + (lane == 0 ? 1 : 0), __syncwarp()) {
+    const int ci = cc->ci;
+    int T = L.lanes, cls = L.cls;
+    const int32_t *order = L.order;
+    int64_t n_items = L.n_items, bnd_group_bytes = L.boundary_group_bytes;
+    int32_t *work_counter = L.work_counter;
+    uint8_t *bnd_base = L.boundary;
+    int64_t bnd_warp_bytes = 0;  // warp stride of the boundary slots (host-given: G groups of this class)
+    if (planned) {
+        const DevScorePlan &dp = *L.dp;
+        cls = dp.var_cls[L.variant][ci];
+        T = dp.cls_lanes[cls];
+        order = L.order + dp.cls_start[cls];
+        n_items = dp.cls_count[cls];
+        work_counter = L.work_counter + cls;
+        bnd_group_bytes = dp.cls_bnd_bytes[cls];
+        bnd_base = nullptr;
+        if (bnd_group_bytes) {
+            // reads in several row chunks: only warps with a boundary slot
+            if (warp_global >= dp.var_bnd_warps[L.variant]) continue;
+            bnd_base = L.boundary + dp.var_bnd_offset[L.variant];
+            // every class of the variant uses the same warp stride, so that
+            // warps working on different classes never share bytes
+            bnd_warp_bytes = dp.var_bnd_slot[L.variant];
+        }
+    }
     const int G = 32 / T;
     const int g = lane / T;
     const int k = lane - g * T;
     const bool on = g < G;
     const int per_warp = G * (PAIR2 ? 2 : 1);
-    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t one = (uint32_t)L.one;
-    const V GO = A::splat(go), GE = A::splat(ge);
-
-    uint8_t *bnd = (on && L.boundary) ? L.boundary + (warp_global * G + g) * L.boundary_group_bytes : nullptr;
-    const int64_t bnd_half = L.boundary_group_bytes / 2;  // bytes per buffer of the double buffer
-    // input already found invalid (a planned batch whose shape changed): the
-    // scratch may be too small for it, so do nothing
-    if (*(volatile const int32_t *)L.status & ST_BAD_INPUT) return;
+    if (!planned) bnd_warp_bytes = G * bnd_group_bytes;
+    if (lane == 0) {
+        cc->order = order;
+        cc->work_counter = work_counter;
+        cc->n_items = n_items;
+        cc->cls = cls;
+        cc->bnd_warp = bnd_base ? bnd_base + warp_global * bnd_warp_bytes : nullptr;
+        cc->bnd_group_bytes = bnd_group_bytes;
+    }
+    __syncwarp();
 
     for (;;) {
         int base = 0;
-        if (lane == 0) base = atomicAdd(L.work_counter, per_warp);
+        if (lane == 0) base = atomicAdd(cc->work_counter, per_warp);
         base = __shfl_sync(FULL, base, 0);
-        if (base >= L.n_items) break;
+        if (base >= cc->n_items) break;
 
         const int64_t item = base + (int64_t)g * (PAIR2 ? 2 : 1);
-        const PairRef pa = load_pair(L, item, on);
-        const PairRef pb = PAIR2 ? load_pair(L, item + 1, on) : PairRef{0, 0, 0, 0};
+        const PairRef pa = load_pair(L, cc->order, cc->n_items, item, on);
+        const PairRef pb = PAIR2 ? load_pair(L, cc->order, cc->n_items, item + 1, on) : PairRef{0, 0, 0, 0};
         const int32_t mg = max(pa.m, pb.m), ng = max(pa.n, pb.n);
         const int32_t mw = __reduce_max_sync(FULL, (unsigned)mg);
         const int32_t nw = __reduce_max_sync(FULL, (unsigned)ng);
@@ -240,6 +296,11 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
             uint32_t wwA = 0, wwB = 0;
             const bool load_bnd = c > 0;
             const bool store_bnd = c + 1 < chunks;
+            // this group's double-buffered boundary row (bytes per buffer: half)
+            uint8_t *const bnd_w = cc->bnd_warp;
+            const int64_t bgb = cc->bnd_group_bytes;
+            uint8_t *const bnd = (on && bnd_w) ? bnd_w + g * bgb : nullptr;
+            const int64_t bnd_half = bgb / 2;
             const V *bin = load_bnd && bnd ? (const V *)(bnd + (c & 1) * bnd_half) : nullptr;
             V *bout = store_bnd && bnd ? (V *)(bnd + ((c + 1) & 1) * bnd_half) : nullptr;
 
@@ -369,22 +430,23 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
             const int64_t it = item + h2;
             int32_t tkey = -1, need32 = 0, wc = 0;
             bool big = false;
-            if (on && k == 0 && it < L.n_items) {
+            if (on && k == 0 && it < cc->n_items) {
                 const uint64_t b = h2 ? bestB : bestA;
-                const int32_t p = L.order[it];
+                const int32_t p = cc->order[it];
                 const uint32_t sc = key_h(b);
                 const int32_t ie = sc ? key_i(b) : -1, je = sc ? key_j(b) : -1;
                 L.out_score[p] = (int32_t)sc;
                 L.out_end[2 * p] = ie;
                 L.out_end[2 * p + 1] = je;
                 if (L.tb_keys) {
-                    tb_cost_key(L.cls, (int32_t)sc, ie, je, L.small_slab_words, L.sc, tkey, need32, wc, big);
+                    tb_cost_key(cc->cls, (int32_t)sc, ie, je, L.small_slab_words, L.sc, tkey, need32, wc, big);
                     L.tb_keys[p] = tkey;
                 }
             }
-            if (L.tb_keys) tb_key_atomics(tkey, L.cls, need32, wc, big, L.tb_hist, L.tb_info);
+            if (L.tb_keys) tb_key_atomics(tkey, cc->cls, need32, wc, big, L.tb_hist, L.tb_info);
         }
     }
+    }  // classes
 }
 
 const int kScoreRows[N_SCORE_ROWS] = {8, 16, 20, 25, 32, 50};
@@ -420,6 +482,16 @@ int launch_score(int rows, int mode, const ScoreLaunch &L, int blocks, int threa
     }
 }
 
+// A device-planned launch of variant v = rows index * N_MODES + mode; the
+// FMA-pipe diagonal add is chosen from the scoring as for launch_score.
+int launch_score_variant(int v, const ScoreLaunch &L, int blocks, cudaStream_t st)
+{
+    if (v < 0 || v >= N_SCORE_VARIANTS || !L.dp) return SW_ERR_INTERNAL;
+    ScoreLaunch V = L;
+    V.variant = v;
+    return launch_score(score_rows_at(v / N_MODES), v % N_MODES, V, blocks, 128, st);
+}
+
 template <int R>
 static const void *kernel_ptr(int mode)
 {
@@ -429,6 +501,16 @@ static const void *kernel_ptr(int mode)
     case MODE_I16W: return (const void *)k_score<R, MODE_I16W, false>;
     default: return nullptr;
     }
+}
+
+int score_variant_blocks(int v, int sm_count, int *blocks)
+{
+    int regs = 0, bps = 0;
+    const int rc = score_kernel_regs(score_rows_at(v / N_MODES), v % N_MODES, &regs, &bps, 128);
+    if (rc) return rc;
+    if (bps < 1) return SW_ERR_INTERNAL;
+    *blocks = bps * sm_count;
+    return SW_OK;
 }
 
 int score_kernel_regs(int rows, int mode, int *regs, int *max_blocks_per_sm, int threads)

@@ -29,10 +29,13 @@
 // the end cell, writes the runs reversed into the pair's CSR slot and
 // reverses them in place.
 //
-// Scheduling.  k_tb_keys gives every pair a cost key (rows x window), a
-// counting sort orders each length class by cost so a warp's groups sweep
-// similar windows, and pairs whose slab exceeds the per-group slab of the
-// main launch form a separate launch with larger slabs.
+// Scheduling.  The score pass's epilogue gives every pair a cost key (rows x
+// window), a counting sort orders each length class by cost so a warp's
+// groups sweep similar windows, and pairs whose slab exceeds the small slab
+// of the main part form a part of their own with larger slabs.  A device
+// planner (sw_devplan.cu) sizes every part and assigns it to one of the
+// persistent launches below; each warp of a launch owns one scratch slot,
+// sized for the largest part of its launch.
 #include <algorithm>
 
 #include "sw_band.cuh"
@@ -131,30 +134,6 @@ __device__ __forceinline__ int64_t slab_need(const TbPair &q, int T)
     return (int64_t)chunks * wcap * T;
 }
 
-// Cost key per pair: class-major, most expensive first within a class.
-// Pairs are visited in index order (coalesced reads of their offsets, score
-// and end cell); pairs the classification left out (key -1) get no key.
-__global__ void k_tb_keys(TbParams P, int64_t n_pairs, const int32_t *__restrict__ score_keys,
-                          int32_t *__restrict__ tb_keys, int32_t *__restrict__ hist, TbClassInfo *__restrict__ info)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; base < n_pairs;
-         base += nwarps * 32) {
-        const int64_t pp = base + lane;
-        const int32_t sk = pp < n_pairs ? score_keys[pp] : -1;
-        int32_t key = -1, cls = 0, need32 = 0, wc = 0;
-        bool big = false;
-        if (sk >= 0) {
-            cls = sk / N_NBUCKET;
-            const TbPair t = tb_pair(P, (int32_t)pp, nullptr);
-            tb_cost_key(cls, t.score, t.ie, t.je, P.small_slab_words, P.sc, key, need32, wc, big);
-        }
-        if (pp < n_pairs) tb_keys[pp] = key;
-        tb_key_atomics(key, cls, need32, wc, big, hist, info);
-    }
-}
-
 // TILED (one lane per pair only): the warp's slabs and boundary rows are
 // interleaved lane-minor -- word (chunk c, column jl) of lane l at
 // [(c * WCAP + jl) * 32 + l] -- so that, all lanes being at the same chunk
@@ -173,38 +152,50 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
-    const int T = L.lanes;
+    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int32_t go = P.sc.go, ge = P.sc.ge;
+    const DevTbPlan &dp = *L.dp;
+    const int v = L.variant;
+    // warps without a scratch slot, and input already found invalid
+    if (warp_global >= dp.var_warps[v]) return;
+    // (an unsupported size means some pairs were not scored, so the
+    // traceback order is incomplete: do nothing)
+    if (*(volatile const int32_t *)L.status & (ST_BAD_INPUT | ST_UNSUPPORTED)) return;
+    uint32_t *const slot = L.slab + dp.var_slot_offset[v] + warp_global * dp.var_slot_words[v];
+
+    for (int pi = 0; pi < dp.var_n[v]; ++pi) {
+    const TbPartPlan &tp = dp.part[dp.var_part[v][pi]];
+    const int T = tp.lanes;
     const int G = 32 / T;
     const int g = lane / T;
     const int k = lane - g * T;
     const bool on = g < G;
     const int rc = T * TB_ROWS;
-    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int WCAP = L.wcap;
-    // slab: TILED -> the warp's tile, indexed with the lane; else the group's slab
-    uint32_t *slab = !on ? nullptr
-                         : TILED ? L.slab + warp_global * 32 * L.slab_group_words
-                                 : L.slab + (warp_global * G + g) * L.slab_group_words;
+    const int WCAP = tp.wcap;
+    const int64_t slab_words = tp.slab_words, bnd_ints = tp.bnd_ints;
+    const int32_t *const order = L.order + tp.start;
+    const int64_t n_items = tp.count;
+    int32_t *const counter = L.work_counter + 2 * tp.cls + tp.part;
+    // the warp's slot: TILED -> one tile indexed with the lane, then the
+    // boundary rows; else every group's slab, then every group's boundary row
+    uint32_t *slab = !on ? nullptr : TILED ? slot : slot + g * slab_words;
     int32_t *bnd = !on ? nullptr
-                       : TILED ? L.boundary + warp_global * 32 * L.boundary_group_ints
-                               : L.boundary + (warp_global * G + g) * L.boundary_group_ints;
-    const int64_t bnd_half = TILED ? 32 * (L.boundary_group_ints / 2) : L.boundary_group_ints / 2;
-    const int32_t go = P.sc.go, ge = P.sc.ge;
-    // input already found invalid (a planned batch whose shape changed)
-    if (*(volatile const int32_t *)L.status & ST_BAD_INPUT) return;
+                       : TILED ? (int32_t *)(slot + 32 * slab_words)
+                               : (int32_t *)(slot + G * slab_words + g * bnd_ints);
+    const int64_t bnd_half = TILED ? 32 * (bnd_ints / 2) : bnd_ints / 2;
 
     for (;;) {
         int base = 0;
-        if (lane == 0) base = atomicAdd(L.work_counter, G);
+        if (lane == 0) base = atomicAdd(counter, G);
         base = __shfl_sync(FULLMASK, base, 0);
-        if (base >= L.n_items) break;
+        if (base >= n_items) break;
         const int64_t item = base + g;
-        const int32_t p = (on && item < L.n_items) ? L.order[item] : -1;
+        const int32_t p = (on && item < n_items) ? order[item] : -1;
         TbPair q = tb_pair(P, p, L.status);
-        const bool over = TILED ? (q.rows > (L.slab_group_words / max(WCAP, 1)) * rc ||
+        const bool over = TILED ? (q.rows > (slab_words / max(WCAP, 1)) * rc ||
                                    min(q.W, rc + (q.b - q.a)) > WCAP)
-                                : (slab_need(q, T) > L.slab_group_words ||
-                                   (q.rows > rc && 4 * (int64_t)min(q.W, rc + (q.b - q.a)) > L.boundary_group_ints));
+                                : (slab_need(q, T) > slab_words ||
+                                   (q.rows > rc && 4 * (int64_t)min(q.W, rc + (q.b - q.a)) > bnd_ints));
         if (q.score > 0 && over) {
             // the launch was sized from the class maxima; never overrun a slab
             // or a boundary row
@@ -430,6 +421,7 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
         }
         __syncwarp();
     }
+    }  // parts
 }
 
 // ---------------------------------------------------------------------------
@@ -467,10 +459,10 @@ __global__ void __launch_bounds__(128) k_traceback(const TracebackLaunch L)
 // grows there), which changes no cell the walk reads.  Boundary rows hold
 // (H | F << 16) per pair and offset, read by the next chunk at its own shift.
 //
-// The sweep leaves each task's tile (64 pairs) in place, and k_tb16_walk then
-// walks every pair with one thread: a walk is a chain of dependent loads from
-// tiles that are long out of L2, so it runs best at full occupancy, apart
-// from the register-heavy sweep.
+// A warp sweeps one task (2G pairs) into the tile of its scratch slot and
+// then walks the task's pairs, one thread per pair, while the other warps of
+// the SM keep sweeping: the walk is a chain of dependent loads, mostly from
+// the L2 the sweep just wrote to.
 
 __device__ __forceinline__ uint32_t mad_u32(uint32_t a, uint32_t b, uint32_t c)
 {
@@ -538,8 +530,222 @@ __device__ __forceinline__ int64_t tb16_word(int c, int t, int lane, int S4)
     return ((((int64_t)c * S4 + (t >> 2)) * 32 + lane) << 2) + (t & 3);
 }
 
+// Collects a CIGAR as the walk emits it (its last run first) and writes it
+// forward into the pair's slot.  The first LB runs emitted -- the whole CIGAR
+// in the common case -- stay in a per-thread buffer and are stored at the
+// end; runs past those are parked at the end of the slot and moved down in
+// batches of loads before stores.  No run is read back from global memory
+// unless the CIGAR has more than LB runs.
+struct FwdCigar {
+    static constexpr int LB = 16;
+    uint32_t *out;
+    int64_t cap;
+    int32_t n;
+    uint32_t op;
+    int32_t len;
+    bool overflow;
+    uint32_t buf[LB];
+    __device__ void push(uint32_t o, int32_t l)
+    {
+        if (l <= 0) return;
+        if (len > 0 && o == op) {
+            len += l;
+            return;
+        }
+        flush();
+        op = o;
+        len = l;
+    }
+    __device__ void flush()
+    {
+        if (len > 0) {
+            const uint32_t run = ((uint32_t)len << 4) | op;
+            if (n >= cap) overflow = true;
+            else if (n < LB) buf[n] = run;
+            else out[cap - 1 - (n - LB)] = run;
+            ++n;
+        }
+        len = 0;
+    }
+    // run e (in emission order) goes to position n - 1 - e
+    __device__ void finish()
+    {
+        if (overflow) return;
+        const int32_t parked = n - LB;
+        if (parked > 0) {
+            const int64_t src = cap - n + LB;  // > 0: every source lies above its target
+            for (int32_t k = 0; k < parked; k += 4) {
+                uint32_t v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (k + u < parked) v[u] = out[src + k + u];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (k + u < parked) out[k + u] = v[u];
+            }
+        }
+        const int32_t nb = n < LB ? n : LB;
+        for (int32_t e = 0; e < nb; ++e) out[n - 1 - e] = buf[e];
+    }
+};
+
+// Walk back from a pair's end cell through the tile of its task (group g,
+// 16-bit half `half`), carrying the exact value of the current state (the
+// tile does not record where H is 0), and write its CIGAR.  A walk keeps the
+// sector of four steps it read last, and the 16-base words of read and
+// window that hold its current row and column.  SAME_KERNEL: the tile was
+// written by this warp in this launch (ordered by __syncwarp) and is read
+// through L2 (ld.global.cg), since the slot is reused by the warp's next
+// task; else it was written by an earlier launch and is read through the
+// read-only cache, where walks of neighbouring groups share 128-byte lines.
+// The walk's CIGAR writer is a separate object (its run buffer is indexed,
+// so it lives in local memory, while the walk's own state stays in
+// registers).
+template <int T, bool SAME_KERNEL>
+struct Walk16 {
+    const uint2 *tile;
+    TbPair qq;
+    int32_t p, i, jj, v;
+    int g, hs, S4, state, cc, clo, chi;
+    int64_t gkey, rkey, wkey, it, limit;
+    uint4 ga, gb;
+    uint32_t rw, ww;
+    bool ok;
+
+    // false when there is nothing to walk (no alignment: 0 runs written)
+    __device__ __forceinline__ bool begin(const TbParams &P, FwdCigar &cg, const uint2 *__restrict__ tile_,
+                                          int32_t p_, int g_, int half, int WCAP, int64_t lane_chunks)
+    {
+        constexpr int rc = T * TB_ROWS;
+        tile = tile_;
+        p = p_;
+        g = g_;
+        hs = 16 * half;
+        S4 = (WCAP + T - 1 + 3) >> 2;
+        qq = tb_pair(P, p, nullptr);
+        // the sweep skipped (and reported) pairs that overrun the tile
+        if ((qq.rows + rc - 1) / rc > lane_chunks || min(qq.W, rc + (qq.b - qq.a)) > WCAP) qq.score = 0;
+        if (qq.score <= 0) {
+            P.cig_n[p] = 0;
+            return false;
+        }
+        const int64_t off = P.cig_off[p];
+        cg.out = P.cig_ops + off;
+        cg.cap = P.cig_off[p + 1] - off;
+        cg.n = 0;
+        cg.op = 0u;
+        cg.len = 0;
+        cg.overflow = false;
+        cg.push(4u, qq.m - 1 - qq.ie);  // trailing soft clip
+        i = qq.ie;
+        jj = qq.W - 1;
+        v = qq.score;  // value of the current state at (i, jj)
+        state = 0;
+        cc = i / rc;
+        chunk_window(qq, cc, rc, clo, chi);
+        gkey = rkey = wkey = -1;
+        ga = gb = make_uint4(0u, 0u, 0u, 0u);
+        rw = ww = 0u;
+        ok = false;
+        // every step moves, or switches into a gap state before moving
+        limit = 2 * ((int64_t)qq.rows + qq.W) + 4;
+        it = 0;
+        return true;
+    }
+
+    // one step; false when the walk is over (done, or inconsistent)
+    __device__ __forceinline__ bool step(const TbParams &P, FwdCigar &cg)
+    {
+        constexpr int rc = T * TB_ROWS;
+        if (it++ >= limit) return false;
+        if (state == 0 && v == 0) {
+            ok = true;
+            return false;
+        }
+        if (i < 0 || jj < 0 || v < 0) return false;
+        if (i < cc * rc) {
+            cc = i / rc;
+            chunk_window(qq, cc, rc, clo, chi);
+        }
+        if (jj < clo || jj > chi) return false;  // left the band: inconsistent
+        const int kk = (i - cc * rc) >> 3, r = i & 7;
+        const int t = (jj - clo) + kk;
+        const int64_t sector = ((int64_t)cc * S4 + (t >> 2)) * 32 + g * T + kk;
+        if (sector != gkey) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(tile + (sector << 2));
+            if (SAME_KERNEL) {  // written by this warp in this launch: through L2
+                ga = __ldcg(src);
+                gb = __ldcg(src + 1);
+            } else {            // written by an earlier launch: the read-only path
+                ga = __ldg(src);
+                gb = __ldg(src + 1);
+            }
+            gkey = sector;
+        }
+        const int sl = t & 3;
+        const uint32_t wlo = sl == 0 ? ga.x : sl == 1 ? ga.z : sl == 2 ? gb.x : gb.z;
+        const uint32_t whi = sl == 0 ? ga.y : sl == 1 ? ga.w : sl == 2 ? gb.y : gb.w;
+        const uint32_t code = ((r < 4 ? wlo : whi) >> (hs + 4 * (r & 3))) & 0xFu;
+        if (state == 0) {
+            if (!(code & 1u)) {
+                // diagonal: H(i-1, j-1) = H(i, j) - s(r_i, w_j)
+                const int64_t rpos = qq.rs + i, wpos = qq.ws + qq.jlo + jj;
+                if ((rpos >> 4) != rkey) {
+                    rkey = rpos >> 4;
+                    rw = __ldg(P.ps.reads + rkey);
+                }
+                if ((wpos >> 4) != wkey) {
+                    wkey = wpos >> 4;
+                    ww = __ldg(P.ps.wins + wkey);
+                }
+                const uint32_t ri = (rw >> (2 * (rpos & 15))) & 3u;
+                const uint32_t wj = (ww >> (2 * (wpos & 15))) & 3u;
+                v -= ri == wj ? P.sc.ma : P.sc.mi;
+                cg.push(0u, 1);
+                --i;
+                --jj;
+            } else {
+                state = (code & 2u) ? 2 : 1;
+            }
+        } else if (state == 1) {
+            cg.push(2u, 1);
+            if (!(code & 4u)) {
+                v -= P.sc.go;  // E(i,j) = H(i,j-1) + o
+                state = 0;
+            } else {
+                v -= P.sc.ge;  // E(i,j) = E(i,j-1) + e
+            }
+            --jj;
+        } else {
+            cg.push(1u, 1);
+            if (!(code & 8u)) {
+                v -= P.sc.go;  // F(i,j) = H(i-1,j) + o
+                state = 0;
+            } else {
+                v -= P.sc.ge;
+            }
+            --i;
+        }
+        return true;
+    }
+
+    __device__ __forceinline__ void end(const TbParams &P, FwdCigar &cg, int32_t *status)
+    {
+        if (!ok) atomicOr(status, ST_INTERNAL);
+        cg.push(4u, i + 1);  // leading soft clip
+        cg.flush();
+        if (cg.overflow) {
+            P.cig_n[p] = -1;
+            atomicOr(status, ST_CAPACITY);
+        } else {
+            cg.finish();
+            P.cig_n[p] = cg.n;
+        }
+    }
+};
+
 template <int T, bool FMA_ADD>
-__global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
+__global__ void __launch_bounds__(128, 4) k_traceback16(const TracebackLaunch L)
 {
     constexpr int G = 32 / T;       // groups per warp, two pairs each
     constexpr int PAIRS = 2 * G;    // pairs per task
@@ -556,32 +762,54 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
     const int lane = threadIdx.x & 31;
     const int g = lane / T, k = lane % T;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int WCAP = L.wcap;
-    const int S4 = (WCAP + T - 1 + 3) >> 2;
-    const int rc = T * TB_ROWS;
-    // one boundary row per group, updated in place: (H | F << 16) of pair x at
-    // offset j in word (j * G + g) * 2 + x
-    uint32_t *bnd = (uint32_t *)L.boundary + warp_global * L.boundary_group_ints;
+    const DevTbPlan &dp = *L.dp;
+    const int v = L.variant;
+    // input already found invalid (an unsupported size means some pairs were
+    // not scored, so the traceback order is incomplete): do nothing
+    if (*(volatile const int32_t *)L.status & (ST_BAD_INPUT | ST_UNSUPPORTED)) return;
+    // the warp's boundary row, and its full slot for tasks it also walks
+    if (warp_global >= dp.var_run_warps[v]) return;
+    uint32_t *const bnd = L.slab + warp_global * dp.var_bnd_words[v];
+    const bool has_slot = warp_global < dp.var_warps[v];
+    uint2 *const own = (uint2 *)(L.slab + dp.var_slot_offset[v] + warp_global * dp.var_slot_words[v]);
     const int32_t go = P.sc.go, ge = P.sc.ge;
     const uint32_t GE2 = splat16(ge), GO2 = splat16(go);
     const uint32_t one = (uint32_t)L.one;
     const uint32_t m1 = 0u - one, two = one + one, four = two + two, eight = four + four;
     const uint32_t mul1 = eight + eight, mul2 = mul1 * mul1, mul3 = mul2 * mul1;  // 16, 256, 4096
     const uint32_t ONES = 0x00010001u;
-    const int64_t lane_chunks = L.slab_group_words / (8 * (int64_t)max(S4, 1));
-    // input already found invalid (a planned batch whose shape changed)
-    if (*(volatile const int32_t *)L.status & ST_BAD_INPUT) return;
 
+    for (int pi = 0; pi < dp.var_n[v]; ++pi) {
+    const TbPartPlan &tp = dp.part[dp.var_part[v][pi]];
+    const int WCAP = tp.wcap;
+    const int S4 = (WCAP + T - 1 + 3) >> 2;
+    const int rc = T * TB_ROWS;
+    const int64_t lane_chunks = tp.slab_words / (8 * (int64_t)max(S4, 1));
+    const int32_t *const order = L.order + tp.start;
+    const int64_t n_items = tp.count;
+    // tasks 0 .. pool_tasks-1 keep their tiles (32 lanes x slab words) in the
+    // pool for k_tb16_walk; the rest are swept into the warp's own slot and
+    // walked at once.  The boundary row is updated in place: (H | F << 16) of
+    // pair x at offset j in word (j * G + g) * 2 + x.
+    const int64_t tile_words = (32 * tp.slab_words + 63) & ~(int64_t)63;
+    const int64_t n_pool = min(n_items, (int64_t)tp.pool_tasks * PAIRS);
+    int32_t *const ctr_pool = L.work_counter + 2 * tp.cls + tp.part;
+    int32_t *const ctr_own = L.work_counter + (CTR_TB_OWN - CTR_TB) + 2 * tp.cls + tp.part;
+
+    for (int phase = 0; phase < 2; ++phase) {
+    if (phase == 1 && !has_slot) break;
     for (;;) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(L.work_counter, PAIRS);
-        base = __shfl_sync(FULLMASK, base, 0);
-        if (base >= L.n_items) break;
+        int bb = 0;
+        if (lane == 0) bb = atomicAdd(phase ? ctr_own : ctr_pool, PAIRS);
+        bb = __shfl_sync(FULLMASK, bb, 0);
+        const int64_t base = phase ? n_pool + bb : bb;
+        if (base >= (phase ? n_items : n_pool)) break;
+        uint2 *const slab = phase ? own : (uint2 *)(L.slab + tp.pool_offset + (int64_t)(bb / PAIRS) * tile_words);
         TbPair q[2];
 #pragma unroll
         for (int x = 0; x < 2; ++x) {
             const int64_t item = base + 2 * g + x;
-            const int32_t p = item < L.n_items ? L.order[item] : -1;
+            const int32_t p = item < n_items ? order[item] : -1;
             q[x] = tb_pair(P, p, k == 0 ? L.status : nullptr);
             const bool over = (q[x].rows + rc - 1) / rc > lane_chunks || min(q[x].W, rc + (q[x].b - q[x].a)) > WCAP;
             if (q[x].score > 0 && over) {
@@ -591,8 +819,6 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
                 q[x].rows = 0;
             }
         }
-        // the task's tile, kept for the walk kernel
-        uint2 *slab = (uint2 *)L.slab + (int64_t)(base / PAIRS) * 32 * (L.slab_group_words / 2);
         const int32_t rows_l = max(q[0].score > 0 ? q[0].rows : 0, q[1].score > 0 ? q[1].rows : 0);
         const int32_t rows_w = __reduce_max_sync(FULLMASK, (unsigned)rows_l);
         const int chunks = (rows_w + rc - 1) / rc;
@@ -710,9 +936,11 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
                         E[r] = e;
                         hu = h;
                     }
-                    // streaming store (the walk reads back a few words of it); a
-                    // lane's four consecutive steps share one 32-byte sector
-                    __stcs(slab + widx, make_uint2(w0, w1));
+                    // a lane's four consecutive steps share one 32-byte
+                    // sector; pooled tiles stream out (walked much later),
+                    // own tiles stay in L2 for the walk right after
+                    if (phase) __stcg(slab + widx, make_uint2(w0, w1));
+                    else __stcs(slab + widx, make_uint2(w0, w1));
                     out_h = hu;
                     out_f = f;
                     if (bout) *(uint2 *)(bout + bidx) = make_uint2(prmt(hu, f, 0x5410u), prmt(hu, f, 0x7632u));
@@ -726,254 +954,149 @@ __global__ void __launch_bounds__(128) k_traceback16(const TracebackLaunch L)
             prev_width = width;
             __syncwarp();
         }
+        // a task in the warp's own slot: its walks, one thread per pair,
+        // while the other warps of the SM keep sweeping; then the slot is
+        // free for the next task
+        if (phase) {
+            for (int wi = lane; wi < PAIRS; wi += 32) {
+                const int64_t item = base + wi;
+                if (item >= n_items) break;
+                Walk16<T, true> w;
+                FwdCigar cg;
+                if (w.begin(P, cg, slab, order[item], wi >> 1, wi & 1, WCAP, lane_chunks)) {
+                    while (w.step(P, cg)) {
+                    }
+                    w.end(P, cg, L.status);
+                }
+            }
+            __syncwarp();
+        }
     }
+    }  // phases
+    }  // parts
 }
 
-// Collects a CIGAR as the walk emits it (its last run first) and writes it
-// forward into the pair's slot.  The first LB runs emitted -- the whole CIGAR
-// in the common case -- stay in a per-thread buffer and are stored at the
-// end; runs past those are parked at the end of the slot and moved down in
-// batches of loads before stores.  No run is read back from global memory
-// unless the CIGAR has more than LB runs.
-struct FwdCigar {
-    static constexpr int LB = 16;
-    uint32_t *out;
-    int64_t cap;
-    int32_t n;
-    uint32_t op;
-    int32_t len;
-    bool overflow;
-    uint32_t buf[LB];
-    __device__ void push(uint32_t o, int32_t l)
-    {
-        if (l <= 0) return;
-        if (len > 0 && o == op) {
-            len += l;
-            return;
-        }
-        flush();
-        op = o;
-        len = l;
-    }
-    __device__ void flush()
-    {
-        if (len > 0) {
-            const uint32_t run = ((uint32_t)len << 4) | op;
-            if (n >= cap) overflow = true;
-            else if (n < LB) buf[n] = run;
-            else out[cap - 1 - (n - LB)] = run;
-            ++n;
-        }
-        len = 0;
-    }
-    // run e (in emission order) goes to position n - 1 - e
-    __device__ void finish()
-    {
-        if (overflow) return;
-        const int32_t parked = n - LB;
-        if (parked > 0) {
-            const int64_t src = cap - n + LB;  // > 0: every source lies above its target
-            for (int32_t k = 0; k < parked; k += 4) {
-                uint32_t v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (k + u < parked) v[u] = out[src + k + u];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (k + u < parked) out[k + u] = v[u];
-            }
-        }
-        const int32_t nb = n < LB ? n : LB;
-        for (int32_t e = 0; e < nb; ++e) out[n - 1 - e] = buf[e];
-    }
-};
-
-// One thread per pair: walk back from the end cell through the tile that
-// k_traceback16<T> wrote (item k of the launch: task k / 2G, group
-// (k % 2G) / 2, half k % 2), carrying the exact value of the current state
-// (the tile does not record where H is 0).  The thread keeps the sector of
-// four steps it read last, and the 16-base words of read and window that
-// hold its current row and column.
+// The walks of a 16-bit launch's pooled tasks: one thread per pair, at full
+// occupancy (a walk is a chain of dependent loads from tiles long out of L2,
+// so many walks in flight hide the latency).  Item k of a part lives in task
+// k / 2G of the part's pool, group (k % 2G) / 2, half k % 2.
 template <int T>
-__global__ void __launch_bounds__(256) k_tb16_walk(const TracebackLaunch L)
+__global__ void __launch_bounds__(256, 4) k_tb16_walk(const TracebackLaunch L)
 {
-    constexpr int G = 32 / T, PAIRS = 2 * G;
+    constexpr int PAIRS = 2 * (32 / T);
     const TbParams &P = L.P;
-    const int WCAP = L.wcap, rc = T * TB_ROWS;
-    const int S4 = (WCAP + T - 1 + 3) >> 2;
-    const int32_t go = P.sc.go, ge = P.sc.ge;
-    const int64_t lane_chunks = L.slab_group_words / (8 * (int64_t)max(S4, 1));
-    if (*(volatile const int32_t *)L.status & ST_BAD_INPUT) return;
-    for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < L.n_items;
-         item += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t p = L.order[item];
-        TbPair qq = tb_pair(P, p, nullptr);
-        // the sweep skipped (and reported) pairs that overrun the tile
-        if ((qq.rows + rc - 1) / rc > lane_chunks || min(qq.W, rc + (qq.b - qq.a)) > WCAP) qq.score = 0;
-        const int64_t off = P.cig_off[p];
-        if (qq.score <= 0) {
-            P.cig_n[p] = 0;
-            continue;
-        }
-        FwdCigar cg;
-        cg.out = P.cig_ops + off;
-        cg.cap = P.cig_off[p + 1] - off;
-        cg.n = 0;
-        cg.op = 0u;
-        cg.len = 0;
-        cg.overflow = false;
-        const uint2 *tile = (const uint2 *)L.slab + (item / PAIRS) * 32 * (L.slab_group_words / 2);
-        const int g = (int)((item % PAIRS) >> 1), hs = 16 * (int)(item & 1);
-        cg.push(4u, qq.m - 1 - qq.ie);  // trailing soft clip
-        int32_t i = qq.ie, jj = qq.W - 1;
-        int32_t v = qq.score;  // value of the current state at (i, jj)
-        int state = 0;
-        int cc = i / rc, clo, chi;
-        chunk_window(qq, cc, rc, clo, chi);
-        int64_t gkey = -1, rkey = -1, wkey = -1;
-        uint4 ga = make_uint4(0u, 0u, 0u, 0u), gb = ga;
-        uint32_t rw = 0u, ww = 0u;
-        bool ok = false;
-        // every step moves, or switches into a gap state before moving
-        const int64_t limit = 2 * ((int64_t)qq.rows + qq.W) + 4;
-        for (int64_t it = 0; it < limit; ++it) {
-            if (state == 0 && v == 0) {
-                ok = true;
-                break;
-            }
-            if (i < 0 || jj < 0 || v < 0) break;
-            if (i < cc * rc) {
-                cc = i / rc;
-                chunk_window(qq, cc, rc, clo, chi);
-            }
-            if (jj < clo || jj > chi) break;  // left the band: inconsistent
-            const int kk = (i - cc * rc) >> 3, r = i & 7;
-            const int t = (jj - clo) + kk;
-            const int64_t sector = ((int64_t)cc * S4 + (t >> 2)) * 32 + g * T + kk;
-            if (sector != gkey) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(tile + (sector << 2));
-                ga = __ldg(src);
-                gb = __ldg(src + 1);
-                gkey = sector;
-            }
-            const int sl = t & 3;
-            const uint32_t wlo = sl == 0 ? ga.x : sl == 1 ? ga.z : sl == 2 ? gb.x : gb.z;
-            const uint32_t whi = sl == 0 ? ga.y : sl == 1 ? ga.w : sl == 2 ? gb.y : gb.w;
-            const uint32_t code = ((r < 4 ? wlo : whi) >> (hs + 4 * (r & 3))) & 0xFu;
-            if (state == 0) {
-                if (!(code & 1u)) {
-                    // diagonal: H(i-1, j-1) = H(i, j) - s(r_i, w_j)
-                    const int64_t rpos = qq.rs + i, wpos = qq.ws + qq.jlo + jj;
-                    if ((rpos >> 4) != rkey) {
-                        rkey = rpos >> 4;
-                        rw = __ldg(P.ps.reads + rkey);
-                    }
-                    if ((wpos >> 4) != wkey) {
-                        wkey = wpos >> 4;
-                        ww = __ldg(P.ps.wins + wkey);
-                    }
-                    const uint32_t ri = (rw >> (2 * (rpos & 15))) & 3u;
-                    const uint32_t wj = (ww >> (2 * (wpos & 15))) & 3u;
-                    v -= ri == wj ? P.sc.ma : P.sc.mi;
-                    cg.push(0u, 1);
-                    --i;
-                    --jj;
-                } else {
-                    state = (code & 2u) ? 2 : 1;
+    const DevTbPlan &dp = *L.dp;
+    const int v = L.variant;
+    if (*(volatile const int32_t *)L.status & (ST_BAD_INPUT | ST_UNSUPPORTED)) return;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int pi = 0; pi < dp.var_n[v]; ++pi) {
+        const TbPartPlan &tp = dp.part[dp.var_part[v][pi]];
+        const int WCAP = tp.wcap;
+        const int S4 = (WCAP + T - 1 + 3) >> 2;
+        const int64_t lane_chunks = tp.slab_words / (8 * (int64_t)max(S4, 1));
+        const int64_t tile_words = (32 * tp.slab_words + 63) & ~(int64_t)63;
+        const int64_t n_pool = min((int64_t)tp.count, (int64_t)tp.pool_tasks * PAIRS);
+        const int32_t *const order = L.order + tp.start;
+        for (int64_t item = tid; item < n_pool; item += nthreads) {
+            const uint2 *tile = (const uint2 *)(L.slab + tp.pool_offset + (item / PAIRS) * tile_words);
+            const int wi = (int)(item % PAIRS);
+            Walk16<T, false> w;
+            FwdCigar cg;
+            if (w.begin(P, cg, tile, order[item], wi >> 1, wi & 1, WCAP, lane_chunks)) {
+                while (w.step(P, cg)) {
                 }
-            } else if (state == 1) {
-                cg.push(2u, 1);
-                if (!(code & 4u)) {
-                    v -= go;  // E(i,j) = H(i,j-1) + o
-                    state = 0;
-                } else {
-                    v -= ge;  // E(i,j) = E(i,j-1) + e
-                }
-                --jj;
-            } else {
-                cg.push(1u, 1);
-                if (!(code & 8u)) {
-                    v -= go;  // F(i,j) = H(i-1,j) + o
-                    state = 0;
-                } else {
-                    v -= ge;
-                }
-                --i;
+                w.end(P, cg, L.status);
             }
-        }
-        if (!ok) atomicOr(L.status, ST_INTERNAL);
-        cg.push(4u, i + 1);  // leading soft clip
-        cg.flush();
-        if (cg.overflow) {
-            P.cig_n[p] = -1;
-            atomicOr(L.status, ST_CAPACITY);
-        } else {
-            cg.finish();
-            P.cig_n[p] = cg.n;
         }
     }
 }
 
-int launch_tb_keys(const TbParams &P, int64_t n_pairs, const int32_t *score_keys, int32_t *tb_keys, int32_t *hist,
-                   TbClassInfo *info, cudaStream_t st)
+// A device-planned launch of traceback variant v: the 16-bit kernel with T =
+// 2^v lanes per pair for v < N_TB16_VARIANTS, else the int32 kernel, tiled or
+// with T lanes per pair.  fma: every substitution score minus gap_open is
+// >= 0, so the 16-bit diagonal add can run on the FMA pipe.
+int launch_traceback_variant(int v, bool fma, const TracebackLaunch &L, int blocks, cudaStream_t st)
 {
-    const int threads = 256;
-    int64_t blocks = (n_pairs + threads - 1) / threads;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    if (blocks < 1) blocks = 1;
-    k_tb_keys<<<(unsigned)blocks, threads, 0, st>>>(P, n_pairs, score_keys, tb_keys, hist, info);
-    count_launch();
-    return launch_status();
-}
-
-int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStream_t st)
-{
-    if (L.packed16) {
-        const bool fma = L.P.sc.mi >= L.P.sc.go;
-        int64_t wb = (L.n_items + 255) / 256;
-        const unsigned wblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(wb, 152 * 8));
-        switch (L.lanes) {
-#define SWGB_TB16(TT)                                                                              \
-    case TT:                                                                                       \
-        if (fma) k_traceback16<TT, true><<<blocks, threads, 0, st>>>(L);                           \
-        else k_traceback16<TT, false><<<blocks, threads, 0, st>>>(L);                              \
-        /* the walks: one thread per pair */                                                       \
-        k_tb16_walk<TT><<<wblocks, 256, 0, st>>>(L);                                                \
+    if (!L.dp || blocks < 1) return SW_ERR_INTERNAL;
+    TracebackLaunch V = L;
+    V.variant = v;
+    switch (v) {
+#define SWGB_TB16(VV, TT)                                                                          \
+    case VV:                                                                                       \
+        if (fma) k_traceback16<TT, true><<<blocks, 128, 0, st>>>(V);                               \
+        else k_traceback16<TT, false><<<blocks, 128, 0, st>>>(V);                                  \
         break;
-            SWGB_TB16(1)
-            SWGB_TB16(2)
-            SWGB_TB16(4)
-            SWGB_TB16(8)
-            SWGB_TB16(16)
-            SWGB_TB16(32)
+        SWGB_TB16(0, 1)
+        SWGB_TB16(1, 2)
+        SWGB_TB16(2, 4)
+        SWGB_TB16(3, 8)
+        SWGB_TB16(4, 16)
+        SWGB_TB16(5, 32)
 #undef SWGB_TB16
-        default:
-            return SW_ERR_INTERNAL;
-        }
-        count_launch();
-    } else if (L.tiled) k_traceback<true><<<blocks, threads, 0, st>>>(L);
-    else k_traceback<false><<<blocks, threads, 0, st>>>(L);
+    case TB_VAR_TILED: k_traceback<true><<<blocks, 128, 0, st>>>(V); break;
+    case TB_VAR_GROUPED: k_traceback<false><<<blocks, 128, 0, st>>>(V); break;
+    default: return SW_ERR_INTERNAL;
+    }
     count_launch();
     return launch_status();
 }
 
-int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads, bool packed16, int lanes)
+int launch_tb_walk_variant(int v, const TracebackLaunch &L, int blocks, cudaStream_t st)
 {
-    cudaError_t e = cudaErrorInvalidValue;
-    if (!packed16) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback<false>, threads, 0);
-    } else {
-        switch (lanes) {
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback16<1, true>, threads, 0); break;
-        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback16<2, true>, threads, 0); break;
-        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback16<4, true>, threads, 0); break;
-        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback16<8, true>, threads, 0); break;
-        case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback16<16, true>, threads, 0); break;
-        case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_traceback16<32, true>, threads, 0); break;
-        default: break;
-        }
+    if (!L.dp || blocks < 1) return SW_ERR_INTERNAL;
+    TracebackLaunch V = L;
+    V.variant = v;
+    switch (v) {
+    case 0: k_tb16_walk<1><<<blocks, 256, 0, st>>>(V); break;
+    case 1: k_tb16_walk<2><<<blocks, 256, 0, st>>>(V); break;
+    case 2: k_tb16_walk<4><<<blocks, 256, 0, st>>>(V); break;
+    case 3: k_tb16_walk<8><<<blocks, 256, 0, st>>>(V); break;
+    case 4: k_tb16_walk<16><<<blocks, 256, 0, st>>>(V); break;
+    case 5: k_tb16_walk<32><<<blocks, 256, 0, st>>>(V); break;
+    default: return SW_ERR_INTERNAL;
     }
-    return cuda_failed(e) ? SW_ERR_CUDA : SW_OK;
+    count_launch();
+    return launch_status();
+}
+
+int tb_walk_variant_blocks(int v, int sm_count, int *blocks)
+{
+    const void *fn = nullptr;
+    switch (v) {
+    case 0: fn = (const void *)k_tb16_walk<1>; break;
+    case 1: fn = (const void *)k_tb16_walk<2>; break;
+    case 2: fn = (const void *)k_tb16_walk<4>; break;
+    case 3: fn = (const void *)k_tb16_walk<8>; break;
+    case 4: fn = (const void *)k_tb16_walk<16>; break;
+    case 5: fn = (const void *)k_tb16_walk<32>; break;
+    default: return SW_ERR_INTERNAL;
+    }
+    int bps = 0;
+    if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 256, 0))) return SW_ERR_CUDA;
+    *blocks = std::max(bps, 1) * sm_count;
+    return SW_OK;
+}
+
+// Blocks of a full-occupancy launch of traceback variant v.
+int traceback_variant_blocks(int v, int sm_count, int *blocks)
+{
+    const void *fn = nullptr;
+    switch (v) {
+    case 0: fn = (const void *)k_traceback16<1, true>; break;
+    case 1: fn = (const void *)k_traceback16<2, true>; break;
+    case 2: fn = (const void *)k_traceback16<4, true>; break;
+    case 3: fn = (const void *)k_traceback16<8, true>; break;
+    case 4: fn = (const void *)k_traceback16<16, true>; break;
+    case 5: fn = (const void *)k_traceback16<32, true>; break;
+    case TB_VAR_TILED: fn = (const void *)k_traceback<true>; break;
+    case TB_VAR_GROUPED: fn = (const void *)k_traceback<false>; break;
+    default: return SW_ERR_INTERNAL;
+    }
+    int bps = 0;
+    if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 128, 0))) return SW_ERR_CUDA;
+    *blocks = std::max(bps, 1) * sm_count;
+    return SW_OK;
 }
 
 }  // namespace swgb

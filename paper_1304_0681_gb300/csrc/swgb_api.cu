@@ -31,68 +31,88 @@ void note_cuda_error(cudaError_t e) { g_cuda_error = (int)e; }
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kTbLanes = 1;            // lanes per pair in the traceback
-constexpr int kSmallSlabWords = 4096;  // per-pair slab of the main traceback launch
-constexpr size_t kSlabBudget = (size_t)4 << 30;
-constexpr int64_t kTiledLaneWords = 4096;  // largest lane tile of a lane-interleaved traceback
-constexpr int64_t kTiledLaneWords16 = 8192;  // the same for the 16-bit traceback (two pairs per lane)
-// Lanes per pair of a multi-lane traceback: the smallest power of two T with
-// the class's longest read in at most this many chunks of 8T rows.  A chunk
-// sweeps its rows' band box, 8T - 1 columns wider than the band, so smaller T
-// wastes fewer cells per pair and larger T keeps fewer pairs per warp waiting.
-// Measured on the uneven batch (2M pairs, reads 75-800 bp), 16-bit sweep:
-// 4 chunks 57.0 ms, 8 chunks 49.6 ms, 16 chunks 64.5 ms of traceback.
-constexpr int kTbChunks32 = 4;
-constexpr int kTbChunks16 = 8;
-// 16-bit traceback tiles kept for the walk: up to this share of the free
-// device memory, at most kTile16Cap; larger batches go in rounds
-constexpr double kTile16FreeShare = 0.4;
-constexpr size_t kTile16Cap = (size_t)64 << 30;
+constexpr int kSmallSlabWords = 4096;  // per-group slab of a traceback's main part
 constexpr int kMaxDevices = 64;
 constexpr int kAuxStreams = 4;
 constexpr int kHostChunks = 2;                 // sw_batch_align_host pipelines a batch in this many chunks
 constexpr int64_t kHostChunkMin = 65536;       // ... of at least this many pairs
-constexpr bool kConcurrentTbParts = false;
+// Scratch budgets of a call, from its pair count (the only size the host
+// knows without reading the device): chunk-boundary rows of the score pass,
+// and the per-warp slots of the traceback.  A warp's slot is sized on the
+// device for its launch's largest part; launches use as many warps as fit.
+constexpr int64_t kScoreBndMin = (int64_t)32 << 20, kScoreBndMax = (int64_t)1 << 30, kScoreBndPerPair = 1024;
+constexpr int64_t kTbMin = (int64_t)64 << 20, kTbPerPair = (int64_t)32 << 10;
+constexpr int64_t kTbCapMax = (int64_t)16 << 30, kTbCapMin = (int64_t)1 << 30;
+constexpr double kTbFreeShare = 0.3;
 
 struct Buffer {
     void *ptr = nullptr;
     size_t bytes = 0;
 };
 
-struct PlanOverride {
-    int32_t max_read_len, lanes, rows;
+// What an execution needs besides scratch: the full-occupancy grid of every
+// launch, the auxiliary streams the score launches fork onto (and the events
+// of the fork and join), and phase events when timing.
+struct ExecCtx {
+    int score_blocks[N_SCORE_VARIANTS] = {};
+    int tb_blocks[N_TB_VARIANTS] = {};
+    int walk_blocks[N_TB16_VARIANTS] = {};
+    cudaStream_t aux[kAuxStreams] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kAuxStreams] = {};
+    bool timing = false;
+    cudaEvent_t *phase = nullptr;  // 4 events, when timing
 };
 
+int exec_ctx_init(ExecCtx &x, int sm_count)
+{
+    int rc = SW_OK;
+    for (int v = 0; v < N_SCORE_VARIANTS; ++v)
+        if ((rc = score_variant_blocks(v, sm_count, &x.score_blocks[v]))) return rc;
+    for (int v = 0; v < N_TB_VARIANTS; ++v)
+        if ((rc = traceback_variant_blocks(v, sm_count, &x.tb_blocks[v]))) return rc;
+    for (int v = 0; v < N_TB16_VARIANTS; ++v)
+        if ((rc = tb_walk_variant_blocks(v, sm_count, &x.walk_blocks[v]))) return rc;
+    for (int k = 0; k < kAuxStreams; ++k) {
+        if (cuda_failed(cudaStreamCreateWithFlags(&x.aux[k], cudaStreamNonBlocking))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaEventCreateWithFlags(&x.join_ev[k], cudaEventDisableTiming))) return SW_ERR_CUDA;
+    }
+    if (cuda_failed(cudaEventCreateWithFlags(&x.fork_ev, cudaEventDisableTiming))) return SW_ERR_CUDA;
+    return SW_OK;
+}
+
+void exec_ctx_free(ExecCtx &x)
+{
+    for (int k = 0; k < kAuxStreams; ++k) {
+        if (x.aux[k]) cudaStreamDestroy(x.aux[k]);
+        if (x.join_ev[k]) cudaEventDestroy(x.join_ev[k]);
+        x.aux[k] = nullptr;
+        x.join_ev[k] = nullptr;
+    }
+    if (x.fork_ev) cudaEventDestroy(x.fork_ev);
+    x.fork_ev = nullptr;
+}
+
 // Library state of one (device, stream): scratch buffers, the status word
-// of the stream's last call, pinned read-back slots, events and auxiliary
-// streams.  Calls on one stream are ordered by the stream; calls on two
-// streams get two states, so their work may overlap on the GPU without
-// sharing scratch.
+// of the stream's last call, events and auxiliary streams.  Calls on one
+// stream are ordered by the stream; calls on two streams get two states,
+// so their work may overlap on the GPU without sharing scratch.
 struct DeviceState {
     bool ready = false;
     int dev = 0;
     int sm_count = 0;
-    int cc_major = 0, cc_minor = 0;
+    ExecCtx x;                       // grids, auxiliary streams, fork and join events
+    int64_t tb_cap = 0;              // largest traceback budget (set at the first traceback)
     Buffer fixed, dyn;
     Buffer stage;            // sw_batch_align_host device staging
-    ClassInfo *info_host = nullptr;  // pinned
-    TbClassInfo *tbinfo_host = nullptr;  // pinned
-    cudaEvent_t last_done = nullptr;
-    bool last_recorded = false;
     int32_t *last_status = nullptr;  // device status word of the last call
+    const DevTbPlan *last_tplan = nullptr;  // traceback plan of the last call with a CIGAR
     bool timing = false;             // record phase events (sw_phase_times)
     bool timed_cells_valid = false;
-    int64_t tb_split[2] = {0, 0};    // pairs per traceback kernel (16-bit, 32-bit) of the last call
-    size_t tile16_budget = 0;        // 16-bit traceback tile budget (set at the first traceback)
     Buffer misc;                     // Stage E task iv: status word and record scan scratch
     Buffer filt;                     // sw_filter_align: features, predictions, selection
     int64_t *seed_stats_host = nullptr;  // pinned: counters of the stream's last sw_seed_windows
     cudaEvent_t phase[4] = {nullptr, nullptr, nullptr, nullptr};
-    // independent launches (length classes, traceback parts) fork onto these
-    // streams and join back, so one launch's tail overlaps the next
-    cudaStream_t aux[kAuxStreams] = {};
-    cudaEvent_t fork_ev = nullptr;
-    cudaEvent_t join_ev[kAuxStreams] = {};
     // sw_batch_align_host: copy streams and per-chunk events
     cudaStream_t copy_in = nullptr, copy_out = nullptr;
     cudaEvent_t host_in_ev[kHostChunks] = {};
@@ -112,21 +132,31 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // Fork: the first n auxiliary streams wait for everything enqueued on st so
 // far.  Join: st waits for all of their work.  (The pattern is legal under
 // stream capture.)
-int fork_streams(DeviceState *ds, cudaStream_t st, int n)
+int fork_streams(const ExecCtx &x, cudaStream_t st, int n)
 {
-    if (cuda_failed(cudaEventRecord(ds->fork_ev, st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaEventRecord(x.fork_ev, st))) return SW_ERR_CUDA;
     for (int k = 0; k < n; ++k)
-        if (cuda_failed(cudaStreamWaitEvent(ds->aux[k], ds->fork_ev, 0))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaStreamWaitEvent(x.aux[k], x.fork_ev, 0))) return SW_ERR_CUDA;
     return SW_OK;
 }
 
-int join_streams(DeviceState *ds, cudaStream_t st, int n)
+int join_streams(const ExecCtx &x, cudaStream_t st, int n)
 {
     for (int k = 0; k < n; ++k) {
-        if (cuda_failed(cudaEventRecord(ds->join_ev[k], ds->aux[k]))) return SW_ERR_CUDA;
-        if (cuda_failed(cudaStreamWaitEvent(st, ds->join_ev[k], 0))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaEventRecord(x.join_ev[k], x.aux[k]))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaStreamWaitEvent(st, x.join_ev[k], 0))) return SW_ERR_CUDA;
     }
     return SW_OK;
+}
+
+bool capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
 }
 
 int ensure(Buffer &b, size_t bytes)
@@ -144,6 +174,15 @@ int ensure(Buffer &b, size_t bytes)
     }
     b.bytes = want;
     return SW_OK;
+}
+
+// As ensure, for a call that may be captured: a buffer cannot grow while
+// the stream is capturing (the first call of a size on a stream allocates).
+int ensure_on(Buffer &b, size_t bytes, cudaStream_t st)
+{
+    if (b.bytes >= bytes) return SW_OK;
+    if (capturing(st)) return SW_ERR_UNSUPPORTED;
+    return ensure(b, bytes);
 }
 
 int device_state(DeviceState **out, cudaStream_t st)
@@ -165,18 +204,11 @@ int device_state(DeviceState **out, cudaStream_t st)
         cudaDeviceProp prop;
         if (cuda_failed(cudaGetDeviceProperties(&prop, dev))) return SW_ERR_NO_DEVICE;
         s.sm_count = prop.multiProcessorCount;
-        s.cc_major = prop.major;
-        s.cc_minor = prop.minor;
-        if (cuda_failed(cudaMallocHost(&s.info_host, sizeof(ClassInfo)))) return SW_ERR_CUDA;
-        if (cuda_failed(cudaMallocHost(&s.tbinfo_host, sizeof(TbClassInfo)))) return SW_ERR_CUDA;
-        if (cuda_failed(cudaEventCreateWithFlags(&s.last_done, cudaEventDisableTiming))) return SW_ERR_CUDA;
+        const int rc = exec_ctx_init(s.x, s.sm_count);
+        if (rc) return rc;
         for (cudaEvent_t &e : s.phase)
             if (cuda_failed(cudaEventCreate(&e))) return SW_ERR_CUDA;
-        for (int k = 0; k < kAuxStreams; ++k) {
-            if (cuda_failed(cudaStreamCreateWithFlags(&s.aux[k], cudaStreamNonBlocking))) return SW_ERR_CUDA;
-            if (cuda_failed(cudaEventCreateWithFlags(&s.join_ev[k], cudaEventDisableTiming))) return SW_ERR_CUDA;
-        }
-        if (cuda_failed(cudaEventCreateWithFlags(&s.fork_ev, cudaEventDisableTiming))) return SW_ERR_CUDA;
+        s.x.phase = s.phase;
         if (cuda_failed(cudaStreamCreateWithFlags(&s.copy_in, cudaStreamNonBlocking))) return SW_ERR_CUDA;
         if (cuda_failed(cudaStreamCreateWithFlags(&s.copy_out, cudaStreamNonBlocking))) return SW_ERR_CUDA;
         for (cudaEvent_t &e : s.host_in_ev)
@@ -185,6 +217,7 @@ int device_state(DeviceState **out, cudaStream_t st)
         s.ready = true;
     }
     s.timing = g_timing[dev];
+    s.x.timing = s.timing;
     g_last_state[dev] = &s;
     *out = &s;
     return SW_OK;
@@ -198,17 +231,10 @@ void free_state(DeviceState *s)
             b->ptr = nullptr;
             b->bytes = 0;
         }
-    if (s->info_host) cudaFreeHost(s->info_host);
     if (s->seed_stats_host) cudaFreeHost(s->seed_stats_host);
-    if (s->tbinfo_host) cudaFreeHost(s->tbinfo_host);
-    if (s->last_done) cudaEventDestroy(s->last_done);
     for (cudaEvent_t e : s->phase)
         if (e) cudaEventDestroy(e);
-    for (int k = 0; k < kAuxStreams; ++k) {
-        if (s->aux[k]) cudaStreamDestroy(s->aux[k]);
-        if (s->join_ev[k]) cudaEventDestroy(s->join_ev[k]);
-    }
-    if (s->fork_ev) cudaEventDestroy(s->fork_ev);
+    exec_ctx_free(s->x);
     if (s->copy_in) cudaStreamDestroy(s->copy_in);
     if (s->copy_out) cudaStreamDestroy(s->copy_out);
     for (cudaEvent_t e : s->host_in_ev)
@@ -249,42 +275,141 @@ int status_to_code(int32_t st)
     return SW_OK;
 }
 
-struct Plan {
-    int lanes, rows;
+// The scratch of one batch execution: arrays sized by the pair count, the
+// class tables and plans, and the dynamic part (score chunk boundaries and
+// traceback slots).
+struct Scratch {
+    int32_t *keys, *order, *hist, *bstart, *cursor, *counters, *tb_keys, *tb_order, *expect;
+    ClassInfo *info;
+    TbClassInfo *tbinfo;
+    DevScorePlan *splan;
+    DevTbPlan *tplan;
+    uint8_t *score_bnd;
+    int64_t score_bnd_bytes;
+    uint32_t *tb;
+    int64_t tb_bytes;
 };
 
-// Lanes per group and rows per lane for reads up to m_max in a mode.  In
-// the 16-bit-key mode a lane block of more than 32 rows needs 6-bit row tags,
-// which leave room for scores up to 510 only (hmax: the class's score bound).
-Plan choose_plan(int mode, int32_t m_max, int64_t hmax)
+// Lays out the pair-count-sized part at base (nullptr: sizes only); returns
+// its bytes.
+size_t fixed_layout(int64_t n_pairs, uint8_t *base, Scratch &S)
 {
-    const int max_rows = (mode == MODE_I16 && hmax > 510) ? 32 : 64;
+    const size_t nh = (size_t)N_CLASS * N_NBUCKET;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        uint8_t *p = base ? base + off : nullptr;
+        off = align_up(off + bytes, 256);
+        return p;
+    };
+    S.keys = (int32_t *)take(sizeof(int32_t) * n_pairs);
+    S.order = (int32_t *)take(sizeof(int32_t) * n_pairs);
+    S.hist = (int32_t *)take(sizeof(int32_t) * nh);
+    S.bstart = (int32_t *)take(sizeof(int32_t) * nh);
+    S.cursor = (int32_t *)take(sizeof(int32_t) * nh);
+    S.info = (ClassInfo *)take(sizeof(ClassInfo));
+    S.counters = (int32_t *)take(sizeof(int32_t) * N_COUNTERS);
+    S.tb_keys = (int32_t *)take(sizeof(int32_t) * n_pairs);
+    S.tb_order = (int32_t *)take(sizeof(int32_t) * n_pairs);
+    S.tbinfo = (TbClassInfo *)take(sizeof(TbClassInfo));
+    S.expect = (int32_t *)take(sizeof(int32_t) * 3 * N_CLASS);
+    S.splan = (DevScorePlan *)take(sizeof(DevScorePlan));
+    S.tplan = (DevTbPlan *)take(sizeof(DevTbPlan));
+    return off;
+}
+
+PlanParams plan_params(const ExecCtx &x, const Scoring &sc, bool allow16, int64_t score_bnd_bytes,
+                       int64_t tb_bytes)
+{
+    PlanParams pp{};
+    pp.sc = sc;
     {
         std::lock_guard<std::mutex> lk(g_plan_mu);
-        for (const PlanOverride &o : g_plans)
-            if (m_max <= o.max_read_len && o.rows <= max_rows) return Plan{o.lanes, o.rows};
+        pp.n_overrides = (int32_t)std::min<size_t>(g_plans.size(), kMaxPlanOverrides);
+        for (int i = 0; i < pp.n_overrides; ++i) pp.ov[i] = g_plans[i];
     }
-    // estimated issue cost per pair-column: padded rows x ~6.5 ALU ops + ~40
-    // ops per lane-step (both measured), scaled by the fraction of lanes a
-    // warp leaves idle
-    double best = 1e300;
-    Plan bp{32, 32};
-    for (int ri = 0; ri < N_SCORE_ROWS; ++ri) {
-        const int R = kScoreRows[ri];
-        if (R > max_rows) continue;
-        for (int T = 1; T <= 32; ++T) {
-            const int chunks = (m_max + T * R - 1) / (T * R);
-            if (chunks > 1 && T < 32) continue;
-            const int G = 32 / T;
-            const double lane_util = (double)(G * T) / 32.0;
-            const double cost = chunks * (double)T * (R * 6.5 + 40.0) / lane_util;
-            if (cost < best - 1e-9) {
-                best = cost;
-                bp = Plan{T, R};
-            }
+    for (int v = 0; v < N_SCORE_VARIANTS; ++v) pp.score_warps[v] = x.score_blocks[v] * (kThreads / 32);
+    for (int v = 0; v < N_TB_VARIANTS; ++v) pp.tb_warps[v] = x.tb_blocks[v] * (kThreads / 32);
+    pp.score_bnd_bytes = score_bnd_bytes;
+    pp.tb_bytes = tb_bytes;
+    pp.small_slab_words = kSmallSlabWords;
+    pp.allow16 = allow16 ? 1 : 0;
+    return pp;
+}
+
+// Enqueues one whole batch on st: classification, the device planners,
+// every score variant (forked over the auxiliary streams), and with a CIGAR
+// the traceback sort, its planner and every traceback variant.  A fixed
+// sequence of memsets and launches: no host synchronisation, no allocation.
+// expect (or nullptr): per-class counts and maxima a plan was made for.
+int enqueue_core(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const Scoring &sc, bool force_i32,
+                 bool allow16, int32_t *out_score, int32_t *out_end, const sw_cigar_t *cig, const Scratch &S,
+                 const int32_t *expect, const ExecCtx &x, cudaStream_t st)
+{
+    int rc = SW_OK;
+    const size_t nh = (size_t)N_CLASS * N_NBUCKET;
+    const PlanParams pp = plan_params(x, sc, allow16, S.score_bnd_bytes, S.tb_bytes);
+    const bool timing = x.timing && x.phase;
+    if (timing && cuda_failed(cudaEventRecord(x.phase[0], st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(S.info, 0, sizeof(ClassInfo), st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(S.counters, 0, sizeof(int32_t) * N_COUNTERS, st))) return SW_ERR_CUDA;
+    if ((rc = launch_classify(ps, n_reads, n_pairs, sc, force_i32, S.keys, S.hist, S.bstart, S.cursor, S.info,
+                              S.order, out_score, out_end, cig ? cig->n_ops : nullptr, st)))
+        return rc;
+    if (expect && (rc = launch_check_counts(S.info, expect, &S.info->status, st))) return rc;
+    if ((rc = launch_plan_score(S.info, pp, S.splan, &S.info->status, st))) return rc;
+    if (cig) {
+        // the score kernels' epilogue writes each pair's traceback cost key
+        // and the class table the traceback planner reads
+        if (cuda_failed(cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaMemsetAsync(S.tbinfo, 0, sizeof(TbClassInfo), st))) return SW_ERR_CUDA;
+        if (cuda_failed(cudaMemsetAsync(S.tb_keys, 0xFF, sizeof(int32_t) * n_pairs, st))) return SW_ERR_CUDA;
+    }
+    if (timing && cuda_failed(cudaEventRecord(x.phase[1], st))) return SW_ERR_CUDA;
+    if ((rc = fork_streams(x, st, kAuxStreams))) return rc;
+    for (int v = 0; v < N_SCORE_VARIANTS; ++v) {
+        ScoreLaunch L{};
+        L.ps = ps;
+        L.sc = sc;
+        L.order = S.order;
+        L.out_score = out_score;
+        L.out_end = out_end;
+        L.boundary = S.score_bnd;
+        L.work_counter = S.counters;
+        L.status = &S.info->status;
+        if (cig) {
+            L.tb_keys = S.tb_keys;
+            L.tb_hist = S.hist;
+            L.tb_info = S.tbinfo;
+            L.small_slab_words = kSmallSlabWords;
+        }
+        L.dp = S.splan;
+        if ((rc = launch_score_variant(v, L, x.score_blocks[v], x.aux[v % kAuxStreams]))) return rc;
+    }
+    if ((rc = join_streams(x, st, kAuxStreams))) return rc;
+    if (timing && cuda_failed(cudaEventRecord(x.phase[2], st))) return SW_ERR_CUDA;
+    if (cig) {
+        if ((rc = launch_scan_scatter(S.tb_keys, n_pairs, S.info->count, S.hist, S.bstart, S.cursor, S.tb_order,
+                                      st)))
+            return rc;
+        if ((rc = launch_plan_tb(S.info, S.tbinfo, S.splan, pp, S.tplan, &S.info->status, st))) return rc;
+        const TbParams P{ps, sc, out_score, out_end, cig->ops, cig->offsets, cig->n_ops, 1, kSmallSlabWords};
+        const bool fma = sc.mi >= sc.go;
+        // one after another: each launch has the whole slot budget
+        for (int v = 0; v < N_TB_VARIANTS; ++v) {
+            TracebackLaunch B{};
+            B.P = P;
+            B.order = S.tb_order;
+            B.slab = S.tb;
+            B.work_counter = S.counters + CTR_TB;
+            B.status = &S.info->status;
+            B.dp = S.tplan;
+            if ((rc = launch_traceback_variant(v, fma, B, x.tb_blocks[v], st))) return rc;
+            if (v < N_TB16_VARIANTS && (rc = launch_tb_walk_variant(v, B, x.walk_blocks[v], st))) return rc;
         }
     }
-    return bp;
+    if (timing && cuda_failed(cudaEventRecord(x.phase[3], st))) return SW_ERR_CUDA;
+    return SW_OK;
 }
 
 int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scoring_t *scoring,
@@ -294,302 +419,35 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
     int rc = device_state(&ds, st);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(ds->mu);
-    if (ds->last_recorded && cuda_failed(cudaStreamWaitEvent(st, ds->last_done, 0))) return SW_ERR_CUDA;
-
     const Scoring sc{scoring->match, scoring->mismatch, scoring->gap_open, scoring->gap_extend};
-    const size_t nh = (size_t)N_CLASS * N_NBUCKET;
-    size_t off = 0;
-    const size_t o_keys = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
-    const size_t o_order = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
-    const size_t o_hist = off; off = align_up(off + sizeof(int32_t) * nh, 256);
-    const size_t o_bstart = off; off = align_up(off + sizeof(int32_t) * nh, 256);
-    const size_t o_cursor = off; off = align_up(off + sizeof(int32_t) * nh, 256);
-    const size_t o_info = off; off = align_up(off + sizeof(ClassInfo), 256);
-    const size_t o_counters = off; off = align_up(off + sizeof(int32_t) * 4 * N_CLASS, 256);
-    const size_t o_tbkeys = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
-    const size_t o_tborder = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
-    const size_t o_tbinfo = off; off = align_up(off + sizeof(TbClassInfo), 256);
-    if ((rc = ensure(ds->fixed, off))) return rc;
-    uint8_t *fx = (uint8_t *)ds->fixed.ptr;
-    int32_t *keys = (int32_t *)(fx + o_keys), *order = (int32_t *)(fx + o_order);
-    int32_t *hist = (int32_t *)(fx + o_hist), *bstart = (int32_t *)(fx + o_bstart);
-    int32_t *cursor = (int32_t *)(fx + o_cursor), *counters = (int32_t *)(fx + o_counters);
-    ClassInfo *info = (ClassInfo *)(fx + o_info);
-    int32_t *tb_keys = (int32_t *)(fx + o_tbkeys), *tb_order = (int32_t *)(fx + o_tborder);
-    TbClassInfo *tbinfo = (TbClassInfo *)(fx + o_tbinfo);
-    ds->last_status = &info->status;
-
-    ds->timed_cells_valid = false;
-    if (ds->timing && cuda_failed(cudaEventRecord(ds->phase[0], st))) return SW_ERR_CUDA;
-    if (cuda_failed(cudaMemsetAsync(hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
-    if (cuda_failed(cudaMemsetAsync(info, 0, sizeof(ClassInfo), st))) return SW_ERR_CUDA;
-    if (cuda_failed(cudaMemsetAsync(counters, 0, sizeof(int32_t) * 4 * N_CLASS, st))) return SW_ERR_CUDA;
-    if ((rc = launch_classify(ps, n_reads, n_pairs, sc, g_score_mode.load() == SW_SCORE_INT32, keys, hist, bstart,
-                              cursor, info, order, out_score,
-                              out_end, cig ? cig->n_ops : nullptr, st)))
-        return rc;
-    if (cuda_failed(cudaMemcpyAsync(ds->info_host, info, sizeof(ClassInfo), cudaMemcpyDeviceToHost, st)))
-        return SW_ERR_CUDA;
-    if (cuda_failed(cudaStreamSynchronize(st))) return SW_ERR_CUDA;
-    const ClassInfo ci = *ds->info_host;
-    if (ci.status) return status_to_code(ci.status);
-
-    // class ranges in the sorted order, plans and scratch needs
-    struct ClassRun {
-        int cls, mode;
-        int64_t start, count;
-        int32_t max_m, max_n;
-        Plan plan;
-        int score_blocks;
-        size_t bnd_bytes_group;
-        size_t bnd_offset;  // of this class's boundary scratch in the dynamic buffer
-    };
-    std::vector<ClassRun> runs;
-    int64_t pos = 0;
-    size_t need_dyn = 0;
-    for (int cls = 0; cls < N_CLASS; ++cls) {
-        const int32_t cnt = ci.count[cls];
-        if (!cnt) continue;
-        ClassRun r{};
-        r.cls = cls;
-        r.mode = cls / N_MCLASS;
-        r.start = pos;
-        r.count = cnt;
-        r.max_m = ci.max_m[cls];
-        r.max_n = ci.max_n[cls];
-        pos += cnt;
-        r.plan = choose_plan(r.mode, r.max_m, (int64_t)sc.ma * std::min(r.max_m, r.max_n));
-        int regs = 0, bps = 0;
-        if ((rc = score_kernel_regs(r.plan.rows, r.mode, &regs, &bps, kThreads))) return rc;
-        if (bps < 1) return SW_ERR_INTERNAL;
-        const int G = 32 / r.plan.lanes;
-        const int per_warp = G * (r.mode == MODE_I32 ? 1 : 2);
-        const int64_t warps_needed = (cnt + per_warp - 1) / per_warp;
-        const int64_t wpb = kThreads / 32;
-        int64_t blocks = std::min<int64_t>((warps_needed + wpb - 1) / wpb, (int64_t)bps * ds->sm_count);
-        r.score_blocks = (int)std::max<int64_t>(blocks, 1);
-        const int chunks = (r.max_m + r.plan.lanes * r.plan.rows - 1) / (r.plan.lanes * r.plan.rows);
-        r.bnd_bytes_group = chunks > 1 ? (size_t)2 * r.max_n * 2 * sizeof(uint32_t) : 0;
-        // classes run concurrently: each gets its own boundary scratch
-        r.bnd_offset = need_dyn;
-        need_dyn += align_up(r.bnd_bytes_group * (size_t)r.score_blocks * wpb * G, 256);
-        runs.push_back(r);
-    }
-    if ((rc = ensure(ds->dyn, std::max<size_t>(need_dyn, 256)))) return rc;
-
-    if (ds->timing && cuda_failed(cudaEventRecord(ds->phase[1], st))) return SW_ERR_CUDA;
-    // with a CIGAR, the score kernels' epilogue also writes the traceback
-    // cost keys and the class table the traceback is sized from
+    Scratch S{};
+    const size_t fixed_bytes = fixed_layout(n_pairs, nullptr, S);
+    const int64_t bnd_bytes = std::min(kScoreBndMax, std::max(kScoreBndMin, n_pairs * kScoreBndPerPair));
+    int64_t tb_bytes = 0;
     if (cig) {
-        if (cuda_failed(cudaMemsetAsync(hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
-        if (cuda_failed(cudaMemsetAsync(tbinfo, 0, sizeof(TbClassInfo), st))) return SW_ERR_CUDA;
-        if (cuda_failed(cudaMemsetAsync(tb_keys, 0xFF, sizeof(int32_t) * n_pairs, st))) return SW_ERR_CUDA;
-    }
-    // one launch per class; several classes fork onto the auxiliary streams
-    const int n_aux_score = runs.size() > 1 ? (int)std::min<size_t>(runs.size(), kAuxStreams) : 0;
-    if (n_aux_score && (rc = fork_streams(ds, st, n_aux_score))) return rc;
-    for (size_t ri = 0; ri < runs.size(); ++ri) {
-        const ClassRun &r = runs[ri];
-        const cudaStream_t cs = n_aux_score ? ds->aux[ri % n_aux_score] : st;
-        ScoreLaunch L{};
-        L.ps = ps;
-        L.sc = sc;
-        L.order = order + r.start;
-        L.n_items = r.count;
-        L.lanes = r.plan.lanes;
-        L.out_score = out_score;
-        L.out_end = out_end;
-        L.boundary = r.bnd_bytes_group ? (uint8_t *)ds->dyn.ptr + r.bnd_offset : nullptr;
-        L.boundary_group_bytes = (int64_t)r.bnd_bytes_group;
-        L.work_counter = counters + r.cls;
-        L.status = &info->status;
-        if (cig) {
-            L.cls = r.cls;
-            L.tb_keys = tb_keys;
-            L.tb_hist = hist;
-            L.tb_info = tbinfo;
-            L.small_slab_words = kSmallSlabWords;
-        }
-        if ((rc = launch_score(r.plan.rows, r.mode, L, r.score_blocks, kThreads, cs))) return rc;
-    }
-    if (n_aux_score && (rc = join_streams(ds, st, n_aux_score))) return rc;
-    if (ds->timing && cuda_failed(cudaEventRecord(ds->phase[2], st))) return SW_ERR_CUDA;
-    if (cig) {
-        // order each class by traceback cost, then size the slabs from the
-        // per-class maxima (a second, small read-back)
-        TbParams P{ps, sc, out_score, out_end, cig->ops, cig->offsets, cig->n_ops, kTbLanes, kSmallSlabWords};
-        if ((rc = launch_scan_scatter(tb_keys, n_pairs, info->count, hist, bstart, cursor, tb_order, st))) return rc;
-        if (cuda_failed(cudaMemcpyAsync(ds->tbinfo_host, tbinfo, sizeof(TbClassInfo), cudaMemcpyDeviceToHost, st)))
-            return SW_ERR_CUDA;
-        if (cuda_failed(cudaStreamSynchronize(st))) return SW_ERR_CUDA;
-        const TbClassInfo ti = *ds->tbinfo_host;
-        int tbps = 0;
-        if ((rc = traceback_kernel_occupancy(&tbps, kThreads, false, 1))) return rc;
-        const bool allow16 = g_tb_mode.load() == SW_TB_AUTO;
-        if (!ds->tile16_budget) {
-            // once per device: a share of the memory free at the first call
-            // (plus what the dynamic buffer already holds)
+        if (!ds->tb_cap) {
+            // once per stream: a share of the memory free at its first traceback
             size_t free_b = 0, total_b = 0;
-            ds->tile16_budget = (size_t)4 << 30;
+            ds->tb_cap = kTbCapMin;
             if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
-                ds->tile16_budget = std::max(ds->tile16_budget,
-                                             std::min(kTile16Cap, (size_t)(kTile16FreeShare * (free_b + ds->dyn.bytes))));
+                ds->tb_cap = std::max(kTbCapMin, std::min(kTbCapMax, (int64_t)(kTbFreeShare * (double)free_b)));
         }
-        const size_t tile16_budget = ds->tile16_budget;
-        const int64_t wpb = kThreads / 32;
-        struct TbRun {
-            int64_t start, count;
-            int64_t slab_words, bnd_ints;  // per group, or per lane when tiled
-            int32_t wcap;
-            bool tiled, packed16;
-            int blocks;
-            int64_t round_tasks;  // 16-bit kernel: tasks (64 pairs) per round
-            int lanes;            // int32 kernels: lanes per pair
-            size_t need;          // scratch bytes of one round
-            size_t offset;        // of its scratch in the dynamic buffer
-            bool one_round;
-            int cls, part;
-        };
-        std::vector<TbRun> tbr;
-        size_t need = 0;
-        for (const ClassRun &r : runs) {
-            const int64_t big = ti.n_big[r.cls];
-            const int64_t max_need = std::max<int64_t>(ti.max_need[r.cls], 1);
-            const int64_t parts[2][2] = {{r.start, big}, {r.start + big, r.count - big}};
-            for (int part = 0; part < 2; ++part) {
-                const int64_t cnt = parts[part][1];
-                if (cnt <= 0) continue;
-                TbRun t{};
-                t.start = parts[part][0];
-                t.count = cnt;
-                const int rc = kTbLanes * TB_ROWS;
-                const int64_t chunks = (r.max_m + rc - 1) / rc;
-                t.wcap = (int32_t)std::max<int64_t>(ti.max_wcap[part][r.cls], 1);
-                // 16-bit halves (two pairs per lane group) wherever the class's
-                // score bound allows it; else int32 lanes.  T lanes share a
-                // pair: one where a lane's tile (every chunk at the widest
-                // window) stays small, else a power of two covering the
-                // longest read in a few chunks (kTbChunks16, kTbChunks32), so
-                // that one pair's cells do not run on a single lane.  A T-lane
-                // chunk window is at most 8 (T - 1) wider than the one-lane
-                // windows the key pass measured.
-                const int64_t wcap4 = (t.wcap + 3) / 4 * 4;
-                t.packed16 = allow16 && r.mode != MODE_I32;
-                int Tl = 1;
-                while (Tl < 32 && (int64_t)Tl * 8 * (t.packed16 ? kTbChunks16 : kTbChunks32) < r.max_m) Tl *= 2;
-                const bool one_lane16 = chunks * wcap4 * 2 <= kTiledLaneWords16;
-                t.tiled = !t.packed16 && chunks * t.wcap <= kTiledLaneWords;
-                t.lanes = (t.packed16 && one_lane16) || t.tiled ? 1 : Tl;
-                if (t.packed16) {
-                    const int T = t.lanes;
-                    const int64_t chunks_t = (r.max_m + 8 * T - 1) / (8 * T);
-                    t.wcap = (int32_t)(t.wcap + 8 * (T - 1));
-                    const int64_t s4 = (t.wcap + T - 1 + 3) / 4;
-                    t.slab_words = chunks_t * s4 * 8;                                      // per lane
-                    t.bnd_ints = chunks_t > 1 ? (int64_t)(32 / T) * 2 * t.wcap : 0;  // per warp: one row
-                } else if (t.tiled) {
-                    t.slab_words = chunks * t.wcap;
-                    t.bnd_ints = chunks > 1 ? (int64_t)2 * 2 * t.wcap : 0;
-                } else {
-                    const int T = t.lanes;
-                    const int64_t chunks_t = (r.max_m + 8 * T - 1) / (8 * T);
-                    const int64_t wcap_t = t.wcap + 8 * (T - 1);
-                    t.slab_words = T == 1 ? (part == 0 ? max_need : std::min<int64_t>(max_need, kSmallSlabWords))
-                                          : chunks_t * wcap_t * T;
-                    t.bnd_ints = chunks_t > 1 ? (int64_t)2 * 2 * wcap_t : 0;
-                }
-                const int per_warp = t.packed16 ? 64 / t.lanes : 32 / t.lanes;
-                if (t.packed16) {
-                    // a tile per task, kept until the walk: tasks go in rounds
-                    // that fit the tile budget
-                    int occ = 0;
-                    const int orc = traceback_kernel_occupancy(&occ, kThreads, true, t.lanes);
-                    if (orc) return orc;
-                    const size_t tile_bytes = (size_t)32 * t.slab_words * 4;
-                    const int64_t tasks = (cnt + per_warp - 1) / per_warp;
-                    t.round_tasks = std::max<int64_t>(1, std::min<int64_t>(tasks, (int64_t)(tile16_budget / tile_bytes)));
-                    const size_t bnd_per_block = (size_t)wpb * t.bnd_ints * 4;
-                    int64_t blocks = std::min<int64_t>((t.round_tasks + wpb - 1) / wpb, (int64_t)std::max(occ, 1) * ds->sm_count);
-                    t.blocks = (int)std::max<int64_t>(blocks, 1);
-                    t.need = tile_bytes * (size_t)t.round_tasks + bnd_per_block * (size_t)t.blocks;
-                    t.one_round = t.round_tasks == tasks;
-                } else {
-                    const size_t per_block = (size_t)wpb * (32 / t.lanes) * (t.slab_words + t.bnd_ints) * 4;
-                    int64_t blocks = std::min<int64_t>(((cnt + per_warp - 1) / per_warp + wpb - 1) / wpb,
-                                                       (int64_t)std::max(tbps, 1) * ds->sm_count);
-                    blocks = std::min<int64_t>(blocks, (int64_t)(kSlabBudget / std::max<size_t>(per_block, 1)));
-                    t.blocks = (int)std::max<int64_t>(blocks, 1);
-                    t.need = per_block * (size_t)t.blocks;
-                    t.one_round = true;
-                }
-                t.cls = r.cls;
-                t.part = part;
-                tbr.push_back(t);
-            }
-        }
-        // Parts run concurrently on the auxiliary streams, each in its own
-        // scratch region, when all of them fit one round of the budget;
-        // otherwise one after another, each from the start of the buffer.
-        size_t total = 0;
-        bool all_one_round = true;
-        for (TbRun &t : tbr) {
-            t.offset = total;
-            total += align_up(t.need, 256);
-            all_one_round = all_one_round && t.one_round;
-            need = std::max(need, t.need);
-        }
-        // (measured: on a one-class batch the big and main parts slowed each
-        // other down, on the uneven batch it gained 0.1 %, so parts run in order)
-        const bool concurrent = kConcurrentTbParts && tbr.size() > 1 && all_one_round &&
-                                total <= std::max(tile16_budget, need);
-        if (!concurrent)
-            for (TbRun &t : tbr) t.offset = 0;
-        if ((rc = ensure(ds->dyn, std::max<size_t>(concurrent ? total : need, 256)))) return rc;
-        ds->tb_split[0] = ds->tb_split[1] = 0;
-        for (const TbRun &t : tbr) ds->tb_split[t.packed16 ? 0 : 1] += t.count;
-        const int n_aux_tb = concurrent ? (int)std::min<size_t>(tbr.size(), kAuxStreams) : 0;
-        if (n_aux_tb && (rc = fork_streams(ds, st, n_aux_tb))) return rc;
-        for (size_t ti2 = 0; ti2 < tbr.size(); ++ti2) {
-            const TbRun &t = tbr[ti2];
-            const cudaStream_t ts = n_aux_tb ? ds->aux[ti2 % std::max(n_aux_tb, 1)] : st;
-            uint8_t *region = (uint8_t *)ds->dyn.ptr + t.offset;
-            TracebackLaunch B{};
-            B.P = P;
-            B.P.lanes = t.lanes;
-            B.lanes = t.lanes;
-            B.slab = (uint32_t *)region;
-            B.slab_group_words = t.slab_words;
-            B.boundary_group_ints = t.bnd_ints;
-            B.wcap = t.wcap;
-            B.tiled = t.tiled;
-            B.packed16 = t.packed16;
-            B.work_counter = counters + 2 * N_CLASS + 2 * t.cls + t.part;
-            B.status = &info->status;
-            if (t.packed16) {
-                const int64_t round_items = t.round_tasks * (64 / t.lanes);
-                const size_t tiles = (size_t)t.round_tasks * 32 * t.slab_words;
-                B.boundary = (int32_t *)region + tiles;
-                for (int64_t r0 = 0; r0 < t.count; r0 += round_items) {
-                    B.order = tb_order + t.start + r0;
-                    B.n_items = std::min<int64_t>(round_items, t.count - r0);
-                    if (r0 > 0 && cuda_failed(cudaMemsetAsync(B.work_counter, 0, sizeof(int32_t), ts)))
-                        return SW_ERR_CUDA;
-                    if ((rc = launch_traceback(B, t.blocks, kThreads, ts))) return rc;
-                }
-            } else {
-                B.order = tb_order + t.start;
-                B.n_items = t.count;
-                const size_t slab_total = (size_t)t.blocks * wpb * (32 / t.lanes) * t.slab_words;
-                B.boundary = (int32_t *)region + slab_total;
-                if ((rc = launch_traceback(B, t.blocks, kThreads, ts))) return rc;
-            }
-        }
-        if (n_aux_tb && (rc = join_streams(ds, st, n_aux_tb))) return rc;
+        tb_bytes = std::min(ds->tb_cap, std::max(kTbMin, n_pairs * kTbPerPair));
     }
-    if (ds->timing && cuda_failed(cudaEventRecord(ds->phase[3], st))) return SW_ERR_CUDA;
+    if ((rc = ensure_on(ds->fixed, fixed_bytes, st))) return rc;
+    if ((rc = ensure_on(ds->dyn, (size_t)(bnd_bytes + tb_bytes), st))) return rc;
+    fixed_layout(n_pairs, (uint8_t *)ds->fixed.ptr, S);
+    S.score_bnd = (uint8_t *)ds->dyn.ptr;
+    S.score_bnd_bytes = bnd_bytes;
+    S.tb = (uint32_t *)((uint8_t *)ds->dyn.ptr + bnd_bytes);
+    S.tb_bytes = tb_bytes;
+    ds->last_status = &S.info->status;
+    ds->timed_cells_valid = false;
+    rc = enqueue_core(ps, n_reads, n_pairs, sc, g_score_mode.load() == SW_SCORE_INT32,
+                      g_tb_mode.load() == SW_TB_AUTO, out_score, out_end, cig, S, nullptr, ds->x, st);
+    if (rc) return rc;
+    if (cig) ds->last_tplan = S.tplan;
     ds->timed_cells_valid = ds->timing;
-    if (cuda_failed(cudaEventRecord(ds->last_done, st))) return SW_ERR_CUDA;
-    ds->last_recorded = true;
     return SW_OK;
 }
 
@@ -617,21 +475,10 @@ int check_common(const void *reads, const int64_t *roff, const void *wins, const
 }
 
 // ---------------------------------------------------------------------------
-// Plans: the launch decisions of one batch shape, taken once, so that the
-// execution itself is a fixed sequence of launches (capturable).
-
-struct PlanScoreRun {
-    int cls, mode, rows, lanes, blocks;
-    int64_t start, count;
-    size_t bnd_bytes_group, bnd_offset;
-};
-
-struct PlanTbRun {
-    int cls, lanes, blocks;
-    bool packed16, tiled;
-    int64_t start, count, slab_words, bnd_ints, round_tasks;
-    int32_t wcap;
-};
+// Plans: one batch shape classified once on the host, its scratch allocated
+// for the worst case of that shape, and every execution the same fixed
+// sequence as sw_batch_align plus a device check that the batch still has
+// the plan's shape.
 
 }  // namespace
 }  // namespace swgb
@@ -643,62 +490,106 @@ struct sw_plan {
     swgb::Scoring sc{};
     bool cigar = false;
     bool force_i32 = false;   // the score mode setting at creation
+    bool allow16 = true;      // the traceback mode setting at creation
     swgb::Buffer fixed, dyn;  // owned: a captured graph keeps pointing here
-    int32_t *keys = nullptr, *order = nullptr, *hist = nullptr, *bstart = nullptr, *cursor = nullptr;
-    int32_t *counters = nullptr, *tb_keys = nullptr, *tb_order = nullptr, *expect = nullptr;
-    swgb::ClassInfo *info = nullptr;
-    swgb::TbClassInfo *tbinfo = nullptr;
-    std::vector<swgb::PlanScoreRun> sruns;
-    std::vector<swgb::PlanTbRun> truns;
-    size_t tb_tiles_bytes = 0;  // offset of the traceback boundary rows in dyn
+    swgb::Scratch S{};
+    swgb::ExecCtx x;          // owned auxiliary streams and events (a capture creates nothing)
 };
 
 namespace swgb {
 namespace {
 
+// Worst-case scratch of a shape: every window may lie inside the band, so
+// a chunk window is at most the class's longest window (and smaller ones may
+// pick other traceback kernels, whose slots are bounded too).
+void plan_budgets(const ClassInfo &ci, const PlanParams &pp, bool cigar, int64_t &bnd_bytes, int64_t &tb_bytes)
+{
+    int64_t slot_s[N_SCORE_VARIANTS] = {};
+    for (int c = 0; c < N_CLASS; ++c) {
+        if (!ci.count[c]) continue;
+        const int mode = c / N_MCLASS;
+        const int32_t mm = ci.max_m[c], mn = ci.max_n[c];
+        int lanes = 1, ri = 0;
+        score_plan_of(mode, mm, (int64_t)pp.sc.ma * std::min(mm, mn), pp.ov, pp.n_overrides, lanes, ri);
+        const int rows = score_rows_at(ri);
+        if ((mm + lanes * rows - 1) / (lanes * rows) > 1) {
+            const int v = ri * N_MODES + mode;
+            slot_s[v] = std::max<int64_t>(slot_s[v], (int64_t)(32 / lanes) * 16 * mn);
+        }
+    }
+    int nb = 0;
+    int64_t per = 0;
+    for (int v = 0; v < N_SCORE_VARIANTS; ++v)
+        if (slot_s[v]) {
+            ++nb;
+            per = std::max(per, slot_s[v] * pp.score_warps[v]);
+        }
+    bnd_bytes = std::max<int64_t>(nb * (int64_t)align_up(per, 256), 256);
+    tb_bytes = 0;
+    if (!cigar) return;
+    // per traceback launch: its widest boundary row, tile and slot over the
+    // classes it may serve, and the pool all of its tasks would fill
+    int64_t bnd_v[N_TB_VARIANTS] = {}, slot_v[N_TB_VARIANTS] = {}, pool_v[N_TB_VARIANTS] = {};
+    for (int c = 0; c < N_CLASS; ++c) {
+        if (!ci.count[c]) continue;
+        const int mode = c / N_MCLASS;
+        const int32_t mm = ci.max_m[c], mn = std::max(ci.max_n[c], 1);
+        const int64_t chunks = (mm + TB_ROWS - 1) / TB_ROWS;
+        // the widest window, and the widest below each kernel switch
+        const int64_t cand[3] = {mn, std::min<int64_t>(mn, kTiledLaneWords16 / (2 * chunks) / 4 * 4),
+                                 std::min<int64_t>(mn, kTiledLaneWords / chunks)};
+        for (int64_t w : cand) {
+            if (w < 1) continue;
+            for (int part = 0; part < 2; ++part) {
+                TbPartPlan t{};
+                const int64_t slot = tb_part_shape(mode, pp.allow16 != 0, mm, chunks * w, (int32_t)w, part,
+                                                   pp.small_slab_words, t);
+                const int v = t.variant;
+                if (v < N_TB16_VARIANTS) {
+                    const int64_t tile = (32 * t.slab_words + 63) & ~(int64_t)63;
+                    const int64_t tasks = (ci.count[c] + 2 * (32 >> v) - 1) / (2 * (32 >> v));
+                    bnd_v[v] = std::max(bnd_v[v], (t.bnd_ints + 63) & ~(int64_t)63);
+                    slot_v[v] = std::max(slot_v[v], tile);
+                    pool_v[v] = std::max(pool_v[v], tasks * tile);  // one candidate per class counts
+                } else {
+                    slot_v[v] = std::max(slot_v[v], (slot + 63) & ~(int64_t)63);
+                }
+            }
+        }
+    }
+    const int64_t cap = kTbCapMax / 4;  // words
+    for (int v = 0; v < N_TB_VARIANTS; ++v) {
+        if (!slot_v[v]) continue;
+        const int64_t w = pp.tb_warps[v];
+        int64_t words;
+        if (v < N_TB16_VARIANTS)
+            words = std::min(w * bnd_v[v], cap) + std::max({std::min(pool_v[v] + slot_v[v], cap),
+                                                            std::min(w * slot_v[v], cap), slot_v[v]});
+        else
+            words = std::max(std::min(w * slot_v[v], cap), 4 * slot_v[v]);
+        tb_bytes = std::max(tb_bytes, 4 * words);
+    }
+}
+
 int plan_build(sw_plan *pl, DeviceState *ds, cudaStream_t st)
 {
     int rc = SW_OK;
-    const size_t nh = (size_t)N_CLASS * N_NBUCKET;
     const int64_t n_pairs = pl->n_pairs;
-    size_t off = 0;
-    const size_t o_keys = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
-    const size_t o_order = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
-    const size_t o_hist = off; off = align_up(off + sizeof(int32_t) * nh, 256);
-    const size_t o_bstart = off; off = align_up(off + sizeof(int32_t) * nh, 256);
-    const size_t o_cursor = off; off = align_up(off + sizeof(int32_t) * nh, 256);
-    const size_t o_info = off; off = align_up(off + sizeof(ClassInfo), 256);
-    const size_t o_counters = off; off = align_up(off + sizeof(int32_t) * 4 * N_CLASS, 256);
-    const size_t o_tbkeys = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
-    const size_t o_tborder = off; off = align_up(off + sizeof(int32_t) * n_pairs, 256);
-    const size_t o_tbinfo = off; off = align_up(off + sizeof(TbClassInfo), 256);
-    const size_t o_expect = off; off = align_up(off + sizeof(int32_t) * 3 * N_CLASS, 256);
-    if ((rc = ensure(pl->fixed, off))) return rc;
-    uint8_t *fx = (uint8_t *)pl->fixed.ptr;
-    pl->keys = (int32_t *)(fx + o_keys);
-    pl->order = (int32_t *)(fx + o_order);
-    pl->hist = (int32_t *)(fx + o_hist);
-    pl->bstart = (int32_t *)(fx + o_bstart);
-    pl->cursor = (int32_t *)(fx + o_cursor);
-    pl->info = (ClassInfo *)(fx + o_info);
-    pl->counters = (int32_t *)(fx + o_counters);
-    pl->tb_keys = (int32_t *)(fx + o_tbkeys);
-    pl->tb_order = (int32_t *)(fx + o_tborder);
-    pl->tbinfo = (TbClassInfo *)(fx + o_tbinfo);
-    pl->expect = (int32_t *)(fx + o_expect);
-
+    Scratch &S = pl->S;
+    if ((rc = ensure(pl->fixed, fixed_layout(n_pairs, nullptr, S)))) return rc;
+    fixed_layout(n_pairs, (uint8_t *)pl->fixed.ptr, S);
     // classify once (it reads offsets only) and read the class table back
-    if (cuda_failed(cudaMemsetAsync(pl->hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
-    if (cuda_failed(cudaMemsetAsync(pl->info, 0, sizeof(ClassInfo), st))) return SW_ERR_CUDA;
-    int32_t *tmp_score = pl->tb_keys, *tmp_end = nullptr;  // empty-window outputs go to scratch
+    const size_t nh = (size_t)N_CLASS * N_NBUCKET;
+    if (cuda_failed(cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemsetAsync(S.info, 0, sizeof(ClassInfo), st))) return SW_ERR_CUDA;
+    int32_t *tmp_score = S.tb_keys, *tmp_end = nullptr;  // empty-window outputs go to scratch
     if ((rc = ensure(pl->dyn, sizeof(int32_t) * 2 * std::max<int64_t>(n_pairs, 1)))) return rc;
     tmp_end = (int32_t *)pl->dyn.ptr;
-    if ((rc = launch_classify(pl->ps, pl->n_reads, n_pairs, pl->sc, pl->force_i32, pl->keys, pl->hist, pl->bstart,
-                              pl->cursor,
-                              pl->info, pl->order, tmp_score, tmp_end, nullptr, st)))
+    if ((rc = launch_classify(pl->ps, pl->n_reads, n_pairs, pl->sc, pl->force_i32, S.keys, S.hist, S.bstart,
+                              S.cursor, S.info, S.order, tmp_score, tmp_end, nullptr, st)))
         return rc;
     ClassInfo ci;
-    if (cuda_failed(cudaMemcpyAsync(&ci, pl->info, sizeof(ClassInfo), cudaMemcpyDeviceToHost, st)))
+    if (cuda_failed(cudaMemcpyAsync(&ci, S.info, sizeof(ClassInfo), cudaMemcpyDeviceToHost, st)))
         return SW_ERR_CUDA;
     if (cuda_failed(cudaStreamSynchronize(st))) return SW_ERR_CUDA;
     if (ci.status) return status_to_code(ci.status);
@@ -707,176 +598,25 @@ int plan_build(sw_plan *pl, DeviceState *ds, cudaStream_t st)
         std::memcpy(ex.data(), ci.count, sizeof(int32_t) * N_CLASS);
         std::memcpy(ex.data() + N_CLASS, ci.max_m, sizeof(int32_t) * N_CLASS);
         std::memcpy(ex.data() + 2 * N_CLASS, ci.max_n, sizeof(int32_t) * N_CLASS);
-        if (cuda_failed(cudaMemcpy(pl->expect, ex.data(), sizeof(int32_t) * 3 * N_CLASS, cudaMemcpyHostToDevice)))
+        if (cuda_failed(cudaMemcpy(S.expect, ex.data(), sizeof(int32_t) * 3 * N_CLASS, cudaMemcpyHostToDevice)))
             return SW_ERR_CUDA;
     }
-
-    // score launches, as sw_batch_align plans them
-    const int64_t wpb = kThreads / 32;
-    int64_t pos = 0;
-    size_t score_scratch = 0;
-    for (int cls = 0; cls < N_CLASS; ++cls) {
-        const int32_t cnt = ci.count[cls];
-        if (!cnt) continue;
-        PlanScoreRun r{};
-        r.cls = cls;
-        r.mode = cls / N_MCLASS;
-        r.start = pos;
-        r.count = cnt;
-        pos += cnt;
-        const int32_t max_m = ci.max_m[cls], max_n = ci.max_n[cls];
-        const Plan plan = choose_plan(r.mode, max_m, (int64_t)pl->sc.ma * std::min(max_m, max_n));
-        r.rows = plan.rows;
-        r.lanes = plan.lanes;
-        int regs = 0, bps = 0;
-        if ((rc = score_kernel_regs(r.rows, r.mode, &regs, &bps, kThreads))) return rc;
-        if (bps < 1) return SW_ERR_INTERNAL;
-        const int G = 32 / r.lanes;
-        const int per_warp = G * (r.mode == MODE_I32 ? 1 : 2);
-        const int64_t warps_needed = (cnt + per_warp - 1) / per_warp;
-        r.blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps_needed + wpb - 1) / wpb, (int64_t)bps * ds->sm_count));
-        const int chunks = (max_m + r.lanes * r.rows - 1) / (r.lanes * r.rows);
-        r.bnd_bytes_group = chunks > 1 ? (size_t)2 * max_n * 2 * sizeof(uint32_t) : 0;
-        r.bnd_offset = score_scratch;
-        score_scratch += align_up(r.bnd_bytes_group * (size_t)r.blocks * wpb * G, 256);
-        pl->sruns.push_back(r);
-    }
-
-    // traceback launches for the worst case: any window may be inside the
-    // band, so a chunk window is at most the class's longest window
-    size_t tb_need = 0;
-    if (pl->cigar) {
-        if (!ds->tile16_budget) {
-            size_t free_b = 0, total_b = 0;
-            ds->tile16_budget = (size_t)4 << 30;
-            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
-                ds->tile16_budget = std::max(ds->tile16_budget,
-                                             std::min(kTile16Cap, (size_t)(kTile16FreeShare * (free_b + ds->dyn.bytes))));
-        }
-        int tbps = 0;
-        if ((rc = traceback_kernel_occupancy(&tbps, kThreads, false, 1))) return rc;
-        const bool allow16 = g_tb_mode.load() == SW_TB_AUTO;
-        for (const PlanScoreRun &r : pl->sruns) {
-            PlanTbRun t{};
-            t.cls = r.cls;
-            t.start = r.start;
-            t.count = r.count;
-            const int32_t max_m = ci.max_m[r.cls], max_n = ci.max_n[r.cls];
-            const int64_t chunks = (max_m + TB_ROWS - 1) / TB_ROWS;
-            const int64_t wcap1 = max_n;
-            const int64_t wcap4 = (wcap1 + 3) / 4 * 4;
-            t.packed16 = allow16 && r.mode != MODE_I32;
-            int Tl = 1;
-            while (Tl < 32 && (int64_t)Tl * 8 * (t.packed16 ? kTbChunks16 : kTbChunks32) < max_m) Tl *= 2;
-            t.tiled = !t.packed16 && chunks * wcap1 <= kTiledLaneWords;
-            t.lanes = (t.packed16 && chunks * wcap4 * 2 <= kTiledLaneWords16) || t.tiled ? 1 : Tl;
-            const int T = t.lanes;
-            const int64_t chunks_t = (max_m + 8 * T - 1) / (8 * T);
-            const int64_t wcap_t = wcap1 + 8 * (T - 1);
-            t.wcap = (int32_t)(t.packed16 ? wcap_t : wcap1);
-            if (t.packed16) {
-                const int64_t s4 = (wcap_t + T - 1 + 3) / 4;
-                t.slab_words = chunks_t * s4 * 8;
-                t.bnd_ints = chunks_t > 1 ? (int64_t)(32 / T) * 2 * wcap_t : 0;
-                int occ = 0;
-                if ((rc = traceback_kernel_occupancy(&occ, kThreads, true, T))) return rc;
-                const size_t tile_bytes = (size_t)32 * t.slab_words * 4;
-                const int per_warp = 64 / T;
-                const int64_t tasks = (t.count + per_warp - 1) / per_warp;
-                t.round_tasks = std::max<int64_t>(1, std::min<int64_t>(tasks, (int64_t)(ds->tile16_budget / tile_bytes)));
-                t.blocks = (int)std::max<int64_t>(1, std::min<int64_t>((t.round_tasks + wpb - 1) / wpb, (int64_t)std::max(occ, 1) * ds->sm_count));
-                tb_need = std::max(tb_need, tile_bytes * (size_t)t.round_tasks + (size_t)wpb * t.bnd_ints * 4 * t.blocks);
-            } else {
-                if (t.tiled) {
-                    t.slab_words = chunks * wcap1;
-                    t.bnd_ints = chunks > 1 ? 4 * wcap1 : 0;
-                } else {
-                    t.slab_words = chunks_t * wcap_t * T;
-                    t.bnd_ints = chunks_t > 1 ? 4 * wcap_t : 0;
-                }
-                const int per_warp = 32 / T;
-                const size_t per_block = (size_t)wpb * per_warp * (t.slab_words + t.bnd_ints) * 4;
-                int64_t blocks = std::min<int64_t>(((t.count + per_warp - 1) / per_warp + wpb - 1) / wpb,
-                                                   (int64_t)std::max(tbps, 1) * ds->sm_count);
-                blocks = std::min<int64_t>(blocks, (int64_t)(kSlabBudget / std::max<size_t>(per_block, 1)));
-                t.blocks = (int)std::max<int64_t>(blocks, 1);
-                t.round_tasks = 0;
-                tb_need = std::max(tb_need, per_block * (size_t)t.blocks);
-            }
-            pl->truns.push_back(t);
-        }
-    }
-    return ensure(pl->dyn, std::max<size_t>(std::max(score_scratch, tb_need), 256));
+    if ((rc = exec_ctx_init(pl->x, ds->sm_count))) return rc;
+    const PlanParams pp = plan_params(pl->x, pl->sc, pl->allow16, 0, 0);
+    int64_t bnd_bytes = 0, tb_bytes = 0;
+    plan_budgets(ci, pp, pl->cigar, bnd_bytes, tb_bytes);
+    if ((rc = ensure(pl->dyn, (size_t)(bnd_bytes + tb_bytes)))) return rc;
+    S.score_bnd = (uint8_t *)pl->dyn.ptr;
+    S.score_bnd_bytes = bnd_bytes;
+    S.tb = (uint32_t *)((uint8_t *)pl->dyn.ptr + bnd_bytes);
+    S.tb_bytes = tb_bytes;
+    return SW_OK;
 }
 
 int plan_execute(sw_plan *pl, int32_t *out_score, int32_t *out_end, const sw_cigar_t *cig, cudaStream_t st)
 {
-    int rc = SW_OK;
-    const size_t nh = (size_t)N_CLASS * N_NBUCKET;
-    const PairSet &ps = pl->ps;
-    if (cuda_failed(cudaMemsetAsync(pl->hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
-    if (cuda_failed(cudaMemsetAsync(pl->info, 0, sizeof(ClassInfo), st))) return SW_ERR_CUDA;
-    if (cuda_failed(cudaMemsetAsync(pl->counters, 0, sizeof(int32_t) * 4 * N_CLASS, st))) return SW_ERR_CUDA;
-    if ((rc = launch_classify(ps, pl->n_reads, pl->n_pairs, pl->sc, pl->force_i32, pl->keys, pl->hist, pl->bstart,
-                              pl->cursor,
-                              pl->info, pl->order, out_score, out_end, cig ? cig->n_ops : nullptr, st)))
-        return rc;
-    if ((rc = launch_check_counts(pl->info, pl->expect, &pl->info->status, st))) return rc;
-    for (const PlanScoreRun &r : pl->sruns) {
-        ScoreLaunch L{};
-        L.ps = ps;
-        L.sc = pl->sc;
-        L.order = pl->order + r.start;
-        L.n_items = r.count;
-        L.lanes = r.lanes;
-        L.out_score = out_score;
-        L.out_end = out_end;
-        L.boundary = r.bnd_bytes_group ? (uint8_t *)pl->dyn.ptr + r.bnd_offset : nullptr;
-        L.boundary_group_bytes = (int64_t)r.bnd_bytes_group;
-        L.work_counter = pl->counters + r.cls;
-        L.status = &pl->info->status;
-        if ((rc = launch_score(r.rows, r.mode, L, r.blocks, kThreads, st))) return rc;
-    }
-    if (!pl->cigar || !cig) return SW_OK;
-    TbParams P{ps, pl->sc, out_score, out_end, cig->ops, cig->offsets, cig->n_ops, 1, kSmallSlabWords};
-    if (cuda_failed(cudaMemsetAsync(pl->hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
-    if (cuda_failed(cudaMemsetAsync(pl->tbinfo, 0, sizeof(TbClassInfo), st))) return SW_ERR_CUDA;
-    if ((rc = launch_tb_keys(P, pl->n_pairs, pl->keys, pl->tb_keys, pl->hist, pl->tbinfo, st))) return rc;
-    if ((rc = launch_scan_scatter(pl->tb_keys, pl->n_pairs, pl->info->count, pl->hist, pl->bstart, pl->cursor,
-                                  pl->tb_order, st)))
-        return rc;
-    const int64_t wpb = kThreads / 32;
-    for (const PlanTbRun &t : pl->truns) {
-        TracebackLaunch B{};
-        B.P = P;
-        B.P.lanes = t.lanes;
-        B.lanes = t.lanes;
-        B.slab = (uint32_t *)pl->dyn.ptr;
-        B.slab_group_words = t.slab_words;
-        B.boundary_group_ints = t.bnd_ints;
-        B.wcap = t.wcap;
-        B.tiled = t.tiled;
-        B.packed16 = t.packed16;
-        B.work_counter = pl->counters + 2 * N_CLASS + 2 * t.cls;
-        B.status = &pl->info->status;
-        if (t.packed16) {
-            const int64_t round_items = t.round_tasks * (64 / t.lanes);
-            B.boundary = (int32_t *)pl->dyn.ptr + (size_t)t.round_tasks * 32 * t.slab_words;
-            for (int64_t r0 = 0; r0 < t.count; r0 += round_items) {
-                B.order = pl->tb_order + t.start + r0;
-                B.n_items = std::min<int64_t>(round_items, t.count - r0);
-                if (r0 > 0 && cuda_failed(cudaMemsetAsync(B.work_counter, 0, sizeof(int32_t), st)))
-                    return SW_ERR_CUDA;
-                if ((rc = launch_traceback(B, t.blocks, kThreads, st))) return rc;
-            }
-        } else {
-            B.order = pl->tb_order + t.start;
-            B.n_items = t.count;
-            B.boundary = (int32_t *)pl->dyn.ptr + (size_t)t.blocks * wpb * (32 / t.lanes) * t.slab_words;
-            if ((rc = launch_traceback(B, t.blocks, kThreads, st))) return rc;
-        }
-    }
-    return SW_OK;
+    return enqueue_core(pl->ps, pl->n_reads, pl->n_pairs, pl->sc, pl->force_i32, pl->allow16, out_score, out_end,
+                        pl->cigar ? cig : nullptr, pl->S, pl->S.expect, pl->x, st);
 }
 
 }  // namespace
@@ -1004,9 +744,9 @@ int sw_batch_align_host(const uint8_t *reads, const int64_t *read_offsets, const
         cudaGetLastError();  // a pageable pointer is not an error here
     }
     // the copy streams start after what the caller enqueued on st
-    if (cuda_failed(cudaEventRecord(ds->fork_ev, st))) return SW_ERR_CUDA;
-    if (cuda_failed(cudaStreamWaitEvent(ds->copy_in, ds->fork_ev, 0))) return SW_ERR_CUDA;
-    if (cuda_failed(cudaStreamWaitEvent(ds->copy_out, ds->fork_ev, 0))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaEventRecord(ds->x.fork_ev, st))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaStreamWaitEvent(ds->copy_in, ds->x.fork_ev, 0))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaStreamWaitEvent(ds->copy_out, ds->x.fork_ev, 0))) return SW_ERR_CUDA;
     if (!copy_in(0)) return SW_ERR_CUDA;
     for (int64_t c = 0; c < n_chunks; ++c) {
         const int64_t p0 = c * chunk, p1 = std::min<int64_t>(n_pairs, p0 + chunk), np = p1 - p0;
@@ -1119,6 +859,7 @@ int sw_set_plan(int32_t max_read_len, int32_t lanes, int32_t r_rows)
     for (int i = 0; i < N_SCORE_ROWS; ++i) ok |= kScoreRows[i] == r_rows;
     if (!ok) return SW_ERR_INVALID_ARG;
     if ((max_read_len + lanes * r_rows - 1) / (lanes * r_rows) > 1 && lanes != 32) return SW_ERR_INVALID_ARG;
+    if (g_plans.size() >= (size_t)kMaxPlanOverrides) return SW_ERR_UNSUPPORTED;
     g_plans.push_back(PlanOverride{max_read_len, lanes, r_rows});
     std::sort(g_plans.begin(), g_plans.end(),
               [](const PlanOverride &a, const PlanOverride &b) { return a.max_read_len < b.max_read_len; });
@@ -1153,8 +894,12 @@ int sw_last_traceback_split(int64_t *out2)
     const int rc = last_state(&ds);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(ds->mu);
-    out2[0] = ds->tb_split[0];
-    out2[1] = ds->tb_split[1];
+    out2[0] = out2[1] = 0;
+    if (!ds->last_tplan) return SW_OK;
+    // the split is planned on the device: wait for it
+    if (cuda_failed(cudaDeviceSynchronize())) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemcpy(out2, ds->last_tplan->split, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost)))
+        return SW_ERR_CUDA;
     return SW_OK;
 }
 
@@ -1230,6 +975,7 @@ int sw_plan_create(const int64_t *read_offsets, int64_t n_reads, const int64_t *
     pl->sc = Scoring{scoring->match, scoring->mismatch, scoring->gap_open, scoring->gap_extend};
     pl->cigar = with_cigar != 0;
     pl->force_i32 = g_score_mode.load() == SW_SCORE_INT32;
+    pl->allow16 = g_tb_mode.load() == SW_TB_AUTO;
     {
         std::lock_guard<std::mutex> lk(ds->mu);
         rc = plan_build(pl, ds, (cudaStream_t)stream);
@@ -1261,7 +1007,7 @@ int sw_plan_status(sw_plan_t *plan, sw_stream_t stream)
     if (!plan) return SW_ERR_INVALID_ARG;
     if (cuda_failed(cudaStreamSynchronize((cudaStream_t)stream))) return SW_ERR_CUDA;
     int32_t v = 0;
-    if (cuda_failed(cudaMemcpy(&v, &plan->info->status, sizeof(v), cudaMemcpyDeviceToHost))) return SW_ERR_CUDA;
+    if (cuda_failed(cudaMemcpy(&v, &plan->S.info->status, sizeof(v), cudaMemcpyDeviceToHost))) return SW_ERR_CUDA;
     return status_to_code(v);
 }
 
@@ -1274,6 +1020,7 @@ int sw_plan_destroy(sw_plan_t *plan)
     cudaDeviceSynchronize();
     if (plan->fixed.ptr) cudaFree(plan->fixed.ptr);
     if (plan->dyn.ptr) cudaFree(plan->dyn.ptr);
+    exec_ctx_free(plan->x);
     if (prev >= 0) cudaSetDevice(prev);
     delete plan;
     return SW_OK;

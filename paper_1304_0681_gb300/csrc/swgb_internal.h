@@ -63,6 +63,8 @@ struct ClassInfo {
 };
 
 struct TbClassInfo;
+struct DevScorePlan;
+struct DevTbPlan;
 
 struct ScoreLaunch {
     PairSet ps;
@@ -83,6 +85,12 @@ struct ScoreLaunch {
     int32_t *tb_hist = nullptr;
     TbClassInfo *tb_info = nullptr;
     int32_t small_slab_words = 0;
+    // device-planned launch (dp != nullptr): the launch serves every class
+    // of score variant `variant` in the plan; order is then the whole
+    // sorted pair order, work_counter the base of the per-class counters and
+    // boundary the base of the chunk-boundary scratch
+    const DevScorePlan *dp = nullptr;
+    int32_t variant = 0;
 };
 
 // What every traceback kernel needs about the batch.
@@ -105,27 +113,205 @@ struct TbClassInfo {
     int32_t max_wcap[2][N_CLASS];  // widest chunk window: [0] big-slab launch, [1] main launch
 };
 
+// A persistent traceback launch: every part of traceback variant `variant`
+// in the device plan.
 struct TracebackLaunch {
     TbParams P;
-    const int32_t *order;
-    int64_t n_items;
-    int32_t lanes;
-    uint32_t *slab;          // traceback bit slabs
-    int64_t slab_group_words;  // per group; tiled: per lane (chunks x wcap)
-    int32_t *boundary;       // chunk boundaries (2 x int32 per column, double-buffered)
-    int64_t boundary_group_ints;  // per group; tiled: per lane (2 x 2 x wcap)
-    int32_t wcap;            // widest chunk window of the launch
-    bool tiled;              // lane-interleaved warp tiles (one lane per pair)
-    bool packed16;           // 16x2 kernel: one lane per two pairs (tiled)
-    int32_t *work_counter;
+    const int32_t *order;    // the whole traceback order (parts index into it)
+    uint32_t *slab;          // base of the per-warp scratch slots
+    int32_t *work_counter;   // base of the per-part counters (2 per class)
     int32_t *status;
     int32_t one = 1;         // a multiplier the compiler cannot fold
+    const DevTbPlan *dp = nullptr;
+    int32_t variant = 0;
 };
 
 // Row counts compiled for the score kernels.
 constexpr int N_SCORE_ROWS = 6;
 extern const int kScoreRows[N_SCORE_ROWS];
 constexpr int TB_ROWS = 8;
+__host__ __device__ inline int score_rows_at(int i)
+{
+    switch (i) {
+    case 0: return 8;
+    case 1: return 16;
+    case 2: return 20;
+    case 3: return 25;
+    case 4: return 32;
+    default: return 50;
+    }
+}
+
+// ---- device-side launch planning ----
+//
+// A batch is aligned by a fixed sequence of launches: the host never reads
+// anything back.  One-block planner kernels turn the classification's
+// per-class facts into the tables below, and every compiled kernel variant
+// is launched once, persistent at full occupancy; a launch serves the
+// classes (or traceback parts) its variant was given and exits at once when
+// it has none.
+constexpr int N_SCORE_VARIANTS = N_SCORE_ROWS * N_MODES;  // variant = rows index * N_MODES + mode
+constexpr int N_TB16_VARIANTS = 6;                        // 16-bit traceback, T = 1, 2, 4, 8, 16, 32
+constexpr int TB_VAR_TILED = 6;                           // int32 traceback, one lane per pair, warp tiles
+constexpr int TB_VAR_GROUPED = 7;                         // int32 traceback, T lanes per pair
+constexpr int N_TB_VARIANTS = 8;
+constexpr int N_TB_PARTS = 2 * N_CLASS;                   // per class: pairs with big slabs, then the rest
+constexpr int kMaxPlanOverrides = 16;
+constexpr int kPlanThreads = 384;                         // >= N_CLASS
+
+struct PlanOverride {
+    int32_t max_read_len, lanes, rows;
+};
+
+// What the planners need besides the batch's class tables (by value).
+struct PlanParams {
+    Scoring sc;
+    int32_t n_overrides;
+    PlanOverride ov[kMaxPlanOverrides];     // sorted by max_read_len
+    int32_t score_warps[N_SCORE_VARIANTS];  // warps each score launch runs
+    int32_t tb_warps[N_TB_VARIANTS];        // warps each traceback launch runs
+    int64_t score_bnd_bytes;                // chunk-boundary scratch of the score launches
+    int64_t tb_bytes;                       // per-warp traceback scratch, shared by the (sequential) launches
+    int32_t small_slab_words;
+    int32_t allow16;                        // 16-bit traceback allowed (SW_TB_AUTO)
+};
+
+struct DevScorePlan {
+    int32_t var_n[N_SCORE_VARIANTS];          // classes of each variant
+    int32_t var_bnd_warps[N_SCORE_VARIANTS];  // warps with a boundary slot (chunked classes only)
+    int64_t var_bnd_offset[N_SCORE_VARIANTS];
+    int64_t var_bnd_slot[N_SCORE_VARIANTS];   // bytes of one warp's boundary slot (its largest class)
+    int32_t cls_start[N_CLASS];               // first position of the class in the sorted order
+    int32_t cls_count[N_CLASS];
+    int32_t cls_lanes[N_CLASS];
+    int32_t cls_bnd_bytes[N_CLASS];           // per group; 0 when a read fits one row chunk
+    int16_t var_cls[N_SCORE_VARIANTS][N_CLASS];  // longest reads first
+};
+
+struct TbPartPlan {
+    int32_t cls, part, start, count;
+    int32_t lanes, wcap;
+    int64_t slab_words, bnd_ints;  // per lane (16-bit), per warp tile (tiled) or per group (grouped)
+    int32_t variant;
+    int32_t pool_tasks;            // 16-bit: tasks whose tiles go to the pool (walked by k_tb16_walk)
+    int64_t pool_offset;           // 16-bit: words from the scratch base to the part's first pooled tile
+};
+
+// Traceback scratch of one launch (words from the scratch base; the launches
+// run one after another and each has the whole budget).  16-bit kernel: the
+// boundary rows of the warps that take part, then full per-warp slots for
+// tasks swept and walked by the warp itself, then the pool of tiles that the
+// separate walk kernel reads.  int32 kernels: per-warp slots only.
+struct DevTbPlan {
+    int32_t var_n[N_TB_VARIANTS];
+    int32_t var_warps[N_TB_VARIANTS];     // warps with a full slot (int32 kernels: the others exit)
+    int64_t var_slot_words[N_TB_VARIANTS];
+    int64_t var_slot_offset[N_TB_VARIANTS];
+    int64_t var_bnd_words[N_TB_VARIANTS];  // 16-bit: boundary row words per warp
+    int32_t var_run_warps[N_TB_VARIANTS];  // 16-bit: warps that take part (each with a boundary row)
+    int64_t split[2];                     // pairs through the 16-bit and the int32 kernels
+    int16_t var_part[N_TB_VARIANTS][N_TB_PARTS];
+    TbPartPlan part[N_TB_PARTS];
+};
+
+// Score-pass plan of a length class: lanes per group and rows per lane
+// (index into score_rows_at) for reads up to m_max in `mode`, hmax the
+// class's score bound.  Overrides first (sorted by max_read_len), else a
+// cost model: padded rows x ~6.5 ALU operations + ~40 per lane-step (both
+// measured), scaled by the share of lanes a warp leaves idle.  In the
+// 16-bit-key mode more than 32 rows per lane need 6-bit row tags, which
+// hold scores up to 510 only.
+__host__ __device__ inline void score_plan_of(int mode, int32_t m_max, int64_t hmax, const PlanOverride *ov,
+                                              int n_ov, int &lanes, int &rows_idx)
+{
+    const int max_rows = (mode == MODE_I16 && hmax > 510) ? 32 : 64;
+    for (int i = 0; i < n_ov; ++i)
+        if (m_max <= ov[i].max_read_len && ov[i].rows <= max_rows) {
+            lanes = ov[i].lanes;
+            rows_idx = 0;
+            for (int r = 0; r < N_SCORE_ROWS; ++r)
+                if (score_rows_at(r) == ov[i].rows) rows_idx = r;
+            return;
+        }
+    // cost = chunks x T x (6.5 R + 40) / (G T / 32) = chunks x (13 R + 80) x 16 / G,
+    // compared exactly as the fraction num / G (integers; the first minimum wins)
+    int64_t best_num = -1, best_den = 1;
+    lanes = 32;
+    rows_idx = 4;
+    for (int ri = 0; ri < N_SCORE_ROWS; ++ri) {
+        const int R = score_rows_at(ri);
+        if (R > max_rows) continue;
+        for (int T = 1; T <= 32; ++T) {
+            const int chunks = (m_max + T * R - 1) / (T * R);
+            if (chunks > 1 && T < 32) continue;
+            const int64_t G = 32 / T;
+            const int64_t num = (int64_t)chunks * (13 * R + 80) * 16;
+            if (best_num < 0 || num * best_den < best_num * G) {
+                best_num = num;
+                best_den = G;
+                lanes = T;
+                rows_idx = ri;
+            }
+        }
+    }
+}
+
+// Traceback launch shape of one part of a class (part 0: pairs whose
+// one-lane slab exceeds small_slab_words, part 1: the rest).  m_max: the
+// class's longest read; max_need: the largest one-lane slab of the class;
+// wcap_in: the part's widest chunk window.  The 16-bit kernel serves every
+// class with a 16-bit score mode unless allow16 is off.  T lanes share a
+// pair: one where a lane's tile (every chunk at the widest window) stays
+// small, else the smallest power of two with the longest read in at most 8
+// (16-bit) or 4 (int32) chunks of 8T rows -- a chunk sweeps its rows' band
+// box, 8T - 1 columns wider than the band, so smaller T wastes fewer cells
+// and larger T keeps fewer pairs per warp waiting (measured on the uneven
+// batch, 16-bit: 4 chunks 57.0 ms, 8 chunks 49.6 ms, 16 chunks 64.5 ms).
+// Also the words one warp's scratch slot needs for this part.
+constexpr int kTbChunks16 = 8, kTbChunks32 = 4;
+constexpr int64_t kTiledLaneWords = 4096, kTiledLaneWords16 = 8192;
+__host__ __device__ inline int64_t tb_part_shape(int mode, bool allow16, int32_t m_max, int64_t max_need,
+                                                 int32_t wcap_in, int part, int32_t small_slab_words, TbPartPlan &t)
+{
+    const int64_t chunks = (m_max + TB_ROWS - 1) / TB_ROWS;
+    int32_t wcap = wcap_in > 1 ? wcap_in : 1;
+    const int64_t wcap4 = (wcap + 3) / 4 * 4;
+    const bool packed16 = allow16 && mode != MODE_I32;
+    int Tl = 1;
+    while (Tl < 32 && (int64_t)Tl * 8 * (packed16 ? kTbChunks16 : kTbChunks32) < m_max) Tl *= 2;
+    const bool one_lane16 = chunks * wcap4 * 2 <= kTiledLaneWords16;
+    const bool tiled = !packed16 && chunks * wcap <= kTiledLaneWords;
+    const int T = (packed16 && one_lane16) || tiled ? 1 : Tl;
+    t.lanes = T;
+    int64_t slot;
+    if (packed16) {
+        const int64_t chunks_t = (m_max + 8 * T - 1) / (8 * T);
+        wcap += 8 * (T - 1);
+        const int64_t s4 = (wcap + T - 1 + 3) / 4;
+        t.slab_words = chunks_t * s4 * 8;                            // per lane
+        t.bnd_ints = chunks_t > 1 ? (int64_t)(32 / T) * 2 * wcap : 0;  // per warp: one row
+        int v = 0;
+        while ((1 << v) < T) ++v;
+        t.variant = v;
+        slot = 32 * t.slab_words + t.bnd_ints;
+    } else if (tiled) {
+        t.slab_words = chunks * wcap;                  // per lane
+        t.bnd_ints = chunks > 1 ? (int64_t)4 * wcap : 0;
+        t.variant = TB_VAR_TILED;
+        slot = 32 * (t.slab_words + t.bnd_ints);
+    } else {
+        const int64_t chunks_t = (m_max + 8 * T - 1) / (8 * T);
+        const int64_t wcap_t = wcap + 8 * (T - 1);
+        const int64_t need = max_need > 1 ? max_need : 1;
+        t.slab_words = T == 1 ? (part == 0 ? need : (need < small_slab_words ? need : small_slab_words))
+                              : chunks_t * wcap_t * T;  // per group
+        t.bnd_ints = chunks_t > 1 ? (int64_t)4 * wcap_t : 0;
+        t.variant = TB_VAR_GROUPED;
+        slot = (int64_t)(32 / T) * (t.slab_words + t.bnd_ints);
+    }
+    t.wcap = wcap;
+    return slot;
+}
 
 // force_i32: every pair takes the int32 score mode (else the narrowest
 // mode its score bound allows)
@@ -135,13 +321,26 @@ int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring
                     int32_t *cig_n, cudaStream_t st);
 int launch_score(int rows, int mode, const ScoreLaunch &L, int blocks, int threads, cudaStream_t st);
 int score_kernel_regs(int rows, int mode, int *regs, int *max_blocks_per_sm, int threads);
-int launch_tb_keys(const TbParams &P, int64_t n_pairs, const int32_t *score_keys, int32_t *tb_keys, int32_t *hist,
-                   TbClassInfo *info, cudaStream_t st);
 int launch_check_counts(const ClassInfo *info, const int32_t *expect, int32_t *status, cudaStream_t st);
+int launch_plan_score(const ClassInfo *info, const PlanParams &pp, DevScorePlan *out, int32_t *status,
+                      cudaStream_t st);
+int launch_plan_tb(const ClassInfo *info, const TbClassInfo *ti, const DevScorePlan *sp, const PlanParams &pp,
+                   DevTbPlan *out, int32_t *status, cudaStream_t st);
+// One persistent launch of score variant v (rows index * N_MODES + mode) at
+// full occupancy; its grid (blocks) comes from score_variant_blocks.
+int launch_score_variant(int v, const ScoreLaunch &L, int blocks, cudaStream_t st);
+int score_variant_blocks(int v, int sm_count, int *blocks);
+int launch_traceback_variant(int v, bool fma, const TracebackLaunch &L, int blocks, cudaStream_t st);
+int traceback_variant_blocks(int v, int sm_count, int *blocks);
+// The walks of a 16-bit traceback launch's pooled tasks (v < N_TB16_VARIANTS).
+int launch_tb_walk_variant(int v, const TracebackLaunch &L, int blocks, cudaStream_t st);
+int tb_walk_variant_blocks(int v, int sm_count, int *blocks);
+// Per-class work counters of one batch: score, traceback (pooled tasks),
+// traceback (tasks a warp sweeps and walks itself).
+constexpr int N_COUNTERS = 6 * N_CLASS;
+constexpr int CTR_TB = 2 * N_CLASS, CTR_TB_OWN = 4 * N_CLASS;
 int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, const int32_t *class_count, int32_t *hist,
                         int32_t *bucket_start, int32_t *cursor, int32_t *order, cudaStream_t st);
-int launch_traceback(const TracebackLaunch &L, int blocks, int threads, cudaStream_t st);
-int traceback_kernel_occupancy(int *max_blocks_per_sm, int threads, bool packed16, int lanes);
 int launch_alu_probe(int kind, int64_t iters, int blocks, int threads, uint32_t *out, cudaStream_t st);
 
 int launch_features(const FeatureParams &P, cudaStream_t st);

@@ -1,7 +1,8 @@
-"""Capturable plans (sw_plan_*): executing a plan, and replaying a CUDA
-graph captured from one, gives the oracle's results bit for bit -- also after
-the batch's bases change under a fixed shape -- and a changed shape is
-reported instead of run."""
+"""CUDA graphs: sw_batch_align itself and plans (sw_plan_*) enqueue a fixed
+sequence of launches with no host wait, so a captured call replays with the
+oracle's results bit for bit -- also after the batch's bases change under a
+fixed shape; a plan reports a changed shape instead of running it, and a
+call that would have to allocate during a capture is refused."""
 import numpy as np
 import pytest
 
@@ -126,3 +127,68 @@ def test_plan_arguments_are_checked():
     with pytest.raises(sw.SwError):  # a score-only plan cannot write a CIGAR
         sw._swgb.sw_plan_align(plan.handle, b.reads, b.windows, b.score, b.end, b.cigar_tuple())
     plan.close()
+
+
+def test_sw_batch_align_itself_is_captured_and_replayed():
+    """The default entry point enqueues a fixed sequence of launches with no
+    host wait, so sw_batch_align itself is captured in a CUDA graph (after
+    one uncaptured call on the capturing stream has set up its scratch) and
+    replayed: bit-exact against the oracle, twice, and after new bases of the
+    same shape are written into the captured input buffers."""
+    import torch
+
+    import paper_1304_0681_gb300 as sw
+    from paper_1304_0681_gb300 import align
+    wl = synth.generate("uneven", seed=12, n_reads=700)
+    b = _batch(wl)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        align(b, DEFAULT, stream=side)  # the stream's scratch, outside the capture
+    side.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        align(b, DEFAULT, stream=side, sync=False)
+    for _ in range(2):
+        _clear(b)
+        graph.replay()
+        torch.cuda.synchronize()
+        sw.sw_sync_status(side)
+        assert_parity(wl, _outputs(b), DEFAULT)
+    wl2 = _same_shape_new_bases(wl, 13)
+    b.reads.copy_(torch.from_numpy(wl2.packed_reads()).cuda())
+    b.windows.copy_(torch.from_numpy(wl2.packed_windows()).cuda())
+    _clear(b)
+    graph.replay()
+    torch.cuda.synchronize()
+    sw.sw_sync_status(side)
+    assert_parity(wl2, _outputs(b), DEFAULT)
+    del graph
+
+
+def test_capture_that_would_allocate_is_refused():
+    """A call whose scratch would have to grow during a capture returns
+    SW_ERR_UNSUPPORTED before enqueuing anything, instead of allocating: here
+    the stream's only earlier call asked for no CIGAR, so it holds no
+    traceback scratch."""
+    import torch
+
+    import paper_1304_0681_gb300 as sw
+    from paper_1304_0681_gb300 import align
+    wl = synth.generate("parity", seed=14, n_reads=200)
+    b = _batch(wl)
+    fresh = torch.cuda.Stream()
+    fresh.wait_stream(torch.cuda.current_stream())
+    align(b, DEFAULT, cigar=False, stream=fresh)
+    graph = torch.cuda.CUDAGraph()
+    err = None
+    with torch.cuda.graph(graph, stream=fresh):
+        try:
+            align(b, DEFAULT, cigar=True, stream=fresh, sync=False)
+        except sw.SwError as e:
+            err = e
+    assert err is not None and err.code == -5  # SW_ERR_UNSUPPORTED
+    del graph
+    # outside a capture the same call allocates and runs
+    align(b, DEFAULT, cigar=True, stream=fresh)
+    assert_parity(wl, _outputs(b), DEFAULT)
