@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_tb(const ClassInfo *__res
                                                           DevTbPlan *__restrict__ out, int32_t *__restrict__ status)
 {
     __shared__ int64_t s_slot[N_TB_PARTS];
+    __shared__ int8_t s_pv[N_TB_PARTS];  // each part's variant (-1: none)
     for (int c = threadIdx.x; c < N_CLASS; c += blockDim.x) {
         const int32_t cnt = info->count[c];
         const int32_t big = ti->n_big[c];
@@ -144,6 +145,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_tb(const ClassInfo *__res
             }
             out->part[2 * c + part] = t;
             s_slot[2 * c + part] = slot;
+            s_pv[2 * c + part] = (int8_t)t.variant;
         }
     }
     __syncthreads();
@@ -163,8 +165,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_tb(const ClassInfo *__res
             // parts 2c (big) and 2c + 1 of class c, classes descending
             const int qi = q0 - lane;
             const int q = qi >= 0 ? (qi ^ 1) : -1;
-            const TbPartPlan *t = q >= 0 ? &out->part[q] : nullptr;
-            const bool hit = t && t->variant == v;
+            const bool hit = q >= 0 && s_pv[q] == v;
+            const TbPartPlan *t = hit ? &out->part[q] : nullptr;
             const unsigned m = __ballot_sync(0xffffffffu, hit);
             if (hit) {
                 out->var_part[v][n + __popc(m & lt)] = (int16_t)q;

@@ -779,37 +779,66 @@ __global__ void __launch_bounds__(128, 4) k_traceback16(const TracebackLaunch L)
     const uint32_t mul1 = eight + eight, mul2 = mul1 * mul1, mul3 = mul2 * mul1;  // 16, 256, 4096
     const uint32_t ONES = 0x00010001u;
 
-    for (int pi = 0; pi < dp.var_n[v]; ++pi) {
-    const TbPartPlan &tp = dp.part[dp.var_part[v][pi]];
-    const int WCAP = tp.wcap;
-    const int S4 = (WCAP + T - 1 + 3) >> 2;
-    const int rc = T * TB_ROWS;
-    const int64_t lane_chunks = tp.slab_words / (8 * (int64_t)max(S4, 1));
-    const int32_t *const order = L.order + tp.start;
-    const int64_t n_items = tp.count;
+    constexpr int rc = T * TB_ROWS;
+    // The part's and phase's values live in shared memory, one record per
+    // warp, read where they are used (held in registers across the sweep
+    // they would crowd out the sweep's own).
+    struct PartCtx {
+        const int32_t *order;
+        int32_t *ctr;        // the phase's work counter
+        uint32_t *pool;      // the part's first pooled tile
+        int64_t n_items, lo, hi, tile_words, lane_chunks;
+        int32_t wcap, s4, pi, phase;
+    };
+    __shared__ PartCtx s_pc[4];  // 128 threads: 4 warps
+    volatile PartCtx *const pc = &s_pc[threadIdx.x >> 5];
+    if (lane == 0) pc->pi = 0;
+    __syncwarp();
+    for (; pc->pi < dp.var_n[v]; __syncwarp(), pc->pi = pc->pi + (lane == 0 ? 1 : 0), __syncwarp()) {
     // tasks 0 .. pool_tasks-1 keep their tiles (32 lanes x slab words) in the
     // pool for k_tb16_walk; the rest are swept into the warp's own slot and
     // walked at once.  The boundary row is updated in place: (H | F << 16) of
     // pair x at offset j in word (j * G + g) * 2 + x.
-    const int64_t tile_words = (32 * tp.slab_words + 63) & ~(int64_t)63;
-    const int64_t n_pool = min(n_items, (int64_t)tp.pool_tasks * PAIRS);
-    int32_t *const ctr_pool = L.work_counter + 2 * tp.cls + tp.part;
-    int32_t *const ctr_own = L.work_counter + (CTR_TB_OWN - CTR_TB) + 2 * tp.cls + tp.part;
+    if (lane == 0) {
+        const TbPartPlan &tp = dp.part[dp.var_part[v][pc->pi]];
+        const int32_t s4 = (tp.wcap + T - 1 + 3) >> 2;
+        pc->order = L.order + tp.start;
+        pc->pool = L.slab + tp.pool_offset;
+        pc->n_items = tp.count;
+        pc->tile_words = (32 * tp.slab_words + 63) & ~(int64_t)63;
+        pc->lane_chunks = tp.slab_words / (8 * (int64_t)max(s4, 1));
+        pc->wcap = tp.wcap;
+        pc->s4 = s4;
+        pc->phase = 0;
+    }
+    __syncwarp();
 
-    for (int phase = 0; phase < 2; ++phase) {
-    if (phase == 1 && !has_slot) break;
+    for (; pc->phase < 2; __syncwarp(), pc->phase = pc->phase + (lane == 0 ? 1 : 0), __syncwarp()) {
+    if (pc->phase == 1 && !has_slot) break;
+    if (lane == 0) {
+        const TbPartPlan &tp = dp.part[dp.var_part[v][pc->pi]];
+        const int64_t n_pool = min((int64_t)tp.count, (int64_t)tp.pool_tasks * PAIRS);
+        const bool ph = pc->phase != 0;
+        pc->ctr = L.work_counter + (ph ? CTR_TB_OWN - CTR_TB : 0) + 2 * tp.cls + tp.part;
+        pc->lo = ph ? n_pool : 0;
+        pc->hi = ph ? (int64_t)tp.count : n_pool;
+    }
+    __syncwarp();
+    const bool own_task = pc->phase != 0;
     for (;;) {
         int bb = 0;
-        if (lane == 0) bb = atomicAdd(phase ? ctr_own : ctr_pool, PAIRS);
+        if (lane == 0) bb = atomicAdd(pc->ctr, PAIRS);
         bb = __shfl_sync(FULLMASK, bb, 0);
-        const int64_t base = phase ? n_pool + bb : bb;
-        if (base >= (phase ? n_items : n_pool)) break;
-        uint2 *const slab = phase ? own : (uint2 *)(L.slab + tp.pool_offset + (int64_t)(bb / PAIRS) * tile_words);
+        const int64_t base = pc->lo + bb;
+        if (base >= pc->hi) break;
+        uint2 *const slab = own_task ? own : (uint2 *)(pc->pool + (int64_t)(bb / PAIRS) * pc->tile_words);
+        const int WCAP = pc->wcap;
+        const int64_t lane_chunks = pc->lane_chunks;
         TbPair q[2];
 #pragma unroll
         for (int x = 0; x < 2; ++x) {
             const int64_t item = base + 2 * g + x;
-            const int32_t p = item < n_items ? order[item] : -1;
+            const int32_t p = item < pc->n_items ? pc->order[item] : -1;
             q[x] = tb_pair(P, p, k == 0 ? L.status : nullptr);
             const bool over = (q[x].rows + rc - 1) / rc > lane_chunks || min(q[x].W, rc + (q[x].b - q[x].a)) > WCAP;
             if (q[x].score > 0 && over) {
@@ -889,7 +918,7 @@ __global__ void __launch_bounds__(128, 4) k_traceback16(const TracebackLaunch L)
                 ws[x].start(P.ps.wins, a0, q[x].score > 0 ? q[x].ws + q[x].n : a0);
             }
             uint32_t out_h = 0u, out_f = 0u;
-            int64_t widx = tb16_word(c, 0, lane, S4);   // tile word of step t
+            int64_t widx = tb16_word(c, 0, lane, pc->s4);   // tile word of step t
             int64_t bidx = ((int64_t)(0 - k) * G + g) * 2;  // boundary word of offset t - k
 
             for (int t = 0; t < steps; ++t) {
@@ -939,7 +968,7 @@ __global__ void __launch_bounds__(128, 4) k_traceback16(const TracebackLaunch L)
                     // a lane's four consecutive steps share one 32-byte
                     // sector; pooled tiles stream out (walked much later),
                     // own tiles stay in L2 for the walk right after
-                    if (phase) __stcg(slab + widx, make_uint2(w0, w1));
+                    if (own_task) __stcg(slab + widx, make_uint2(w0, w1));
                     else __stcs(slab + widx, make_uint2(w0, w1));
                     out_h = hu;
                     out_f = f;
@@ -957,13 +986,13 @@ __global__ void __launch_bounds__(128, 4) k_traceback16(const TracebackLaunch L)
         // a task in the warp's own slot: its walks, one thread per pair,
         // while the other warps of the SM keep sweeping; then the slot is
         // free for the next task
-        if (phase) {
+        if (own_task) {
             for (int wi = lane; wi < PAIRS; wi += 32) {
                 const int64_t item = base + wi;
-                if (item >= n_items) break;
+                if (item >= pc->n_items) break;
                 Walk16<T, true> w;
                 FwdCigar cg;
-                if (w.begin(P, cg, slab, order[item], wi >> 1, wi & 1, WCAP, lane_chunks)) {
+                if (w.begin(P, cg, slab, pc->order[item], wi >> 1, wi & 1, pc->wcap, pc->lane_chunks)) {
                     while (w.step(P, cg)) {
                     }
                     w.end(P, cg, L.status);

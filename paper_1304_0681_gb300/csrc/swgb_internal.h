@@ -234,24 +234,27 @@ __host__ __device__ inline void score_plan_of(int mode, int32_t m_max, int64_t h
             return;
         }
     // cost = chunks x T x (6.5 R + 40) / (G T / 32) = chunks x (13 R + 80) x 16 / G,
-    // compared exactly as the fraction num / G (integers; the first minimum wins)
+    // compared exactly as the fraction num / G (integers; the first minimum
+    // over R ascending, then T ascending, wins).  Plans with one row chunk
+    // need T >= ceil(m / R), and G = floor(32 / T) does not grow with T, so
+    // for each R the smallest such T is the first minimum (T = 32 with one
+    // chunk is never better); reads longer than 32 R take T = 32 in chunks.
     int64_t best_num = -1, best_den = 1;
     lanes = 32;
     rows_idx = 4;
     for (int ri = 0; ri < N_SCORE_ROWS; ++ri) {
         const int R = score_rows_at(ri);
         if (R > max_rows) continue;
-        for (int T = 1; T <= 32; ++T) {
-            const int chunks = (m_max + T * R - 1) / (T * R);
-            if (chunks > 1 && T < 32) continue;
-            const int64_t G = 32 / T;
-            const int64_t num = (int64_t)chunks * (13 * R + 80) * 16;
-            if (best_num < 0 || num * best_den < best_num * G) {
-                best_num = num;
-                best_den = G;
-                lanes = T;
-                rows_idx = ri;
-            }
+        const int t_min = (m_max + R - 1) / R;
+        const int T = t_min <= 32 ? (t_min > 0 ? t_min : 1) : 32;
+        const int chunks = t_min <= 32 ? 1 : (m_max + 32 * R - 1) / (32 * R);
+        const int64_t G = 32 / T;
+        const int64_t num = (int64_t)chunks * (13 * R + 80) * 16;
+        if (best_num < 0 || num * best_den < best_num * G) {
+            best_num = num;
+            best_den = G;
+            lanes = T;
+            rows_idx = ri;
         }
     }
 }
