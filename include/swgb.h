@@ -236,9 +236,22 @@ int sw_mlp_refresh(float *model, sw_stream_t stream);
 int sw_set_mlp_kernel(int32_t kind);
 int sw_mlp_forward(const float *model, const uint16_t *features, int64_t n, float *out, sw_stream_t stream);
 
-/* Gradient of mean((y - target)^2) over n samples (fp32 forward and
- * backward), written to the model's gradient region.  Sample s uses feature
- * row idx[s] and target[idx[s]] (idx device int32[n], or NULL for s). */
+/* Gradient of mean((y - target)^2) over n samples, written to the model's
+ * gradient region.  Sample s uses feature row idx[s] and target[idx[s]] (idx
+ * device int32[n], or NULL for s).  By default (SW_GRAD_AUTO), when
+ * `features` is 16-byte aligned, the 5th-generation tensor cores compute the
+ * five products of the forward and backward pass (bf16 operands: the
+ * features, the weights as the serving copies round them, the hidden
+ * activation and the two error signals; fp32 accumulation in tensor memory),
+ * one partial gradient per CTA, summed in a fixed order (the result does not
+ * depend on scheduling).  SW_GRAD_FP32 computes forward and backward in fp32
+ * on the CUDA cores instead.  A timed-out tensor-core wait is reported as
+ * SW_ERR_DEVICE_TIMEOUT by sw_sync_status.  sw_set_mlp_grad_kernel is
+ * process-wide; SW_ERR_INVALID_ARG for other values.  The library keeps the
+ * partial gradients in scratch of this stream (33,153 floats per CTA). */
+#define SW_GRAD_AUTO 0
+#define SW_GRAD_FP32 1
+int sw_set_mlp_grad_kernel(int32_t kind);
 int sw_mlp_grad(float *model, const uint16_t *features, const float *target, const int32_t *idx, int64_t n,
                 sw_stream_t stream);
 

@@ -28,7 +28,7 @@ EXPORTS = ("sw_cigar_capacity", "sw_cigar_offsets", "sw_packed_bytes", "sw_batch
            "sw_junctions_export",
            "sw_plan_rows", "sw_alu_probe", "sw_phase_timing", "sw_phase_times", "sw_batch_align_noalloc",
            "sw_batch_align_masked", "sw_filter_features", "sw_mlp_bytes", "sw_mlp_init", "sw_mlp_refresh",
-           "sw_mlp_forward", "sw_set_mlp_kernel", "sw_mlp_grad", "sw_mlp_adam", "sw_filter_select", "sw_best_per_read",
+           "sw_mlp_forward", "sw_set_mlp_kernel", "sw_set_mlp_grad_kernel", "sw_mlp_grad", "sw_mlp_adam", "sw_filter_select", "sw_best_per_read",
            "sw_top_hits", "sw_filter_align", "sw_filter_train_step", "sw_get_status",
            # include/swgb_seed.h
            "sw_index_table_words", "sw_index_build", "sw_seed_windows", "sw_reads_two_strands",
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_mlp_refresh.restype = ctypes.c_int
     lib.sw_set_mlp_kernel.argtypes = [i32]
     lib.sw_set_mlp_kernel.restype = ctypes.c_int
+    lib.sw_set_mlp_grad_kernel.argtypes = [i32]
+    lib.sw_set_mlp_grad_kernel.restype = ctypes.c_int
     lib.sw_mlp_forward.argtypes = [p, p, i64, p, p]
     lib.sw_mlp_forward.restype = ctypes.c_int
     lib.sw_mlp_grad.argtypes = [p, p, p, p, i64, p]
@@ -439,6 +441,14 @@ SW_MLP_MMA_SYNC = 1
 
 def sw_set_mlp_kernel(kind: int) -> None:
     _check(_lib.sw_set_mlp_kernel(int(kind)), "sw_set_mlp_kernel")
+
+
+SW_GRAD_AUTO = 0
+SW_GRAD_FP32 = 1
+
+
+def sw_set_mlp_grad_kernel(kind: int) -> None:
+    _check(_lib.sw_set_mlp_grad_kernel(int(kind)), "sw_set_mlp_grad_kernel")
 
 
 def sw_mlp_forward(model, features, n: int, out, stream=None) -> None:

@@ -672,6 +672,7 @@ int launch_best_per_read(const int32_t *score, const int64_t *cand_off, int64_t 
 using namespace swgb;
 
 static std::atomic<int32_t> g_mlp_kind{SW_MLP_AUTO};  // set by sw_set_mlp_kernel
+static std::atomic<int32_t> g_grad_kind{SW_GRAD_AUTO};  // set by sw_set_mlp_grad_kernel
 
 static int sm_count_now(int *sms)
 {
@@ -736,6 +737,13 @@ int sw_mlp_forward(const float *model, const uint16_t *features, int64_t n, floa
     return launch_mlp_forward(model, features, n, out, sms, (cudaStream_t)stream);
 }
 
+int sw_set_mlp_grad_kernel(int32_t kind)
+{
+    if (kind != SW_GRAD_AUTO && kind != SW_GRAD_FP32) return SW_ERR_INVALID_ARG;
+    g_grad_kind.store(kind);
+    return SW_OK;
+}
+
 int sw_mlp_grad(float *model, const uint16_t *features, const float *target, const int32_t *idx, int64_t n,
                 sw_stream_t stream)
 {
@@ -743,7 +751,16 @@ int sw_mlp_grad(float *model, const uint16_t *features, const float *target, con
     int sms = 0;
     int rc = sm_count_now(&sms);
     if (rc) return rc;
-    return launch_mlp_grad(model, features, target, idx, n, sms, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    // the tensor-core kernel reads 16-byte feature rows
+    if (g_grad_kind.load() == SW_GRAD_AUTO && !((uintptr_t)features & 15u)) {
+        int32_t *status = nullptr;
+        if ((rc = aux_status_word(st, &status))) return rc;
+        float *partial = nullptr;
+        if ((rc = grad_scratch(st, sizeof(float) * (size_t)MD_NP * mlp_grad_tc_parts(n, sms), &partial))) return rc;
+        return launch_mlp_grad_tc(model, features, target, idx, n, sms, partial, status, st);
+    }
+    return launch_mlp_grad(model, features, target, idx, n, sms, st);
 }
 
 int sw_mlp_adam(float *model, float lr, int32_t step, sw_stream_t stream)

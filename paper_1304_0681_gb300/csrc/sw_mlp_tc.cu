@@ -189,6 +189,10 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
     const float b3 = model[MD_B3];
     uint32_t ph1 = 0, ph2 = 0;
     bool ok = true;
+    // commits not yet seen complete (every thread tracks them alike): at most
+    // one on each barrier, waited for again before the tensor memory is freed
+    bool pend1 = false, pend2 = false;
+    uint32_t pph1 = 0, pph2 = 0;
     auto layer1 = [&](int xb, uint32_t acc) {
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks)
@@ -196,10 +200,13 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
                      smem_desc(s_base + SM_W1 + 256 * ks, 128, 1024), idesc_bf16(128, 256), ks > 0);
         mma_commit(bar1);
     };
-    auto wait_all = [&](uint32_t bar, uint32_t &ph) -> bool {
+    auto wait_all = [&](uint32_t bar, uint32_t &ph, bool &pend, uint32_t &pph) -> bool {
+        pph = ph;
         const bool got = mbar_wait(bar, ph);
         ph ^= 1u;
-        return __syncthreads_and(got) != 0;
+        const bool all = __syncthreads_and(got) != 0;
+        pend = !all;
+        return all;
     };
 
     // tile `tile` uses X buffer xb and accumulator columns 256 * xb
@@ -209,13 +216,15 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
         fence_async_smem();
         __syncthreads();
         if (tid == 0) layer1(0, tmem);
+        pend1 = true;
+        pph1 = ph1;
     }
     for (; tile < tiles && ok; tile += gridDim.x, xb ^= 1) {
         const int64_t next = tile + gridDim.x;
         const uint32_t acc = tmem + 256u * (uint32_t)xb;
         // the next tile's features, while this one computes
         if (next < tiles) load_x(next, xb ^ 1);
-        ok = wait_all(bar1, ph1);  // layer 1 of this tile
+        ok = wait_all(bar1, ph1, pend1, pph1);  // layer 1 of this tile
         fence_after_sync();
         if (!ok) break;
         // h = bf16(relu(D + b1)): warp (quarter, half) takes 32 rows x 128 columns
@@ -256,7 +265,11 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
             mma_commit(bar2);
             if (next < tiles) layer1(xb ^ 1, tmem + 256u * (uint32_t)(xb ^ 1));
         }
-        ok = wait_all(bar2, ph2);
+        if (next < tiles) {
+            pend1 = true;
+            pph1 = ph1;
+        }
+        ok = wait_all(bar2, ph2, pend2, pph2);
         fence_after_sync();
         if (!ok) break;
         // y = w3 . relu(D + b2) + b3: warp (quarter, half) sums 32 of the 64 columns
@@ -280,11 +293,372 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
         }
     }
     if (!ok && tid == 0) atomicOr(status, ST_TIMEOUT);
+    // a wait that ran out, or a break after one, can leave tensor-core work
+    // in flight: wait for it once more (bounded) before the memory is freed
+    if (pend1) __syncthreads_and(mbar_wait(bar1, pph1));
+    if (pend2) __syncthreads_and(mbar_wait(bar2, pph2));
     cp_async_wait_all();
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
+
+// ------------------------------------------------------------------ training
+//
+// The gradient of mean((y - target)^2) over a minibatch on the tensor cores.
+// A CTA takes tiles of 128 samples; per tile five MMAs (M 128, bf16 operands
+// in shared memory, fp32 accumulators in tensor memory):
+//   Z1   = X . W1              (K 64,  N 256)   TMEM columns 0..255
+//   Z2   = A1 . W2             (K 256, N 64)    columns 0..63
+//   dA1  = dZ2 . W2^T          (K 64,  N 256)   columns 0..255
+//   gW2  += A1^T . dZ2         (K 128, N 64)    columns 256..383, two M halves
+//   gW1^T += dZ1^T . X         (K 128, N 64)    columns 384..511, two M halves
+// with the CUDA cores in between: A1 = bf16(relu(Z1 + b1)), the output y,
+// dy = 2 (y - t), dZ2 = dy w3 [Z2 + b2 > 0], dZ1 = dA1 [A1 > 0], and the
+// bias gradients (column sums in fp32); the 1/n of the mean multiplies the
+// final sums.  The weight-gradient sums stay in
+// tensor memory across the CTA's tiles; at the end each CTA writes its
+// partial gradient, and k_mlp_grad_reduce adds the partials in CTA order (so
+// the result does not depend on scheduling).  Every operand is K-major: the
+// transposed copies (X^T, A1^T, dZ2^T, dZ1^T) are written by the epilogues.
+// Shared memory regions are reused as their contents die:
+//   R1  A1 [128][256]           -> dZ1^T [256][128]
+//   R2  A1^T [256][128]
+//   R3  W1^T [256][64] -> W2^T [64][256] -> W2 [256][64]
+//   R5  X [128][64]             -> dZ2 [128][64]
+//   R6  X^T [64][128]
+//   R7  dZ2^T [64][128]
+
+constexpr int GB_R1 = 0;
+constexpr int GB_R2 = GB_R1 + 65536;
+constexpr int GB_R3 = GB_R2 + 65536;
+constexpr int GB_R5 = GB_R3 + 32768;
+constexpr int GB_R6 = GB_R5 + 16384;
+constexpr int GB_R7 = GB_R6 + 16384;
+constexpr int GB_B1 = GB_R7 + 16384;      // b1 [256]
+constexpr int GB_B2 = GB_B1 + 1024;       // b2 [64]
+constexpr int GB_W3 = GB_B2 + 256;        // w3 [64]
+constexpr int GB_T = GB_W3 + 256;         // targets of the tile [128]
+constexpr int GB_YP = GB_T + 512;         // partial outputs [2][128]
+// bias gradients, one row per TMEM lane quarter (each warp adds only to its
+// own quarter's row and column half, and the rows are added in order at the
+// end, so the sums do not depend on warp scheduling)
+constexpr int GB_GB1 = GB_YP + 1024;      // gb1 [4][256]
+constexpr int GB_GB2 = GB_GB1 + 4096;     // gb2 [4][64]
+constexpr int GB_GW3 = GB_GB2 + 1024;     // gw3 [4][64]
+constexpr int GB_GB3 = GB_GW3 + 1024;     // gb3 [4]
+constexpr int GB_BAR = GB_GB3 + 16;       // mbarrier (8 B), TMEM base (4 B)
+constexpr int GB_USED = GB_BAR + 64;
+
+// 2-byte bf16 store of v at byte offset off of shared memory
+__device__ __forceinline__ void st_bf16(unsigned char *smem, uint32_t off, float v)
+{
+    *reinterpret_cast<__nv_bfloat16 *>(smem + off) = __float2bfloat16_rn(v);
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+__global__ void __launch_bounds__(256, 1) k_mlp_grad_tc(const float *__restrict__ model,
+                                                        const __nv_bfloat16 *__restrict__ feat,
+                                                        const float *__restrict__ target,
+                                                        const int32_t *__restrict__ idx, int64_t n,
+                                                        float *__restrict__ partial, int32_t *status)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    float *b1 = reinterpret_cast<float *>(smem + GB_B1);
+    float *b2 = reinterpret_cast<float *>(smem + GB_B2);
+    float *w3 = reinterpret_cast<float *>(smem + GB_W3);
+    float *ts = reinterpret_cast<float *>(smem + GB_T);
+    float *yp = reinterpret_cast<float *>(smem + GB_YP);
+    float *gb1 = reinterpret_cast<float *>(smem + GB_GB1);
+    float *gb2 = reinterpret_cast<float *>(smem + GB_GB2);
+    float *gw3 = reinterpret_cast<float *>(smem + GB_GW3);
+    float *gb3 = reinterpret_cast<float *>(smem + GB_GB3);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + GB_BAR);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + GB_BAR + 8);
+    const uint32_t s_base = smem_u32(smem);
+    const uint32_t mbar = smem_u32(bar);
+
+    for (int i = tid; i < 256; i += blockDim.x) b1[i] = model[MD_B1 + i];
+    for (int i = tid; i < 64; i += blockDim.x) {
+        b2[i] = model[MD_B2 + i];
+        w3[i] = model[MD_W3 + i];
+    }
+    for (int i = tid; i < 4 * 256; i += blockDim.x) gb1[i] = 0.f;
+    for (int i = tid; i < 4 * 64; i += blockDim.x) {
+        gb2[i] = 0.f;
+        gw3[i] = 0.f;
+    }
+    if (tid < 4) gb3[tid] = 0.f;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar));
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t accA = tmem, accB = tmem + 256u, accC = tmem + 384u;
+    const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
+    const float b3 = model[MD_B3];
+    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    uint32_t ph = 0, pending_ph = 0;
+    bool ok = true, pending = false;
+    // one commit, then every thread waits for it (bounded, uniform verdict);
+    // a wait that runs out leaves the commit pending
+    auto commit_wait = [&]() -> bool {
+        if (tid == 0) mma_commit(mbar);
+        pending = true;
+        pending_ph = ph;
+        const bool got = mbar_wait(mbar, ph);
+        ph ^= 1u;
+        const bool all = __syncthreads_and(got) != 0;
+        if (all) pending = false;
+        fence_after_sync();
+        return all;
+    };
+    // generic-proxy shared-memory writes, visible to the next MMAs
+    auto publish = [&]() {
+        fence_async_smem();
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+    };
+    // copies a [rows][cols] bf16 matrix from global memory into K-major layout
+    auto load_kmajor = [&](int region, const uint4 *g, int rows, int cols) {
+        const int per_row = cols / 8;
+        for (int c = tid; c < rows * per_row; c += blockDim.x) {
+            const int r = c / per_row, k = (c % per_row) * 8;
+            *reinterpret_cast<uint4 *>(smem + region + kmajor_off(r, k, cols)) = g[c];
+        }
+    };
+    bool first = true;
+    for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const int64_t row0 = tile * TC_ROWS;
+        // 1. X (K-major along features), X^T (along samples), targets, W1^T
+        for (int c = tid; c < TC_ROWS * 8; c += blockDim.x) {
+            const int r = c >> 3, k = (c & 7) * 8;
+            const int64_t s = row0 + r;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (s < n) {
+                const int64_t row = idx ? idx[s] : s;
+                v = reinterpret_cast<const uint4 *>(feat)[row * 8 + (c & 7)];
+            }
+            *reinterpret_cast<uint4 *>(smem + GB_R5 + kmajor_off(r, k, 64)) = v;
+            const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                *reinterpret_cast<__nv_bfloat16 *>(smem + GB_R6 + kmajor_off(k + q, r, 128)) = e[q];
+        }
+        for (int r = tid; r < TC_ROWS; r += blockDim.x) {
+            const int64_t s = row0 + r;
+            ts[r] = s < n ? target[idx ? idx[s] : s] : 0.f;
+        }
+        load_kmajor(GB_R3, reinterpret_cast<const uint4 *>(model + MD_W1T), 256, 64);
+        publish();
+        // 2. Z1 = X . W1
+        if (tid == 0)
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+                mma_bf16(accA, smem_desc(s_base + GB_R5 + 256 * ks, 128, 1024),
+                         smem_desc(s_base + GB_R3 + 256 * ks, 128, 1024), idesc_bf16(128, 256), ks > 0);
+        if (!(ok = commit_wait())) break;
+        // 3. W2^T for layer 2; A1 = bf16(relu(Z1 + b1)) as A1 and A1^T
+        load_kmajor(GB_R3, reinterpret_cast<const uint4 *>(model + MD_W2T), 64, 256);
+        {
+            const int r = 32 * quarter + lane;
+            for (int c0 = 128 * half; c0 < 128 * half + 128; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(accA + lane_off + (uint32_t)c0, v);
+                tmem_wait_ld();
+                uint32_t pk[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float x0 = fmaxf(__uint_as_float(v[2 * j]) + b1[c0 + 2 * j], 0.f);
+                    const float x1 = fmaxf(__uint_as_float(v[2 * j + 1]) + b1[c0 + 2 * j + 1], 0.f);
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+                    pk[j] = *reinterpret_cast<const uint32_t *>(&h);
+                    *reinterpret_cast<__nv_bfloat16 *>(smem + GB_R2 + kmajor_off(c0 + 2 * j, r, 128)) = h.x;
+                    *reinterpret_cast<__nv_bfloat16 *>(smem + GB_R2 + kmajor_off(c0 + 2 * j + 1, r, 128)) = h.y;
+                }
+                *reinterpret_cast<uint4 *>(smem + GB_R1 + kmajor_off(r, c0, 256)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4 *>(smem + GB_R1 + kmajor_off(r, c0 + 8, 256)) =
+                    make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+        }
+        publish();
+        // 4. Z2 = A1 . W2
+        if (tid == 0)
+#pragma unroll
+            for (int ks = 0; ks < 16; ++ks)
+                mma_bf16(accA, smem_desc(s_base + GB_R1 + 256 * ks, 128, 4096),
+                         smem_desc(s_base + GB_R3 + 256 * ks, 128, 4096), idesc_bf16(128, 64), ks > 0);
+        if (!(ok = commit_wait())) break;
+        // 5. W2 for dA1 (bf16 of the fp32 parameters, as the serving copies
+        // round them); y, dy, dZ2 (as dZ2 and dZ2^T) and the small gradients
+        for (int c = tid; c < 256 * 8; c += blockDim.x) {
+            const int r = c >> 3, k = (c & 7) * 8;
+            const float4 *src = reinterpret_cast<const float4 *>(model + MD_W2 + r * 64 + k);
+            const float4 lo = src[0], hi = src[1];
+            const __nv_bfloat162 p0 = __floats2bfloat162_rn(lo.x, lo.y), p1 = __floats2bfloat162_rn(lo.z, lo.w);
+            const __nv_bfloat162 p2 = __floats2bfloat162_rn(hi.x, hi.y), p3 = __floats2bfloat162_rn(hi.z, hi.w);
+            *reinterpret_cast<uint4 *>(smem + GB_R3 + kmajor_off(r, k, 64)) =
+                make_uint4(*reinterpret_cast<const uint32_t *>(&p0), *reinterpret_cast<const uint32_t *>(&p1),
+                           *reinterpret_cast<const uint32_t *>(&p2), *reinterpret_cast<const uint32_t *>(&p3));
+        }
+        {
+            const int r = 32 * quarter + lane;
+            const bool valid = row0 + r < n;
+            float z[32];
+            for (int c0 = 0; c0 < 32; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(accA + lane_off + (uint32_t)(32 * half + c0), v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) z[c0 + j] = __uint_as_float(v[j]) + b2[32 * half + c0 + j];
+            }
+            float y = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) y += fmaxf(z[j], 0.f) * w3[32 * half + j];
+            yp[half * 128 + r] = y;
+            __syncthreads();
+            // per-sample 2 (y - t); the 1/n of the mean is applied once, to
+            // the sums, so the bf16 signals do not depend on the batch size
+            const float dy = valid ? 2.f * (yp[r] + yp[128 + r] + b3 - ts[r]) : 0.f;
+            float dz[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int c = 32 * half + j;
+                dz[j] = z[j] > 0.f ? dy * w3[c] : 0.f;
+                st_bf16(smem, GB_R7 + kmajor_off(c, r, 128), dz[j]);
+                const float s2 = warp_sum(dz[j]);
+                const float s3 = warp_sum(fmaxf(z[j], 0.f) * dy);
+                if (lane == 0) {
+                    gb2[quarter * 64 + c] += s2;
+                    gw3[quarter * 64 + c] += s3;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(dz[j + 2 * q], dz[j + 2 * q + 1]);
+                    pk[q] = *reinterpret_cast<const uint32_t *>(&h);
+                }
+                *reinterpret_cast<uint4 *>(smem + GB_R5 + kmajor_off(r, 32 * half + j, 64)) =
+                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+            if (half == 0) {
+                const float s = warp_sum(dy);
+                if (lane == 0) gb3[quarter] += s;
+            }
+        }
+        publish();
+        // 6. dA1 = dZ2 . W2^T, and gW2 += A1^T . dZ2 (two 128-row halves)
+        if (tid == 0) {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+                mma_bf16(accA, smem_desc(s_base + GB_R5 + 256 * ks, 128, 1024),
+                         smem_desc(s_base + GB_R3 + 256 * ks, 128, 1024), idesc_bf16(128, 256), ks > 0);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+                for (int ks = 0; ks < 8; ++ks)
+                    mma_bf16(accB + 64u * hh, smem_desc(s_base + GB_R2 + 32768 * hh + 256 * ks, 128, 2048),
+                             smem_desc(s_base + GB_R7 + 256 * ks, 128, 2048), idesc_bf16(128, 64),
+                             (!first || ks > 0) ? 1u : 0u);
+        }
+        if (!(ok = commit_wait())) break;
+        // 7. dZ1 = dA1 [A1 > 0], as dZ1^T; gb1
+        {
+            const int r = 32 * quarter + lane;
+            for (int c0 = 128 * half; c0 < 128 * half + 128; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(accA + lane_off + (uint32_t)c0, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int c = c0 + j;
+                    const float a = __bfloat162float(
+                        *reinterpret_cast<const __nv_bfloat16 *>(smem + GB_R2 + kmajor_off(c, r, 128)));
+                    const float d = a > 0.f ? __uint_as_float(v[j]) : 0.f;
+                    st_bf16(smem, GB_R1 + kmajor_off(c, r, 128), d);
+                    const float s1 = warp_sum(d);
+                    if (lane == 0) gb1[quarter * 256 + c] += s1;
+                }
+            }
+        }
+        publish();
+        // 8. gW1^T += dZ1^T . X (two 128-row halves)
+        if (tid == 0)
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+                for (int ks = 0; ks < 8; ++ks)
+                    mma_bf16(accC + 64u * hh, smem_desc(s_base + GB_R1 + 32768 * hh + 256 * ks, 128, 2048),
+                             smem_desc(s_base + GB_R6 + 256 * ks, 128, 2048), idesc_bf16(128, 64),
+                             (!first || ks > 0) ? 1u : 0u);
+        if (!(ok = commit_wait())) break;
+        first = false;
+    }
+    // the CTA's partial gradient: gW1, gW2 from tensor memory, biases
+    if (ok && !first) {
+        float *out = partial + (int64_t)blockIdx.x * MD_NP;
+        const int j = 128 * half + 32 * quarter + lane;  // hidden unit of this lane
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(accB + 64u * (uint32_t)half + lane_off + (uint32_t)c0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int q = 0; q < 16; ++q) out[MD_W2 + j * 64 + c0 + q] = __uint_as_float(v[q]);
+            tmem_ld16(accC + 64u * (uint32_t)half + lane_off + (uint32_t)c0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int q = 0; q < 16; ++q) out[MD_W1 + (c0 + q) * 256 + j] = __uint_as_float(v[q]);
+        }
+        __syncthreads();
+        for (int i = tid; i < 256; i += blockDim.x)
+            out[MD_B1 + i] = ((gb1[i] + gb1[256 + i]) + gb1[512 + i]) + gb1[768 + i];
+        for (int i = tid; i < 64; i += blockDim.x) {
+            out[MD_B2 + i] = ((gb2[i] + gb2[64 + i]) + gb2[128 + i]) + gb2[192 + i];
+            out[MD_W3 + i] = ((gw3[i] + gw3[64 + i]) + gw3[128 + i]) + gw3[192 + i];
+        }
+        if (tid == 0) out[MD_B3] = ((gb3[0] + gb3[1]) + gb3[2]) + gb3[3];
+    } else if (!ok && tid == 0) {
+        atomicOr(status, ST_TIMEOUT);
+    }
+    // a commit whose wait ran out may still have tensor-core work in flight:
+    // wait for it once more (bounded) before the tensor memory is released
+    if (pending) {
+        const bool got = mbar_wait(mbar, pending_ph);
+        __syncthreads_and(got);
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
+// G = the sum of the CTAs' partial gradients, in CTA order, over n samples.
+__global__ void k_mlp_grad_reduce(const float *__restrict__ partial, int n_part, float inv_n, float *__restrict__ G)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < MD_NP; i += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int p = 0; p < n_part; ++p) s += partial[(int64_t)p * MD_NP + i];
+        G[i] = s * inv_n;
+    }
 }
 
 }  // namespace
@@ -303,6 +677,27 @@ int launch_mlp_forward_tc(const float *model, const uint16_t *feat, int64_t n, f
     k_mlp_forward_tc<<<grid, 256, SM_TOTAL, st>>>(model, reinterpret_cast<const __nv_bfloat16 *>(feat), n, out,
                                                    status);
     count_launch();
+    return launch_status();
+}
+
+int mlp_grad_tc_parts(int64_t n, int sm_count)
+{
+    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, sm_count));
+}
+
+int launch_mlp_grad_tc(float *model, const uint16_t *feat, const float *target, const int32_t *idx, int64_t n,
+                       int sm_count, float *partial, int32_t *status, cudaStream_t st)
+{
+    if (cuda_failed(cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, GB_USED)))
+        return SW_ERR_CUDA;
+    static_assert(GB_USED <= SM_TOTAL, "shared memory layout");
+    const int grid = mlp_grad_tc_parts(n, sm_count);
+    k_mlp_grad_tc<<<grid, 256, GB_USED, st>>>(model, reinterpret_cast<const __nv_bfloat16 *>(feat), target, idx, n,
+                                               partial, status);
+    k_mlp_grad_reduce<<<(int)((MD_NP + 255) / 256), 256, 0, st>>>(partial, grid, (float)(1.0 / (double)n),
+                                                                    model + MD_G);
+    count_launch(2);
     return launch_status();
 }
 

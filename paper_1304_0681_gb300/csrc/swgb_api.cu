@@ -111,6 +111,7 @@ struct DeviceState {
     bool timed_cells_valid = false;
     Buffer misc;                     // Stage E task iv: status word and record scan scratch
     Buffer filt;                     // sw_filter_align: features, predictions, selection
+    Buffer grad;                     // sw_mlp_grad: per-CTA partial gradients
     int64_t *seed_stats_host = nullptr;  // pinned: counters of the stream's last sw_seed_windows
     cudaEvent_t phase[4] = {nullptr, nullptr, nullptr, nullptr};
     // sw_batch_align_host: copy streams and per-chunk events
@@ -225,7 +226,7 @@ int device_state(DeviceState **out, cudaStream_t st)
 
 void free_state(DeviceState *s)
 {
-    for (Buffer *b : {&s->fixed, &s->dyn, &s->stage, &s->misc, &s->filt})
+    for (Buffer *b : {&s->fixed, &s->dyn, &s->stage, &s->misc, &s->filt, &s->grad})
         if (b->ptr) {
             cudaFree(b->ptr);
             b->ptr = nullptr;
@@ -1125,6 +1126,17 @@ int filter_scratch(cudaStream_t st, size_t bytes, uint8_t **ptr)
     std::lock_guard<std::mutex> lk(ds->mu);
     if ((rc = ensure(ds->filt, bytes))) return rc;
     *ptr = (uint8_t *)ds->filt.ptr;
+    return SW_OK;
+}
+
+int grad_scratch(cudaStream_t st, size_t bytes, float **ptr)
+{
+    DeviceState *ds = nullptr;
+    int rc = device_state(&ds, st);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ds->mu);
+    if ((rc = ensure(ds->grad, bytes))) return rc;
+    *ptr = (float *)ds->grad.ptr;
     return SW_OK;
 }
 

@@ -384,6 +384,13 @@ int launch_dense_cigar(const uint32_t *ops, const int64_t *off, const int32_t *n
 
 int launch_mlp_forward_tc(const float *model, const uint16_t *feat, int64_t n, float *out, int sm_count,
                           int32_t *status, cudaStream_t st);
+// The gradient on the tensor cores: one partial per CTA (partial: that many
+// x MD_NP floats), then their sum in CTA order into the model's gradient.
+int mlp_grad_tc_parts(int64_t n, int sm_count);
+int launch_mlp_grad_tc(float *model, const uint16_t *feat, const float *target, const int32_t *idx, int64_t n,
+                       int sm_count, float *partial, int32_t *status, cudaStream_t st);
+// Scratch of sw_mlp_grad on this stream (grown on demand).
+int grad_scratch(cudaStream_t st, size_t bytes, float **ptr);
 // A device status word for calls outside the alignment path: cleared on
 // `st`, and the word sw_sync_status reads until the next call sets another.
 int aux_status_word(cudaStream_t st, int32_t **status);

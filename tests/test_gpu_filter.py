@@ -12,8 +12,16 @@ Tolerances (derived from the arithmetic):
   accumulation order and activations whose fp32 value sits next to a bf16
   rounding boundary (one bf16 ulp, 2^-8 relative, on a few of 256 terms);
   1e-2 relative plus 1e-3 absolute covers that with margin.
-- gradient: fp32 forward and backward against fp64: relative 1e-3 of the
-  largest gradient component.
+- gradient, fp32 kernel (SW_GRAD_FP32): fp32 forward and backward against
+  fp64: relative 1e-3 of the largest gradient component.
+- gradient, tensor-core kernel (the default): its products take bf16
+  operands (the weights as the serving copies round them, the hidden
+  activation, the two error signals).  On inputs built so that every one of
+  those roundings and every fp32 sum is exact it must equal the fp64
+  gradient up to the final 1/n (2e-6 relative).  On random inputs the
+  activation rounding (2^-9 relative per element, through the ReLU masks)
+  leaves it within 1e-2 (norm) of the fp64 gradient taken at the bf16
+  weights, and within 3e-2 of the exact one.
 - Adam: fp32 against fp64, 1e-5 relative.
 - selection and best hit: bit-exact (the margin decision is taken in fp32 on
   both sides).
@@ -88,9 +96,19 @@ def test_forward_matches_oracle():
     np.testing.assert_allclose(got, ref, rtol=1e-2, atol=1e-3)
 
 
-def test_gradient_matches_oracle():
+@pytest.fixture
+def grad_kernel():
+    """Select a gradient kernel for one test, and restore the default."""
+    import paper_1304_0681_gb300 as sw
+    yield lambda kind: sw._swgb.sw_set_mlp_grad_kernel(kind)
+    sw._swgb.sw_set_mlp_grad_kernel(sw._swgb.SW_GRAD_AUTO)
+
+
+def test_gradient_matches_oracle(grad_kernel):
     import torch
+    import paper_1304_0681_gb300 as sw
     from paper_1304_0681_gb300 import filter as flt
+    grad_kernel(sw._swgb.SW_GRAD_FP32)
     rng = np.random.default_rng(1)
     model = flt.FilterModel(seed=4)
     n = 300
@@ -107,12 +125,93 @@ def test_gradient_matches_oracle():
     np.testing.assert_allclose(got, ref, atol=1e-3 * scale, rtol=0)
 
 
-def test_gradient_shares_combine_to_the_full_batch():
+def _exact_network(rng):
+    """A sparse network whose every bf16 rounding point is exact: weights in
+    {+-0.5, +-1} (three per hidden unit in W1, three per output in W2),
+    biases and w3 in quarters, so z1, A1, z2, the error signals and dA1 are
+    short binary fractions, and fp32 sums of them over tens of thousands of
+    samples stay exact."""
+    W1 = np.zeros((64, 256))
+    for j in range(256):
+        W1[rng.choice(64, 3, replace=False), j] = rng.choice([-1.0, -0.5, 0.5, 1.0], 3)
+    W2 = np.zeros((256, 64))
+    for k in range(64):
+        W2[rng.choice(256, 3, replace=False), k] = rng.choice([-1.0, -0.5, 0.5, 1.0], 3)
+    b1 = rng.choice([-0.5, 0.0, 0.25, 0.5], 256)
+    b2 = rng.choice([-0.25, 0.0, 0.25], 64)
+    w3 = rng.choice([-0.5, -0.25, 0.0, 0.25, 0.5], 64)
+    return fo.Params(W1, b1, W2, b2, w3, 0.5)
+
+
+def test_tensor_core_gradient_is_exact_when_every_rounding_is(grad_kernel):
+    """The tensor-core kernel on an exactly representable network: features
+    in quarters, targets y - delta with delta in {+-0.25, +-0.5, +-1} (the
+    output y from the fp64 forward, exact in fp32), so every bf16 operand and
+    fp32 sum is exact and the gradient must equal the fp64 one up to the
+    final multiplication by 1/n.  20,000 samples in a random order: several
+    CTAs that sum more than one 128-sample tile, and a ragged last tile."""
+    import torch
+    import paper_1304_0681_gb300 as sw
+    from paper_1304_0681_gb300 import filter as flt
+    grad_kernel(sw._swgb.SW_GRAD_AUTO)
+    rng = np.random.default_rng(11)
+    P = _exact_network(rng)
+    n = 20_000
+    x = rng.choice([0.0, 0.25, 0.5, 0.75], (n, 64))
+    y, (_, z1, _, z2, _) = fo.forward(P, x)
+    assert (z1 > 0).mean() > 0.2 and (z1 <= 0).mean() > 0.2 and (z2 > 0).mean() > 0.2 and (z2 <= 0).mean() > 0.2
+    t = y - rng.choice([-1.0, -0.5, -0.25, 0.25, 0.5, 1.0], n)
+    model = flt.FilterModel(seed=0)
+    model.set_params(P.flat())
+    xb = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).cuda().view(torch.int16)
+    tt = torch.from_numpy(t.astype(np.float32)).cuda()
+    assert np.array_equal(tt.cpu().numpy().astype(np.float64), t)
+    idx = torch.from_numpy(rng.permutation(n).astype(np.int32)).cuda()
+    model.grad(xb, tt, idx)
+    sw.sw_sync_status()
+    got = model.gradient().cpu().numpy().astype(np.float64)
+    ref = fo.backward(P, x, t)
+    assert np.count_nonzero(ref) > 10_000
+    np.testing.assert_allclose(got, ref, rtol=2e-6, atol=1e-7 * np.abs(ref).max())
+
+
+def test_tensor_core_gradient_is_close_to_fp64(grad_kernel):
+    """Random network and features: within 1e-2 (norm) of the fp64 gradient
+    at the bf16 weights, 3e-2 of the exact gradient; and the same bits on a
+    second call (the partial sums are added in a fixed order)."""
+    import torch
+    import paper_1304_0681_gb300 as sw
+    from paper_1304_0681_gb300 import filter as flt
+    grad_kernel(sw._swgb.SW_GRAD_AUTO)
+    rng = np.random.default_rng(12)
+    model = flt.FilterModel(seed=3)
+    n = 8192 + 77
+    x = fo.bf16_round(rng.uniform(0, 0.5, (n, 64)))
+    t = rng.uniform(0, 1, n).astype(np.float32).astype(np.float64)
+    xb = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).cuda().view(torch.int16)
+    tt = torch.from_numpy(t.astype(np.float32)).cuda()
+    model.grad(xb, tt)
+    g1 = model.gradient().clone()
+    model.grad(xb, tt)
+    sw.sw_sync_status()
+    assert torch.equal(g1, model.gradient())
+    got = g1.cpu().numpy().astype(np.float64)
+    P = _model_params(model)
+    Pb = fo.Params(fo.bf16_round(P.W1), P.b1, fo.bf16_round(P.W2), P.b2, P.w3, P.b3)
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel(got, fo.backward(Pb, x, t)) < 1e-2
+    assert rel(got, fo.backward(P, x, t)) < 3e-2
+
+
+@pytest.mark.parametrize("kind", ["tensor_core", "fp32"])
+def test_gradient_shares_combine_to_the_full_batch(kind, grad_kernel):
     """The data-parallel step: each rank's mean gradient over its share of a
     minibatch, weighted by its share and summed (what the all-reduce does),
     equals the gradient of the whole minibatch; three shares, one empty."""
     import torch
+    import paper_1304_0681_gb300 as sw
     from paper_1304_0681_gb300 import filter as flt
+    grad_kernel(sw._swgb.SW_GRAD_AUTO if kind == "tensor_core" else sw._swgb.SW_GRAD_FP32)
     rng = np.random.default_rng(6)
     model = flt.FilterModel(seed=7)
     n = 257
