@@ -45,9 +45,18 @@
 // when the column's H is strictly larger (so the smallest column wins).  The
 // 16-bit keys need (H << TAGB) + TAGM < 32768: H <= 1022 with 5-bit row
 // tags (up to 32 rows per lane), H <= 510 with 6-bit tags (up to 64 rows;
-// the host picks such plans only for classes whose score bound allows it);
-// pairs with larger possible scores use 32-bit
-// keys built from each half (MODE_I16W) or the int32 mode.
+// the host picks such plans only for classes whose score bound allows it).
+//
+// Pairs with larger possible scores (up to 32000) keep their two halves
+// (MODE_I16W) but build no keys: a three-way-max tree over the rows gives
+// each half's column maximum, and when a half's running best strictly rises
+// the lane copies the column's R values into a per-thread snapshot slot for
+// that pair (shared memory, four rows per 16-byte store).  After the chunk
+// the best cell's row is the first row of the snapshot holding the best
+// value: the snapshot is the column where the best was first reached.  This
+// moves the row tracking off the ALU pipe (the kernel's limit) onto the
+// shared-memory stores, so the wide mode costs the same ALU operations per
+// cell as the 16-bit-key mode.  The int32 mode covers the rest.
 #include "sw_band.cuh"
 #include "sw_device.cuh"
 #include "swgb_internal.h"
@@ -139,6 +148,37 @@ __device__ __forceinline__ uint32_t mad_add(uint32_t a, uint32_t one, uint32_t c
     return d;
 }
 
+// Rows 4q .. 4q+3 of a lane's column as one 16-byte word (rows past R: 0,
+// which never equals a best value, as bests are >= 1).
+template <int R, typename V>
+__device__ __forceinline__ uint4 quad_of(const V (&h)[R], int q)
+{
+    const int r = 4 * q;
+    return make_uint4((uint32_t)h[r], r + 1 < R ? (uint32_t)h[r + 1] : 0u, r + 2 < R ? (uint32_t)h[r + 2] : 0u,
+                      r + 3 < R ? (uint32_t)h[r + 3] : 0u);
+}
+
+// First row of a snapshot whose half (shift 0: low, 16: high) equals best.
+template <int R>
+__device__ __forceinline__ int snapshot_row(const uint4 *snap, unsigned stride, uint32_t best, int shift)
+{
+    int row = R - 1;
+    for (int q = (R + 3) / 4 - 1; q >= 0; --q) {
+        const uint4 v = snap[q * stride];
+        if (((v.w >> shift) & 0xFFFFu) == best) row = 4 * q + 3;
+        if (((v.z >> shift) & 0xFFFFu) == best) row = 4 * q + 2;
+        if (((v.y >> shift) & 0xFFFFu) == best) row = 4 * q + 1;
+        if (((v.x >> shift) & 0xFFFFu) == best) row = 4 * q;
+    }
+    return row;
+}
+
+// Dynamic shared memory of a launch: the MODE_I16W snapshot slots.
+__host__ __device__ constexpr int score_snapshot_bytes(int rows, int mode, int threads)
+{
+    return mode == MODE_I16W ? 2 * ((rows + 3) / 4) * 16 * threads : 0;
+}
+
 template <int R, int MODE, bool FMA_ADD>
 __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
 {
@@ -162,6 +202,13 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
             s_tab[threadIdx.x] = threadIdx.x < 4 ? prmt(mis4, ma4, 0x3210u + (4u << (4u * threadIdx.x))) : 0u;
         __syncthreads();
     }
+
+    // MODE_I16W snapshot slots: quad q of pair A at snapA[q * blockDim.x],
+    // of pair B at snapB[q * blockDim.x] (a warp's stores hit distinct banks)
+    constexpr int R4 = (R + 3) / 4;
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    uint4 *const snapA = reinterpret_cast<uint4 *>(s_dyn) + threadIdx.x;
+    uint4 *const snapB = snapA + R4 * blockDim.x;
 
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -289,7 +336,7 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
             V diag_in = 0;             // H(i0-1, j-1)
             V out_h = 0, out_f = 0;    // bottom row (H, F - o) handed to the next lane
             // running best of this chunk
-            uint32_t bk0 = PAIR2 && MODE == MODE_I16 ? TAGM * 0x10001u : 0u, bk1 = 0u;
+            uint32_t bk0 = PAIR2 && MODE == MODE_I16 ? TAGM * 0x10001u : 0u;
             uint32_t rowA = 0, rowB = 0;
             int32_t jA = 0, jB = 0;
             // window stream: 2-bit codes of the next columns (up to 16)
@@ -335,7 +382,7 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
                     if (PAIR2) wwB >>= 2;
                 }
                 V hd = diag_in, hu = up_h, f = up_f;
-                uint32_t ck0 = 0, ck1 = 0, pk0 = 0, pk1 = 0;  // column keys, pending key
+                uint32_t ck0 = 0, pk0 = 0;  // column key (MODE_I16W: column maximum), pending key
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const V s = (V)prmt(twA, twB, sel[r]);
@@ -346,34 +393,27 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
                     hd = h[r];
                     h[r] = hn;
                     hu = hn;
-                    uint32_t k0, k1 = 0;
+                    uint32_t k0;
                     if (MODE == MODE_I32) {
                         k0 = mad_add((uint32_t)hn, 1u << TAGB, TAGM - (uint32_t)r);
                     } else if (MODE == MODE_I16) {
                         k0 = mad_add((uint32_t)hn, 1u << TAGB, (TAGM - (uint32_t)r) * 0x10001u);
                     } else {
-                        k0 = mad_add((uint32_t)hn, 65536u, TAGM - (uint32_t)r);
-                        k1 = ((uint32_t)hn & 0xFFFF0000u) | (TAGM - (uint32_t)r);
+                        k0 = (uint32_t)hn;
                     }
-                    // three-way max over pairs of rows
+                    // three-way max over pairs of rows (H >= 0, so the relu
+                    // max of the first pair is exact)
                     if (r % 2 == 0) {
                         pk0 = k0;
-                        pk1 = k1;
-                    } else if (MODE == MODE_I16) {
+                    } else if (PAIR2) {
                         ck0 = r == 1 ? __vimax_s16x2_relu(pk0, k0) : __vimax3_s16x2(ck0, pk0, k0);
                     } else {
                         ck0 = r == 1 ? max(pk0, k0) : (uint32_t)__vimax3_s32((int)ck0, (int)pk0, (int)k0);
-                        if (MODE == MODE_I16W)
-                            ck1 = r == 1 ? max(pk1, k1) : (uint32_t)__vimax3_s32((int)ck1, (int)pk1, (int)k1);
                     }
                 }
                 if (R % 2 == 1) {
-                    if (MODE == MODE_I16) {
-                        ck0 = R == 1 ? pk0 : __vimax_s16x2_relu(ck0, pk0);
-                    } else {
-                        ck0 = R == 1 ? pk0 : max(ck0, pk0);
-                        if (MODE == MODE_I16W) ck1 = R == 1 ? pk1 : max(ck1, pk1);
-                    }
+                    if (PAIR2) ck0 = R == 1 ? pk0 : __vimax_s16x2_relu(ck0, pk0);
+                    else ck0 = R == 1 ? pk0 : max(ck0, pk0);
                 }
                 diag_in = up_h;
                 out_h = h[R - 1];
@@ -397,8 +437,21 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
                     if (up & 0xFFFFu) { rowA = ck0; jA = j; }
                     if (up > 0xFFFFu) { rowB = ck0; jB = j; }
                 } else {
-                    if (ck0 > (bk0 | 0xFFFFu)) { bk0 = ck0; jA = j; }
-                    if (ck1 > (bk1 | 0xFFFFu)) { bk1 = ck1; jB = j; }
+                    // per-half maximum of H; a half that rose is a strict
+                    // improvement: keep the column for the row search
+                    const uint32_t nb = __vimax_s16x2_relu(bk0, ck0);
+                    const uint32_t up = nb ^ bk0;
+                    bk0 = nb;
+                    if (up & 0xFFFFu) {
+                        jA = j;
+#pragma unroll
+                        for (int q = 0; q < R4; ++q) snapA[q * blockDim.x] = quad_of<R>(h, q);
+                    }
+                    if (up > 0xFFFFu) {
+                        jB = j;
+#pragma unroll
+                        for (int q = 0; q < R4; ++q) snapB[q * blockDim.x] = quad_of<R>(h, q);
+                    }
                 }
             }
             // fold the chunk's best into the 64-bit per-lane best
@@ -411,9 +464,9 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
                 if (ha) bestA = max(bestA, cell_key(ha, jA, rbase + (int)TAGM - (int)(rowA & TAGM)));
                 if (hb) bestB = max(bestB, cell_key(hb, jB, rbase + (int)TAGM - (int)((rowB >> 16) & TAGM)));
             } else {
-                const uint32_t ha = bk0 >> 16, hb = bk1 >> 16;
-                if (ha) bestA = max(bestA, cell_key(ha, jA, rbase + (int)TAGM - (int)(bk0 & 0xFFFFu)));
-                if (hb) bestB = max(bestB, cell_key(hb, jB, rbase + (int)TAGM - (int)(bk1 & 0xFFFFu)));
+                const uint32_t ha = bk0 & 0xFFFFu, hb = bk0 >> 16;
+                if (ha) bestA = max(bestA, cell_key(ha, jA, rbase + snapshot_row<R>(snapA, blockDim.x, ha, 0)));
+                if (hb) bestB = max(bestB, cell_key(hb, jB, rbase + snapshot_row<R>(snapB, blockDim.x, hb, 16)));
             }
             __syncwarp();
         }
@@ -454,11 +507,12 @@ const int kScoreRows[N_SCORE_ROWS] = {8, 16, 20, 25, 32, 50};
 template <int R>
 static int launch_r(int mode, bool fma, const ScoreLaunch &L, int blocks, int threads, cudaStream_t st)
 {
+    const int smem = score_snapshot_bytes(R, MODE_I16W, threads);
     if (mode == MODE_I32) k_score<R, MODE_I32, true><<<blocks, threads, 0, st>>>(L);
     else if (mode == MODE_I16 && fma) k_score<R, MODE_I16, true><<<blocks, threads, 0, st>>>(L);
     else if (mode == MODE_I16) k_score<R, MODE_I16, false><<<blocks, threads, 0, st>>>(L);
-    else if (mode == MODE_I16W && fma) k_score<R, MODE_I16W, true><<<blocks, threads, 0, st>>>(L);
-    else if (mode == MODE_I16W) k_score<R, MODE_I16W, false><<<blocks, threads, 0, st>>>(L);
+    else if (mode == MODE_I16W && fma) k_score<R, MODE_I16W, true><<<blocks, threads, smem, st>>>(L);
+    else if (mode == MODE_I16W) k_score<R, MODE_I16W, false><<<blocks, threads, smem, st>>>(L);
     else return SW_ERR_INTERNAL;
     count_launch();
     return launch_status();
@@ -493,12 +547,13 @@ int launch_score_variant(int v, const ScoreLaunch &L, int blocks, cudaStream_t s
 }
 
 template <int R>
-static const void *kernel_ptr(int mode)
+static const void *kernel_ptr(int mode, bool fma)
 {
     switch (mode) {
     case MODE_I32: return (const void *)k_score<R, MODE_I32, true>;
-    case MODE_I16: return (const void *)k_score<R, MODE_I16, false>;
-    case MODE_I16W: return (const void *)k_score<R, MODE_I16W, false>;
+    case MODE_I16: return fma ? (const void *)k_score<R, MODE_I16, true> : (const void *)k_score<R, MODE_I16, false>;
+    case MODE_I16W:
+        return fma ? (const void *)k_score<R, MODE_I16W, true> : (const void *)k_score<R, MODE_I16W, false>;
     default: return nullptr;
     }
 }
@@ -513,24 +568,36 @@ int score_variant_blocks(int v, int sm_count, int *blocks)
     return SW_OK;
 }
 
+// Registers and resident blocks per SM of the (rows, mode) kernels; also
+// lets them take their dynamic shared memory, so it runs before any launch
+// of them (both diagonal-add forms; the grid follows the fewer blocks).
 int score_kernel_regs(int rows, int mode, int *regs, int *max_blocks_per_sm, int threads)
 {
-    const void *fn = nullptr;
-    switch (rows) {
-    case 8: fn = kernel_ptr<8>(mode); break;
-    case 16: fn = kernel_ptr<16>(mode); break;
-    case 20: fn = kernel_ptr<20>(mode); break;
-    case 25: fn = kernel_ptr<25>(mode); break;
-    case 32: fn = kernel_ptr<32>(mode); break;
-    case 50: fn = kernel_ptr<50>(mode); break;
-    default: return SW_ERR_INVALID_ARG;
+    const int smem = score_snapshot_bytes(rows, mode, threads);
+    *regs = 0;
+    *max_blocks_per_sm = 0;
+    for (int f = 0; f < 2; ++f) {
+        const void *fn = nullptr;
+        switch (rows) {
+        case 8: fn = kernel_ptr<8>(mode, f); break;
+        case 16: fn = kernel_ptr<16>(mode, f); break;
+        case 20: fn = kernel_ptr<20>(mode, f); break;
+        case 25: fn = kernel_ptr<25>(mode, f); break;
+        case 32: fn = kernel_ptr<32>(mode, f); break;
+        case 50: fn = kernel_ptr<50>(mode, f); break;
+        default: return SW_ERR_INVALID_ARG;
+        }
+        if (!fn) return SW_ERR_INVALID_ARG;
+        if (smem > 48 * 1024 &&
+            cuda_failed(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+            return SW_ERR_CUDA;
+        cudaFuncAttributes a;
+        if (cuda_failed(cudaFuncGetAttributes(&a, fn))) return SW_ERR_CUDA;
+        int bps = 0;
+        if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, smem))) return SW_ERR_CUDA;
+        *regs = std::max(*regs, a.numRegs);
+        *max_blocks_per_sm = f == 0 ? bps : std::min(*max_blocks_per_sm, bps);
     }
-    if (!fn) return SW_ERR_INVALID_ARG;
-    cudaFuncAttributes a;
-    if (cuda_failed(cudaFuncGetAttributes(&a, fn))) return SW_ERR_CUDA;
-    *regs = a.numRegs;
-    if (cuda_failed(cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, fn, threads, 0)))
-        return SW_ERR_CUDA;
     return SW_OK;
 }
 

@@ -105,7 +105,10 @@ def test_int32_path_long_reads():
 @pytest.mark.parametrize("alphabet", [2, 4])
 def test_random_lengths_and_ties(alphabet):
     wl = synth.random_pairs(1500, (1, 200), (0, 260), seed=10 + alphabet, alphabet=alphabet)
-    for sc in (DEFAULT, (1, -1, -2, -1), (3, 0, -3, -3)):
+    # WIDE16 puts reads of 21 bases and more in the wide 16-bit mode, whose
+    # end-cell row comes from a column snapshot: 2-letter alphabets make
+    # rows of that column tie
+    for sc in (DEFAULT, (1, -1, -2, -1), (3, 0, -3, -3), WIDE16):
         got = run_gpu(wl, sc)
         assert_parity(wl, got, sc)
 
@@ -167,16 +170,19 @@ def test_key_mode_boundaries():
 
 @pytest.mark.parametrize("lanes,rows", [(1, 8), (3, 16), (4, 25), (5, 20), (7, 16), (13, 8), (32, 8), (32, 32),
                                         (2, 50), (3, 50)])
-def test_lane_plans(lanes, rows):
+@pytest.mark.parametrize("scoring", [DEFAULT, WIDE16], ids=["keys16", "wide16"])
+def test_lane_plans(lanes, rows, scoring):
     """Every (lanes, rows) plan gives the same answer, including plans that
-    split a read into several row chunks (lanes * rows < read length)."""
+    split a read into several row chunks (lanes * rows < read length), in
+    the 16-bit-key mode and in the wide 16-bit mode (row snapshots, whose
+    last 16-byte word is partly padding when rows is not a multiple of 4)."""
     import paper_1304_0681_gb300 as sw
     if lanes * rows < 100 and lanes != 32:
         pytest.skip("plan must cover the read unless it uses 32 lanes")
     wl = synth.generate("parity", seed=5, n_reads=300)
     sw.sw_set_plan(100, lanes, rows)
-    got = run_gpu(wl, DEFAULT)
-    assert_parity(wl, got, DEFAULT)
+    got = run_gpu(wl, scoring)
+    assert_parity(wl, got, scoring)
 
 
 def test_multichunk_long_reads():
@@ -190,7 +196,7 @@ def test_multichunk_long_reads():
         L = min(r1 - r0, w1 - w0 - 10)
         wl.windows[w0 + 5:w0 + 5 + L] = wl.reads[r0:r0 + L]
     sw.sw_set_plan(100000, 32, 8)
-    for sc in (DEFAULT, (1, -1, -2, -1)):
+    for sc in (DEFAULT, (1, -1, -2, -1), (20, -10, -25, -2)):
         got = run_gpu(wl, sc)
         assert_parity(wl, got, sc)
 
