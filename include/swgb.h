@@ -197,9 +197,10 @@ int sw_batch_align_masked(const uint8_t *reads, const int64_t *read_offsets, int
  * is window p of window_offsets (device int64[n_pairs + 1]).
  *
  * sw_filter_features: per pair 64 bf16 features (device uint16[n_pairs * 64],
- * row-major): the 4-mers q = 64 b0 + 16 b1 + 4 b2 + b3 of read and window
- * are counted, and f[k] = sum over b of min(c_read(4k+b), c_window(4k+b)) /
- * (m - 3) for k = 0..63 (0 when the read is shorter than 4).
+ * row-major, 16-byte aligned; SW_ERR_INVALID_ARG otherwise): the 4-mers
+ * q = 64 b0 + 16 b1 + 4 b2 + b3 of read and window are counted, and
+ * f[k] = sum over b of min(c_read(4k+b), c_window(4k+b)) / (m - 3) for
+ * k = 0..63 (0 when the read is shorter than 4).
  */
 int sw_filter_features(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads,
                        const uint8_t *windows, const int64_t *window_offsets,

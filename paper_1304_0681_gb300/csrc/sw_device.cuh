@@ -62,13 +62,4 @@ __device__ __forceinline__ uint32_t key_h(uint64_t k) { return (uint32_t)(k >> 3
 __device__ __forceinline__ int32_t key_j(uint64_t k) { return 0x1FFFFF - (int32_t)((k >> 16) & 0x1FFFFF); }
 __device__ __forceinline__ int32_t key_i(uint64_t k) { return 0xFFFF - (int32_t)(k & 0xFFFF); }
 
-// Status bits written by kernels (atomicOr) and read back by the host.
-enum : int32_t {
-    ST_BAD_INPUT = 1,
-    ST_CAPACITY = 2,
-    ST_INTERNAL = 4,
-    ST_TIMEOUT = 8,
-    ST_UNSUPPORTED = 16,
-};
-
 }  // namespace swgb

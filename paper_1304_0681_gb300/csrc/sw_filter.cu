@@ -12,10 +12,12 @@
 // divided by m - 3, giving 64 values stored as bf16.
 //
 // Network 64 -> 256 -> 64 -> 1 with ReLU: y = w3 . relu(W2^T relu(W1^T f +
-// b1) + b2) + b3.  Serving runs on the tensor cores (mma.sync bf16 with fp32
-// accumulation, weights in shared memory); training uses an fp32 forward and
-// backward on the CUDA cores (mean squared error against SW score / (match m))
-// and Adam.
+// b1) + b2) + b3.  Serving runs on the tensor cores (tcgen05 with TMEM
+// accumulators, sw_mlp_tc.cu; an mma.sync kernel here is the selectable
+// alternative), bf16 operands and fp32 accumulation.  Training minimises the
+// mean squared error against SW score / (match m): the gradient on the
+// tensor cores as well (sw_mlp_tc.cu; an fp32 CUDA-core kernel here is the
+// selectable alternative), then Adam.
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -568,9 +570,9 @@ static int grid_for(int64_t items, int threads, int cap)
     return (int)(b < 1 ? 1 : b);
 }
 
-int launch_features(const FeatureParams &P, cudaStream_t st)
+int launch_features(const FeatureParams &P, int sm_count, cudaStream_t st)
 {
-    k_features<<<grid_for(P.n_reads, 8, 152 * 16), 256, 0, st>>>(P);
+    k_features<<<grid_for(P.n_reads, 8, (int64_t)sm_count * 16), 256, 0, st>>>(P);
     count_launch();
     return launch_status();
 }
@@ -692,11 +694,14 @@ int sw_filter_features(const uint8_t *reads, const int64_t *read_offsets, int64_
     if (n_reads == 0) return SW_OK;
     if (!reads || !read_offsets || !windows || !window_offsets || !cand_offsets || !out_features)
         return SW_ERR_INVALID_ARG;
-    if (((uintptr_t)reads & 15u) || ((uintptr_t)windows & 15u) || ((uintptr_t)out_features & 3u))
+    if (((uintptr_t)reads & 15u) || ((uintptr_t)windows & 15u) || ((uintptr_t)out_features & 15u))
         return SW_ERR_INVALID_ARG;
     FeatureParams P{(const uint32_t *)reads, read_offsets, n_reads, (const uint32_t *)windows, window_offsets,
                     cand_offsets, out_features};
-    return launch_features(P, (cudaStream_t)stream);
+    int sms = 0;
+    const int rc = sm_count_now(&sms);
+    if (rc) return rc;
+    return launch_features(P, sms, (cudaStream_t)stream);
 }
 
 int64_t sw_mlp_bytes(void) { return mlp_floats() * (int64_t)sizeof(float); }

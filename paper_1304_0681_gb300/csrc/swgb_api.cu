@@ -266,16 +266,6 @@ bool scoring_ok(const sw_scoring_t *s)
            s->match - s->gap_open <= 127;
 }
 
-int status_to_code(int32_t st)
-{
-    if (st & ST_BAD_INPUT) return SW_ERR_DEVICE_INPUT;
-    if (st & ST_UNSUPPORTED) return SW_ERR_UNSUPPORTED;
-    if (st & ST_CAPACITY) return SW_ERR_CAPACITY;
-    if (st & ST_TIMEOUT) return SW_ERR_DEVICE_TIMEOUT;
-    if (st & ST_INTERNAL) return SW_ERR_INTERNAL;
-    return SW_OK;
-}
-
 // The scratch of one batch execution: arrays sized by the pair count, the
 // class tables and plans, and the dynamic part (score chunk boundaries and
 // traceback slots).

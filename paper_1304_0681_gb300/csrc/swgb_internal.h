@@ -7,6 +7,29 @@
 
 namespace swgb {
 
+// Status bits written by kernels (atomicOr) and read back by the host.
+enum : int32_t {
+    ST_BAD_INPUT = 1,
+    ST_CAPACITY = 2,
+    ST_INTERNAL = 4,
+    ST_TIMEOUT = 8,
+    ST_UNSUPPORTED = 16,
+};
+
+// The error code a call returns for a device status word: invalid input
+// first, then an unsupported shape, an exhausted capacity, a device wait
+// that ran out (a tensor-core kernel's bounded mbarrier wait), and internal
+// errors; SW_OK when no bit is set.
+inline int status_to_code(int32_t st)
+{
+    if (st & ST_BAD_INPUT) return SW_ERR_DEVICE_INPUT;
+    if (st & ST_UNSUPPORTED) return SW_ERR_UNSUPPORTED;
+    if (st & ST_CAPACITY) return SW_ERR_CAPACITY;
+    if (st & ST_TIMEOUT) return SW_ERR_DEVICE_TIMEOUT;
+    if (st & ST_INTERNAL) return SW_ERR_INTERNAL;
+    return SW_OK;
+}
+
 // Inputs of one batch as the kernels see them (all device pointers).
 struct PairSet {
     const uint32_t *reads;      // packed reads (words)
@@ -346,7 +369,7 @@ int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, const int32_t *cla
                         int32_t *bucket_start, int32_t *cursor, int32_t *order, cudaStream_t st);
 int launch_alu_probe(int kind, int64_t iters, int blocks, int threads, uint32_t *out, cudaStream_t st);
 
-int launch_features(const FeatureParams &P, cudaStream_t st);
+int launch_features(const FeatureParams &P, int sm_count, cudaStream_t st);
 int64_t mlp_floats();
 int launch_mlp_init(float *model, uint64_t seed, cudaStream_t st);
 int launch_mlp_refresh(float *model, cudaStream_t st);

@@ -56,24 +56,28 @@ class FilterModel:
         _swgb.sw_mlp_adam(self.buf, lr, self.step)
 
     def train(self, features: torch.Tensor, target: torch.Tensor, epochs: int = 4, batch: int = 8192,
-              lr: float = 2e-3, seed: int = 0, group=None) -> list:
+              lr: float = 2e-3, seed: int = 0, group=None, samples: torch.Tensor | None = None) -> list:
         """Minibatch Adam on the mean squared error; returns the mean loss of
-        each epoch measured with the serving forward.
+        each epoch measured with the serving forward.  `samples` (int32 row
+        indices, repeats allowed) is the multiset an epoch draws from, in a new
+        random order each epoch; by default every row once.
 
         With a process group, every rank holds the same training set and the
         same seed: each takes its share of every minibatch, and the gradients
         are combined by an all-reduce before the (identical) Adam step, so
         all ranks keep the same parameters as one rank training alone."""
-        n = features.shape[0]
+        n_rows = features.shape[0]
         gen = torch.Generator(device=features.device)
         gen.manual_seed(seed)
         rank, world = 0, 1
         if group is not None:
             import torch.distributed as dist
             rank, world = dist.get_rank(group), dist.get_world_size(group)
+        n = n_rows if samples is None else samples.numel()
         losses = []
         for _ in range(epochs):
-            perm = torch.randperm(n, generator=gen, device=features.device).to(torch.int32)
+            perm = torch.randperm(n, generator=gen, device=features.device)
+            perm = (perm if samples is None else samples[perm]).to(torch.int32)
             for s in range(0, n - batch + 1, batch):
                 if world == 1:
                     self.grad(features, target, perm[s:s + batch])
@@ -185,6 +189,22 @@ def filtered_batches(model: FilterModel, batches, k: int, tau: float, scoring, n
     from .seed import run_on_worker_streams
     return run_on_worker_streams(model.buf.device, list(batches),
                                  lambda bt, s: _filter_host_batch(model, bt, k, tau, scoring), n_streams)
+
+
+def oversample_top(score: np.ndarray, cand_offsets: np.ndarray, top: int = 1, times: int = 4) -> np.ndarray:
+    """Training rows with each read's `top` best-scoring candidates (by SW
+    score, ties by index) repeated `times` times and every other candidate
+    once: the mean squared error then weighs the ordering at the top of a
+    read's list, which decides best-hit recall, above the bulk of decoys.
+    Host-side bookkeeping over scores already computed on the GPU."""
+    nr = len(cand_offsets) - 1
+    counts = np.diff(cand_offsets)
+    rid = np.repeat(np.arange(nr), counts)
+    order = np.lexsort((np.arange(len(score)), -np.asarray(score), rid))
+    rank = np.empty(len(score), np.int64)
+    rank[order] = np.arange(len(score)) - np.repeat(cand_offsets[:-1], counts)[order]
+    rows = np.arange(len(score), dtype=np.int64)
+    return np.concatenate([rows, np.repeat(rows[rank < top], times - 1)]).astype(np.int32)
 
 
 def targets(score: torch.Tensor, read_len: torch.Tensor, match: int) -> torch.Tensor:

@@ -48,3 +48,23 @@ def test_calibrate_reports_none_when_unreachable():
     pred = np.array([0.9, 0.5, 0.0], np.float32)
     score = np.array([1, 2, 9])
     assert flt.calibrate(pred, score, off, 1.0, ks=(1, 2), taus=[0.0, 0.1]) is None
+
+
+@pytest.mark.parametrize("top,times", [(1, 4), (2, 3), (1, 1)])
+def test_oversample_top_against_a_loop(top, times):
+    """The training multiset of filter.oversample_top: every row once, plus
+    each read's `top` best rows (score descending, lower index first on
+    ties) `times - 1` more times; checked against a per-read loop."""
+    from paper_1304_0681_gb300 import filter as flt
+    rng = np.random.default_rng(top * 10 + times)
+    counts = rng.integers(0, 9, 300)
+    off = np.zeros(len(counts) + 1, np.int64)
+    np.cumsum(counts, out=off[1:])
+    score = rng.integers(0, 4, int(off[-1]))            # ties on purpose
+    got = np.sort(flt.oversample_top(score, off, top, times))
+    want = list(range(int(off[-1])))
+    for r in range(len(counts)):
+        rows = sorted(range(off[r], off[r + 1]), key=lambda p: (-score[p], p))
+        for p in rows[:top]:
+            want += [p] * (times - 1)
+    np.testing.assert_array_equal(got, np.sort(np.array(want, dtype=np.int64)))

@@ -75,6 +75,34 @@ def test_features_match_oracle():
     np.testing.assert_allclose(got3, ref3, rtol=2 ** -8, atol=0)
 
 
+def test_features_of_giant_windows():
+    """Windows longer than 65,538 bases, where a 4-mer can occur more often
+    than 16-bit counters hold (a homopolymer run here), take 32-bit
+    counters; next to them in the same candidate group, ordinary windows."""
+    import torch
+    from paper_1304_0681_gb300 import filter as flt
+    rng = np.random.default_rng(21)
+    # 7,997 AAAA in the read, 71,997 in the first window: counted modulo
+    # 2^16 the window's would be 6,461 and the shared count would drop
+    reads = [np.zeros(8100, np.uint8), rng.integers(0, 4, 300).astype(np.uint8)]
+    reads[0][8000:] = rng.integers(0, 4, 100)
+    wins = [np.zeros(75_000, np.uint8), rng.integers(0, 4, 500).astype(np.uint8),
+            rng.integers(0, 4, 66_000).astype(np.uint8), np.zeros(3, np.uint8),
+            rng.integers(0, 4, 1200).astype(np.uint8)]
+    wins[0][-3000:] = rng.integers(0, 4, 3000)
+    pair_read = np.array([0, 0, 0, 1, 1], np.int64)
+    roff = np.concatenate([[0], np.cumsum([len(r) for r in reads])]).astype(np.int64)
+    woff = np.concatenate([[0], np.cumsum([len(w) for w in wins])]).astype(np.int64)
+    wl = synth.Workload("giant", np.concatenate(reads), roff, np.concatenate(wins), woff, pair_read,
+                        np.array([0, 3, 5], np.int64), np.zeros(5, np.uint8), np.zeros(2, np.int32))
+    b = _batch(wl)
+    co = torch.from_numpy(wl.cand_offsets).cuda()
+    got = _bf16_to_f64(flt.features(b, co))
+    ref = fo.bf16_round(fo.features_batch(wl.reads, wl.read_offsets, wl.windows, wl.window_offsets, wl.pair_read))
+    np.testing.assert_allclose(got, ref, rtol=2 ** -8, atol=0)
+    assert ref[0][0] > 0.98  # nearly every read 4-mer is AAAA, all shared
+
+
 def _model_params(model):
     return fo.Params.from_flat(model.params().cpu().numpy().astype(np.float64))
 
