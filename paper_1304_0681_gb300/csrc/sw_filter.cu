@@ -33,61 +33,61 @@ constexpr unsigned FM = 0xffffffffu;
 
 // ---------------------------------------------------------------- features
 
-// Count the 4-mers of bases [s, s+len) into hist (shared, 256 x uint32);
-// lane l takes positions 8l .. 8l+7 of every 256.
-__device__ __forceinline__ void count_kmers32(const uint32_t *__restrict__ buf, int64_t s, int32_t len,
-                                              uint32_t *hist, int lane)
+// 4-mers are indexed in stream order, w = b0 + 4 b1 + 16 b2 + 64 b3 (b0 the
+// first base, as the 2-bit packing stores it), so a 4-mer's counter address
+// is one shift and one mask of the packed word.  Feature slot k = 16 b0 +
+// 4 b1 + b2 is prefix p = w & 63 = slot_prefix(k) read the other way round,
+// summed over the last base b3 = w >> 6.
+__device__ __forceinline__ int slot_prefix(int k) { return (k >> 4) + 4 * ((k >> 2) & 3) + 16 * (k & 3); }
+
+// The up-to-8 4-mers at positions base .. base + cnt - 1 of v (bases base ..
+// base + 10 in bits 0 .. 21) as counter increments: 32-bit counters at word w.
+__device__ __forceinline__ void bump8_words(uint32_t v, int cnt, uint32_t *hist)
+{
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+        if (t < cnt) atomicAdd(&hist[(v >> (2 * t)) & 0xFFu], 1u);
+}
+
+// Byte counters, four per word: word p = w & 63, byte b3 = w >> 6.
+__device__ __forceinline__ void bump8_bytes(uint32_t v, int cnt, uint32_t *hist)
+{
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+        if (t < cnt) {
+            const uint32_t w = v >> (2 * t);
+            atomicAdd(&hist[w & 63u], 1u << ((w >> 3) & 0x18u));
+        }
+}
+
+// Count the 4-mers of bases [s, s+len) into hist; lane l takes positions
+// 8l .. 8l+7 of every 256.  BYTES: four byte counters per word (exact while
+// no 4-mer occurs more than 255 times, i.e. for at most 258 bases), else
+// 256 32-bit counters.
+template <bool BYTES>
+__device__ __forceinline__ void count_kmers(const uint32_t *__restrict__ buf, int64_t s, int32_t len,
+                                            uint32_t *hist, int lane)
 {
     const int nk = len - 3;  // number of 4-mers
     for (int base = lane * 8; base < nk; base += 32 * 8) {
         // 8 k-mers starting at base .. base+7 need bases base .. base+10
         const uint32_t v = load_bases(buf, s + base, min(11, len - base));
-        const int cnt = min(8, nk - base);
-        for (int t = 0; t < cnt; ++t) {
-            const uint32_t w = (v >> (2 * t)) & 0xFFu;  // b0 in bits 0-1 ... b3 in bits 6-7
-            const uint32_t q = ((w & 3u) << 6) | (((w >> 2) & 3u) << 4) | (((w >> 4) & 3u) << 2) | (w >> 6);
-            atomicAdd(&hist[q], 1u);
-        }
-    }
-}
-
-// Same counts as bytes, four per word: word q >> 2 (the 3-base prefix), byte
-// q & 3 (the last base).  Exact while no 4-mer occurs more than 255 times,
-// i.e. for sequences of at most 258 bases.
-__device__ __forceinline__ void count_kmers8(const uint32_t *__restrict__ buf, int64_t s, int32_t len,
-                                             uint32_t *hist, int lane)
-{
-    const int nk = len - 3;
-    for (int base = lane * 8; base < nk; base += 32 * 8) {
-        const uint32_t v = load_bases(buf, s + base, min(11, len - base));
-        const int cnt = min(8, nk - base);
-        for (int t = 0; t < cnt; ++t) {
-            const uint32_t w = (v >> (2 * t)) & 0xFFu;
-            const uint32_t pre = ((w & 3u) << 4) | (((w >> 2) & 3u) << 2) | ((w >> 4) & 3u);
-            atomicAdd(&hist[pre], 1u << (8u * (w >> 6)));
-        }
+        if (BYTES) bump8_bytes(v, nk - base, hist);
+        else bump8_words(v, nk - base, hist);
     }
 }
 
 constexpr int kByteCountMax = 258;
 
 // Byte counters of the 4-mers at positions first .. first + cnt - 1 of a
-// sequence (first + cnt <= len - 3): two 19-base loads, 16 k-mers each.
+// sequence (first + cnt <= len - 3), eight at a time.
 __device__ __forceinline__ void count_run8(const uint32_t *__restrict__ buf, int64_t s, int32_t len, int first,
                                            int cnt, uint32_t *hist)
 {
-    for (int h = 0; h < cnt; h += 16) {
+    for (int h = 0; h < cnt; h += 8) {
         const int q = first + h;
-        const int k = min(16, cnt - h);              // k-mers of this half
-        const int nb = min(k + 3, len - q);          // bases they span
-        const uint32_t lo = load_bases(buf, s + q, min(16, nb));
-        const uint32_t hi = nb > 16 ? load_bases(buf, s + q + 16, nb - 16) : 0u;
-        const uint64_t v = ((uint64_t)hi << 32) | lo;
-        for (int t = 0; t < k; ++t) {
-            const uint32_t w = (uint32_t)(v >> (2 * t)) & 0xFFu;
-            const uint32_t pre = ((w & 3u) << 4) | (((w >> 2) & 3u) << 2) | ((w >> 4) & 3u);
-            atomicAdd(&hist[pre], 1u << (8u * (w >> 6)));
-        }
+        const uint32_t v = load_bases(buf, s + q, min(11, len - q));
+        bump8_bytes(v, cnt - h, hist);
     }
 }
 
@@ -99,6 +99,9 @@ __global__ void __launch_bounds__(256) k_features(FeatureParams P)
     // byte-counter path: four candidates at a time, 8 lanes and 64 words each
     const int sg = lane >> 3, sl = lane & 7;
     uint32_t *hs = hist[warp][1] + 64 * sg;
+    // this lane's output slots: 8 sl .. 8 sl + 7 on the byte path, 2 lane
+    // and 2 lane + 1 on the word path (prefixes p and p + 16)
+    const int pw = slot_prefix(2 * lane);
     for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < P.n_reads; r += (int64_t)gridDim.x * 8) {
         const int64_t c0 = P.cand_off[r], c1 = P.cand_off[r + 1];
         if (c0 >= c1) continue;
@@ -108,8 +111,8 @@ __global__ void __launch_bounds__(256) k_features(FeatureParams P)
         for (int q = lane; q < 256; q += 32) hr[q] = 0;
         __syncwarp();
         if (m >= 4) {
-            if (rbytes) count_kmers8(P.reads, rs, m, hr, lane);
-            else count_kmers32(P.reads, rs, m, hr, lane);
+            if (rbytes) count_kmers<true>(P.reads, rs, m, hr, lane);
+            else count_kmers<false>(P.reads, rs, m, hr, lane);
         }
         __syncwarp();
         const float inv = m >= 4 ? 1.f / (float)(m - 3) : 0.f;
@@ -137,9 +140,10 @@ __global__ void __launch_bounds__(256) k_features(FeatureParams P)
                     uint32_t f2[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int k0 = 8 * sl + 2 * q;
-                        const uint32_t a = (uint32_t)__dp4a(__vminu4(hr[k0], hs[k0]), 0x01010101u, 0u);
-                        const uint32_t b = (uint32_t)__dp4a(__vminu4(hr[k0 + 1], hs[k0 + 1]), 0x01010101u, 0u);
+                        // slots 8 sl + 2q and + 1: prefixes p and p + 16
+                        const int p0 = slot_prefix(8 * sl + 2 * q);
+                        const uint32_t a = (uint32_t)__dp4a(__vminu4(hr[p0], hs[p0]), 0x01010101u, 0u);
+                        const uint32_t b = (uint32_t)__dp4a(__vminu4(hr[p0 + 16], hs[p0 + 16]), 0x01010101u, 0u);
                         const __nv_bfloat162 f = __floats2bfloat162_rn((float)a * inv, (float)b * inv);
                         f2[q] = *reinterpret_cast<const uint32_t *>(&f);
                     }
@@ -155,32 +159,25 @@ __global__ void __launch_bounds__(256) k_features(FeatureParams P)
             const int32_t n = (int32_t)(P.win_off[p + 1] - ws);
             uint32_t s0 = 0, s1 = 0;
             if (rbytes && n <= kByteCountMax) {
-                // byte counters: feature k = byte sum of min(read word k, window word k)
+                // byte counters: feature p = byte sum of min(read word p, window word p)
                 hw[lane] = 0;
                 hw[lane + 32] = 0;
                 __syncwarp();
-                if (n >= 4 && m >= 4) count_kmers8(P.wins, ws, n, hw, lane);
+                if (n >= 4 && m >= 4) count_kmers<true>(P.wins, ws, n, hw, lane);
                 __syncwarp();
-                s0 = (uint32_t)__dp4a(__vminu4(hr[2 * lane], hw[2 * lane]), 0x01010101u, 0u);
-                s1 = (uint32_t)__dp4a(__vminu4(hr[2 * lane + 1], hw[2 * lane + 1]), 0x01010101u, 0u);
+                s0 = (uint32_t)__dp4a(__vminu4(hr[pw], hw[pw]), 0x01010101u, 0u);
+                s1 = (uint32_t)__dp4a(__vminu4(hr[pw + 16], hw[pw + 16]), 0x01010101u, 0u);
             } else {
                 for (int q = lane; q < 256; q += 32) hw[q] = 0;
                 __syncwarp();
-                if (n >= 4 && m >= 4) count_kmers32(P.wins, ws, n, hw, lane);
+                if (n >= 4 && m >= 4) count_kmers<false>(P.wins, ws, n, hw, lane);
                 __syncwarp();
-                if (rbytes) {
-                    // read in bytes, window in words
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        s0 += min((hr[2 * lane] >> (8 * b)) & 0xFFu, hw[8 * lane + b]);
-                        s1 += min((hr[2 * lane + 1] >> (8 * b)) & 0xFFu, hw[8 * lane + 4 + b]);
-                    }
-                } else {
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        s0 += min(hr[8 * lane + b], hw[8 * lane + b]);
-                        s1 += min(hr[8 * lane + 4 + b], hw[8 * lane + 4 + b]);
-                    }
+                for (int b = 0; b < 4; ++b) {
+                    const uint32_t r0 = rbytes ? (hr[pw] >> (8 * b)) & 0xFFu : hr[pw + 64 * b];
+                    const uint32_t r1 = rbytes ? (hr[pw + 16] >> (8 * b)) & 0xFFu : hr[pw + 16 + 64 * b];
+                    s0 += min(r0, hw[pw + 64 * b]);
+                    s1 += min(r1, hw[pw + 16 + 64 * b]);
                 }
             }
             const __nv_bfloat162 f = __floats2bfloat162_rn((float)s0 * inv, (float)s1 * inv);
