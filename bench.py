@@ -76,6 +76,7 @@ def _args():
     ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain exhaustive arm")
     ap.add_argument("--e2e-batches", type=int, default=8, help="host batches of the full-mix end-to-end leg")
     ap.add_argument("--no-extra", action="store_true", help="skip the uneven and full-mix sections")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the autotuned re-run of the uneven batch")
     ap.add_argument("--no-seeding", action="store_true", help="skip the seeding section")
     ap.add_argument("--only-seeding", action="store_true", help="run the seeding section alone")
     ap.add_argument("--seed-ref", default="human", help="reference recipe of the seeding section")
@@ -83,6 +84,8 @@ def _args():
     ap.add_argument("--seed-sets", default="T2,T4", help="read sets of the seeding section")
     ap.add_argument("--only-mlp", type=int, default=0, metavar="ROWS",
                     help="time only the filter network's forward on ROWS random feature rows (both kernels)")
+    ap.add_argument("--only-features", type=int, default=0, metavar="READS",
+                    help="time only the feature kernel on READS reads of the full-mix workload")
     ap.add_argument("--pairs", type=int, default=None,
                     help="smaller case of the workload (profiling); default: the full workload")
     return ap.parse_args()
@@ -407,22 +410,43 @@ def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
                                 cigar=True)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    for _ in range(2):
-        align(b, SCORING, cigar=True)
-    torch.cuda.synchronize()
-    sw.sw_phase_timing(True)
-    ms, phases = [], []
-    for _ in range(steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        align(b, SCORING, cigar=True, sync=False)
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-        phases.append(sw.sw_phase_times())
-    sw.sw_sync_status()
-    sw.sw_phase_timing(False)
+    def timed(n_steps):
+        for _ in range(2):
+            align(b, SCORING, cigar=True)
+        torch.cuda.synchronize()
+        sw.sw_phase_timing(True)
+        ms, phases = [], []
+        for _ in range(n_steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            align(b, SCORING, cigar=True, sync=False)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            phases.append(sw.sw_phase_times())
+        sw.sw_sync_status()
+        sw.sw_phase_timing(False)
+        return ms, phases
+
+    ms, phases = timed(steps)
+    # the same batch with autotuned lane plans: every length class's
+    # candidate plans timed on a sample of its pairs, the fastest installed
+    # (paper_1304_0681_gb300.autotune), then the cost model's plans restored
+    tuned = None
+    if not args.no_autotune:
+        from paper_1304_0681_gb300 import autotune
+        t0 = time.perf_counter()
+        chosen = autotune.tune(wl, SCORING, sample_pairs=100_000, use_cache=False)
+        tune_s = time.perf_counter() - t0
+        ms_t, ph_t = timed(steps)
+        sw.sw_set_plan(0, 1, 8)
+        tuned = {"plans": {str(m): list(v) for m, v in sorted(chosen.items())},
+                 "cost_model_plans": {str(m): list(sw.sw_plan_query(m, m + 200, SCORING[0])) for m in sorted(chosen)},
+                 "tune_s": tune_s, "sample_pairs_per_class": 100_000,
+                 "ms_per_step": statistics.mean(ms_t), "score_ms": statistics.mean(p[1] for p in ph_t),
+                 "cost_model_ms_per_step": statistics.mean(ms),
+                 "cost_model_score_ms": statistics.mean(p[1] for p in phases)}
     # Stage E task iv on the aligned batch: records above a score threshold
     # and GT-AG / CT-AC junctions (synthetic reference coordinates: one
     # contig per 100k windows, windows back to back)
@@ -486,6 +510,7 @@ def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
             "phase_ms": {"classify": statistics.mean(p[0] for p in phases), "score": score_ms,
                          "traceback": statistics.mean(p[2] for p in phases)},
             "score_roofline_frac": cells / (score_ms * 1e-3) / 1e9 / peak_gcups,
+            "autotuned": tuned,
             "stage_e_records_junctions": stage_e_res, "cpu_baseline": oracle_sw}
 
 
@@ -549,7 +574,7 @@ def _seeding_section(args, rank, steps: int) -> dict:
         t = statistics.mean(ms)
         lookups, hits_kept, sectors = sw._swgb.sw_seed_stats()
         if "gather_probe_loads_per_s" not in res:
-            res["gather_probe_loads_per_s"] = sw._swgb.sw_gather_probe(32, 64)
+            res["gather_probe_loads_per_s"] = _probe("probe_gather", 32, 64)
         sec = {"reads": rs.n_reads, "read_len": int(rs.read_offsets[1]), "eps": synth.READ_SETS[name]["eps"],
                "spliced_share": 0.10, "windows": n_win, "windows_per_read": n_win / rs.n_reads,
                "seed_ms": t, "seed_reads_per_s": rs.n_reads / (t * 1e-3), "steps": steps,
@@ -557,7 +582,7 @@ def _seeding_section(args, rank, steps: int) -> dict:
                "roofline": {"bound": "scattered 32-byte sectors", "kernel": "k_seed (+ k_seed_large, place)",
                             "achieved": sectors / (t * 1e-3), "peak": res["gather_probe_loads_per_s"],
                             "unit": "sectors/s", "frac": sectors / (t * 1e-3) / res["gather_probe_loads_per_s"],
-                            "peak_basis": "measured random 4-byte loads/s over a 16 GiB buffer (sw_gather_probe)",
+                            "peak_basis": "measured random 4-byte loads/s over a 16 GiB buffer (probe_gather, bench_probes.cu)",
                             "per_unit": "table sectors of each seed lookup + sectors of its kept bucket"}}
         if name == "T2":
             sd.map_reads(idx, rd, ro, rs.n_reads, SCORING)  # warm
@@ -725,8 +750,9 @@ def _graph_section(rank, n_pairs: int = 16384, reps: int = 50) -> dict:
 
 
 def run_mlp_only(args) -> None:
-    """The filter network's forward alone: ROWS random bf16 feature rows
-    through the tensor-memory kernel and the warp-MMA kernel."""
+    """The filter network alone on ROWS random bf16 feature rows: the forward
+    through the tensor-memory kernel and the warp-MMA kernel, and the
+    training gradient through the tensor-core and the fp32 kernel."""
     import torch
 
     from paper_1304_0681_gb300 import _swgb
@@ -752,8 +778,101 @@ def run_mlp_only(args) -> None:
         ms = e0.elapsed_time(e1) / args.steps
         res[name] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}
     _swgb.sw_set_mlp_kernel(_swgb.SW_MLP_AUTO)
+    # the training gradient over the same rows (random targets): forward,
+    # backward and the weight-gradient sums; 3 x the forward's FLOPs
+    ng = min(n, 2_000_000)  # the fp32 kernel takes one sample per loop step: bound its run
+    xg = x[:ng]
+    tgt = torch.rand(ng, device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+    grad = {"rows": ng}
+    for kind, name in ((_swgb.SW_GRAD_AUTO, "tcgen05"), (_swgb.SW_GRAD_FP32, "fp32_cuda_cores")):
+        _swgb.sw_set_mlp_grad_kernel(kind)
+        for _ in range(args.warmup):
+            model.grad(xg, tgt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            model.grad(xg, tgt)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        grad[name] = {"ms": ms, "samples_per_s": ng / (ms * 1e-3), "tflops": 3 * flops / n * ng / (ms * 1e-3) / 1e12}
+    _swgb.sw_set_mlp_grad_kernel(_swgb.SW_GRAD_AUTO)
     _swgb.sw_sync_status()
-    print(json.dumps({"section": "filter network forward", "rows": n, "flop_per_row": flops // n, **res}), flush=True)
+    print(json.dumps({"section": "filter network forward", "rows": n, "flop_per_row": flops // n, **res,
+                      "gradient": grad}), flush=True)
+
+
+def run_features_only(args) -> None:
+    """The filter's feature kernel alone on READS reads of the full-mix
+    workload (generated on the device), with its algorithmic bytes and 4-mer
+    rate."""
+    import torch
+
+    import synth
+    from paper_1304_0681_gb300 import _swgb
+    n = args.only_features
+    wl = synth.generate_device("fullmix", seed=0, n_reads=n)
+    out = torch.empty((wl.n_pairs, 64), dtype=torch.int16, device="cuda")
+
+    def run():
+        _swgb.sw_filter_features(wl.reads, wl.read_offsets, n, wl.windows, wl.window_offsets, wl.cand_offsets, out)
+
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    _swgb.sw_sync_status()
+    t = min(ms)
+    n_bytes = _feature_bytes(wl)
+    kmers = int((wl.window_offsets[1:] - wl.window_offsets[:-1] - 3).clamp(min=0).sum().item())
+    print(json.dumps({"section": "filter features", "reads": n, "pairs": wl.n_pairs, "ms": t,
+                      "algorithmic_bytes": n_bytes, "gb_per_s": n_bytes / (t * 1e-3) / 1e9,
+                      "window_kmers_per_s": kmers / (t * 1e-3)}), flush=True)
+
+
+PROBES_SRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "bench_probes.cu")
+PROBES_LIB = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libswgb_probes.so")
+_probes_lib = None
+
+
+def build_probes(force: bool = False) -> str:
+    """Compile bench_probes.cu (the roofline probes, outside the alignment
+    library) into libswgb_probes.so beside it, for sm_103a."""
+    if force or not os.path.exists(PROBES_LIB) or os.path.getmtime(PROBES_LIB) < os.path.getmtime(PROBES_SRC):
+        tmp = PROBES_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call([os.environ.get("NVCC", "nvcc"), "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
+                               "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-cudart", "static",
+                               PROBES_SRC, "-o", tmp])
+        os.replace(tmp, PROBES_LIB)
+    return PROBES_LIB
+
+
+def _probe(name: str, a: int, b: int) -> float:
+    """probe_alu(kind, iters) or probe_gather(log2_words, rounds) on the
+    current stream: operations or loads per second."""
+    import ctypes
+
+    import torch
+    global _probes_lib
+    if _probes_lib is None:
+        lib = ctypes.CDLL(build_probes())
+        for fn in (lib.probe_alu, lib.probe_gather):
+            fn.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+            fn.restype = ctypes.c_int
+        _probes_lib = lib
+    out = ctypes.c_double(0.0)
+    rc = getattr(_probes_lib, name)(a, b, ctypes.byref(out), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc:
+        raise RuntimeError(f"{name} failed: {rc}")
+    return out.value
 
 
 class _OracleReads:
@@ -943,7 +1062,7 @@ def _fullmix_headline(args, rank: int, ws: int, pg, peak: dict, local: int) -> d
                                  "peak": peak["hbm_gbs"], "unit": "GB/s",
                                  "frac": feat_bytes / (feat_ms * 1e-3) / 1e9 / peak["hbm_gbs"],
                                  "algorithmic_bytes": feat_bytes,
-                                 "per_unit": "packed read and window bytes of each pair + 128 B of bf16 features"},
+                                 "per_unit": "packed bytes of each read once and of each window + 128 B of bf16 features per pair"},
            "training": {key: training[key] for key in ("pairs", "samples_per_epoch", "epochs", "train_s",
                                                        "train_samples_per_s", "gradient")}}
 
@@ -991,11 +1110,11 @@ def _fullmix_headline(args, rank: int, ws: int, pg, peak: dict, local: int) -> d
 
 
 def _feature_bytes(wl) -> int:
-    """Algorithmic bytes of the feature kernel over a device workload: the
-    packed read of each pair, the packed window, and the 64 bf16 features
-    written."""
+    """Algorithmic bytes of the feature kernel over a device workload: each
+    packed read once, each packed window, and the 64 bf16 features of each
+    pair written."""
     rl = (wl.read_offsets[1:] - wl.read_offsets[:-1])
-    read_bytes = int(((rl[wl.pair_read] + 3) // 4).sum().item())
+    read_bytes = int(((rl + 3) // 4).sum().item())
     win_bytes = int((((wl.window_offsets[1:] - wl.window_offsets[:-1]) + 3) // 4).sum().item())
     return read_bytes + win_bytes + 128 * wl.n_pairs
 
@@ -1138,9 +1257,8 @@ def _measure_peaks() -> dict:
     rate x 2 cells / 7 operations per cell, and beside it the measured rate
     of the DPX + multiply-add mix the kernel issues; HBM from the measured
     copy bandwidth of this machine's GPUs, else the fallback figure."""
-    import paper_1304_0681_gb300 as sw
-    dpx = sw.sw_alu_probe(1, 20000)
-    mix = sw.sw_alu_probe(6, 20000)
+    dpx = _probe("probe_alu", 1, 20000)
+    mix = _probe("probe_alu", 6, 20000)
     hbm, hbm_basis = 6800.0, "fallback 6.8 TB/s"
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -1188,6 +1306,10 @@ def _summary(head, thr, unev, filt, graph, seeding) -> dict:
         s["uneven_2M"] = {"gcups": _r(unev["gcups"]), "ms": _r(unev["ms_per_step"]),
                           "phase_ms": [_r(v, 3) for v in unev["phase_ms"].values()],
                           "score_frac": _r(unev["score_roofline_frac"], 3)}
+        if unev.get("autotuned"):
+            at = unev["autotuned"]
+            s["uneven_2M"]["tuned_ms"] = _r(at["ms_per_step"])
+            s["uneven_2M"]["tuned_score_ms"] = _r(at["score_ms"], 3)
     if filt:
         s["filter_500k"] = {"filtered_rps": _r(filt["filtered"]["reads_per_s"]),
                             "plain_rps": _r(filt["plain"]["reads_per_s"]),
@@ -1282,6 +1404,8 @@ def main():
         return run_reference(args, ws, rank)
     if args.only_mlp:
         return run_mlp_only(args)
+    if args.only_features:
+        return run_features_only(args)
 
     import torch
 

@@ -526,6 +526,18 @@ int64_t sw_launch_count(void);
 int sw_set_plan(int32_t max_read_len, int32_t lanes, int32_t r_rows);
 
 /*
+ * The plan (lanes, rows) the score pass gives a length class whose longest
+ * read is max_read_len and longest window max_window_len under a scoring
+ * with this match score: the arithmetic mode follows from the score bound
+ * match x min(max_read_len, max_window_len) as for a pair, then the
+ * overrides of sw_set_plan apply (an override with more than 32 rows is
+ * skipped by a 16-bit-key class whose bound exceeds 510), else the built-in
+ * cost model.  Host-only; SW_ERR_INVALID_ARG for null outputs or values out
+ * of range.
+ */
+int sw_plan_query(int32_t max_read_len, int32_t max_window_len, int32_t match, int32_t *lanes, int32_t *r_rows);
+
+/*
  * Traceback arithmetic.  SW_TB_AUTO (the default) recomputes two pairs per
  * lane in 16-bit halves for every length class whose score bound
  * (match x min(m, n)) is at most 32000, and uses 32-bit arithmetic for the
@@ -570,17 +582,6 @@ int sw_plan_rows(int32_t *rows, int32_t cap);
  */
 int sw_phase_timing(int32_t enable);
 int sw_phase_times(float *ms3);
-
-/*
- * ALU throughput probe (measurement support, not part of the method): runs
- * `iters` iterations of 8 independent chains of one instruction kind on every
- * SM and writes the achieved instructions per second (warp-lane operations,
- * i.e. 32 per warp instruction).  kind: 0 = 32-bit add-max (DPX), 1 = 16x2
- * add-max (DPX), 2 = 16x2 three-way max (DPX), 3 = 32-bit integer add,
- * 4 = byte permute, 5 = 32-bit multiply-add, 6 = a mix of kinds 1 and 5.
- * Allocates and frees a small device buffer.
- */
-int sw_alu_probe(int32_t kind, int64_t iters, double *ops_per_s, sw_stream_t stream);
 
 #ifdef __cplusplus
 }

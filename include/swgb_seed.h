@@ -131,14 +131,6 @@ int sw_seed_windows(const uint32_t *table, const uint32_t *positions, const int6
  */
 int sw_seed_stats(sw_stream_t stream, int64_t *out3);
 
-/*
- * sw_gather_probe -- measures random 4-byte loads per second over a
- * 2^log2_words-word buffer (20..34; the library allocates and frees it):
- * every thread of 8 blocks per SM keeps 8 independent loads in flight for
- * 8 * rounds loads.  Each load touches one 32-byte sector, so the rate is
- * the scattered-sector ceiling that seeding is measured against.
- */
-int sw_gather_probe(int32_t log2_words, int64_t rounds, double *loads_per_s, sw_stream_t stream);
 
 /*
  * sw_reads_two_strands -- out holds read r at offsets r and its reverse

@@ -22,17 +22,17 @@ ERRORS = {
 
 #: every symbol include/swgb.h declares
 EXPORTS = ("sw_cigar_capacity", "sw_cigar_offsets", "sw_packed_bytes", "sw_batch_align", "sw_stream_release", "sw_last_cuda_error", "sw_batch_align_indexed",
-           "sw_batch_align_host", "sw_sync_status", "sw_strerror", "sw_launch_count", "sw_set_plan", "sw_set_traceback_mode", "sw_set_score_mode",
+           "sw_batch_align_host", "sw_sync_status", "sw_strerror", "sw_launch_count", "sw_set_plan", "sw_plan_query", "sw_set_traceback_mode", "sw_set_score_mode",
            "sw_last_traceback_split", "sw_plan_create", "sw_plan_align", "sw_plan_status", "sw_plan_destroy",
            "sw_batch_align_host_dense", "sw_records", "sw_junction_table_words", "sw_junction_table_clear", "sw_junctions_detect",
            "sw_junctions_export",
-           "sw_plan_rows", "sw_alu_probe", "sw_phase_timing", "sw_phase_times", "sw_batch_align_noalloc",
+           "sw_plan_rows", "sw_phase_timing", "sw_phase_times", "sw_batch_align_noalloc",
            "sw_batch_align_masked", "sw_filter_features", "sw_mlp_bytes", "sw_mlp_init", "sw_mlp_refresh",
            "sw_mlp_forward", "sw_set_mlp_kernel", "sw_set_mlp_grad_kernel", "sw_mlp_grad", "sw_mlp_adam", "sw_filter_select", "sw_best_per_read",
            "sw_top_hits", "sw_filter_align", "sw_filter_train_step", "sw_get_status",
            # include/swgb_seed.h
            "sw_index_table_words", "sw_index_build", "sw_seed_windows", "sw_reads_two_strands",
-           "sw_extract_windows", "sw_seed_stats", "sw_gather_probe")
+           "sw_extract_windows", "sw_seed_stats")
 
 
 class SwError(RuntimeError):
@@ -130,8 +130,6 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_last_cuda_error.restype = ctypes.c_int
     lib.sw_seed_stats.argtypes = [p, p]
     lib.sw_seed_stats.restype = ctypes.c_int
-    lib.sw_gather_probe.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_double), p]
-    lib.sw_gather_probe.restype = ctypes.c_int
     lib.sw_index_table_words.argtypes = [i32]
     lib.sw_index_table_words.restype = i64
     lib.sw_index_build.argtypes = [p, i64, p, i32, i32, p, p, p, p]
@@ -151,6 +149,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_launch_count.restype = i64
     lib.sw_set_plan.argtypes = [i32, i32, i32]
     lib.sw_set_plan.restype = ctypes.c_int
+    lib.sw_plan_query.argtypes = [i32, i32, i32, p, p]
+    lib.sw_plan_query.restype = ctypes.c_int
     lib.sw_set_traceback_mode.argtypes = [i32]
     lib.sw_set_traceback_mode.restype = ctypes.c_int
     lib.sw_set_score_mode.argtypes = [i32]
@@ -183,8 +183,6 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_phase_timing.restype = ctypes.c_int
     lib.sw_phase_times.argtypes = [p]
     lib.sw_phase_times.restype = ctypes.c_int
-    lib.sw_alu_probe.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_double), p]
-    lib.sw_alu_probe.restype = ctypes.c_int
     return lib
 
 
@@ -357,6 +355,15 @@ def sw_set_plan(max_read_len: int, lanes: int, rows: int) -> None:
     _check(_lib.sw_set_plan(int(max_read_len), int(lanes), int(rows)), "sw_set_plan")
 
 
+def sw_plan_query(max_read_len: int, max_window_len: int, match: int) -> tuple:
+    """(lanes, rows) of the score pass for a length class with these maxima."""
+    out = (ctypes.c_int32 * 2)()
+    _check(_lib.sw_plan_query(int(max_read_len), int(max_window_len), int(match),
+                              ctypes.cast(ctypes.byref(out, 0), ctypes.c_void_p),
+                              ctypes.cast(ctypes.byref(out, 4), ctypes.c_void_p)), "sw_plan_query")
+    return int(out[0]), int(out[1])
+
+
 SW_TB_AUTO = 0
 SW_TB_INT32 = 1
 
@@ -386,12 +393,6 @@ def sw_plan_rows() -> list:
     buf = (ctypes.c_int32 * n)()
     _lib.sw_plan_rows(ctypes.cast(buf, ctypes.c_void_p), n)
     return list(buf)
-
-
-def sw_alu_probe(kind: int, iters: int, stream=None) -> float:
-    out = ctypes.c_double(0.0)
-    _check(_lib.sw_alu_probe(int(kind), int(iters), ctypes.byref(out), _stream(stream)), "sw_alu_probe")
-    return out.value
 
 
 def sw_phase_timing(enable: bool) -> None:
@@ -543,13 +544,6 @@ def sw_seed_stats(stream=None) -> tuple:
     buf = (ctypes.c_int64 * 3)()
     _check(_lib.sw_seed_stats(_stream(stream), ctypes.cast(buf, ctypes.c_void_p)), "sw_seed_stats")
     return int(buf[0]), int(buf[1]), int(buf[2])
-
-
-def sw_gather_probe(log2_words: int = 32, rounds: int = 64, stream=None) -> float:
-    """Random 4-byte loads per second (one 32-byte sector each)."""
-    out = ctypes.c_double(0.0)
-    _check(_lib.sw_gather_probe(int(log2_words), int(rounds), ctypes.byref(out), _stream(stream)), "sw_gather_probe")
-    return out.value
 
 
 def sw_cigar_offsets(read_offsets, pair_read, n_pairs: int, out_offsets, stream=None) -> None:

@@ -49,10 +49,7 @@ __global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring
                 if (cig_n) cig_n[p] = 0;
             } else {
                 const int64_t hmax = (int64_t)sc.ma * (m < n ? m : n);
-                int mode = MODE_I32;
-                if (force_i32) mode = MODE_I32;
-                else if (hmax <= 1022) mode = MODE_I16;  // (H << 5) | 31 fits 15 bits
-                else if (hmax <= 32000) mode = MODE_I16W;
+                const int mode = score_mode_for(hmax, force_i32);
                 cls = mode * N_MCLASS + mclass_of((int32_t)m);
                 int nb = (int)((n - 1) >> 5);
                 nb = nb > N_NBUCKET - 1 ? N_NBUCKET - 1 : nb;

@@ -857,6 +857,27 @@ int sw_set_plan(int32_t max_read_len, int32_t lanes, int32_t r_rows)
     return SW_OK;
 }
 
+int sw_plan_query(int32_t max_read_len, int32_t max_window_len, int32_t match, int32_t *lanes, int32_t *r_rows)
+{
+    if (!lanes || !r_rows || max_read_len < 1 || max_read_len > SW_MAX_READ_LEN || max_window_len < 1 ||
+        match < 1 || match > 127)
+        return SW_ERR_INVALID_ARG;
+    const int64_t hmax = (int64_t)match * std::min(max_read_len, max_window_len);
+    const int mode = score_mode_for(hmax, g_score_mode.load() == SW_SCORE_INT32);
+    PlanOverride ov[kMaxPlanOverrides];
+    int n_ov = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        n_ov = (int)std::min<size_t>(g_plans.size(), kMaxPlanOverrides);
+        for (int i = 0; i < n_ov; ++i) ov[i] = g_plans[i];
+    }
+    int l = 0, ri = 0;
+    score_plan_of(mode, max_read_len, hmax, ov, n_ov, l, ri);
+    *lanes = l;
+    *r_rows = score_rows_at(ri);
+    return SW_OK;
+}
+
 int sw_set_traceback_mode(int32_t mode)
 {
     if (mode != SW_TB_AUTO && mode != SW_TB_INT32) return SW_ERR_INVALID_ARG;
@@ -914,34 +935,6 @@ int sw_phase_times(float *ms3)
     if (cuda_failed(cudaEventSynchronize(ds->phase[3]))) return SW_ERR_CUDA;
     for (int i = 0; i < 3; ++i)
         if (cuda_failed(cudaEventElapsedTime(&ms3[i], ds->phase[i], ds->phase[i + 1]))) return SW_ERR_CUDA;
-    return SW_OK;
-}
-
-int sw_alu_probe(int32_t kind, int64_t iters, double *ops_per_s, sw_stream_t stream)
-{
-    if (!ops_per_s || iters < 1 || kind < 0 || kind > 6) return SW_ERR_INVALID_ARG;
-    DeviceState *ds = nullptr;
-    int rc = device_state(&ds, (cudaStream_t)stream);
-    if (rc) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    const int threads = 256, blocks = ds->sm_count * 8;
-    uint32_t *out = nullptr;
-    if (cuda_failed(cudaMalloc(&out, sizeof(uint32_t) * threads * blocks))) return SW_ERR_CUDA;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    rc = launch_alu_probe(kind, iters / 8 + 1, blocks, threads, out, st);  // warm-up
-    cudaEventRecord(e0, st);
-    if (!rc) rc = launch_alu_probe(kind, iters, blocks, threads, out, st);
-    cudaEventRecord(e1, st);
-    float ms = 0.f;
-    if (!rc && (cuda_failed(cudaEventSynchronize(e1)) || cuda_failed(cudaEventElapsedTime(&ms, e0, e1))))
-        rc = SW_ERR_CUDA;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(out);
-    if (rc) return rc;
-    *ops_per_s = (double)blocks * threads * 8.0 * (double)iters / (ms * 1e-3);
     return SW_OK;
 }
 
@@ -1370,40 +1363,6 @@ int sw_seed_stats(sw_stream_t stream, int64_t *out3)
     std::lock_guard<std::mutex> lk(ds->mu);
     if (!ds->seed_stats_host) return SW_ERR_INVALID_ARG;
     for (int i = 0; i < 3; ++i) out3[i] = ds->seed_stats_host[i];
-    return SW_OK;
-}
-
-int sw_gather_probe(int32_t log2_words, int64_t rounds, double *loads_per_s, sw_stream_t stream)
-{
-    if (!loads_per_s || log2_words < 20 || log2_words > 34 || rounds < 1) return SW_ERR_INVALID_ARG;
-    DeviceState *ds = nullptr;
-    int rc = device_state(&ds, (cudaStream_t)stream);
-    if (rc) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    const size_t words = (size_t)1 << log2_words;
-    const int threads = 256, blocks = ds->sm_count * 8;
-    uint32_t *buf = nullptr, *out = nullptr;
-    if (cuda_failed(cudaMalloc(&buf, words * sizeof(uint32_t)))) return SW_ERR_CUDA;
-    if (cuda_failed(cudaMalloc(&out, sizeof(uint32_t) * threads * blocks))) {
-        cudaFree(buf);
-        return SW_ERR_CUDA;
-    }
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    float ms = 0.f;
-    rc = cuda_failed(cudaMemsetAsync(buf, 0x5A, words * sizeof(uint32_t), st)) ? SW_ERR_CUDA : SW_OK;
-    if (!rc && (cuda_failed(cudaEventCreate(&e0)) || cuda_failed(cudaEventCreate(&e1)))) rc = SW_ERR_CUDA;
-    if (!rc) rc = launch_gather_probe(buf, words - 1, rounds / 8 + 1, blocks, threads, out, st);  // warm-up
-    if (!rc && cuda_failed(cudaEventRecord(e0, st))) rc = SW_ERR_CUDA;
-    if (!rc) rc = launch_gather_probe(buf, words - 1, rounds, blocks, threads, out, st);
-    if (!rc && cuda_failed(cudaEventRecord(e1, st))) rc = SW_ERR_CUDA;
-    if (!rc && (cuda_failed(cudaEventSynchronize(e1)) || cuda_failed(cudaEventElapsedTime(&ms, e0, e1))))
-        rc = SW_ERR_CUDA;
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    cudaFree(out);
-    cudaFree(buf);
-    if (rc) return rc;
-    *loads_per_s = (double)blocks * threads * 8.0 * (double)rounds / (ms * 1e-3);
     return SW_OK;
 }
 

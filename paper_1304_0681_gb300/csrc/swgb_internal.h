@@ -237,6 +237,17 @@ struct DevTbPlan {
     TbPartPlan part[N_TB_PARTS];
 };
 
+// Score-pass arithmetic of a pair (or class) whose scores are at most hmax
+// (match x min(m, n)): 16-bit keys while (H << 5) | 31 fits 15 bits, 16-bit
+// halves up to 32000, else 32-bit lanes.
+__host__ __device__ inline int score_mode_for(int64_t hmax, bool force_i32)
+{
+    if (force_i32) return MODE_I32;
+    if (hmax <= 1022) return MODE_I16;
+    if (hmax <= 32000) return MODE_I16W;
+    return MODE_I32;
+}
+
 // Score-pass plan of a length class: lanes per group and rows per lane
 // (index into score_rows_at) for reads up to m_max in `mode`, hmax the
 // class's score bound.  Overrides first (sorted by max_read_len), else a
@@ -367,7 +378,6 @@ constexpr int N_COUNTERS = 6 * N_CLASS;
 constexpr int CTR_TB = 2 * N_CLASS, CTR_TB_OWN = 4 * N_CLASS;
 int launch_scan_scatter(const int32_t *keys, int64_t n_pairs, const int32_t *class_count, int32_t *hist,
                         int32_t *bucket_start, int32_t *cursor, int32_t *order, cudaStream_t st);
-int launch_alu_probe(int kind, int64_t iters, int blocks, int threads, uint32_t *out, cudaStream_t st);
 
 int launch_features(const FeatureParams &P, int sm_count, cudaStream_t st);
 int64_t mlp_floats();
@@ -469,8 +479,6 @@ int launch_seed_windows(const uint32_t *reads, const int64_t *roff, int64_t n_re
                         const uint32_t *positions, const int64_t *chrom_off, int n_chrom, const SeedKParams &p,
                         int max_read, int block_hits, SeedOutPtrs out, int64_t capacity, uint8_t *scratch,
                         int64_t *stats_host, int sm_count, int32_t *status, cudaStream_t st);
-int launch_gather_probe(const uint32_t *buf, uint64_t mask, int64_t rounds, int blocks, int threads, uint32_t *out,
-                        cudaStream_t st);
 int launch_extract_windows(const uint32_t *genome, int64_t n_bases, const int64_t *start, const int32_t *len,
                            int64_t n, uint32_t *dst, int64_t cap_bases, int64_t *woff, int64_t *blk, int sm_count,
                            int32_t *status, cudaStream_t st);

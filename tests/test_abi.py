@@ -77,10 +77,6 @@ def test_seeding_arguments_are_checked_before_any_device_work():
                              None, 1, None, 0, None, None)
     assert rc == -5
     assert lib.sw_seed_stats(None, None) == -1
-    out = ctypes.c_double()
-    assert lib.sw_gather_probe(10, 4, ctypes.byref(out), None) == -1
-    assert lib.sw_gather_probe(32, 0, ctypes.byref(out), None) == -1
-    assert lib.sw_gather_probe(32, 4, None, None) == -1
 
 
 def test_top_hits_arguments_are_checked_before_any_device_work():
