@@ -50,10 +50,12 @@
 // Pairs with larger possible scores (up to 32000) keep their two halves
 // (MODE_I16W) but build no keys: a three-way-max tree over the rows gives
 // each half's column maximum, and when a half's running best strictly rises
-// the lane copies the column's R values into a per-thread snapshot slot for
-// that pair (shared memory, four rows per 16-byte store).  After the chunk
-// the best cell's row is the first row of the snapshot holding the best
-// value: the snapshot is the column where the best was first reached.  This
+// the lane copies the column's R values into one of its two snapshot slots
+// (shared memory, four rows per 16-byte store): the slot the other pair does
+// not point to, or either when both pairs rise in the same column, so a
+// column is stored once.  Each pair points to the slot of the column where
+// its best was first reached, and after the chunk the best cell's row is the
+// first row of that snapshot holding the best value.  This
 // moves the row tracking off the ALU pipe (the kernel's limit) onto the
 // shared-memory stores, so the wide mode costs the same ALU operations per
 // cell as the 16-bit-key mode.  The int32 mode covers the rest.
@@ -203,12 +205,11 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
         __syncthreads();
     }
 
-    // MODE_I16W snapshot slots: quad q of pair A at snapA[q * blockDim.x],
-    // of pair B at snapB[q * blockDim.x] (a warp's stores hit distinct banks)
+    // MODE_I16W snapshot slots s = 0, 1: quad q of slot s at
+    // snap[(s * R4 + q) * blockDim.x] (a warp's stores hit distinct banks)
     constexpr int R4 = (R + 3) / 4;
     extern __shared__ __align__(16) unsigned char s_dyn[];
-    uint4 *const snapA = reinterpret_cast<uint4 *>(s_dyn) + threadIdx.x;
-    uint4 *const snapB = snapA + R4 * blockDim.x;
+    uint4 *const snap = reinterpret_cast<uint4 *>(s_dyn) + threadIdx.x;
 
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -338,6 +339,7 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
             // running best of this chunk
             uint32_t bk0 = PAIR2 && MODE == MODE_I16 ? TAGM * 0x10001u : 0u;
             uint32_t rowA = 0, rowB = 0;
+            int slotA = 0, slotB = 1;  // MODE_I16W: the snapshot slot each pair points to
             int32_t jA = 0, jB = 0;
             // window stream: 2-bit codes of the next columns (up to 16)
             uint32_t wwA = 0, wwB = 0;
@@ -442,15 +444,15 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
                     const uint32_t nb = __vimax_s16x2_relu(bk0, ck0);
                     const uint32_t up = nb ^ bk0;
                     bk0 = nb;
-                    if (up & 0xFFFFu) {
-                        jA = j;
+                    const bool upA = (up & 0xFFFFu) != 0, upB = up > 0xFFFFu;
+                    if (upA || upB) {
+                        // one store per step: a slot that the other pair does not point to
+                        const int s = (upA && upB) ? 0 : (upA ? (slotB ^ 1) : (slotA ^ 1));
+                        uint4 *const dst = snap + s * R4 * blockDim.x;
 #pragma unroll
-                        for (int q = 0; q < R4; ++q) snapA[q * blockDim.x] = quad_of<R>(h, q);
-                    }
-                    if (up > 0xFFFFu) {
-                        jB = j;
-#pragma unroll
-                        for (int q = 0; q < R4; ++q) snapB[q * blockDim.x] = quad_of<R>(h, q);
+                        for (int q = 0; q < R4; ++q) dst[q * blockDim.x] = quad_of<R>(h, q);
+                        if (upA) { slotA = s; jA = j; }
+                        if (upB) { slotB = s; jB = j; }
                     }
                 }
             }
@@ -465,8 +467,9 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
                 if (hb) bestB = max(bestB, cell_key(hb, jB, rbase + (int)TAGM - (int)((rowB >> 16) & TAGM)));
             } else {
                 const uint32_t ha = bk0 & 0xFFFFu, hb = bk0 >> 16;
-                if (ha) bestA = max(bestA, cell_key(ha, jA, rbase + snapshot_row<R>(snapA, blockDim.x, ha, 0)));
-                if (hb) bestB = max(bestB, cell_key(hb, jB, rbase + snapshot_row<R>(snapB, blockDim.x, hb, 16)));
+                const unsigned bd = blockDim.x;
+                if (ha) bestA = max(bestA, cell_key(ha, jA, rbase + snapshot_row<R>(snap + slotA * R4 * bd, bd, ha, 0)));
+                if (hb) bestB = max(bestB, cell_key(hb, jB, rbase + snapshot_row<R>(snap + slotB * R4 * bd, bd, hb, 16)));
             }
             __syncwarp();
         }
