@@ -431,19 +431,20 @@ def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
 
     ms, phases = timed(steps)
     # the same batch with autotuned lane plans: every length class's
-    # candidate plans timed on a sample of its pairs, the fastest installed
-    # (paper_1304_0681_gb300.autotune), then the cost model's plans restored
+    # candidate plans timed on a 1M-pair sample of the whole batch, one class
+    # at a time (paper_1304_0681_gb300.autotune), then the cost model's plans
+    # restored
     tuned = None
     if not args.no_autotune:
         from paper_1304_0681_gb300 import autotune
         t0 = time.perf_counter()
-        chosen = autotune.tune(wl, SCORING, sample_pairs=100_000, use_cache=False)
+        chosen = autotune.tune(wl, SCORING, sample_pairs=1_000_000, use_cache=False)
         tune_s = time.perf_counter() - t0
         ms_t, ph_t = timed(steps)
         sw.sw_set_plan(0, 1, 8)
         tuned = {"plans": {str(m): list(v) for m, v in sorted(chosen.items())},
                  "cost_model_plans": {str(m): list(sw.sw_plan_query(m, m + 200, SCORING[0])) for m in sorted(chosen)},
-                 "tune_s": tune_s, "sample_pairs_per_class": 100_000,
+                 "tune_s": tune_s, "sample_pairs": 1_000_000,
                  "ms_per_step": statistics.mean(ms_t), "score_ms": statistics.mean(p[1] for p in ph_t),
                  "cost_model_ms_per_step": statistics.mean(ms),
                  "cost_model_score_ms": statistics.mean(p[1] for p in phases)}

@@ -3,11 +3,11 @@
 The score pass splits the rows of a read over T lanes holding R rows each.
 Which (T, R) is fastest depends on the read-length class (padding, lane
 utilisation, register pressure and occupancy), so this module times a set of
-candidate plans per class, together with the built-in cost model's plan, on
-a sample of the caller's batch with the library's own phase timers, installs
-the fastest with sw_set_plan (the cost model's plan unless another beats it
-by a margin), and keeps the choice in a small JSON cache keyed by GPU name,
-class and scoring.
+candidate plans of each class on a sample of the caller's whole batch with
+the library's own phase timers (one class changed at a time, starting from
+the built-in cost model's plans), installs the fastest with sw_set_plan, and
+keeps the choice in a small JSON cache keyed by GPU name, classes and
+scoring.
 """
 from __future__ import annotations
 
@@ -38,9 +38,19 @@ def candidate_plans(m_max: int, rows=None):
     return sorted(set(out))
 
 
-def _time_plan(batch: DeviceBatch, scoring, m_max: int, plan, reps: int = 3) -> float:
+MAX_CLASSES = 16  # the library holds at most 16 plan overrides
+
+
+def _install(plans: dict) -> None:
+    """One override per class (the classes' longest reads, ascending): each
+    class gets exactly its own plan."""
     _swgb.sw_set_plan(0, 1, 8)
-    _swgb.sw_set_plan(m_max, *plan)
+    for m_max in sorted(plans):
+        _swgb.sw_set_plan(m_max, *plans[m_max])
+
+
+def _time(batch: DeviceBatch, scoring, reps: int = 3) -> float:
+    """Score-pass milliseconds of the batch under the installed plans."""
     align(batch, scoring, cigar=False)
     _swgb.sw_phase_timing(True)
     times = []
@@ -58,57 +68,68 @@ def _admissible(plan, m_max: int, n_max: int, match: int) -> bool:
     return plan[1] <= 32 or not 510 < bound <= 1022
 
 
-def tune(workload, scoring, sample_pairs: int = 400_000, seed: int = 0, use_cache: bool = True,
-         keep_margin: float = 0.02) -> dict:
+def tune(workload, scoring, sample_pairs: int = 1_000_000, seed: int = 0, use_cache: bool = True,
+         keep_margin: float = 0.01) -> dict:
     """Tune every read-length class of a synth.Workload; returns and installs
-    {max_read_len: (T, R)}.  The candidates of a class are candidate_plans
-    (those its score bound admits) and the built-in cost model's plan, timed
-    on up to sample_pairs of the class's pairs; the cost model's plan is kept
-    unless another is faster by more than keep_margin."""
+    {max_read_len: (T, R)}.
+
+    The classes share the GPU in one call (their launches overlap), so a
+    plan is timed in the context of the whole batch: on a sample of up to
+    sample_pairs pairs of every class, each class in turn tries its
+    candidates (candidate_plans that its score bound admits) while every
+    other class keeps its current plan, starting from the built-in cost
+    model's; a class moves to another plan only when the whole score pass
+    gets faster by more than keep_margin.  Batches with more classes than
+    the library holds overrides keep the cost model."""
     gpu = torch.cuda.get_device_name()
+    m = workload.pair_read_lengths
+    n = workload.window_lengths
+    # length classes in 16-base steps up to 1,024, as the classifier forms them
+    cls = np.where(m <= 1024, (m + 15) // 16, 64 + (m - 1024 + 127) // 128)
+    classes = np.unique(cls)
+    info = {}
+    for c in classes:
+        pairs = np.nonzero(cls == c)[0]
+        info[int(m[pairs].max())] = int(n[pairs].max())
+    _swgb.sw_set_plan(0, 1, 8)
+    model = {m_max: tuple(_swgb.sw_plan_query(m_max, max(n_max, 1), scoring[0])) for m_max, n_max in info.items()}
+    if len(model) > MAX_CLASSES:
+        return {}
+    key = f"{gpu}|{sorted(info.items())}|{tuple(scoring)}|{len(m)}"
     cache = {}
     if use_cache and os.path.exists(CACHE):
         try:
             cache = json.load(open(CACHE))
         except ValueError:
             cache = {}
-    m = workload.pair_read_lengths
-    n = workload.window_lengths
-    # length classes in 16-base steps, as the classifier forms them
-    cls = (m + 15) // 16
-    chosen = {}
+    if key in cache:
+        chosen = {int(k): tuple(v) for k, v in cache[key].items()}
+        _install(chosen)
+        return chosen
     rng = np.random.default_rng(seed)
-    for c in np.unique(cls):
-        pairs = np.nonzero(cls == c)[0]
-        m_max = int(m[pairs].max())
-        key = f"{gpu}|m<={m_max}|n~{int(np.median(n[pairs]))}|{tuple(scoring)}"
-        if key in cache:
-            chosen[m_max] = tuple(cache[key])
-            continue
-        pick = np.sort(rng.choice(pairs, min(len(pairs), sample_pairs), replace=False))
-        sub = workload.pair_slice(pick)
-        b = DeviceBatch.from_packed(sub.packed_reads(), sub.read_offsets, sub.packed_windows(), sub.window_offsets,
-                                    cigar=False)
-        n_max = int(n[pairs].max())
-        _swgb.sw_set_plan(0, 1, 8)
-        model = tuple(_swgb.sw_plan_query(m_max, max(n_max, 1), scoring[0]))
-        plans = [model] + [p for p in candidate_plans(m_max) if p != model and _admissible(p, m_max, n_max, scoring[0])]
-        times = {}
-        for plan in plans:
+    pick = np.arange(len(m)) if len(m) <= sample_pairs else np.sort(rng.choice(len(m), sample_pairs, replace=False))
+    sub = workload.pair_slice(pick)
+    b = DeviceBatch.from_packed(sub.packed_reads(), sub.read_offsets, sub.packed_windows(), sub.window_offsets,
+                                cigar=False)
+    chosen = dict(model)
+    _install(chosen)
+    best_ms = _time(b, scoring)
+    for m_max in sorted(info):
+        for plan in candidate_plans(m_max):
+            if plan == chosen[m_max] or not _admissible(plan, m_max, info[m_max], scoring[0]):
+                continue
+            trial = dict(chosen)
+            trial[m_max] = plan
             try:
-                times[plan] = _time_plan(b, scoring, m_max, plan)
+                _install(trial)
+                ms = _time(b, scoring)
             except _swgb.SwError:
                 continue
-        if times:
-            best = min(times, key=times.get)
-            if model in times and times[model] <= times[best] * (1.0 + keep_margin):
-                best = model
-            chosen[m_max] = best
-            cache[key] = list(best)
-    _swgb.sw_set_plan(0, 1, 8)
-    for m_max in sorted(chosen):
-        _swgb.sw_set_plan(m_max, *chosen[m_max])
+            if ms < best_ms * (1.0 - keep_margin):
+                best_ms, chosen = ms, trial
+    _install(chosen)
     if use_cache:
+        cache[key] = {str(k): list(v) for k, v in chosen.items()}
         try:
             json.dump(cache, open(CACHE, "w"), indent=1)
         except OSError:

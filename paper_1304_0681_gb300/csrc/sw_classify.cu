@@ -15,6 +15,16 @@ __global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring
                            int32_t *__restrict__ out_score, int32_t *__restrict__ out_end,
                            int32_t *__restrict__ cig_n)
 {
+    // the block's per-class count and maxima, added to the global table once
+    // at the end: a batch has few classes, and a global atomic per key group
+    // would send every warp to the same few addresses
+    __shared__ int32_t s_count[N_CLASS], s_max_n[N_CLASS], s_max_m[N_CLASS];
+    for (int c = threadIdx.x; c < N_CLASS; c += blockDim.x) {
+        s_count[c] = 0;
+        s_max_n[c] = 0;
+        s_max_m[c] = 0;
+    }
+    __syncthreads();
     // warp-strided so that every lane of a warp takes part in the key groups
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -64,12 +74,19 @@ __global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring
             const unsigned mx_m = __reduce_max_sync(g.mask, (unsigned)m);
             if (g.rank == 0) {
                 atomicAdd(&hist[key], g.size);
-                atomicAdd(&info->count[cls], g.size);
-                atomicMax(&info->max_n[cls], (int32_t)mx_n);
-                atomicMax(&info->max_m[cls], (int32_t)mx_m);
+                atomicAdd(&s_count[cls], g.size);
+                atomicMax(&s_max_n[cls], (int32_t)mx_n);
+                atomicMax(&s_max_m[cls], (int32_t)mx_m);
             }
         }
     }
+    __syncthreads();
+    for (int c = threadIdx.x; c < N_CLASS; c += blockDim.x)
+        if (s_count[c]) {
+            atomicAdd(&info->count[c], s_count[c]);
+            atomicMax(&info->max_n[c], s_max_n[c]);
+            atomicMax(&info->max_m[c], s_max_m[c]);
+        }
 }
 
 // Exclusive scan of the key histogram.  Keys are class-major (N_NBUCKET
