@@ -204,10 +204,10 @@ def _oracle_sample(wl, frac: float = 0.01, seed: int = 3, cigar: bool = True, fu
             "extrapolated_full_s": (full_cells or wl.cells()) / rate, "extrapolated": True}
 
 
-def _traffic_record(kernel_file: str):
-    """DRAM bytes per launch of the score kernel from the committed ncu
-    summary, if it was captured from the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+def _traffic_record(kernel_file: str, name: str = "traffic.json"):
+    """DRAM bytes of the score kernel from a committed ncu summary, if it was
+    captured from the current kernel source."""
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
@@ -1039,6 +1039,13 @@ def _fullmix_headline(args, rank: int, ws: int, pg, peak: dict, local: int) -> d
           "traceback": statistics.mean(p[2] for p in phases)}
     achieved = sel_cells / (ph["score"] * 1e-3) / 1e9
     feat_bytes = _feature_bytes(wl)
+    # DRAM bytes of the score kernel over one filtered step: an ncu capture
+    # of a smaller full mix (every k_score launch of its last filtered call),
+    # scaled by the pairs aligned (the kernel reads each aligned pair's
+    # packed read and window once)
+    trec = _traffic_record(os.path.join(ROOT, "paper_1304_0681_gb300", "csrc", "sw_score.cu"),
+                           "traffic_fullmix.json")
+    traffic = trec["dram_bytes_per_step"] * aligned / trec["aligned_pairs"] if trec else None
     out = {"value": all_reads / total_s, "ms_per_step": total_s * 1e3 / args.steps, "clocks": clk,
            "gpu_launches": int(launches),
            "config": {"workload": WORKLOADS[name], "reads_per_gpu": n_reads, "pairs_per_gpu": n_pairs,
@@ -1055,7 +1062,10 @@ def _fullmix_headline(args, rank: int, ws: int, pg, peak: dict, local: int) -> d
                      "api": "sw_batch_align_indexed + sw_best_per_read"},
            "speedup_reads_per_s": t_plain / t_filt, "best_hit_recall": recall,
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak["gcups"], "unit": "GCUPS",
-                        "frac": achieved / peak["gcups"], "traffic": None,
+                        "frac": achieved / peak["gcups"], "traffic": traffic,
+                        "traffic_basis": (f"dram read + write of every k_score launch of one filtered step, ncu on "
+                                          f"{trec['reads']} reads, scaled by aligned pairs ({trec['aligned_pairs']} "
+                                          f"-> {aligned})") if trec else None,
                         "kernel": "k_score on the selected pairs (score + end cell), all of a step's launches",
                         "peak_basis": peak["basis"], "frac_of_mix_peak": achieved / peak["mix_gcups"],
                         "mix_peak": peak["mix_gcups"], "mix_peak_basis": peak["mix_basis"]},

@@ -140,8 +140,14 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_tb(const ClassInfo *__res
             int64_t slot = 0;
             if (t.count > 0) {
                 const int64_t need = ti->max_need[c] > 1 ? ti->max_need[c] : 1;
+                // a part too small to give a task (64 / T pairs) to a quarter
+                // of the warps of a launch spreads each pair over more lanes
+                // (at most 8): the tasks then finish sooner, which is what a
+                // small batch waits for
+                int min_lanes = 1;
+                while (min_lanes < 8 && (int64_t)t.count * min_lanes < (int64_t)pp.tb_warps[0] * 16) min_lanes *= 2;
                 slot = tb_part_shape(c / N_MCLASS, pp.allow16 != 0, info->max_m[c], need, ti->max_wcap[part][c],
-                                     part, pp.small_slab_words, t);
+                                     part, pp.small_slab_words, t, min_lanes);
             }
             out->part[2 * c + part] = t;
             s_slot[2 * c + part] = slot;

@@ -31,15 +31,22 @@ constexpr int TC_ROWS = 128;        // pairs per tile (MMA M)
 constexpr uint32_t TC_TMEM_COLS = 512;  // the whole tensor memory (one CTA per SM)
 constexpr int64_t TC_WAIT_LIMIT = 1 << 20;  // polls of an mbarrier before giving up
 
+// The forward's biases ride in the MMAs: each layer's K gets one more block
+// of 16, whose first two columns are 1 in the A operand (features, hidden
+// units) and the bias split into two bf16 parts, hi = bf16(b) and
+// lo = bf16(b - hi), in the B operand (weights); the other 14 are 0.  The
+// fp32 accumulator then holds x . W + hi + lo, and hi + lo equals the fp32
+// bias to about 16 bits, so the epilogues only apply ReLU.
+constexpr int FK1 = 64 + 16;                   // layer-1 K
+constexpr int FK2 = 256 + 16;                  // layer-2 K
+
 // shared memory layout (bytes)
-constexpr int SM_W1 = 0;                       // B of layer 1: 256 x 64 bf16
-constexpr int SM_W2 = SM_W1 + 256 * 64 * 2;    // B of layer 2: 64 x 256 bf16
-constexpr int SM_XSZ = 128 * 64 * 2;           // one X buffer
-constexpr int SM_X = SM_W2 + 64 * 256 * 2;     // A of layer 1: 2 x (128 x 64 bf16)
-constexpr int SM_H = SM_X + 2 * SM_XSZ;        // A of layer 2: 128 x 256 bf16
-constexpr int SM_B1 = SM_H + 128 * 256 * 2;    // 256 fp32
-constexpr int SM_B2 = SM_B1 + 256 * 4;         // 64 fp32
-constexpr int SM_W3 = SM_B2 + 64 * 4;          // 64 fp32
+constexpr int SM_W1 = 0;                       // B of layer 1: 256 x FK1 bf16
+constexpr int SM_W2 = SM_W1 + 256 * FK1 * 2;   // B of layer 2: 64 x FK2 bf16
+constexpr int SM_XSZ = 128 * FK1 * 2;          // one X buffer
+constexpr int SM_X = SM_W2 + 64 * FK2 * 2;     // A of layer 1: 2 x (128 x FK1 bf16)
+constexpr int SM_H = SM_X + 2 * SM_XSZ;        // A of layer 2: 128 x FK2 bf16
+constexpr int SM_W3 = SM_H + 128 * FK2 * 2;    // 64 fp32
 constexpr int SM_PART = SM_W3 + 64 * 4;        // 128 fp32 partial dots
 constexpr int SM_BAR = SM_PART + 128 * 4;      // 2 mbarriers (16 B), TMEM base (4 B)
 constexpr int SM_USED = SM_BAR + 64;
@@ -131,8 +138,6 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, half = warp >> 2;  // TMEM lane quarter, column half
-    float *b1 = reinterpret_cast<float *>(smem + SM_B1);
-    float *b2 = reinterpret_cast<float *>(smem + SM_B2);
     float *w3 = reinterpret_cast<float *>(smem + SM_W3);
     float *part = reinterpret_cast<float *>(smem + SM_PART);  // layer-2 partial dots [128]
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + SM_BAR);  // [0] layer 1, [1] layer 2
@@ -145,16 +150,37 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
         const uint4 *g2 = reinterpret_cast<const uint4 *>(model + MD_W2T);  // [64][256] bf16
         for (int c = tid; c < 256 * 8; c += blockDim.x) {
             const int r = c >> 3, k = (c & 7) * 8;
-            *reinterpret_cast<uint4 *>(smem + SM_W1 + kmajor_off(r, k, 64)) = g1[c];
+            *reinterpret_cast<uint4 *>(smem + SM_W1 + kmajor_off(r, k, FK1)) = g1[c];
         }
         for (int c = tid; c < 64 * 32; c += blockDim.x) {
             const int r = c >> 5, k = (c & 31) * 8;
-            *reinterpret_cast<uint4 *>(smem + SM_W2 + kmajor_off(r, k, 256)) = g2[c];
+            *reinterpret_cast<uint4 *>(smem + SM_W2 + kmajor_off(r, k, FK2)) = g2[c];
         }
-        for (int i = tid; i < 256; i += blockDim.x) b1[i] = model[MD_B1 + i];
-        for (int i = tid; i < 64; i += blockDim.x) {
-            b2[i] = model[MD_B2 + i];
-            w3[i] = model[MD_W3 + i];
+        // the bias blocks: (hi, lo, 0 ...) in row r of the weights, (1, 1,
+        // 0 ...) in every row of both feature buffers and of the hidden units
+        auto bias8 = [](float b) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(b - __bfloat162float(hi));
+            return make_uint4((uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16), 0u,
+                              0u, 0u);
+        };
+        const uint4 ones = make_uint4(0x3F803F80u, 0u, 0u, 0u), zero = make_uint4(0u, 0u, 0u, 0u);
+        for (int r = tid; r < 256; r += blockDim.x) {
+            *reinterpret_cast<uint4 *>(smem + SM_W1 + kmajor_off(r, 64, FK1)) = bias8(model[MD_B1 + r]);
+            *reinterpret_cast<uint4 *>(smem + SM_W1 + kmajor_off(r, 72, FK1)) = zero;
+        }
+        for (int r = tid; r < 64; r += blockDim.x) {
+            *reinterpret_cast<uint4 *>(smem + SM_W2 + kmajor_off(r, 256, FK2)) = bias8(model[MD_B2 + r]);
+            *reinterpret_cast<uint4 *>(smem + SM_W2 + kmajor_off(r, 264, FK2)) = zero;
+            w3[r] = model[MD_W3 + r];
+        }
+        for (int r = tid; r < TC_ROWS; r += blockDim.x) {
+            for (int xb = 0; xb < 2; ++xb) {
+                *reinterpret_cast<uint4 *>(smem + SM_X + xb * SM_XSZ + kmajor_off(r, 64, FK1)) = ones;
+                *reinterpret_cast<uint4 *>(smem + SM_X + xb * SM_XSZ + kmajor_off(r, 72, FK1)) = zero;
+            }
+            *reinterpret_cast<uint4 *>(smem + SM_H + kmajor_off(r, 256, FK2)) = ones;
+            *reinterpret_cast<uint4 *>(smem + SM_H + kmajor_off(r, 264, FK2)) = zero;
         }
     }
     if (warp == 0) {
@@ -174,7 +200,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
         for (int c = tid; c < TC_ROWS * 8; c += blockDim.x) {
             const int r = c >> 3, k = (c & 7) * 8;
             const bool in = row0 + r < n;
-            cp_async16(s_base + SM_X + xb * SM_XSZ + kmajor_off(r, k, 64), g + (in ? (row0 + r) * 8 + (c & 7) : 0),
+            cp_async16(s_base + SM_X + xb * SM_XSZ + kmajor_off(r, k, FK1), g + (in ? (row0 + r) * 8 + (c & 7) : 0),
                        in ? 16u : 0u);
         }
         cp_async_commit();
@@ -195,9 +221,9 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
     uint32_t pph1 = 0, pph2 = 0;
     auto layer1 = [&](int xb, uint32_t acc) {
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks)
-            mma_bf16(acc, smem_desc(s_base + SM_X + xb * SM_XSZ + 256 * ks, 128, 1024),
-                     smem_desc(s_base + SM_W1 + 256 * ks, 128, 1024), idesc_bf16(128, 256), ks > 0);
+        for (int ks = 0; ks < FK1 / 16; ++ks)
+            mma_bf16(acc, smem_desc(s_base + SM_X + xb * SM_XSZ + 256 * ks, 128, FK1 / 8 * 128),
+                     smem_desc(s_base + SM_W1 + 256 * ks, 128, FK1 / 8 * 128), idesc_bf16(128, 256), ks > 0);
         mma_commit(bar1);
     };
     auto wait_all = [&](uint32_t bar, uint32_t &ph, bool &pend, uint32_t &pph) -> bool {
@@ -227,25 +253,32 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
         ok = wait_all(bar1, ph1, pend1, pph1);  // layer 1 of this tile
         fence_after_sync();
         if (!ok) break;
-        // h = bf16(relu(D + b1)): warp (quarter, half) takes 32 rows x 128 columns
+        // h = bf16(relu(D)) (the bias is in D): warp (quarter, half) takes 32
+        // rows x 128 columns, 64 columns per tensor-memory round trip
         {
             const int r = 32 * quarter + lane;
             const uint32_t la = acc + ((uint32_t)(32 * quarter) << 16);
-            for (int c0 = 128 * half; c0 < 128 * half + 128; c0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(la + (uint32_t)c0, v);
-                tmem_wait_ld();
-                uint32_t pk[8];
+#pragma unroll 1
+            for (int c0 = 128 * half; c0 < 128 * half + 128; c0 += 64) {
+                uint32_t v[4][16];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float x0 = fmaxf(__uint_as_float(v[2 * j]) + b1[c0 + 2 * j], 0.f);
-                    const float x1 = fmaxf(__uint_as_float(v[2 * j + 1]) + b1[c0 + 2 * j + 1], 0.f);
-                    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-                    pk[j] = *reinterpret_cast<const uint32_t *>(&h);
+                for (int q = 0; q < 4; ++q) tmem_ld16(la + (uint32_t)(c0 + 16 * q), v[q]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(__uint_as_float(v[q][2 * j]), 0.f),
+                                                                       fmaxf(__uint_as_float(v[q][2 * j + 1]), 0.f));
+                        pk[j] = *reinterpret_cast<const uint32_t *>(&h);
+                    }
+                    const int c = c0 + 16 * q;
+                    *reinterpret_cast<uint4 *>(smem + SM_H + kmajor_off(r, c, FK2)) =
+                        make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    *reinterpret_cast<uint4 *>(smem + SM_H + kmajor_off(r, c + 8, FK2)) =
+                        make_uint4(pk[4], pk[5], pk[6], pk[7]);
                 }
-                *reinterpret_cast<uint4 *>(smem + SM_H + kmajor_off(r, c0, 256)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                *reinterpret_cast<uint4 *>(smem + SM_H + kmajor_off(r, c0 + 8, 256)) =
-                    make_uint4(pk[4], pk[5], pk[6], pk[7]);
             }
         }
         // the next tile's features have landed (each thread waits for its own
@@ -259,9 +292,9 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
             // layer 2 of this tile (first 64 columns of its accumulator), then
             // layer 1 of the next tile into the other accumulator
 #pragma unroll
-            for (int ks = 0; ks < 16; ++ks)
-                mma_bf16(acc, smem_desc(s_base + SM_H + 256 * ks, 128, 4096),
-                         smem_desc(s_base + SM_W2 + 256 * ks, 128, 4096), idesc_bf16(128, 64), ks > 0);
+            for (int ks = 0; ks < FK2 / 16; ++ks)
+                mma_bf16(acc, smem_desc(s_base + SM_H + 256 * ks, 128, FK2 / 8 * 128),
+                         smem_desc(s_base + SM_W2 + 256 * ks, 128, FK2 / 8 * 128), idesc_bf16(128, 64), ks > 0);
             mma_commit(bar2);
             if (next < tiles) layer1(xb ^ 1, tmem + 256u * (uint32_t)(xb ^ 1));
         }
@@ -272,17 +305,19 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
         ok = wait_all(bar2, ph2, pend2, pph2);
         fence_after_sync();
         if (!ok) break;
-        // y = w3 . relu(D + b2) + b3: warp (quarter, half) sums 32 of the 64 columns
+        // y = w3 . relu(D) + b3 (the bias b2 is in D): warp (quarter, half)
+        // sums 32 of the 64 columns
         {
             float accv = 0.f;
             const uint32_t la = acc + ((uint32_t)(32 * quarter) << 16);
-            for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(la + (uint32_t)c0, v);
-                tmem_wait_ld();
+            uint32_t v[2][16];
+            tmem_ld16(la + (uint32_t)(32 * half), v[0]);
+            tmem_ld16(la + (uint32_t)(32 * half + 16), v[1]);
+            tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 16; ++j) accv += fmaxf(__uint_as_float(v[j]) + b2[c0 + j], 0.f) * w3[c0 + j];
-            }
+            for (int q = 0; q < 2; ++q)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) accv += fmaxf(__uint_as_float(v[q][j]), 0.f) * w3[32 * half + 16 * q + j];
             const int r = 32 * quarter + lane;
             if (half == 1) part[r] = accv;
             fence_before_sync();

@@ -308,7 +308,8 @@ __host__ __device__ inline void score_plan_of(int mode, int32_t m_max, int64_t h
 constexpr int kTbChunks16 = 8, kTbChunks32 = 4;
 constexpr int64_t kTiledLaneWords = 4096, kTiledLaneWords16 = 8192;
 __host__ __device__ inline int64_t tb_part_shape(int mode, bool allow16, int32_t m_max, int64_t max_need,
-                                                 int32_t wcap_in, int part, int32_t small_slab_words, TbPartPlan &t)
+                                                 int32_t wcap_in, int part, int32_t small_slab_words, TbPartPlan &t,
+                                                 int min_lanes16 = 1)
 {
     const int64_t chunks = (m_max + TB_ROWS - 1) / TB_ROWS;
     int32_t wcap = wcap_in > 1 ? wcap_in : 1;
@@ -318,7 +319,8 @@ __host__ __device__ inline int64_t tb_part_shape(int mode, bool allow16, int32_t
     while (Tl < 32 && (int64_t)Tl * 8 * (packed16 ? kTbChunks16 : kTbChunks32) < m_max) Tl *= 2;
     const bool one_lane16 = chunks * wcap4 * 2 <= kTiledLaneWords16;
     const bool tiled = !packed16 && chunks * wcap <= kTiledLaneWords;
-    const int T = (packed16 && one_lane16) || tiled ? 1 : Tl;
+    int T = (packed16 && one_lane16) || tiled ? 1 : Tl;
+    if (packed16 && T < min_lanes16) T = min_lanes16;
     t.lanes = T;
     int64_t slot;
     if (packed16) {
