@@ -35,7 +35,23 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_score(const ClassInfo *__
             const int mode = c / N_MCLASS;
             const int32_t mm = info->max_m[c], mn = info->max_n[c];
             int ri = 0;
-            score_plan_of(mode, mm, (int64_t)pp.sc.ma * min(mm, mn), pp.ov, pp.n_overrides, lanes, ri);
+            const int64_t hmax = (int64_t)pp.sc.ma * min(mm, mn);
+            score_plan_of(mode, mm, hmax, pp.ov, pp.n_overrides, lanes, ri);
+            // a class with fewer tasks than half its launch's warps (a small
+            // batch) finishes when one task does: fewer rows per lane, on
+            // more lanes, shorten the task while it still fits one row chunk
+            // (not when an override chose the plan)
+            bool chosen = false;
+            for (int i = 0; i < pp.n_overrides; ++i) chosen |= mm <= pp.ov[i].max_read_len;
+            while (!chosen && ri > 0) {
+                const int64_t per_warp = (int64_t)(32 / lanes) * (mode != MODE_I32 ? 2 : 1);
+                const int64_t tasks = (cnt + per_warp - 1) / per_warp;
+                if (2 * tasks >= pp.score_warps[ri * N_MODES + mode]) break;
+                const int t2 = (mm + score_rows_at(ri - 1) - 1) / score_rows_at(ri - 1);
+                if (t2 > 32) break;
+                --ri;
+                lanes = t2;
+            }
             const int rows = score_rows_at(ri);
             const int chunks = (mm + lanes * rows - 1) / (lanes * rows);
             // per group: two buffers x longest window x (H, F) x 4 bytes
