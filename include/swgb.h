@@ -532,8 +532,11 @@ int sw_set_plan(int32_t max_read_len, int32_t lanes, int32_t r_rows);
  * match x min(max_read_len, max_window_len) as for a pair, then the
  * overrides of sw_set_plan apply (an override with more than 32 rows is
  * skipped by a 16-bit-key class whose bound exceeds 510), else the built-in
- * cost model.  Host-only; SW_ERR_INVALID_ARG for null outputs or values out
- * of range.
+ * cost model.  Without an override, a class whose pairs would give fewer
+ * tasks than half the warps of its launch (a small batch) runs with fewer
+ * rows per lane on more lanes; the query reports the plan before that
+ * adjustment, which depends on the class's pair count.  Host-only;
+ * SW_ERR_INVALID_ARG for null outputs or values out of range.
  */
 int sw_plan_query(int32_t max_read_len, int32_t max_window_len, int32_t match, int32_t *lanes, int32_t *r_rows);
 
@@ -552,14 +555,18 @@ int sw_set_traceback_mode(int32_t mode);
 /*
  * Score-pass arithmetic.  SW_SCORE_AUTO (the default) gives each pair the
  * narrowest exact mode its score bound match x min(m, n) allows: two pairs
- * per lane in 16-bit halves up to 32000, 32-bit lanes above.  SW_SCORE_INT32
- * runs every pair in 32-bit lanes (and so, with a CIGAR, through the 32-bit
- * traceback kernels).  Both give the same scores, end cells and CIGARs.
- * Returns SW_ERR_INVALID_ARG for any other value.  Process-wide; applies to
- * calls made after it, and a plan keeps the setting it was created under.
+ * per lane in 16-bit halves up to 32000 (with 16-bit best-cell keys up to
+ * 1022, without keys above), 32-bit lanes above.  SW_SCORE_INT32 runs every
+ * pair in 32-bit lanes (and so, with a CIGAR, through the 32-bit traceback
+ * kernels).  SW_SCORE_WIDE16 runs every pair whose bound is at most 32000 in
+ * 16-bit halves without keys (the end row from column snapshots).  All give
+ * the same scores, end cells and CIGARs.  Returns SW_ERR_INVALID_ARG for any
+ * other value.  Process-wide; applies to calls made after it, and a plan
+ * keeps the setting it was created under.
  */
 #define SW_SCORE_AUTO 0
 #define SW_SCORE_INT32 1
+#define SW_SCORE_WIDE16 2
 int sw_set_score_mode(int32_t mode);
 
 /*

@@ -13,13 +13,13 @@ from ._swgb import (SwError, sw_batch_align, sw_batch_align_host, sw_batch_align
                     sw_batch_align_noalloc,
                     sw_cigar_capacity, sw_launch_count, sw_packed_bytes, sw_phase_times, sw_phase_timing,
                     sw_plan_rows, sw_plan_query, sw_set_plan, sw_set_score_mode, sw_set_traceback_mode, sw_last_traceback_split, sw_strerror,
-                    sw_sync_status, SW_SCORE_AUTO, SW_SCORE_INT32, SW_TB_AUTO, SW_TB_INT32)
+                    sw_sync_status, SW_SCORE_AUTO, SW_SCORE_INT32, SW_SCORE_WIDE16, SW_TB_AUTO, SW_TB_INT32)
 from .device import BatchPlan, DeviceBatch, align
 from .seed import KmerIndex, SeedParams, map_batches, map_reads, seed_windows
 
 __all__ = ["SwError", "sw_batch_align", "sw_batch_align_host", "sw_batch_align_host_dense", "sw_batch_align_indexed",
            "sw_batch_align_noalloc",
            "sw_cigar_capacity", "sw_launch_count", "sw_packed_bytes", "sw_phase_times", "sw_phase_timing",
-           "sw_plan_rows", "sw_plan_query", "sw_set_plan", "sw_set_score_mode", "sw_set_traceback_mode", "SW_SCORE_AUTO", "SW_SCORE_INT32", "sw_last_traceback_split", "SW_TB_AUTO", "SW_TB_INT32", "sw_strerror",
+           "sw_plan_rows", "sw_plan_query", "sw_set_plan", "sw_set_score_mode", "sw_set_traceback_mode", "SW_SCORE_AUTO", "SW_SCORE_INT32", "SW_SCORE_WIDE16", "sw_last_traceback_split", "SW_TB_AUTO", "SW_TB_INT32", "sw_strerror",
            "sw_sync_status", "DeviceBatch", "BatchPlan", "align", "_swgb",
            "KmerIndex", "SeedParams", "seed_windows", "map_reads", "map_batches"]

@@ -374,6 +374,7 @@ def sw_set_traceback_mode(mode: int) -> None:
 
 SW_SCORE_AUTO = 0
 SW_SCORE_INT32 = 1
+SW_SCORE_WIDE16 = 2
 
 
 def sw_set_score_mode(mode: int) -> None:

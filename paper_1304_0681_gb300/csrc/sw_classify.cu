@@ -10,7 +10,7 @@
 
 namespace swgb {
 
-__global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring sc, bool force_i32,
+__global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring sc, int score_setting,
                            int32_t *__restrict__ keys, int32_t *__restrict__ hist, ClassInfo *__restrict__ info,
                            int32_t *__restrict__ out_score, int32_t *__restrict__ out_end,
                            int32_t *__restrict__ cig_n)
@@ -59,7 +59,7 @@ __global__ void k_classify(PairSet ps, int64_t n_reads, int64_t n_pairs, Scoring
                 if (cig_n) cig_n[p] = 0;
             } else {
                 const int64_t hmax = (int64_t)sc.ma * (m < n ? m : n);
-                const int mode = score_mode_for(hmax, force_i32);
+                const int mode = score_mode_for(hmax, score_setting);
                 cls = mode * N_MCLASS + mclass_of((int32_t)m);
                 int nb = (int)((n - 1) >> 5);
                 nb = nb > N_NBUCKET - 1 ? N_NBUCKET - 1 : nb;
@@ -168,7 +168,7 @@ int launch_check_counts(const ClassInfo *info, const int32_t *expect, int32_t *s
     return launch_status();
 }
 
-int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring sc, bool force_i32,
+int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring sc, int score_setting,
                     int32_t *keys, int32_t *hist, int32_t *bucket_start, int32_t *cursor,
                     ClassInfo *info, int32_t *order, int32_t *out_score, int32_t *out_end,
                     int32_t *cig_n, cudaStream_t st)
@@ -177,7 +177,7 @@ int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring
     int64_t blocks = (n_pairs + threads - 1) / threads;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_classify<<<(unsigned)blocks, threads, 0, st>>>(ps, n_reads, n_pairs, sc, force_i32, keys, hist, info, out_score,
+    k_classify<<<(unsigned)blocks, threads, 0, st>>>(ps, n_reads, n_pairs, sc, score_setting, keys, hist, info, out_score,
                                                      out_end, cig_n);
     k_scan<<<N_CLASS, N_NBUCKET, 0, st>>>(hist, info->count, bucket_start, cursor);
     k_scatter<<<(unsigned)blocks, threads, 0, st>>>(keys, n_pairs, cursor, order);

@@ -332,7 +332,7 @@ PlanParams plan_params(const ExecCtx &x, const Scoring &sc, bool allow16, int64_
 // the traceback sort, its planner and every traceback variant.  A fixed
 // sequence of memsets and launches: no host synchronisation, no allocation.
 // expect (or nullptr): per-class counts and maxima a plan was made for.
-int enqueue_core(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const Scoring &sc, bool force_i32,
+int enqueue_core(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const Scoring &sc, int score_setting,
                  bool allow16, int32_t *out_score, int32_t *out_end, const sw_cigar_t *cig, const Scratch &S,
                  const int32_t *expect, const ExecCtx &x, cudaStream_t st)
 {
@@ -344,7 +344,7 @@ int enqueue_core(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const Scor
     if (cuda_failed(cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * nh, st))) return SW_ERR_CUDA;
     if (cuda_failed(cudaMemsetAsync(S.info, 0, sizeof(ClassInfo), st))) return SW_ERR_CUDA;
     if (cuda_failed(cudaMemsetAsync(S.counters, 0, sizeof(int32_t) * N_COUNTERS, st))) return SW_ERR_CUDA;
-    if ((rc = launch_classify(ps, n_reads, n_pairs, sc, force_i32, S.keys, S.hist, S.bstart, S.cursor, S.info,
+    if ((rc = launch_classify(ps, n_reads, n_pairs, sc, score_setting, S.keys, S.hist, S.bstart, S.cursor, S.info,
                               S.order, out_score, out_end, cig ? cig->n_ops : nullptr, st)))
         return rc;
     if (expect && (rc = launch_check_counts(S.info, expect, &S.info->status, st))) return rc;
@@ -434,7 +434,7 @@ int run_batch(const PairSet &ps, int64_t n_reads, int64_t n_pairs, const sw_scor
     S.tb_bytes = tb_bytes;
     ds->last_status = &S.info->status;
     ds->timed_cells_valid = false;
-    rc = enqueue_core(ps, n_reads, n_pairs, sc, g_score_mode.load() == SW_SCORE_INT32,
+    rc = enqueue_core(ps, n_reads, n_pairs, sc, g_score_mode.load(),
                       g_tb_mode.load() == SW_TB_AUTO, out_score, out_end, cig, S, nullptr, ds->x, st);
     if (rc) return rc;
     if (cig) ds->last_tplan = S.tplan;
@@ -480,7 +480,7 @@ struct sw_plan {
     int64_t n_reads = 0, n_pairs = 0;
     swgb::Scoring sc{};
     bool cigar = false;
-    bool force_i32 = false;   // the score mode setting at creation
+    int score_setting = SW_SCORE_AUTO;  // the score mode setting at creation
     bool allow16 = true;      // the traceback mode setting at creation
     swgb::Buffer fixed, dyn;  // owned: a captured graph keeps pointing here
     swgb::Scratch S{};
@@ -576,7 +576,7 @@ int plan_build(sw_plan *pl, DeviceState *ds, cudaStream_t st)
     int32_t *tmp_score = S.tb_keys, *tmp_end = nullptr;  // empty-window outputs go to scratch
     if ((rc = ensure(pl->dyn, sizeof(int32_t) * 2 * std::max<int64_t>(n_pairs, 1)))) return rc;
     tmp_end = (int32_t *)pl->dyn.ptr;
-    if ((rc = launch_classify(pl->ps, pl->n_reads, n_pairs, pl->sc, pl->force_i32, S.keys, S.hist, S.bstart,
+    if ((rc = launch_classify(pl->ps, pl->n_reads, n_pairs, pl->sc, pl->score_setting, S.keys, S.hist, S.bstart,
                               S.cursor, S.info, S.order, tmp_score, tmp_end, nullptr, st)))
         return rc;
     ClassInfo ci;
@@ -606,7 +606,7 @@ int plan_build(sw_plan *pl, DeviceState *ds, cudaStream_t st)
 
 int plan_execute(sw_plan *pl, int32_t *out_score, int32_t *out_end, const sw_cigar_t *cig, cudaStream_t st)
 {
-    return enqueue_core(pl->ps, pl->n_reads, pl->n_pairs, pl->sc, pl->force_i32, pl->allow16, out_score, out_end,
+    return enqueue_core(pl->ps, pl->n_reads, pl->n_pairs, pl->sc, pl->score_setting, pl->allow16, out_score, out_end,
                         pl->cigar ? cig : nullptr, pl->S, pl->S.expect, pl->x, st);
 }
 
@@ -863,7 +863,7 @@ int sw_plan_query(int32_t max_read_len, int32_t max_window_len, int32_t match, i
         match < 1 || match > 127)
         return SW_ERR_INVALID_ARG;
     const int64_t hmax = (int64_t)match * std::min(max_read_len, max_window_len);
-    const int mode = score_mode_for(hmax, g_score_mode.load() == SW_SCORE_INT32);
+    const int mode = score_mode_for(hmax, g_score_mode.load());
     PlanOverride ov[kMaxPlanOverrides];
     int n_ov = 0;
     {
@@ -887,7 +887,7 @@ int sw_set_traceback_mode(int32_t mode)
 
 int sw_set_score_mode(int32_t mode)
 {
-    if (mode != SW_SCORE_AUTO && mode != SW_SCORE_INT32) return SW_ERR_INVALID_ARG;
+    if (mode != SW_SCORE_AUTO && mode != SW_SCORE_INT32 && mode != SW_SCORE_WIDE16) return SW_ERR_INVALID_ARG;
     g_score_mode.store(mode);
     return SW_OK;
 }
@@ -958,7 +958,7 @@ int sw_plan_create(const int64_t *read_offsets, int64_t n_reads, const int64_t *
     pl->n_pairs = n_pairs;
     pl->sc = Scoring{scoring->match, scoring->mismatch, scoring->gap_open, scoring->gap_extend};
     pl->cigar = with_cigar != 0;
-    pl->force_i32 = g_score_mode.load() == SW_SCORE_INT32;
+    pl->score_setting = g_score_mode.load();
     pl->allow16 = g_tb_mode.load() == SW_TB_AUTO;
     {
         std::lock_guard<std::mutex> lk(ds->mu);

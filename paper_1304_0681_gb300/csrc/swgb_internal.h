@@ -238,12 +238,13 @@ struct DevTbPlan {
 };
 
 // Score-pass arithmetic of a pair (or class) whose scores are at most hmax
-// (match x min(m, n)): 16-bit keys while (H << 5) | 31 fits 15 bits, 16-bit
-// halves up to 32000, else 32-bit lanes.
-__host__ __device__ inline int score_mode_for(int64_t hmax, bool force_i32)
+// (match x min(m, n)) under a sw_set_score_mode setting: 16-bit keys while
+// (H << 5) | 31 fits 15 bits, 16-bit halves up to 32000, else 32-bit lanes;
+// SW_SCORE_WIDE16 skips the 16-bit keys, SW_SCORE_INT32 takes 32-bit lanes.
+__host__ __device__ inline int score_mode_for(int64_t hmax, int setting)
 {
-    if (force_i32) return MODE_I32;
-    if (hmax <= 1022) return MODE_I16;
+    if (setting == SW_SCORE_INT32) return MODE_I32;
+    if (hmax <= 1022 && setting != SW_SCORE_WIDE16) return MODE_I16;
     if (hmax <= 32000) return MODE_I16W;
     return MODE_I32;
 }
@@ -352,9 +353,10 @@ __host__ __device__ inline int64_t tb_part_shape(int mode, bool allow16, int32_t
     return slot;
 }
 
-// force_i32: every pair takes the int32 score mode (else the narrowest
+// score_setting: the sw_set_score_mode value (SW_SCORE_INT32: every pair in
+// the int32 mode; SW_SCORE_WIDE16: no 16-bit keys; else the narrowest
 // mode its score bound allows)
-int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring sc, bool force_i32,
+int launch_classify(const PairSet &ps, int64_t n_reads, int64_t n_pairs, Scoring sc, int score_setting,
                     int32_t *keys, int32_t *hist, int32_t *bucket_start, int32_t *cursor,
                     ClassInfo *info, int32_t *order, int32_t *out_score, int32_t *out_end,
                     int32_t *cig_n, cudaStream_t st);

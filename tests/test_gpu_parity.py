@@ -69,10 +69,26 @@ def test_parity_workload_int32_score_kernel():
     assert_parity(wl, got, DEFAULT, cigar=False)
 
 
+def test_parity_workload_wide16_score_kernel():
+    """The parity workload through the wide 16-bit mode (no 16-bit keys; the
+    end row from column snapshots) although its scores would fit the key
+    mode, and tie-heavy random pairs of 1-200 bases: score and end cell
+    against the oracle, bit-exact, and the same CIGARs behind them."""
+    import paper_1304_0681_gb300 as sw
+    for wl in (synth.generate("parity"), synth.random_pairs(1500, (1, 200), (0, 260), seed=31, alphabet=2)):
+        sw.sw_set_score_mode(sw.SW_SCORE_WIDE16)
+        try:
+            got = run_gpu(wl, DEFAULT)
+        finally:
+            sw.sw_set_score_mode(sw.SW_SCORE_AUTO)
+        assert_parity(wl, got, DEFAULT)
+
+
 def test_score_mode_setting_rejects_other_values():
     import paper_1304_0681_gb300 as sw
-    with pytest.raises(sw.SwError):
-        sw.sw_set_score_mode(2)
+    for bad in (3, -1):
+        with pytest.raises(sw.SwError):
+            sw.sw_set_score_mode(bad)
 
 
 def test_traceback_kernel_split(request):
