@@ -556,7 +556,7 @@ int sw_set_traceback_mode(int32_t mode);
  * Score-pass arithmetic.  SW_SCORE_AUTO (the default) gives each pair the
  * narrowest exact mode its score bound match x min(m, n) allows: two pairs
  * per lane in 16-bit halves up to 32000 (with 16-bit best-cell keys up to
- * 1022, without keys above), 32-bit lanes above.  SW_SCORE_INT32 runs every
+ * 510, without keys above), 32-bit lanes above.  SW_SCORE_INT32 runs every
  * pair in 32-bit lanes (and so, with a CIGAR, through the 32-bit traceback
  * kernels).  SW_SCORE_WIDE16 runs every pair whose bound is at most 32000 in
  * 16-bit halves without keys (the end row from column snapshots).  All give

@@ -44,8 +44,9 @@
 // gives the column's best key, and the lane's running best is replaced only
 // when the column's H is strictly larger (so the smallest column wins).  The
 // 16-bit keys need (H << TAGB) + TAGM < 32768: H <= 1022 with 5-bit row
-// tags (up to 32 rows per lane), H <= 510 with 6-bit tags (up to 64 rows;
-// the host picks such plans only for classes whose score bound allows it).
+// tags (up to 32 rows per lane), H <= 510 with 6-bit tags (up to 64 rows).
+// The classifier gives this mode to pairs whose score bound is at most 510;
+// with the SW_SCORE_AUTO setting larger bounds take the wide mode below.
 //
 // Pairs with larger possible scores (up to 32000) keep their two halves
 // (MODE_I16W) but build no keys: a three-way-max tree over the rows gives

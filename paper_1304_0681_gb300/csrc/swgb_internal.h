@@ -238,13 +238,16 @@ struct DevTbPlan {
 };
 
 // Score-pass arithmetic of a pair (or class) whose scores are at most hmax
-// (match x min(m, n)) under a sw_set_score_mode setting: 16-bit keys while
-// (H << 5) | 31 fits 15 bits, 16-bit halves up to 32000, else 32-bit lanes;
+// (match x min(m, n)) under a sw_set_score_mode setting: 16-bit keys up to
+// 510, where 6-bit row tags leave every plan (up to 64 rows per lane) open,
+// 16-bit halves without keys up to 32000, else 32-bit lanes;
 // SW_SCORE_WIDE16 skips the 16-bit keys, SW_SCORE_INT32 takes 32-bit lanes.
+// (Keys would fit up to 1022 with 5-bit tags, at most 32 rows per lane; the
+// wide mode with 50 rows per lane measured faster on those classes.)
 __host__ __device__ inline int score_mode_for(int64_t hmax, int setting)
 {
     if (setting == SW_SCORE_INT32) return MODE_I32;
-    if (hmax <= 1022 && setting != SW_SCORE_WIDE16) return MODE_I16;
+    if (hmax <= 510 && setting != SW_SCORE_WIDE16) return MODE_I16;
     if (hmax <= 32000) return MODE_I16W;
     return MODE_I32;
 }

@@ -10,9 +10,9 @@ from gpu_helpers import assert_parity, run_gpu
 pytestmark = pytest.mark.gpu
 
 DEFAULT = (5, -4, -10, -1)
-# match*min(m,n) decides the arithmetic: <= 1022 -> 16-bit lanes with 16-bit
-# keys (at most 32 rows per lane above 510), <= 32000 -> 16-bit lanes with
-# 32-bit keys, else int32 lanes
+# match*min(m,n) decides the arithmetic: <= 510 -> 16-bit lanes with 16-bit
+# keys, <= 32000 -> 16-bit lanes without keys (end rows from column
+# snapshots), else int32 lanes
 WIDE16 = (50, -30, -60, -5)
 INT32 = (120, -60, -7, -3)
 
@@ -163,9 +163,10 @@ def _workload(reads, wins):
 
 def test_key_mode_boundaries():
     """Reads around the limits of the arithmetic modes: match * min(m, n) at
-    and just above 510 (6-bit row tags) and 1022 (the end of 16-bit keys),
-    with three scorings.  Planted copies of the read score at the top of each
-    range, and 2-letter alphabets make rows tie, which the row tags decide."""
+    and just above 510 (the end of 16-bit keys with 6-bit row tags) and 1022
+    (where 5-bit tags would end), with three scorings.  Planted copies of the
+    read score at the top of each range, and 2-letter alphabets make rows
+    tie, which the row tags or the snapshots decide."""
     rng = np.random.default_rng(7)
     reads, wins = [], []
     for m in (101, 102, 103, 203, 204, 205, 206, 300, 408, 409, 410, 411, 510, 511, 512, 513, 1022, 1023, 1024):

@@ -1,8 +1,7 @@
 """sw_plan_query (host-only, no GPU): the plan the score pass gives a length
 class follows sw_set_plan's overrides -- the first whose max_read_len covers
-the class, skipped when a 16-bit-key class (score bound 511..1022) would need
-more than 32 rows -- and otherwise the built-in cost model, whose choices
-are pinned against brute force by tests/test_plan_host.py."""
+the class -- and otherwise the built-in cost model, whose choices are pinned
+against brute force by tests/test_plan_host.py."""
 import pytest
 
 
@@ -27,11 +26,12 @@ def test_overrides_and_their_limits(sw):
     assert sw.sw_plan_query(400, 500, 5) == base[400]  # beyond every override
     sw.sw_set_plan(0, 1, 8)
     assert sw.sw_plan_query(150, 250, 5) == base[150]  # cleared
-    # 50 rows need 6-bit row tags: a 16-bit-key class above 510 skips it,
-    # a class with a bound of at most 510 or a wide class takes it
+    # 50 rows need 6-bit row tags, which the 16-bit-key mode has wherever
+    # the classifier uses it (bounds up to 510); wider bounds run without
+    # keys: every class takes the 50-row override
     sw.sw_set_plan(150, 3, 50)
-    assert sw.sw_plan_query(150, 250, 5) != (3, 50)    # bound 750, 16-bit keys
-    assert sw.sw_plan_query(150, 250, 3) == (3, 50)    # bound 450
+    assert sw.sw_plan_query(150, 250, 5) == (3, 50)    # bound 750: wide 16-bit mode
+    assert sw.sw_plan_query(150, 250, 3) == (3, 50)    # bound 450: 16-bit keys
     assert sw.sw_plan_query(150, 250, 50) == (3, 50)   # bound 7500: wide 16-bit mode
 
 
