@@ -136,11 +136,13 @@ def bf16_round(x: np.ndarray) -> np.ndarray:
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def select_candidates(pred, cand_offsets, k: int, tau: float):
+def select_candidates(pred, cand_offsets, k: int, tau: float, delta: float = 0.0):
     """Per read: the k best-predicted candidates, or all of them when the
     gap between the k-th and the (k+1)-th prediction is below tau.  Ties in
-    the prediction keep the lower candidate index first.  Returns a boolean
-    mask over pairs."""
+    the prediction keep the lower candidate index first.  When the read does
+    not fall back, every further candidate predicted within delta of the
+    read's best (best - pred < delta) joins the k; delta = 0 adds none.
+    Returns a boolean mask over pairs."""
     sel = np.zeros(len(pred), dtype=bool)
     for r in range(len(cand_offsets) - 1):
         a, b = int(cand_offsets[r]), int(cand_offsets[r + 1])
@@ -149,12 +151,16 @@ def select_candidates(pred, cand_offsets, k: int, tau: float):
             sel[a:b] = True
             continue
         order = np.lexsort((np.arange(c), -pred[a:b]))
-        # the margin decision is taken in fp32, the precision of the kernel
+        # the margin decisions are taken in fp32, the precision of the kernel
         gap = np.float32(pred[a + order[k - 1]]) - np.float32(pred[a + order[k]])
         if gap < np.float32(tau):
             sel[a:b] = True
-        else:
-            sel[a + order[:k]] = True
+            continue
+        sel[a + order[:k]] = True
+        top = np.float32(pred[a + order[0]])
+        for j in range(c):
+            if top - np.float32(pred[a + j]) < np.float32(delta):
+                sel[a + j] = True
     return sel
 
 

@@ -185,3 +185,37 @@ def test_select_candidates_edges():
     np.testing.assert_array_equal(sel[5:], [True, True, True])   # margin 0 < tau: all
     sel = fo.select_candidates(pred, off, k=1, tau=0.0)
     np.testing.assert_array_equal(sel[5:], [True, False, False])
+
+
+def test_select_candidates_within_delta_of_the_best():
+    """The relative rule: beyond the k, a candidate joins when the read's
+    best prediction exceeds its own by less than delta (strictly); the
+    distance is taken from the best, not from the k-th; a fallback read
+    keeps all; delta = 0 adds nothing.  Dyadic predictions, exact in fp32."""
+    off = np.array([0, 5, 8, 11])
+    pred = np.array([0.875, 0.8125, 0.5, 0.75, 0.84375,   # read 0: best 0.875 at index 0
+                     0.5, 0.5, 0.5,                        # read 1: three-way tie
+                     0.25, 1.0, 0.9375])                   # read 2: best at index 1
+    # read 0, k = 1: 0.875 - 0.84375 = 1/32 < 1/16 joins; 0.875 - 0.8125 = 1/16 does not
+    sel = fo.select_candidates(pred, off, k=1, tau=0.0, delta=0.0625)
+    np.testing.assert_array_equal(sel[:5], [True, False, False, False, True])
+    sel = fo.select_candidates(pred, off, k=1, tau=0.0, delta=0.1)
+    np.testing.assert_array_equal(sel[:5], [True, True, False, False, True])
+    # k = 2 picks 0.875 and 0.84375; measured from the k-th (0.84375) 0.8125
+    # would be 1/32 away and join, measured from the best it is 1/16 away
+    sel = fo.select_candidates(pred, off, k=2, tau=0.0, delta=0.0625)
+    np.testing.assert_array_equal(sel[:5], [True, False, False, False, True])
+    # ties: delta 0 keeps the lower index only, any delta > 0 takes all three
+    sel = fo.select_candidates(pred, off, k=1, tau=0.0, delta=0.0)
+    np.testing.assert_array_equal(sel[5:8], [True, False, False])
+    sel = fo.select_candidates(pred, off, k=1, tau=0.0, delta=2.0 ** -10)
+    np.testing.assert_array_equal(sel[5:8], [True, True, True])
+    # read 2: 1.0 - 0.9375 = 1/16 < 0.07 joins; 0.25 does not
+    sel = fo.select_candidates(pred, off, k=1, tau=0.0, delta=0.07)
+    np.testing.assert_array_equal(sel[8:], [False, True, True])
+    # a margin below tau falls back to all candidates whatever delta is
+    sel = fo.select_candidates(pred, off, k=1, tau=0.05, delta=0.01)
+    np.testing.assert_array_equal(sel[:5], [True] * 5)
+    # the default adds nothing
+    np.testing.assert_array_equal(fo.select_candidates(pred, off, 1, 0.0),
+                                  fo.select_candidates(pred, off, 1, 0.0, 0.0))

@@ -37,6 +37,11 @@ MUTANTS = {
     "select_all_only_below_k": ("if c <= k:", "if c < k:"),
     "select_ties_high_index": ("np.lexsort((np.arange(c), -pred[a:b]))", "np.lexsort((-np.arange(c), -pred[a:b]))"),
     "select_gap_le": ("if gap < np.float32(tau):", "if gap <= np.float32(tau):"),
+    "select_delta_le": ("if top - np.float32(pred[a + j]) < np.float32(delta):",
+                        "if top - np.float32(pred[a + j]) <= np.float32(delta):"),
+    "select_delta_from_kth": ("top = np.float32(pred[a + order[0]])", "top = np.float32(pred[a + order[k - 1]])"),
+    "select_delta_on_fallback_only": ("        sel[a + order[:k]] = True\n        top",
+                                      "        sel[a + order[:k]] = True\n        continue\n        top"),
     "best_is_min": ("out[r] = int(s.max())", "out[r] = int(s.min())"),
 }
 
