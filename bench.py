@@ -228,9 +228,9 @@ FILTER_WORKLOADS = {
 def _train_filter(name: str, rank: int, n_train: int, n_cal: int, epochs: int):
     """The filter network trained on the GPU by the library's own forward,
     backward and Adam kernels, on SW scores the method itself computes for
-    the pairs of another seed of the workload; then (k, tau) picked on a
-    held-out seed for >= 99.6% best-hit recall.  Not timed as part of a
-    step.  Returns (model, k, tau, facts)."""
+    the pairs of another seed of the workload; then (k, tau, delta) picked
+    on a held-out seed for >= 99.6% best-hit recall.  Not timed as part of
+    a step.  Returns (model, k, tau, delta, facts)."""
     import numpy as np
     import torch
 
@@ -266,13 +266,14 @@ def _train_filter(name: str, rank: int, n_train: int, n_cal: int, epochs: int):
     flt.exhaustive_best(b_cal, co_cal, SCORING)
     pred_cal = model.forward(flt.features(b_cal, co_cal)).cpu().numpy()
     cal = flt.calibrate(pred_cal, b_cal.score.cpu().numpy().astype(np.int64), wl_cal.cand_offsets, 0.996)
-    k, tau = (cal[0], cal[1]) if cal else (8, 1.0)  # no setting reached the recall: align every candidate
+    # no setting reached the recall: align every candidate
+    k, tau, delta = cal[:3] if cal else (8, 1.0, 0.0)
     del b_cal
     facts = {"pairs": n_train_pairs, "samples_per_epoch": n_samples, "epochs": epochs, "loss_per_epoch": losses,
              "train_s": train_s, "train_samples_per_s": n_samples * epochs / max(train_s, 1e-9),
              "gradient": "tensor cores (tcgen05), bf16 operands, fp32 accumulation",
              "setup_s": time.perf_counter() - t0, "calibration": cal}
-    return model, k, tau, facts
+    return model, k, tau, delta, facts
 
 
 def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int = 500_000,
@@ -280,7 +281,7 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
     """Plain vs learned-filtered best-hit search on a candidate workload
     (default: 500k reads of 150 bp, U{1..64} candidate windows of 250 bp, one
     true at 1-3% divergence, paralog decoys at 5-20% or random).  The network
-    is trained on SW scores of pairs from another seed, and (k, tau) are
+    is trained on SW scores of pairs from another seed, and (k, tau, delta) are
     picked on a held-out seed for >= 99.6% best-hit recall; neither is timed.
     A step is one whole search over the batch (score and end, no CIGAR).
     With on_device the timed batch is generated on the GPU (the same
@@ -299,7 +300,7 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
                                     pair_read=wl.pair_read, cigar=False)
         return wl, b, torch.from_numpy(wl.cand_offsets).cuda()
 
-    model, k, tau, training = _train_filter(name, rank, n_train, n_cal, epochs)
+    model, k, tau, delta, training = _train_filter(name, rank, n_train, n_cal, epochs)
     cal = training["calibration"]
 
     if on_device:
@@ -332,7 +333,7 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
 
     (best_plain, _), ms_plain = timed(lambda: flt.exhaustive_best(b, co, SCORING))
     best_plain = best_plain.cpu().numpy()
-    res, ms_filt = timed(lambda: flt.filtered_best(b, co, model, k, tau, SCORING))
+    res, ms_filt = timed(lambda: flt.filtered_best(b, co, model, k, tau, SCORING, delta=delta))
     best_filt = res.best_score.cpu().numpy()
     aligned = int(res.mask.sum().item())
     sel_cells = int(pair_cells[res.mask > 0].sum().item())
@@ -343,7 +344,7 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
     feats = flt.features(b, co)
     pred = model.forward(feats)
     e1.record(stream)
-    flt.filtered_best(b, co, model, k, tau, SCORING, feats=feats)
+    flt.filtered_best(b, co, model, k, tau, SCORING, feats=feats, delta=delta)
     e2.record(stream)
     e2.synchronize()
     recall = float(np.mean(best_filt == best_plain))
@@ -362,12 +363,12 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
         pipe = {"batches": n_b, "includes": "copies in and out, features, network, selection, SW on the selected "
                                             "pairs, top hit and mapping quality per read; wall clock"}
         for ns in (1, 2, 3):
-            flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns)  # warm each stream's scratch
+            flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns, delta=delta)  # warm each stream's scratch
             torch.cuda.synchronize()
             walls = []
             for _ in range(steps):
                 t0 = time.perf_counter()
-                outs = flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns)
+                outs = flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns, delta=delta)
                 torch.cuda.synchronize()
                 walls.append(time.perf_counter() - t0)
             wt = statistics.mean(walls)
@@ -391,8 +392,9 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
                          "features_and_mlp_ms": e0.elapsed_time(e1), "select_align_best_ms": e1.elapsed_time(e2),
                          "gcups_aligned": sel_cells / (ms_filt * 1e-3) / 1e9},
             "speedup_reads_per_s": ms_plain / ms_filt, "best_hit_recall": recall, "k": k, "tau": tau,
+            "delta": delta,
             "filtered_pipelined_from_host": pipe,
-            "calibration_recall": cal[3] if cal else None, "training": training, "steps": steps}
+            "calibration_recall": cal[4] if cal else None, "training": training, "steps": steps}
 
 
 def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
@@ -942,7 +944,7 @@ def _fullmix_headline(args, rank: int, ws: int, pg, peak: dict, local: int) -> d
     from paper_1304_0681_gb300.shard import reduce_run
 
     name = "fullmix"
-    model, k, tau, training = _train_filter(name, rank, n_train=40_000, n_cal=100_000, epochs=16)
+    model, k, tau, delta, training = _train_filter(name, rank, n_train=40_000, n_cal=100_000, epochs=16)
     t0 = time.perf_counter()
     wl = synth.generate_device(name, seed=rank, n_reads=args.fullmix_reads)
     torch.cuda.synchronize()
@@ -960,7 +962,8 @@ def _fullmix_headline(args, rank: int, ws: int, pg, peak: dict, local: int) -> d
 
     def filtered():
         _swgb.sw_filter_align(wl.reads, wl.read_offsets, n_reads, wl.windows, wl.window_offsets, wl.pair_read,
-                              wl.cand_offsets, n_pairs, model.buf, k, tau, SCORING, score, end, mask, best, cand)
+                              wl.cand_offsets, n_pairs, model.buf, k, tau, delta, SCORING, score, end, mask, best,
+                              cand)
 
     def plain():
         _swgb.sw_batch_align_indexed(wl.reads, wl.read_offsets, n_reads, wl.windows, wl.window_offsets,
@@ -1049,7 +1052,8 @@ def _fullmix_headline(args, rank: int, ws: int, pg, peak: dict, local: int) -> d
     out = {"value": all_reads / total_s, "ms_per_step": total_s * 1e3 / args.steps, "clocks": clk,
            "gpu_launches": int(launches),
            "config": {"workload": WORKLOADS[name], "reads_per_gpu": n_reads, "pairs_per_gpu": n_pairs,
-                      "cells_exhaustive_per_gpu": cells, "k": k, "tau": tau, "scoring": list(SCORING),
+                      "cells_exhaustive_per_gpu": cells, "k": k, "tau": tau, "delta": delta,
+                      "scoring": list(SCORING),
                       "api": "sw_filter_align (features, network, selection, SW score + end, best per read)",
                       "l2": "inputs larger than L2 (about 12 GB of packed windows per step)",
                       "generated_on_gpu_s": gen_s},
@@ -1096,13 +1100,13 @@ def _fullmix_headline(args, rank: int, ws: int, pg, peak: dict, local: int) -> d
             del sub
         torch.cuda.empty_cache()
         ns = max(1, args.e2e_streams)
-        outs = flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns)  # each stream's scratch
+        outs = flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns, delta=delta)  # each stream's scratch
         torch.cuda.synchronize()
         reps = max(2, min(args.steps, 3))
         walls = []
         for _ in range(reps):
             t0 = time.perf_counter()
-            outs = flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns)
+            outs = flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns, delta=delta)
             torch.cuda.synchronize()
             walls.append(time.perf_counter() - t0)
         e2e_reads, e2e_s = reduce_run(n_reads, statistics.mean(walls))
@@ -1302,6 +1306,7 @@ def _summary(head, thr, unev, filt, graph, seeding) -> dict:
                             "plain_rps": _r(head["plain"]["reads_per_s"]),
                             "speedup": _r(head["speedup_reads_per_s"], 3), "recall": _r(head["best_hit_recall"], 5),
                             "k": head["config"]["k"], "tau": head["config"]["tau"],
+                            "delta": head["config"].get("delta"),
                             "aligned_share": _r(head["filtered"]["aligned_share"], 3),
                             "plain_gcups": _r(head["plain"]["gcups"]),
                             "score_frac": _r(head["roofline"]["frac"], 3),
@@ -1325,7 +1330,7 @@ def _summary(head, thr, unev, filt, graph, seeding) -> dict:
         s["filter_500k"] = {"filtered_rps": _r(filt["filtered"]["reads_per_s"]),
                             "plain_rps": _r(filt["plain"]["reads_per_s"]),
                             "speedup": _r(filt["speedup_reads_per_s"], 3), "recall": _r(filt["best_hit_recall"], 5),
-                            "k": filt["k"], "tau": filt["tau"]}
+                            "k": filt["k"], "tau": filt["tau"], "delta": filt.get("delta")}
     if graph:
         s["graph_16k"] = {"direct_ms": _r(graph["direct_ms_per_batch"], 3),
                           "graph_ms": _r(graph["graph_ms_per_batch"], 3)}

@@ -260,13 +260,19 @@ int sw_mlp_grad(float *model, const uint16_t *features, const float *target, con
  * step counts from 1.  Also refreshes the bf16 copies. */
 int sw_mlp_adam(float *model, float lr, int32_t step, sw_stream_t stream);
 
-/* Per read: mark its k best-predicted candidates (ties: lower candidate
- * index first) in pair_mask (device uint8[n_pairs]), or all of them when
- * the k-th and (k+1)-th predictions differ by less than tau, or when the read
- * has at most k candidates.  1 <= k <= SW_FILTER_MAX_K. */
+/* Per read: mark in pair_mask (device uint8[n_pairs]) its k best-predicted
+ * candidates (ties: lower candidate index first) and every other candidate
+ * whose prediction is less than delta below the read's best; or all of them
+ * when the k-th and (k+1)-th predictions differ by less than tau, or when
+ * the read has at most k candidates.  Differences are taken in fp32.  The
+ * relative rule (delta) is this library's addition to the top-k filter: it
+ * keeps the candidates of reads whose best few predictions are close
+ * together without aligning every candidate of those reads; delta = 0
+ * turns it off.  1 <= k <= SW_FILTER_MAX_K, delta >= 0, else
+ * SW_ERR_INVALID_ARG. */
 #define SW_FILTER_MAX_K 16
 int sw_filter_select(const float *pred, const int64_t *cand_offsets, int64_t n_reads, int32_t k, float tau,
-                     uint8_t *pair_mask, sw_stream_t stream);
+                     float delta, uint8_t *pair_mask, sw_stream_t stream);
 
 /* Per read: the largest score over its candidates with pair_mask[p] != 0
  * (pair_mask may be NULL: all), and that candidate's index within the read
@@ -276,7 +282,7 @@ int sw_best_per_read(const int32_t *score, const int64_t *cand_offsets, int64_t 
 
 /*
  * sw_filter_align -- the filtered search in one call: sw_filter_features,
- * sw_mlp_forward, sw_filter_select (k, tau), sw_batch_align_masked (score
+ * sw_mlp_forward, sw_filter_select (k, tau, delta), sw_batch_align_masked (score
  * and end; unselected pairs get score -1 and end (-1, -1)) and
  * sw_best_per_read over the selected pairs.  Reads, windows and offsets as
  * sw_batch_align_indexed; pair_read (device int64[n_pairs]) must agree with
@@ -291,9 +297,9 @@ int sw_best_per_read(const int32_t *score, const int64_t *cand_offsets, int64_t 
  */
 int sw_filter_align(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads, const uint8_t *windows,
                     const int64_t *window_offsets, const int64_t *pair_read, const int64_t *cand_offsets,
-                    int64_t n_pairs, const float *model, int32_t k, float tau, const sw_scoring_t *scoring,
-                    int32_t *out_score, int32_t *out_end, uint8_t *pair_mask, int32_t *best_score,
-                    int32_t *best_cand, sw_stream_t stream);
+                    int64_t n_pairs, const float *model, int32_t k, float tau, float delta,
+                    const sw_scoring_t *scoring, int32_t *out_score, int32_t *out_end, uint8_t *pair_mask,
+                    int32_t *best_score, int32_t *best_cand, sw_stream_t stream);
 
 /* One training step: sw_mlp_grad over the n samples (idx may be NULL), then
  * sw_mlp_adam with lr and step (from 1).  SW_ERR_INVALID_ARG for n < 1, a

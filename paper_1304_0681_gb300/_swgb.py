@@ -109,14 +109,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_mlp_grad.restype = ctypes.c_int
     lib.sw_mlp_adam.argtypes = [p, ctypes.c_float, i32, p]
     lib.sw_mlp_adam.restype = ctypes.c_int
-    lib.sw_filter_select.argtypes = [p, p, i64, i32, ctypes.c_float, p, p]
+    lib.sw_filter_select.argtypes = [p, p, i64, i32, ctypes.c_float, ctypes.c_float, p, p]
     lib.sw_filter_select.restype = ctypes.c_int
     lib.sw_best_per_read.argtypes = [p, p, i64, p, p, p, p]
     lib.sw_best_per_read.restype = ctypes.c_int
     lib.sw_top_hits.argtypes = [p, p, i64, p, p, p, p, p, p]
     lib.sw_top_hits.restype = ctypes.c_int
-    lib.sw_filter_align.argtypes = [p, p, i64, p, p, p, p, i64, p, i32, ctypes.c_float, ctypes.POINTER(Scoring),
-                                    p, p, p, p, p, p]
+    lib.sw_filter_align.argtypes = [p, p, i64, p, p, p, p, i64, p, i32, ctypes.c_float, ctypes.c_float,
+                                    ctypes.POINTER(Scoring), p, p, p, p, p, p]
     lib.sw_filter_align.restype = ctypes.c_int
     lib.sw_filter_train_step.argtypes = [p, p, p, p, i64, ctypes.c_float, i32, p]
     lib.sw_filter_train_step.restype = ctypes.c_int
@@ -466,9 +466,10 @@ def sw_mlp_adam(model, lr: float, step: int, stream=None) -> None:
     _check(_lib.sw_mlp_adam(_ptr(model), ctypes.c_float(lr), int(step), _stream(stream)), "sw_mlp_adam")
 
 
-def sw_filter_select(pred, cand_offsets, n_reads: int, k: int, tau: float, pair_mask, stream=None) -> None:
+def sw_filter_select(pred, cand_offsets, n_reads: int, k: int, tau: float, delta: float, pair_mask,
+                     stream=None) -> None:
     _check(_lib.sw_filter_select(_ptr(pred), _ptr(cand_offsets), int(n_reads), int(k), ctypes.c_float(tau),
-                                 _ptr(pair_mask), _stream(stream)), "sw_filter_select")
+                                 ctypes.c_float(delta), _ptr(pair_mask), _stream(stream)), "sw_filter_select")
 
 
 def sw_best_per_read(score, cand_offsets, n_reads: int, pair_mask, best_score, best_cand, stream=None) -> None:
@@ -477,12 +478,12 @@ def sw_best_per_read(score, cand_offsets, n_reads: int, pair_mask, best_score, b
 
 
 def sw_filter_align(reads, read_offsets, n_reads: int, windows, window_offsets, pair_read, cand_offsets,
-                    n_pairs: int, model, k: int, tau: float, scoring, out_score, out_end, pair_mask, best_score,
-                    best_cand, stream=None) -> None:
+                    n_pairs: int, model, k: int, tau: float, delta: float, scoring, out_score, out_end, pair_mask,
+                    best_score, best_cand, stream=None) -> None:
     sc = _scoring(scoring)
     _check(_lib.sw_filter_align(_ptr(reads), _ptr(read_offsets), int(n_reads), _ptr(windows), _ptr(window_offsets),
                                 _ptr(pair_read), _ptr(cand_offsets), int(n_pairs), _ptr(model), int(k),
-                                ctypes.c_float(tau), ctypes.byref(sc), _ptr(out_score), _ptr(out_end), _ptr(pair_mask),
+                                ctypes.c_float(tau), ctypes.c_float(delta), ctypes.byref(sc), _ptr(out_score), _ptr(out_end), _ptr(pair_mask),
                                 _ptr(best_score), _ptr(best_cand), _stream(stream)), "sw_filter_align")
 
 

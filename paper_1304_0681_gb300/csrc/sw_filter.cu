@@ -491,10 +491,12 @@ __global__ void k_mlp_adam(float *model, float lr, int32_t step)
 
 // ---------------------------------------------------- selection and best hit
 
-// Per read: the k best predictions (ties: lower candidate index first); if
-// the k-th and the (k+1)-th are closer than tau, every candidate.
+// Per read: the k best predictions (ties: lower candidate index first) and
+// every other candidate whose prediction lies less than delta below the
+// read's best; if the k-th and the (k+1)-th are closer than tau, every
+// candidate.  The differences are taken in fp32.
 __global__ void k_select(const float *__restrict__ pred, const int64_t *__restrict__ cand_off, int64_t n_reads,
-                         int32_t k, float tau, uint8_t *__restrict__ mask)
+                         int32_t k, float tau, float delta, uint8_t *__restrict__ mask)
 {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_reads;
          r += (int64_t)gridDim.x * blockDim.x) {
@@ -523,7 +525,8 @@ __global__ void k_select(const float *__restrict__ pred, const int64_t *__restri
             if (cnt < k + 1) ++cnt;
         }
         const bool all = bv[k - 1] - bv[k] < tau;
-        for (int64_t p = a; p < b; ++p) mask[p] = all ? 1 : 0;
+        const float top = bv[0];
+        for (int64_t p = a; p < b; ++p) mask[p] = (all || top - pred[p] < delta) ? 1 : 0;
         if (!all)
             for (int q = 0; q < k; ++q) mask[bi[q]] = 1;
     }
@@ -647,10 +650,10 @@ int launch_mlp_adam(float *model, float lr, int32_t step, cudaStream_t st)
     return launch_status();
 }
 
-int launch_select(const float *pred, const int64_t *cand_off, int64_t n_reads, int32_t k, float tau, uint8_t *mask,
-                  cudaStream_t st)
+int launch_select(const float *pred, const int64_t *cand_off, int64_t n_reads, int32_t k, float tau, float delta,
+                  uint8_t *mask, cudaStream_t st)
 {
-    k_select<<<grid_for(n_reads, 128, 152 * 32), 128, 0, st>>>(pred, cand_off, n_reads, k, tau, mask);
+    k_select<<<grid_for(n_reads, 128, 152 * 32), 128, 0, st>>>(pred, cand_off, n_reads, k, tau, delta, mask);
     count_launch();
     return launch_status();
 }
@@ -772,12 +775,12 @@ int sw_mlp_adam(float *model, float lr, int32_t step, sw_stream_t stream)
 }
 
 int sw_filter_select(const float *pred, const int64_t *cand_offsets, int64_t n_reads, int32_t k, float tau,
-                     uint8_t *pair_mask, sw_stream_t stream)
+                     float delta, uint8_t *pair_mask, sw_stream_t stream)
 {
-    if (n_reads < 0 || k < 1 || k > SW_FILTER_MAX_K) return SW_ERR_INVALID_ARG;
+    if (n_reads < 0 || k < 1 || k > SW_FILTER_MAX_K || !(delta >= 0.f)) return SW_ERR_INVALID_ARG;
     if (n_reads == 0) return SW_OK;
     if (!pred || !cand_offsets || !pair_mask) return SW_ERR_INVALID_ARG;
-    return launch_select(pred, cand_offsets, n_reads, k, tau, pair_mask, (cudaStream_t)stream);
+    return launch_select(pred, cand_offsets, n_reads, k, tau, delta, pair_mask, (cudaStream_t)stream);
 }
 
 int sw_best_per_read(const int32_t *score, const int64_t *cand_offsets, int64_t n_reads, const uint8_t *pair_mask,
@@ -792,11 +795,11 @@ int sw_best_per_read(const int32_t *score, const int64_t *cand_offsets, int64_t 
 
 int sw_filter_align(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads, const uint8_t *windows,
                     const int64_t *window_offsets, const int64_t *pair_read, const int64_t *cand_offsets,
-                    int64_t n_pairs, const float *model, int32_t k, float tau, const sw_scoring_t *scoring,
-                    int32_t *out_score, int32_t *out_end, uint8_t *pair_mask, int32_t *best_score,
-                    int32_t *best_cand, sw_stream_t stream)
+                    int64_t n_pairs, const float *model, int32_t k, float tau, float delta,
+                    const sw_scoring_t *scoring, int32_t *out_score, int32_t *out_end, uint8_t *pair_mask,
+                    int32_t *best_score, int32_t *best_cand, sw_stream_t stream)
 {
-    if (n_reads < 0 || n_pairs < 0 || k < 1 || k > SW_FILTER_MAX_K) return SW_ERR_INVALID_ARG;
+    if (n_reads < 0 || n_pairs < 0 || k < 1 || k > SW_FILTER_MAX_K || !(delta >= 0.f)) return SW_ERR_INVALID_ARG;
     if (n_reads == 0) return n_pairs == 0 ? SW_OK : SW_ERR_INVALID_ARG;
     if (!cand_offsets || !best_score) return SW_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -827,7 +830,7 @@ int sw_filter_align(const uint8_t *reads, const int64_t *read_offsets, int64_t n
     if ((rc = sw_filter_features(reads, read_offsets, n_reads, windows, window_offsets, cand_offsets, feat, stream)))
         return rc;
     if ((rc = sw_mlp_forward(model, feat, n_pairs, pred, stream))) return rc;
-    if ((rc = sw_filter_select(pred, cand_offsets, n_reads, k, tau, mask, stream))) return rc;
+    if ((rc = sw_filter_select(pred, cand_offsets, n_reads, k, tau, delta, mask, stream))) return rc;
     if ((rc = sw_batch_align_masked(reads, read_offsets, n_reads, windows, window_offsets, pair_read, mask, n_pairs,
                                     scoring, out_score, out_end, nullptr, stream)))
         return rc;

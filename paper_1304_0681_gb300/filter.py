@@ -125,13 +125,14 @@ class FilteredResult:
 
 
 def filtered_best(batch: DeviceBatch, cand_offsets: torch.Tensor, model: FilterModel, k: int, tau: float, scoring,
-                  feats: torch.Tensor | None = None) -> FilteredResult:
-    """Features -> network -> top-k / fallback selection -> SW on the
-    selected pairs -> best hit per read (score and end only)."""
+                  feats: torch.Tensor | None = None, delta: float = 0.0) -> FilteredResult:
+    """Features -> network -> top-k (+ within delta of the best) / fallback
+    selection -> SW on the selected pairs -> best hit per read (score and
+    end only)."""
     feats = features(batch, cand_offsets) if feats is None else feats
     pred = model.forward(feats)
     mask = torch.empty(batch.n_pairs, dtype=torch.uint8, device=pred.device)
-    _swgb.sw_filter_select(pred, cand_offsets, batch.n_reads, k, tau, mask)
+    _swgb.sw_filter_select(pred, cand_offsets, batch.n_reads, k, tau, delta, mask)
     _swgb.sw_batch_align_masked(batch.reads, batch.read_offsets, batch.n_reads, batch.windows, batch.window_offsets,
                                 batch.pair_read, mask, batch.n_pairs, scoring, batch.score, batch.end, None)
     best = torch.empty(batch.n_reads, dtype=torch.int32, device=pred.device)
@@ -158,7 +159,8 @@ class FilterBatchResult:
     aligned_pairs: int
 
 
-def _filter_host_batch(model: FilterModel, batch, k: int, tau: float, scoring) -> FilterBatchResult:
+def _filter_host_batch(model: FilterModel, batch, k: int, tau: float, scoring,
+                       delta: float = 0.0) -> FilterBatchResult:
     """One host batch (packed reads, read offsets, packed windows, window
     offsets, pair -> read, candidate offsets; pinned CPU tensors) through the
     filtered search on the current stream, results copied back."""
@@ -170,7 +172,7 @@ def _filter_host_batch(model: FilterModel, batch, k: int, tau: float, scoring) -
                     torch.empty(2 * n_pairs, dtype=torch.int32, device=dev), None, None, None)
     pred = model.forward(features(b, coff))
     mask = torch.empty(n_pairs, dtype=torch.uint8, device=dev)
-    _swgb.sw_filter_select(pred, coff, n_reads, k, tau, mask)
+    _swgb.sw_filter_select(pred, coff, n_reads, k, tau, delta, mask)
     _swgb.sw_batch_align_masked(b.reads, b.read_offsets, n_reads, b.windows, b.window_offsets, b.pair_read, mask,
                                 n_pairs, scoring, b.score, b.end, None)
     top = top_hits(b.score, coff, n_reads, mask)
@@ -180,7 +182,8 @@ def _filter_host_batch(model: FilterModel, batch, k: int, tau: float, scoring) -
                              int(out[3 * n_reads]))
 
 
-def filtered_batches(model: FilterModel, batches, k: int, tau: float, scoring, n_streams: int = 2) -> list:
+def filtered_batches(model: FilterModel, batches, k: int, tau: float, scoring, n_streams: int = 2,
+                     delta: float = 0.0) -> list:
     """The filtered search over a sequence of host batches (see
     _filter_host_batch for their layout): copy in, features, network,
     selection, SW on the selected pairs, top hits, copy out, with n_streams
@@ -188,7 +191,7 @@ def filtered_batches(model: FilterModel, batches, k: int, tau: float, scoring, n
     batch, in order."""
     from .seed import run_on_worker_streams
     return run_on_worker_streams(model.buf.device, list(batches),
-                                 lambda bt, s: _filter_host_batch(model, bt, k, tau, scoring), n_streams)
+                                 lambda bt, s: _filter_host_batch(model, bt, k, tau, scoring, delta), n_streams)
 
 
 def oversample_top(score: np.ndarray, cand_offsets: np.ndarray, top: int = 1, times: int = 4) -> np.ndarray:
@@ -212,21 +215,41 @@ def targets(score: torch.Tensor, read_len: torch.Tensor, match: int) -> torch.Te
     return score.to(torch.float32) / (float(match) * read_len.to(torch.float32))
 
 
+def _segment_max(vals: np.ndarray, cand_offsets: np.ndarray, counts: np.ndarray) -> np.ndarray:
+    """Per read: the largest of its candidates' vals (-1 with no candidates)."""
+    out = np.full(len(counts), -1, np.int64)
+    nz = counts > 0
+    if nz.any():
+        out[nz] = np.maximum.reduceat(vals, cand_offsets[:-1][nz])
+    return out
+
+
 def calibrate(pred: np.ndarray, score: np.ndarray, cand_offsets: np.ndarray, recall_target: float,
-              ks=(1, 2, 3, 4, 6, 8), taus=None):
-    """Pick (k, tau) with the fewest aligned pairs whose best-hit recall on
-    a held-out set reaches recall_target.  Host-side bookkeeping over
-    predictions and exhaustive scores already computed on the GPU."""
+              ks=(1, 2, 3, 4, 5, 6, 7, 8), taus=None, deltas=None):
+    """Pick (k, tau, delta) with the fewest aligned pairs whose best-hit
+    recall on a held-out set reaches recall_target; returns (k, tau, delta,
+    aligned pairs, recall), or None when no grid point reaches it.  A read
+    aligns all its candidates when it has at most k or when its k-th and
+    (k+1)-th predictions are closer than tau; otherwise its k best plus
+    every candidate predicted within delta of its best (sw_filter_select's
+    rule).  Host-side bookkeeping over predictions and exhaustive scores
+    already computed on the GPU."""
     taus = taus if taus is not None else [0.0, 0.005, 0.01, 0.02, 0.03, 0.05, 0.08, 0.12, 0.2]
+    deltas = deltas if deltas is not None else [0.0, 0.03, 0.05, 0.08, 0.1, 0.12, 0.15, 0.2]
+    pred = np.asarray(pred, np.float32)
+    score = np.asarray(score, np.int64)
+    cand_offsets = np.asarray(cand_offsets, np.int64)
     nr = len(cand_offsets) - 1
     counts = np.diff(cand_offsets)
     rid = np.repeat(np.arange(nr), counts)
-    true_best = np.full(nr, -1, np.int64)
-    np.maximum.at(true_best, rid, score)
+    true_best = _segment_max(score, cand_offsets, counts)
     # rank of each candidate within its read by prediction (desc), ties by index
     order = np.lexsort((np.arange(len(pred)), -pred, rid))
     rank = np.empty(len(pred), np.int64)
     rank[order] = np.arange(len(pred)) - np.repeat(cand_offsets[:-1], counts)[order]
+    top_pred = np.full(nr, -np.inf, np.float32)
+    top_pred[rid[rank == 0]] = pred[rank == 0]
+    below_top = top_pred[rid] - pred          # fp32, as the kernel takes it
     best = None
     for k in ks:
         sel_pred = np.full(nr, -np.inf, np.float32)
@@ -235,16 +258,17 @@ def calibrate(pred: np.ndarray, score: np.ndarray, cand_offsets: np.ndarray, rec
         m_k1 = rank == k
         sel_pred[rid[m_k]] = pred[m_k]
         nxt_pred[rid[m_k1]] = pred[m_k1]
-        topk_best = np.full(nr, -1, np.int64)
-        sel = rank < k
-        np.maximum.at(topk_best, rid[sel], score[sel])
         with np.errstate(invalid="ignore"):  # reads with <= k candidates: -inf - -inf
-            gap = sel_pred.astype(np.float32) - nxt_pred.astype(np.float32)
-        for tau in taus:
-            fall = (counts <= k) | (gap < np.float32(tau))
-            got = np.where(fall, true_best, topk_best)
-            recall = float(np.mean(got == true_best))
-            aligned = int(np.sum(np.where(fall, counts, np.minimum(counts, k))))
-            if recall >= recall_target and (best is None or aligned < best[2]):
-                best = (k, float(tau), aligned, recall)
+            gap = sel_pred - nxt_pred
+        fall_by_tau = [(counts <= k) | (gap < np.float32(tau)) for tau in taus]
+        for delta in deltas:
+            sel = (rank < k) | (below_top < np.float32(delta))
+            kept_best = _segment_max(np.where(sel, score, -1), cand_offsets, counts)
+            kept = np.bincount(rid[sel], minlength=nr)
+            for tau, fall in zip(taus, fall_by_tau):
+                got = np.where(fall, true_best, kept_best)
+                recall = float(np.mean(got == true_best))
+                aligned = int(np.sum(np.where(fall, counts, kept)))
+                if recall >= recall_target and (best is None or aligned < best[3]):
+                    best = (k, float(tau), float(delta), aligned, recall)
     return best

@@ -93,8 +93,9 @@ def test_top_hits_arguments_are_checked_before_any_device_work():
 
 
 def test_filter_entry_points_check_arguments_before_any_device_work():
-    """sw_filter_align and sw_filter_train_step reject bad counts, k outside
-    1..SW_FILTER_MAX_K and missing arrays before touching a device."""
+    """sw_filter_align, sw_filter_select and sw_filter_train_step reject bad
+    counts, k outside 1..SW_FILTER_MAX_K, a negative or NaN delta and missing
+    arrays before touching a device."""
     import ctypes
 
     from paper_1304_0681_gb300 import _swgb
@@ -102,11 +103,20 @@ def test_filter_entry_points_check_arguments_before_any_device_work():
     sc = ctypes.byref(_swgb.Scoring(5, -4, -10, -1))
     f = ctypes.c_float
 
-    def align(n_reads, n_pairs, k=3, cand=1, model=1, best=1):
-        return lib.sw_filter_align(1, 1, n_reads, 1, 1, 1, cand, n_pairs, model, k, f(0.0), sc, 1, 1, None, best,
-                                   None, None)
+    def align(n_reads, n_pairs, k=3, cand=1, model=1, best=1, delta=0.0):
+        return lib.sw_filter_align(1, 1, n_reads, 1, 1, 1, cand, n_pairs, model, k, f(0.0), f(delta), sc, 1, 1, None,
+                                   best, None, None)
     assert align(-1, 0) == -1
     assert align(2, 5, k=0) == -1 and align(2, 5, k=17) == -1
+    assert align(2, 5, delta=-0.01) == -1 and align(2, 5, delta=float("nan")) == -1
+    assert align(0, 0, delta=0.5) == 0
+
+    def select(n_reads, k=3, delta=0.0, pred=1, mask=1):
+        return lib.sw_filter_select(pred, 1, n_reads, k, f(0.0), f(delta), mask, None)
+    assert select(-1) == -1 and select(4, k=0) == -1 and select(4, k=17) == -1
+    assert select(4, delta=-1.0) == -1 and select(4, delta=float("nan")) == -1
+    assert select(0) == 0 and select(0, delta=0.25) == 0
+    assert select(4, pred=None) == -1 and select(4, mask=None) == -1
     assert align(0, 0) == 0
     assert align(0, 5) == -1
     assert align(3, 5, cand=None) == -1 and align(3, 5, best=None) == -1

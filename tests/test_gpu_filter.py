@@ -288,10 +288,13 @@ def test_select_and_best_match_oracle():
     pred = np.round(rng.uniform(0, 1, n), 2).astype(np.float32)  # many exact ties
     score = rng.integers(0, 500, n).astype(np.int32)
     dpred, doff = torch.from_numpy(pred).cuda(), torch.from_numpy(off).cuda()
-    for k, tau in ((1, 0.0), (1, 0.05), (3, 0.02), (8, 0.1), (16, 0.0)):
+    # delta: the relative rule, with differences of two-decimal predictions
+    # landing on the boundary (0.01, 0.05) in fp32 on both sides
+    for k, tau, delta in ((1, 0.0, 0.0), (1, 0.05, 0.0), (3, 0.02, 0.0), (8, 0.1, 0.0), (16, 0.0, 0.0),
+                          (1, 0.0, 0.01), (1, 0.0, 0.05), (2, 0.01, 0.03), (4, 0.0, 0.12), (3, 0.02, 1.5)):
         mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
-        sw._swgb.sw_filter_select(dpred, doff, 500, k, tau, mask)
-        ref = fo.select_candidates(pred.astype(np.float64), off, k, tau)
+        sw._swgb.sw_filter_select(dpred, doff, 500, k, tau, delta, mask)
+        ref = fo.select_candidates(pred.astype(np.float64), off, k, tau, delta)
         np.testing.assert_array_equal(mask.cpu().numpy().astype(bool), ref)
         best = torch.zeros(500, dtype=torch.int32, device="cuda")
         cand = torch.zeros(500, dtype=torch.int32, device="cuda")
@@ -507,7 +510,19 @@ def test_filter_align_in_one_call():
     k, tau = 3, 0.0
     co = torch.from_numpy(wl.cand_offsets).cuda()
     b = _batch(wl)
-    res = flt.filtered_best(b, co, model, k, tau, SCORING)
+    # delta: the 30 % quantile of the distances below each read's best
+    # prediction, so that it adds candidates beyond the 3 and leaves others out
+    pred0 = model.forward(flt.features(b, co)).cpu().numpy()
+    counts = np.diff(wl.cand_offsets)
+    assert counts.min() >= 1
+    top = np.maximum.reduceat(pred0, wl.cand_offsets[:-1])
+    delta = float(np.quantile(np.repeat(top, counts) - pred0, 0.3))
+    assert delta > 0
+    res = flt.filtered_best(b, co, model, k, tau, SCORING, delta=delta)
+    pred = res.pred.cpu().numpy().astype(np.float64)
+    ref = fo.select_candidates(pred, wl.cand_offsets, k, tau, delta)
+    np.testing.assert_array_equal(res.mask.cpu().numpy().astype(bool), ref)
+    assert ref.sum() > int(np.minimum(counts, k).sum())   # delta added candidates
     torch.cuda.synchronize()
     assert 0 < int(res.mask.sum().item()) < wl.n_pairs
     for own_mask in (True, False):
@@ -516,7 +531,7 @@ def test_filter_align_in_one_call():
         best = torch.full((wl.n_reads,), -7, dtype=torch.int32, device="cuda")
         cand = torch.full_like(best, -7)
         _swgb.sw_filter_align(b2.reads, b2.read_offsets, wl.n_reads, b2.windows, b2.window_offsets, b2.pair_read, co,
-                              wl.n_pairs, model.buf, k, tau, SCORING, b2.score, b2.end, mask, best, cand)
+                              wl.n_pairs, model.buf, k, tau, delta, SCORING, b2.score, b2.end, mask, best, cand)
         _swgb.sw_get_status()
         assert torch.equal(b2.score, b.score) and torch.equal(b2.end, b.end)
         assert torch.equal(best, res.best_score) and torch.equal(cand, res.best_cand)
@@ -527,7 +542,7 @@ def test_filter_align_in_one_call():
     best = torch.full((3,), 5, dtype=torch.int32, device="cuda")
     cand = torch.full_like(best, 5)
     _swgb.sw_filter_align(b.reads, b.read_offsets, 3, b.windows, b.window_offsets, b.pair_read, zero, 0, model.buf,
-                          k, tau, SCORING, b.score, b.end, None, best, cand)
+                          k, tau, delta, SCORING, b.score, b.end, None, best, cand)
     torch.cuda.synchronize()
     assert (best == -1).all() and (cand == -1).all()
 
