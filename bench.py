@@ -75,7 +75,7 @@ def _args():
     ap.add_argument("--fullmix-reads", type=int, default=10_000_000, help="reads of the full-mix workload")
     ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain exhaustive arm")
     ap.add_argument("--e2e-batches", type=int, default=8, help="host batches of the full-mix end-to-end leg")
-    ap.add_argument("--no-extra", action="store_true", help="skip the uneven and full-mix sections")
+    ap.add_argument("--no-extra", action="store_true", help="run the headline section alone")
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuned re-run of the uneven batch")
     ap.add_argument("--no-seeding", action="store_true", help="skip the seeding section")
     ap.add_argument("--only-seeding", action="store_true", help="run the seeding section alone")
@@ -229,7 +229,9 @@ def _train_filter(name: str, rank: int, n_train: int, n_cal: int, epochs: int):
     """The filter network trained on the GPU by the library's own forward,
     backward and Adam kernels, on SW scores the method itself computes for
     the pairs of another seed of the workload; then (k, tau, delta) picked
-    on a held-out seed for >= 99.6% best-hit recall.  Not timed as part of
+    on a held-out seed for >= 99.7% best-hit recall (the 0.2-point margin
+    over the 99.5% goal absorbs the optimism of picking the cheapest of a
+    few hundred settings on the same held-out set).  Not timed as part of
     a step.  Returns (model, k, tau, delta, facts)."""
     import numpy as np
     import torch
@@ -265,7 +267,7 @@ def _train_filter(name: str, rank: int, n_train: int, n_cal: int, epochs: int):
     wl_cal, b_cal, co_cal = load(2000 + rank, n_cal)
     flt.exhaustive_best(b_cal, co_cal, SCORING)
     pred_cal = model.forward(flt.features(b_cal, co_cal)).cpu().numpy()
-    cal = flt.calibrate(pred_cal, b_cal.score.cpu().numpy().astype(np.int64), wl_cal.cand_offsets, 0.996)
+    cal = flt.calibrate(pred_cal, b_cal.score.cpu().numpy().astype(np.int64), wl_cal.cand_offsets, 0.997)
     # no setting reached the recall: align every candidate
     k, tau, delta = cal[:3] if cal else (8, 1.0, 0.0)
     del b_cal
@@ -282,7 +284,7 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
     (default: 500k reads of 150 bp, U{1..64} candidate windows of 250 bp, one
     true at 1-3% divergence, paralog decoys at 5-20% or random).  The network
     is trained on SW scores of pairs from another seed, and (k, tau, delta) are
-    picked on a held-out seed for >= 99.6% best-hit recall; neither is timed.
+    picked on a held-out seed for >= 99.7% best-hit recall; neither is timed.
     A step is one whole search over the batch (score and end, no CIGAR).
     With on_device the timed batch is generated on the GPU (the same
     workload as the host generator's) and the oracle is timed on a prefix of
