@@ -164,6 +164,27 @@ def select_candidates(pred, cand_offsets, k: int, tau: float, delta: float = 0.0
     return sel
 
 
+def rule_for_length(rules, m: int):
+    """The selection rule of a read of length m: the first of `rules`
+    (tuples (max_read_len, k, tau, delta) in ascending max_read_len) with
+    m <= max_read_len, else the last one."""
+    for rule in rules:
+        if m <= rule[0]:
+            return rule
+    return rules[-1]
+
+
+def select_by_length(pred, cand_offsets, read_lengths, rules):
+    """select_candidates with (k, tau, delta) taken per read from the rule
+    of its length (rule_for_length).  Returns a boolean mask over pairs."""
+    sel = np.zeros(len(pred), dtype=bool)
+    for r in range(len(cand_offsets) - 1):
+        a, b = int(cand_offsets[r]), int(cand_offsets[r + 1])
+        _, k, tau, delta = rule_for_length(rules, int(read_lengths[r]))
+        sel[a:b] = select_candidates(pred[a:b], np.array([0, b - a]), k, tau, delta)
+    return sel
+
+
 def best_per_read(score, cand_offsets, mask=None):
     """Max SW score over the (selected) candidates of each read (-1 if none)."""
     out = np.full(len(cand_offsets) - 1, -1, dtype=np.int64)

@@ -219,3 +219,33 @@ def test_select_candidates_within_delta_of_the_best():
     # the default adds nothing
     np.testing.assert_array_equal(fo.select_candidates(pred, off, 1, 0.0),
                                   fo.select_candidates(pred, off, 1, 0.0, 0.0))
+
+
+def test_select_by_length_takes_each_read_s_rule():
+    """Per-length rules: a read uses the first rule whose max_read_len is at
+    least its length (equality included), a read longer than every bound the
+    last rule; the rule's k, tau and delta apply as in select_candidates.
+    Dyadic predictions, exact in fp32."""
+    pred = np.array([0.875, 0.8125, 0.5, 0.84375,      # read 0 (length 100)
+                     0.875, 0.8125, 0.5, 0.84375,      # read 1 (length 101)
+                     0.875, 0.8125, 0.5, 0.84375,      # read 2 (length 900)
+                     0.5, 0.25, 0.125])                # read 3 (length 150)
+    off = np.array([0, 4, 8, 12, 15])
+    lengths = np.array([100, 101, 900, 150])
+    rules = [(100, 1, 0.0, 0.0), (150, 2, 0.0, 0.0), (400, 1, 0.0, 0.1)]
+    assert fo.rule_for_length(rules, 100) == rules[0]
+    assert fo.rule_for_length(rules, 101) == rules[1] and fo.rule_for_length(rules, 150) == rules[1]
+    assert fo.rule_for_length(rules, 151) == rules[2] and fo.rule_for_length(rules, 10 ** 6) == rules[2]
+    sel = fo.select_by_length(pred, off, lengths, rules)
+    # read 0: k = 1 -> the best only
+    np.testing.assert_array_equal(sel[0:4], [True, False, False, False])
+    # read 1: k = 2 -> 0.875 and 0.84375
+    np.testing.assert_array_equal(sel[4:8], [True, False, False, True])
+    # read 2 (longer than every bound: the last rule): k = 1 plus everything
+    # less than 0.1 below 0.875 (0.8125 and 0.84375)
+    np.testing.assert_array_equal(sel[8:12], [True, True, False, True])
+    # read 3: k = 2 of 3
+    np.testing.assert_array_equal(sel[12:15], [True, True, False])
+    # one rule reproduces select_candidates
+    np.testing.assert_array_equal(fo.select_by_length(pred, off, lengths, [(0, 2, 0.01, 0.05)]),
+                                  fo.select_candidates(pred, off, 2, 0.01, 0.05))

@@ -40,6 +40,8 @@ MUTANTS = {
     "select_delta_le": ("if top - np.float32(pred[a + j]) < np.float32(delta):",
                         "if top - np.float32(pred[a + j]) <= np.float32(delta):"),
     "select_delta_from_kth": ("top = np.float32(pred[a + order[0]])", "top = np.float32(pred[a + order[k - 1]])"),
+    "rule_bound_exclusive": ("        if m <= rule[0]:", "        if m < rule[0]:"),
+    "rule_past_bounds_first": ("    return rules[-1]", "    return rules[0]"),
     "select_delta_on_fallback_only": ("        sel[a + order[:k]] = True\n        top",
                                       "        sel[a + order[:k]] = True\n        continue\n        top"),
     "best_is_min": ("out[r] = int(s.max())", "out[r] = int(s.min())"),
