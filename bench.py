@@ -228,11 +228,12 @@ FILTER_WORKLOADS = {
 def _train_filter(name: str, rank: int, n_train: int, n_cal: int, epochs: int):
     """The filter network trained on the GPU by the library's own forward,
     backward and Adam kernels, on SW scores the method itself computes for
-    the pairs of another seed of the workload; then (k, tau, delta) picked
+    the pairs of another seed of the workload; then selection rules by read
+    length ((k, tau, delta) per length class, fewest aligned cells) picked
     on a held-out seed for >= 99.7% best-hit recall (the 0.2-point margin
-    over the 99.5% goal absorbs the optimism of picking the cheapest of a
-    few hundred settings on the same held-out set).  Not timed as part of
-    a step.  Returns (model, k, tau, delta, facts)."""
+    over the 99.5% goal absorbs the optimism of picking the cheapest of many
+    settings on the same held-out set).  Not timed as part of a step.
+    Returns (model, rules, facts)."""
     import numpy as np
     import torch
 
@@ -267,15 +268,21 @@ def _train_filter(name: str, rank: int, n_train: int, n_cal: int, epochs: int):
     wl_cal, b_cal, co_cal = load(2000 + rank, n_cal)
     flt.exhaustive_best(b_cal, co_cal, SCORING)
     pred_cal = model.forward(flt.features(b_cal, co_cal)).cpu().numpy()
-    cal = flt.calibrate(pred_cal, b_cal.score.cpu().numpy().astype(np.int64), wl_cal.cand_offsets, 0.997)
+    t2 = time.perf_counter()
+    cal = flt.calibrate_by_length(pred_cal, b_cal.score.cpu().numpy().astype(np.int64), wl_cal.cand_offsets,
+                                  wl_cal.read_lengths, wl_cal.window_lengths, 0.997)
+    calib_s = time.perf_counter() - t2
     # no setting reached the recall: align every candidate
-    k, tau, delta = cal[:3] if cal else (8, 1.0, 0.0)
+    rules = cal[0] if cal else flt.one_rule(8, 1.0)
     del b_cal
+    cal_cells = float((wl_cal.pair_read_lengths.astype(np.int64) * wl_cal.window_lengths).sum())
+    cal = {"rules": rules, "aligned_cells_share": cal[1] / cal_cells, "aligned_pairs_share": cal[2] / wl_cal.n_pairs,
+           "recall": cal[3], "reads": wl_cal.n_reads, "host_s": calib_s} if cal else None
     facts = {"pairs": n_train_pairs, "samples_per_epoch": n_samples, "epochs": epochs, "loss_per_epoch": losses,
              "train_s": train_s, "train_samples_per_s": n_samples * epochs / max(train_s, 1e-9),
              "gradient": "tensor cores (tcgen05), bf16 operands, fp32 accumulation",
              "setup_s": time.perf_counter() - t0, "calibration": cal}
-    return model, k, tau, delta, facts
+    return model, rules, facts
 
 
 def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int = 500_000,
@@ -283,7 +290,7 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
     """Plain vs learned-filtered best-hit search on a candidate workload
     (default: 500k reads of 150 bp, U{1..64} candidate windows of 250 bp, one
     true at 1-3% divergence, paralog decoys at 5-20% or random).  The network
-    is trained on SW scores of pairs from another seed, and (k, tau, delta) are
+    is trained on SW scores of pairs from another seed, and selection rules are
     picked on a held-out seed for >= 99.7% best-hit recall; neither is timed.
     A step is one whole search over the batch (score and end, no CIGAR).
     With on_device the timed batch is generated on the GPU (the same
@@ -302,7 +309,7 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
                                     pair_read=wl.pair_read, cigar=False)
         return wl, b, torch.from_numpy(wl.cand_offsets).cuda()
 
-    model, k, tau, delta, training = _train_filter(name, rank, n_train, n_cal, epochs)
+    model, rules, training = _train_filter(name, rank, n_train, n_cal, epochs)
     cal = training["calibration"]
 
     if on_device:
@@ -335,7 +342,7 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
 
     (best_plain, _), ms_plain = timed(lambda: flt.exhaustive_best(b, co, SCORING))
     best_plain = best_plain.cpu().numpy()
-    res, ms_filt = timed(lambda: flt.filtered_best(b, co, model, k, tau, SCORING, delta=delta))
+    res, ms_filt = timed(lambda: flt.filtered_best(b, co, model, rules, SCORING))
     best_filt = res.best_score.cpu().numpy()
     aligned = int(res.mask.sum().item())
     sel_cells = int(pair_cells[res.mask > 0].sum().item())
@@ -346,7 +353,7 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
     feats = flt.features(b, co)
     pred = model.forward(feats)
     e1.record(stream)
-    flt.filtered_best(b, co, model, k, tau, SCORING, feats=feats, delta=delta)
+    flt.filtered_best(b, co, model, rules, SCORING, feats=feats)
     e2.record(stream)
     e2.synchronize()
     recall = float(np.mean(best_filt == best_plain))
@@ -365,12 +372,12 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
         pipe = {"batches": n_b, "includes": "copies in and out, features, network, selection, SW on the selected "
                                             "pairs, top hit and mapping quality per read; wall clock"}
         for ns in (1, 2, 3):
-            flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns, delta=delta)  # warm each stream's scratch
+            flt.filtered_batches(model, hb, rules, SCORING, n_streams=ns)  # warm each stream's scratch
             torch.cuda.synchronize()
             walls = []
             for _ in range(steps):
                 t0 = time.perf_counter()
-                outs = flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns, delta=delta)
+                outs = flt.filtered_batches(model, hb, rules, SCORING, n_streams=ns)
                 torch.cuda.synchronize()
                 walls.append(time.perf_counter() - t0)
             wt = statistics.mean(walls)
@@ -393,10 +400,9 @@ def _filter_section(args, rank, steps: int, name: str = "filter", n_reads: int =
                          "aligned_pairs": aligned, "aligned_cells": sel_cells,
                          "features_and_mlp_ms": e0.elapsed_time(e1), "select_align_best_ms": e1.elapsed_time(e2),
                          "gcups_aligned": sel_cells / (ms_filt * 1e-3) / 1e9},
-            "speedup_reads_per_s": ms_plain / ms_filt, "best_hit_recall": recall, "k": k, "tau": tau,
-            "delta": delta,
+            "speedup_reads_per_s": ms_plain / ms_filt, "best_hit_recall": recall, "selection_rules": rules,
             "filtered_pipelined_from_host": pipe,
-            "calibration_recall": cal[4] if cal else None, "training": training, "steps": steps}
+            "calibration_recall": cal["recall"] if cal else None, "training": training, "steps": steps}
 
 
 def _uneven_section(args, rank, steps: int, peak_gcups: float) -> dict:
@@ -946,7 +952,7 @@ def _fullmix_headline(args, rank: int, ws: int, pg, peak: dict, local: int) -> d
     from paper_1304_0681_gb300.shard import reduce_run
 
     name = "fullmix"
-    model, k, tau, delta, training = _train_filter(name, rank, n_train=40_000, n_cal=100_000, epochs=16)
+    model, rules, training = _train_filter(name, rank, n_train=40_000, n_cal=100_000, epochs=16)
     t0 = time.perf_counter()
     wl = synth.generate_device(name, seed=rank, n_reads=args.fullmix_reads)
     torch.cuda.synchronize()
@@ -964,8 +970,7 @@ def _fullmix_headline(args, rank: int, ws: int, pg, peak: dict, local: int) -> d
 
     def filtered():
         _swgb.sw_filter_align(wl.reads, wl.read_offsets, n_reads, wl.windows, wl.window_offsets, wl.pair_read,
-                              wl.cand_offsets, n_pairs, model.buf, k, tau, delta, SCORING, score, end, mask, best,
-                              cand)
+                              wl.cand_offsets, n_pairs, model.buf, rules, SCORING, score, end, mask, best, cand)
 
     def plain():
         _swgb.sw_batch_align_indexed(wl.reads, wl.read_offsets, n_reads, wl.windows, wl.window_offsets,
@@ -1054,7 +1059,7 @@ def _fullmix_headline(args, rank: int, ws: int, pg, peak: dict, local: int) -> d
     out = {"value": all_reads / total_s, "ms_per_step": total_s * 1e3 / args.steps, "clocks": clk,
            "gpu_launches": int(launches),
            "config": {"workload": WORKLOADS[name], "reads_per_gpu": n_reads, "pairs_per_gpu": n_pairs,
-                      "cells_exhaustive_per_gpu": cells, "k": k, "tau": tau, "delta": delta,
+                      "cells_exhaustive_per_gpu": cells, "selection_rules": rules,
                       "scoring": list(SCORING),
                       "api": "sw_filter_align (features, network, selection, SW score + end, best per read)",
                       "l2": "inputs larger than L2 (about 12 GB of packed windows per step)",
@@ -1080,7 +1085,7 @@ def _fullmix_headline(args, rank: int, ws: int, pg, peak: dict, local: int) -> d
                                  "frac": feat_bytes / (feat_ms * 1e-3) / 1e9 / peak["hbm_gbs"],
                                  "algorithmic_bytes": feat_bytes,
                                  "per_unit": "packed bytes of each read once and of each window + 128 B of bf16 features per pair"},
-           "training": {key: training[key] for key in ("pairs", "samples_per_epoch", "epochs", "train_s",
+           "training": {key: training[key] for key in ("pairs", "samples_per_epoch", "epochs", "train_s", "calibration",
                                                        "train_samples_per_s", "gradient")}}
 
     # end to end: the same reads from pinned host memory in batches, through
@@ -1102,13 +1107,13 @@ def _fullmix_headline(args, rank: int, ws: int, pg, peak: dict, local: int) -> d
             del sub
         torch.cuda.empty_cache()
         ns = max(1, args.e2e_streams)
-        outs = flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns, delta=delta)  # each stream's scratch
+        outs = flt.filtered_batches(model, hb, rules, SCORING, n_streams=ns)  # each stream's scratch
         torch.cuda.synchronize()
         reps = max(2, min(args.steps, 3))
         walls = []
         for _ in range(reps):
             t0 = time.perf_counter()
-            outs = flt.filtered_batches(model, hb, k, tau, SCORING, n_streams=ns, delta=delta)
+            outs = flt.filtered_batches(model, hb, rules, SCORING, n_streams=ns)
             torch.cuda.synchronize()
             walls.append(time.perf_counter() - t0)
         e2e_reads, e2e_s = reduce_run(n_reads, statistics.mean(walls))
@@ -1307,8 +1312,7 @@ def _summary(head, thr, unev, filt, graph, seeding) -> dict:
         s["fullmix_10M"] = {"filtered_rps": _r(head["filtered"]["reads_per_s"]),
                             "plain_rps": _r(head["plain"]["reads_per_s"]),
                             "speedup": _r(head["speedup_reads_per_s"], 3), "recall": _r(head["best_hit_recall"], 5),
-                            "k": head["config"]["k"], "tau": head["config"]["tau"],
-                            "delta": head["config"].get("delta"),
+                            "rules": [list(r) for r in head["config"]["selection_rules"]],
                             "aligned_share": _r(head["filtered"]["aligned_share"], 3),
                             "plain_gcups": _r(head["plain"]["gcups"]),
                             "score_frac": _r(head["roofline"]["frac"], 3),
@@ -1332,7 +1336,7 @@ def _summary(head, thr, unev, filt, graph, seeding) -> dict:
         s["filter_500k"] = {"filtered_rps": _r(filt["filtered"]["reads_per_s"]),
                             "plain_rps": _r(filt["plain"]["reads_per_s"]),
                             "speedup": _r(filt["speedup_reads_per_s"], 3), "recall": _r(filt["best_hit_recall"], 5),
-                            "k": filt["k"], "tau": filt["tau"], "delta": filt.get("delta")}
+                            "rules": [list(r) for r in filt["selection_rules"]]}
     if graph:
         s["graph_16k"] = {"direct_ms": _r(graph["direct_ms_per_batch"], 3),
                           "graph_ms": _r(graph["graph_ms_per_batch"], 3)}

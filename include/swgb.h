@@ -274,6 +274,28 @@ int sw_mlp_adam(float *model, float lr, int32_t step, sw_stream_t stream);
 int sw_filter_select(const float *pred, const int64_t *cand_offsets, int64_t n_reads, int32_t k, float tau,
                      float delta, uint8_t *pair_mask, sw_stream_t stream);
 
+/* One selection rule: reads of length up to max_read_len select as
+ * sw_filter_select with this k, tau and delta. */
+typedef struct {
+    int32_t max_read_len;
+    int32_t k;
+    float tau;
+    float delta;
+} sw_select_rule_t;
+#define SW_FILTER_MAX_RULES 16
+
+/* sw_filter_select with the rule chosen per read by its length m (from
+ * read_offsets, device int64[n_reads + 1] in bases): the first of `rules`
+ * (host memory, n_rules of them, max_read_len ascending) with
+ * m <= max_read_len, else the last.  The rules let short reads, whose
+ * features rank candidates less reliably, keep more candidates than long
+ * ones.  read_offsets may be NULL with a single rule.  SW_ERR_INVALID_ARG
+ * for n_rules outside 1..SW_FILTER_MAX_RULES, descending bounds, a rule's k
+ * outside 1..SW_FILTER_MAX_K or a negative or NaN delta. */
+int sw_filter_select_by_length(const float *pred, const int64_t *cand_offsets, const int64_t *read_offsets,
+                               int64_t n_reads, const sw_select_rule_t *rules, int32_t n_rules,
+                               uint8_t *pair_mask, sw_stream_t stream);
+
 /* Per read: the largest score over its candidates with pair_mask[p] != 0
  * (pair_mask may be NULL: all), and that candidate's index within the read
  * (first on ties); -1 and -1 when none. */
@@ -282,7 +304,8 @@ int sw_best_per_read(const int32_t *score, const int64_t *cand_offsets, int64_t 
 
 /*
  * sw_filter_align -- the filtered search in one call: sw_filter_features,
- * sw_mlp_forward, sw_filter_select (k, tau, delta), sw_batch_align_masked (score
+ * sw_mlp_forward, sw_filter_select_by_length (rules, n_rules: checked as
+ * there, before any device work), sw_batch_align_masked (score
  * and end; unselected pairs get score -1 and end (-1, -1)) and
  * sw_best_per_read over the selected pairs.  Reads, windows and offsets as
  * sw_batch_align_indexed; pair_read (device int64[n_pairs]) must agree with
@@ -297,7 +320,7 @@ int sw_best_per_read(const int32_t *score, const int64_t *cand_offsets, int64_t 
  */
 int sw_filter_align(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads, const uint8_t *windows,
                     const int64_t *window_offsets, const int64_t *pair_read, const int64_t *cand_offsets,
-                    int64_t n_pairs, const float *model, int32_t k, float tau, float delta,
+                    int64_t n_pairs, const float *model, const sw_select_rule_t *rules, int32_t n_rules,
                     const sw_scoring_t *scoring, int32_t *out_score, int32_t *out_end, uint8_t *pair_mask,
                     int32_t *best_score, int32_t *best_cand, sw_stream_t stream);
 

@@ -28,7 +28,7 @@ EXPORTS = ("sw_cigar_capacity", "sw_cigar_offsets", "sw_packed_bytes", "sw_batch
            "sw_junctions_export",
            "sw_plan_rows", "sw_phase_timing", "sw_phase_times", "sw_batch_align_noalloc",
            "sw_batch_align_masked", "sw_filter_features", "sw_mlp_bytes", "sw_mlp_init", "sw_mlp_refresh",
-           "sw_mlp_forward", "sw_set_mlp_kernel", "sw_set_mlp_grad_kernel", "sw_mlp_grad", "sw_mlp_adam", "sw_filter_select", "sw_best_per_read",
+           "sw_mlp_forward", "sw_set_mlp_kernel", "sw_set_mlp_grad_kernel", "sw_mlp_grad", "sw_mlp_adam", "sw_filter_select", "sw_filter_select_by_length", "sw_best_per_read",
            "sw_top_hits", "sw_filter_align", "sw_filter_train_step", "sw_get_status",
            # include/swgb_seed.h
            "sw_index_table_words", "sw_index_build", "sw_seed_windows", "sw_reads_two_strands",
@@ -46,6 +46,23 @@ class SwError(RuntimeError):
 class Scoring(ctypes.Structure):
     _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32),
                 ("gap_open", ctypes.c_int32), ("gap_extend", ctypes.c_int32)]
+
+
+class SelectRule(ctypes.Structure):
+    """sw_select_rule_t: reads up to max_read_len select with (k, tau, delta)."""
+    _fields_ = [("max_read_len", ctypes.c_int32), ("k", ctypes.c_int32), ("tau", ctypes.c_float),
+                ("delta", ctypes.c_float)]
+
+
+SW_FILTER_MAX_RULES = 16
+
+
+def _rules(rules):
+    """A ctypes array of sw_select_rule_t from (max_read_len, k, tau, delta)
+    tuples, and its length."""
+    rules = list(rules)
+    arr = (SelectRule * max(len(rules), 1))(*[SelectRule(int(m), int(k), float(t), float(d)) for m, k, t, d in rules])
+    return arr, len(rules)
 
 
 class Cigar(ctypes.Structure):
@@ -115,7 +132,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sw_best_per_read.restype = ctypes.c_int
     lib.sw_top_hits.argtypes = [p, p, i64, p, p, p, p, p, p]
     lib.sw_top_hits.restype = ctypes.c_int
-    lib.sw_filter_align.argtypes = [p, p, i64, p, p, p, p, i64, p, i32, ctypes.c_float, ctypes.c_float,
+    lib.sw_filter_select_by_length.argtypes = [p, p, p, i64, ctypes.POINTER(SelectRule), i32, p, p]
+    lib.sw_filter_select_by_length.restype = ctypes.c_int
+    lib.sw_filter_align.argtypes = [p, p, i64, p, p, p, p, i64, p, ctypes.POINTER(SelectRule), i32,
                                     ctypes.POINTER(Scoring), p, p, p, p, p, p]
     lib.sw_filter_align.restype = ctypes.c_int
     lib.sw_filter_train_step.argtypes = [p, p, p, p, i64, ctypes.c_float, i32, p]
@@ -472,18 +491,28 @@ def sw_filter_select(pred, cand_offsets, n_reads: int, k: int, tau: float, delta
                                  ctypes.c_float(delta), _ptr(pair_mask), _stream(stream)), "sw_filter_select")
 
 
+def sw_filter_select_by_length(pred, cand_offsets, read_offsets, n_reads: int, rules, pair_mask,
+                               stream=None) -> None:
+    """rules: (max_read_len, k, tau, delta) tuples, max_read_len ascending."""
+    arr, n = _rules(rules)
+    _check(_lib.sw_filter_select_by_length(_ptr(pred), _ptr(cand_offsets), _ptr(read_offsets), int(n_reads), arr, n,
+                                           _ptr(pair_mask), _stream(stream)), "sw_filter_select_by_length")
+
+
 def sw_best_per_read(score, cand_offsets, n_reads: int, pair_mask, best_score, best_cand, stream=None) -> None:
     _check(_lib.sw_best_per_read(_ptr(score), _ptr(cand_offsets), int(n_reads), _ptr(pair_mask), _ptr(best_score),
                                  _ptr(best_cand), _stream(stream)), "sw_best_per_read")
 
 
 def sw_filter_align(reads, read_offsets, n_reads: int, windows, window_offsets, pair_read, cand_offsets,
-                    n_pairs: int, model, k: int, tau: float, delta: float, scoring, out_score, out_end, pair_mask,
-                    best_score, best_cand, stream=None) -> None:
+                    n_pairs: int, model, rules, scoring, out_score, out_end, pair_mask, best_score, best_cand,
+                    stream=None) -> None:
+    """rules: (max_read_len, k, tau, delta) tuples, max_read_len ascending."""
     sc = _scoring(scoring)
+    arr, n = _rules(rules)
     _check(_lib.sw_filter_align(_ptr(reads), _ptr(read_offsets), int(n_reads), _ptr(windows), _ptr(window_offsets),
-                                _ptr(pair_read), _ptr(cand_offsets), int(n_pairs), _ptr(model), int(k),
-                                ctypes.c_float(tau), ctypes.c_float(delta), ctypes.byref(sc), _ptr(out_score), _ptr(out_end), _ptr(pair_mask),
+                                _ptr(pair_read), _ptr(cand_offsets), int(n_pairs), _ptr(model), arr, n,
+                                ctypes.byref(sc), _ptr(out_score), _ptr(out_end), _ptr(pair_mask),
                                 _ptr(best_score), _ptr(best_cand), _stream(stream)), "sw_filter_align")
 
 

@@ -491,15 +491,25 @@ __global__ void k_mlp_adam(float *model, float lr, int32_t step)
 
 // ---------------------------------------------------- selection and best hit
 
-// Per read: the k best predictions (ties: lower candidate index first) and
-// every other candidate whose prediction lies less than delta below the
-// read's best; if the k-th and the (k+1)-th are closer than tau, every
-// candidate.  The differences are taken in fp32.
-__global__ void k_select(const float *__restrict__ pred, const int64_t *__restrict__ cand_off, int64_t n_reads,
-                         int32_t k, float tau, float delta, uint8_t *__restrict__ mask)
+// Per read, with the (k, tau, delta) of the rule for its length (the first
+// rule whose bound is at least the read's length, else the last; without
+// read offsets the first rule): the k best predictions (ties: lower
+// candidate index first) and every other candidate whose prediction lies
+// less than delta below the read's best; if the k-th and the (k+1)-th are
+// closer than tau, every candidate.  The differences are taken in fp32.
+__global__ void k_select(const float *__restrict__ pred, const int64_t *__restrict__ cand_off,
+                         const int64_t *__restrict__ read_off, int64_t n_reads, const SelectRules rules,
+                         uint8_t *__restrict__ mask)
 {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_reads;
          r += (int64_t)gridDim.x * blockDim.x) {
+        int q = 0;
+        if (read_off) {
+            const int64_t m = read_off[r + 1] - read_off[r];
+            while (q + 1 < rules.n && m > rules.max_len[q]) ++q;
+        }
+        const int k = rules.k[q];
+        const float tau = rules.tau[q], delta = rules.delta[q];
         const int64_t a = cand_off[r], b = cand_off[r + 1];
         const int64_t c = b - a;
         if (c <= k) {
@@ -516,9 +526,9 @@ __global__ void k_select(const float *__restrict__ pred, const int64_t *__restri
             while (pos > 0 && bv[pos - 1] < v) --pos;  // strictly better moves up: ties keep index order
             if (pos > k) continue;
             const int last = cnt < k + 1 ? cnt : k;
-            for (int q = last; q > pos; --q) {
-                bv[q] = bv[q - 1];
-                bi[q] = bi[q - 1];
+            for (int q2 = last; q2 > pos; --q2) {
+                bv[q2] = bv[q2 - 1];
+                bi[q2] = bi[q2 - 1];
             }
             bv[pos] = v;
             bi[pos] = p;
@@ -528,7 +538,7 @@ __global__ void k_select(const float *__restrict__ pred, const int64_t *__restri
         const float top = bv[0];
         for (int64_t p = a; p < b; ++p) mask[p] = (all || top - pred[p] < delta) ? 1 : 0;
         if (!all)
-            for (int q = 0; q < k; ++q) mask[bi[q]] = 1;
+            for (int q2 = 0; q2 < k; ++q2) mask[bi[q2]] = 1;
     }
 }
 
@@ -650,10 +660,10 @@ int launch_mlp_adam(float *model, float lr, int32_t step, cudaStream_t st)
     return launch_status();
 }
 
-int launch_select(const float *pred, const int64_t *cand_off, int64_t n_reads, int32_t k, float tau, float delta,
-                  uint8_t *mask, cudaStream_t st)
+int launch_select(const float *pred, const int64_t *cand_off, const int64_t *read_off, int64_t n_reads,
+                  const SelectRules &rules, uint8_t *mask, cudaStream_t st)
 {
-    k_select<<<grid_for(n_reads, 128, 152 * 32), 128, 0, st>>>(pred, cand_off, n_reads, k, tau, delta, mask);
+    k_select<<<grid_for(n_reads, 128, 152 * 32), 128, 0, st>>>(pred, cand_off, read_off, n_reads, rules, mask);
     count_launch();
     return launch_status();
 }
@@ -774,13 +784,45 @@ int sw_mlp_adam(float *model, float lr, int32_t step, sw_stream_t stream)
     return launch_mlp_adam(model, lr, step, (cudaStream_t)stream);
 }
 
+// Host-side check of a rule table: 1..SW_FILTER_MAX_RULES rules with
+// ascending bounds, 1 <= k <= SW_FILTER_MAX_K and delta >= 0 each.
+static int make_rules(const sw_select_rule_t *rules, int32_t n_rules, SelectRules *out)
+{
+    if (!rules || n_rules < 1 || n_rules > SW_FILTER_MAX_RULES) return SW_ERR_INVALID_ARG;
+    out->n = n_rules;
+    for (int q = 0; q < n_rules; ++q) {
+        const sw_select_rule_t &u = rules[q];
+        if (u.k < 1 || u.k > SW_FILTER_MAX_K || !(u.delta >= 0.f)) return SW_ERR_INVALID_ARG;
+        if (q > 0 && u.max_read_len < rules[q - 1].max_read_len) return SW_ERR_INVALID_ARG;
+        out->max_len[q] = u.max_read_len;
+        out->k[q] = u.k;
+        out->tau[q] = u.tau;
+        out->delta[q] = u.delta;
+    }
+    return SW_OK;
+}
+
 int sw_filter_select(const float *pred, const int64_t *cand_offsets, int64_t n_reads, int32_t k, float tau,
                      float delta, uint8_t *pair_mask, sw_stream_t stream)
 {
-    if (n_reads < 0 || k < 1 || k > SW_FILTER_MAX_K || !(delta >= 0.f)) return SW_ERR_INVALID_ARG;
+    const sw_select_rule_t one{INT32_MAX, k, tau, delta};
+    SelectRules rules;
+    if (n_reads < 0 || make_rules(&one, 1, &rules)) return SW_ERR_INVALID_ARG;
     if (n_reads == 0) return SW_OK;
     if (!pred || !cand_offsets || !pair_mask) return SW_ERR_INVALID_ARG;
-    return launch_select(pred, cand_offsets, n_reads, k, tau, delta, pair_mask, (cudaStream_t)stream);
+    return launch_select(pred, cand_offsets, nullptr, n_reads, rules, pair_mask, (cudaStream_t)stream);
+}
+
+int sw_filter_select_by_length(const float *pred, const int64_t *cand_offsets, const int64_t *read_offsets,
+                               int64_t n_reads, const sw_select_rule_t *rules, int32_t n_rules, uint8_t *pair_mask,
+                               sw_stream_t stream)
+{
+    SelectRules sr;
+    if (n_reads < 0 || make_rules(rules, n_rules, &sr)) return SW_ERR_INVALID_ARG;
+    if (n_reads == 0) return SW_OK;
+    if (!pred || !cand_offsets || !pair_mask || (n_rules > 1 && !read_offsets)) return SW_ERR_INVALID_ARG;
+    return launch_select(pred, cand_offsets, n_rules > 1 ? read_offsets : nullptr, n_reads, sr, pair_mask,
+                         (cudaStream_t)stream);
 }
 
 int sw_best_per_read(const int32_t *score, const int64_t *cand_offsets, int64_t n_reads, const uint8_t *pair_mask,
@@ -795,11 +837,12 @@ int sw_best_per_read(const int32_t *score, const int64_t *cand_offsets, int64_t 
 
 int sw_filter_align(const uint8_t *reads, const int64_t *read_offsets, int64_t n_reads, const uint8_t *windows,
                     const int64_t *window_offsets, const int64_t *pair_read, const int64_t *cand_offsets,
-                    int64_t n_pairs, const float *model, int32_t k, float tau, float delta,
+                    int64_t n_pairs, const float *model, const sw_select_rule_t *rules, int32_t n_rules,
                     const sw_scoring_t *scoring, int32_t *out_score, int32_t *out_end, uint8_t *pair_mask,
                     int32_t *best_score, int32_t *best_cand, sw_stream_t stream)
 {
-    if (n_reads < 0 || n_pairs < 0 || k < 1 || k > SW_FILTER_MAX_K || !(delta >= 0.f)) return SW_ERR_INVALID_ARG;
+    SelectRules sr;
+    if (n_reads < 0 || n_pairs < 0 || make_rules(rules, n_rules, &sr)) return SW_ERR_INVALID_ARG;
     if (n_reads == 0) return n_pairs == 0 ? SW_OK : SW_ERR_INVALID_ARG;
     if (!cand_offsets || !best_score) return SW_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -830,7 +873,8 @@ int sw_filter_align(const uint8_t *reads, const int64_t *read_offsets, int64_t n
     if ((rc = sw_filter_features(reads, read_offsets, n_reads, windows, window_offsets, cand_offsets, feat, stream)))
         return rc;
     if ((rc = sw_mlp_forward(model, feat, n_pairs, pred, stream))) return rc;
-    if ((rc = sw_filter_select(pred, cand_offsets, n_reads, k, tau, delta, mask, stream))) return rc;
+    if ((rc = launch_select(pred, cand_offsets, n_rules > 1 ? read_offsets : nullptr, n_reads, sr, mask, st)))
+        return rc;
     if ((rc = sw_batch_align_masked(reads, read_offsets, n_reads, windows, window_offsets, pair_read, mask, n_pairs,
                                     scoring, out_score, out_end, nullptr, stream)))
         return rc;

@@ -395,8 +395,16 @@ int launch_mlp_forward(const float *model, const uint16_t *feat, int64_t n, floa
 int launch_mlp_grad(float *model, const uint16_t *feat, const float *target, const int32_t *idx, int64_t n,
                     int sm_count, cudaStream_t st);
 int launch_mlp_adam(float *model, float lr, int32_t step, cudaStream_t st);
-int launch_select(const float *pred, const int64_t *cand_off, int64_t n_reads, int32_t k, float tau, float delta,
-                  uint8_t *mask, cudaStream_t st);
+// The filter's selection rules, by value in the kernel's parameters.
+struct SelectRules {
+    int32_t n;
+    int32_t max_len[SW_FILTER_MAX_RULES];
+    int32_t k[SW_FILTER_MAX_RULES];
+    float tau[SW_FILTER_MAX_RULES];
+    float delta[SW_FILTER_MAX_RULES];
+};
+int launch_select(const float *pred, const int64_t *cand_off, const int64_t *read_off, int64_t n_reads,
+                  const SelectRules &rules, uint8_t *mask, cudaStream_t st);
 int launch_best_per_read(const int32_t *score, const int64_t *cand_off, int64_t n_reads, const uint8_t *mask,
                          int32_t *best, int32_t *best_cand, cudaStream_t st);
 

@@ -2,8 +2,11 @@
 
 The paper aligns each read against every extended CAL.  Here a small network
 predicts each candidate's SW score from 4-mer features, only the top-k
-candidates of a read are aligned, and reads whose top predictions are too
-close to call (margin below tau) fall back to aligning every candidate.
+candidates of a read (and those predicted within delta of its best) are
+aligned, and reads whose top predictions are too close to call (margin below
+tau) fall back to aligning every candidate.  (k, tau, delta) may differ by
+read length: a selection is a list of rules (max_read_len, k, tau, delta),
+the first rule whose bound is at least the read's length applying.
 Reported scores are always SW scores of aligned candidates.
 
 Every computation runs in libswgb kernels; this module only allocates the
@@ -20,6 +23,12 @@ from . import _swgb
 from .device import DeviceBatch
 
 N_FEAT = 64
+ALL_LENGTHS = 2 ** 31 - 1
+
+
+def one_rule(k: int, tau: float, delta: float = 0.0) -> list:
+    """The same (k, tau, delta) for reads of every length."""
+    return [(ALL_LENGTHS, int(k), float(tau), float(delta))]
 
 
 class FilterModel:
@@ -124,15 +133,15 @@ class FilteredResult:
     pred: torch.Tensor         # float per pair
 
 
-def filtered_best(batch: DeviceBatch, cand_offsets: torch.Tensor, model: FilterModel, k: int, tau: float, scoring,
-                  feats: torch.Tensor | None = None, delta: float = 0.0) -> FilteredResult:
-    """Features -> network -> top-k (+ within delta of the best) / fallback
-    selection -> SW on the selected pairs -> best hit per read (score and
-    end only)."""
+def filtered_best(batch: DeviceBatch, cand_offsets: torch.Tensor, model: FilterModel, rules, scoring,
+                  feats: torch.Tensor | None = None) -> FilteredResult:
+    """Features -> network -> selection by the rules (top-k, within delta
+    of the best, fallback) -> SW on the selected pairs -> best hit per read
+    (score and end only)."""
     feats = features(batch, cand_offsets) if feats is None else feats
     pred = model.forward(feats)
     mask = torch.empty(batch.n_pairs, dtype=torch.uint8, device=pred.device)
-    _swgb.sw_filter_select(pred, cand_offsets, batch.n_reads, k, tau, delta, mask)
+    _swgb.sw_filter_select_by_length(pred, cand_offsets, batch.read_offsets, batch.n_reads, rules, mask)
     _swgb.sw_batch_align_masked(batch.reads, batch.read_offsets, batch.n_reads, batch.windows, batch.window_offsets,
                                 batch.pair_read, mask, batch.n_pairs, scoring, batch.score, batch.end, None)
     best = torch.empty(batch.n_reads, dtype=torch.int32, device=pred.device)
@@ -159,8 +168,7 @@ class FilterBatchResult:
     aligned_pairs: int
 
 
-def _filter_host_batch(model: FilterModel, batch, k: int, tau: float, scoring,
-                       delta: float = 0.0) -> FilterBatchResult:
+def _filter_host_batch(model: FilterModel, batch, rules, scoring) -> FilterBatchResult:
     """One host batch (packed reads, read offsets, packed windows, window
     offsets, pair -> read, candidate offsets; pinned CPU tensors) through the
     filtered search on the current stream, results copied back."""
@@ -172,7 +180,7 @@ def _filter_host_batch(model: FilterModel, batch, k: int, tau: float, scoring,
                     torch.empty(2 * n_pairs, dtype=torch.int32, device=dev), None, None, None)
     pred = model.forward(features(b, coff))
     mask = torch.empty(n_pairs, dtype=torch.uint8, device=dev)
-    _swgb.sw_filter_select(pred, coff, n_reads, k, tau, delta, mask)
+    _swgb.sw_filter_select_by_length(pred, coff, roff, n_reads, rules, mask)
     _swgb.sw_batch_align_masked(b.reads, b.read_offsets, n_reads, b.windows, b.window_offsets, b.pair_read, mask,
                                 n_pairs, scoring, b.score, b.end, None)
     top = top_hits(b.score, coff, n_reads, mask)
@@ -182,8 +190,7 @@ def _filter_host_batch(model: FilterModel, batch, k: int, tau: float, scoring,
                              int(out[3 * n_reads]))
 
 
-def filtered_batches(model: FilterModel, batches, k: int, tau: float, scoring, n_streams: int = 2,
-                     delta: float = 0.0) -> list:
+def filtered_batches(model: FilterModel, batches, rules, scoring, n_streams: int = 2) -> list:
     """The filtered search over a sequence of host batches (see
     _filter_host_batch for their layout): copy in, features, network,
     selection, SW on the selected pairs, top hits, copy out, with n_streams
@@ -191,7 +198,7 @@ def filtered_batches(model: FilterModel, batches, k: int, tau: float, scoring, n
     batch, in order."""
     from .seed import run_on_worker_streams
     return run_on_worker_streams(model.buf.device, list(batches),
-                                 lambda bt, s: _filter_host_batch(model, bt, k, tau, scoring, delta), n_streams)
+                                 lambda bt, s: _filter_host_batch(model, bt, rules, scoring), n_streams)
 
 
 def oversample_top(score: np.ndarray, cand_offsets: np.ndarray, top: int = 1, times: int = 4) -> np.ndarray:
@@ -272,3 +279,115 @@ def calibrate(pred: np.ndarray, score: np.ndarray, cand_offsets: np.ndarray, rec
                 if recall >= recall_target and (best is None or aligned < best[3]):
                     best = (k, float(tau), float(delta), aligned, recall)
     return best
+
+
+# Upper bounds of the read-length classes calibrate_by_length gives rules to
+# (about a factor 1.4 apart); longer reads form one more class.
+LENGTH_BOUNDS = (80, 112, 160, 224, 320, 448, 640, 896, 1280, 1792, 2560)
+
+
+def _selection_table(pred, score, cand_offsets, ks, taus, deltas):
+    """For every grid point (k, tau, delta): per read whether the selection
+    keeps a best-scoring candidate, and the mask of selected pairs."""
+    nr = len(cand_offsets) - 1
+    counts = np.diff(cand_offsets)
+    rid = np.repeat(np.arange(nr), counts)
+    true_best = _segment_max(score, cand_offsets, counts)
+    order = np.lexsort((np.arange(len(pred)), -pred, rid))
+    rank = np.empty(len(pred), np.int64)
+    rank[order] = np.arange(len(pred)) - np.repeat(cand_offsets[:-1], counts)[order]
+    top_pred = np.full(nr, -np.inf, np.float32)
+    top_pred[rid[rank == 0]] = pred[rank == 0]
+    below_top = top_pred[rid] - pred
+    for k in ks:
+        sel_pred = np.full(nr, -np.inf, np.float32)
+        nxt_pred = np.full(nr, -np.inf, np.float32)
+        sel_pred[rid[rank == k - 1]] = pred[rank == k - 1]
+        nxt_pred[rid[rank == k]] = pred[rank == k]
+        with np.errstate(invalid="ignore"):
+            gap = sel_pred - nxt_pred
+        for delta in deltas:
+            kept = (rank < k) | (below_top < np.float32(delta))
+            kept_best = _segment_max(np.where(kept, score, -1), cand_offsets, counts)
+            for tau in taus:
+                fall = (counts <= k) | (gap < np.float32(tau))
+                hit = np.where(fall, true_best, kept_best) == true_best
+                yield (k, float(tau), float(delta)), hit, kept | fall[rid], rid
+
+
+def calibrate_by_length(pred: np.ndarray, score: np.ndarray, cand_offsets: np.ndarray, read_lengths: np.ndarray,
+                        window_lengths: np.ndarray, recall_target: float, bounds=LENGTH_BOUNDS,
+                        ks=(1, 2, 3, 4, 5, 6, 7, 8), taus=None, deltas=None):
+    """Selection rules by read length: one (k, tau, delta) per length class
+    (reads up to each of `bounds`, and longer ones), chosen together so that
+    the aligned cells (read length x window length of the selected pairs)
+    are fewest while the best-hit recall over all reads reaches
+    recall_target.  An exact minimum over the grid: a dynamic program over
+    the classes on the number of reads whose best hit is missed.  Returns
+    (rules, aligned cells, aligned pairs, recall) or None when no choice
+    reaches the target; rules as sw_filter_select_by_length takes them.
+    Host-side bookkeeping over predictions and exhaustive scores already
+    computed on the GPU."""
+    taus = taus if taus is not None else [0.0, 0.01, 0.03]
+    deltas = deltas if deltas is not None else [0.0, 0.02, 0.04, 0.06, 0.08, 0.1, 0.12, 0.15, 0.2, 0.25, 0.3]
+    pred = np.asarray(pred, np.float32)
+    score = np.asarray(score, np.int64)
+    cand_offsets = np.asarray(cand_offsets, np.int64)
+    read_lengths = np.asarray(read_lengths, np.int64)
+    nr = len(cand_offsets) - 1
+    if nr == 0:
+        return None
+    cls = np.searchsorted(np.asarray(bounds), read_lengths, side="left")  # m <= bounds[c]
+    n_cls = len(bounds) + 1
+    need = int(np.ceil(recall_target * nr - 1e-9))     # reads whose best hit must be kept
+    max_miss = nr - need
+    if max_miss < 0:
+        return None
+    pair_cells = read_lengths[np.repeat(np.arange(nr), np.diff(cand_offsets))] * np.asarray(window_lengths, np.int64)
+    # per class and grid point: missed reads, aligned cells, aligned pairs
+    opts = {c: [] for c in range(n_cls) if np.any(cls == c)}
+    for key, hit, sel, rid in _selection_table(pred, score, cand_offsets, ks, taus or [0.0], deltas):
+        miss = np.bincount(cls[~hit], minlength=n_cls)
+        cells = np.bincount(cls[rid[sel]], weights=pair_cells[sel], minlength=n_cls)
+        pairs = np.bincount(cls[rid[sel]], minlength=n_cls)
+        for c in opts:
+            opts[c].append((int(miss[c]), float(cells[c]), int(pairs[c]), key))
+    # dynamic program: best[b] = fewest cells over the classes so far with b misses
+    INF = float("inf")
+    best = np.full(max_miss + 1, INF)
+    best[0] = 0.0
+    picks = []
+    for c in sorted(opts):
+        nb = np.full(max_miss + 1, INF)
+        arg = np.full(max_miss + 1, -1, np.int64)
+        for i, (mi, ce, _, _) in enumerate(opts[c]):
+            if mi > max_miss:
+                continue
+            cand = np.full(max_miss + 1, INF)
+            cand[mi:] = best[:max_miss + 1 - mi] + ce
+            better = cand < nb
+            nb[better] = cand[better]
+            arg[better] = i
+        picks.append((c, arg, best))
+        best = nb
+    b = int(np.argmin(best))
+    if not np.isfinite(best[b]):
+        return None
+    chosen = {}
+    for c, arg, prev in reversed(picks):
+        i = int(arg[b])
+        chosen[c] = opts[c][i]
+        b -= opts[c][i][0]
+    rules = []
+    for c in sorted(chosen):
+        bound = bounds[c] if c < len(bounds) else ALL_LENGTHS
+        k, tau, delta = chosen[c][3]
+        if rules and rules[-1][1:] == (k, tau, delta):
+            rules[-1] = (bound, k, tau, delta)      # the same setting as the class below: one rule
+        else:
+            rules.append((bound, k, tau, delta))
+    rules[-1] = (ALL_LENGTHS,) + rules[-1][1:]
+    misses = sum(v[0] for v in chosen.values())
+    cells = sum(v[1] for v in chosen.values())
+    pairs = sum(v[2] for v in chosen.values())
+    return rules, cells, pairs, (nr - misses) / nr

@@ -103,13 +103,30 @@ def test_filter_entry_points_check_arguments_before_any_device_work():
     sc = ctypes.byref(_swgb.Scoring(5, -4, -10, -1))
     f = ctypes.c_float
 
-    def align(n_reads, n_pairs, k=3, cand=1, model=1, best=1, delta=0.0):
-        return lib.sw_filter_align(1, 1, n_reads, 1, 1, 1, cand, n_pairs, model, k, f(0.0), f(delta), sc, 1, 1, None,
+    def rules(*rs):
+        arr, n = _swgb._rules(rs)
+        return arr, n
+
+    def align(n_reads, n_pairs, k=3, cand=1, model=1, best=1, delta=0.0, rs=None):
+        arr, n = rs if rs is not None else rules((1000, k, 0.0, delta))
+        return lib.sw_filter_align(1, 1, n_reads, 1, 1, 1, cand, n_pairs, model, arr, n, sc, 1, 1, None,
                                    best, None, None)
     assert align(-1, 0) == -1
     assert align(2, 5, k=0) == -1 and align(2, 5, k=17) == -1
     assert align(2, 5, delta=-0.01) == -1 and align(2, 5, delta=float("nan")) == -1
     assert align(0, 0, delta=0.5) == 0
+    assert align(2, 5, rs=rules()) == -1                                  # no rule
+    assert align(2, 5, rs=rules((200, 2, 0.0, 0.0), (100, 2, 0.0, 0.0))) == -1   # descending bounds
+    assert align(2, 5, rs=rules(*[(i, 1, 0.0, 0.0) for i in range(17)])) == -1   # too many
+    assert align(0, 0, rs=rules((100, 2, 0.0, 0.0), (100, 3, 0.0, 0.1))) == 0    # equal bounds are ascending
+
+    def by_length(n_reads, rs, roff=1, pred=1, mask=1):
+        arr, n = rs
+        return lib.sw_filter_select_by_length(pred, 1, roff, n_reads, arr, n, mask, None)
+    two = rules((100, 2, 0.0, 0.0), (200, 3, 0.0, 0.1))
+    assert by_length(-1, two) == -1 and by_length(0, two) == 0
+    assert by_length(4, two, roff=None) == -1 and by_length(4, two, pred=None) == -1
+    assert by_length(4, rules((100, 2, 0.0, -1.0))) == -1 and by_length(4, rules()) == -1
 
     def select(n_reads, k=3, delta=0.0, pred=1, mask=1):
         return lib.sw_filter_select(pred, 1, n_reads, k, f(0.0), f(delta), mask, None)

@@ -1,7 +1,9 @@
 """Host-side bookkeeping of the learned filter: the choice of (k, tau,
-delta) for a best-hit recall target (filter.calibrate) against a brute
-force that runs the filter oracle's selection and best hit for every grid
-point."""
+delta) for a best-hit recall target (filter.calibrate, and per read-length
+class filter.calibrate_by_length) against brute forces that run the filter
+oracle's selection and best hit for every grid point."""
+import itertools
+
 import numpy as np
 import pytest
 
@@ -72,3 +74,57 @@ def test_oversample_top_against_a_loop(top, times):
         for p in rows[:top]:
             want += [p] * (times - 1)
     np.testing.assert_array_equal(got, np.sort(np.array(want, dtype=np.int64)))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_calibrate_by_length_matches_brute_force(seed):
+    """filter.calibrate_by_length reaches the fewest aligned cells of any
+    per-class choice on its grid (a brute force over every combination, from
+    per-class outcomes that the filter oracle's selection computes), and its
+    rules, run through the oracle's select_by_length, give the cells and
+    recall it reports."""
+    from paper_1304_0681_gb300 import filter as flt
+    rng = np.random.default_rng(100 + seed)
+    nr = 240
+    read_len = rng.choice([50, 100, 300], nr)           # length classes <= 80, <= 112, <= 320
+    counts = rng.integers(0, 12, nr)
+    off = np.zeros(nr + 1, np.int64)
+    np.cumsum(counts, out=off[1:])
+    n = int(off[-1])
+    win_len = rng.integers(100, 400, n)
+    score = rng.integers(0, 6, n)
+    noise = np.where(np.repeat(read_len, counts) > 100, 0.08, 0.25)   # long reads rank better
+    pred = (score / 6.0 + rng.normal(0, 1, n) * noise).astype(np.float32)
+    pred[rng.random(n) < 0.05] = 0.5
+    ks, taus, deltas = (1, 2, 4), [0.0, 0.05], [0.0, 0.1]
+    grid = [(k, t, d) for k in ks for d in deltas for t in taus]
+    true_best = fo.best_per_read(score, off)
+    cells_of = np.repeat(read_len, counts) * win_len
+    per = {}
+    for L in (50, 100, 300):
+        rows = []
+        for k, t, d in grid:
+            sel = fo.select_candidates(pred, off, k, t, d)
+            got = fo.best_per_read(score, off, sel)
+            in_cls = read_len == L
+            miss = int(np.sum((got != true_best) & in_cls))
+            cells = int(cells_of[sel & np.repeat(in_cls, counts)].sum())
+            rows.append((miss, cells))
+        per[L] = rows
+    for target in (0.85, 0.95, 1.0):
+        need = int(np.ceil(target * nr - 1e-9))
+        want = None
+        for combo in itertools.product(range(len(grid)), repeat=3):
+            miss = sum(per[L][i][0] for L, i in zip((50, 100, 300), combo))
+            cells = sum(per[L][i][1] for L, i in zip((50, 100, 300), combo))
+            if nr - miss >= need and (want is None or cells < want):
+                want = cells
+        got = flt.calibrate_by_length(pred, score, off, read_len, win_len, target, ks=ks, taus=taus, deltas=deltas)
+        if want is None:
+            assert got is None
+            continue
+        rules, cells, pairs, recall = got
+        assert cells == want, (target, cells, want)
+        sel = fo.select_by_length(pred, off, read_len, rules)
+        assert int(cells_of[sel].sum()) == cells and int(sel.sum()) == pairs
+        assert float(np.mean(fo.best_per_read(score, off, sel) == true_best)) == recall >= need / nr

@@ -302,6 +302,41 @@ def test_select_and_best_match_oracle():
         np.testing.assert_array_equal(best.cpu().numpy(), fo.best_per_read(score, off, ref))
 
 
+def test_select_by_length_matches_oracle():
+    """sw_filter_select_by_length against the oracle's select_by_length:
+    read lengths on and next to every rule bound, reads past the last bound,
+    reads without candidates, ties; and its argument checks."""
+    import torch
+    from paper_1304_0681_gb300 import _swgb
+    rng = np.random.default_rng(4)
+    nr = 700
+    rules = [(100, 1, 0.0, 0.05), (150, 3, 0.02, 0.0), (400, 2, 0.0, 0.12), (800, 4, 0.05, 0.01)]
+    lengths = rng.choice([75, 99, 100, 101, 149, 150, 151, 399, 400, 401, 800, 801, 3000], nr)
+    counts = rng.integers(0, 30, nr)
+    off = np.zeros(nr + 1, np.int64)
+    np.cumsum(counts, out=off[1:])
+    roff = np.zeros(nr + 1, np.int64)
+    np.cumsum(lengths, out=roff[1:])
+    n = int(off[-1])
+    pred = np.round(rng.uniform(0, 1, n), 2).astype(np.float32)   # exact ties, differences on the bounds
+    dpred, doff, droff = (torch.from_numpy(x).cuda() for x in (pred, off, roff))
+    for rs in (rules, rules[:1], rules[2:], [(0, 2, 0.0, 0.0), (0, 5, 0.0, 0.3)]):
+        mask = torch.full((n,), 9, dtype=torch.uint8, device="cuda")
+        _swgb.sw_filter_select_by_length(dpred, doff, droff, nr, rs, mask)
+        ref = fo.select_by_length(pred.astype(np.float64), off, lengths, rs)
+        np.testing.assert_array_equal(mask.cpu().numpy(), ref.astype(np.uint8), err_msg=str(rs))
+    # one rule needs no read offsets
+    mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    _swgb.sw_filter_select_by_length(dpred, doff, None, nr, rules[1:2], mask)
+    np.testing.assert_array_equal(mask.cpu().numpy().astype(bool), fo.select_candidates(pred, off, 3, 0.02, 0.0))
+    for bad in ([], rules[::-1], [(100, 0, 0.0, 0.0)], [(100, 17, 0.0, 0.0)], [(100, 2, 0.0, -0.5)],
+                [(i, 1, 0.0, 0.0) for i in range(17)]):
+        with pytest.raises(_swgb.SwError):
+            _swgb.sw_filter_select_by_length(dpred, doff, droff, nr, bad, mask)
+    with pytest.raises(_swgb.SwError):   # several rules need the read offsets
+        _swgb.sw_filter_select_by_length(dpred, doff, None, nr, rules, mask)
+
+
 def test_masked_alignment():
     import torch
     import paper_1304_0681_gb300 as sw
@@ -438,8 +473,10 @@ def test_fullmix_workload_full_size_sampled():
     end = b.end.cpu().numpy().reshape(-1, 2)
     best = best.cpu().numpy()
     model = flt.FilterModel(seed=3)
-    res = flt.filtered_best(b, dw.cand_offsets, model, 3, 0.02, SCORING)
+    rules = [(112, 4, 0.02, 0.0), (448, 3, 0.02, 0.001), (flt.ALL_LENGTHS, 2, 0.02, 0.0)]
+    res = flt.filtered_best(b, dw.cand_offsets, model, rules, SCORING)
     fbest, mask = res.best_score.cpu().numpy(), res.mask.cpu().numpy()
+    pred = res.pred.cpu().numpy()
     co = dw.cand_offsets.cpu().numpy()
     span = 1200
     for r0 in (0, dw.n_reads // 2 - span // 2, dw.n_reads - span):
@@ -452,6 +489,10 @@ def test_fullmix_workload_full_size_sampled():
         np.testing.assert_array_equal(score[p0:p1], ref["score"])
         np.testing.assert_array_equal(end[p0:p1, 0], ref["i_end"])
         np.testing.assert_array_equal(end[p0:p1, 1], ref["j_end"])
+        # the selection of these reads, by the rules of their lengths
+        np.testing.assert_array_equal(mask[p0:p1] > 0,
+                                      fo.select_by_length(pred[p0:p1].astype(np.float64), h.cand_offsets,
+                                                          h.read_lengths, rules))
         for r in range(span):
             a, z = h.cand_offsets[r], h.cand_offsets[r + 1]
             assert best[r0 + r] == ref["score"][a:z].max()
@@ -474,7 +515,7 @@ def test_filtered_batches_pipelined():
     # tau = 0: no margin fallback (an untrained network's predictions lie too
     # close together for any positive margin), so reads with more than k
     # candidates align only k of them
-    k, tau = 3, 0.0
+    rules = flt.one_rule(3, 0.0)
     bounds = [0, 300, 301, 700, 1200]
     batches = []
     for a, b in zip(bounds[:-1], bounds[1:]):
@@ -484,14 +525,14 @@ def test_filtered_batches_pipelined():
                                        sub.window_offsets, sub.pair_read, sub.cand_offsets)))
     whole = _batch(wl)
     co = torch.from_numpy(wl.cand_offsets).cuda()
-    res = flt.filtered_best(whole, co, model, k, tau, SCORING)
+    res = flt.filtered_best(whole, co, model, rules, SCORING)
     top = stage_e.top_hits(whole.score, co, wl.n_reads, res.mask)
     torch.cuda.synchronize()
     want = {f: top[f].cpu().numpy() for f in ("best_score", "best_cand", "mapq")}
     n_aligned = int(res.mask.sum().item())
     assert 0 < n_aligned < wl.n_pairs
     for ns in (1, 3):
-        out = flt.filtered_batches(model, batches, k, tau, SCORING, n_streams=ns)
+        out = flt.filtered_batches(model, batches, rules, SCORING, n_streams=ns)
         for f in ("best_score", "best_cand", "mapq"):
             np.testing.assert_array_equal(np.concatenate([getattr(o, f) for o in out]), want[f], err_msg=f)
         assert sum(o.aligned_pairs for o in out) == n_aligned
@@ -499,30 +540,34 @@ def test_filtered_batches_pipelined():
 
 def test_filter_align_in_one_call():
     """sw_filter_align gives the selection, scores, end cells and best hits
-    of the step-by-step filtered search (features, network, selection,
-    masked SW, best hit), with the caller's mask and with the library's."""
+    of the step-by-step filtered search (features, network, selection by
+    read-length rules, masked SW, best hit), with the caller's mask and with
+    the library's; the selection equals the oracle's on the network's own
+    predictions."""
     import torch
 
     from paper_1304_0681_gb300 import _swgb
     from paper_1304_0681_gb300 import filter as flt
-    wl = synth.generate("filter", seed=14, n_reads=600)
+    wl = synth.generate("fullmix", seed=14, n_reads=600)
     model = flt.FilterModel(seed=6)
-    k, tau = 3, 0.0
     co = torch.from_numpy(wl.cand_offsets).cuda()
     b = _batch(wl)
-    # delta: the 30 % quantile of the distances below each read's best
-    # prediction, so that it adds candidates beyond the 3 and leaves others out
+    # deltas: quantiles of the distances below each read's best prediction,
+    # so that they add candidates beyond the k and leave others out
     pred0 = model.forward(flt.features(b, co)).cpu().numpy()
     counts = np.diff(wl.cand_offsets)
     assert counts.min() >= 1
     top = np.maximum.reduceat(pred0, wl.cand_offsets[:-1])
-    delta = float(np.quantile(np.repeat(top, counts) - pred0, 0.3))
-    assert delta > 0
-    res = flt.filtered_best(b, co, model, k, tau, SCORING, delta=delta)
+    gaps = np.repeat(top, counts) - pred0
+    rules = [(112, 3, 0.0, float(np.quantile(gaps, 0.3))), (300, 2, 0.0, float(np.quantile(gaps, 0.1))),
+             (flt.ALL_LENGTHS, 1, 0.0, 0.0)]
+    assert rules[0][3] > 0 and rules[1][3] > 0
+    res = flt.filtered_best(b, co, model, rules, SCORING)
     pred = res.pred.cpu().numpy().astype(np.float64)
-    ref = fo.select_candidates(pred, wl.cand_offsets, k, tau, delta)
+    ref = fo.select_by_length(pred, wl.cand_offsets, wl.read_lengths, rules)
     np.testing.assert_array_equal(res.mask.cpu().numpy().astype(bool), ref)
-    assert ref.sum() > int(np.minimum(counts, k).sum())   # delta added candidates
+    k_of = np.array([fo.rule_for_length(rules, int(m))[1] for m in wl.read_lengths])
+    assert ref.sum() > int(np.minimum(counts, k_of).sum())   # delta added candidates
     torch.cuda.synchronize()
     assert 0 < int(res.mask.sum().item()) < wl.n_pairs
     for own_mask in (True, False):
@@ -531,7 +576,7 @@ def test_filter_align_in_one_call():
         best = torch.full((wl.n_reads,), -7, dtype=torch.int32, device="cuda")
         cand = torch.full_like(best, -7)
         _swgb.sw_filter_align(b2.reads, b2.read_offsets, wl.n_reads, b2.windows, b2.window_offsets, b2.pair_read, co,
-                              wl.n_pairs, model.buf, k, tau, delta, SCORING, b2.score, b2.end, mask, best, cand)
+                              wl.n_pairs, model.buf, rules, SCORING, b2.score, b2.end, mask, best, cand)
         _swgb.sw_get_status()
         assert torch.equal(b2.score, b.score) and torch.equal(b2.end, b.end)
         assert torch.equal(best, res.best_score) and torch.equal(cand, res.best_cand)
@@ -542,7 +587,7 @@ def test_filter_align_in_one_call():
     best = torch.full((3,), 5, dtype=torch.int32, device="cuda")
     cand = torch.full_like(best, 5)
     _swgb.sw_filter_align(b.reads, b.read_offsets, 3, b.windows, b.window_offsets, b.pair_read, zero, 0, model.buf,
-                          k, tau, delta, SCORING, b.score, b.end, None, best, cand)
+                          rules, SCORING, b.score, b.end, None, best, cand)
     torch.cuda.synchronize()
     assert (best == -1).all() and (cand == -1).all()
 
