@@ -225,15 +225,16 @@ FILTER_WORKLOADS = {
 }
 
 
-def _train_filter(name: str, rank: int, n_train: int, n_cal: int, epochs: int):
+def _train_filter(name: str, rank: int, n_train: int, n_cal: int, epochs: int, model_seeds=(1, 2, 3)):
     """The filter network trained on the GPU by the library's own forward,
     backward and Adam kernels, on SW scores the method itself computes for
-    the pairs of another seed of the workload; then selection rules by read
-    length ((k, tau, delta) per length class, fewest aligned cells) picked
-    on a held-out seed for >= 99.7% best-hit recall (the 0.2-point margin
-    over the 99.5% goal absorbs the optimism of picking the cheapest of many
-    settings on the same held-out set).  Not timed as part of a step.
-    Returns (model, rules, facts)."""
+    the pairs of another seed of the workload (one network per seed in
+    model_seeds); then selection rules by read length ((k, tau, delta) per
+    length class, fewest aligned cells) picked on a held-out seed for >=
+    99.7% best-hit recall, and the network whose rules align the fewest
+    cells kept (the 0.2-point margin over the 99.5% goal absorbs the
+    optimism of picking the cheapest of many settings on the same held-out
+    set).  Not timed as part of a step.  Returns (model, rules, facts)."""
     import numpy as np
     import torch
 
@@ -252,32 +253,42 @@ def _train_filter(name: str, rank: int, n_train: int, n_cal: int, epochs: int):
     flt.exhaustive_best(b_tr, co_tr, SCORING)
     feats_tr = flt.features(b_tr, co_tr)
     tgt = flt.targets(b_tr.score, torch.from_numpy(wl_tr.pair_read_lengths).cuda(), SCORING[0])
-    # each read's best candidate four times: weighs the top of the ranking
-    samples = torch.from_numpy(flt.oversample_top(b_tr.score.cpu().numpy(), wl_tr.cand_offsets, 1, 4)).cuda()
-    model = flt.FilterModel(seed=1)
-    model.train(feats_tr, tgt, epochs=1, batch=4096, lr=1e-3, samples=samples)  # loads the kernels (untimed)
-    model = flt.FilterModel(seed=1)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    losses = model.train(feats_tr, tgt, epochs=epochs, batch=4096, lr=1e-3, samples=samples)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t1
+    # each read's three best candidates three times: weighs the top of the ranking
+    samples = torch.from_numpy(flt.oversample_top(b_tr.score.cpu().numpy(), wl_tr.cand_offsets, 3, 3)).cuda()
+    flt.FilterModel(seed=0).train(feats_tr, tgt, epochs=1, batch=4096, lr=1e-3, samples=samples)  # loads the kernels
     n_train_pairs = wl_tr.n_pairs
     n_samples = samples.numel()
-    del b_tr, feats_tr, tgt
     wl_cal, b_cal, co_cal = load(2000 + rank, n_cal)
     flt.exhaustive_best(b_cal, co_cal, SCORING)
-    pred_cal = model.forward(flt.features(b_cal, co_cal)).cpu().numpy()
-    t2 = time.perf_counter()
-    cal = flt.calibrate_by_length(pred_cal, b_cal.score.cpu().numpy().astype(np.int64), wl_cal.cand_offsets,
-                                  wl_cal.read_lengths, wl_cal.window_lengths, 0.997)
-    calib_s = time.perf_counter() - t2
+    feats_cal = flt.features(b_cal, co_cal)
+    score_cal = b_cal.score.cpu().numpy().astype(np.int64)
+    cal_cells = float((wl_cal.pair_read_lengths.astype(np.int64) * wl_cal.window_lengths).sum())
+    # a few networks from different initialisations; the held-out set picks
+    # the one whose calibrated rules align the fewest cells
+    best, tried, calib_s = None, [], 0.0
+    for seed in model_seeds:
+        model = flt.FilterModel(seed=seed)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        losses = model.train(feats_tr, tgt, epochs=epochs, batch=4096, lr=1e-3, samples=samples)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t1
+        pred_cal = model.forward(feats_cal).cpu().numpy()
+        t2 = time.perf_counter()
+        cal = flt.calibrate_by_length(pred_cal, score_cal, wl_cal.cand_offsets, wl_cal.read_lengths,
+                                      wl_cal.window_lengths, 0.997)
+        calib_s += time.perf_counter() - t2
+        share = cal[1] / cal_cells if cal else 1.0
+        tried.append({"seed": seed, "aligned_cells_share": share, "train_s": train_s})
+        if best is None or share < best[0]:
+            best = (share, seed, model, cal, losses, train_s)
+    share, seed, model, cal, losses, train_s = best
     # no setting reached the recall: align every candidate
     rules = cal[0] if cal else flt.one_rule(8, 1.0)
-    del b_cal
-    cal_cells = float((wl_cal.pair_read_lengths.astype(np.int64) * wl_cal.window_lengths).sum())
-    cal = {"rules": rules, "aligned_cells_share": cal[1] / cal_cells, "aligned_pairs_share": cal[2] / wl_cal.n_pairs,
-           "recall": cal[3], "reads": wl_cal.n_reads, "host_s": calib_s} if cal else None
+    del b_tr, feats_tr, tgt, b_cal, feats_cal
+    cal = {"rules": rules, "aligned_cells_share": share, "aligned_pairs_share": cal[2] / wl_cal.n_pairs,
+           "recall": cal[3], "reads": wl_cal.n_reads, "host_s": calib_s, "networks": tried,
+           "chosen_seed": seed} if cal else None
     facts = {"pairs": n_train_pairs, "samples_per_epoch": n_samples, "epochs": epochs, "loss_per_epoch": losses,
              "train_s": train_s, "train_samples_per_s": n_samples * epochs / max(train_s, 1e-9),
              "gradient": "tensor cores (tcgen05), bf16 operands, fp32 accumulation",
