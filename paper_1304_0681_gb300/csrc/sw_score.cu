@@ -386,14 +386,33 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
                 }
                 V hd = diag_in, hu = up_h, f = up_f;
                 uint32_t ck0 = 0, pk0 = 0;  // column key (MODE_I16W: column maximum), pending key
+                // MODE_I16W: each row forms the next row's diagonal term from
+                // its H of the previous column before overwriting it (no copy
+                // of the old H); measured faster in this mode only
+                constexpr bool EARLY_DIAG = MODE == MODE_I16W;
+                V dn = 0;
+                if (EARLY_DIAG) {
+                    const V s0 = (V)prmt(twA, twB, sel[0]);
+                    dn = FMA_ADD ? (V)mad_add((uint32_t)diag_in, one, (uint32_t)s0) : A::add(diag_in, s0);
+                }
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const V s = (V)prmt(twA, twB, sel[r]);
-                    e[r] = A::addmax(e[r], GE, h[r]);
+                    V d;
+                    if (EARLY_DIAG) {
+                        d = dn;
+                        e[r] = A::addmax(e[r], GE, h[r]);
+                        if (r + 1 < R) {
+                            const V s1 = (V)prmt(twA, twB, sel[r + 1]);
+                            dn = FMA_ADD ? (V)mad_add((uint32_t)h[r], one, (uint32_t)s1) : A::add(h[r], s1);
+                        }
+                    } else {
+                        const V s = (V)prmt(twA, twB, sel[r]);
+                        e[r] = A::addmax(e[r], GE, h[r]);
+                        d = FMA_ADD ? (V)mad_add((uint32_t)hd, one, (uint32_t)s) : A::add(hd, s);
+                        hd = h[r];
+                    }
                     f = A::addmax(f, GE, hu);
-                    const V d = FMA_ADD ? (V)mad_add((uint32_t)hd, one, (uint32_t)s) : A::add(hd, s);
                     const V hn = A::addmax_relu(A::max3(d, e[r], f), GO, 0);
-                    hd = h[r];
                     h[r] = hn;
                     hu = hn;
                     uint32_t k0;
