@@ -17,7 +17,12 @@
 // k of a group holds read rows k*R .. k*R+R-1 of the current row chunk in
 // registers and sweeps the window columns; lane k works on column t-k at step
 // t, receiving the row above its block from lane k-1 with one shuffle per
-// value (a wavefront along the anti-diagonal).  Reads longer than T*R are
+// value (a wavefront along the anti-diagonal).  The int16 modes take two
+// columns per step (2(t-k) and 2(t-k)+1, four shuffles): the second column's
+// rows run one row behind the first's, reading the first column's H as its
+// previous column while the first reads the second's of the step before
+// (two register arrays, no copies), so the two columns' F chains -- each
+// row's F, max and ReLU depend on the row above -- overlap.  Reads longer than T*R are
 // processed in chunks of T*R rows; the last lane of a chunk stores its bottom
 // row (H+o, F per column) to global scratch for the first lane of the next
 // chunk.  A warp takes floor(32/T) groups' worth of pairs at a time from a
@@ -148,6 +153,14 @@ __device__ __forceinline__ uint32_t mad_add(uint32_t a, uint32_t one, uint32_t c
 {
     uint32_t d;
     asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(one), "r"(c));
+    return d;
+}
+
+// x >> 16 on the FMA pipe (the high word of x * 65536)
+__device__ __forceinline__ uint32_t hi16_fma(uint32_t x)
+{
+    uint32_t d;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(x), "r"(0x10000u));
     return d;
 }
 
@@ -354,89 +367,181 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
             const V *bin = load_bnd && bnd ? (const V *)(bnd + (c & 1) * bnd_half) : nullptr;
             V *bout = store_bnd && bnd ? (V *)(bnd + ((c + 1) & 1) * bnd_half) : nullptr;
 
+            if constexpr (PAIR2) {
+            // two columns per iteration: column j0 = 2(u - k) from h (its
+            // previous column in h1) and column j0 + 1 from h1, interleaved
+            // one row apart so that their F chains overlap
+            V h1[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) h1[r] = 0;
+            // selectors two rows to a word (prmt reads the low 16 bits; odd
+            // rows are shifted down on the FMA pipe where they are used)
+            uint32_t sel2[(R + 1) / 2];
+#pragma unroll
+            for (int r = 0; r < R; r += 2) sel2[r / 2] = sel[r] | (r + 1 < R ? sel[r + 1] << 16 : 0u);
+            auto selr = [&](int r) -> uint32_t { return (r & 1) ? hi16_fma(sel2[r / 2]) : sel2[r / 2]; };
+            V out_h1 = 0, out_f1 = 0;
+            const int iters = (nw + 1) / 2 + T - 1;
+            auto col_best = [&](const V (&hv)[R], uint32_t ck, int jj) {
+                if constexpr (MODE == MODE_I16) {
+                    const uint32_t nb = __vimax_s16x2_relu(bk0, ck | (TAGM * 0x10001u));
+                    const uint32_t up = nb ^ bk0;
+                    bk0 = nb;
+                    if (up & 0xFFFFu) { rowA = ck; jA = jj; }
+                    if (up > 0xFFFFu) { rowB = ck; jB = jj; }
+                    return;
+                }
+                const uint32_t nb = __vimax_s16x2_relu(bk0, ck);
+                const uint32_t up = nb ^ bk0;
+                bk0 = nb;
+                const bool upA = (up & 0xFFFFu) != 0, upB = up > 0xFFFFu;
+                if (upA || upB) {
+                    const int sl = (upA && upB) ? 0 : (upA ? (slotB ^ 1) : (slotA ^ 1));
+                    uint4 *const dst = snap + sl * R4 * blockDim.x;
+#pragma unroll
+                    for (int q = 0; q < R4; ++q) dst[q * blockDim.x] = quad_of<R>(hv, q);
+                    if (upA) { slotA = sl; jA = jj; }
+                    if (upB) { slotB = sl; jB = jj; }
+                }
+            };
+            for (int u = 0; u < iters; ++u) {
+                const int j0 = 2 * (u - k);
+                V up_h0 = __shfl_up_sync(FULL, out_h, 1);
+                V up_f0 = __shfl_up_sync(FULL, out_f, 1);
+                V up_h1 = __shfl_up_sync(FULL, out_h1, 1);
+                V up_f1 = __shfl_up_sync(FULL, out_f1, 1);
+                if (k == 0) {
+                    up_h0 = bin && j0 < ng ? bin[2 * j0] : 0;
+                    up_f0 = bin && j0 < ng ? bin[2 * j0 + 1] : 0;
+                    up_h1 = bin && j0 + 1 < ng ? bin[2 * j0 + 2] : 0;
+                    up_f1 = bin && j0 + 1 < ng ? bin[2 * j0 + 3] : 0;
+                }
+                uint32_t t0A = 0, t0B = 0, t1A = 0, t1B = 0;
+                if (j0 >= 0) {
+                    if ((j0 & 15) == 0) {
+                        wwA = j0 < pa.n ? load_bases(L.ps.wins, pa.ws + j0, min(16, pa.n - j0)) : 0u;
+                        wwB = j0 < pb.n ? load_bases(L.ps.wins, pb.ws + j0, min(16, pb.n - j0)) : 0u;
+                    }
+                    if (2 * u + 1 < nmin_w) {  // every real pair of the warp has columns j0 and j0 + 1
+                        t0A = s_tab[wwA & 3u];
+                        t1A = s_tab[(wwA >> 2) & 3u];
+                        t0B = s_tab[wwB & 3u];
+                        t1B = s_tab[(wwB >> 2) & 3u];
+                    } else {
+                        t0A = s_tab[j0 < pa.n ? wwA & 3u : 4u];
+                        t1A = s_tab[j0 + 1 < pa.n ? (wwA >> 2) & 3u : 4u];
+                        t0B = s_tab[j0 < pb.n ? wwB & 3u : 4u];
+                        t1B = s_tab[j0 + 1 < pb.n ? (wwB >> 2) & 3u : 4u];
+                    }
+                    wwA >>= 4;
+                    wwB >>= 4;
+                }
+                V hu0 = up_h0, f0 = up_f0, hu1 = up_h1, f1 = up_f1;
+                uint32_t ckA = 0, pkA = 0, ckB = 0, pkB = 0;
+                V d0n, d1n;
+                uint32_t sprev = selr(0);  // selector of the row the second column needs next
+                {
+                    const V s0 = (V)prmt(t0A, t0B, sprev);
+                    const V s1 = (V)prmt(t1A, t1B, sprev);
+                    d0n = FMA_ADD ? (V)mad_add((uint32_t)diag_in, one, (uint32_t)s0) : A::add(diag_in, s0);
+                    d1n = FMA_ADD ? (V)mad_add((uint32_t)up_h0, one, (uint32_t)s1) : A::add(up_h0, s1);
+                }
+#pragma unroll
+                for (int r = 0; r <= R; ++r) {
+                    const uint32_t snext = r + 1 < R ? selr(r + 1) : 0u;
+                    if (r < R) {  // column j0, row r
+                        const V d = d0n;
+                        e[r] = A::addmax(e[r], GE, h1[r]);
+                        if (r + 1 < R) {
+                            const V sn = (V)prmt(t0A, t0B, snext);
+                            d0n = FMA_ADD ? (V)mad_add((uint32_t)h1[r], one, (uint32_t)sn) : A::add(h1[r], sn);
+                        }
+                        f0 = A::addmax(f0, GE, hu0);
+                        const V hn = A::addmax_relu(A::max3(d, e[r], f0), GO, 0);
+                        h[r] = hn;
+                        hu0 = hn;
+                        const uint32_t k0 = MODE == MODE_I16 ? mad_add((uint32_t)hn, 1u << TAGB, (TAGM - (uint32_t)r) * 0x10001u)
+                                                             : (uint32_t)hn;
+                        if (r % 2 == 0) pkA = k0;
+                        else ckA = r == 1 ? __vimax_s16x2_relu(pkA, k0) : __vimax3_s16x2(ckA, pkA, k0);
+                    }
+                    if (r >= 1) {  // column j0 + 1, row r - 1
+                        const int q = r - 1;
+                        const V d = d1n;
+                        e[q] = A::addmax(e[q], GE, h[q]);
+                        if (q + 1 < R) {
+                            const V sn = (V)prmt(t1A, t1B, sprev);  // row q + 1 = r
+                            d1n = FMA_ADD ? (V)mad_add((uint32_t)h[q], one, (uint32_t)sn) : A::add(h[q], sn);
+                        }
+                        f1 = A::addmax(f1, GE, hu1);
+                        const V hn = A::addmax_relu(A::max3(d, e[q], f1), GO, 0);
+                        h1[q] = hn;
+                        hu1 = hn;
+                        const uint32_t k1 = MODE == MODE_I16 ? mad_add((uint32_t)hn, 1u << TAGB, (TAGM - (uint32_t)q) * 0x10001u)
+                                                             : (uint32_t)hn;
+                        if (q % 2 == 0) pkB = k1;
+                        else ckB = q == 1 ? __vimax_s16x2_relu(pkB, k1) : __vimax3_s16x2(ckB, pkB, k1);
+                    }
+                    sprev = snext;
+                }
+                if (R % 2 == 1) {
+                    ckA = R == 1 ? pkA : __vimax_s16x2_relu(ckA, pkA);
+                    ckB = R == 1 ? pkB : __vimax_s16x2_relu(ckB, pkB);
+                }
+                diag_in = up_h1;
+                out_h = hu0;
+                out_f = f0;
+                out_h1 = hu1;
+                out_f1 = f1;
+                if (bout && k == T - 1 && j0 >= 0) {
+                    if (j0 < ng) {
+                        bout[2 * j0] = out_h;
+                        bout[2 * j0 + 1] = out_f;
+                    }
+                    if (j0 + 1 < ng) {
+                        bout[2 * j0 + 2] = out_h1;
+                        bout[2 * j0 + 3] = out_f1;
+                    }
+                }
+                // strict improvement keeps the first column: j0 before j0 + 1
+                col_best(h, ckA, j0);
+                col_best(h1, ckB, j0 + 1);
+            }
+            } else {
+            // int32: one pair per group, one column per step
             for (int t = 0; t < steps; ++t) {
                 const int j = t - k;
                 V up_h = __shfl_up_sync(FULL, out_h, 1);
                 V up_f = __shfl_up_sync(FULL, out_f, 1);
                 if (k == 0) {
-                    if (bin && j < ng) {
-                        up_h = bin[2 * j];
-                        up_f = bin[2 * j + 1];
-                    } else {
-                        up_h = 0;
-                        up_f = 0;
-                    }
+                    up_h = bin && j < ng ? bin[2 * j] : 0;
+                    up_f = bin && j < ng ? bin[2 * j + 1] : 0;
                 }
-                // column tables
-                uint32_t twA = 0, twB = 0;
+                // column table
+                uint32_t twA = 0;
                 if (j >= 0) {
-                    if ((j & 15) == 0) {
-                        wwA = j < pa.n ? load_bases(L.ps.wins, pa.ws + j, min(16, pa.n - j)) : 0u;
-                        if (PAIR2) wwB = j < pb.n ? load_bases(L.ps.wins, pb.ws + j, min(16, pb.n - j)) : 0u;
-                    }
-                    if (t < nmin_w) {  // every real pair of the warp has column j
-                        twA = s_tab[wwA & 3u];
-                        if (PAIR2) twB = s_tab[wwB & 3u];
-                    } else {
-                        twA = s_tab[j < pa.n ? wwA & 3u : 4u];
-                        if (PAIR2) twB = s_tab[j < pb.n ? wwB & 3u : 4u];
-                    }
+                    if ((j & 15) == 0) wwA = j < pa.n ? load_bases(L.ps.wins, pa.ws + j, min(16, pa.n - j)) : 0u;
+                    twA = s_tab[j < pa.n ? wwA & 3u : 4u];
                     wwA >>= 2;
-                    if (PAIR2) wwB >>= 2;
                 }
                 V hd = diag_in, hu = up_h, f = up_f;
-                uint32_t ck0 = 0, pk0 = 0;  // column key (MODE_I16W: column maximum), pending key
-                // MODE_I16W: each row forms the next row's diagonal term from
-                // its H of the previous column before overwriting it (no copy
-                // of the old H); measured faster in this mode only
-                constexpr bool EARLY_DIAG = MODE == MODE_I16W;
-                V dn = 0;
-                if (EARLY_DIAG) {
-                    const V s0 = (V)prmt(twA, twB, sel[0]);
-                    dn = FMA_ADD ? (V)mad_add((uint32_t)diag_in, one, (uint32_t)s0) : A::add(diag_in, s0);
-                }
+                uint32_t ck0 = 0, pk0 = 0;  // column key, pending key
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    V d;
-                    if (EARLY_DIAG) {
-                        d = dn;
-                        e[r] = A::addmax(e[r], GE, h[r]);
-                        if (r + 1 < R) {
-                            const V s1 = (V)prmt(twA, twB, sel[r + 1]);
-                            dn = FMA_ADD ? (V)mad_add((uint32_t)h[r], one, (uint32_t)s1) : A::add(h[r], s1);
-                        }
-                    } else {
-                        const V s = (V)prmt(twA, twB, sel[r]);
-                        e[r] = A::addmax(e[r], GE, h[r]);
-                        d = FMA_ADD ? (V)mad_add((uint32_t)hd, one, (uint32_t)s) : A::add(hd, s);
-                        hd = h[r];
-                    }
+                    const V s = (V)prmt(twA, 0u, sel[r]);
+                    e[r] = A::addmax(e[r], GE, h[r]);
+                    const V d = (V)mad_add((uint32_t)hd, one, (uint32_t)s);  // exact in int32 for any sign
+                    hd = h[r];
                     f = A::addmax(f, GE, hu);
                     const V hn = A::addmax_relu(A::max3(d, e[r], f), GO, 0);
                     h[r] = hn;
                     hu = hn;
-                    uint32_t k0;
-                    if (MODE == MODE_I32) {
-                        k0 = mad_add((uint32_t)hn, 1u << TAGB, TAGM - (uint32_t)r);
-                    } else if (MODE == MODE_I16) {
-                        k0 = mad_add((uint32_t)hn, 1u << TAGB, (TAGM - (uint32_t)r) * 0x10001u);
-                    } else {
-                        k0 = (uint32_t)hn;
-                    }
-                    // three-way max over pairs of rows (H >= 0, so the relu
-                    // max of the first pair is exact)
-                    if (r % 2 == 0) {
-                        pk0 = k0;
-                    } else if (PAIR2) {
-                        ck0 = r == 1 ? __vimax_s16x2_relu(pk0, k0) : __vimax3_s16x2(ck0, pk0, k0);
-                    } else {
-                        ck0 = r == 1 ? max(pk0, k0) : (uint32_t)__vimax3_s32((int)ck0, (int)pk0, (int)k0);
-                    }
+                    const uint32_t k0 = mad_add((uint32_t)hn, 1u << TAGB, TAGM - (uint32_t)r);
+                    // three-way max over pairs of rows
+                    if (r % 2 == 0) pk0 = k0;
+                    else ck0 = r == 1 ? max(pk0, k0) : (uint32_t)__vimax3_s32((int)ck0, (int)pk0, (int)k0);
                 }
-                if (R % 2 == 1) {
-                    if (PAIR2) ck0 = R == 1 ? pk0 : __vimax_s16x2_relu(ck0, pk0);
-                    else ck0 = R == 1 ? pk0 : max(ck0, pk0);
-                }
+                if (R % 2 == 1) ck0 = R == 1 ? pk0 : max(ck0, pk0);
                 diag_in = up_h;
                 out_h = h[R - 1];
                 out_f = f;
@@ -445,36 +550,11 @@ __global__ void __launch_bounds__(128) k_score(const ScoreLaunch L)
                     bout[2 * j + 1] = out_f;
                 }
                 // strict improvement of H keeps the first (smallest) column
-                if (MODE == MODE_I32) {
-                    if (ck0 > (bk0 | TAGM)) {
-                        bk0 = ck0;
-                        jA = j;
-                    }
-                } else if (MODE == MODE_I16) {
-                    // per-half max of (H << TAGB) | TAGM; a half that rose is a
-                    // strict improvement of H (keys are >= 0, so relu max is exact)
-                    const uint32_t nb = __vimax_s16x2_relu(bk0, ck0 | (TAGM * 0x10001u));
-                    const uint32_t up = nb ^ bk0;
-                    bk0 = nb;
-                    if (up & 0xFFFFu) { rowA = ck0; jA = j; }
-                    if (up > 0xFFFFu) { rowB = ck0; jB = j; }
-                } else {
-                    // per-half maximum of H; a half that rose is a strict
-                    // improvement: keep the column for the row search
-                    const uint32_t nb = __vimax_s16x2_relu(bk0, ck0);
-                    const uint32_t up = nb ^ bk0;
-                    bk0 = nb;
-                    const bool upA = (up & 0xFFFFu) != 0, upB = up > 0xFFFFu;
-                    if (upA || upB) {
-                        // one store per step: a slot that the other pair does not point to
-                        const int s = (upA && upB) ? 0 : (upA ? (slotB ^ 1) : (slotA ^ 1));
-                        uint4 *const dst = snap + s * R4 * blockDim.x;
-#pragma unroll
-                        for (int q = 0; q < R4; ++q) dst[q * blockDim.x] = quad_of<R>(h, q);
-                        if (upA) { slotA = s; jA = j; }
-                        if (upB) { slotB = s; jB = j; }
-                    }
+                if (ck0 > (bk0 | TAGM)) {
+                    bk0 = ck0;
+                    jA = j;
                 }
+            }
             }
             // fold the chunk's best into the 64-bit per-lane best
             const int rbase = c * rows_per_chunk + k * R;
