@@ -74,7 +74,7 @@ def _args():
     ap.add_argument("--filter-reads", type=int, default=500_000)
     ap.add_argument("--fullmix-reads", type=int, default=10_000_000, help="reads of the full-mix workload")
     ap.add_argument("--plain-steps", type=int, default=3, help="timed steps of the plain exhaustive arm")
-    ap.add_argument("--e2e-batches", type=int, default=8, help="host batches of the full-mix end-to-end leg")
+    ap.add_argument("--e2e-batches", type=int, default=16, help="host batches of the full-mix end-to-end leg")
     ap.add_argument("--no-extra", action="store_true", help="run the headline section alone")
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuned re-run of the uneven batch")
     ap.add_argument("--no-seeding", action="store_true", help="skip the seeding section")
