@@ -2,20 +2,27 @@
 // tensor cores (tcgen05): 64 -> 256 -> 64 -> 1, bf16 operands, fp32
 // accumulation in tensor memory.
 //
-// One persistent CTA of 4 warps per SM holds both weight matrices in shared
-// memory and takes tiles of 128 pairs:
-//   1. the tile's features (128 x 64 bf16) are copied into shared memory;
-//   2. one thread issues four tcgen05.mma (M 128, N 256, K 16) into TMEM;
-//   3. each warp reads its 32 rows back with tcgen05.ld, adds b1, applies
-//      ReLU, rounds to bf16 and stores them as the next A operand;
-//   4. sixteen tcgen05.mma (M 128, N 64, K 16) compute layer 2 into TMEM;
-//   5. each thread reads its row, adds b2, applies ReLU and takes the dot
-//      product with w3 (+ b3) in fp32.
-// Operands use the K-major layout without swizzle: 8-row x 16-byte core
-// matrices, core matrices along K 128 bytes apart (leading byte offset) and
-// 8-row groups K/8 x 128 bytes apart (stride byte offset).  Completion of the
-// MMAs is signalled through an mbarrier that tcgen05.commit arrives on; every
-// wait on it is bounded and a timeout is reported, never waited out.
+// Forward: one persistent CTA per SM holds both weight matrices in shared
+// memory; two warp groups of 4 warps take alternate tiles of 128 pairs,
+// each with its own 256 TMEM columns, so one group's epilogues run while
+// the other's MMAs keep the tensor core busy.  Per tile:
+//   1. the tile's features (128 x 64 bf16) are copied into the group's
+//      shared-memory buffer;
+//   2. one thread issues five tcgen05.mma (M 128, N 256, K 16; the fifth
+//      carries the bias, see below) into the group's TMEM columns;
+//   3. each warp reads its 32 rows back with tcgen05.ld, applies ReLU,
+//      rounds to bf16 and writes the hidden units back into tensor memory
+//      (tcgen05.st, two to a column);
+//   4. seventeen tcgen05.mma (M 128, N 64, K 16) take that as their A
+//      operand from tensor memory and compute layer 2;
+//   5. each thread reads its row, applies ReLU and takes the dot product
+//      with w3 (+ b3) in fp32.
+// Shared-memory operands use the K-major layout without swizzle: 8-row x
+// 16-byte core matrices, core matrices along K 128 bytes apart (leading
+// byte offset) and 8-row groups K/8 x 128 bytes apart (stride byte offset).
+// Completion of the MMAs is signalled through mbarriers that
+// tcgen05.commit arrives on; every wait on one is bounded and a timeout is
+// reported, never waited out.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -40,16 +47,7 @@ constexpr int64_t TC_WAIT_LIMIT = 1 << 20;  // polls of an mbarrier before givin
 constexpr int FK1 = 64 + 16;                   // layer-1 K
 constexpr int FK2 = 256 + 16;                  // layer-2 K
 
-// shared memory layout (bytes)
-constexpr int SM_W1 = 0;                       // B of layer 1: 256 x FK1 bf16
-constexpr int SM_W2 = SM_W1 + 256 * FK1 * 2;   // B of layer 2: 64 x FK2 bf16
-constexpr int SM_XSZ = 128 * FK1 * 2;          // one X buffer
-constexpr int SM_X = SM_W2 + 64 * FK2 * 2;     // A of layer 1: 2 x (128 x FK1 bf16)
-constexpr int SM_H = SM_X + 2 * SM_XSZ;        // A of layer 2: 128 x FK2 bf16
-constexpr int SM_W3 = SM_H + 128 * FK2 * 2;    // 64 fp32
-constexpr int SM_PART = SM_W3 + 64 * 4;        // 128 fp32 partial dots
-constexpr int SM_BAR = SM_PART + 128 * 4;      // 2 mbarriers (16 B), TMEM base (4 B)
-constexpr int SM_USED = SM_BAR + 64;
+constexpr int SM_XSZ = 128 * FK1 * 2;          // one tile of features (A of layer 1)
 constexpr int SM_TOTAL = 227 * 1024;           // all of it: headroom past the used bytes
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -127,37 +125,93 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// 8 warps.  Tile t's layer-1 accumulator lives in TMEM columns 256 (t % 2) ..
-// +255 and its layer-2 accumulator in the first 64 of them, so the layer-1
-// MMA of tile t+1 runs on the tensor core while the warps finish tile t.
-// Features are double-buffered with asynchronous copies one tile ahead.
+// 16 consecutive 32-bit columns of this warp's 32 TMEM lanes from registers
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// an MMA whose A operand (M 128 rows, one per TMEM lane, K along columns,
+// two bf16 per column) is in tensor memory
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// barrier `id` over the 128 threads of one warp group
+__device__ __forceinline__ void group_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+// and-reduction of a predicate over the 128 threads of a warp group
+__device__ __forceinline__ bool group_and(bool v, int id)
+{
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\tbar.red.and.pred q, %2, 128, p;\n\t"
+        "selp.b32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((int)v), "r"(id)
+        : "memory");
+    return r != 0;
+}
+
+// Two warp groups of 4 warps, each with its own tiles (alternate tiles of
+// the CTA), its own 256 TMEM columns and its own feature buffer, so that one
+// group's epilogues run while the other group's MMAs occupy the tensor core.
+// The hidden layer stays in tensor memory: the group's epilogue reads the
+// layer-1 accumulator (fp32, columns 0..255 of its region), applies ReLU,
+// rounds to bf16 and writes the 256 hidden units two to a column into
+// columns 0..127 of the same region (each column is read before it is
+// overwritten), plus the bias block (ones) in columns 128..135; layer 2
+// then takes its A operand from there and accumulates into columns
+// 192..255.  Shared memory holds only the weights and the feature buffers.
+constexpr int FW_W1 = 0;
+constexpr int FW_W2 = FW_W1 + 256 * FK1 * 2;
+constexpr int FW_X = FW_W2 + 64 * FK2 * 2;       // 2 groups x (128 x FK1 bf16)
+constexpr int FW_W3 = FW_X + 2 * SM_XSZ;
+constexpr int FW_BAR = FW_W3 + 64 * 4;          // 4 mbarriers (bar1, bar2 per group), TMEM base
+constexpr int FW_USED = FW_BAR + 64;
+
 __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restrict__ model,
-                                                           const __nv_bfloat16 *__restrict__ feat, int64_t n,
-                                                           float *__restrict__ out, int32_t *status)
+                                                            const __nv_bfloat16 *__restrict__ feat, int64_t n,
+                                                            float *__restrict__ out, int32_t *status)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, half = warp >> 2;  // TMEM lane quarter, column half
-    float *w3 = reinterpret_cast<float *>(smem + SM_W3);
-    float *part = reinterpret_cast<float *>(smem + SM_PART);  // layer-2 partial dots [128]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + SM_BAR);  // [0] layer 1, [1] layer 2
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM_BAR + 16);
+    const int grp = warp >> 2, quarter = warp & 3, gtid = tid & 127;
+    const int bar_id = 1 + grp;  // named barrier of the group
+    float *w3 = reinterpret_cast<float *>(smem + FW_W3);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + FW_BAR);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + FW_BAR + 32);
     const uint32_t s_base = smem_u32(smem);
-    const uint32_t bar1 = smem_u32(bar), bar2 = smem_u32(bar + 1);
+    const uint32_t bar1 = smem_u32(bar + 2 * grp), bar2 = smem_u32(bar + 2 * grp + 1);
+    const uint32_t xoff = FW_X + grp * SM_XSZ;
 
     {
         const uint4 *g1 = reinterpret_cast<const uint4 *>(model + MD_W1T);  // [256][64] bf16
         const uint4 *g2 = reinterpret_cast<const uint4 *>(model + MD_W2T);  // [64][256] bf16
         for (int c = tid; c < 256 * 8; c += blockDim.x) {
             const int r = c >> 3, k = (c & 7) * 8;
-            *reinterpret_cast<uint4 *>(smem + SM_W1 + kmajor_off(r, k, FK1)) = g1[c];
+            *reinterpret_cast<uint4 *>(smem + FW_W1 + kmajor_off(r, k, FK1)) = g1[c];
         }
         for (int c = tid; c < 64 * 32; c += blockDim.x) {
             const int r = c >> 5, k = (c & 31) * 8;
-            *reinterpret_cast<uint4 *>(smem + SM_W2 + kmajor_off(r, k, FK2)) = g2[c];
+            *reinterpret_cast<uint4 *>(smem + FW_W2 + kmajor_off(r, k, FK2)) = g2[c];
         }
-        // the bias blocks: (hi, lo, 0 ...) in row r of the weights, (1, 1,
-        // 0 ...) in every row of both feature buffers and of the hidden units
         auto bias8 = [](float b) {
             const __nv_bfloat16 hi = __float2bfloat16_rn(b);
             const __nv_bfloat16 lo = __float2bfloat16_rn(b - __bfloat162float(hi));
@@ -166,21 +220,19 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
         };
         const uint4 ones = make_uint4(0x3F803F80u, 0u, 0u, 0u), zero = make_uint4(0u, 0u, 0u, 0u);
         for (int r = tid; r < 256; r += blockDim.x) {
-            *reinterpret_cast<uint4 *>(smem + SM_W1 + kmajor_off(r, 64, FK1)) = bias8(model[MD_B1 + r]);
-            *reinterpret_cast<uint4 *>(smem + SM_W1 + kmajor_off(r, 72, FK1)) = zero;
+            *reinterpret_cast<uint4 *>(smem + FW_W1 + kmajor_off(r, 64, FK1)) = bias8(model[MD_B1 + r]);
+            *reinterpret_cast<uint4 *>(smem + FW_W1 + kmajor_off(r, 72, FK1)) = zero;
         }
         for (int r = tid; r < 64; r += blockDim.x) {
-            *reinterpret_cast<uint4 *>(smem + SM_W2 + kmajor_off(r, 256, FK2)) = bias8(model[MD_B2 + r]);
-            *reinterpret_cast<uint4 *>(smem + SM_W2 + kmajor_off(r, 264, FK2)) = zero;
+            *reinterpret_cast<uint4 *>(smem + FW_W2 + kmajor_off(r, 256, FK2)) = bias8(model[MD_B2 + r]);
+            *reinterpret_cast<uint4 *>(smem + FW_W2 + kmajor_off(r, 264, FK2)) = zero;
             w3[r] = model[MD_W3 + r];
         }
         for (int r = tid; r < TC_ROWS; r += blockDim.x) {
             for (int xb = 0; xb < 2; ++xb) {
-                *reinterpret_cast<uint4 *>(smem + SM_X + xb * SM_XSZ + kmajor_off(r, 64, FK1)) = ones;
-                *reinterpret_cast<uint4 *>(smem + SM_X + xb * SM_XSZ + kmajor_off(r, 72, FK1)) = zero;
+                *reinterpret_cast<uint4 *>(smem + FW_X + xb * SM_XSZ + kmajor_off(r, 64, FK1)) = ones;
+                *reinterpret_cast<uint4 *>(smem + FW_X + xb * SM_XSZ + kmajor_off(r, 72, FK1)) = zero;
             }
-            *reinterpret_cast<uint4 *>(smem + SM_H + kmajor_off(r, 256, FK2)) = ones;
-            *reinterpret_cast<uint4 *>(smem + SM_H + kmajor_off(r, 264, FK2)) = zero;
         }
     }
     if (warp == 0) {
@@ -188,157 +240,139 @@ __global__ void __launch_bounds__(256, 1) k_mlp_forward_tc(const float *__restri
                      "r"(TC_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar2));
-    }
-    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
-    // the features of one tile into X buffer xb (rows past n read as zero)
-    auto load_x = [&](int64_t tile, int xb) {
-        const int64_t row0 = tile * TC_ROWS;
-        const uint4 *g = reinterpret_cast<const uint4 *>(feat);
-        for (int c = tid; c < TC_ROWS * 8; c += blockDim.x) {
-            const int r = c >> 3, k = (c & 7) * 8;
-            const bool in = row0 + r < n;
-            cp_async16(s_base + SM_X + xb * SM_XSZ + kmajor_off(r, k, FK1), g + (in ? (row0 + r) * 8 + (c & 7) : 0),
-                       in ? 16u : 0u);
-        }
-        cp_async_commit();
-    };
-    int64_t tile = blockIdx.x;
-    if (tile < tiles) load_x(tile, 0);
-    fence_async_smem();
+    if (tid < 4) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + tid)));
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
+    const uint32_t region = tmem + 256u * (uint32_t)grp;            // this group's 256 columns
+    const uint32_t lane_q = (uint32_t)(32 * quarter) << 16;         // this warp's TMEM lanes
     const float b3 = model[MD_B3];
-    uint32_t ph1 = 0, ph2 = 0;
-    bool ok = true;
-    // commits not yet seen complete (every thread tracks them alike): at most
-    // one on each barrier, waited for again before the tensor memory is freed
-    bool pend1 = false, pend2 = false;
-    uint32_t pph1 = 0, pph2 = 0;
-    auto layer1 = [&](int xb, uint32_t acc) {
+    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    const int64_t stride = 2 * (int64_t)gridDim.x;
+    // the features of one tile into the group's buffer (rows past n read as zero)
+    auto load_x = [&](int64_t tile) {
+        const int64_t row0 = tile * TC_ROWS;
+        const uint4 *g = reinterpret_cast<const uint4 *>(feat);
+        for (int c = gtid; c < TC_ROWS * 8; c += 128) {
+            const int r = c >> 3, k = (c & 7) * 8;
+            const bool in = row0 + r < n;
+            cp_async16(s_base + xoff + kmajor_off(r, k, FK1), g + (in ? (row0 + r) * 8 + (c & 7) : 0), in ? 16u : 0u);
+        }
+        cp_async_commit();
+    };
+    auto layer1 = [&]() {
 #pragma unroll
         for (int ks = 0; ks < FK1 / 16; ++ks)
-            mma_bf16(acc, smem_desc(s_base + SM_X + xb * SM_XSZ + 256 * ks, 128, FK1 / 8 * 128),
-                     smem_desc(s_base + SM_W1 + 256 * ks, 128, FK1 / 8 * 128), idesc_bf16(128, 256), ks > 0);
+            mma_bf16(region, smem_desc(s_base + xoff + 256 * ks, 128, FK1 / 8 * 128),
+                     smem_desc(s_base + FW_W1 + 256 * ks, 128, FK1 / 8 * 128), idesc_bf16(128, 256), ks > 0);
         mma_commit(bar1);
     };
-    auto wait_all = [&](uint32_t bar, uint32_t &ph, bool &pend, uint32_t &pph) -> bool {
+    uint32_t ph1 = 0, ph2 = 0;
+    bool ok = true, pend1 = false, pend2 = false;
+    uint32_t pph1 = 0, pph2 = 0;
+    auto wait_group = [&](uint32_t b, uint32_t &ph, bool &pend, uint32_t &pph) -> bool {
         pph = ph;
-        const bool got = mbar_wait(bar, ph);
+        const bool got = mbar_wait(b, ph);
         ph ^= 1u;
-        const bool all = __syncthreads_and(got) != 0;
+        const bool all = group_and(got, bar_id);
         pend = !all;
         return all;
     };
 
-    // tile `tile` uses X buffer xb and accumulator columns 256 * xb
-    int xb = 0;
+    int64_t tile = blockIdx.x + (int64_t)grp * gridDim.x;
     if (tile < tiles) {
+        load_x(tile);
         cp_async_wait_all();
         fence_async_smem();
-        __syncthreads();
-        if (tid == 0) layer1(0, tmem);
+        group_sync(bar_id);
+        if (gtid == 0) layer1();
         pend1 = true;
         pph1 = ph1;
     }
-    for (; tile < tiles && ok; tile += gridDim.x, xb ^= 1) {
-        const int64_t next = tile + gridDim.x;
-        const uint32_t acc = tmem + 256u * (uint32_t)xb;
-        // the next tile's features, while this one computes
-        if (next < tiles) load_x(next, xb ^ 1);
-        ok = wait_all(bar1, ph1, pend1, pph1);  // layer 1 of this tile
+    for (; tile < tiles && ok; tile += stride) {
+        const int64_t next = tile + stride;
+        ok = wait_group(bar1, ph1, pend1, pph1);  // layer 1 of this tile: the feature buffer is free again
         fence_after_sync();
         if (!ok) break;
-        // h = bf16(relu(D)) (the bias is in D): warp (quarter, half) takes 32
-        // rows x 128 columns, 64 columns per tensor-memory round trip
-        {
-            const int r = 32 * quarter + lane;
-            const uint32_t la = acc + ((uint32_t)(32 * quarter) << 16);
+        if (next < tiles) load_x(next);
+        // hidden units: relu(D) as bf16, two to a column, into columns 0..127
 #pragma unroll 1
-            for (int c0 = 128 * half; c0 < 128 * half + 128; c0 += 64) {
-                uint32_t v[4][16];
+        for (int c0 = 0; c0 < 256; c0 += 64) {
+            uint32_t v[4][16];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) tmem_ld16(la + (uint32_t)(c0 + 16 * q), v[q]);
-                tmem_wait_ld();
+            for (int q = 0; q < 4; ++q) tmem_ld16(region + lane_q + (uint32_t)(c0 + 16 * q), v[q]);
+            tmem_wait_ld();
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint32_t pk[8];
+            for (int h2 = 0; h2 < 2; ++h2) {
+                uint32_t pk[16];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(__uint_as_float(v[q][2 * j]), 0.f),
-                                                                       fmaxf(__uint_as_float(v[q][2 * j + 1]), 0.f));
-                        pk[j] = *reinterpret_cast<const uint32_t *>(&h);
-                    }
-                    const int c = c0 + 16 * q;
-                    *reinterpret_cast<uint4 *>(smem + SM_H + kmajor_off(r, c, FK2)) =
-                        make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    *reinterpret_cast<uint4 *>(smem + SM_H + kmajor_off(r, c + 8, FK2)) =
-                        make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                for (int j = 0; j < 16; ++j) {
+                    const int q = 2 * h2 + (j >> 3), e = 2 * (j & 7);
+                    const __nv_bfloat162 hh = __floats2bfloat162_rn(fmaxf(__uint_as_float(v[q][e]), 0.f),
+                                                                    fmaxf(__uint_as_float(v[q][e + 1]), 0.f));
+                    pk[j] = *reinterpret_cast<const uint32_t *>(&hh);
                 }
+                tmem_st16(region + lane_q + (uint32_t)(c0 / 2 + 16 * h2), pk);
             }
         }
-        // the next tile's features have landed (each thread waits for its own
-        // copies; the barrier below publishes them)
+        {
+            const uint32_t bias_blk[8] = {0x3F803F80u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+            tmem_st8(region + lane_q + 128u, bias_blk);
+        }
+        tmem_wait_st();
+        fence_before_sync();
+        group_sync(bar_id);
+        fence_after_sync();
+        if (gtid == 0) {
+#pragma unroll
+            for (int ks = 0; ks < FK2 / 16; ++ks)
+                mma_bf16_ta(region + 192u, region + (uint32_t)(8 * ks),
+                            smem_desc(s_base + FW_W2 + 256 * ks, 128, FK2 / 8 * 128), idesc_bf16(128, 64), ks > 0);
+            mma_commit(bar2);
+        }
+        pend2 = true;
+        pph2 = ph2;
+        ok = wait_group(bar2, ph2, pend2, pph2);
+        fence_after_sync();
+        if (!ok) break;
+        // y = w3 . relu(D) + b3: each thread its row, all 64 columns
+        {
+            float acc = 0.f;
+            uint32_t v[4][16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tmem_ld16(region + lane_q + 192u + (uint32_t)(16 * q), v[q]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc += fmaxf(__uint_as_float(v[q][j]), 0.f) * w3[16 * q + j];
+            const int64_t row = tile * TC_ROWS + 32 * quarter + lane;
+            if (row < n) out[row] = acc + b3;
+        }
+        // the next tile's features have landed; its layer 1 may now overwrite the region
         cp_async_wait_all();
         fence_async_smem();
         fence_before_sync();
-        __syncthreads();
+        group_sync(bar_id);
         fence_after_sync();
-        if (tid == 0) {
-            // layer 2 of this tile (first 64 columns of its accumulator), then
-            // layer 1 of the next tile into the other accumulator
-#pragma unroll
-            for (int ks = 0; ks < FK2 / 16; ++ks)
-                mma_bf16(acc, smem_desc(s_base + SM_H + 256 * ks, 128, FK2 / 8 * 128),
-                         smem_desc(s_base + SM_W2 + 256 * ks, 128, FK2 / 8 * 128), idesc_bf16(128, 64), ks > 0);
-            mma_commit(bar2);
-            if (next < tiles) layer1(xb ^ 1, tmem + 256u * (uint32_t)(xb ^ 1));
-        }
         if (next < tiles) {
+            if (gtid == 0) layer1();
             pend1 = true;
             pph1 = ph1;
         }
-        ok = wait_all(bar2, ph2, pend2, pph2);
-        fence_after_sync();
-        if (!ok) break;
-        // y = w3 . relu(D) + b3 (the bias b2 is in D): warp (quarter, half)
-        // sums 32 of the 64 columns
-        {
-            float accv = 0.f;
-            const uint32_t la = acc + ((uint32_t)(32 * quarter) << 16);
-            uint32_t v[2][16];
-            tmem_ld16(la + (uint32_t)(32 * half), v[0]);
-            tmem_ld16(la + (uint32_t)(32 * half + 16), v[1]);
-            tmem_wait_ld();
-#pragma unroll
-            for (int q = 0; q < 2; ++q)
-#pragma unroll
-                for (int j = 0; j < 16; ++j) accv += fmaxf(__uint_as_float(v[q][j]), 0.f) * w3[32 * half + 16 * q + j];
-            const int r = 32 * quarter + lane;
-            if (half == 1) part[r] = accv;
-            fence_before_sync();
-            __syncthreads();
-            fence_after_sync();
-            const int64_t row = tile * TC_ROWS + r;
-            if (half == 0 && row < n) out[row] = accv + part[r] + b3;
-        }
     }
-    if (!ok && tid == 0) atomicOr(status, ST_TIMEOUT);
-    // a wait that ran out, or a break after one, can leave tensor-core work
-    // in flight: wait for it once more (bounded) before the memory is freed
-    if (pend1) __syncthreads_and(mbar_wait(bar1, pph1));
-    if (pend2) __syncthreads_and(mbar_wait(bar2, pph2));
+    if (!ok && gtid == 0) atomicOr(status, ST_TIMEOUT);
+    // a wait that ran out can leave tensor-core work in flight: wait for it
+    // once more (bounded) before the memory is freed
+    if (pend1) group_and(mbar_wait(bar1, pph1), bar_id);
+    if (pend2) group_and(mbar_wait(bar2, pph2), bar_id);
     cp_async_wait_all();
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
-
 
 // ------------------------------------------------------------------ training
 //
@@ -704,12 +738,12 @@ int launch_mlp_forward_tc(const float *model, const uint16_t *feat, int64_t n, f
     // per call: the attribute belongs to the current device, and calls may
     // come from several host threads at once
     if (cuda_failed(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SM_TOTAL)))
+                                         FW_USED)))
         return SW_ERR_CUDA;
-    static_assert(SM_USED <= SM_TOTAL, "shared memory layout");
+    static_assert(FW_USED <= SM_TOTAL, "shared memory layout");
     const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, sm_count));
-    k_mlp_forward_tc<<<grid, 256, SM_TOTAL, st>>>(model, reinterpret_cast<const __nv_bfloat16 *>(feat), n, out,
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + 1) / 2, sm_count));
+    k_mlp_forward_tc<<<grid, 256, FW_USED, st>>>(model, reinterpret_cast<const __nv_bfloat16 *>(feat), n, out,
                                                    status);
     count_launch();
     return launch_status();
