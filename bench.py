@@ -225,7 +225,7 @@ FILTER_WORKLOADS = {
 }
 
 
-def _train_filter(name: str, rank: int, n_train: int, n_cal: int, epochs: int, model_seeds=(1, 2, 3)):
+def _train_filter(name: str, rank: int, n_train: int, n_cal: int, epochs: int, model_seeds=(1, 2, 3, 4, 5, 6)):
     """The filter network trained on the GPU by the library's own forward,
     backward and Adam kernels, on SW scores the method itself computes for
     the pairs of another seed of the workload (one network per seed in
