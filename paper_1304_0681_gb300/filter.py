@@ -286,9 +286,9 @@ def calibrate(pred: np.ndarray, score: np.ndarray, cand_offsets: np.ndarray, rec
 LENGTH_BOUNDS = (80, 112, 160, 224, 320, 448, 640, 896, 1280, 1792, 2560)
 
 
-def _selection_table(pred, score, cand_offsets, ks, taus, deltas):
+def _selection_table(pred, score, cand_offsets, pair_cells, ks, taus, deltas):
     """For every grid point (k, tau, delta): per read whether the selection
-    keeps a best-scoring candidate, and the mask of selected pairs."""
+    keeps a best-scoring candidate, and the cells and pairs it aligns."""
     nr = len(cand_offsets) - 1
     counts = np.diff(cand_offsets)
     rid = np.repeat(np.arange(nr), counts)
@@ -299,6 +299,7 @@ def _selection_table(pred, score, cand_offsets, ks, taus, deltas):
     top_pred = np.full(nr, -np.inf, np.float32)
     top_pred[rid[rank == 0]] = pred[rank == 0]
     below_top = top_pred[rid] - pred
+    all_cells = np.bincount(rid, weights=pair_cells, minlength=nr)
     for k in ks:
         sel_pred = np.full(nr, -np.inf, np.float32)
         nxt_pred = np.full(nr, -np.inf, np.float32)
@@ -309,10 +310,13 @@ def _selection_table(pred, score, cand_offsets, ks, taus, deltas):
         for delta in deltas:
             kept = (rank < k) | (below_top < np.float32(delta))
             kept_best = _segment_max(np.where(kept, score, -1), cand_offsets, counts)
+            kept_cells = np.bincount(rid[kept], weights=pair_cells[kept], minlength=nr)
+            kept_pairs = np.bincount(rid[kept], minlength=nr)
             for tau in taus:
                 fall = (counts <= k) | (gap < np.float32(tau))
                 hit = np.where(fall, true_best, kept_best) == true_best
-                yield (k, float(tau), float(delta)), hit, kept | fall[rid], rid
+                yield ((k, float(tau), float(delta)), hit, np.where(fall, all_cells, kept_cells),
+                       np.where(fall, counts, kept_pairs))
 
 
 def calibrate_by_length(pred: np.ndarray, score: np.ndarray, cand_offsets: np.ndarray, read_lengths: np.ndarray,
@@ -343,15 +347,17 @@ def calibrate_by_length(pred: np.ndarray, score: np.ndarray, cand_offsets: np.nd
     max_miss = nr - need
     if max_miss < 0:
         return None
-    pair_cells = read_lengths[np.repeat(np.arange(nr), np.diff(cand_offsets))] * np.asarray(window_lengths, np.int64)
+    pair_cells = (read_lengths[np.repeat(np.arange(nr), np.diff(cand_offsets))] *
+                  np.asarray(window_lengths, np.int64)).astype(np.float64)
     # per class and grid point: missed reads, aligned cells, aligned pairs
     opts = {c: [] for c in range(n_cls) if np.any(cls == c)}
-    for key, hit, sel, rid in _selection_table(pred, score, cand_offsets, ks, taus or [0.0], deltas):
+    for key, hit, cells_r, pairs_r in _selection_table(pred, score, cand_offsets, pair_cells, ks, taus or [0.0],
+                                                       deltas):
         miss = np.bincount(cls[~hit], minlength=n_cls)
-        cells = np.bincount(cls[rid[sel]], weights=pair_cells[sel], minlength=n_cls)
-        pairs = np.bincount(cls[rid[sel]], minlength=n_cls)
+        cells = np.bincount(cls, weights=cells_r, minlength=n_cls)
+        pairs = np.bincount(cls, weights=pairs_r, minlength=n_cls)
         for c in opts:
-            opts[c].append((int(miss[c]), float(cells[c]), int(pairs[c]), key))
+            opts[c].append((int(miss[c]), float(cells[c]), int(round(pairs[c])), key))
     # dynamic program: best[b] = fewest cells over the classes so far with b misses
     INF = float("inf")
     best = np.full(max_miss + 1, INF)
