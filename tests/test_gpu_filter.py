@@ -124,6 +124,29 @@ def test_forward_matches_oracle():
     np.testing.assert_allclose(got, ref, rtol=1e-2, atol=1e-3)
 
 
+def test_forward_with_many_tiles_per_warp_group():
+    """The tensor-memory forward when each of a CTA's two warp groups takes
+    several tiles (its mbarrier phases wrap, its tensor-memory columns and
+    feature buffer are reused) and the last tile is ragged: every row
+    against the oracle on the bf16-rounded network."""
+    import torch
+    from paper_1304_0681_gb300 import filter as flt
+    rng = np.random.default_rng(12)
+    model = flt.FilterModel(seed=4)
+    n = 152 * 128 * 2 * 3 + 77
+    x = rng.uniform(0, 0.4, (n, 64))
+    xb = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).cuda().view(torch.int16)
+    got = model.forward(xb).cpu().numpy()
+    import paper_1304_0681_gb300 as sw
+    sw._swgb.sw_sync_status()
+    P = _model_params(model)
+    Pb = fo.Params(fo.bf16_round(P.W1), P.b1, fo.bf16_round(P.W2), P.b2, P.w3, P.b3)
+    X = fo.bf16_round(x)
+    a1 = fo.bf16_round(np.maximum(X @ Pb.W1 + Pb.b1, 0))
+    ref = np.maximum(a1 @ Pb.W2 + Pb.b2, 0) @ Pb.w3 + Pb.b3
+    np.testing.assert_allclose(got, ref, rtol=1e-2, atol=1e-3)
+
+
 @pytest.fixture
 def grad_kernel():
     """Select a gradient kernel for one test, and restore the default."""
