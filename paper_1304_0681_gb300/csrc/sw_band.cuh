@@ -41,28 +41,30 @@ __device__ __forceinline__ Band band_of(int32_t score, int32_t ie, int32_t je, c
 
 // Traceback sort key of a pair of class cls (class-major): pairs whose
 // one-lane slab exceeds small_slab_words first, then the rest, each by
-// falling cost (rows x chunk window, ~19 % and ~9 % buckets).  Also the
-// one-lane slab words (need) and chunk window (wc) the launch sizing uses.
-// score <= 0: no alignment (cost 1, need 0).
+// falling chunk window (~9 % and ~4 % buckets).  A warp sweeps the widest
+// window of its pairs at every chunk, so pairs of one task should share the
+// width: sorted by it, a task of the 1M-pair batch of 100 x 200 pairs
+// sweeps 1.07x the cells of its pairs' own windows, against 1.24x sorted by
+// rows x width.  Also the one-lane slab words (need) and chunk window (wc)
+// the launch sizing uses.  score <= 0: no alignment (width 0, need 0).
 __device__ __forceinline__ void tb_cost_key(int cls, int32_t score, int32_t ie, int32_t je, int32_t small_slab_words,
                                             const Scoring &sc, int32_t &key, int32_t &need32, int32_t &wc, bool &big)
 {
     int64_t need = 0;
-    float cost = 1.f;
     wc = 0;
     if (score > 0) {
         const Band t = band_of(score, ie, je, sc);
         const int32_t w = min(t.W, 8 + (t.b - t.a));
         need = (int64_t)((t.rows + 7) / 8) * w;
-        cost = (float)t.rows * (float)w;
         wc = w;
     }
+    const float lw = __log2f((float)(wc > 1 ? wc : 1));
     big = need > small_slab_words;
     if (big) {
-        const int cb = min(63, max(0, (int)(4.f * __log2f(cost)) - 40));
+        const int cb = min(63, max(0, (int)(8.f * lw) - 32));
         key = cls * N_NBUCKET + (63 - cb);
     } else {
-        const int cb = min(191, max(0, (int)(8.f * __log2f(cost))));
+        const int cb = min(191, max(0, (int)(16.f * lw)));
         key = cls * N_NBUCKET + 64 + (191 - cb);
     }
     need32 = (int32_t)(need < (int64_t)INT32_MAX ? need : (int64_t)INT32_MAX);
